@@ -1,0 +1,309 @@
+"""Pins for the oracle: closed forms, invariants, an independent dense route.
+
+Every check here ties ``oracle/`` to something other than itself: textbook
+states (Bell, GHZ, QFT of basis states), norm and echo invariants, the dense
+Kronecker/expm construction of ``oracle/dense.py``, exact diagonalisation,
+the free-fermion closed form of the open TFIM, and finite differences.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dense, sv
+from oracle.adam import adam_step
+from workloads import Circuit, PAULI_DTYPE, pauli_terms
+from workloads import generators as gen
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+
+def ir(c):
+    return c.to_ir()
+
+
+# ---------------------------------------------------------------- conventions
+def test_little_endian_qubit_order():
+    for q in range(5):
+        c = Circuit(5).x(q)
+        g, p = ir(c)
+        psi = sv.apply(5, g, p, None)
+        assert psi[1 << q] == 1 and np.count_nonzero(psi) == 1
+
+
+def test_gate_matrices_match_generator_route():
+    """Closed-form entries of every gate == expm/projector construction."""
+    rng = np.random.default_rng(5)
+    names1 = ["I", "X", "Y", "Z", "H", "S", "T", "RX", "RY", "RZ"]
+    names2 = ["CX", "CZ", "CP", "SWAP", "RZZ"]
+    for name in names1 + names2:
+        for _ in range(3):
+            th = rng.uniform(-4, 4)
+            c = Circuit(2)
+            qs = (0,) if name in names1 else (1, 0)
+            if name in ("RX", "RY", "RZ", "CP", "RZZ"):
+                c.add(name, qs, param=0, scale=0.7, angle0=0.1)
+            else:
+                c.add(name, qs)
+            g, p = ir(c)
+            params = np.array([th])
+            M = sv.gate_matrix(g[0], p, params)
+            n = len(qs)
+            g1 = g.copy()
+            if n == 2:
+                g1["q"][0][:2] = (1, 0)
+            D = dense.gate_operator(n, g1[0], p, params)
+            np.testing.assert_allclose(M, D, atol=1e-14)
+
+
+# ------------------------------------------------------------- textbook states
+def test_bell_and_ghz():
+    c = Circuit(2).h(0).cx(0, 1)
+    psi = sv.apply(2, *ir(c), None)
+    np.testing.assert_allclose(psi, [2 ** -0.5, 0, 0, 2 ** -0.5], atol=1e-15)
+    n = 7
+    c = Circuit(n).h(0)
+    for q in range(n - 1):
+        c.cx(q, q + 1)
+    psi = sv.apply(n, *ir(c), None)
+    ref = np.zeros(1 << n, complex)
+    ref[0] = ref[-1] = 2 ** -0.5
+    np.testing.assert_allclose(psi, ref, atol=1e-14)
+
+
+def qft_circuit(n):
+    c = Circuit(n)
+    for a in range(n - 1, -1, -1):
+        c.h(a)
+        for b in range(a - 1, -1, -1):
+            c.cp(b, a, angle=math.pi / (1 << (a - b)))
+    for i in range(n // 2):
+        c.swap(i, n - 1 - i)
+    return c
+
+
+@pytest.mark.parametrize("n", [3, 5, 6])
+def test_qft_of_basis_states(n):
+    """QFT|j> = N^-1/2 sum_k e^{2 pi i j k / N} |k>: uniform magnitudes, known phases."""
+    N = 1 << n
+    g, p = ir(qft_circuit(n))
+    for j in [0, 1, 3, N - 1, N // 2 + 1]:
+        psi0 = np.zeros(N, complex)
+        psi0[j] = 1
+        psi = sv.apply(n, g, p, None, psi=psi0)
+        k = np.arange(N)
+        ref = np.exp(2j * math.pi * j * k / N) / math.sqrt(N)
+        np.testing.assert_allclose(psi, ref, atol=1e-13)
+
+
+# ----------------------------------------------------------------- invariants
+def inverse_circuit(c):
+    inv = Circuit(c.n)
+    for (name, qubits, param, scale, angle0, mat) in reversed(c.ops):
+        if name in ("RX", "RY", "RZ", "RZZ", "CP"):
+            inv.add(name, qubits, param=param, scale=-scale, angle0=-angle0)
+        elif name in ("U1", "U2", "UK"):
+            inv.unitary(qubits, mat.conj().T)
+        elif name == "S":
+            inv.unitary(qubits, np.diag([1, -1j]))
+        elif name == "T":
+            inv.unitary(qubits, np.diag([1, np.exp(-1j * math.pi / 4)]))
+        else:
+            inv.add(name, qubits)
+    inv.n_params = c.n_params
+    return inv
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_norm_and_echo(seed):
+    n = 8
+    c, th = gen.random_circuit(n, 150, seed=seed)
+    psi0 = gen.random_state(n, seed + 10)
+    psi = sv.apply(n, *ir(c), th, psi=psi0)
+    assert abs(np.linalg.norm(psi) - 1) < 1e-13
+    back = sv.apply(n, *ir(inverse_circuit(c)), th, psi=psi)
+    np.testing.assert_allclose(back, psi0, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_against_dense_kron_route(seed):
+    n = 6
+    c, th = gen.random_circuit(n, 60, seed=seed)
+    g, p = ir(c)
+    psi = sv.apply(n, g, p, th)
+    ref = dense.run(n, g, p, th)
+    np.testing.assert_allclose(psi, ref, atol=1e-12)
+
+
+# ------------------------------------------------------------------ config 1
+def test_ry_cx_ladder_is_real_and_theta0_values():
+    c, th = gen.ry_cx_ladder(10, 4, seed=0)
+    g, p = ir(c)
+    psi = sv.apply(10, g, p, th)
+    assert np.all(psi.imag == 0.0)
+    psi0 = sv.apply(10, g, p, np.zeros_like(th))
+    terms = gen.tfim_terms(10, 1.0, 1.0)
+    zz = pauli_terms([{0: "Z", 1: "Z"}])
+    assert abs(sv.expect(10, psi0, zz)[0] - 1) < 1e-14
+    assert abs(sv.energy(10, g, p, np.zeros_like(th), terms) + 9) < 1e-13
+
+
+def test_product_state_closed_form_energy_and_gradient():
+    """No CX: <Z_i> = cos t_i, <X_i> = sin t_i with t_i = sum_l theta[l, i]."""
+    n, L, gfield = 6, 3, 0.8
+    rng = np.random.default_rng(3)
+    th = rng.uniform(-math.pi, math.pi, (L, n))
+    c = Circuit(n)
+    for l in range(L):
+        for q in range(n):
+            c.ry(q, param=l * n + q)
+    g, p = ir(c)
+    terms = gen.tfim_terms(n, 1.0, gfield)
+    t = th.sum(0)
+    E = -np.sum(np.cos(t[:-1]) * np.cos(t[1:])) - gfield * np.sum(np.sin(t))
+    assert abs(sv.energy(n, g, p, th.ravel(), terms) - E) < 1e-13
+    dE = np.zeros(n)
+    for i in range(n):
+        if i > 0:
+            dE[i] += np.sin(t[i]) * np.cos(t[i - 1])
+        if i < n - 1:
+            dE[i] += np.sin(t[i]) * np.cos(t[i + 1])
+        dE[i] -= gfield * np.cos(t[i])
+    ps = sv.grad_param_shift(n, g, p, th.ravel(), terms)
+    np.testing.assert_allclose(ps, np.tile(dE, L), atol=1e-12)
+
+
+# ------------------------------------------------------------------ observables
+def test_pauli_y_phase_and_z_basis_signs():
+    c = Circuit(1).h(0).s(0)            # (|0> + i|1>)/sqrt2
+    psi = sv.apply(1, *ir(c), None)
+    assert abs(sv.expect(1, psi, pauli_terms([{0: "Y"}]))[0] - 1) < 1e-15
+    n = 5
+    for x in [0, 5, 31, 18]:
+        psi = np.zeros(1 << n, complex)
+        psi[x] = 1
+        z = pauli_terms([{0: "Z", 2: "Z", 4: "Z"}])
+        sign = (-1) ** bin(x & 0b10101).count("1")
+        assert sv.expect(n, psi, z)[0] == sign
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_expectations_and_h_apply_against_dense(seed):
+    n = 6
+    psi = gen.random_state(n, seed)
+    strings = gen.random_pauli_strings(n, 20, weight=3, seed=seed)
+    vals = sv.expect(n, psi, strings)
+    for s, v in zip(strings, vals):
+        P = dense.pauli_operator(n, s["xmask"], s["zmask"])
+        assert abs(np.vdot(psi, P @ psi) - v) < 1e-13
+        assert abs(v.imag) < 1e-13
+    terms = gen.xxz_terms(n, np.linspace(0.5, 1.5, n - 1), 0.7, 0.4)
+    Hd = dense.hamiltonian_matrix(n, terms)
+    np.testing.assert_allclose(sv.hamiltonian_apply(n, psi, terms), Hd @ psi, atol=1e-13)
+
+
+# ------------------------------------------------------------- exact energies
+def test_free_fermion_special_cases():
+    assert abs(dense.tfim_ground_energy_free_fermion([], [0.7]) + 0.7) < 1e-15
+    J = np.array([0.6, 1.2, 0.9])
+    g = np.array([0.3, 0.5, 1.1, 0.2])
+    assert abs(dense.tfim_ground_energy_free_fermion(np.zeros(3), g) + g.sum()) < 1e-14
+    assert abs(dense.tfim_ground_energy_free_fermion(J, np.zeros(4)) + J.sum()) < 1e-14
+
+
+def test_critical_open_chain_closed_form():
+    """J = g = 1 open chain: E0(N) = 1 - csc(pi / (4N + 2))."""
+    for N in [1, 2, 3, 10, 40, 400]:
+        ref = 1 - 1 / math.sin(math.pi / (4 * N + 2))
+        assert abs(dense.tfim_ground_energy_free_fermion(np.ones(N - 1), np.ones(N)) - ref) < 1e-9 * N
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8, 10])
+def test_ed_equals_free_fermion(n):
+    rng = np.random.default_rng(n)
+    J = rng.uniform(0.5, 1.5, n - 1)
+    g = rng.uniform(0.2, 2.0)
+    terms = gen.tfim_terms(n, J, g)
+    e_ed = dense.ground_energy_ed(n, terms)
+    e_ff = dense.tfim_ground_energy_free_fermion(J, np.full(n, g))
+    assert abs(e_ed - e_ff) < 1e-10
+
+
+def test_variational_energy_above_ground():
+    n = 8
+    b = gen.tfim_batch(n, 4, layers=2, seed=1)
+    g, p = ir(b["circuit"])
+    for i in range(4):
+        e = sv.energy(n, g, p, b["theta"][i], b["terms"], b["coeffs"][i])
+        e0 = dense.tfim_ground_energy_free_fermion(b["J"][i], np.full(n, b["g"][i]))
+        assert e >= e0 - 1e-12
+
+
+def test_energy_equals_dense_quadratic_form():
+    n = 7
+    c, th = gen.ry_cx_ladder(n, 3, seed=4)
+    g, p = ir(c)
+    terms = gen.tfim_terms(n, 1.0, 1.0)
+    psi = dense.run(n, g, p, th)
+    Hd = dense.hamiltonian_matrix(n, terms)
+    assert abs(sv.energy(n, g, p, th, terms) - np.vdot(psi, Hd @ psi).real) < 1e-12
+
+
+# ------------------------------------------------------------------ gradients
+@pytest.mark.parametrize("seed", [0, 1])
+def test_param_shift_equals_finite_difference(seed):
+    n = 5
+    c, th = gen.random_circuit(n, 40, seed=seed)
+    g, p = ir(c)
+    terms = gen.xxz_terms(n, 1.0, 0.5, 0.3)
+    ps = sv.grad_param_shift(n, g, p, th, terms)
+    fd = sv.grad_fd(n, g, p, th, terms, h=1e-5)
+    np.testing.assert_allclose(ps, fd, atol=2e-9)
+
+
+def test_shared_parameter_gradient_sums_over_gates():
+    n = 3
+    c = Circuit(n)
+    c.rx(0, param=0).ry(1, param=0, scale=-2.0).rzz(0, 1, param=0, scale=0.5).cx(1, 2)
+    g, p = ir(c)
+    terms = gen.tfim_terms(n, 1.0, 0.7)
+    th = np.array([0.37])
+    ps = sv.grad_param_shift(n, g, p, th, terms)
+    fd = sv.grad_fd(n, g, p, th, terms, h=1e-5)
+    assert abs(ps[0] - fd[0]) < 1e-9
+
+
+# ---------------------------------------------------------------- optimiser
+def test_adam_first_step_closed_form():
+    th0 = np.array([0.3, -1.0, 2.0])
+    grad = np.array([0.5, -2e-3, 0.0])
+    th1, m, v = adam_step(th0, np.zeros(3), np.zeros(3), grad, 1, lr=0.02, eps=1e-8)
+    np.testing.assert_allclose(th1, th0 - 0.02 * grad / (np.abs(grad) + 1e-8), rtol=1e-14)
+
+
+def test_adam_quadratic_converges():
+    th = np.array([3.0, -2.0])
+    m = v = np.zeros(2)
+    for t in range(1, 2001):
+        th, m, v = adam_step(th, m, v, 2 * th, t, lr=0.05)
+    assert np.all(np.abs(th) < 1e-2)
+
+
+# ------------------------------------------------------------------- inputs
+def test_haar_su4_is_special_unitary():
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        u = gen.haar_su4(rng)
+        assert np.linalg.norm(u.conj().T @ u - np.eye(4)) < 1e-14
+        assert abs(np.linalg.det(u) - 1) < 1e-13
+
+
+def test_rejects_bad_gates():
+    c = Circuit(3).cx(0, 0)
+    with pytest.raises(ValueError):
+        sv.apply(3, *ir(c), None)
+    c = Circuit(3).x(3)
+    with pytest.raises(ValueError):
+        sv.apply(3, *ir(c), None)
+    with pytest.raises(ValueError):
+        sv.expect(3, sv.zero_state(3), np.array([(8, 0, 1.0)], dtype=PAULI_DTYPE))

@@ -1,0 +1,308 @@
+"""Seeded synthetic inputs (circuits, observables, batches) for both sides.
+
+Holds no simulation arithmetic: every function here only draws random numbers
+and lays them out in the flat input format of ``workloads.ir``.  Random draws
+use ``numpy.random.default_rng(seed)`` in the order documented per function so
+the same seed gives bit-identical inputs to the oracle and to the CUDA path.
+
+Workload shapes follow the paper's circuits: the TFIM VQE ansatz of Sec. I.B,
+the SU(4) brickwork of the QML and MIPT demonstrations (Sec. VII.B, VII.C),
+and the parameter layouts they quote.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .ir import Circuit, PAULI_DTYPE
+
+TWO_PI = 2.0 * math.pi
+
+
+# ---------------------------------------------------------------------------
+# random unitaries
+# ---------------------------------------------------------------------------
+def haar_su4(rng: np.random.Generator) -> np.ndarray:
+    """Haar-random SU(4) matrix (MIPT/QML brickwork gates, Sec. VII.C).
+
+    Z = (A + iB)/sqrt(2) with A, B = rng.standard_normal((2, 4, 4)) (A first);
+    Q, R = qr(Z); Q <- Q diag(R_ii/|R_ii|) (Mezzadri's phase fix);
+    U = Q / det(Q)^(1/4) with the principal fourth root.
+    """
+    a, b = rng.standard_normal((2, 4, 4))
+    z = (a + 1j * b) / math.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    d = np.diag(r)
+    q = q * (d / np.abs(d))[None, :]
+    det = np.linalg.det(q)
+    return q / np.power(det, 0.25)
+
+
+def haar_unitary(rng: np.random.Generator, dim: int) -> np.ndarray:
+    """Haar-random U(dim) by the same QR recipe (no determinant fix)."""
+    a, b = rng.standard_normal((2, dim, dim))
+    z = (a + 1j * b) / math.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    d = np.diag(r)
+    return q * (d / np.abs(d))[None, :]
+
+
+# ---------------------------------------------------------------------------
+# circuits
+# ---------------------------------------------------------------------------
+def ry_cx_ladder(n: int = 10, layers: int = 4, seed: int = 0):
+    """Layers of [RY(theta[l, q]) on every qubit, CX(0,1), CX(1,2), ... CX(n-2, n-1)].
+
+    theta = rng.uniform(-pi, pi, (layers, n)); param index = l*n + q.
+    Returns (Circuit, theta flat float64[layers*n]).
+    """
+    rng = np.random.default_rng(seed)
+    theta = rng.uniform(-math.pi, math.pi, size=(layers, n))
+    c = Circuit(n)
+    for l in range(layers):
+        for q in range(n):
+            c.ry(q, param=l * n + q)
+        for q in range(n - 1):
+            c.cx(q, q + 1)
+    return c, theta.reshape(-1).copy()
+
+
+def brickwork_bonds(n: int, t: int):
+    """Bonds (i, i+1) of brickwork layer t on an open chain: i = t mod 2, step 2."""
+    return [(i, i + 1) for i in range(t % 2, n - 1, 2)]
+
+
+def su4_brickwork(n: int, depth: int, rot: str = "RX", seed: int = 0):
+    """Haar SU(4) brickwork interleaved with a rotation layer.
+
+    Layer t: one Haar SU(4) on every bond of ``brickwork_bonds(n, t)``, then
+    ``rot``(theta[t, q]) on every qubit q.  Draw order: all SU(4) matrices in
+    gate order, then theta = rng.uniform(-pi, pi, (depth, n)).
+    Param index = t*n + q.  Returns (Circuit, theta flat).
+    """
+    rng = np.random.default_rng(seed)
+    mats = [[haar_su4(rng) for _ in brickwork_bonds(n, t)] for t in range(depth)]
+    theta = rng.uniform(-math.pi, math.pi, size=(depth, n))
+    c = Circuit(n)
+    for t in range(depth):
+        for (a, b), u in zip(brickwork_bonds(n, t), mats[t]):
+            c.unitary((a, b), u)
+        for q in range(n):
+            c.add(rot, (q,), param=t * n + q)
+    return c, theta.reshape(-1).copy()
+
+
+def slice_circuit(c: Circuit, nq: int) -> Circuit:
+    """Drop every op whose support is not inside {0..nq-1}; params keep indices."""
+    out = Circuit(nq)
+    for (name, qubits, param, scale, angle0, mat) in c.ops:
+        if all(q < nq for q in qubits):
+            out.add(name, qubits, param=param, scale=scale, angle0=angle0, matrix=mat)
+    out.n_params = c.n_params
+    return out
+
+
+def hea_ring(n: int, layers: int = 12):
+    """Hardware-efficient ring ansatz (TFIM VQE ansatz of Sec. I.B, widened).
+
+    Layer l: RX(theta[l,0,q]) for all q, RY(theta[l,1,q]) for all q, then
+    RZZ(theta[l,2,i]) on (i, (i+1) mod n) for i = 0..n-1.
+    Param index = l*3n + k*n + q; P = 3*n*layers.
+    """
+    c = Circuit(n)
+    for l in range(layers):
+        base = l * 3 * n
+        for q in range(n):
+            c.rx(q, param=base + q)
+        for q in range(n):
+            c.ry(q, param=base + n + q)
+        for i in range(n):
+            c.rzz(i, (i + 1) % n, param=base + 2 * n + i)
+    c.n_params = 3 * n * layers
+    return c
+
+
+def random_circuit(n: int, n_ops: int, seed: int = 0, kinds=None):
+    """Random mix of every op kind on random qubits (test input)."""
+    rng = np.random.default_rng(seed)
+    kinds = kinds or ["X", "Y", "Z", "H", "S", "T", "RX", "RY", "RZ", "CX", "CZ",
+                      "CP", "SWAP", "RZZ", "U1", "U2", "U3", "U4"]
+    c = Circuit(n)
+    p = 0
+    for _ in range(n_ops):
+        k = kinds[int(rng.integers(len(kinds)))]
+        if k in ("U3", "U4") and n < int(k[1]):
+            k = "U2"
+        if k in ("CX", "CZ", "CP", "SWAP", "RZZ", "U2") and n < 2:
+            k = "RX"
+        if k in ("X", "Y", "Z", "H", "S", "T"):
+            c.add(k, (int(rng.integers(n)),))
+        elif k in ("RX", "RY", "RZ"):
+            c.add(k, (int(rng.integers(n)),), param=p,
+                  scale=float(rng.choice([1.0, -0.5, 2.0])),
+                  angle0=float(rng.uniform(-1, 1)))
+            p += 1
+        elif k in ("CX", "CZ", "SWAP"):
+            a, b = rng.choice(n, 2, replace=False)
+            c.add(k, (int(a), int(b)))
+        elif k in ("CP", "RZZ"):
+            a, b = rng.choice(n, 2, replace=False)
+            c.add(k, (int(a), int(b)), param=p, scale=1.0,
+                  angle0=float(rng.uniform(-1, 1)))
+            p += 1
+        elif k == "U1":
+            c.unitary((int(rng.integers(n)),), haar_unitary(rng, 2))
+        elif k == "U2":
+            a, b = rng.choice(n, 2, replace=False)
+            c.unitary((int(a), int(b)), haar_unitary(rng, 4))
+        else:
+            kq = int(k[1])
+            qs = rng.choice(n, kq, replace=False)
+            c.unitary(tuple(int(q) for q in qs), haar_unitary(rng, 1 << kq))
+    c.n_params = p
+    theta = rng.uniform(-math.pi, math.pi, size=p)
+    return c, theta
+
+
+# ---------------------------------------------------------------------------
+# observables
+# ---------------------------------------------------------------------------
+def tfim_terms(n: int, J=1.0, g=1.0) -> np.ndarray:
+    """Open-chain TFIM H = -sum_i J_i Z_i Z_{i+1} - g sum_i X_i (Sec. I.B).
+
+    Term order: the n-1 ZZ bonds, then the n X fields.
+    """
+    J = np.broadcast_to(np.asarray(J, dtype=np.float64), (max(n - 1, 0),))
+    out = np.zeros(max(n - 1, 0) + n, dtype=PAULI_DTYPE)
+    for i in range(n - 1):
+        out[i] = (0, (1 << i) | (1 << (i + 1)), -float(J[i]))
+    for i in range(n):
+        out[n - 1 + i] = (1 << i, 0, -float(g))
+    return out
+
+
+def xxz_terms(n: int, J, delta: float, g: float) -> np.ndarray:
+    """Open-chain XXZ: sum_i J_i (X X + Y Y + delta Z Z)_{i,i+1} - g sum_i X_i.
+
+    Term order: per bond XX, YY, ZZ; then the n X fields.
+    """
+    J = np.broadcast_to(np.asarray(J, dtype=np.float64), (max(n - 1, 0),))
+    out = np.zeros(3 * (n - 1) + n, dtype=PAULI_DTYPE)
+    k = 0
+    for i in range(n - 1):
+        m = (1 << i) | (1 << (i + 1))
+        out[k] = (m, 0, float(J[i])); k += 1
+        out[k] = (m, m, float(J[i])); k += 1
+        out[k] = (0, m, float(J[i]) * float(delta)); k += 1
+    for i in range(n):
+        out[k] = (1 << i, 0, -float(g)); k += 1
+    return out
+
+
+def random_pauli_strings(n: int, count: int, weight: int = 4, seed: int = 0) -> np.ndarray:
+    """Random weight-w Pauli strings, coefficient 1.
+
+    Per string: qubits = rng.choice(n, w, replace=False), then
+    kinds = rng.integers(0, 3, w) with 0 -> X, 1 -> Y, 2 -> Z.
+    """
+    rng = np.random.default_rng(seed)
+    out = np.zeros(count, dtype=PAULI_DTYPE)
+    for s in range(count):
+        qs = rng.choice(n, weight, replace=False)
+        ks = rng.integers(0, 3, weight)
+        xm = zm = 0
+        for q, k in zip(qs, ks):
+            if k in (0, 1):
+                xm |= 1 << int(q)
+            if k in (1, 2):
+                zm |= 1 << int(q)
+        out[s] = (xm, zm, 1.0)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# batched VQE inputs
+# ---------------------------------------------------------------------------
+def tfim_batch(n: int, batch: int, layers: int = 12, seed: int = 0):
+    """B TFIM chains on the ring ansatz.
+
+    Draw order: J = rng.uniform(0.5, 1.5, (B, n-1)); g = rng.uniform(0.2, 2.0, B);
+    theta = rng.uniform(-pi, pi, (B, 3*n*layers)).
+    Returns dict(circuit, terms (structure, coeff -1), coeffs [B][T], theta, J, g).
+    """
+    rng = np.random.default_rng(seed)
+    J = rng.uniform(0.5, 1.5, size=(batch, n - 1))
+    g = rng.uniform(0.2, 2.0, size=batch)
+    P = 3 * n * layers
+    theta = rng.uniform(-math.pi, math.pi, size=(batch, P))
+    terms = tfim_terms(n, 1.0, 1.0)
+    coeffs = np.concatenate([-J, -np.repeat(g[:, None], n, axis=1)], axis=1)
+    return dict(n=n, circuit=hea_ring(n, layers), terms=terms, coeffs=coeffs,
+                theta=theta, J=J, g=g)
+
+
+def ragged_sizes(batch: int, choices=(12, 14, 16, 18, 20), seed: int = 0) -> np.ndarray:
+    """n_b drawn uniformly from ``choices`` (rng.integers index draw)."""
+    rng = np.random.default_rng(seed)
+    return np.asarray(choices)[rng.integers(0, len(choices), batch)]
+
+
+def warmstart_chains(count: int, n_min: int = 14, n_max: int = 20, seed: int = 0):
+    """TFIM/XXZ chains for the learned warm start.
+
+    Per chain, in order: kind = rng.integers(0, 2) (0 TFIM, 1 XXZ);
+    n = rng.integers(n_min, n_max + 1); J = rng.uniform(0.5, 1.5, n-1);
+    delta = rng.uniform(0, 1.5) (kept for TFIM, unused there);
+    g = rng.uniform(0.2, 2.0).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        kind = int(rng.integers(0, 2))
+        n = int(rng.integers(n_min, n_max + 1))
+        J = rng.uniform(0.5, 1.5, n - 1)
+        delta = float(rng.uniform(0.0, 1.5))
+        g = float(rng.uniform(0.2, 2.0))
+        out.append(dict(kind=kind, n=n, J=J, delta=delta, g=g))
+    return out
+
+
+def chain_terms(chain) -> np.ndarray:
+    """Observable of one warm-start chain."""
+    if chain["kind"] == 0:
+        return tfim_terms(chain["n"], chain["J"], chain["g"])
+    return xxz_terms(chain["n"], chain["J"], chain["delta"], chain["g"])
+
+
+def chain_features(chain, n_max: int = 20) -> np.ndarray:
+    """[J_1..J_{n_max-1} zero-padded, delta, g, n/n_max, one-hot kind] (24 for n_max 20)."""
+    f = np.zeros(n_max - 1 + 5, dtype=np.float64)
+    f[: chain["n"] - 1] = chain["J"]
+    f[n_max - 1] = chain["delta"] if chain["kind"] == 1 else 0.0
+    f[n_max] = chain["g"]
+    f[n_max + 1] = chain["n"] / n_max
+    f[n_max + 2 + chain["kind"]] = 1.0
+    return f
+
+
+def random_thetas(shape, seed: int = 0) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-math.pi, math.pi, size=shape)
+
+
+def amplitude_encoded_batch(batch: int, n: int, seed: int = 0) -> np.ndarray:
+    """Normalised non-negative real vectors of length 2^n (pixel-like amplitude
+    encoding of Sec. VII.B); draw rng.random((B, 2^n)). complex128."""
+    rng = np.random.default_rng(seed)
+    x = rng.random((batch, 1 << n))
+    x /= np.linalg.norm(x, axis=1, keepdims=True)
+    return x.astype(np.complex128)
+
+
+def random_state(n: int, seed: int = 0) -> np.ndarray:
+    """Normalised complex Gaussian state (test input)."""
+    rng = np.random.default_rng(seed)
+    a, b = rng.standard_normal((2, 1 << n))
+    v = a + 1j * b
+    return v / np.linalg.norm(v)
