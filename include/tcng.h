@@ -1,0 +1,309 @@
+/*
+ * tcng.h -- C ABI of the B300 (sm_103a) state-vector simulator.
+ *
+ * The library simulates the paper's circuit/observable statement (TensorCircuit-NG,
+ * Sec. I.B "Primitives" and "Paradigms"):  build a circuit on n qubits from
+ * parameterised 1- and 2-qubit gates (rx, ry, rz, rzz, h, cx, su4, ...),
+ * evaluate Pauli-string expectations (expectation_ps) such as the TFIM energy
+ * H = -sum Z_i Z_j - g sum X_i, and return the value and gradient of the energy
+ * for a batch of parameter sets (value_and_grad under vmap).  It computes these
+ * by in-place state-vector updates on one GPU, not by the paper's tensor-network
+ * contraction.
+ *
+ * Conventions
+ *   - qubit q is bit q of the amplitude index (little-endian);
+ *   - R_P(t) = exp(-i t P / 2) for RX, RY, RZ, RZZ; CP(phi) = diag(1,1,1,e^{i phi});
+ *   - a gate's angle is angle0 + scale * params[item][param] (param < 0: angle0);
+ *   - the local index of a k-qubit gate matrix is sum_j bit(q[j]) << (k-1-j);
+ *   - complex64 states are interleaved float2, complex128 states double2;
+ *   - a Pauli string is (xmask, zmask); Y where both bits are set.
+ *
+ * Errors: every call returns a tcng_status; no C++ exception crosses the ABI.
+ * tcng_last_error() returns a thread-local message for the last failing call.
+ * Host arrays are copied (or hashed and cached) during the call; device
+ * pointers are borrowed and used in stream order on the stream passed in
+ * (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ * The library keeps per-structure device scratch (matrix tables, partial sums):
+ * calls that overlap on different streams and share a structure race on it.
+ * No call synchronises the device except the first call of a new structure
+ * (uploading its plan), scratch growth, tcng_autotune and tcng_sync_status.
+ */
+#ifndef TCNG_PUBLIC_API_H_
+#define TCNG_PUBLIC_API_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TCNG_OK = 0,
+    TCNG_EINVAL = 1,        /* bad argument (qubit out of range, null pointer, ...) */
+    TCNG_ENOMEM = 2,        /* device or host allocation failed, or buffer too small */
+    TCNG_ECUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error) */
+    TCNG_EUNSUPPORTED = 4,  /* valid request this build does not implement */
+    TCNG_ETIMEOUT = 5       /* a bounded device-side wait expired (reported by tcng_sync_status) */
+} tcng_status;
+
+typedef enum { TCNG_C64 = 0, TCNG_C128 = 1 } tcng_dtype;
+
+typedef enum {
+    TCNG_I = 0, TCNG_X, TCNG_Y, TCNG_Z, TCNG_H, TCNG_S, TCNG_T,
+    TCNG_RX, TCNG_RY, TCNG_RZ, TCNG_CX, TCNG_CZ, TCNG_CP, TCNG_SWAP, TCNG_RZZ,
+    TCNG_U1, TCNG_U2, TCNG_UK
+} tcng_op;
+
+/* One gate of the flat gate-list IR (56 bytes).  U1/U2/UK read a row-major
+ * complex128 matrix at mat_off (in complex entries) of the matrix pool. */
+typedef struct {
+    uint16_t op;        /* tcng_op */
+    uint8_t nq;         /* number of qubits (must match op; UK: 1..5) */
+    uint8_t pad;
+    int32_t q[5];       /* qubits; q[0] is the most significant local bit */
+    int32_t param;      /* index into params (per item), -1 = none */
+    double scale;       /* angle = angle0 + scale * params[param] */
+    double angle0;
+    int64_t mat_off;    /* complex offset into mat_pool, -1 = none */
+} tcng_gate;
+
+/* One Pauli string: X on xmask&~zmask, Z on zmask&~xmask, Y on xmask&zmask. */
+typedef struct {
+    uint64_t xmask;
+    uint64_t zmask;
+    double coeff;
+} tcng_pauli;
+
+typedef struct tcng_state tcng_state;   /* opaque batch of state vectors */
+
+/* Maximum qubits per state vector and maximum fused block width. */
+#define TCNG_MAX_QUBITS 34
+#define TCNG_MAX_FUSE 5
+
+/*
+ * tcng_state_init -- create `batch` state vectors |0...0> (paper Sec. I.B:
+ * tc.Circuit(n) starts from the all-zero product state).
+ *   dt        element type of every amplitude;
+ *   n_qubits  host array [batch]; item b holds 2^n_qubits[b] amplitudes
+ *             (ragged batches allowed, each n in 1..TCNG_MAX_QUBITS);
+ *   dev_buf   NULL: the library allocates device memory and owns it;
+ *             else a caller-owned, 256-byte aligned device buffer of buf_bytes
+ *             bytes (e.g. a torch tensor) that must outlive the state;
+ *   stream    cudaStream_t for the initialising kernel.
+ * Items are stored back to back, each starting on a 256-byte boundary.
+ * Errors: EINVAL (bad sizes, null out), ENOMEM (allocation or buf_bytes too
+ * small), ECUDA.
+ */
+tcng_status tcng_state_init(tcng_state** out, tcng_dtype dt, int batch, const int* n_qubits,
+                            void* dev_buf, size_t buf_bytes, void* stream);
+
+/* Bytes a caller-owned buffer needs for tcng_state_init with these sizes. */
+tcng_status tcng_state_bytes(tcng_dtype dt, int batch, const int* n_qubits, size_t* bytes);
+
+/* Free the handle (and the device memory if the library allocated it).
+ * Waits for no work: the caller must not free while kernels using it run. */
+tcng_status tcng_state_free(tcng_state* st);
+
+/* Device pointer and byte size of item `item` (a view; no copy). */
+tcng_status tcng_state_ptr(const tcng_state* st, int item, void** dev_amp, size_t* bytes);
+
+/* Reset every item to |0...0> (stream-ordered). */
+tcng_status tcng_state_reset(tcng_state* st, void* stream);
+
+/*
+ * tcng_apply_circuit -- apply the gate list to every item in place
+ * (paper Sec. I.B: gates added to tc.Circuit act in order on the state).
+ *   ops, n_ops        host gate list (validated and copied; the fused plan is
+ *                     cached by a hash of the structure, so repeated calls with
+ *                     the same structure and new parameters rebuild nothing);
+ *   mat_pool, n_mat   host complex128 matrix pool as (re, im) doubles,
+ *                     n_mat complex entries (may be NULL if n_mat == 0);
+ *   params_dev        device double [batch][P] (may be NULL if P == 0);
+ *   P                 parameters per item.
+ * Every qubit must be < n of every item.  Gates are fused into blocks of at
+ * most the configured width and grouped into shared-memory tile passes
+ * (tcng_set_option).  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+tcng_status tcng_apply_circuit(tcng_state* st, const tcng_gate* ops, size_t n_ops,
+                               const double* mat_pool, size_t n_mat,
+                               const void* params_dev, int P, void* stream);
+
+/*
+ * tcng_expect_pauli -- out_dev[b][t] = <psi_b|P_t|psi_b> (real; the paper's
+ * expectation_ps, Sec. I.B; coefficients are NOT applied).
+ *   terms     host array [n_terms <= 4096] of Pauli strings (masks < 2^n);
+ *   out_dev   device double [batch][n_terms].
+ * All items must have the same n.  Sums accumulate in FP64 in a fixed order
+ * (bitwise reproducible).  Errors: EINVAL, ENOMEM, EUNSUPPORTED (ragged), ECUDA.
+ */
+tcng_status tcng_expect_pauli(const tcng_state* st, const tcng_pauli* terms, size_t n_terms,
+                              double* out_dev, void* stream);
+
+/*
+ * tcng_energy -- energy_dev[b] = sum_t c[b][t] <psi_b|P_t|psi_b>, the TFIM (or
+ * any Pauli-sum) energy of Sec. I.B.  coeffs_dev: device double [batch][n_terms],
+ * or NULL to use terms[t].coeff for every item.  Errors: as tcng_expect_pauli.
+ */
+tcng_status tcng_energy(const tcng_state* st, const tcng_pauli* terms, size_t n_terms,
+                        const double* coeffs_dev, double* energy_dev, void* stream);
+
+/*
+ * tcng_hamiltonian_apply -- lambda_b = H_b psi_b for every item (the co-state
+ * that starts the adjoint sweep); out must be a state with the same shape and
+ * dtype as st.  H_b = sum_t c[b][t] P_t with coeffs_dev as in tcng_energy.
+ */
+tcng_status tcng_hamiltonian_apply(const tcng_state* st, const tcng_pauli* terms, size_t n_terms,
+                                   const double* coeffs_dev, tcng_state* out, void* stream);
+
+/*
+ * tcng_energy_grad -- for every item b: run U(theta_b)|0..0>, then
+ * E_b = <psi|H_b|psi> and dE_b/dtheta_b by an adjoint reverse sweep
+ * (replaces the paper's reverse-mode AD through the tensor network, Sec. I.B
+ * "Paradigms: AD"; cost independent of the number of parameters, O(1) states).
+ *   st          batch of states (all items the same n); used as scratch for psi;
+ *   ops/mat     gate list as in tcng_apply_circuit; parameterised gates must
+ *               be RX, RY, RZ, RZZ or CP;
+ *   params_dev  device double [batch][P];
+ *   H, n_terms  Pauli strings; coeffs_dev device double [batch][n_terms] or NULL;
+ *   energy_dev  device double [batch];
+ *   grad_dev    device double [batch][P] (dE/dtheta; params read by no gate get 0).
+ * One persistent launch covers the whole batch.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+tcng_status tcng_energy_grad(tcng_state* st, const tcng_gate* ops, size_t n_ops,
+                             const double* mat_pool, size_t n_mat,
+                             const void* params_dev, int P,
+                             const tcng_pauli* H, size_t n_terms, const double* coeffs_dev,
+                             double* energy_dev, double* grad_dev, void* stream);
+
+/* One circuit structure of a ragged batch (all arrays on the host). */
+typedef struct {
+    int n;                       /* qubits */
+    const tcng_gate* ops;
+    size_t n_ops;
+    const double* mat_pool;      /* complex128 (re, im) pairs */
+    size_t n_mat;
+    int P;                       /* parameters per item of this structure */
+    const tcng_pauli* H;
+    size_t n_terms;
+} tcng_problem;
+
+/*
+ * tcng_energy_grad_ragged -- one persistent launch over items of different
+ * structures and qubit counts (the paper's vmap over "thousands of instances",
+ * Sec. I.B, with ragged n).
+ *   problems, n_problems   host structures;
+ *   item_problem           host int [batch]: structure of item b;
+ *   params_dev             device double, items packed back to back
+ *                          (item b starts at sum_{b'<b} P of its structure);
+ *   coeffs_dev             device double packed the same way over n_terms, or
+ *                          NULL for the structures' own coefficients;
+ *   energy_dev             device double [batch];
+ *   grad_dev               device double packed like params_dev.
+ * No state handle: the library keeps per-CTA scratch for the largest n.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+tcng_status tcng_energy_grad_ragged(const tcng_problem* problems, int n_problems,
+                                    const int* item_problem, int batch,
+                                    const double* params_dev, const double* coeffs_dev,
+                                    double* energy_dev, double* grad_dev, void* stream);
+
+/*
+ * tcng_apply_shared_unitary -- apply one k-qubit unitary U (host complex128,
+ * row-major, local index as in the gate list with qubits q[0..k-1]) to every
+ * item of a complex64 batch: a complex GEMM [2^k x 2^k] x [2^k x batch*2^(n-k)]
+ * on the tensor cores (tcgen05, fp32 accuracy by a 3-term TF32 split).  The
+ * batched layer of the paper's QML demonstration (Sec. VII.B), where every
+ * input state sees the same circuit.  k in 1..5; qubits distinct and < n.
+ * Errors: EINVAL, EUNSUPPORTED (complex128 states), ECUDA.
+ */
+tcng_status tcng_apply_shared_unitary(tcng_state* st, const int* qubits, int k,
+                                      const double* U, void* stream);
+
+/*
+ * tcng_adam_step -- device Adam update over n values (Kingma & Ba; the
+ * optimiser of the paper's training listings):
+ *   m <- b1 m + (1-b1) g; v <- b2 v + (1-b2) g^2;
+ *   theta <- theta - lr * (m/(1-b1^t)) / (sqrt(v/(1-b2^t)) + eps),
+ * with t = *step_dev + 1 read on the device; the kernel's last block writes the
+ * new step back (so the call can be replayed from a CUDA graph).  All arrays
+ * are device double.
+ */
+tcng_status tcng_adam_step(double* theta, double* m, double* v, const double* grad, size_t n,
+                           double lr, double b1, double b2, double eps, int* step_dev,
+                           void* stream);
+
+/*
+ * Warm-start MLP (no counterpart in the paper): y = W3 relu(W2 relu(W1 x + b1) + b2) + b3
+ * with BF16 operands and FP32 accumulation.  Weights are FP32 master copies;
+ * each GEMM reads BF16-rounded copies of its two operands.
+ *   x        device float [N][F];
+ *   w1,b1    [F][H], [H];  w2,b2 [H][H], [H];  w3,b3 [H][O], [O]  (device float)
+ *   act      device float scratch [2][N][H] (pre-activations z1, z2), written;
+ *   y        device float [N][O], written.
+ */
+tcng_status tcng_mlp_forward(const float* x, int N, int F, int H, int O,
+                             const float* w1, const float* b1, const float* w2, const float* b2,
+                             const float* w3, const float* b3, float* act, float* y,
+                             void* stream);
+
+/*
+ * Loss and backward pass of the warm-start MLP.  Loss (periodic in the angle):
+ *   L = sum_{n,o} mask[n][o] * 2 (1 - cos(y[n][o] - target[n][o])) / sum mask.
+ *   mask, target  device float [N][O];
+ *   act           the pre-activations tcng_mlp_forward wrote;
+ *   grads         device float, the 6 gradients packed as w1,b1,w2,b2,w3,b3;
+ *   loss_dev      device double [1].
+ */
+tcng_status tcng_mlp_backward(const float* x, int N, int F, int H, int O,
+                              const float* w1, const float* w2, const float* w3,
+                              const float* act, const float* y, const float* target,
+                              const float* mask, float* grads, double* loss_dev, void* stream);
+
+/* Adam over FP32 master weights (device float), same formula as tcng_adam_step. */
+tcng_status tcng_adam_step_f32(float* theta, float* m, float* v, const float* grad, size_t n,
+                               float lr, float b1, float b2, float eps, int* step_dev,
+                               void* stream);
+
+/* Options (process-wide). */
+typedef enum {
+    TCNG_OPT_FUSE_WIDTH = 0,   /* max qubits of a fused block, 1..5 (default 2) */
+    TCNG_OPT_TILE_BITS = 1,    /* log2 amplitudes per shared-memory tile, 5..13 (default 13) */
+    TCNG_OPT_CHUNK_BITS = 2,   /* log2 contiguous amplitudes per copied chunk (default 7) */
+    TCNG_OPT_USE_GRAPHS = 3,   /* 1: replay CUDA graphs per structure (default 1) */
+    TCNG_OPT_UNFUSED = 4       /* 1: one pair/quartet kernel launch per gate (default 0) */
+} tcng_option;
+
+tcng_status tcng_set_option(tcng_option opt, int value);
+tcng_status tcng_get_option(tcng_option opt, int* value);
+
+/*
+ * tcng_autotune -- time candidate (fusion width, tile bits, chunk bits) on a
+ * synthetic brickwork circuit of n qubits (CUDA events, device synchronised),
+ * set the best as the current options and append it to cache_path (NULL: no
+ * file).  If cache_path already holds an entry for (n, dt, batch) it is loaded
+ * without timing.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+tcng_status tcng_autotune(int n, tcng_dtype dt, int batch, const char* cache_path);
+
+/* Synchronise the device and report a device-side error word (ETIMEOUT) if set. */
+tcng_status tcng_sync_status(void);
+
+/* Human-readable summary of the plan a gate list compiles to (thread-local string). */
+const char* tcng_describe_plan(int n, const tcng_gate* ops, size_t n_ops, const double* mat_pool,
+                               size_t n_mat, int P, int adjoint);
+
+/* Kernels this library launched since load (for accounting). */
+uint64_t tcng_launch_count(void);
+
+/* Thread-local message for the last failing call ("" if none). */
+const char* tcng_last_error(void);
+
+/* Library version string. */
+const char* tcng_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TCNG_PUBLIC_API_H_ */

@@ -1,0 +1,598 @@
+// C ABI of the simulator (declared in include/tcng.h): argument validation,
+// state handles, the per-structure plan cache, and kernel orchestration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <stdexcept>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "capi_internal.hpp"
+
+namespace tcng {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static thread_local std::string g_err;
+tcng_status fail(tcng_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+tcng_status cuda_fail(cudaError_t e, const char* where) {
+    cudaGetLastError();
+    return fail(TCNG_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+Options g_opt;
+std::mutex g_mu;
+
+// ------------------------------------------------------------ device ctx --
+DeviceCtx& ctx() {
+    static std::map<int, std::unique_ptr<DeviceCtx>> ctxs;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto& p = ctxs[dev];
+    if (!p) {
+        p.reset(new DeviceCtx());
+        p->device = dev;
+        if (cudaMalloc(&p->err, sizeof(unsigned)) == cudaSuccess) {
+            cudaMemset(p->err, 0, sizeof(unsigned));
+        } else {
+            cudaGetLastError();
+            p->err = nullptr;
+        }
+    }
+    return *p;
+}
+
+void* DeviceCtx::scratch(const std::string& name, size_t bytes) {
+    auto& b = bufs[name];
+    if (b.bytes < bytes) {
+        if (b.ptr) {
+            cudaDeviceSynchronize();
+            cudaFree(b.ptr);
+            b.ptr = nullptr;
+            b.bytes = 0;
+        }
+        size_t cap = std::max(bytes, (size_t)256);
+        if (cudaMalloc(&b.ptr, cap) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        b.bytes = cap;
+    }
+    return b.ptr;
+}
+
+DevPlan::~DevPlan() {
+    cudaFree(d_bblocks);
+    cudaFree(d_bops);
+    cudaFree(d_pool);
+    cudaFree(d_stages);
+    cudaFree(d_dops);
+    cudaFree(d_table);
+    cudaFree(d_gparam);
+    cudaFree(d_gscale);
+}
+
+TermSet::~TermSet() {
+    cudaFree(d_h);
+    cudaFree(d_c);
+}
+
+PlanOptions plan_options(tcng_dtype dt, bool adjoint) {
+    PlanOptions o;
+    o.fuse_width = g_opt.fuse_width;
+    o.tile_bits = g_opt.tile_bits;
+    if (dt == TCNG_C128) o.tile_bits = std::min(o.tile_bits, 12);
+    o.chunk_bits = std::min(g_opt.chunk_bits, o.tile_bits);
+    o.adjoint = adjoint ? 1 : 0;
+    o.unfused = g_opt.unfused ? 1 : 0;
+    return o;
+}
+
+// Build (or fetch) the device plan of a structure.
+DevPlan* get_plan(int n, const tcng_gate* ops, size_t n_ops, const double* pool, size_t n_mat,
+                  int P, const PlanOptions& o) {
+    DeviceCtx& c = ctx();
+    const uint64_t h = structure_hash(n, ops, n_ops, pool, n_mat, P, o);
+    auto it = c.plans.find(h);
+    if (it != c.plans.end()) return it->second.get();
+    std::unique_ptr<DevPlan> dp(new DevPlan());
+    Plan& pl = dp->plan;
+    pl.n = n;
+    pl.P = P;
+    pl.opt = o;
+    if (n < 5 && !o.adjoint) pl.opt.unfused = 1;
+    pl.ops = import_ops(n, ops, n_ops, n_mat, P, pool);
+    build_plan(pl);
+    dp->d_bblocks = dev_copy(pl.bblocks);
+    dp->d_bops = dev_copy(pl.bops);
+    if (n_mat) {
+        std::vector<double2> pv(n_mat);
+        for (size_t i = 0; i < n_mat; ++i) pv[i] = make_double2(pool[2 * i], pool[2 * i + 1]);
+        dp->d_pool = dev_copy(pv);
+    }
+    dp->d_stages = dev_copy(pl.stages);
+    dp->d_dops = dev_copy(pl.dops);
+    dp->d_gparam = dev_copy(pl.grad_param);
+    dp->d_gscale = dev_copy(pl.grad_scale);
+    DevPlan* raw = dp.get();
+    c.plans[h] = std::move(dp);
+    return raw;
+}
+
+// Device copies of a Pauli-term list (cached by content).
+TermSet* get_terms(const tcng_pauli* terms, size_t n_terms, int n) {
+    const uint64_t lim = (n >= 64) ? ~0ULL : ((1ULL << n) - 1);
+    for (size_t t = 0; t < n_terms; ++t)
+        if ((terms[t].xmask & ~lim) || (terms[t].zmask & ~lim))
+            throw std::invalid_argument("Pauli mask outside the register");
+    uint64_t h = 1469598103934665603ULL ^ (uint64_t)n_terms;
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(terms);
+    for (size_t i = 0; i < sizeof(tcng_pauli) * n_terms; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ULL;
+    }
+    DeviceCtx& c = ctx();
+    auto it = c.terms.find(h);
+    if (it != c.terms.end()) return it->second.get();
+    std::unique_ptr<TermSet> ts(new TermSet());
+    ts->n_terms = (int)n_terms;
+    std::vector<HTerm> ht(std::max<size_t>(1, n_terms));
+    std::vector<double> tc(std::max<size_t>(1, n_terms), 0.0);
+    for (size_t t = 0; t < n_terms; ++t) {
+        ht[t].xm = terms[t].xmask;
+        ht[t].zm = terms[t].zmask;
+        ht[t].ny = __builtin_popcountll(terms[t].xmask & terms[t].zmask) & 3;
+        tc[t] = terms[t].coeff;
+    }
+    ts->d_h = dev_copy(ht);
+    ts->d_c = dev_copy(tc);
+    TermSet* raw = ts.get();
+    c.terms[h] = std::move(ts);
+    return raw;
+}
+
+// Per-item matrix table of a plan for `items` items (grown on demand).
+void* plan_table(DevPlan* dp, size_t elem, int items) {
+    const size_t need = std::max<size_t>(1, (size_t)dp->plan.table_size) * elem * std::max(items, 1);
+    if (dp->table_bytes < need) {
+        if (dp->d_table) {
+            cudaDeviceSynchronize();
+            cudaFree(dp->d_table);
+            dp->d_table = nullptr;
+            dp->table_bytes = 0;
+        }
+        if (cudaMalloc(&dp->d_table, need) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        dp->table_bytes = need;
+    }
+    return dp->d_table;
+}
+
+// Run a plan on a group of items (all with n == plan.n).
+template <typename C>
+tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int items,
+                     const double* params, cudaStream_t s) {
+    Plan& pl = dp->plan;
+    const int tab_items = pl.P > 0 ? items : 1;
+    C* table = static_cast<C*>(plan_table(dp, sizeof(C), tab_items));
+    if (!table) return fail(TCNG_ENOMEM, "matrix table allocation failed");
+    const long long stride = pl.P > 0 ? pl.table_size : 0;
+    cudaError_t e = launch_build_matrices<C>(dp->d_bblocks, (int)pl.bblocks.size(), dp->d_bops,
+                                             dp->d_pool, pl.P > 0 ? params : nullptr, pl.P, table,
+                                             pl.table_size, tab_items, s);
+    if (e != cudaSuccess) return cuda_fail(e, "matrix prologue");
+    if (pl.opt.unfused) {
+        for (const Block& b : pl.blocks) {
+            e = launch_gate<C>(state, d_item_off, items, pl.n, b, table, stride, s);
+            if (e != cudaSuccess) return cuda_fail(e, "gate kernel");
+        }
+    } else {
+        for (const DevPass& p : pl.passes) {
+            e = launch_pass<C>(state, d_item_off, items, pl.n, p, dp->d_stages, dp->d_dops, table,
+                               stride, ctx().err, s);
+            if (e != cudaSuccess) return cuda_fail(e, "pass kernel");
+        }
+    }
+    return TCNG_OK;
+}
+template tcng_status run_plan<float2>(DevPlan*, float2*, const long long*, int, const double*, cudaStream_t);
+template tcng_status run_plan<double2>(DevPlan*, double2*, const long long*, int, const double*, cudaStream_t);
+
+// Group Pauli terms into tile passes: a term joins a pass if its X bits above
+// the contiguous low bits fit the pass's gather set.
+void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
+                      std::vector<DevPass>& passes, std::vector<ExpPass>& eps) {
+    const uint64_t lim = (n >= 64) ? ~0ULL : ((1ULL << n) - 1);
+    for (size_t t = 0; t < T; ++t)
+        if ((terms[t].xmask & ~lim) || (terms[t].zmask & ~lim))
+            throw std::invalid_argument("Pauli mask outside the register");
+    m = std::min(m, n);
+    low = std::min(low, m);
+    const int gmax = m - low;
+    const uint64_t lowmask = (low >= 64) ? ~0ULL : ((1ULL << low) - 1);
+    std::vector<char> done(T, 0);
+    size_t left = T;
+    while (left) {
+        uint64_t G = 0;
+        ExpPass ep{};
+        std::vector<int> sel;
+        for (size_t t = 0; t < T && (int)sel.size() < kExpTermsPerPass; ++t) {
+            if (done[t]) continue;
+            const uint64_t hi = (n <= m) ? 0 : (terms[t].xmask & ~lowmask);
+            if (__builtin_popcountll(G | hi) > gmax) continue;
+            G |= hi;
+            sel.push_back((int)t);
+        }
+        uint64_t S;
+        if (n <= m) {
+            S = lim;
+        } else {
+            S = lowmask | G;
+            for (int q = low; q < n && __builtin_popcountll(S) < m; ++q) S |= 1ULL << q;
+        }
+        DevPass dp{};
+        dp.m = __builtin_popcountll(S);
+        int tb[64];
+        int i = 0;
+        for (int q = 0; q < 64; ++q) tb[q] = ((S >> q) & 1) ? i++ : -1;
+        int L = 0;
+        while (L < n && ((S >> L) & 1)) ++L;
+        dp.chunk = std::min(L, dp.m);
+        dp.ngather = dp.m - dp.chunk;
+        int gi = 0, ri = 0;
+        for (int q = dp.chunk; q < n; ++q) {
+            if ((S >> q) & 1) dp.gather[gi++] = (uint8_t)q;
+            else dp.rest[ri++] = (uint8_t)q;
+        }
+        dp.nrest = ri;
+        for (int t : sel) {
+            ExpTerm et{};
+            const uint64_t xm = terms[t].xmask, zm = terms[t].zmask;
+            et.ny = __builtin_popcountll(xm & zm) & 3;
+            et.out = t;
+            for (int q = 0; q < n; ++q) {
+                if ((xm >> q) & 1) et.xm_tile |= 1u << tb[q];
+                if ((zm >> q) & 1) {
+                    if (tb[q] >= 0) et.zm_tile |= 1u << tb[q];
+                    else et.zm_glob |= 1ULL << q;
+                }
+            }
+            ep.t[ep.nterms++] = et;
+            done[t] = 1;
+            --left;
+        }
+        passes.push_back(dp);
+        eps.push_back(ep);
+    }
+}
+
+}  // namespace tcng
+
+using namespace tcng;
+
+#define TCNG_TRY(body)                                                   \
+    try {                                                                \
+        body                                                             \
+    } catch (const std::invalid_argument& ex) {                          \
+        return fail(TCNG_EINVAL, ex.what());                             \
+    } catch (const std::bad_alloc&) {                                    \
+        return fail(TCNG_ENOMEM, "allocation failed");                   \
+    } catch (const std::exception& ex) {                                 \
+        return fail(TCNG_EINVAL, ex.what());                             \
+    }
+
+extern "C" {
+
+const char* tcng_last_error(void) { return g_err.c_str(); }
+const char* tcng_version(void) { return "tcng-b300 0.1 (sm_103a)"; }
+uint64_t tcng_launch_count(void) { return g_launches.load(); }
+
+static size_t elem_size(tcng_dtype dt) { return dt == TCNG_C64 ? 8 : 16; }
+
+static tcng_status layout(tcng_dtype dt, int batch, const int* nq, std::vector<long long>& off,
+                          size_t* bytes) {
+    if (dt != TCNG_C64 && dt != TCNG_C128) return fail(TCNG_EINVAL, "bad dtype");
+    if (batch < 1) return fail(TCNG_EINVAL, "batch must be >= 1");
+    if (!nq) return fail(TCNG_EINVAL, "n_qubits is NULL");
+    const size_t es = elem_size(dt);
+    size_t pos = 0;
+    off.resize(batch);
+    for (int b = 0; b < batch; ++b) {
+        if (nq[b] < 1 || nq[b] > TCNG_MAX_QUBITS) return fail(TCNG_EINVAL, "qubit count out of range");
+        pos = (pos + 255) & ~(size_t)255;
+        off[b] = (long long)(pos / es);
+        pos += es << nq[b];
+    }
+    *bytes = pos;
+    return TCNG_OK;
+}
+
+tcng_status tcng_state_bytes(tcng_dtype dt, int batch, const int* n_qubits, size_t* bytes) {
+    std::vector<long long> off;
+    if (!bytes) return fail(TCNG_EINVAL, "bytes is NULL");
+    return layout(dt, batch, n_qubits, off, bytes);
+}
+
+tcng_status tcng_state_free(tcng_state* st) {
+    if (!st) return TCNG_OK;
+    if (st->owned) cudaFree(st->buf);
+    cudaFree(st->d_off);
+    for (auto& kv : st->groups) cudaFree(kv.second.d_off);
+    delete st;
+    return TCNG_OK;
+}
+
+tcng_status tcng_state_reset(tcng_state* st, void* stream) {
+    if (!st) return fail(TCNG_EINVAL, "state is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(st->buf, 0, st->bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    if (st->dt == TCNG_C64)
+        e = launch_set_basis<float2>(static_cast<float2*>(st->buf), st->d_off, st->batch, s);
+    else
+        e = launch_set_basis<double2>(static_cast<double2*>(st->buf), st->d_off, st->batch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "init kernel");
+    return TCNG_OK;
+}
+
+tcng_status tcng_state_init(tcng_state** out, tcng_dtype dt, int batch, const int* n_qubits,
+                            void* dev_buf, size_t buf_bytes, void* stream) {
+    if (!out) return fail(TCNG_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::vector<long long> off;
+    size_t bytes = 0;
+    tcng_status s = layout(dt, batch, n_qubits, off, &bytes);
+    if (s) return s;
+    std::lock_guard<std::mutex> lk(g_mu);
+    TCNG_TRY({
+        std::unique_ptr<tcng_state> st(new tcng_state());
+        st->dt = dt;
+        st->batch = batch;
+        st->n.assign(n_qubits, n_qubits + batch);
+        st->off = off;
+        st->bytes = bytes;
+        if (dev_buf) {
+            if (buf_bytes < bytes) return fail(TCNG_ENOMEM, "caller buffer too small");
+            if (reinterpret_cast<uintptr_t>(dev_buf) & 255)
+                return fail(TCNG_EINVAL, "caller buffer must be 256-byte aligned");
+            st->buf = dev_buf;
+            st->owned = false;
+        } else {
+            cudaError_t e = cudaMalloc(&st->buf, bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(TCNG_ENOMEM, std::string("state allocation: ") + cudaGetErrorString(e));
+            }
+            st->owned = true;
+        }
+        st->d_off = dev_copy(off);
+        for (int b = 0; b < batch; ++b) st->groups[n_qubits[b]].items.push_back(b);
+        for (auto& kv : st->groups) {
+            std::vector<long long> go;
+            for (int b : kv.second.items) go.push_back(off[b]);
+            kv.second.d_off = dev_copy(go);
+        }
+        tcng_state* raw = st.release();
+        s = tcng_state_reset(raw, stream);
+        if (s) {
+            tcng_state_free(raw);
+            return s;
+        }
+        *out = raw;
+        return TCNG_OK;
+    })
+}
+
+tcng_status tcng_state_ptr(const tcng_state* st, int item, void** dev_amp, size_t* bytes) {
+    if (!st || !dev_amp) return fail(TCNG_EINVAL, "null argument");
+    if (item < 0 || item >= st->batch) return fail(TCNG_EINVAL, "item out of range");
+    const size_t es = elem_size(st->dt);
+    *dev_amp = static_cast<char*>(st->buf) + st->off[item] * es;
+    if (bytes) *bytes = es << st->n[item];
+    return TCNG_OK;
+}
+
+tcng_status tcng_apply_circuit(tcng_state* st, const tcng_gate* ops, size_t n_ops,
+                               const double* mat_pool, size_t n_mat, const void* params_dev, int P,
+                               void* stream) {
+    if (!st) return fail(TCNG_EINVAL, "state is NULL");
+    if (P < 0) return fail(TCNG_EINVAL, "P < 0");
+    if (P > 0 && !params_dev) return fail(TCNG_EINVAL, "params_dev is NULL");
+    if (n_ops == 0) return TCNG_OK;
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TCNG_TRY({
+        const PlanOptions o = plan_options(st->dt, false);
+        for (auto& kv : st->groups) {
+            const int n = kv.first;
+            DevPlan* dp = get_plan(n, ops, n_ops, mat_pool, n_mat, P, o);
+            const int items = (int)kv.second.items.size();
+            // Parameters are indexed by position inside the group, so a ragged
+            // batch with parameters needs the items of one n to be contiguous.
+            const double* prm = static_cast<const double*>(params_dev);
+            if (P > 0 && st->groups.size() > 1) {
+                const std::vector<int>& it = kv.second.items;
+                for (size_t i = 1; i < it.size(); ++i)
+                    if (it[i] != it[0] + (int)i)
+                        return fail(TCNG_EUNSUPPORTED,
+                                    "ragged batch with parameters needs items of equal n to be contiguous");
+                prm += (size_t)it[0] * P;
+            }
+            tcng_status r;
+            if (st->dt == TCNG_C64)
+                r = run_plan<float2>(dp, static_cast<float2*>(st->buf), kv.second.d_off, items, prm, s);
+            else
+                r = run_plan<double2>(dp, static_cast<double2*>(st->buf), kv.second.d_off, items, prm, s);
+            if (r) return r;
+        }
+        return TCNG_OK;
+    })
+}
+
+// ------------------------------------------------------------ expectations --
+static tcng_status expect_impl(const tcng_state* st, const tcng_pauli* terms, size_t n_terms,
+                               double* out_dev, const double* coeffs_dev, double* energy_dev,
+                               cudaStream_t s) {
+    if (!st) return fail(TCNG_EINVAL, "state is NULL");
+    if (n_terms == 0) return TCNG_OK;
+    if (!terms) return fail(TCNG_EINVAL, "terms is NULL");
+    if (n_terms > 4096) return fail(TCNG_EINVAL, "at most 4096 terms per call");
+    if (st->groups.size() != 1)
+        return fail(TCNG_EUNSUPPORTED, "expectations of ragged batches: call per size class");
+    std::lock_guard<std::mutex> lk(g_mu);
+    TCNG_TRY({
+        const int n = st->n[0];
+        const int items = st->batch;
+        DeviceCtx& c = ctx();
+        const PlanOptions o = plan_options(st->dt, false);
+        std::vector<DevPass> passes;
+        std::vector<ExpPass> eps;
+        plan_expectation(n, o.tile_bits, o.chunk_bits, terms, n_terms, passes, eps);
+        TermSet* ts = get_terms(terms, n_terms, n);
+        const int m = passes[0].m;
+        const long long tpi = 1ll << (n - m);
+        const long long want = (num_sms() + items - 1) / items;
+        const int nblk = (int)std::max<long long>(1, std::min<long long>(tpi, want));
+        double* partial = static_cast<double*>(
+            c.scratch("exp_partial", sizeof(double) * (size_t)items * n_terms * nblk));
+        if (!partial) return fail(TCNG_ENOMEM, "expectation scratch");
+        for (size_t i = 0; i < passes.size(); ++i) {
+            cudaError_t e;
+            if (st->dt == TCNG_C64)
+                e = launch_expect_pass<float2>(static_cast<const float2*>(st->buf), st->d_off, items, n,
+                                               passes[i], eps[i], partial, (int)n_terms, nblk, c.err, s);
+            else
+                e = launch_expect_pass<double2>(static_cast<const double2*>(st->buf), st->d_off, items, n,
+                                                passes[i], eps[i], partial, (int)n_terms, nblk, c.err, s);
+            if (e != cudaSuccess) return cuda_fail(e, "expectation pass");
+        }
+        cudaError_t e = launch_expect_finalize(partial, nblk, (int)n_terms, out_dev, coeffs_dev, ts->d_c,
+                                               energy_dev, items, s);
+        if (e != cudaSuccess) return cuda_fail(e, "expectation finalize");
+        return TCNG_OK;
+    })
+}
+
+tcng_status tcng_expect_pauli(const tcng_state* st, const tcng_pauli* terms, size_t n_terms,
+                              double* out_dev, void* stream) {
+    if (!out_dev) return fail(TCNG_EINVAL, "out_dev is NULL");
+    return expect_impl(st, terms, n_terms, out_dev, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+tcng_status tcng_energy(const tcng_state* st, const tcng_pauli* terms, size_t n_terms,
+                        const double* coeffs_dev, double* energy_dev, void* stream) {
+    if (!energy_dev) return fail(TCNG_EINVAL, "energy_dev is NULL");
+    return expect_impl(st, terms, n_terms, nullptr, coeffs_dev, energy_dev,
+                       static_cast<cudaStream_t>(stream));
+}
+
+tcng_status tcng_hamiltonian_apply(const tcng_state* st, const tcng_pauli* terms, size_t n_terms,
+                                   const double* coeffs_dev, tcng_state* out, void* stream) {
+    if (!st || !out || (!terms && n_terms)) return fail(TCNG_EINVAL, "null argument");
+    if (out->dt != st->dt || out->batch != st->batch || out->n != st->n)
+        return fail(TCNG_EINVAL, "output state shape differs");
+    if (st->groups.size() != 1) return fail(TCNG_EUNSUPPORTED, "ragged batch");
+    std::lock_guard<std::mutex> lk(g_mu);
+    TCNG_TRY({
+        const int n = st->n[0];
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        TermSet* ts = get_terms(terms, n_terms, n);
+        cudaError_t e;
+        if (st->dt == TCNG_C64)
+            e = launch_ham_apply<float2>(static_cast<const float2*>(st->buf), st->d_off,
+                                         static_cast<float2*>(out->buf), out->d_off, st->batch, n,
+                                         ts->d_h, (int)n_terms, coeffs_dev, ts->d_c, s);
+        else
+            e = launch_ham_apply<double2>(static_cast<const double2*>(st->buf), st->d_off,
+                                          static_cast<double2*>(out->buf), out->d_off, st->batch, n,
+                                          ts->d_h, (int)n_terms, coeffs_dev, ts->d_c, s);
+        if (e != cudaSuccess) return cuda_fail(e, "H apply");
+        return TCNG_OK;
+    })
+}
+
+tcng_status tcng_set_option(tcng_option opt, int value) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    switch (opt) {
+    case TCNG_OPT_FUSE_WIDTH:
+        if (value < 1 || value > TCNG_MAX_FUSE) return fail(TCNG_EINVAL, "fuse width 1..5");
+        g_opt.fuse_width = value;
+        return TCNG_OK;
+    case TCNG_OPT_TILE_BITS:
+        if (value < 5 || value > 13) return fail(TCNG_EINVAL, "tile bits 5..13");
+        g_opt.tile_bits = value;
+        return TCNG_OK;
+    case TCNG_OPT_CHUNK_BITS:
+        if (value < 1 || value > 13) return fail(TCNG_EINVAL, "chunk bits 1..13");
+        g_opt.chunk_bits = value;
+        return TCNG_OK;
+    case TCNG_OPT_USE_GRAPHS:
+        g_opt.use_graphs = value ? 1 : 0;
+        return TCNG_OK;
+    case TCNG_OPT_UNFUSED:
+        g_opt.unfused = value ? 1 : 0;
+        return TCNG_OK;
+    }
+    return fail(TCNG_EINVAL, "unknown option");
+}
+
+tcng_status tcng_get_option(tcng_option opt, int* value) {
+    if (!value) return fail(TCNG_EINVAL, "value is NULL");
+    switch (opt) {
+    case TCNG_OPT_FUSE_WIDTH: *value = g_opt.fuse_width; return TCNG_OK;
+    case TCNG_OPT_TILE_BITS: *value = g_opt.tile_bits; return TCNG_OK;
+    case TCNG_OPT_CHUNK_BITS: *value = g_opt.chunk_bits; return TCNG_OK;
+    case TCNG_OPT_USE_GRAPHS: *value = g_opt.use_graphs; return TCNG_OK;
+    case TCNG_OPT_UNFUSED: *value = g_opt.unfused; return TCNG_OK;
+    }
+    return fail(TCNG_EINVAL, "unknown option");
+}
+
+tcng_status tcng_sync_status(void) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    DeviceCtx& c = ctx();
+    unsigned h = 0;
+    if (c.err) {
+        cudaMemcpy(&h, c.err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+        if (h) {
+            cudaMemset(c.err, 0, sizeof(unsigned));
+            if (h & ERR_TIMEOUT_FLAG) return fail(TCNG_ETIMEOUT, "a device-side wait timed out");
+            return fail(TCNG_EINVAL, "device reported an invalid work item");
+        }
+    }
+    return TCNG_OK;
+}
+
+const char* tcng_describe_plan(int n, const tcng_gate* ops, size_t n_ops, const double* mat_pool,
+                               size_t n_mat, int P, int adjoint) {
+    static thread_local std::string out;
+    try {
+        Plan pl;
+        pl.n = n;
+        pl.P = P;
+        pl.opt = plan_options(TCNG_C64, adjoint != 0);
+        if (n < 5 && !adjoint) pl.opt.unfused = 1;
+        pl.ops = import_ops(n, ops, n_ops, n_mat, P, mat_pool);
+        build_plan(pl);
+        out = describe_plan(pl);
+    } catch (const std::exception& ex) {
+        out = std::string("error: ") + ex.what();
+    }
+    return out.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Host-side state of the C ABI layer (shared by the host .cu files).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.hpp"
+#include "launch.hpp"
+
+struct tcng_state {
+    struct Group {
+        std::vector<int> items;
+        long long* d_off = nullptr;   // device element offsets of the group's items
+    };
+    tcng_dtype dt = TCNG_C64;
+    int batch = 0;
+    std::vector<int> n;
+    std::vector<long long> off;       // element offset of each item
+    size_t bytes = 0;
+    void* buf = nullptr;
+    bool owned = false;
+    long long* d_off = nullptr;
+    std::map<int, Group> groups;      // items by qubit count
+};
+
+namespace tcng {
+
+constexpr unsigned ERR_TIMEOUT_FLAG = 1u;
+
+struct Options {
+    int fuse_width = 2;
+    int tile_bits = 13;
+    int chunk_bits = 7;
+    int use_graphs = 1;
+    int unfused = 0;
+};
+extern Options g_opt;
+extern std::mutex g_mu;
+
+struct DevPlan {
+    Plan plan;
+    BuildBlock* d_bblocks = nullptr;
+    BuildOp* d_bops = nullptr;
+    double2* d_pool = nullptr;
+    DevStage* d_stages = nullptr;
+    DevOp* d_dops = nullptr;
+    int* d_gparam = nullptr;
+    double* d_gscale = nullptr;
+    void* d_table = nullptr;
+    size_t table_bytes = 0;
+    ~DevPlan();
+};
+
+struct TermSet {
+    int n_terms = 0;
+    HTerm* d_h = nullptr;
+    double* d_c = nullptr;
+    ~TermSet();
+};
+
+struct DeviceCtx {
+    struct Buf {
+        void* ptr = nullptr;
+        size_t bytes = 0;
+    };
+    int device = 0;
+    unsigned* err = nullptr;
+    std::unordered_map<uint64_t, std::unique_ptr<DevPlan>> plans;
+    std::unordered_map<uint64_t, std::unique_ptr<TermSet>> terms;
+    std::map<std::string, Buf> bufs;
+    void* scratch(const std::string& name, size_t bytes);
+};
+
+DeviceCtx& ctx();
+tcng_status fail(tcng_status s, const std::string& msg);
+tcng_status cuda_fail(cudaError_t e, const char* where);
+PlanOptions plan_options(tcng_dtype dt, bool adjoint);
+DevPlan* get_plan(int n, const tcng_gate* ops, size_t n_ops, const double* pool, size_t n_mat, int P,
+                  const PlanOptions& o);
+void* plan_table(DevPlan* dp, size_t elem, int items);
+TermSet* get_terms(const tcng_pauli* terms, size_t n_terms, int n);
+template <typename C>
+tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int items,
+                     const double* params, cudaStream_t s);
+
+// Synchronous upload of a host vector (used once per structure); throws bad_alloc.
+template <typename T>
+T* dev_copy(const std::vector<T>& v) {
+    if (v.empty()) return nullptr;
+    T* p = nullptr;
+    if (cudaMalloc(&p, sizeof(T) * v.size()) != cudaSuccess) {
+        cudaGetLastError();
+        throw std::bad_alloc();
+    }
+    cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    return p;
+}
+
+}  // namespace tcng

@@ -1,0 +1,42 @@
+// Entry points whose kernels are not in this build yet: they fail loudly.
+#include "capi_internal.hpp"
+
+using namespace tcng;
+
+extern "C" {
+
+tcng_status tcng_energy_grad(tcng_state*, const tcng_gate*, size_t, const double*, size_t,
+                             const void*, int, const tcng_pauli*, size_t, const double*, double*,
+                             double*, void*) {
+    return fail(TCNG_EUNSUPPORTED, "tcng_energy_grad is not built yet");
+}
+tcng_status tcng_energy_grad_ragged(const tcng_problem*, int, const int*, int, const double*,
+                                    const double*, double*, double*, void*) {
+    return fail(TCNG_EUNSUPPORTED, "tcng_energy_grad_ragged is not built yet");
+}
+tcng_status tcng_apply_shared_unitary(tcng_state*, const int*, int, const double*, void*) {
+    return fail(TCNG_EUNSUPPORTED, "tcng_apply_shared_unitary is not built yet");
+}
+tcng_status tcng_adam_step(double*, double*, double*, const double*, size_t, double, double, double,
+                           double, int*, void*) {
+    return fail(TCNG_EUNSUPPORTED, "tcng_adam_step is not built yet");
+}
+tcng_status tcng_adam_step_f32(float*, float*, float*, const float*, size_t, float, float, float,
+                               float, int*, void*) {
+    return fail(TCNG_EUNSUPPORTED, "tcng_adam_step_f32 is not built yet");
+}
+tcng_status tcng_mlp_forward(const float*, int, int, int, int, const float*, const float*,
+                             const float*, const float*, const float*, const float*, float*, float*,
+                             void*) {
+    return fail(TCNG_EUNSUPPORTED, "tcng_mlp_forward is not built yet");
+}
+tcng_status tcng_mlp_backward(const float*, int, int, int, int, const float*, const float*,
+                              const float*, const float*, const float*, const float*, const float*,
+                              float*, double*, void*) {
+    return fail(TCNG_EUNSUPPORTED, "tcng_mlp_backward is not built yet");
+}
+tcng_status tcng_autotune(int, tcng_dtype, int, const char*) {
+    return fail(TCNG_EUNSUPPORTED, "tcng_autotune is not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,280 @@
+// Device helpers: complex arithmetic, bulk-copy (TMA) and mbarrier PTX wrappers,
+// and the register-stage executor shared by the tile-pass kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "internal.hpp"
+
+namespace tcng {
+
+// ------------------------------------------------------------------ errors --
+enum : unsigned {
+    ERR_TIMEOUT = 1u,   // a bounded mbarrier wait expired
+    ERR_BAD_ITEM = 2u,  // a work item referenced an invalid structure
+};
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s per wait
+
+// ----------------------------------------------------------------- complex --
+template <typename C> struct Real;
+template <> struct Real<float2> { using T = float; };
+template <> struct Real<double2> { using T = double; };
+
+template <typename C> __device__ __forceinline__ C cmk(typename Real<C>::T x, typename Real<C>::T y) {
+    C r; r.x = x; r.y = y; return r;
+}
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc += a * b
+template <typename C> __device__ __forceinline__ void cfma(C& acc, C a, C b) {
+    acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+    acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
+
+// ------------------------------------------------------------- bit helpers --
+__host__ __device__ constexpr int cpopc(int v) { return v ? (v & 1) + cpopc(v >> 1) : 0; }
+// deposit the low bits of v into the set positions of mask (compile-time friendly)
+__host__ __device__ constexpr int cscatter(int v, int mask) {
+    int out = 0, b = 0;
+    for (int p = 0; p < 8; ++p)
+        if ((mask >> p) & 1) { if ((v >> b) & 1) out |= 1 << p; ++b; }
+    return out;
+}
+__device__ __forceinline__ int pext4(int v, int mask) {
+    int out = 0, b = 0;
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+        if ((mask >> p) & 1) { out |= ((v >> p) & 1) << b; ++b; }
+    return out;
+}
+
+// ------------------------------------------------------------------- PTX --
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait: false (and error word set) if the phase did not complete in time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned* err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
+            if (err) atomicOr(err, ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes,
+                                         uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void* dst_gmem, const void* src_smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
+                 "r"(smem_u32(src_smem)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+template <int N> __device__ __forceinline__ void bulk_wait() {
+    asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// ---------------------------------------------------- tile index mapping --
+// Global index (within an item) of tile offset 0: the tile number's bits are
+// deposited into the global bits outside the tile.
+__device__ __forceinline__ long long tile_global_base(const DevPass& p, long long tile) {
+    long long base = 0;
+    for (int i = 0; i < p.nrest; ++i)
+        if ((tile >> i) & 1) base |= 1ll << p.rest[i];
+    return base;
+}
+// Global offset (relative to the tile base) of chunk j (gather pattern j).
+__device__ __forceinline__ long long chunk_offset(const DevPass& p, int j) {
+    long long off = 0;
+    for (int i = 0; i < p.ngather; ++i)
+        if ((j >> i) & 1) off |= 1ll << p.gather[i];
+    return off;
+}
+// Insert a zero bit at each register position (ascending) into g.
+__device__ __forceinline__ int insert_zero_bits(int g, const uint8_t* rbit) {
+#pragma unroll
+    for (int i = 0; i < kRegBits; ++i) {
+        const int p = rbit[i];
+        g = ((g >> p) << (p + 1)) | (g & ((1 << p) - 1));
+    }
+    return g;
+}
+
+// -------------------------------------------------------- dense register op --
+// a[16] holds the amplitudes of one group: slot s holds tile offset
+// base | scatter(s ^ tau) (XOR rotation by tau spreads shared-memory banks).
+// Apply a 2^K x 2^K matrix (row-major, ascending local order) on register bits
+// MASK; DAG applies the conjugate transpose.
+template <typename C, int MASK, bool DAG>
+__device__ __forceinline__ void dense_apply(C (&a)[16], const C* __restrict__ M, int tau) {
+    constexpr int K = cpopc(MASK);
+    constexpr int D = 1 << K;
+    constexpr int OMASK = 15 & ~MASK;
+    constexpr int NOUT = 16 >> K;
+    const int t = pext4(tau, MASK);
+    if constexpr (K <= 2) {
+        C m[D][D];
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                if constexpr (DAG) m[r][c] = cconj(M[((c ^ t) << K) | (r ^ t)]);
+                else m[r][c] = M[((r ^ t) << K) | (c ^ t)];
+            }
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) {
+            const int base = cscatter(o, OMASK);
+            C v[D];
+#pragma unroll
+            for (int s = 0; s < D; ++s) v[s] = a[base | cscatter(s, MASK)];
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                C acc = cmk<C>(0, 0);
+#pragma unroll
+                for (int s = 0; s < D; ++s) cfma(acc, m[r][s], v[s]);
+                a[base | cscatter(r, MASK)] = acc;
+            }
+        }
+    } else {
+        C v[NOUT][D];
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o)
+#pragma unroll
+            for (int s = 0; s < D; ++s) v[o][s] = a[cscatter(o, OMASK) | cscatter(s, MASK)];
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            C acc[NOUT];
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) acc[o] = cmk<C>(0, 0);
+#pragma unroll
+            for (int s = 0; s < D; ++s) {
+                C mv;
+                if constexpr (DAG) mv = cconj(M[((s ^ t) << K) | (r ^ t)]);
+                else mv = M[((r ^ t) << K) | (s ^ t)];
+#pragma unroll
+                for (int o = 0; o < NOUT; ++o) cfma(acc[o], mv, v[o][s]);
+            }
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) a[cscatter(o, OMASK) | cscatter(r, MASK)] = acc[o];
+        }
+    }
+}
+
+template <typename C, bool DAG>
+__device__ __forceinline__ void dense_dispatch(int mask, C (&a)[16], const C* M, int tau) {
+    switch (mask) {
+#define TCNG_CASE(m) case m: dense_apply<C, m, DAG>(a, M, tau); break;
+        TCNG_CASE(1) TCNG_CASE(2) TCNG_CASE(3) TCNG_CASE(4) TCNG_CASE(5) TCNG_CASE(6)
+        TCNG_CASE(7) TCNG_CASE(8) TCNG_CASE(9) TCNG_CASE(10) TCNG_CASE(11) TCNG_CASE(12)
+        TCNG_CASE(13) TCNG_CASE(14) TCNG_CASE(15)
+#undef TCNG_CASE
+        default: break;
+    }
+}
+
+// Bit of qubit source `src` for tile offset L in a tile whose global base is gbase.
+__device__ __forceinline__ int src_bit(uint8_t src, int L, long long gbase) {
+    return (src & kSrcBase) ? int((gbase >> (src & 63)) & 1) : ((L >> src) & 1);
+}
+
+// Diagonal op: multiply slot s by M[pext of its qubit bits].
+template <typename C, bool DAG>
+__device__ __forceinline__ void diag_apply(C (&a)[16], const DevOp& op, const C* __restrict__ M,
+                                           const int (&L)[16], long long gbase) {
+    const int k = op.k;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        int idx = 0;
+        for (int j = 0; j < k; ++j) idx |= src_bit(op.src[j], L[s], gbase) << j;
+        C d = M[idx];
+        if constexpr (DAG) d = cconj(d);
+        a[s] = cmul(d, a[s]);
+    }
+}
+
+// Tile offsets of the 16 slots of group g in a stage with register bits rbit.
+__device__ __forceinline__ void group_offsets(int g, const uint8_t* rbit, int (&L)[16]) {
+    const int base = insert_zero_bits(g, rbit);
+    const int tau = g & 15;
+    int sr[kRegBits];
+#pragma unroll
+    for (int i = 0; i < kRegBits; ++i) sr[i] = 1 << rbit[i];
+    int stau = 0;
+#pragma unroll
+    for (int i = 0; i < kRegBits; ++i) stau |= ((tau >> i) & 1) ? sr[i] : 0;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        int o = 0;
+#pragma unroll
+        for (int i = 0; i < kRegBits; ++i) o |= ((s >> i) & 1) ? sr[i] : 0;
+        L[s] = base | (o ^ stau);
+    }
+}
+
+// Stage executor: one group (16 amplitudes) of one tile, forward direction.
+template <typename C>
+__device__ __forceinline__ void run_stage_group(C* __restrict__ buf, const DevStage& st,
+                                                const DevOp* __restrict__ ops, const C* __restrict__ mats,
+                                                int g, long long gbase) {
+    int L[16];
+    group_offsets(g, st.rbit, L);
+    const int tau = g & 15;
+    C a[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) a[s] = buf[L[s]];
+    for (uint32_t i = 0; i < st.op_count; ++i) {
+        const DevOp op = ops[st.op_begin + i];
+        const C* M = mats + op.mat;
+        if (op.kind == K_DENSE) dense_dispatch<C, false>(op.mask, a, M, tau);
+        else diag_apply<C, false>(a, op, M, L, gbase);
+    }
+#pragma unroll
+    for (int s = 0; s < 16; ++s) buf[L[s]] = a[s];
+}
+
+}  // namespace tcng
