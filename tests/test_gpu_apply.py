@@ -1,0 +1,211 @@
+"""GPU parity: tcng_apply_circuit / tcng_expect_pauli / tcng_energy vs the oracle.
+
+Tolerances (relative L2 error of amplitudes; absolute for <P> with |<P>| <= 1;
+|dE| / sum|c| for energies): complex128 1e-12, complex64 1e-5 and fidelity
+>= 1 - 1e-5.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import sv  # noqa: E402
+from workloads import generators as gen  # noqa: E402
+
+TOL = {"c64": 1e-5, "c128": 1e-12}
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2602_14167_b300 import build
+    build.build()
+    from paper_2602_14167_b300 import tcng
+    return tcng
+
+
+@pytest.fixture(autouse=True)
+def default_options(T):
+    saved = {o: T.tcng_get_option(o) for o in range(5)}
+    yield
+    for o, v in saved.items():
+        T.tcng_set_option(o, v)
+
+
+def run(n, gates, pool, theta, dtype, batch=1):
+    from paper_2602_14167_b300 import StateBatch
+    st = StateBatch(n, batch=batch, dtype=dtype)
+    prm = None
+    if theta is not None and np.size(theta):
+        prm = torch.tensor(np.atleast_2d(theta), dtype=torch.float64, device="cuda")
+        if prm.shape[0] != batch:
+            prm = prm.expand(batch, -1).contiguous()
+    st.apply(gates, pool, prm)
+    torch.cuda.synchronize()
+    return st
+
+
+def relerr(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def check_state(psi, ref, dtype):
+    assert relerr(psi, ref) < TOL[dtype], relerr(psi, ref)
+    if dtype == "c64":
+        fid = abs(np.vdot(ref, psi)) ** 2 / (np.vdot(psi, psi).real * np.vdot(ref, ref).real)
+        assert fid >= 1 - 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n", [5, 7, 10, 13, 15, 17])
+def test_random_circuit_all_ops(T, n, dtype):
+    c, th = gen.random_circuit(n, 120, seed=n)
+    g, p = c.to_ir()
+    st = run(n, g, p, th, dtype)
+    check_state(st.amplitudes(0).cpu().numpy(), sv.apply(n, g, p, th), dtype)
+
+
+@pytest.mark.parametrize("width", [1, 2, 3, 4, 5])
+def test_fusion_widths(T, width):
+    T.tcng_set_option(T.OPT_FUSE_WIDTH, width)
+    n = 14
+    c, th = gen.random_circuit(n, 150, seed=100 + width)
+    g, p = c.to_ir()
+    st = run(n, g, p, th, "c128")
+    check_state(st.amplitudes(0).cpu().numpy(), sv.apply(n, g, p, th), "c128")
+
+
+@pytest.mark.parametrize("tile,chunk", [(6, 2), (8, 3), (9, 1), (13, 7), (12, 12)])
+def test_small_tiles_many_passes(T, tile, chunk):
+    """Small tiles force many gather passes at a size the oracle does instantly."""
+    T.tcng_set_option(T.OPT_TILE_BITS, tile)
+    T.tcng_set_option(T.OPT_CHUNK_BITS, chunk)
+    n = 12
+    c, th = gen.su4_brickwork(n, 6, "RZ", seed=7)
+    g, p = c.to_ir()
+    for dtype in ("c64", "c128"):
+        st = run(n, g, p, th, dtype)
+        check_state(st.amplitudes(0).cpu().numpy(), sv.apply(n, g, p, th), dtype)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_unfused_pair_quartet_kernels(T, dtype):
+    T.tcng_set_option(T.OPT_UNFUSED, 1)
+    n = 11
+    c, th = gen.random_circuit(n, 100, seed=3)
+    g, p = c.to_ir()
+    st = run(n, g, p, th, dtype)
+    check_state(st.amplitudes(0).cpu().numpy(), sv.apply(n, g, p, th), dtype)
+
+
+def test_batch_with_per_item_params(T):
+    n, B = 9, 5
+    c = gen.hea_ring(n, 3)
+    g, p = c.to_ir()
+    th = gen.random_thetas((B, c.n_params), seed=1)
+    st = run(n, g, p, th, "c128", batch=B)
+    for b in range(B):
+        check_state(st.amplitudes(b).cpu().numpy(), sv.apply(n, g, p, th[b]), "c128")
+
+
+def test_config1_ry_cx_ladder(T):
+    """n=10 complex128: full state, <Z0 Z1> and the TFIM energy (g=1)."""
+    c, th = gen.ry_cx_ladder(10, 4, seed=0)
+    g, p = c.to_ir()
+    st = run(10, g, p, th, "c128")
+    ref = sv.apply(10, g, p, th)
+    check_state(st.amplitudes(0).cpu().numpy(), ref, "c128")
+    from workloads import pauli_terms
+    zz = pauli_terms([{0: "Z", 1: "Z"}])
+    assert abs(float(st.expect(zz)[0, 0]) - sv.expect(10, ref, zz)[0].real) < 1e-12
+    terms = gen.tfim_terms(10, 1.0, 1.0)
+    e = float(st.energy(terms)[0])
+    e_ref = sv.energy(10, g, p, th, terms)
+    assert abs(e - e_ref) / np.abs(terms["coeff"]).sum() < 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_config2_n24_brickwork(T, dtype):
+    """n=24, depth-20 SU(4) brickwork with RX layers; energy and 32 weight-4 strings."""
+    n = 24
+    c, th = gen.su4_brickwork(n, 20, "RX", seed=0)
+    g, p = c.to_ir()
+    st = run(n, g, p, th, dtype)
+    ref = sv.apply(n, g, p, th)
+    check_state(st.amplitudes(0).cpu().numpy(), ref, dtype)
+    strings = gen.random_pauli_strings(n, 32, 4, seed=1)
+    vals = st.expect(strings)[0].cpu().numpy()
+    vref = sv.expect(n, ref, strings).real
+    assert np.max(np.abs(vals - vref)) < TOL[dtype]
+    terms = gen.tfim_terms(n, 1.0, 1.0)
+    e = float(st.energy(terms)[0])
+    e_ref = float(np.dot(terms["coeff"], sv.expect(n, ref, terms).real))
+    assert abs(e - e_ref) / np.abs(terms["coeff"]).sum() < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n", [6, 11, 16])
+def test_expectations_random_strings(T, n, dtype):
+    psi0 = gen.random_state(n, seed=n)
+    from paper_2602_14167_b300 import StateBatch
+    st = StateBatch(n, dtype=dtype)
+    st.amplitudes(0).copy_(torch.tensor(psi0, dtype=st.cdtype, device="cuda"))
+    strings = np.concatenate([gen.random_pauli_strings(n, 40, min(4, n), seed=2),
+                              gen.random_pauli_strings(n, 10, 1, seed=3),
+                              gen.tfim_terms(n, 0.7, 0.3)])
+    vals = st.expect(strings)[0].cpu().numpy()
+    ref_psi = st.amplitudes(0).cpu().numpy().astype(np.complex128)
+    vref = sv.expect(n, ref_psi, strings).real
+    assert np.max(np.abs(vals - vref)) < (1e-6 if dtype == "c64" else 1e-12)
+
+
+def test_energy_per_item_coefficients(T):
+    n, B = 12, 4
+    b = gen.tfim_batch(n, B, layers=2, seed=3)
+    g, p = b["circuit"].to_ir()
+    st = run(n, g, p, b["theta"], "c128", batch=B)
+    coeffs = torch.tensor(b["coeffs"], dtype=torch.float64, device="cuda")
+    e = st.energy(b["terms"], coeffs).cpu().numpy()
+    for i in range(B):
+        e_ref = sv.energy(n, g, p, b["theta"][i], b["terms"], b["coeffs"][i])
+        assert abs(e[i] - e_ref) < 1e-11
+
+
+def test_hamiltonian_apply(T):
+    n = 10
+    from paper_2602_14167_b300 import StateBatch
+    st = StateBatch(n, dtype="c128")
+    out = StateBatch(n, dtype="c128")
+    psi0 = gen.random_state(n, seed=4)
+    st.amplitudes(0).copy_(torch.tensor(psi0, device="cuda"))
+    terms = gen.xxz_terms(n, np.linspace(0.5, 1.5, n - 1), 0.6, 0.4)
+    T.tcng_hamiltonian_apply(st.handle, terms, None, out.handle)
+    torch.cuda.synchronize()
+    ref = sv.hamiltonian_apply(n, psi0, terms)
+    assert relerr(out.amplitudes(0).cpu().numpy(), ref) < 1e-12
+
+
+def test_expectation_is_deterministic(T):
+    n = 18
+    c, th = gen.su4_brickwork(n, 4, "RZ", seed=5)
+    g, p = c.to_ir()
+    st = run(n, g, p, th, "c64")
+    s = gen.random_pauli_strings(n, 20, 4, seed=6)
+    a = st.expect(s).cpu().numpy()
+    b = st.expect(s).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_invalid_arguments_are_rejected(T):
+    from paper_2602_14167_b300 import StateBatch
+    st = StateBatch(6, dtype="c64")
+    from workloads import Circuit
+    bad = Circuit(7).x(6)
+    g, p = bad.to_ir()
+    with pytest.raises(T.TcngError):
+        st.apply(g, p)
+    with pytest.raises(T.TcngError):
+        st.expect(np.array([(1 << 6, 0, 1.0)], dtype=T.PAULI_DTYPE))
+    T.tcng_sync_status()
