@@ -1,0 +1,304 @@
+"""Benchmark: 32-qubit complex64 state-vector step on one B300 per rank.
+
+One step = |0..0> init, a depth-14 Haar-SU(4) brickwork with RZ(theta) layers
+(fused into <=2-qubit blocks and grouped into shared-memory tile passes), the
+64 random weight-4 Pauli-string expectations and the open-chain TFIM energy
+(g = 1).  Metric: statevector GB/s = HBM bytes the step's kernels move (every
+tile pass reads and writes the 32 GiB state once, every expectation pass reads
+it once, init writes it once) / step time.  The state (32 GiB) is far larger
+than L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+N > 1 runs under torch.distributed.run: one independent replica per GPU
+(the single-state workload does not shard), value = sum over replicas.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import generators as gen  # noqa: E402
+
+N_QUBITS = 32
+DEPTH = 14
+N_STRINGS = 64
+METRIC = "statevector GB/s (% HBM peak) at 32 qubits; VQE energy+adjoint-grad evals/s"
+REF_N = 28          # oracle sample size (complex128, 4 GiB)
+REF_GATES = 4       # gates per reference step
+
+
+def workload():
+    c, theta = gen.su4_brickwork(N_QUBITS, DEPTH, "RZ", seed=0)
+    gates, pool = c.to_ir()
+    strings = gen.random_pauli_strings(N_QUBITS, N_STRINGS, 4, seed=1)
+    tfim = gen.tfim_terms(N_QUBITS, 1.0, 1.0)
+    return c, gates, pool, theta, strings, tfim
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": smax or None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(steps: int, gates_per_step: int):
+    """Time the oracle (as it stands) on the 28-qubit slice: c128 state, unfused gates."""
+    from oracle import sv
+    c, *_ = workload()
+    sl = gen.slice_circuit(c, REF_N)
+    g, p = sl.to_ir()
+    _, theta = gen.su4_brickwork(N_QUBITS, DEPTH, "RZ", seed=0)
+    psi = sv.zero_state(REF_N)
+    state_bytes = 16 * (1 << REF_N)
+    times = []
+    k = 0
+    for _ in range(steps):
+        sel = g[k:k + gates_per_step]
+        k += gates_per_step
+        t0 = time.perf_counter()
+        psi = sv.apply(REF_N, sel, p, theta, psi=psi)
+        times.append(time.perf_counter() - t0)
+    moved = 2 * state_bytes * gates_per_step
+    return moved, times, sv.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    moved, times, cores = oracle_sample(args.warmup + args.steps, REF_GATES)
+    t = sum(times[args.warmup:])
+    value = moved * args.steps / t / 1e9
+    sample = (f"oracle (plain C, complex128, unfused) applying {REF_GATES} gates per step of the "
+              f"{REF_N}-qubit slice of the depth-{DEPTH} brickwork; GB/s = 2 x state bytes per gate")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+           "config": {"workload": f"su4 brickwork n={REF_N} (slice of n={N_QUBITS}) depth {DEPTH}",
+                      "note": "bounded CPU sample"},
+           "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    from paper_2602_14167_b300 import StateBatch
+    from paper_2602_14167_b300 import tcng as T
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    c, gates, pool, theta, strings, tfim = workload()
+    st = StateBatch(N_QUBITS, dtype="c64", device=dev)
+    S = 8 * (1 << N_QUBITS)
+    params = torch.tensor(theta, dtype=torch.float64, device=dev).reshape(1, -1)
+    vals = torch.empty((1, N_STRINGS), dtype=torch.float64, device=dev)
+    energy = torch.empty(1, dtype=torch.float64, device=dev)
+    P = params.shape[1]
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        T.tcng_state_reset(st.handle)
+        T.tcng_apply_circuit(st.handle, gates, pool, params, P)
+        T.tcng_expect_pauli(st.handle, strings, vals)
+        T.tcng_energy(st.handle, tfim, None, energy)
+
+    # warm-up (first call builds and uploads the plans)
+    T.tcng_profile_enable(True)
+    step()
+    prof1 = T.tcng_profile_read(reset=True)
+    n_pass = prof1.get("pass_kernel_c64", (0, 0))[0]
+    n_exp = prof1.get("expect_pass_c64", (0, 0))[0]
+    step_bytes = S + n_pass * 2 * S + n_exp * S
+    for _ in range(max(0, args.warmup - 1)):
+        step()
+    torch.cuda.synchronize()
+    T.tcng_profile_read(reset=True)
+
+    # timed region: device-resident inputs
+    l0 = T.tcng_launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = T.tcng_launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    prof = T.tcng_profile_read(reset=True)
+    T.tcng_profile_enable(False)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t[0])
+    ms_step = ms / args.steps
+    value = world * step_bytes * args.steps / (ms * 1e-3) / 1e9
+
+    # end to end through the public API: theta from pinned host, results back to pinned host
+    theta_host = torch.tensor(theta, dtype=torch.float64).reshape(1, -1).pin_memory()
+    vals_host = torch.empty((1, N_STRINGS), dtype=torch.float64).pin_memory()
+    e_host = torch.empty(1, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        params.copy_(theta_host, non_blocking=True)
+        step()
+        vals_host.copy_(vals, non_blocking=True)
+        e_host.copy_(energy, non_blocking=True)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t[0])
+    e2e = world * step_bytes * args.steps / t_e2e / 1e9
+
+    peak, peak_kind = peaks()
+    pk = prof.get("pass_kernel_c64", (0, 0.0))
+    avg_pass_ms = pk[1] / max(pk[0], 1)
+    achieved = 2 * S / (avg_pass_ms * 1e-3) / 1e9 if pk[0] else None
+    out = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+           "data": "synthetic",
+           "config": {"workload": f"su4 brickwork + RZ layers, n={N_QUBITS}, depth {DEPTH}, "
+                                  f"{N_STRINGS} weight-4 Pauli strings + TFIM energy",
+                      "qubits": N_QUBITS, "depth": DEPTH, "state_GiB": S / 2**30,
+                      "tile_passes_per_step": n_pass, "expect_passes_per_step": n_exp,
+                      "step_bytes_GB": step_bytes / 1e9,
+                      "ms_per_layer": ms_step / DEPTH,
+                      "l2": "inputs larger than L2 (32 GiB state), no flush",
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": (achieved / peak) if achieved else None, "traffic": None,
+                        "kernel": "pass_kernel_c64", "peak_kind": peak_kind,
+                        "algorithmic_bytes_per_launch": 2 * S,
+                        "avg_launch_ms": avg_pass_ms},
+           "kernel_ms": {k: [v[0], v[1]] for k, v in prof.items()},
+           "clocks": clk.summary(),
+           "e2e": {"value": e2e, "unit": "GB/s", "h2d_bytes_per_step": int(theta_host.numel() * 8),
+                   "d2h_bytes_per_step": int((N_STRINGS + 1) * 8)},
+           "gpu_launches": int(launches)}
+    st.free()
+    del st
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        moved, times, cores = oracle_sample(3, 4)
+        v = moved * len(times) / sum(times) / 1e9
+        out["cpu_baseline"] = {
+            "value": v, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle applying 12 unfused gates of the {REF_N}-qubit complex128 slice "
+                      f"({sum(times):.1f} s); GB/s = 2 x state bytes per gate / time"}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -293,6 +293,16 @@ tcng_status tcng_sync_status(void);
 const char* tcng_describe_plan(int n, const tcng_gate* ops, size_t n_ops, const double* mat_pool,
                                size_t n_mat, int P, int adjoint);
 
+/*
+ * Kernel timing with CUDA events recorded on the launch stream around every
+ * kernel this library launches (off by default; a few microseconds per launch
+ * when on).  tcng_profile_read synchronises the device and writes
+ * "name count total_ms\n" lines, one per kernel kind, into buf (NUL-terminated,
+ * truncated to len); reset clears the records.
+ */
+tcng_status tcng_profile_enable(int on);
+tcng_status tcng_profile_read(char* buf, size_t len, int reset);
+
 /* Kernels this library launched since load (for accounting). */
 uint64_t tcng_launch_count(void);
 

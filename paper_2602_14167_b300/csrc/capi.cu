@@ -34,6 +34,29 @@ tcng_status cuda_fail(cudaError_t e, const char* where) {
 Options g_opt;
 std::mutex g_mu;
 
+// ------------------------------------------------------------- profiling --
+struct ProfRec {
+    std::string name;
+    cudaEvent_t e0, e1;
+};
+static bool g_prof = false;
+static std::mutex g_prof_mu;
+static std::vector<ProfRec> g_prof_recs;
+
+ProfScope::ProfScope(const char* nm, cudaStream_t st) : name(nm), s(st) {
+    if (!g_prof) return;
+    cudaEventCreate(&e0);
+    cudaEventRecord(e0, s);
+}
+ProfScope::~ProfScope() {
+    if (!e0) return;
+    cudaEvent_t e1;
+    cudaEventCreate(&e1);
+    cudaEventRecord(e1, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_recs.push_back({name, e0, e1});
+}
+
 // ------------------------------------------------------------ device ctx --
 DeviceCtx& ctx() {
     static std::map<int, std::unique_ptr<DeviceCtx>> ctxs;
@@ -190,19 +213,25 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
     C* table = static_cast<C*>(plan_table(dp, sizeof(C), tab_items));
     if (!table) return fail(TCNG_ENOMEM, "matrix table allocation failed");
     const long long stride = pl.P > 0 ? pl.table_size : 0;
-    cudaError_t e = launch_build_matrices<C>(dp->d_bblocks, (int)pl.bblocks.size(), dp->d_bops,
+    cudaError_t e;
+    {
+    ProfScope ps("build_matrices", s);
+    e = launch_build_matrices<C>(dp->d_bblocks, (int)pl.bblocks.size(), dp->d_bops,
                                              dp->d_pool, pl.P > 0 ? params : nullptr, pl.P, table,
                                              pl.table_size, tab_items, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "matrix prologue");
     if (pl.opt.unfused) {
         for (const Block& b : pl.blocks) {
+            ProfScope ps(b.diag ? "gate_diag" : (b.k <= 2 ? "gate_pair_quartet" : "gate_dense"), s);
             e = launch_gate<C>(state, d_item_off, items, pl.n, b, table, stride, s);
             if (e != cudaSuccess) return cuda_fail(e, "gate kernel");
         }
     } else {
         for (const DevPass& p : pl.passes) {
-            e = launch_pass<C>(state, d_item_off, items, pl.n, p, dp->d_stages, dp->d_dops, table,
-                               stride, ctx().err, s);
+            ProfScope ps(sizeof(C) == 8 ? "pass_kernel_c64" : "pass_kernel_c128", s);
+            e = launch_pass<C>(state, d_item_off, items, pl.n, p, pl.stages.data(), dp->d_stages,
+                               dp->d_dops, table, stride, ctx().err, s);
             if (e != cudaSuccess) return cuda_fail(e, "pass kernel");
         }
     }
@@ -471,6 +500,7 @@ static tcng_status expect_impl(const tcng_state* st, const tcng_pauli* terms, si
         if (!partial) return fail(TCNG_ENOMEM, "expectation scratch");
         for (size_t i = 0; i < passes.size(); ++i) {
             cudaError_t e;
+            ProfScope ps(st->dt == TCNG_C64 ? "expect_pass_c64" : "expect_pass_c128", s);
             if (st->dt == TCNG_C64)
                 e = launch_expect_pass<float2>(static_cast<const float2*>(st->buf), st->d_off, items, n,
                                                passes[i], eps[i], partial, (int)n_terms, nblk, c.err, s);
@@ -479,6 +509,7 @@ static tcng_status expect_impl(const tcng_state* st, const tcng_pauli* terms, si
                                                 passes[i], eps[i], partial, (int)n_terms, nblk, c.err, s);
             if (e != cudaSuccess) return cuda_fail(e, "expectation pass");
         }
+        ProfScope ps("expect_finalize", s);
         cudaError_t e = launch_expect_finalize(partial, nblk, (int)n_terms, out_dev, coeffs_dev, ts->d_c,
                                                energy_dev, items, s);
         if (e != cudaSuccess) return cuda_fail(e, "expectation finalize");
@@ -573,6 +604,41 @@ tcng_status tcng_sync_status(void) {
             if (h & ERR_TIMEOUT_FLAG) return fail(TCNG_ETIMEOUT, "a device-side wait timed out");
             return fail(TCNG_EINVAL, "device reported an invalid work item");
         }
+    }
+    return TCNG_OK;
+}
+
+tcng_status tcng_profile_enable(int on) {
+    g_prof = on != 0;
+    return TCNG_OK;
+}
+
+tcng_status tcng_profile_read(char* buf, size_t len, int reset) {
+    if (!buf || !len) return fail(TCNG_EINVAL, "buffer is NULL");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::map<std::string, std::pair<long, double>> agg;
+    for (const ProfRec& r : g_prof_recs) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, r.e0, r.e1);
+        auto& a = agg[r.name];
+        a.first += 1;
+        a.second += ms;
+    }
+    std::string out;
+    char line[256];
+    for (auto& kv : agg) {
+        snprintf(line, sizeof line, "%s %ld %.6f\n", kv.first.c_str(), kv.second.first, kv.second.second);
+        out += line;
+    }
+    snprintf(buf, len, "%s", out.c_str());
+    if (reset) {
+        for (ProfRec& r : g_prof_recs) {
+            cudaEventDestroy(r.e0);
+            cudaEventDestroy(r.e1);
+        }
+        g_prof_recs.clear();
     }
     return TCNG_OK;
 }

@@ -78,6 +78,15 @@ struct DeviceCtx {
     void* scratch(const std::string& name, size_t bytes);
 };
 
+// Event-timed scope around one kernel launch (active only when profiling is on).
+struct ProfScope {
+    ProfScope(const char* name, cudaStream_t s);
+    ~ProfScope();
+    const char* name;
+    cudaStream_t s;
+    cudaEvent_t e0 = nullptr;
+};
+
 DeviceCtx& ctx();
 tcng_status fail(tcng_status s, const std::string& msg);
 tcng_status cuda_fail(cudaError_t e, const char* where);

@@ -135,27 +135,17 @@ __device__ __forceinline__ long long chunk_offset(const DevPass& p, int j) {
         if ((j >> i) & 1) off |= 1ll << p.gather[i];
     return off;
 }
-// Insert a zero bit at each register position (ascending) into g.
-__device__ __forceinline__ int insert_zero_bits(int g, const uint8_t* rbit) {
-#pragma unroll
-    for (int i = 0; i < kRegBits; ++i) {
-        const int p = rbit[i];
-        g = ((g >> p) << (p + 1)) | (g & ((1 << p) - 1));
-    }
-    return g;
-}
-
 // -------------------------------------------------------- dense register op --
-// a[16] holds the amplitudes of one group: slot s holds tile offset
+// a[2^R] holds the amplitudes of one group: slot s holds tile offset
 // base | scatter(s ^ tau) (XOR rotation by tau spreads shared-memory banks).
 // Apply a 2^K x 2^K matrix (row-major, ascending local order) on register bits
 // MASK; DAG applies the conjugate transpose.
-template <typename C, int MASK, bool DAG>
-__device__ __forceinline__ void dense_apply(C (&a)[16], const C* __restrict__ M, int tau) {
+template <typename C, int R, int MASK, bool DAG>
+__device__ __forceinline__ void dense_apply(C (&a)[1 << R], const C* __restrict__ M, int tau) {
     constexpr int K = cpopc(MASK);
     constexpr int D = 1 << K;
-    constexpr int OMASK = 15 & ~MASK;
-    constexpr int NOUT = 16 >> K;
+    constexpr int OMASK = ((1 << R) - 1) & ~MASK;
+    constexpr int NOUT = (1 << R) >> K;
     const int t = pext4(tau, MASK);
     if constexpr (K <= 2) {
         C m[D][D];
@@ -205,13 +195,21 @@ __device__ __forceinline__ void dense_apply(C (&a)[16], const C* __restrict__ M,
     }
 }
 
-template <typename C, bool DAG>
-__device__ __forceinline__ void dense_dispatch(int mask, C (&a)[16], const C* M, int tau) {
+template <typename C, int R, bool DAG, int MASK>
+__device__ __forceinline__ void dense_case(C (&a)[1 << R], const C* M, int tau) {
+    if constexpr (MASK < (1 << R)) dense_apply<C, R, MASK, DAG>(a, M, tau);
+}
+
+template <typename C, int R, bool DAG>
+__device__ __forceinline__ void dense_dispatch(int mask, C (&a)[1 << R], const C* M, int tau) {
     switch (mask) {
-#define TCNG_CASE(m) case m: dense_apply<C, m, DAG>(a, M, tau); break;
+#define TCNG_CASE(m) case m: dense_case<C, R, DAG, m>(a, M, tau); break;
         TCNG_CASE(1) TCNG_CASE(2) TCNG_CASE(3) TCNG_CASE(4) TCNG_CASE(5) TCNG_CASE(6)
         TCNG_CASE(7) TCNG_CASE(8) TCNG_CASE(9) TCNG_CASE(10) TCNG_CASE(11) TCNG_CASE(12)
-        TCNG_CASE(13) TCNG_CASE(14) TCNG_CASE(15)
+        TCNG_CASE(13) TCNG_CASE(14) TCNG_CASE(15) TCNG_CASE(16) TCNG_CASE(17) TCNG_CASE(18)
+        TCNG_CASE(19) TCNG_CASE(20) TCNG_CASE(21) TCNG_CASE(22) TCNG_CASE(23) TCNG_CASE(24)
+        TCNG_CASE(25) TCNG_CASE(26) TCNG_CASE(27) TCNG_CASE(28) TCNG_CASE(29) TCNG_CASE(30)
+        TCNG_CASE(31)
 #undef TCNG_CASE
         default: break;
     }
@@ -223,12 +221,12 @@ __device__ __forceinline__ int src_bit(uint8_t src, int L, long long gbase) {
 }
 
 // Diagonal op: multiply slot s by M[pext of its qubit bits].
-template <typename C, bool DAG>
-__device__ __forceinline__ void diag_apply(C (&a)[16], const DevOp& op, const C* __restrict__ M,
-                                           const int (&L)[16], long long gbase) {
+template <typename C, int R, bool DAG>
+__device__ __forceinline__ void diag_apply(C (&a)[1 << R], const DevOp& op, const C* __restrict__ M,
+                                           const int (&L)[1 << R], long long gbase) {
     const int k = op.k;
 #pragma unroll
-    for (int s = 0; s < 16; ++s) {
+    for (int s = 0; s < (1 << R); ++s) {
         int idx = 0;
         for (int j = 0; j < k; ++j) idx |= src_bit(op.src[j], L[s], gbase) << j;
         C d = M[idx];
@@ -237,44 +235,73 @@ __device__ __forceinline__ void diag_apply(C (&a)[16], const DevOp& op, const C*
     }
 }
 
-// Tile offsets of the 16 slots of group g in a stage with register bits rbit.
-__device__ __forceinline__ void group_offsets(int g, const uint8_t* rbit, int (&L)[16]) {
-    const int base = insert_zero_bits(g, rbit);
-    const int tau = g & 15;
-    int sr[kRegBits];
+// Insert a zero bit at each of the R register positions (ascending) into g.
+template <int R>
+__device__ __forceinline__ int insert_zero_bits(int g, const uint8_t* rbit) {
 #pragma unroll
-    for (int i = 0; i < kRegBits; ++i) sr[i] = 1 << rbit[i];
+    for (int i = 0; i < R; ++i) {
+        const int p = rbit[i];
+        g = ((g >> p) << (p + 1)) | (g & ((1 << p) - 1));
+    }
+    return g;
+}
+
+// Tile offsets of the 2^R slots of group g in a stage with register bits rbit.
+template <int R>
+__device__ __forceinline__ void group_offsets(int g, const uint8_t* rbit, int (&L)[1 << R]) {
+    const int base = insert_zero_bits<R>(g, rbit);
+    const int tau = g & ((1 << R) - 1);
+    int sr[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) sr[i] = 1 << rbit[i];
     int stau = 0;
 #pragma unroll
-    for (int i = 0; i < kRegBits; ++i) stau |= ((tau >> i) & 1) ? sr[i] : 0;
+    for (int i = 0; i < R; ++i) stau |= ((tau >> i) & 1) ? sr[i] : 0;
 #pragma unroll
-    for (int s = 0; s < 16; ++s) {
+    for (int s = 0; s < (1 << R); ++s) {
         int o = 0;
 #pragma unroll
-        for (int i = 0; i < kRegBits; ++i) o |= ((s >> i) & 1) ? sr[i] : 0;
+        for (int i = 0; i < R; ++i) o |= ((s >> i) & 1) ? sr[i] : 0;
         L[s] = base | (o ^ stau);
     }
 }
 
-// Stage executor: one group (16 amplitudes) of one tile, forward direction.
-template <typename C>
+// Stage executor: one group (2^R amplitudes) of one tile, forward direction.
+template <typename C, int R>
 __device__ __forceinline__ void run_stage_group(C* __restrict__ buf, const DevStage& st,
                                                 const DevOp* __restrict__ ops, const C* __restrict__ mats,
                                                 int g, long long gbase) {
-    int L[16];
-    group_offsets(g, st.rbit, L);
-    const int tau = g & 15;
-    C a[16];
+    int L[1 << R];
+    group_offsets<R>(g, st.rbit, L);
+    const int tau = g & ((1 << R) - 1);
+    C a[1 << R];
 #pragma unroll
-    for (int s = 0; s < 16; ++s) a[s] = buf[L[s]];
+    for (int s = 0; s < (1 << R); ++s) a[s] = buf[L[s]];
     for (uint32_t i = 0; i < st.op_count; ++i) {
         const DevOp op = ops[st.op_begin + i];
         const C* M = mats + op.mat;
-        if (op.kind == K_DENSE) dense_dispatch<C, false>(op.mask, a, M, tau);
-        else diag_apply<C, false>(a, op, M, L, gbase);
+        if (op.kind == K_DENSE) dense_dispatch<C, R, false>(op.mask, a, M, tau);
+        else diag_apply<C, R, false>(a, op, M, L, gbase);
     }
 #pragma unroll
-    for (int s = 0; s < 16; ++s) buf[L[s]] = a[s];
+    for (int s = 0; s < (1 << R); ++s) buf[L[s]] = a[s];
+}
+
+// One stage over a whole tile by the CTA (no trailing barrier).  RMAX = 4
+// compiles only the 16-amplitude path; RMAX = 5 adds the 32-amplitude one.
+template <typename C, int RMAX>
+__device__ __forceinline__ void run_stage(C* __restrict__ buf, const DevStage& st,
+                                          const DevOp* __restrict__ ops, const C* __restrict__ mats,
+                                          int tile_bits, long long gbase) {
+    if (RMAX == kMaxRegBits && st.nreg == kMaxRegBits) {
+        const int ngroups = 1 << (tile_bits - kMaxRegBits);
+        for (int g = threadIdx.x; g < ngroups; g += blockDim.x)
+            run_stage_group<C, RMAX>(buf, st, ops, mats, g, gbase);
+    } else {
+        const int ngroups = 1 << (tile_bits - kRegBits);
+        for (int g = threadIdx.x; g < ngroups; g += blockDim.x)
+            run_stage_group<C, kRegBits>(buf, st, ops, mats, g, gbase);
+    }
 }
 
 }  // namespace tcng

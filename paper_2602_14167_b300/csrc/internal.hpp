@@ -24,7 +24,8 @@
 
 namespace tcng {
 
-constexpr int kRegBits = 4;          // R: amplitudes per thread per stage = 16
+constexpr int kRegBits = 4;          // R of an ordinary stage: 16 amplitudes per thread
+constexpr int kMaxRegBits = 5;       // R of a stage holding a 5-qubit block: 32 amplitudes
 constexpr int kMaxTileBits = 14;
 constexpr int kMaxPassMat = 2048;    // complex entries of block matrices per pass (smem)
 constexpr int kMaxGather = 12;
@@ -60,8 +61,10 @@ struct DevOp {               // 16 bytes
 };
 static_assert(sizeof(DevOp) == 16, "DevOp layout");
 
-struct DevStage {            // 16 bytes
-    uint8_t rbit[kRegBits];  // tile bit of register bit i (ascending)
+struct DevStage {            // 20 bytes
+    uint8_t rbit[kMaxRegBits];  // tile bit of register bit i (ascending)
+    uint8_t nreg;            // R: 4, or 5 for a stage holding a 5-qubit block
+    uint8_t pad[2];
     uint32_t op_begin;
     uint32_t op_count;
     uint32_t n_grad;         // adjoint: parameterised ops in this stage

@@ -294,7 +294,7 @@ __device__ __forceinline__ void issue_tile_store(C* state, const long long* item
     bulk_commit();
 }
 
-template <typename C>
+template <typename C, int RMAX>
 __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
                                                     const long long* __restrict__ item_off,
                                                     const __grid_constant__ DevPass p,
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
                                                     const C* __restrict__ table,
                                                     long long table_stride, TileCtx tc,
                                                     unsigned* __restrict__ err) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile_elems = 1 << p.m;
     C* bufs = reinterpret_cast<C*>(smem_raw);
     C* mats = bufs + (long long)tc.nbuf * tile_elems;
@@ -325,7 +325,6 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
                 issue_tile_load(state, item_off, p, tc, t, bufs + (long long)i * tile_elems, &bars[i], lane);
         }
     long long cur_item = -1;
-    const int ngroups = tile_elems >> kRegBits;
     int it = 0;
     for (long long t = first; t < tc.total_tiles; t += stride, ++it) {
         const int b = it % tc.nbuf;
@@ -343,8 +342,7 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
         const long long gbase = tile_global_base(p, t % tc.tiles_per_item);
         for (int s = 0; s < p.stage_count; ++s) {
             const DevStage st = stages[p.stage_begin + s];
-            for (int g = tid; g < ngroups; g += blockDim.x)
-                run_stage_group<C>(buf, st, ops, mats, g, gbase);
+            run_stage<C, RMAX>(buf, st, ops, mats, p.m, gbase);
             __syncthreads();
         }
         fence_proxy_async_smem();
@@ -374,7 +372,7 @@ __global__ void __launch_bounds__(512) expect_pass_kernel(const C* __restrict__ 
                                                           TileCtx tc, double* __restrict__ partial,
                                                           int n_out, unsigned* __restrict__ err) {
     using R = typename Real<C>::T;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile_elems = 1 << p.m;
     C* bufs = reinterpret_cast<C*>(smem_raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(bufs + (long long)tc.nbuf * tile_elems);
@@ -610,29 +608,48 @@ static size_t pass_smem_bytes(const DevPass& p, int nbuf) {
            8 * (size_t)nbuf;
 }
 
-constexpr size_t kSmemLimit = 227 * 1024;
+// Largest dynamic shared memory a kernel may request: the device opt-in limit
+// minus the kernel's static shared memory.  Sets the attribute once.
+template <typename K>
+static size_t dyn_smem_limit(K kernel, bool* done, size_t* cached) {
+    if (!*done) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, kernel);
+        size_t lim = optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            lim = 48 * 1024 - fa.sharedSizeBytes;
+        }
+        *cached = lim;
+        *done = true;
+    }
+    return *cached;
+}
 
 template <typename C>
 cudaError_t launch_pass(C* state, const long long* item_off, int items, int n, const DevPass& p,
-                        const DevStage* stages, const DevOp* ops, const C* table,
-                        long long table_stride, unsigned* err, cudaStream_t s) {
+                        const DevStage* host_stages, const DevStage* stages, const DevOp* ops,
+                        const C* table, long long table_stride, unsigned* err, cudaStream_t s) {
     const int nbuf = 3;
     const size_t smem = pass_smem_bytes<C>(p, nbuf);
-    if (smem > kSmemLimit) return cudaErrorInvalidConfiguration;
+    bool wide = false;
+    for (int i = 0; i < p.stage_count; ++i) wide = wide || host_stages[p.stage_begin + i].nreg > kRegBits;
+    auto kern = wide ? pass_kernel<C, kMaxRegBits> : pass_kernel<C, kRegBits>;
+    static bool done[2] = {false, false};
+    static size_t lim[2] = {0, 0};
+    if (smem > dyn_smem_limit(kern, &done[wide], &lim[wide])) return cudaErrorInvalidConfiguration;
     TileCtx tc = make_ctx(p, n, items, sizeof(C), nbuf);
     const int threads = std::max(32, (1 << p.m) >> kRegBits);
-    static bool attr_set[2] = {false, false};
-    const int di = sizeof(C) == 8 ? 0 : 1;
-    if (!attr_set[di]) {
-        cudaFuncSetAttribute(pass_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
-        attr_set[di] = true;
-    }
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_kernel<C>, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (per_sm < 1) per_sm = 1;
     long long grid = std::min<long long>(tc.total_tiles, (long long)num_sms() * per_sm);
-    pass_kernel<C><<<(unsigned)grid, threads, smem, s>>>(state, item_off, p, stages, ops, table,
-                                                        table_stride, tc, err);
+    kern<<<(unsigned)grid, threads, smem, s>>>(state, item_off, p, stages, ops, table, table_stride,
+                                               tc, err);
     count_launch();
     return cudaGetLastError();
 }
@@ -643,15 +660,10 @@ cudaError_t launch_expect_pass(const C* state, const long long* item_off, int it
                                int nblk, unsigned* err, cudaStream_t s) {
     const int nbuf = 2;
     const size_t smem = (size_t)nbuf * (sizeof(C) << p.m) + 8 * nbuf;
-    if (smem > kSmemLimit) return cudaErrorInvalidConfiguration;
+    static bool done = false;
+    static size_t lim = 0;
+    if (smem > dyn_smem_limit(expect_pass_kernel<C>, &done, &lim)) return cudaErrorInvalidConfiguration;
     TileCtx tc = make_ctx(p, n, items, sizeof(C), nbuf);
-    static bool attr_set[2] = {false, false};
-    const int di = sizeof(C) == 8 ? 0 : 1;
-    if (!attr_set[di]) {
-        cudaFuncSetAttribute(expect_pass_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemLimit);
-        attr_set[di] = true;
-    }
     const int threads = std::min(512, std::max(32, 1 << p.m));
     dim3 grid((unsigned)nblk, (unsigned)items);
     expect_pass_kernel<C><<<grid, threads, smem, s>>>(state, item_off, p, ep, tc, partial, n_out, err);
@@ -687,8 +699,8 @@ cudaError_t launch_ham_apply(const C* psi, const long long* off_in, C* out, cons
     template cudaError_t launch_gate<C>(C*, const long long*, int, int, const Block&, const C*,       \
                                         long long, cudaStream_t);                                     \
     template cudaError_t launch_pass<C>(C*, const long long*, int, int, const DevPass&,               \
-                                        const DevStage*, const DevOp*, const C*, long long,           \
-                                        unsigned*, cudaStream_t);                                     \
+                                        const DevStage*, const DevStage*, const DevOp*, const C*,     \
+                                        long long, unsigned*, cudaStream_t);                          \
     template cudaError_t launch_expect_pass<C>(const C*, const long long*, int, int, const DevPass&,  \
                                                const ExpPass&, double*, int, int, unsigned*,          \
                                                cudaStream_t);                                         \

@@ -39,8 +39,8 @@ cudaError_t launch_gate(C* state, const long long* item_off, int items, int n, c
                         const C* table, long long table_stride, cudaStream_t s);
 template <typename C>
 cudaError_t launch_pass(C* state, const long long* item_off, int items, int n, const DevPass& p,
-                        const DevStage* stages, const DevOp* ops, const C* table,
-                        long long table_stride, unsigned* err, cudaStream_t s);
+                        const DevStage* host_stages, const DevStage* stages, const DevOp* ops,
+                        const C* table, long long table_stride, unsigned* err, cudaStream_t s);
 template <typename C>
 cudaError_t launch_expect_pass(const C* state, const long long* item_off, int items, int n,
                                const DevPass& p, const ExpPass& ep, double* partial, int n_out,

@@ -334,13 +334,15 @@ void build_plan(Plan& plan) {
             size_t left = pass_list.size();
             dp.stage_begin = (int)plan.stages.size();
             uint32_t Rset = 0;  // tile-bit mask
+            int Rcap = kRegBits;
             std::vector<int> cur;
             auto close_stage = [&]() {
                 if (cur.empty()) return;
                 DevStage st{};
                 // pad register set with the highest free tile bits
-                for (int tb = dp.m - 1; tb >= 0 && __builtin_popcount(Rset) < kRegBits; --tb)
+                for (int tb = dp.m - 1; tb >= 0 && __builtin_popcount(Rset) < Rcap; --tb)
                     Rset |= 1u << tb;
+                st.nreg = (uint8_t)Rcap;
                 int ri = 0;
                 int reg_of_tb[kMaxTileBits + 2];
                 for (int tb = 0; tb < dp.m; ++tb) {
@@ -393,6 +395,7 @@ void build_plan(Plan& plan) {
                 plan.stages.push_back(st);
                 cur.clear();
                 Rset = 0;
+                Rcap = kRegBits;
             };
             std::vector<std::vector<int>> pdeps(plan.blocks.size());
             for (int b : pass_list)
@@ -415,7 +418,9 @@ void build_plan(Plan& plan) {
                         qm &= qm - 1;
                         tbm |= 1u << tb_of_q[q];
                     }
-                    if (__builtin_popcount(Rset | tbm) <= kRegBits) {
+                    // a 5-qubit block opens a 32-amplitude stage of its own bits
+                    if (cur.empty() && __builtin_popcount(tbm) > kRegBits) Rcap = kMaxRegBits;
+                    if (__builtin_popcount(Rset | tbm) <= Rcap) {
                         pick = b;
                         Rset |= tbm;
                         break;

@@ -73,6 +73,8 @@ def lib():
             "tcng_get_option": [i32, C.POINTER(i32)],
             "tcng_autotune": [i32, i32, i32, C.c_char_p],
             "tcng_sync_status": [],
+            "tcng_profile_enable": [i32],
+            "tcng_profile_read": [C.c_char_p, sz, i32],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -269,6 +271,21 @@ def tcng_sync_status():
     _check(lib().tcng_sync_status())
 
 
+def tcng_profile_enable(on=True):
+    _check(lib().tcng_profile_enable(int(bool(on))))
+
+
+def tcng_profile_read(reset=True):
+    """{kernel: (launches, total_ms)} of the event-timed launches since the last reset."""
+    buf = C.create_string_buffer(1 << 16)
+    _check(lib().tcng_profile_read(buf, len(buf), int(reset)))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out
+
+
 def tcng_describe_plan(n, gates, pool, P, adjoint=False):
     g = _gates(gates)
     p, n_mat = _pool(pool)
@@ -294,5 +311,6 @@ EXPORTED = [
     "tcng_energy_grad", "tcng_energy_grad_ragged", "tcng_apply_shared_unitary", "tcng_adam_step",
     "tcng_adam_step_f32", "tcng_mlp_forward", "tcng_mlp_backward", "tcng_set_option",
     "tcng_get_option", "tcng_autotune", "tcng_sync_status", "tcng_describe_plan",
+    "tcng_profile_enable", "tcng_profile_read",
     "tcng_launch_count", "tcng_last_error", "tcng_version",
 ]
