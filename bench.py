@@ -39,11 +39,11 @@ REF_N = 28          # oracle sample size (complex128, 4 GiB)
 REF_GATES = 4       # gates per reference step
 
 
-def workload():
-    c, theta = gen.su4_brickwork(N_QUBITS, DEPTH, "RZ", seed=0)
+def workload(n=N_QUBITS, depth=DEPTH):
+    c, theta = gen.su4_brickwork(n, depth, "RZ", seed=0)
     gates, pool = c.to_ir()
-    strings = gen.random_pauli_strings(N_QUBITS, N_STRINGS, 4, seed=1)
-    tfim = gen.tfim_terms(N_QUBITS, 1.0, 1.0)
+    strings = gen.random_pauli_strings(n, N_STRINGS, 4, seed=1)
+    tfim = gen.tfim_terms(n, 1.0, 1.0)
     return c, gates, pool, theta, strings, tfim
 
 
@@ -169,9 +169,10 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    c, gates, pool, theta, strings, tfim = workload()
-    st = StateBatch(N_QUBITS, dtype="c64", device=dev)
-    S = 8 * (1 << N_QUBITS)
+    NQ, DP = args.qubits, args.depth
+    c, gates, pool, theta, strings, tfim = workload(NQ, DP)
+    st = StateBatch(NQ, dtype="c64", device=dev)
+    S = 8 * (1 << NQ)
     params = torch.tensor(theta, dtype=torch.float64, device=dev).reshape(1, -1)
     vals = torch.empty((1, N_STRINGS), dtype=torch.float64, device=dev)
     energy = torch.empty(1, dtype=torch.float64, device=dev)
@@ -255,7 +256,7 @@ def run_gpu(args):
                       "qubits": N_QUBITS, "depth": DEPTH, "state_GiB": S / 2**30,
                       "tile_passes_per_step": n_pass, "expect_passes_per_step": n_exp,
                       "step_bytes_GB": step_bytes / 1e9,
-                      "ms_per_layer": ms_step / DEPTH,
+                      "ms_per_layer": ms_step / DP,
                       "l2": "inputs larger than L2 (32 GiB state), no flush",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -292,6 +293,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--qubits", type=int, default=N_QUBITS, help="smaller cases for profiling only")
+    ap.add_argument("--depth", type=int, default=DEPTH, help="smaller cases for profiling only")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
