@@ -5,15 +5,6 @@ using namespace tcng;
 
 extern "C" {
 
-tcng_status tcng_energy_grad(tcng_state*, const tcng_gate*, size_t, const double*, size_t,
-                             const void*, int, const tcng_pauli*, size_t, const double*, double*,
-                             double*, void*) {
-    return fail(TCNG_EUNSUPPORTED, "tcng_energy_grad is not built yet");
-}
-tcng_status tcng_energy_grad_ragged(const tcng_problem*, int, const int*, int, const double*,
-                                    const double*, double*, double*, void*) {
-    return fail(TCNG_EUNSUPPORTED, "tcng_energy_grad_ragged is not built yet");
-}
 tcng_status tcng_apply_shared_unitary(tcng_state*, const int*, int, const double*, void*) {
     return fail(TCNG_EUNSUPPORTED, "tcng_apply_shared_unitary is not built yet");
 }

@@ -29,6 +29,8 @@ constexpr int kMaxRegBits = 5;       // R of a stage holding a 5-qubit block: 32
 constexpr int kMaxTileBits = 14;
 constexpr int kMaxPassMat = 2048;    // complex entries of block matrices per pass (smem)
 constexpr int kMaxGather = 12;
+constexpr int kMaxStageGrads = 32;   // adjoint: parameterised ops per stage
+constexpr int kMaxGradSlots = 2048;  // adjoint: parameterised ops per circuit
 
 // ---- device program ---------------------------------------------------------
 enum OpKind : uint8_t {

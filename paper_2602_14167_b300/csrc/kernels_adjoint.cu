@@ -1,0 +1,427 @@
+// Batched energy + adjoint gradient: one persistent launch over B items.
+//
+// Paper: Sec. I.B "Paradigms" -- value_and_grad of the TFIM energy, vmapped over
+// a batch of parameter sets ("thousands of independent circuit instances").
+// The paper differentiates by reverse-mode AD through the tensor network; here
+// the gradient comes from an adjoint sweep that keeps two states:
+//   forward   psi = U_K ... U_1 |0>,
+//   co-state  lambda = H psi,  E = Re <psi|lambda>,
+//   reverse   for k = K..1:  g_k += Im <lambda|G_k|psi>  (U_k = exp(-i theta G_k / 2)),
+//             psi <- U_k^dag psi,  lambda <- U_k^dag lambda,
+// so memory is O(1) states whatever the number of parameters.
+//
+// Each CTA pops items from a global counter (largest n first).  States of up to
+// 2^13 (complex64) / 2^12 (complex128) amplitudes live in shared memory for the
+// whole item ("resident"); larger ones stream through per-CTA global scratch in
+// 2^12 / 2^11-amplitude tiles with bulk asynchronous copies.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "adjoint.hpp"
+#include "device.cuh"
+
+namespace tcng {
+
+// ------------------------------------------------------------ reductions --
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename R>
+__device__ __forceinline__ R im_conj_mul(R lx, R ly, R px, R py) {  // Im(conj(l) p)
+    return lx * py - ly * px;
+}
+
+// Im<lambda|X|psi> or Im<lambda|Y|psi> of one group for a gate on register bit BIT.
+template <typename C, int R, int BIT>
+__device__ __forceinline__ typename Real<C>::T grad_xy(bool is_y, const C (&p)[1 << R],
+                                                      const C (&l)[1 << R], int flip) {
+    using T = typename Real<C>::T;
+    T acc = 0;
+    if constexpr (BIT < R) {
+#pragma unroll
+        for (int s = 0; s < (1 << R); ++s) {
+            if ((s >> BIT) & 1) continue;
+            const int s1 = s | (1 << BIT);
+            if (!is_y) {
+                acc += im_conj_mul(l[s].x, l[s].y, p[s1].x, p[s1].y) +
+                       im_conj_mul(l[s1].x, l[s1].y, p[s].x, p[s].y);
+            } else {
+                // slot s holds logical 0 unless flipped: <l|Y|p> = i [conj(l1) p0 - conj(l0) p1],
+                // Im(i z) = Re(z); swapping the logical roles negates the sum
+                acc += (l[s1].x * p[s].x + l[s1].y * p[s].y) - (l[s].x * p[s1].x + l[s].y * p[s1].y);
+            }
+        }
+        if (is_y && flip) acc = -acc;
+    }
+    return acc;
+}
+
+// Gradient contribution Im<lambda|G|psi> of one group, for a lone parameterised op.
+template <typename C, int R>
+__device__ __forceinline__ typename Real<C>::T grad_part(const DevOp& op, const C (&p)[1 << R],
+                                                        const C (&l)[1 << R], int tau,
+                                                        const int (&L)[1 << R], long long gbase) {
+    using T = typename Real<C>::T;
+    T acc = 0;
+    if (op.grad == G_X || op.grad == G_Y) {
+        const int bit = __ffs(op.mask) - 1;          // register bit of the gate
+        const int flip = (tau >> bit) & 1;            // slot with bit 0 holds logical `flip`
+        const bool is_y = op.grad == G_Y;
+        switch (bit) {
+        case 0: acc = grad_xy<C, R, 0>(is_y, p, l, flip); break;
+        case 1: acc = grad_xy<C, R, 1>(is_y, p, l, flip); break;
+        case 2: acc = grad_xy<C, R, 2>(is_y, p, l, flip); break;
+        case 3: acc = grad_xy<C, R, 3>(is_y, p, l, flip); break;
+        default: acc = grad_xy<C, R, 4>(is_y, p, l, flip); break;
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < (1 << R); ++s) {
+            const int b0 = src_bit(op.src[0], L[s], gbase);
+            T w;
+            if (op.grad == G_Z) {
+                w = b0 ? T(-1) : T(1);
+            } else {
+                const int b1 = src_bit(op.src[1], L[s], gbase);
+                w = (op.grad == G_ZZ) ? ((b0 ^ b1) ? T(-1) : T(1)) : T(b0 & b1);
+            }
+            acc += w * im_conj_mul(l[s].x, l[s].y, p[s].x, p[s].y);
+        }
+    }
+    return acc;
+}
+
+// Reverse stage over one tile: ops in reverse order, gradient before uncompute.
+// red[w][j] accumulates warp w's share of the stage's j-th gradient op.
+template <typename C, int R>
+__device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, const DevStage& st,
+                                  const DevOp* __restrict__ ops, const C* __restrict__ mats,
+                                  int tile_bits, long long gbase, float* red) {
+    using T = typename Real<C>::T;
+    const int ngroups = 1 << (tile_bits - R);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int g0 = 0; g0 < ngroups; g0 += blockDim.x) {
+        const int g = g0 + threadIdx.x;
+        const bool active = g < ngroups;
+        int L[1 << R];
+        C p[1 << R], l[1 << R];
+        const int tau = g & ((1 << R) - 1);
+        if (active) {
+            group_offsets<R>(g, st.rbit, L);
+#pragma unroll
+            for (int s = 0; s < (1 << R); ++s) {
+                p[s] = pbuf[L[s]];
+                l[s] = lbuf[L[s]];
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < (1 << R); ++s) {
+                L[s] = 0;
+                p[s] = cmk<C>(0, 0);
+                l[s] = cmk<C>(0, 0);
+            }
+        }
+        int j = 0;
+        for (int i = (int)st.op_count - 1; i >= 0; --i) {
+            const DevOp op = ops[st.op_begin + i];
+            const C* M = mats + op.mat;
+            if (op.grad != G_NONE) {
+                T v = active ? grad_part<C, R>(op, p, l, tau, L, gbase) : T(0);
+                const float w = warp_sum((float)v);
+                if (lane == 0) red[warp * kMaxStageGrads + j] += w;
+                ++j;
+            }
+            if (active) {
+                if (op.kind == K_DENSE) {
+                    dense_dispatch<C, R, true>(op.mask, p, M, tau);
+                    dense_dispatch<C, R, true>(op.mask, l, M, tau);
+                } else {
+                    diag_apply<C, R, true>(p, op, M, L, gbase);
+                    diag_apply<C, R, true>(l, op, M, L, gbase);
+                }
+            }
+        }
+        if (active) {
+#pragma unroll
+            for (int s = 0; s < (1 << R); ++s) {
+                pbuf[L[s]] = p[s];
+                lbuf[L[s]] = l[s];
+            }
+        }
+    }
+}
+
+// Forward stage over one tile (all threads; inactive ones idle).
+template <typename C, int RMAX>
+__device__ __forceinline__ void run_stage_fwd(C* __restrict__ buf, const DevStage& st,
+                                              const DevOp* __restrict__ ops, const C* __restrict__ mats,
+                                              int tile_bits, long long gbase) {
+    run_stage<C, RMAX>(buf, st, ops, mats, tile_bits, gbase);
+}
+
+// ---------------------------------------------------------- tile movement --
+// Synchronous copy of one tile (chunks of 2^chunk amplitudes) between global
+// and shared memory for up to two states; warp 0 issues the copies.
+template <typename C>
+__device__ bool tile_load(const DevPass& p, long long tile, C* const* gptr, C* const* sbuf, int nst,
+                          uint64_t* bar, uint32_t* phase, unsigned* err) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        const long long base = tile_global_base(p, tile);
+        const uint32_t chunk_bytes = (uint32_t)(sizeof(C) << p.chunk);
+        const int nchunks = 1 << p.ngather;
+        if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(nst * (sizeof(C) << p.m)));
+        __syncwarp();
+        for (int s = 0; s < nst; ++s)
+            for (int j = lane; j < nchunks; j += 32)
+                bulk_g2s(sbuf[s] + ((long long)j << p.chunk), gptr[s] + base + chunk_offset(p, j),
+                         chunk_bytes, bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, *phase, err);
+    *phase ^= 1u;
+    return ok;
+}
+
+__device__ __forceinline__ void fence_proxy_async_all() {
+    asm volatile("fence.proxy.async;" ::: "memory");
+}
+
+template <typename C>
+__device__ void tile_store(const DevPass& p, long long tile, C* const* gptr, C* const* sbuf, int nst) {
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x & 31;
+        const long long base = tile_global_base(p, tile);
+        const uint32_t chunk_bytes = (uint32_t)(sizeof(C) << p.chunk);
+        const int nchunks = 1 << p.ngather;
+        for (int s = 0; s < nst; ++s)
+            for (int j = lane; j < nchunks; j += 32)
+                bulk_s2g(gptr[s] + base + chunk_offset(p, j), sbuf[s] + ((long long)j << p.chunk),
+                         chunk_bytes);
+        bulk_commit();
+        bulk_wait<0>();
+        fence_proxy_async_all();
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ kernel --
+template <typename C, int RMAX>
+__global__ void __launch_bounds__(256, 1) adjoint_kernel(AdjArgs a) {
+    using T = typename Real<C>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x;
+    const int nthreads = blockDim.x;
+    const int nwarps = nthreads >> 5;
+    // layout: [psi tile | lam tile] (2 * 2^mres) | mats window | gacc | red | bar
+    const int res_elems = 1 << a.res_bits;
+    C* sp = reinterpret_cast<C*>(smem_raw);
+    C* sl = sp + res_elems;
+    C* mats = sl + res_elems;
+    double* gacc = reinterpret_cast<double*>(mats + kMaxPassMat);
+    float* red = reinterpret_cast<float*>(gacc + kMaxGradSlots);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(red + 32 * kMaxStageGrads);
+    __shared__ int s_item;
+    __shared__ double s_red[32];
+    __shared__ int s_abort;
+    uint32_t phase = 0;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    C* scratch_p = reinterpret_cast<C*>(a.scratch) + (long long)blockIdx.x * 2 * a.scratch_elems;
+    C* scratch_l = scratch_p + a.scratch_elems;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int idx = s_item;
+        if (idx >= a.batch || s_abort) break;
+        const ItemDesc it = a.items[a.order[idx]];
+        const StructDesc S = a.structs[it.s];
+        const C* table = reinterpret_cast<const C*>(a.tables) + it.table_off;
+        const double* coeff = a.coeffs ? a.coeffs + it.coeff_off : S.tcoef;
+        const bool resident = S.resident != 0;
+        const int n = S.n_eff;
+        const long long N = 1ll << n;
+        C* gp = resident ? nullptr : scratch_p;
+        C* gl = resident ? nullptr : scratch_l;
+        // ---------------- forward: psi = U |0> ----------------
+        if (resident) {
+            for (long long x = tid; x < N; x += nthreads) sp[x] = cmk<C>(x == 0 ? 1 : 0, 0);
+        } else {
+            for (long long x = tid; x < N; x += nthreads) gp[x] = cmk<C>(x == 0 ? 1 : 0, 0);
+        }
+        for (int g = tid; g < S.n_grad; g += nthreads) gacc[g] = 0.0;
+        fence_proxy_async_all();   // generic writes of psi before bulk copies read it
+        __syncthreads();
+        for (int pi = 0; pi < S.n_passes && !s_abort; ++pi) {
+            const DevPass P = S.passes[pi];
+            for (int i = tid; i < P.mat_count; i += nthreads) mats[i] = table[P.mat_begin + i];
+            __syncthreads();
+            const long long ntiles = resident ? 1 : (1ll << (n - P.m));
+            for (long long t = 0; t < ntiles; ++t) {
+                if (!resident) {
+                    C* gptr[1] = {gp};
+                    C* sb[1] = {sp};
+                    if (!tile_load<C>(P, t, gptr, sb, 1, bar, &phase, a.err)) s_abort = 1;
+                    __syncthreads();
+                    if (s_abort) break;
+                }
+                const long long gbase = resident ? 0 : tile_global_base(P, t);
+                for (int si = 0; si < P.stage_count; ++si) {
+                    const DevStage st = S.stages[P.stage_begin + si];
+                    run_stage_fwd<C, RMAX>(sp, st, S.dops, mats, P.m, gbase);
+                    __syncthreads();
+                }
+                if (!resident) {
+                    C* gptr[1] = {gp};
+                    C* sb[1] = {sp};
+                    tile_store<C>(P, t, gptr, sb, 1);
+                }
+            }
+            __syncthreads();
+        }
+        if (s_abort) break;
+        const C* psi = resident ? sp : gp;
+        C* lam = resident ? sl : gl;
+        // optional copy of the forward state to the caller's state buffer
+        if (it.psi_out_off >= 0) {
+            C* out = reinterpret_cast<C*>(a.psi_out) + it.psi_out_off;
+            const long long Nn = 1ll << S.n;
+            for (long long x = tid; x < Nn; x += nthreads) out[x] = psi[x];
+        }
+        // ---------------- lambda = H psi, E = Re <psi|lambda> ----------------
+        double e_part = 0.0;
+        for (long long x = tid; x < N; x += nthreads) {
+            T ar = 0, ai = 0;
+            for (int t = 0; t < S.n_terms; ++t) {
+                const HTerm h = S.terms[t];
+                const long long y = x ^ (long long)h.xm;
+                const C v = psi[y];
+                const T c = (T)coeff[t];
+                const int sg = __popcll((unsigned long long)y & h.zm) & 1;
+                T vr = v.x, vi = v.y, tr;
+                switch (h.ny & 3) {
+                case 1: tr = -vi; vi = vr; vr = tr; break;
+                case 2: vr = -vr; vi = -vi; break;
+                case 3: tr = vi; vi = -vr; vr = tr; break;
+                default: break;
+                }
+                if (sg) { vr = -vr; vi = -vi; }
+                ar += c * vr;
+                ai += c * vi;
+            }
+            lam[x] = cmk<C>(ar, ai);
+            const C p = psi[x];
+            e_part += (double)(p.x * ar + p.y * ai);
+        }
+        fence_proxy_async_all();   // generic writes of lambda before bulk copies read it
+        {
+            double v = warp_sum(e_part);
+            if ((tid & 31) == 0) s_red[tid >> 5] = v;
+            __syncthreads();
+            if (tid == 0) {
+                double e = 0;
+                for (int w = 0; w < nwarps; ++w) e += s_red[w];
+                a.energy[a.order[idx]] = e;
+            }
+            __syncthreads();
+        }
+        // ---------------- reverse sweep ----------------
+        if (a.want_grad) {
+            for (int pi = S.n_passes - 1; pi >= 0 && !s_abort; --pi) {
+                const DevPass P = S.passes[pi];
+                for (int i = tid; i < P.mat_count; i += nthreads) mats[i] = table[P.mat_begin + i];
+                __syncthreads();
+                const long long ntiles = resident ? 1 : (1ll << (n - P.m));
+                C* tp = sp;
+                C* tl = resident ? sl : sp + (1 << P.m);
+                for (long long t = 0; t < ntiles; ++t) {
+                    if (!resident) {
+                        C* gptr[2] = {gp, gl};
+                        C* sb[2] = {tp, tl};
+                        if (!tile_load<C>(P, t, gptr, sb, 2, bar, &phase, a.err)) s_abort = 1;
+                        __syncthreads();
+                        if (s_abort) break;
+                    }
+                    const long long gbase = resident ? 0 : tile_global_base(P, t);
+                    for (int si = P.stage_count - 1; si >= 0; --si) {
+                        const DevStage st = S.stages[P.stage_begin + si];
+                        for (int i = tid; i < nwarps * kMaxStageGrads; i += nthreads) red[i] = 0.f;
+                        __syncthreads();
+                        if (RMAX == kMaxRegBits && st.nreg == kMaxRegBits)
+                            run_stage_adjoint<C, RMAX>(tp, tl, st, S.dops, mats, P.m, gbase, red);
+                        else
+                            run_stage_adjoint<C, kRegBits>(tp, tl, st, S.dops, mats, P.m, gbase, red);
+                        __syncthreads();
+                        // fold this stage's gradient partials (fixed order) into gacc
+                        if (tid < (int)st.n_grad) {
+                            int j = 0, slot = -1;
+                            for (int i = (int)st.op_count - 1; i >= 0; --i) {
+                                const DevOp op = S.dops[st.op_begin + i];
+                                if (op.grad != G_NONE) {
+                                    if (j == tid) { slot = op.slot; break; }
+                                    ++j;
+                                }
+                            }
+                            double s = 0;
+                            for (int w = 0; w < nwarps; ++w) s += red[w * kMaxStageGrads + tid];
+                            gacc[slot] += s;
+                        }
+                        __syncthreads();
+                    }
+                    if (!resident) {
+                        C* gptr[2] = {gp, gl};
+                        C* sb[2] = {tp, tl};
+                        tile_store<C>(P, t, gptr, sb, 2);
+                    }
+                }
+                __syncthreads();
+            }
+            if (s_abort) break;
+            // ---------------- gradient output ----------------
+            double* grad = a.grad + it.grad_off;
+            for (int q = tid; q < S.P; q += nthreads) grad[q] = 0.0;
+            __syncthreads();
+            if (tid == 0)
+                for (int g = 0; g < S.n_grad; ++g) grad[S.gparam[g]] += S.gscale[g] * gacc[g];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename C>
+size_t adjoint_smem_bytes(int res_bits) {
+    return 2 * (sizeof(C) << res_bits) + sizeof(C) * kMaxPassMat + sizeof(double) * kMaxGradSlots +
+           sizeof(float) * 32 * kMaxStageGrads + 16;
+}
+
+template <typename C>
+cudaError_t launch_adjoint(const AdjArgs& a, bool wide, int grid, cudaStream_t s) {
+    const size_t smem = adjoint_smem_bytes<C>(a.res_bits);
+    auto kern = wide ? adjoint_kernel<C, kMaxRegBits> : adjoint_kernel<C, kRegBits>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 256, smem, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_adjoint<float2>(const AdjArgs&, bool, int, cudaStream_t);
+template cudaError_t launch_adjoint<double2>(const AdjArgs&, bool, int, cudaStream_t);
+template size_t adjoint_smem_bytes<float2>(int);
+template size_t adjoint_smem_bytes<double2>(int);
+
+}  // namespace tcng

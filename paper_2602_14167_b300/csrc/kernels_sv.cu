@@ -67,12 +67,13 @@ __global__ void build_matrices_kernel(const BuildBlock* __restrict__ blocks,
                                       const double2* __restrict__ pool,
                                       const double* __restrict__ params, int P,
                                       C* __restrict__ table, long long table_stride,
-                                      int item_base) {
+                                      int item_base, const long long* __restrict__ prm_off,
+                                      const long long* __restrict__ tab_off) {
     const int bi = blockIdx.x;
     const int item = blockIdx.y + item_base;
     const BuildBlock blk = blocks[bi];
     const int D = 1 << blk.k;
-    const double* th = params ? params + (long long)item * P : nullptr;
+    const double* th = params ? params + (prm_off ? prm_off[item] : (long long)item * P) : nullptr;
     __shared__ double2 opm[1024];
     double2 col[32];
     const int c = threadIdx.x;
@@ -113,7 +114,7 @@ __global__ void build_matrices_kernel(const BuildBlock* __restrict__ blocks,
         }
     }
     if (c < D) {
-        C* out = table + (long long)item * table_stride + blk.out_off;
+        C* out = table + (tab_off ? tab_off[item] : (long long)item * table_stride) + blk.out_off;
         if (blk.diag) {
             out[c] = cmk<C>(col[c].x, col[c].y);
         } else {
@@ -532,7 +533,22 @@ cudaError_t launch_build_matrices(const BuildBlock* blocks, int n_blocks, const 
     for (int i0 = 0; i0 < items; i0 += 65535) {
         dim3 grid(n_blocks, std::min(65535, items - i0));
         build_matrices_kernel<C><<<grid, 32, 0, s>>>(blocks, bops, pool, params, P, table,
-                                                      table_stride, i0);
+                                                      table_stride, i0, nullptr, nullptr);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+template <typename C>
+cudaError_t launch_build_matrices_indexed(const BuildBlock* blocks, int n_blocks, const BuildOp* bops,
+                                          const double2* pool, const double* params, C* table,
+                                          const long long* prm_off, const long long* tab_off,
+                                          int items, cudaStream_t s) {
+    if (n_blocks == 0 || items == 0) return cudaSuccess;
+    for (int i0 = 0; i0 < items; i0 += 65535) {
+        dim3 grid(n_blocks, std::min(65535, items - i0));
+        build_matrices_kernel<C><<<grid, 32, 0, s>>>(blocks, bops, pool, params, 0, table, 0, i0,
+                                                      prm_off, tab_off);
         count_launch();
     }
     return cudaGetLastError();
@@ -696,6 +712,10 @@ cudaError_t launch_ham_apply(const C* psi, const long long* off_in, C* out, cons
                                                   const double2*, const double*, int, C*, long long,  \
                                                   int, cudaStream_t);                                 \
     template cudaError_t launch_set_basis<C>(C*, const long long*, int, cudaStream_t);                \
+    template cudaError_t launch_build_matrices_indexed<C>(const BuildBlock*, int, const BuildOp*,     \
+                                                          const double2*, const double*, C*,          \
+                                                          const long long*, const long long*, int,    \
+                                                          cudaStream_t);                              \
     template cudaError_t launch_gate<C>(C*, const long long*, int, int, const Block&, const C*,       \
                                         long long, cudaStream_t);                                     \
     template cudaError_t launch_pass<C>(C*, const long long*, int, int, const DevPass&,               \

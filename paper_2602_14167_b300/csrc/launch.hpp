@@ -33,6 +33,11 @@ cudaError_t launch_build_matrices(const BuildBlock* blocks, int n_blocks, const 
                                   const double2* pool, const double* params, int P, C* table,
                                   long long table_stride, int items, cudaStream_t s);
 template <typename C>
+cudaError_t launch_build_matrices_indexed(const BuildBlock* blocks, int n_blocks, const BuildOp* bops,
+                                          const double2* pool, const double* params, C* table,
+                                          const long long* prm_off, const long long* tab_off,
+                                          int items, cudaStream_t s);
+template <typename C>
 cudaError_t launch_set_basis(C* state, const long long* item_off, int items, cudaStream_t s);
 template <typename C>
 cudaError_t launch_gate(C* state, const long long* item_off, int items, int n, const Block& blk,

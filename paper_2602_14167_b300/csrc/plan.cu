@@ -335,6 +335,7 @@ void build_plan(Plan& plan) {
             dp.stage_begin = (int)plan.stages.size();
             uint32_t Rset = 0;  // tile-bit mask
             int Rcap = kRegBits;
+            int cur_grads = 0;
             std::vector<int> cur;
             auto close_stage = [&]() {
                 if (cur.empty()) return;
@@ -383,7 +384,8 @@ void build_plan(Plan& plan) {
                     }
                     if (o.adjoint && blk.param_single) {
                         d.grad = (uint8_t)blk.grad;
-                        if (plan.n_grad > 0xFFFF) throw std::invalid_argument("too many parameterised gates");
+                        if (plan.n_grad >= kMaxGradSlots)
+                            throw std::invalid_argument("adjoint: at most 2048 parameterised gates per circuit");
                         d.slot = (uint16_t)plan.n_grad++;
                         ++st.n_grad;
                         plan.grad_param.push_back(blk.param);
@@ -396,6 +398,7 @@ void build_plan(Plan& plan) {
                 cur.clear();
                 Rset = 0;
                 Rcap = kRegBits;
+                cur_grads = 0;
             };
             std::vector<std::vector<int>> pdeps(plan.blocks.size());
             for (int b : pass_list)
@@ -410,6 +413,7 @@ void build_plan(Plan& plan) {
                         if (!done[d]) { ready = false; break; }
                     if (!ready) continue;
                     const Block& blk = plan.blocks[b];
+                    if (o.adjoint && blk.param_single && cur_grads >= kMaxStageGrads) continue;
                     if (blk.diag) { pick = b; break; }
                     uint32_t tbm = 0;
                     uint64_t qm = blk.qmask;
@@ -433,6 +437,7 @@ void build_plan(Plan& plan) {
                 }
                 done[pick] = 1;
                 cur.push_back(pick);
+                if (plan.blocks[pick].param_single) ++cur_grads;
                 --left;
             }
             close_stage();

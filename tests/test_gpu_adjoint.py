@@ -1,0 +1,183 @@
+"""GPU parity of the batched energy + adjoint gradient against the oracle.
+
+Energy error |dE| / sum|c|; gradient error ||dg|| / max(||g_ref||, 1e-3 sum|c|)
+with g_ref the oracle's exact parameter-shift gradient; complex128 1e-12,
+complex64 1e-5.  Full-size batches are checked on sampled items: the energy
+exactly, the gradient through a directional finite difference of the oracle.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import sv  # noqa: E402
+from workloads import Circuit  # noqa: E402
+from workloads import generators as gen  # noqa: E402
+
+TOL = {"c64": 1e-5, "c128": 1e-12}
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2602_14167_b300 import build
+    build.build()
+    from paper_2602_14167_b300 import tcng
+    return tcng
+
+
+def energy_grad(T, n, gates, pool, theta, terms, coeffs=None, dtype="c128"):
+    from paper_2602_14167_b300 import StateBatch
+    theta = np.atleast_2d(theta)
+    B, P = theta.shape
+    st = StateBatch(n, batch=B, dtype=dtype)
+    prm = torch.tensor(theta, dtype=torch.float64, device="cuda")
+    cf = None if coeffs is None else torch.tensor(np.atleast_2d(coeffs), dtype=torch.float64,
+                                                  device="cuda")
+    e = torch.empty(B, dtype=torch.float64, device="cuda")
+    g = torch.empty((B, P), dtype=torch.float64, device="cuda")
+    T.tcng_energy_grad(st.handle, gates, pool, prm, P, terms, cf, e, g)
+    T.tcng_sync_status()
+    return e.cpu().numpy(), g.cpu().numpy(), st
+
+
+def check(e, g, e_ref, g_ref, csum, dtype):
+    assert abs(e - e_ref) / csum < TOL[dtype], (e, e_ref)
+    den = max(np.linalg.norm(g_ref), 1e-3 * csum)
+    assert np.linalg.norm(g - g_ref) / den < TOL[dtype], np.linalg.norm(g - g_ref) / den
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,layers", [(3, 2), (6, 2), (9, 2), (12, 1)])
+def test_ring_ansatz_resident(T, n, layers, dtype):
+    b = gen.tfim_batch(n, 1, layers=layers, seed=n)
+    g, p = b["circuit"].to_ir()
+    th, cf = b["theta"][0], b["coeffs"][0]
+    e, gr, _ = energy_grad(T, n, g, p, th, b["terms"], cf, dtype)
+    e_ref = sv.energy(n, g, p, th, b["terms"], cf)
+    g_ref = sv.grad_param_shift(n, g, p, th, b["terms"], cf)
+    check(e[0], gr[0], e_ref, g_ref, np.abs(cf).sum(), dtype)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_streamed_states(T, dtype):
+    """n = 15 exceeds the shared-memory resident size: tiles stream through scratch."""
+    n = 15
+    b = gen.tfim_batch(n, 1, layers=1, seed=2)
+    g, p = b["circuit"].to_ir()
+    th, cf = b["theta"][0], b["coeffs"][0]
+    e, gr, _ = energy_grad(T, n, g, p, th, b["terms"], cf, dtype)
+    e_ref = sv.energy(n, g, p, th, b["terms"], cf)
+    g_ref = sv.grad_param_shift(n, g, p, th, b["terms"], cf)
+    check(e[0], gr[0], e_ref, g_ref, np.abs(cf).sum(), dtype)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_all_parameterised_kinds_with_constant_gates(T, seed):
+    n = 7
+    c, th = gen.random_circuit(n, 70, seed=seed)
+    g, p = c.to_ir()
+    terms = np.concatenate([gen.xxz_terms(n, 0.9, 0.6, 0.4), gen.random_pauli_strings(n, 6, 3, seed)])
+    e, gr, _ = energy_grad(T, n, g, p, th, terms)
+    e_ref = sv.energy(n, g, p, th, terms)
+    g_ref = sv.grad_param_shift(n, g, p, th, terms)
+    check(e[0], gr[0], e_ref, g_ref, np.abs(terms["coeff"]).sum(), "c128")
+    fd = sv.grad_fd(n, g, p, th, terms, h=1e-5)
+    assert np.max(np.abs(gr[0] - fd)) < 1e-8
+
+
+def test_shared_parameters_and_scales(T):
+    n = 6
+    c = Circuit(n)
+    for q in range(n):
+        c.h(q)
+    for q in range(n):
+        c.rx(q, param=0, scale=0.5).ry(q, param=1 + q % 2, scale=-1.5)
+    for q in range(n - 1):
+        c.rzz(q, q + 1, param=3, angle=0.2).cp(q, q + 1, param=4, scale=2.0)
+    g, p = c.to_ir()
+    th = np.array([0.3, -0.7, 1.1, 0.4, -0.2])
+    terms = gen.tfim_terms(n, 1.0, 0.8)
+    e, gr, _ = energy_grad(T, n, g, p, th, terms)
+    check(e[0], gr[0], sv.energy(n, g, p, th, terms), sv.grad_param_shift(n, g, p, th, terms),
+          np.abs(terms["coeff"]).sum(), "c128")
+
+
+def test_batch_items_and_forward_state(T):
+    n, B = 8, 6
+    b = gen.tfim_batch(n, B, layers=2, seed=9)
+    g, p = b["circuit"].to_ir()
+    e, gr, st = energy_grad(T, n, g, p, b["theta"], b["terms"], b["coeffs"], "c64")
+    for i in range(B):
+        e_ref = sv.energy(n, g, p, b["theta"][i], b["terms"], b["coeffs"][i])
+        g_ref = sv.grad_param_shift(n, g, p, b["theta"][i], b["terms"], b["coeffs"][i])
+        check(e[i], gr[i], e_ref, g_ref, np.abs(b["coeffs"][i]).sum(), "c64")
+        psi = st.amplitudes(i).cpu().numpy()
+        ref = sv.apply(n, g, p, b["theta"][i])
+        assert np.linalg.norm(psi - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_ragged_batch_one_launch(T):
+    from paper_2602_14167_b300 import tcng
+    ns = [6, 14, 9, 6]
+    probs, thetas, coeffs, structs = [], [], [], {}
+    for n in sorted(set(ns)):
+        c = gen.hea_ring(n, 1)
+        g, p = c.to_ir()
+        structs[n] = len(probs)
+        probs.append(dict(n=n, gates=g, pool=p, P=c.n_params, terms=gen.tfim_terms(n, 1.0, 1.0)))
+    item_problem = [structs[n] for n in ns]
+    rng = np.random.default_rng(0)
+    for n in ns:
+        P = probs[structs[n]]["P"]
+        thetas.append(rng.uniform(-np.pi, np.pi, P))
+        coeffs.append(-rng.uniform(0.5, 1.5, 2 * n - 1))
+    prm = torch.tensor(np.concatenate(thetas), dtype=torch.float64, device="cuda")
+    cf = torch.tensor(np.concatenate(coeffs), dtype=torch.float64, device="cuda")
+    e = torch.empty(len(ns), dtype=torch.float64, device="cuda")
+    gr = torch.empty_like(prm)
+    tcng.tcng_energy_grad_ragged(probs, item_problem, prm, cf, e, gr)
+    tcng.tcng_sync_status()
+    e = e.cpu().numpy()
+    gr = gr.cpu().numpy()
+    off = 0
+    for i, n in enumerate(ns):
+        pr = probs[structs[n]]
+        P = pr["P"]
+        e_ref = sv.energy(n, pr["gates"], pr["pool"], thetas[i], pr["terms"], coeffs[i])
+        g_ref = sv.grad_param_shift(n, pr["gates"], pr["pool"], thetas[i], pr["terms"], coeffs[i])
+        check(e[i], gr[off:off + P], e_ref, g_ref, np.abs(coeffs[i]).sum(), "c64")
+        off += P
+
+
+def test_full_size_batch_sampled(T):
+    """n = 16, B = 1024, 12 layers (576 parameters): sampled items vs the oracle."""
+    n, B = 16, 1024
+    b = gen.tfim_batch(n, B, layers=12, seed=0)
+    g, p = b["circuit"].to_ir()
+    e, gr, _ = energy_grad(T, n, g, p, b["theta"], b["terms"], b["coeffs"], "c64")
+    rng = np.random.default_rng(1)
+    for i in [0, 511, B - 1]:
+        th, cf = b["theta"][i], b["coeffs"][i]
+        csum = np.abs(cf).sum()
+        assert abs(e[i] - sv.energy(n, g, p, th, b["terms"], cf)) / csum < 1e-5
+        v = rng.standard_normal(th.size)
+        v /= np.linalg.norm(v)
+        h = 1e-4
+        dd = (sv.energy(n, g, p, th + h * v, b["terms"], cf) -
+              sv.energy(n, g, p, th - h * v, b["terms"], cf)) / (2 * h)
+        assert abs(np.dot(gr[i], v) - dd) / csum < 1e-5
+    assert np.all(np.isfinite(gr))
+
+
+def test_energy_above_free_fermion_ground(T):
+    n, B = 12, 64
+    b = gen.tfim_batch(n, B, layers=3, seed=4)
+    g, p = b["circuit"].to_ir()
+    e, _, _ = energy_grad(T, n, g, p, b["theta"], b["terms"], b["coeffs"], "c64")
+    from oracle import dense
+    for i in range(B):
+        e0 = dense.tfim_ground_energy_free_fermion(b["J"][i], np.full(n, b["g"][i]))
+        assert e[i] >= e0 - 1e-5
