@@ -105,7 +105,7 @@ __device__ __forceinline__ typename Real<C>::T grad_part(const DevOp& op, const 
 template <typename C, int R>
 __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, const DevStage& st,
                                   const DevOp* __restrict__ ops, const C* __restrict__ mats,
-                                  int tile_bits, long long gbase, float* red) {
+                                  int tile_bits, long long gbase, typename Real<C>::T* red) {
     using T = typename Real<C>::T;
     const int ngroups = 1 << (tile_bits - R);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -136,7 +136,7 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
             const C* M = mats + op.mat;
             if (op.grad != G_NONE) {
                 T v = active ? grad_part<C, R>(op, p, l, tau, L, gbase) : T(0);
-                const float w = warp_sum((float)v);
+                const T w = warp_sum(v);
                 if (lane == 0) red[warp * kMaxStageGrads + j] += w;
                 ++j;
             }
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(AdjArgs a) {
     C* sl = sp + res_elems;
     C* mats = sl + res_elems;
     double* gacc = reinterpret_cast<double*>(mats + kMaxPassMat);
-    float* red = reinterpret_cast<float*>(gacc + kMaxGradSlots);
+    T* red = reinterpret_cast<T*>(gacc + kMaxGradSlots);
     uint64_t* bar = reinterpret_cast<uint64_t*>(red + 32 * kMaxStageGrads);
     __shared__ int s_item;
     __shared__ double s_red[32];
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(AdjArgs a) {
                     const long long gbase = resident ? 0 : tile_global_base(P, t);
                     for (int si = P.stage_count - 1; si >= 0; --si) {
                         const DevStage st = S.stages[P.stage_begin + si];
-                        for (int i = tid; i < nwarps * kMaxStageGrads; i += nthreads) red[i] = 0.f;
+                        for (int i = tid; i < nwarps * kMaxStageGrads; i += nthreads) red[i] = T(0);
                         __syncthreads();
                         if (RMAX == kMaxRegBits && st.nreg == kMaxRegBits)
                             run_stage_adjoint<C, RMAX>(tp, tl, st, S.dops, mats, P.m, gbase, red);
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(AdjArgs a) {
 template <typename C>
 size_t adjoint_smem_bytes(int res_bits) {
     return 2 * (sizeof(C) << res_bits) + sizeof(C) * kMaxPassMat + sizeof(double) * kMaxGradSlots +
-           sizeof(float) * 32 * kMaxStageGrads + 16;
+           sizeof(typename Real<C>::T) * 32 * kMaxStageGrads + 16;
 }
 
 template <typename C>
