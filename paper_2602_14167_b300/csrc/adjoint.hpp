@@ -55,7 +55,7 @@ struct AdjArgs {
 };
 
 template <typename C>
-cudaError_t launch_adjoint(const AdjArgs& a, bool wide, int grid, cudaStream_t s);
+cudaError_t launch_adjoint(const AdjArgs& a, int grid, cudaStream_t s);
 template <typename C>
 size_t adjoint_smem_bytes(int res_bits);
 

@@ -35,7 +35,6 @@ struct AdjLayout {
     long long table_elems = 0;
     int res_bits = 0;
     int max_stream_n = 0;
-    bool wide = false;
     ~AdjLayout() {
         cudaFree(d_structs);
         cudaFree(d_items);
@@ -101,8 +100,6 @@ static AdjLayout* get_layout(const tcng_problem* probs, int n_probs, const int* 
         TermSet* ts = get_terms(p.H, p.n_terms, p.n);
         lay->plans.push_back(dp);
         lay->termsets.push_back(ts);
-        for (const DevStage& st : dp->plan.stages)
-            if (st.nreg > kRegBits) lay->wide = true;
         if (!resident) lay->max_stream_n = std::max(lay->max_stream_n, n_eff);
         StructDesc sd{};
         sd.n = p.n;
@@ -216,7 +213,7 @@ static tcng_status run_adjoint(AdjLayout* lay, int batch, const double* params, 
     a.scratch_elems = selems;
     a.err = c.err;
     ProfScope ps(sizeof(C) == 8 ? "adjoint_kernel_c64" : "adjoint_kernel_c128", s);
-    e = launch_adjoint<C>(a, lay->wide, grid, s);
+    e = launch_adjoint<C>(a, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel");
     return TCNG_OK;
 }

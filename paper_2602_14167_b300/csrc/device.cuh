@@ -287,16 +287,67 @@ __device__ __forceinline__ void run_stage_group(C* __restrict__ buf, const DevSt
     for (int s = 0; s < (1 << R); ++s) buf[L[s]] = a[s];
 }
 
-// One stage over a whole tile by the CTA (no trailing barrier).  RMAX = 4
-// compiles only the 16-amplitude path; RMAX = 5 adds the 32-amplitude one.
-template <typename C, int RMAX>
+// Generic stage executor working directly on the shared-memory tile, one op at
+// a time (used for stages holding a 5-qubit block, which are rare: unrolling
+// 32-amplitude register groups would dominate compile time).  DAG applies the
+// conjugate transpose in reverse op order.  Contains barriers: call with the
+// whole CTA.
+template <typename C, bool DAG>
+__device__ void run_stage_smem(C* __restrict__ buf, const DevStage& st, const DevOp* __restrict__ ops,
+                               const C* __restrict__ mats, int tile_bits, long long gbase) {
+    const int N = 1 << tile_bits;
+    for (uint32_t ii = 0; ii < st.op_count; ++ii) {
+        const uint32_t i = DAG ? st.op_count - 1 - ii : ii;
+        const DevOp op = ops[st.op_begin + i];
+        const C* M = mats + op.mat;
+        if (op.kind == K_DENSE) {
+            int tb[TCNG_MAX_FUSE];
+            int k = 0;
+            for (int r = 0; r < st.nreg; ++r)
+                if ((op.mask >> r) & 1) tb[k++] = st.rbit[r];
+            const int D = 1 << k;
+            for (int c = threadIdx.x; c < (N >> k); c += blockDim.x) {
+                int x = c;
+                for (int j = 0; j < k; ++j) x = ((x >> tb[j]) << (tb[j] + 1)) | (x & ((1 << tb[j]) - 1));
+                C v[32];
+                for (int s = 0; s < D; ++s) {
+                    int y = x;
+                    for (int j = 0; j < k; ++j)
+                        if ((s >> j) & 1) y |= 1 << tb[j];
+                    v[s] = buf[y];
+                }
+                for (int r = 0; r < D; ++r) {
+                    C acc = cmk<C>(0, 0);
+                    for (int s = 0; s < D; ++s) {
+                        const C m = DAG ? cconj(M[s * D + r]) : M[r * D + s];
+                        cfma(acc, m, v[s]);
+                    }
+                    int y = x;
+                    for (int j = 0; j < k; ++j)
+                        if ((r >> j) & 1) y |= 1 << tb[j];
+                    buf[y] = acc;
+                }
+            }
+        } else {
+            for (int L = threadIdx.x; L < N; L += blockDim.x) {
+                int idx = 0;
+                for (int j = 0; j < op.k; ++j) idx |= src_bit(op.src[j], L, gbase) << j;
+                C d = M[idx];
+                if (DAG) d = cconj(d);
+                buf[L] = cmul(d, buf[L]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// One stage over a whole tile by the CTA (no trailing barrier for register stages).
+template <typename C>
 __device__ __forceinline__ void run_stage(C* __restrict__ buf, const DevStage& st,
                                           const DevOp* __restrict__ ops, const C* __restrict__ mats,
                                           int tile_bits, long long gbase) {
-    if (RMAX == kMaxRegBits && st.nreg == kMaxRegBits) {
-        const int ngroups = 1 << (tile_bits - kMaxRegBits);
-        for (int g = threadIdx.x; g < ngroups; g += blockDim.x)
-            run_stage_group<C, RMAX>(buf, st, ops, mats, g, gbase);
+    if (st.nreg > kRegBits) {
+        run_stage_smem<C, false>(buf, st, ops, mats, tile_bits, gbase);
     } else {
         const int ngroups = 1 << (tile_bits - kRegBits);
         for (int g = threadIdx.x; g < ngroups; g += blockDim.x)

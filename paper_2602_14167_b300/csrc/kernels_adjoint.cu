@@ -160,13 +160,6 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
     }
 }
 
-// Forward stage over one tile (all threads; inactive ones idle).
-template <typename C, int RMAX>
-__device__ __forceinline__ void run_stage_fwd(C* __restrict__ buf, const DevStage& st,
-                                              const DevOp* __restrict__ ops, const C* __restrict__ mats,
-                                              int tile_bits, long long gbase) {
-    run_stage<C, RMAX>(buf, st, ops, mats, tile_bits, gbase);
-}
 
 // ---------------------------------------------------------- tile movement --
 // Synchronous copy of one tile (chunks of 2^chunk amplitudes) between global
@@ -216,7 +209,7 @@ __device__ void tile_store(const DevPass& p, long long tile, C* const* gptr, C* 
 }
 
 // ------------------------------------------------------------------ kernel --
-template <typename C, int RMAX>
+template <typename C>
 __global__ void __launch_bounds__(256, 1) adjoint_kernel(AdjArgs a) {
     using T = typename Real<C>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -282,7 +275,7 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(AdjArgs a) {
                 const long long gbase = resident ? 0 : tile_global_base(P, t);
                 for (int si = 0; si < P.stage_count; ++si) {
                     const DevStage st = S.stages[P.stage_begin + si];
-                    run_stage_fwd<C, RMAX>(sp, st, S.dops, mats, P.m, gbase);
+                    run_stage<C>(sp, st, S.dops, mats, P.m, gbase);
                     __syncthreads();
                 }
                 if (!resident) {
@@ -361,10 +354,12 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(AdjArgs a) {
                         const DevStage st = S.stages[P.stage_begin + si];
                         for (int i = tid; i < nwarps * kMaxStageGrads; i += nthreads) red[i] = T(0);
                         __syncthreads();
-                        if (RMAX == kMaxRegBits && st.nreg == kMaxRegBits)
-                            run_stage_adjoint<C, RMAX>(tp, tl, st, S.dops, mats, P.m, gbase, red);
-                        else
+                        if (st.nreg > kRegBits) {   // 5-qubit constant block: no gradient ops here
+                            run_stage_smem<C, true>(tp, st, S.dops, mats, P.m, gbase);
+                            run_stage_smem<C, true>(tl, st, S.dops, mats, P.m, gbase);
+                        } else {
                             run_stage_adjoint<C, kRegBits>(tp, tl, st, S.dops, mats, P.m, gbase, red);
+                        }
                         __syncthreads();
                         // fold this stage's gradient partials (fixed order) into gacc
                         if (tid < (int)st.n_grad) {
@@ -409,9 +404,9 @@ size_t adjoint_smem_bytes(int res_bits) {
 }
 
 template <typename C>
-cudaError_t launch_adjoint(const AdjArgs& a, bool wide, int grid, cudaStream_t s) {
+cudaError_t launch_adjoint(const AdjArgs& a, int grid, cudaStream_t s) {
     const size_t smem = adjoint_smem_bytes<C>(a.res_bits);
-    auto kern = wide ? adjoint_kernel<C, kMaxRegBits> : adjoint_kernel<C, kRegBits>;
+    auto kern = adjoint_kernel<C>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, 256, smem, s>>>(a);
@@ -419,8 +414,8 @@ cudaError_t launch_adjoint(const AdjArgs& a, bool wide, int grid, cudaStream_t s
     return cudaGetLastError();
 }
 
-template cudaError_t launch_adjoint<float2>(const AdjArgs&, bool, int, cudaStream_t);
-template cudaError_t launch_adjoint<double2>(const AdjArgs&, bool, int, cudaStream_t);
+template cudaError_t launch_adjoint<float2>(const AdjArgs&, int, cudaStream_t);
+template cudaError_t launch_adjoint<double2>(const AdjArgs&, int, cudaStream_t);
 template size_t adjoint_smem_bytes<float2>(int);
 template size_t adjoint_smem_bytes<double2>(int);
 

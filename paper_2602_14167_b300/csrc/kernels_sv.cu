@@ -295,7 +295,7 @@ __device__ __forceinline__ void issue_tile_store(C* state, const long long* item
     bulk_commit();
 }
 
-template <typename C, int RMAX>
+template <typename C>
 __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
                                                     const long long* __restrict__ item_off,
                                                     const __grid_constant__ DevPass p,
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
         const long long gbase = tile_global_base(p, t % tc.tiles_per_item);
         for (int s = 0; s < p.stage_count; ++s) {
             const DevStage st = stages[p.stage_begin + s];
-            run_stage<C, RMAX>(buf, st, ops, mats, p.m, gbase);
+            run_stage<C>(buf, st, ops, mats, p.m, gbase);
             __syncthreads();
         }
         fence_proxy_async_smem();
@@ -652,12 +652,11 @@ cudaError_t launch_pass(C* state, const long long* item_off, int items, int n, c
                         const C* table, long long table_stride, unsigned* err, cudaStream_t s) {
     const int nbuf = 3;
     const size_t smem = pass_smem_bytes<C>(p, nbuf);
-    bool wide = false;
-    for (int i = 0; i < p.stage_count; ++i) wide = wide || host_stages[p.stage_begin + i].nreg > kRegBits;
-    auto kern = wide ? pass_kernel<C, kMaxRegBits> : pass_kernel<C, kRegBits>;
-    static bool done[2] = {false, false};
-    static size_t lim[2] = {0, 0};
-    if (smem > dyn_smem_limit(kern, &done[wide], &lim[wide])) return cudaErrorInvalidConfiguration;
+    (void)host_stages;
+    auto kern = pass_kernel<C>;
+    static bool done = false;
+    static size_t lim = 0;
+    if (smem > dyn_smem_limit(kern, &done, &lim)) return cudaErrorInvalidConfiguration;
     TileCtx tc = make_ctx(p, n, items, sizeof(C), nbuf);
     const int threads = std::max(32, (1 << p.m) >> kRegBits);
     int per_sm = 1;

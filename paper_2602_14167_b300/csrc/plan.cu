@@ -413,7 +413,9 @@ void build_plan(Plan& plan) {
                         if (!done[d]) { ready = false; break; }
                     if (!ready) continue;
                     const Block& blk = plan.blocks[b];
-                    if (o.adjoint && blk.param_single && cur_grads >= kMaxStageGrads) continue;
+                    if (o.adjoint && blk.param_single &&
+                        (cur_grads >= kMaxStageGrads || Rcap > kRegBits))
+                        continue;   // gradient ops stay in 16-amplitude register stages
                     if (blk.diag) { pick = b; break; }
                     uint32_t tbm = 0;
                     uint64_t qm = blk.qmask;
