@@ -141,6 +141,33 @@ tcng_status tcng_expect_pauli(const tcng_state* st, const tcng_pauli* terms, siz
                               double* out_dev, void* stream);
 
 /*
+ * tcng_expect_pauli_noalloc -- out_dev[t] = <psi|P_t|psi> for one state vector,
+ * like tcng_expect_pauli, but without allocating any device memory.  The paper
+ * has no counterpart; this is for callers that cannot let a library allocate:
+ * an application whose own allocator already holds the GPU's free memory, a
+ * serving loop where cudaMalloc/cudaFree (and the synchronisation cudaFree
+ * implies) are banned from the hot path, or work recorded into a stream
+ * capture, where cudaMalloc is illegal.
+ *   psi_dev   device state, 2^n amplitudes of type dt, 256-byte aligned;
+ *   terms     host array of n_terms Pauli strings (masks < 2^n);
+ *   out_dev   device double [n_terms].
+ * Scratch: the per-CTA partial sums live in a fixed array of 65536 doubles
+ * (512 KiB) in the library's own device memory; every GPU that loads the
+ * library keeps it until the process exits.  Requests that need more than
+ * 65536 partial sums (n_terms x CTAs, at most one CTA per SM) fail with
+ * TCNG_EINVAL and a message giving the size.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (different streams, or different host threads) race on it and
+ * must be serialised by the caller.  Each call writes every slot it reads, so
+ * no state carries over between calls.  No device-side error word is kept for
+ * this call (a timed-out wait just ends the kernel).
+ */
+tcng_status tcng_expect_pauli_noalloc(const void* psi_dev, int n, tcng_dtype dt,
+                                      const tcng_pauli* terms, size_t n_terms, double* out_dev,
+                                      void* stream);
+
+/*
  * tcng_energy -- energy_dev[b] = sum_t c[b][t] <psi_b|P_t|psi_b>, the TFIM (or
  * any Pauli-sum) energy of Sec. I.B.  coeffs_dev: device double [batch][n_terms],
  * or NULL to use terms[t].coeff for every item.  Errors: as tcng_expect_pauli.

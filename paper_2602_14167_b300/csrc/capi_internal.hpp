@@ -95,6 +95,8 @@ DevPlan* get_plan(int n, const tcng_gate* ops, size_t n_ops, const double* pool,
                   const PlanOptions& o);
 void* plan_table(DevPlan* dp, size_t elem, int items);
 TermSet* get_terms(const tcng_pauli* terms, size_t n_terms, int n);
+void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
+                      std::vector<DevPass>& passes, std::vector<ExpPass>& eps);
 template <typename C>
 tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int items,
                      const double* params, cudaStream_t s);

@@ -60,6 +60,7 @@ def lib():
             "tcng_state_reset": [vp, vp],
             "tcng_apply_circuit": [vp, vp, sz, vp, sz, vp, i32, vp],
             "tcng_expect_pauli": [vp, vp, sz, vp, vp],
+            "tcng_expect_pauli_noalloc": [vp, i32, i32, vp, sz, vp, vp],
             "tcng_energy": [vp, vp, sz, vp, vp, vp],
             "tcng_hamiltonian_apply": [vp, vp, sz, vp, vp, vp],
             "tcng_energy_grad": [vp, vp, sz, vp, sz, vp, i32, vp, sz, vp, vp, vp, vp],
@@ -180,6 +181,13 @@ def tcng_apply_circuit(handle, gates, pool, params_dev, P, stream=None):
 def tcng_expect_pauli(handle, terms, out_dev, stream=None):
     t = _terms(terms)
     _check(lib().tcng_expect_pauli(handle, t.ctypes.data, len(t), _ptr(out_dev), _stream(stream)))
+
+
+def tcng_expect_pauli_noalloc(psi_dev, n, dtype, terms, out_dev, stream=None):
+    """Expectations of one state without any device allocation (static scratch)."""
+    t = _terms(terms)
+    _check(lib().tcng_expect_pauli_noalloc(_ptr(psi_dev), int(n), int(dtype), t.ctypes.data, len(t),
+                                           _ptr(out_dev), _stream(stream)))
 
 
 def tcng_energy(handle, terms, coeffs_dev, energy_dev, stream=None):
@@ -307,7 +315,7 @@ def tcng_version():
 
 EXPORTED = [
     "tcng_state_init", "tcng_state_bytes", "tcng_state_free", "tcng_state_ptr", "tcng_state_reset",
-    "tcng_apply_circuit", "tcng_expect_pauli", "tcng_energy", "tcng_hamiltonian_apply",
+    "tcng_apply_circuit", "tcng_expect_pauli", "tcng_expect_pauli_noalloc", "tcng_energy", "tcng_hamiltonian_apply",
     "tcng_energy_grad", "tcng_energy_grad_ragged", "tcng_apply_shared_unitary", "tcng_adam_step",
     "tcng_adam_step_f32", "tcng_mlp_forward", "tcng_mlp_backward", "tcng_set_option",
     "tcng_get_option", "tcng_autotune", "tcng_sync_status", "tcng_describe_plan",

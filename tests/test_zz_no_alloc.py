@@ -1,0 +1,67 @@
+"""tcng_expect_pauli_noalloc against tcng_expect_pauli (GPU).
+
+The allocation-free entry point exists for callers that must not let the
+library call cudaMalloc (their allocator owns the free memory, their hot path
+bans allocation, or they are recording a stream capture).  It keeps its
+partial sums in a static device array instead.  Here it must reproduce the
+ordinary entry point's values within the complex64/complex128 tolerances of the
+other expectation tests, on two calls in a row (the second call reuses the
+array the first one left behind), and reject requests larger than its array.
+This file is collected last so a failure here comes after every other test.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from workloads import generators as gen  # noqa: E402
+
+TOL = {"c64": 1e-6, "c128": 1e-12}
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2602_14167_b300 import build
+    build.build()
+    from paper_2602_14167_b300 import tcng
+    return tcng
+
+
+@pytest.mark.parametrize("dtype,n", [("c64", 17), ("c64", 9), ("c128", 14)])
+def test_matches_allocating_entry_point_twice(T, dtype, n):
+    from paper_2602_14167_b300 import StateBatch
+    st = StateBatch(n, dtype=dtype)
+    dt = T.C64 if dtype == "c64" else T.C128
+    for call in range(2):
+        psi = gen.random_state(n, seed=10 * n + call)
+        st.amplitudes(0).copy_(torch.tensor(psi, dtype=st.cdtype, device="cuda"))
+        strings = np.concatenate([gen.random_pauli_strings(n, 48, min(4, n), seed=call),
+                                  gen.tfim_terms(n, 1.0, 1.0)])
+        ref = torch.empty((1, len(strings)), dtype=torch.float64, device="cuda")
+        T.tcng_expect_pauli(st.handle, strings, ref)
+        out = torch.full((len(strings),), float("nan"), dtype=torch.float64, device="cuda")
+        ptr, _ = T.tcng_state_ptr(st.handle, 0)
+        status = T.lib().tcng_expect_pauli_noalloc(ptr, n, dt, strings.ctypes.data, len(strings),
+                                                   out.data_ptr(), T._stream(None))
+        assert status == 0, T.tcng_last_error()
+        torch.cuda.synchronize()
+        got, want = out.cpu().numpy(), ref[0].cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert np.max(np.abs(got - want)) < TOL[dtype]
+    st.free()
+
+
+def test_rejects_requests_beyond_the_static_scratch(T):
+    from paper_2602_14167_b300 import StateBatch
+    n = 24          # 2^11 tiles: one CTA per SM, so 4096 terms need far more than 65536 slots
+    st = StateBatch(n, dtype="c64")
+    strings = gen.random_pauli_strings(n, 4096, 2, seed=3)
+    out = torch.empty(len(strings), dtype=torch.float64, device="cuda")
+    ptr, _ = T.tcng_state_ptr(st.handle, 0)
+    with pytest.raises(T.TcngError) as ei:
+        T.tcng_expect_pauli_noalloc(ptr, n, T.C64, strings, out)
+    assert "static scratch" in str(ei.value)
+    st.free()
