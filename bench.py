@@ -272,6 +272,8 @@ def run_gpu(args):
     st.free()
     del st
     torch.cuda.empty_cache()
+    if not args.no_vqe:
+        out["vqe"] = vqe_bench(args, dev, dist, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         moved, times, cores = oracle_sample(3, 4)
         v = moved * len(times) / sum(times) / 1e9
@@ -286,6 +288,102 @@ def run_gpu(args):
     return 0
 
 
+def vqe_bench(args, dev, dist, world):
+    """Batched energy + adjoint-gradient evaluations per second (TFIM ring ansatz,
+    12 layers): n=16, B=1024, and a ragged batch of 1024 items with n in
+    {12,14,16,18,20}; against the plain one-circuit parameter-shift gradient
+    (2P+1 single-circuit energy evaluations) on the same GPU."""
+    import torch
+    from paper_2602_14167_b300 import tcng as T
+    from paper_2602_14167_b300 import StateBatch
+    from paper_2602_14167_b300.vqe import VQEBatch
+
+    res = {}
+    n, B = 16, 1024
+    b = gen.tfim_batch(n, B, layers=12, seed=0)
+    g, p = b["circuit"].to_ir()
+    vb = VQEBatch(n, g, p, b["terms"], B, coeffs=b["coeffs"], dtype="c64", device=dev)
+    theta = torch.tensor(b["theta"], dtype=torch.float64, device=dev)
+    for _ in range(max(3, args.warmup)):
+        vb.energy_and_grad(theta)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        vb.energy_and_grad(theta)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t[0])
+    res["n16_b1024"] = {"evals_per_s": world * B / (ms * 1e-3), "ms_per_batch": ms,
+                        "params_per_item": vb.P}
+    del vb
+
+    # ragged batch, one persistent launch
+    ns = gen.ragged_sizes(B, seed=0)
+    probs, sidx = [], {}
+    for nn in sorted(set(int(x) for x in ns)):
+        c = gen.hea_ring(nn, 12)
+        gg, pp = c.to_ir()
+        sidx[nn] = len(probs)
+        probs.append(dict(n=nn, gates=gg, pool=pp, P=c.n_params, terms=gen.tfim_terms(nn, 1.0, 1.0)))
+    item_problem = [sidx[int(x)] for x in ns]
+    rng = np.random.default_rng(1)
+    th = np.concatenate([rng.uniform(-np.pi, np.pi, probs[s]["P"]) for s in item_problem])
+    cf = np.concatenate([-rng.uniform(0.5, 1.5, 2 * probs[s]["n"] - 1) for s in item_problem])
+    prm = torch.tensor(th, device=dev)
+    cfd = torch.tensor(cf, device=dev)
+    en = torch.empty(B, dtype=torch.float64, device=dev)
+    gr = torch.empty_like(prm)
+    for _ in range(3):
+        T.tcng_energy_grad_ragged(probs, item_problem, prm, cfd, en, gr)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        T.tcng_energy_grad_ragged(probs, item_problem, prm, cfd, en, gr)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_r = e0.elapsed_time(e1) / args.steps
+    res["ragged_b1024"] = {"evals_per_s": world * B / (ms_r * 1e-3), "ms_per_batch": ms_r,
+                           "n_mix": {str(k): int((ns == k).sum()) for k in sorted(sidx)}}
+
+    # baseline: one circuit, parameter shift (2P + 1 energies), same GPU kernels
+    st = StateBatch(n, dtype="c64", device=dev)
+    P = 3 * n * 12
+    th1 = torch.tensor(b["theta"][0], dtype=torch.float64, device=dev).reshape(1, -1)
+    cf1 = torch.tensor(b["coeffs"][0], dtype=torch.float64, device=dev).reshape(1, -1)
+    en1 = torch.empty(1, dtype=torch.float64, device=dev)
+    terms = b["terms"]
+
+    def one_energy():
+        T.tcng_state_reset(st.handle)
+        T.tcng_apply_circuit(st.handle, g, p, th1, P)
+        T.tcng_energy(st.handle, terms, cf1, en1)
+
+    for _ in range(5):
+        one_energy()
+    torch.cuda.synchronize()
+    n_evals = 64
+    t0 = time.perf_counter()
+    for _ in range(n_evals):
+        one_energy()
+    torch.cuda.synchronize()
+    per_energy = (time.perf_counter() - t0) / n_evals
+    per_grad = per_energy * (2 * P + 1)
+    res["baseline_param_shift"] = {"evals_per_s": 1.0 / per_grad, "ms_per_energy": per_energy * 1e3,
+                                   "energies_per_gradient": 2 * P + 1,
+                                   "note": "one circuit at a time, tcng_apply_circuit + tcng_energy, "
+                                           f"timed over {n_evals} energies and scaled to 2P+1"}
+    res["speedup_vs_param_shift"] = res["n16_b1024"]["evals_per_s"] / res["baseline_param_shift"]["evals_per_s"]
+    st.free()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -293,6 +391,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-vqe", action="store_true", help="skip the batched VQE measurement")
     ap.add_argument("--qubits", type=int, default=N_QUBITS, help="smaller cases for profiling only")
     ap.add_argument("--depth", type=int, default=DEPTH, help="smaller cases for profiling only")
     args = ap.parse_args()

@@ -8,14 +8,6 @@ extern "C" {
 tcng_status tcng_apply_shared_unitary(tcng_state*, const int*, int, const double*, void*) {
     return fail(TCNG_EUNSUPPORTED, "tcng_apply_shared_unitary is not built yet");
 }
-tcng_status tcng_adam_step(double*, double*, double*, const double*, size_t, double, double, double,
-                           double, int*, void*) {
-    return fail(TCNG_EUNSUPPORTED, "tcng_adam_step is not built yet");
-}
-tcng_status tcng_adam_step_f32(float*, float*, float*, const float*, size_t, float, float, float,
-                               float, int*, void*) {
-    return fail(TCNG_EUNSUPPORTED, "tcng_adam_step_f32 is not built yet");
-}
 tcng_status tcng_mlp_forward(const float*, int, int, int, int, const float*, const float*,
                              const float*, const float*, const float*, const float*, float*, float*,
                              void*) {

@@ -407,8 +407,12 @@ template <typename C>
 cudaError_t launch_adjoint(const AdjArgs& a, int grid, cudaStream_t s) {
     const size_t smem = adjoint_smem_bytes<C>(a.res_bits);
     auto kern = adjoint_kernel<C>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    static size_t set_bytes = 0;   // set once (the call is not legal inside every stream capture)
+    if (set_bytes < smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set_bytes = smem;
+    }
     kern<<<grid, 256, smem, s>>>(a);
     count_launch();
     return cudaGetLastError();
