@@ -28,6 +28,8 @@ class VQEBatch:
         self.gates, self.pool, self.terms = gates, pool, terms
         self.P = int(max((int(g["param"]) for g in gates), default=-1) + 1)
         self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         self.state = StateBatch(n, batch=batch, dtype=dtype, device=self.device)
         self.coeffs = None
         if coeffs is not None:
