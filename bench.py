@@ -154,6 +154,14 @@ def run_reference(args):
     return 0
 
 
+def run_vqe_only(args):
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    print(json.dumps({"vqe": vqe_bench(args, dev, None, 1)}))
+    return 0
+
+
 def run_gpu(args):
     import torch
     from paper_2602_14167_b300 import StateBatch
@@ -299,7 +307,7 @@ def vqe_bench(args, dev, dist, world):
     from paper_2602_14167_b300.vqe import VQEBatch
 
     res = {}
-    n, B = 16, 1024
+    n, B = 16, args.vqe_batch
     b = gen.tfim_batch(n, B, layers=12, seed=0)
     g, p = b["circuit"].to_ir()
     vb = VQEBatch(n, g, p, b["terms"], B, coeffs=b["coeffs"], dtype="c64", device=dev)
@@ -320,11 +328,13 @@ def vqe_bench(args, dev, dist, world):
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t[0])
-    res["n16_b1024"] = {"evals_per_s": world * B / (ms * 1e-3), "ms_per_batch": ms,
+    res[f"n16_b{B}"] = {"evals_per_s": world * B / (ms * 1e-3), "ms_per_batch": ms,
                         "params_per_item": vb.P}
     del vb
 
     # ragged batch, one persistent launch
+    if args.vqe_only:
+        return res
     ns = gen.ragged_sizes(B, seed=0)
     probs, sidx = [], {}
     for nn in sorted(set(int(x) for x in ns)):
@@ -349,7 +359,7 @@ def vqe_bench(args, dev, dist, world):
     e1.record()
     torch.cuda.synchronize()
     ms_r = e0.elapsed_time(e1) / args.steps
-    res["ragged_b1024"] = {"evals_per_s": world * B / (ms_r * 1e-3), "ms_per_batch": ms_r,
+    res[f"ragged_b{B}"] = {"evals_per_s": world * B / (ms_r * 1e-3), "ms_per_batch": ms_r,
                            "n_mix": {str(k): int((ns == k).sum()) for k in sorted(sidx)}}
 
     # baseline: one circuit, parameter shift (2P + 1 energies), same GPU kernels
@@ -379,7 +389,7 @@ def vqe_bench(args, dev, dist, world):
                                    "energies_per_gradient": 2 * P + 1,
                                    "note": "one circuit at a time, tcng_apply_circuit + tcng_energy, "
                                            f"timed over {n_evals} energies and scaled to 2P+1"}
-    res["speedup_vs_param_shift"] = res["n16_b1024"]["evals_per_s"] / res["baseline_param_shift"]["evals_per_s"]
+    res["speedup_vs_param_shift"] = res[f"n16_b{B}"]["evals_per_s"] / res["baseline_param_shift"]["evals_per_s"]
     st.free()
     return res
 
@@ -392,6 +402,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-vqe", action="store_true", help="skip the batched VQE measurement")
+    ap.add_argument("--vqe-only", action="store_true", help="only the n=16 batched VQE (profiling)")
+    ap.add_argument("--vqe-batch", type=int, default=1024, help="VQE batch (profiling only)")
     ap.add_argument("--qubits", type=int, default=N_QUBITS, help="smaller cases for profiling only")
     ap.add_argument("--depth", type=int, default=DEPTH, help="smaller cases for profiling only")
     args = ap.parse_args()
@@ -399,6 +411,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.vqe_only:
+        return run_vqe_only(args)
     return run_gpu(args)
 
 
