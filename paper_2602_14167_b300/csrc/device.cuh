@@ -36,6 +36,7 @@ template <typename C> __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.
 
 // ------------------------------------------------------------- bit helpers --
 __host__ __device__ constexpr int cpopc(int v) { return v ? (v & 1) + cpopc(v >> 1) : 0; }
+__host__ __device__ constexpr int cctz(int v) { return (v & 1) ? 0 : 1 + cctz(v >> 1); }
 // deposit the low bits of v into the set positions of mask (compile-time friendly)
 __host__ __device__ constexpr int cscatter(int v, int mask) {
     int out = 0, b = 0;
@@ -220,16 +221,38 @@ __device__ __forceinline__ int src_bit(uint8_t src, int L, long long gbase) {
     return (src & kSrcBase) ? int((gbase >> (src & 63)) & 1) : ((L >> src) & 1);
 }
 
-// Diagonal op: multiply slot s by M[pext of its qubit bits].
+// Phase-table index of every slot for a diagonal op: the index of slot 0 from its
+// tile offset, then one XOR per slot -- flipping register bit i flips index bit
+// e_i (the source fed by that register bit, from the planner's nibbles).
+template <int R>
+__device__ __forceinline__ void diag_index(const DevOp& op, const int (&L)[1 << R], long long gbase,
+                                           int (&idx)[1 << R]) {
+    int i0 = 0;
+    for (int j = 0; j < op.k; ++j) i0 |= src_bit(op.src[j], L[0], gbase) << j;
+    const int nib = op.mask | (op.pad << 8);
+    int e[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int jj = (i < 4) ? ((nib >> (4 * i)) & 15) : 0;
+        e[i] = jj ? (1 << (jj - 1)) : 0;
+    }
+    idx[0] = i0;
+#pragma unroll
+    for (int s = 1; s < (1 << R); ++s) {
+        const int low = cctz(s);                   // compile-time after unrolling
+        idx[s] = idx[s & (s - 1)] ^ e[low];
+    }
+}
+
+// Diagonal op: multiply slot s by M[idx(s)].
 template <typename C, int R, bool DAG>
 __device__ __forceinline__ void diag_apply(C (&a)[1 << R], const DevOp& op, const C* __restrict__ M,
                                            const int (&L)[1 << R], long long gbase) {
-    const int k = op.k;
+    int idx[1 << R];
+    diag_index<R>(op, L, gbase, idx);
 #pragma unroll
     for (int s = 0; s < (1 << R); ++s) {
-        int idx = 0;
-        for (int j = 0; j < k; ++j) idx |= src_bit(op.src[j], L[s], gbase) << j;
-        C d = M[idx];
+        C d = M[idx[s]];
         if constexpr (DAG) d = cconj(d);
         a[s] = cmul(d, a[s]);
     }

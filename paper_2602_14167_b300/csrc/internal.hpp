@@ -54,10 +54,11 @@ constexpr uint8_t kSrcBase = 0x80;
 struct DevOp {               // 16 bytes
     uint8_t kind;            // OpKind
     uint8_t k;               // qubits
-    uint8_t mask;            // K_DENSE: register-bit mask (popcount k)
+    uint8_t mask;            // K_DENSE: register-bit mask (popcount k); K_DIAG: see pad
     uint8_t grad;            // GradKind (adjoint plans only)
     uint8_t src[5];          // K_DIAG: qubit sources (ascending qubit order)
-    uint8_t pad;
+    uint8_t pad;             // K_DIAG: (pad << 8 | mask) holds one nibble per register bit i:
+                             //   j + 1 if register bit i is source j, else 0
     uint16_t slot;           // adjoint: gradient slot of a parameterised op
     uint32_t mat;            // complex offset inside the pass's matrix window
 };

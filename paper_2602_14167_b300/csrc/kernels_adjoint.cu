@@ -84,16 +84,15 @@ __device__ __forceinline__ typename Real<C>::T grad_part(const DevOp& op, const 
         default: acc = grad_xy<C, R, 4>(is_y, p, l, flip); break;
         }
     } else {
+        int idx[1 << R];
+        diag_index<R>(op, L, gbase, idx);
 #pragma unroll
         for (int s = 0; s < (1 << R); ++s) {
-            const int b0 = src_bit(op.src[0], L[s], gbase);
+            const int b = idx[s];   // bit j = value of source j (ascending qubits)
             T w;
-            if (op.grad == G_Z) {
-                w = b0 ? T(-1) : T(1);
-            } else {
-                const int b1 = src_bit(op.src[1], L[s], gbase);
-                w = (op.grad == G_ZZ) ? ((b0 ^ b1) ? T(-1) : T(1)) : T(b0 & b1);
-            }
+            if (op.grad == G_Z) w = (b & 1) ? T(-1) : T(1);
+            else if (op.grad == G_ZZ) w = (__popc(b & 3) & 1) ? T(-1) : T(1);
+            else w = (b == 3) ? T(1) : T(0);
             acc += w * im_conj_mul(l[s].x, l[s].y, p[s].x, p[s].y);
         }
     }
@@ -296,30 +295,53 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(AdjArgs a) {
             for (long long x = tid; x < Nn; x += nthreads) out[x] = psi[x];
         }
         // ---------------- lambda = H psi, E = Re <psi|lambda> ----------------
+        // Resident: psi is in shared memory.  Streamed: psi is read tile by tile
+        // (2^(res_bits-1) contiguous amplitudes) into shared memory; partners
+        // outside the tile come from global memory.
         double e_part = 0.0;
-        for (long long x = tid; x < N; x += nthreads) {
-            T ar = 0, ai = 0;
-            for (int t = 0; t < S.n_terms; ++t) {
-                const HTerm h = S.terms[t];
-                const long long y = x ^ (long long)h.xm;
-                const C v = psi[y];
-                const T c = (T)coeff[t];
-                const int sg = __popcll((unsigned long long)y & h.zm) & 1;
-                T vr = v.x, vi = v.y, tr;
-                switch (h.ny & 3) {
-                case 1: tr = -vi; vi = vr; vr = tr; break;
-                case 2: vr = -vr; vi = -vi; break;
-                case 3: tr = vi; vi = -vr; vr = tr; break;
-                default: break;
+        {
+            const int tb = resident ? n : a.res_bits - 1;
+            const long long tn = 1ll << tb;
+            const long long ntile = resident ? 1 : (N >> tb);
+            for (long long t = 0; t < ntile; ++t) {
+                if (!resident) {
+                    if (tid == 0) {
+                        mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(C) * tn));
+                        bulk_g2s(sp, gp + t * tn, (uint32_t)(sizeof(C) * tn), bar);
+                    }
+                    if (!mbar_wait_bounded(bar, phase, a.err)) s_abort = 1;
+                    phase ^= 1u;
+                    __syncthreads();
+                    if (s_abort) break;
                 }
-                if (sg) { vr = -vr; vi = -vi; }
-                ar += c * vr;
-                ai += c * vi;
+                for (long long xl = tid; xl < tn; xl += nthreads) {
+                    const long long x = t * tn + xl;
+                    T ar = 0, ai = 0;
+                    for (int q = 0; q < S.n_terms; ++q) {
+                        const HTerm h = S.terms[q];
+                        const long long y = x ^ (long long)h.xm;
+                        const C v = ((y >> tb) == t) ? sp[y & (tn - 1)] : psi[y];
+                        const T c = (T)coeff[q];
+                        const int sg = __popcll((unsigned long long)y & h.zm) & 1;
+                        T vr = v.x, vi = v.y, tr;
+                        switch (h.ny & 3) {
+                        case 1: tr = -vi; vi = vr; vr = tr; break;
+                        case 2: vr = -vr; vi = -vi; break;
+                        case 3: tr = vi; vi = -vr; vr = tr; break;
+                        default: break;
+                        }
+                        if (sg) { vr = -vr; vi = -vi; }
+                        ar += c * vr;
+                        ai += c * vi;
+                    }
+                    lam[x] = cmk<C>(ar, ai);
+                    const C p = sp[xl];
+                    e_part += (double)(p.x * ar + p.y * ai);
+                }
+                __syncthreads();   // tile buffer reused by the next load
             }
-            lam[x] = cmk<C>(ar, ai);
-            const C p = psi[x];
-            e_part += (double)(p.x * ar + p.y * ai);
         }
+        if (s_abort) break;
         fence_proxy_async_all();   // generic writes of lambda before bulk copies read it
         {
             double v = warp_sum(e_part);

@@ -366,12 +366,19 @@ void build_plan(Plan& plan) {
                     uint64_t qm = blk.qmask;
                     if (blk.diag) {
                         d.kind = K_DIAG;
+                        uint16_t nib = 0;
                         while (qm) {
                             int q = __builtin_ctzll(qm);
                             qm &= qm - 1;
-                            d.src[j++] = (tb_of_q[q] >= 0) ? (uint8_t)tb_of_q[q]
-                                                           : (uint8_t)(kSrcBase | q);
+                            d.src[j] = (tb_of_q[q] >= 0) ? (uint8_t)tb_of_q[q]
+                                                         : (uint8_t)(kSrcBase | q);
+                            if (tb_of_q[q] >= 0 && reg_of_tb[tb_of_q[q]] >= 0 &&
+                                reg_of_tb[tb_of_q[q]] < kRegBits)
+                                nib |= (uint16_t)((j + 1) << (4 * reg_of_tb[tb_of_q[q]]));
+                            ++j;
                         }
+                        d.mask = (uint8_t)(nib & 0xFF);
+                        d.pad = (uint8_t)(nib >> 8);
                     } else {
                         d.kind = K_DENSE;
                         while (qm) {
