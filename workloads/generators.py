@@ -275,17 +275,6 @@ def chain_terms(chain) -> np.ndarray:
     return xxz_terms(chain["n"], chain["J"], chain["delta"], chain["g"])
 
 
-def chain_features(chain, n_max: int = 20) -> np.ndarray:
-    """[J_1..J_{n_max-1} zero-padded, delta, g, n/n_max, one-hot kind] (24 for n_max 20)."""
-    f = np.zeros(n_max - 1 + 5, dtype=np.float64)
-    f[: chain["n"] - 1] = chain["J"]
-    f[n_max - 1] = chain["delta"] if chain["kind"] == 1 else 0.0
-    f[n_max] = chain["g"]
-    f[n_max + 1] = chain["n"] / n_max
-    f[n_max + 2 + chain["kind"]] = 1.0
-    return f
-
-
 def random_thetas(shape, seed: int = 0) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return rng.uniform(-math.pi, math.pi, size=shape)
