@@ -5,9 +5,6 @@ using namespace tcng;
 
 extern "C" {
 
-tcng_status tcng_apply_shared_unitary(tcng_state*, const int*, int, const double*, void*) {
-    return fail(TCNG_EUNSUPPORTED, "tcng_apply_shared_unitary is not built yet");
-}
 tcng_status tcng_autotune(int, tcng_dtype, int, const char*) {
     return fail(TCNG_EUNSUPPORTED, "tcng_autotune is not built yet");
 }
