@@ -178,6 +178,10 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     NQ, DP = args.qubits, args.depth
+    for opt, val in ((T.OPT_FUSE_WIDTH, args.fuse_width), (T.OPT_TILE_BITS, args.tile_bits),
+                     (T.OPT_CHUNK_BITS, args.chunk_bits)):
+        if val:
+            T.tcng_set_option(opt, val)
     c, gates, pool, theta, strings, tfim = workload(NQ, DP)
     st = StateBatch(NQ, dtype="c64", device=dev)
     S = 8 * (1 << NQ)
@@ -264,6 +268,9 @@ def run_gpu(args):
                       "qubits": N_QUBITS, "depth": DEPTH, "state_GiB": S / 2**30,
                       "tile_passes_per_step": n_pass, "expect_passes_per_step": n_exp,
                       "step_bytes_GB": step_bytes / 1e9,
+                      "fuse_width": T.tcng_get_option(T.OPT_FUSE_WIDTH),
+                      "tile_bits": T.tcng_get_option(T.OPT_TILE_BITS),
+                      "chunk_bits": T.tcng_get_option(T.OPT_CHUNK_BITS),
                       "ms_per_layer": ms_step / DP,
                       "l2": "inputs larger than L2 (32 GiB state), no flush",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -403,6 +410,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-vqe", action="store_true", help="skip the batched VQE measurement")
     ap.add_argument("--vqe-only", action="store_true", help="only the n=16 batched VQE (profiling)")
+    ap.add_argument("--fuse-width", type=int, default=0, help="override the fusion width (tuning)")
+    ap.add_argument("--tile-bits", type=int, default=0, help="override the tile bits (tuning)")
+    ap.add_argument("--chunk-bits", type=int, default=0, help="override the chunk bits (tuning)")
     ap.add_argument("--vqe-batch", type=int, default=1024, help="VQE batch (profiling only)")
     ap.add_argument("--qubits", type=int, default=N_QUBITS, help="smaller cases for profiling only")
     ap.add_argument("--depth", type=int, default=DEPTH, help="smaller cases for profiling only")

@@ -5,8 +5,4 @@ using namespace tcng;
 
 extern "C" {
 
-tcng_status tcng_autotune(int, tcng_dtype, int, const char*) {
-    return fail(TCNG_EUNSUPPORTED, "tcng_autotune is not built yet");
-}
-
 }  // extern "C"

@@ -93,3 +93,23 @@ def test_graph_and_eager_runs_agree(T):
     t2, _ = vb.optimize(b["theta"], steps=20, lr=0.03, use_graph=True)
     torch.cuda.synchronize()
     assert torch.equal(t1, t2)
+
+
+def test_autotune_sets_options_and_caches(T, tmp_path):
+    cache = str(tmp_path / "tune.txt")
+    saved = {o: T.tcng_get_option(o) for o in range(5)}
+    try:
+        T.tcng_autotune(18, T.C64, 1, cache)
+        fw, tb, cb = (T.tcng_get_option(o) for o in (T.OPT_FUSE_WIDTH, T.OPT_TILE_BITS, T.OPT_CHUNK_BITS))
+        assert 1 <= fw <= 3 and 11 <= tb <= 13 and 5 <= cb <= 8
+        line = open(cache).read().split()
+        assert [int(v) for v in line[:6]] == [18, 0, 1, fw, tb, cb]
+        # a second call loads the entry instead of timing
+        for o, v in saved.items():
+            T.tcng_set_option(o, v)
+        T.tcng_autotune(18, T.C64, 1, cache)
+        assert T.tcng_get_option(T.OPT_TILE_BITS) == tb
+        assert len(open(cache).read().splitlines()) == 1
+    finally:
+        for o, v in saved.items():
+            T.tcng_set_option(o, v)
