@@ -408,42 +408,30 @@ __global__ void __launch_bounds__(512) expect_pass_kernel(const C* __restrict__ 
         __syncthreads();
         if (s_abort) break;
         const long long gbase = tile_global_base(p, t % tc.tiles_per_item);
-        // per-term sign of the tile base and per-thread FP32 partials for this tile
-        R part[kExpTermsPerPass];
-        int sgn0[kExpTermsPerPass];
 #pragma unroll
         for (int j = 0; j < kExpTermsPerPass; ++j) {
-            part[j] = 0;
-            sgn0[j] = j < ep.nterms ? (__popcll((unsigned long long)gbase & ep.t[j].zm_glob) & 1) : 0;
-        }
-        for (int L = tid; L < tile_elems; L += blockDim.x) {
-            const C a = buf[L];
-            const R pa = a.x * a.x + a.y * a.y;
-#pragma unroll
-            for (int j = 0; j < kExpTermsPerPass; ++j) {
-                if (j < ep.nterms) {
-                    const ExpTerm& T = ep.t[j];
-                    const int sg = (__popc((unsigned)L & T.zm_tile) + sgn0[j]) & 1;
+            if (j < ep.nterms) {
+                const ExpTerm& T = ep.t[j];
+                const int sgn0 = __popcll((unsigned long long)gbase & T.zm_glob) & 1;
+                R part = 0;
+                for (int L = tid; L < tile_elems; L += blockDim.x) {
+                    const C a = buf[L];
+                    const C bb = buf[L ^ (int)T.xm_tile];
+                    const R wr = bb.x * a.x + bb.y * a.y;   // conj(b) * a
+                    const R wi = bb.x * a.y - bb.y * a.x;
                     R v;
-                    if (T.xm_tile == 0) {
-                        v = pa;                      // Z-only string: |psi_x|^2
-                    } else {
-                        const C bb = buf[L ^ (int)T.xm_tile];
-                        const R wr = bb.x * a.x + bb.y * a.y;   // conj(b) * a
-                        const R wi = bb.x * a.y - bb.y * a.x;
-                        switch (T.ny & 3) {
-                        case 0: v = wr; break;
-                        case 1: v = -wi; break;
-                        case 2: v = -wr; break;
-                        default: v = wi; break;
-                        }
+                    switch (T.ny & 3) {
+                    case 0: v = wr; break;
+                    case 1: v = -wi; break;
+                    case 2: v = -wr; break;
+                    default: v = wi; break;
                     }
-                    part[j] += sg ? -v : v;
+                    const int sg = (__popc((unsigned)L & T.zm_tile) + sgn0) & 1;
+                    part += sg ? -v : v;
                 }
+                acc[j] += (double)part;
             }
         }
-#pragma unroll
-        for (int j = 0; j < kExpTermsPerPass; ++j) acc[j] += (double)part[j];
         __syncthreads();  // everyone done reading buf before it is refilled
         if (warp == 0) {
             const long long tn = t + (long long)tc.nbuf * stride;
