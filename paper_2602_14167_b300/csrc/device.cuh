@@ -269,11 +269,11 @@ __device__ __forceinline__ int insert_zero_bits(int g, const uint8_t* rbit) {
     return g;
 }
 
-// Tile offsets of the 2^R slots of group g in a stage with register bits rbit.
+// Tile offsets of the 2^R slots of group g in a stage with register bits rbit
+// (slot s holds offset base | scatter(s ^ tau)).
 template <int R>
-__device__ __forceinline__ void group_offsets(int g, const uint8_t* rbit, int (&L)[1 << R]) {
+__device__ __forceinline__ void group_offsets(int g, int tau, const uint8_t* rbit, int (&L)[1 << R]) {
     const int base = insert_zero_bits<R>(g, rbit);
-    const int tau = g & ((1 << R) - 1);
     int sr[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) sr[i] = 1 << rbit[i];
@@ -290,13 +290,16 @@ __device__ __forceinline__ void group_offsets(int g, const uint8_t* rbit, int (&
 }
 
 // Stage executor: one group (2^R amplitudes) of one tile, forward direction.
-template <typename C, int R>
+// ROT: XOR-rotate the slots by the group index (only needed when the register
+// bits include a bank-selecting tile bit); without it every thread reads the
+// same matrix entries (shared-memory broadcast, compile-time indices).
+template <typename C, int R, bool ROT>
 __device__ __forceinline__ void run_stage_group(C* __restrict__ buf, const DevStage& st,
                                                 const DevOp* __restrict__ ops, const C* __restrict__ mats,
                                                 int g, long long gbase) {
     int L[1 << R];
-    group_offsets<R>(g, st.rbit, L);
-    const int tau = g & ((1 << R) - 1);
+    const int tau = ROT ? (g & ((1 << R) - 1)) : 0;
+    group_offsets<R>(g, tau, st.rbit, L);
     C a[1 << R];
 #pragma unroll
     for (int s = 0; s < (1 << R); ++s) a[s] = buf[L[s]];
@@ -371,10 +374,14 @@ __device__ __forceinline__ void run_stage(C* __restrict__ buf, const DevStage& s
                                           int tile_bits, long long gbase) {
     if (st.nreg > kRegBits) {
         run_stage_smem<C, false>(buf, st, ops, mats, tile_bits, gbase);
+    } else if (st.rotate) {
+        const int ngroups = 1 << (tile_bits - kRegBits);
+        for (int g = threadIdx.x; g < ngroups; g += blockDim.x)
+            run_stage_group<C, kRegBits, true>(buf, st, ops, mats, g, gbase);
     } else {
         const int ngroups = 1 << (tile_bits - kRegBits);
         for (int g = threadIdx.x; g < ngroups; g += blockDim.x)
-            run_stage_group<C, kRegBits>(buf, st, ops, mats, g, gbase);
+            run_stage_group<C, kRegBits, false>(buf, st, ops, mats, g, gbase);
     }
 }
 

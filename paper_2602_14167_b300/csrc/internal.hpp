@@ -67,7 +67,8 @@ static_assert(sizeof(DevOp) == 16, "DevOp layout");
 struct DevStage {            // 20 bytes
     uint8_t rbit[kMaxRegBits];  // tile bit of register bit i (ascending)
     uint8_t nreg;            // R: 4, or 5 for a stage holding a 5-qubit block
-    uint8_t pad[2];
+    uint8_t rotate;          // 1: slots XOR-rotated per group (register bits include tile bits 0..3)
+    uint8_t pad;
     uint32_t op_begin;
     uint32_t op_count;
     uint32_t n_grad;         // adjoint: parameterised ops in this stage

@@ -113,9 +113,9 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
         const bool active = g < ngroups;
         int L[1 << R];
         C p[1 << R], l[1 << R];
-        const int tau = g & ((1 << R) - 1);
+        const int tau = st.rotate ? (g & ((1 << R) - 1)) : 0;
         if (active) {
-            group_offsets<R>(g, st.rbit, L);
+            group_offsets<R>(g, tau, st.rbit, L);
 #pragma unroll
             for (int s = 0; s < (1 << R); ++s) {
                 p[s] = pbuf[L[s]];

@@ -344,6 +344,9 @@ void build_plan(Plan& plan) {
                 for (int tb = dp.m - 1; tb >= 0 && __builtin_popcount(Rset) < Rcap; --tb)
                     Rset |= 1u << tb;
                 st.nreg = (uint8_t)Rcap;
+                // shared-memory banks are picked by tile bits 0..3 (8-byte amplitudes): only then
+                // do the slots need the per-group XOR rotation
+                st.rotate = (Rset & 0xFu) ? 1 : 0;
                 int ri = 0;
                 int reg_of_tb[kMaxTileBits + 2];
                 for (int tb = 0; tb < dp.m; ++tb) {
