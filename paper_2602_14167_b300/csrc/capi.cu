@@ -207,7 +207,7 @@ void* plan_table(DevPlan* dp, size_t elem, int items) {
 // Run a plan on a group of items (all with n == plan.n).
 template <typename C>
 tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int items,
-                     const double* params, cudaStream_t s) {
+                     const double* params, cudaStream_t s, void* tma_base, long long item_stride) {
     Plan& pl = dp->plan;
     const int tab_items = pl.P > 0 ? items : 1;
     C* table = static_cast<C*>(plan_table(dp, sizeof(C), tab_items));
@@ -229,16 +229,34 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
         }
     } else {
         for (const DevPass& p : pl.passes) {
+            TmaTile tma{};
+            if (tma_base && (items == 1 || item_stride > 0))
+                tma = make_tma_tile(tma_base, pl.n, (int)sizeof(C), p, items, item_stride);
             ProfScope ps(sizeof(C) == 8 ? "pass_kernel_c64" : "pass_kernel_c128", s);
             e = launch_pass<C>(state, d_item_off, items, pl.n, p, pl.stages.data(), dp->d_stages,
-                               dp->d_dops, table, stride, ctx().err, s);
+                               dp->d_dops, table, stride, ctx().err, s, &tma);
             if (e != cudaSuccess) return cuda_fail(e, "pass kernel");
         }
     }
     return TCNG_OK;
 }
-template tcng_status run_plan<float2>(DevPlan*, float2*, const long long*, int, const double*, cudaStream_t);
-template tcng_status run_plan<double2>(DevPlan*, double2*, const long long*, int, const double*, cudaStream_t);
+template tcng_status run_plan<float2>(DevPlan*, float2*, const long long*, int, const double*, cudaStream_t,
+                                      void*, long long);
+template tcng_status run_plan<double2>(DevPlan*, double2*, const long long*, int, const double*, cudaStream_t,
+                                       void*, long long);
+
+// Device address of a group's first item and the spacing of its items in bytes
+// (-1 if they are not equally spaced).
+static void group_span(const tcng_state* st, const std::vector<int>& items, void** base, long long* stride) {
+    const size_t es = st->dt == TCNG_C64 ? 8 : 16;
+    *base = static_cast<char*>(st->buf) + st->off[items[0]] * es;
+    *stride = items.size() > 1 ? (long long)((st->off[items[1]] - st->off[items[0]]) * es) : 0;
+    for (size_t i = 1; i < items.size(); ++i)
+        if ((long long)((st->off[items[i]] - st->off[items[0]]) * es) != (long long)i * *stride) {
+            *stride = -1;
+            return;
+        }
+}
 
 // Group Pauli terms into tile passes: a term joins a pass if its X bits above
 // the contiguous low bits fit the pass's gather set.
@@ -460,11 +478,14 @@ tcng_status tcng_apply_circuit(tcng_state* st, const tcng_gate* ops, size_t n_op
                                     "ragged batch with parameters needs items of equal n to be contiguous");
                 prm += (size_t)it[0] * P;
             }
+            void* tb = nullptr;
+            long long ts = -1;
+            group_span(st, kv.second.items, &tb, &ts);
             tcng_status r;
             if (st->dt == TCNG_C64)
-                r = run_plan<float2>(dp, static_cast<float2*>(st->buf), kv.second.d_off, items, prm, s);
+                r = run_plan<float2>(dp, static_cast<float2*>(st->buf), kv.second.d_off, items, prm, s, tb, ts);
             else
-                r = run_plan<double2>(dp, static_cast<double2*>(st->buf), kv.second.d_off, items, prm, s);
+                r = run_plan<double2>(dp, static_cast<double2*>(st->buf), kv.second.d_off, items, prm, s, tb, ts);
             if (r) return r;
         }
         return TCNG_OK;
@@ -498,15 +519,21 @@ static tcng_status expect_impl(const tcng_state* st, const tcng_pauli* terms, si
         double* partial = static_cast<double*>(
             c.scratch("exp_partial", sizeof(double) * (size_t)items * n_terms * nblk));
         if (!partial) return fail(TCNG_ENOMEM, "expectation scratch");
+        void* tb = nullptr;
+        long long tstride = -1;
+        group_span(st, st->groups.begin()->second.items, &tb, &tstride);
         for (size_t i = 0; i < passes.size(); ++i) {
             cudaError_t e;
+            TmaTile tma{};
+            if (items == 1 || tstride > 0)
+                tma = make_tma_tile(tb, n, st->dt == TCNG_C64 ? 8 : 16, passes[i], items, tstride);
             ProfScope ps(st->dt == TCNG_C64 ? "expect_pass_c64" : "expect_pass_c128", s);
             if (st->dt == TCNG_C64)
                 e = launch_expect_pass<float2>(static_cast<const float2*>(st->buf), st->d_off, items, n,
-                                               passes[i], eps[i], partial, (int)n_terms, nblk, c.err, s);
+                                               passes[i], eps[i], partial, (int)n_terms, nblk, c.err, s, &tma);
             else
                 e = launch_expect_pass<double2>(static_cast<const double2*>(st->buf), st->d_off, items, n,
-                                                passes[i], eps[i], partial, (int)n_terms, nblk, c.err, s);
+                                                passes[i], eps[i], partial, (int)n_terms, nblk, c.err, s, &tma);
             if (e != cudaSuccess) return cuda_fail(e, "expectation pass");
         }
         ProfScope ps("expect_finalize", s);

@@ -97,9 +97,12 @@ void* plan_table(DevPlan* dp, size_t elem, int items);
 TermSet* get_terms(const tcng_pauli* terms, size_t n_terms, int n);
 void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
                       std::vector<DevPass>& passes, std::vector<ExpPass>& eps);
+// tma_base: device address of the group's first item and item_stride its spacing
+// in bytes (< 0: items not equally spaced -> per-chunk bulk copies).
 template <typename C>
 tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int items,
-                     const double* params, cudaStream_t s);
+                     const double* params, cudaStream_t s, void* tma_base = nullptr,
+                     long long item_stride = -1);
 
 // Synchronous upload of a host vector (used once per structure); throws bad_alloc.
 template <typename T>

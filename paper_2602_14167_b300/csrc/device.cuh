@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "internal.hpp"
+#include "launch.hpp"
 
 namespace tcng {
 
@@ -118,6 +119,72 @@ template <int N> __device__ __forceinline__ void bulk_wait_read() {
 }
 template <int N> __device__ __forceinline__ void bulk_wait() {
     asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// --------------------------------------------------- TMA tensor copies --
+// One multi-dimensional tensor copy of a whole tile (see TmaTile).
+__device__ __forceinline__ void tma_tile_coords(const TmaTile& t, long long tile_local, int item,
+                                                int (&c)[5]) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        c[i] = 0;
+        if (i < t.rank) {
+            if (t.kind[i] == 1) c[i] = (int)((tile_local >> t.shift[i]) & ((1ll << t.len[i]) - 1));
+            else if (t.kind[i] == 2) c[i] = item;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_tile(const TmaTile& t, void* dst, uint64_t* bar, const int (&c)[5]) {
+    const uint64_t map = reinterpret_cast<uint64_t>(&t.map);
+    const uint32_t d = smem_u32(dst), b = smem_u32(bar);
+    switch (t.rank) {
+    case 1:
+        asm volatile("cp.async.bulk.tensor.1d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2}], [%3];"
+                     ::"r"(d), "l"(map), "r"(c[0]), "r"(b) : "memory");
+        break;
+    case 2:
+        asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                     ::"r"(d), "l"(map), "r"(c[0]), "r"(c[1]), "r"(b) : "memory");
+        break;
+    case 3:
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                     ::"r"(d), "l"(map), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(b) : "memory");
+        break;
+    case 4:
+        asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                     ::"r"(d), "l"(map), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(b) : "memory");
+        break;
+    default:
+        asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+                     ::"r"(d), "l"(map), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(b) : "memory");
+        break;
+    }
+}
+__device__ __forceinline__ void tma_store_tile(const TmaTile& t, const void* src, const int (&c)[5]) {
+    const uint64_t map = reinterpret_cast<uint64_t>(&t.map);
+    const uint32_t sp = smem_u32(src);
+    switch (t.rank) {
+    case 1:
+        asm volatile("cp.async.bulk.tensor.1d.global.shared::cta.tile.bulk_group [%0, {%1}], [%2];"
+                     ::"l"(map), "r"(c[0]), "r"(sp) : "memory");
+        break;
+    case 2:
+        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];"
+                     ::"l"(map), "r"(c[0]), "r"(c[1]), "r"(sp) : "memory");
+        break;
+    case 3:
+        asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];"
+                     ::"l"(map), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(sp) : "memory");
+        break;
+    case 4:
+        asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];"
+                     ::"l"(map), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(sp) : "memory");
+        break;
+    default:
+        asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];"
+                     ::"l"(map), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(sp) : "memory");
+        break;
+    }
 }
 
 // ---------------------------------------------------- tile index mapping --

@@ -273,8 +273,17 @@ struct TileCtx {
 template <typename C>
 __device__ __forceinline__ void issue_tile_load(const C* state, const long long* item_off,
                                                 const DevPass& p, const TileCtx& tc, long long tile,
-                                                C* buf, uint64_t* bar, int lane) {
+                                                C* buf, uint64_t* bar, int lane, const TmaTile& tma) {
     const long long item = tile / tc.tiles_per_item;
+    if (tma.rank) {   // one tensor copy for the whole tile
+        if (lane == 0) {
+            int c[5];
+            tma_tile_coords(tma, tile % tc.tiles_per_item, (int)item, c);
+            mbar_arrive_expect_tx(bar, tc.tile_bytes);
+            tma_load_tile(tma, buf, bar, c);
+        }
+        return;
+    }
     const long long base = tile_global_base(p, tile % tc.tiles_per_item);
     const C* src = state + item_off[item] + base;
     if (lane == 0) mbar_arrive_expect_tx(bar, tc.tile_bytes);
@@ -286,8 +295,17 @@ __device__ __forceinline__ void issue_tile_load(const C* state, const long long*
 template <typename C>
 __device__ __forceinline__ void issue_tile_store(C* state, const long long* item_off, const DevPass& p,
                                                  const TileCtx& tc, long long tile, const C* buf,
-                                                 int lane) {
+                                                 int lane, const TmaTile& tma) {
     const long long item = tile / tc.tiles_per_item;
+    if (tma.rank) {
+        if (lane == 0) {
+            int c[5];
+            tma_tile_coords(tma, tile % tc.tiles_per_item, (int)item, c);
+            tma_store_tile(tma, buf, c);
+        }
+        bulk_commit();
+        return;
+    }
     const long long base = tile_global_base(p, tile % tc.tiles_per_item);
     C* dst = state + item_off[item] + base;
     for (int j = lane; j < tc.nchunks; j += 32)
@@ -303,10 +321,11 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
                                                     const DevOp* __restrict__ ops,
                                                     const C* __restrict__ table,
                                                     long long table_stride, TileCtx tc,
-                                                    unsigned* __restrict__ err) {
+                                                    unsigned* __restrict__ err,
+                                                    const __grid_constant__ TmaTile tma) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile_elems = 1 << p.m;
-    C* bufs = reinterpret_cast<C*>(smem_raw);
+    C* bufs = reinterpret_cast<C*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     C* mats = bufs + (long long)tc.nbuf * tile_elems;
     uint64_t* bars = reinterpret_cast<uint64_t*>(mats + ((p.mat_count + 1) & ~1));
     __shared__ int s_abort;
@@ -323,7 +342,7 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
         for (int i = 0; i < tc.nbuf - 1; ++i) {
             const long long t = first + i * stride;
             if (t < tc.total_tiles)
-                issue_tile_load(state, item_off, p, tc, t, bufs + (long long)i * tile_elems, &bars[i], lane);
+                issue_tile_load(state, item_off, p, tc, t, bufs + (long long)i * tile_elems, &bars[i], lane, tma);
         }
     long long cur_item = -1;
     int it = 0;
@@ -349,13 +368,13 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
         fence_proxy_async_smem();
         __syncthreads();
         if (warp == 0) {
-            issue_tile_store(state, item_off, p, tc, t, buf, lane);
+            issue_tile_store(state, item_off, p, tc, t, buf, lane, tma);
             const long long tn = t + (long long)(tc.nbuf - 1) * stride;
             if (tn < tc.total_tiles) {
                 const int bn = (it + tc.nbuf - 1) % tc.nbuf;
                 bulk_wait_read<1>();
                 __syncwarp();
-                issue_tile_load(state, item_off, p, tc, tn, bufs + (long long)bn * tile_elems, &bars[bn], lane);
+                issue_tile_load(state, item_off, p, tc, tn, bufs + (long long)bn * tile_elems, &bars[bn], lane, tma);
             }
         }
     }
@@ -371,11 +390,12 @@ __global__ void __launch_bounds__(512) expect_pass_kernel(const C* __restrict__ 
                                                           const __grid_constant__ DevPass p,
                                                           const __grid_constant__ ExpPass ep,
                                                           TileCtx tc, double* __restrict__ partial,
-                                                          int n_out, unsigned* __restrict__ err) {
+                                                          int n_out, unsigned* __restrict__ err,
+                                                          const __grid_constant__ TmaTile tma) {
     using R = typename Real<C>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile_elems = 1 << p.m;
-    C* bufs = reinterpret_cast<C*>(smem_raw);
+    C* bufs = reinterpret_cast<C*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     uint64_t* bars = reinterpret_cast<uint64_t*>(bufs + (long long)tc.nbuf * tile_elems);
     __shared__ double red[32][kExpTermsPerPass];
     __shared__ int s_abort;
@@ -394,7 +414,7 @@ __global__ void __launch_bounds__(512) expect_pass_kernel(const C* __restrict__ 
     if (warp == 0)
         for (int i = 0; i < tc.nbuf; ++i) {
             const long long t = first + i * stride;
-            if (t < t1) issue_tile_load(state, item_off, p, tc, t, bufs + (long long)i * tile_elems, &bars[i], lane);
+            if (t < t1) issue_tile_load(state, item_off, p, tc, t, bufs + (long long)i * tile_elems, &bars[i], lane, tma);
         }
     double acc[kExpTermsPerPass];
 #pragma unroll
@@ -436,7 +456,7 @@ __global__ void __launch_bounds__(512) expect_pass_kernel(const C* __restrict__ 
         if (warp == 0) {
             const long long tn = t + (long long)tc.nbuf * stride;
             if (tn < t1) issue_tile_load(state, item_off, p, tc, tn, bufs + (long long)b * tile_elems,
-                                         &bars[b], lane);
+                                         &bars[b], lane, tma);
         }
     }
     // deterministic block reduction: warp tree, then warps in order
@@ -620,7 +640,7 @@ static TileCtx make_ctx(const DevPass& p, int n, int items, int elem_bytes, int 
 
 template <typename C>
 static size_t pass_smem_bytes(const DevPass& p, int nbuf) {
-    return (size_t)nbuf * (sizeof(C) << p.m) + sizeof(C) * ((p.mat_count + 1) & ~1) +
+    return 128 + (size_t)nbuf * (sizeof(C) << p.m) + sizeof(C) * ((p.mat_count + 1) & ~1) +
            8 * (size_t)nbuf;
 }
 
@@ -649,7 +669,8 @@ static size_t dyn_smem_limit(K kernel, bool* done, size_t* cached) {
 template <typename C>
 cudaError_t launch_pass(C* state, const long long* item_off, int items, int n, const DevPass& p,
                         const DevStage* host_stages, const DevStage* stages, const DevOp* ops,
-                        const C* table, long long table_stride, unsigned* err, cudaStream_t s) {
+                        const C* table, long long table_stride, unsigned* err, cudaStream_t s,
+                        const TmaTile* tma) {
     const int nbuf = 3;
     const size_t smem = pass_smem_bytes<C>(p, nbuf);
     (void)host_stages;
@@ -663,8 +684,9 @@ cudaError_t launch_pass(C* state, const long long* item_off, int items, int n, c
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (per_sm < 1) per_sm = 1;
     long long grid = std::min<long long>(tc.total_tiles, (long long)num_sms() * per_sm);
+    const TmaTile t0{};
     kern<<<(unsigned)grid, threads, smem, s>>>(state, item_off, p, stages, ops, table, table_stride,
-                                               tc, err);
+                                               tc, err, tma ? *tma : t0);
     count_launch();
     return cudaGetLastError();
 }
@@ -672,16 +694,18 @@ cudaError_t launch_pass(C* state, const long long* item_off, int items, int n, c
 template <typename C>
 cudaError_t launch_expect_pass(const C* state, const long long* item_off, int items, int n,
                                const DevPass& p, const ExpPass& ep, double* partial, int n_out,
-                               int nblk, unsigned* err, cudaStream_t s) {
+                               int nblk, unsigned* err, cudaStream_t s, const TmaTile* tma) {
     const int nbuf = 2;
-    const size_t smem = (size_t)nbuf * (sizeof(C) << p.m) + 8 * nbuf;
+    const size_t smem = 128 + (size_t)nbuf * (sizeof(C) << p.m) + 8 * nbuf;
     static bool done = false;
     static size_t lim = 0;
     if (smem > dyn_smem_limit(expect_pass_kernel<C>, &done, &lim)) return cudaErrorInvalidConfiguration;
     TileCtx tc = make_ctx(p, n, items, sizeof(C), nbuf);
     const int threads = std::min(512, std::max(32, 1 << p.m));
     dim3 grid((unsigned)nblk, (unsigned)items);
-    expect_pass_kernel<C><<<grid, threads, smem, s>>>(state, item_off, p, ep, tc, partial, n_out, err);
+    const TmaTile t0{};
+    expect_pass_kernel<C><<<grid, threads, smem, s>>>(state, item_off, p, ep, tc, partial, n_out, err,
+                                                      tma ? *tma : t0);
     count_launch();
     return cudaGetLastError();
 }
@@ -719,10 +743,10 @@ cudaError_t launch_ham_apply(const C* psi, const long long* off_in, C* out, cons
                                         long long, cudaStream_t);                                     \
     template cudaError_t launch_pass<C>(C*, const long long*, int, int, const DevPass&,               \
                                         const DevStage*, const DevStage*, const DevOp*, const C*,     \
-                                        long long, unsigned*, cudaStream_t);                          \
+                                        long long, unsigned*, cudaStream_t, const TmaTile*);          \
     template cudaError_t launch_expect_pass<C>(const C*, const long long*, int, int, const DevPass&,  \
                                                const ExpPass&, double*, int, int, unsigned*,          \
-                                               cudaStream_t);                                         \
+                                               cudaStream_t, const TmaTile*);                         \
     template cudaError_t launch_ham_apply<C>(const C*, const long long*, C*, const long long*, int,   \
                                              int, const HTerm*, int, const double*, const double*,    \
                                              cudaStream_t);

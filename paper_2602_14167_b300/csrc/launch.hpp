@@ -1,6 +1,7 @@
 // Kernel launchers (defined in the .cu files, called by the C ABI layer).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "internal.hpp"
@@ -22,6 +23,23 @@ struct ExpPass {
     int nterms;
     ExpTerm t[kExpTermsPerPass];
 };
+// One multi-dimensional TMA tensor copy per tile: the n index bits split into
+// runs; tile runs are box dimensions (<= 256 elements), rest runs and the item
+// index are box-1 dimensions addressed by coordinates.
+struct alignas(64) TmaTile {
+    CUtensorMap map;
+    int32_t rank;              // 0: not usable (fall back to per-chunk bulk copies)
+    int8_t kind[5];            // 0 tile run (coordinate 0), 1 rest run, 2 item
+    int8_t shift[5];           // rest run: first bit of the tile number it takes
+    int8_t len[5];             // rest run: number of bits
+    int8_t pad;
+};
+
+// Build the tensor map of a pass (returns rank 0 if the pass needs > 5 dims or
+// the encoder rejects it).  items > 1 needs equally spaced items (stride bytes).
+TmaTile make_tma_tile(void* base, int n, int elem_bytes, const DevPass& p, int items,
+                      long long item_stride_bytes);
+
 struct HTerm {
     uint64_t xm, zm;
     int32_t ny;
@@ -45,11 +63,12 @@ cudaError_t launch_gate(C* state, const long long* item_off, int items, int n, c
 template <typename C>
 cudaError_t launch_pass(C* state, const long long* item_off, int items, int n, const DevPass& p,
                         const DevStage* host_stages, const DevStage* stages, const DevOp* ops,
-                        const C* table, long long table_stride, unsigned* err, cudaStream_t s);
+                        const C* table, long long table_stride, unsigned* err, cudaStream_t s,
+                        const TmaTile* tma = nullptr);
 template <typename C>
 cudaError_t launch_expect_pass(const C* state, const long long* item_off, int items, int n,
                                const DevPass& p, const ExpPass& ep, double* partial, int n_out,
-                               int nblk, unsigned* err, cudaStream_t s);
+                               int nblk, unsigned* err, cudaStream_t s, const TmaTile* tma = nullptr);
 cudaError_t launch_expect_finalize(const double* partial, int nblk, int n_out, double* out,
                                    const double* coeffs, const double* term_coeff, double* energy,
                                    int items, cudaStream_t s);

@@ -1,0 +1,91 @@
+// Host side of the tile tensor maps (cuTensorMapEncodeTiled through the
+// runtime's driver entry point, so the library needs no libcuda link).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "launch.hpp"
+
+namespace tcng {
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+TmaTile make_tma_tile(void* base, int n, int elem_bytes, const DevPass& p, int items,
+                      long long item_stride_bytes) {
+    TmaTile t;
+    std::memset(&t, 0, sizeof t);
+    auto fn = encode_fn();
+    if (!fn) return t;
+    // membership of each index bit in the tile
+    std::vector<int> in_tile(n, 0);
+    for (int q = 0; q < p.chunk; ++q) in_tile[q] = 1;
+    for (int i = 0; i < p.ngather; ++i) in_tile[p.gather[i]] = 1;
+    const int e = elem_bytes / 8;          // 8-byte elements per amplitude
+    cuuint64_t gdim[5], gstride[5];
+    cuuint32_t box[5], estr[5];
+    int rank = 0, rest_seen = 0;
+    for (int q = 0; q < n;) {
+        const int tile = in_tile[q];
+        int len = 1;
+        while (q + len < n && in_tile[q + len] == tile) ++len;
+        // split tile runs so every box dimension stays <= 256 elements
+        int done = 0;
+        while (done < len) {
+            int piece = len - done;
+            if (tile) {
+                const int cap = (rank == 0) ? (e == 1 ? 8 : 7) : 8;
+                if (piece > cap) piece = cap;
+            }
+            if (rank == 5) return TmaTile{};   // too many dimensions
+            const int start = q + done;
+            const cuuint64_t ext = 1ull << piece;
+            gdim[rank] = (rank == 0) ? ext * e : ext;
+            if (rank > 0) gstride[rank - 1] = (cuuint64_t)elem_bytes << start;
+            box[rank] = tile ? (cuuint32_t)gdim[rank] : 1;
+            estr[rank] = 1;
+            t.kind[rank] = tile ? 0 : 1;
+            t.shift[rank] = (int8_t)(tile ? 0 : rest_seen);
+            t.len[rank] = (int8_t)(tile ? 0 : piece);
+            if (!tile) rest_seen += piece;
+            if (rank == 0 && !tile) return TmaTile{};   // bit 0 is always a tile bit
+            ++rank;
+            done += piece;
+        }
+        q += len;
+    }
+    if (items > 1) {
+        if (rank == 5) return TmaTile{};
+        gdim[rank] = (cuuint64_t)items;
+        gstride[rank - 1] = (cuuint64_t)item_stride_bytes;
+        box[rank] = 1;
+        estr[rank] = 1;
+        t.kind[rank] = 2;
+        ++rank;
+    }
+    CUresult r = fn(&t.map, CU_TENSOR_MAP_DATA_TYPE_INT64, (cuuint32_t)rank, base, gdim, gstride, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return TmaTile{};
+    t.rank = rank;
+    return t;
+}
+
+}  // namespace tcng
