@@ -298,7 +298,9 @@ typedef enum {
     TCNG_OPT_TILE_BITS = 1,    /* log2 amplitudes per shared-memory tile, 5..13 (default 13) */
     TCNG_OPT_CHUNK_BITS = 2,   /* log2 contiguous amplitudes per copied chunk (default 7) */
     TCNG_OPT_USE_GRAPHS = 3,   /* 1: replay CUDA graphs per structure (default 1) */
-    TCNG_OPT_UNFUSED = 4       /* 1: one pair/quartet kernel launch per gate (default 0) */
+    TCNG_OPT_UNFUSED = 4,      /* 1: one pair/quartet kernel launch per gate (default 0) */
+    TCNG_OPT_TENSOR_CORES = 5  /* 1: complex64 tile passes apply fused blocks (<= 4 qubits) on the
+                                  tensor cores when all items share one parameter set (default 1) */
 } tcng_option;
 
 tcng_status tcng_set_option(tcng_option opt, int value);

@@ -104,6 +104,8 @@ DevPlan::~DevPlan() {
     cudaFree(d_table);
     cudaFree(d_gparam);
     cudaFree(d_gscale);
+    cudaFree(d_tcops);
+    cudaFree(d_tcdense);
 }
 
 TermSet::~TermSet() {
@@ -465,8 +467,25 @@ tcng_status tcng_apply_circuit(tcng_state* st, const tcng_gate* ops, size_t n_op
         const PlanOptions o = plan_options(st->dt, false);
         for (auto& kv : st->groups) {
             const int n = kv.first;
-            DevPlan* dp = get_plan(n, ops, n_ops, mat_pool, n_mat, P, o);
             const int items = (int)kv.second.items.size();
+            void* tb = nullptr;
+            long long ts = -1;
+            group_span(st, kv.second.items, &tb, &ts);
+            // tensor-core passes: complex64, one parameter set (or none) for all items
+            if (st->dt == TCNG_C64 && g_opt.tensor_cores && !g_opt.unfused && n >= 11 &&
+                (P == 0 || items == 1) && (items == 1 || ts > 0)) {
+                PlanOptions ot = o;
+                ot.tc = 1;
+                ot.fuse_width = std::min(4, std::max(2, g_opt.fuse_width == 2 ? 4 : g_opt.fuse_width));
+                DevPlan* dpt = get_plan(n, ops, n_ops, mat_pool, n_mat, P, ot);
+                tcng_status r = run_plan_tc(dpt, static_cast<float2*>(st->buf), kv.second.d_off, items,
+                                            static_cast<const double*>(params_dev), s, tb, ts);
+                if (r != TCNG_EUNSUPPORTED) {
+                    if (r) return r;
+                    continue;
+                }
+            }
+            DevPlan* dp = get_plan(n, ops, n_ops, mat_pool, n_mat, P, o);
             // Parameters are indexed by position inside the group, so a ragged
             // batch with parameters needs the items of one n to be contiguous.
             const double* prm = static_cast<const double*>(params_dev);
@@ -478,9 +497,6 @@ tcng_status tcng_apply_circuit(tcng_state* st, const tcng_gate* ops, size_t n_op
                                     "ragged batch with parameters needs items of equal n to be contiguous");
                 prm += (size_t)it[0] * P;
             }
-            void* tb = nullptr;
-            long long ts = -1;
-            group_span(st, kv.second.items, &tb, &ts);
             tcng_status r;
             if (st->dt == TCNG_C64)
                 r = run_plan<float2>(dp, static_cast<float2*>(st->buf), kv.second.d_off, items, prm, s, tb, ts);
@@ -603,6 +619,9 @@ tcng_status tcng_set_option(tcng_option opt, int value) {
     case TCNG_OPT_UNFUSED:
         g_opt.unfused = value ? 1 : 0;
         return TCNG_OK;
+    case TCNG_OPT_TENSOR_CORES:
+        g_opt.tensor_cores = value ? 1 : 0;
+        return TCNG_OK;
     }
     return fail(TCNG_EINVAL, "unknown option");
 }
@@ -615,6 +634,7 @@ tcng_status tcng_get_option(tcng_option opt, int* value) {
     case TCNG_OPT_CHUNK_BITS: *value = g_opt.chunk_bits; return TCNG_OK;
     case TCNG_OPT_USE_GRAPHS: *value = g_opt.use_graphs; return TCNG_OK;
     case TCNG_OPT_UNFUSED: *value = g_opt.unfused; return TCNG_OK;
+    case TCNG_OPT_TENSOR_CORES: *value = g_opt.tensor_cores; return TCNG_OK;
     }
     return fail(TCNG_EINVAL, "unknown option");
 }

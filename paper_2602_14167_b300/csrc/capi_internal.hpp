@@ -40,6 +40,7 @@ struct Options {
     int chunk_bits = 7;
     int use_graphs = 1;
     int unfused = 0;
+    int tensor_cores = 1;
 };
 extern Options g_opt;
 extern std::mutex g_mu;
@@ -55,6 +56,12 @@ struct DevPlan {
     double* d_gscale = nullptr;
     void* d_table = nullptr;
     size_t table_bytes = 0;
+    // tensor-core passes
+    std::vector<TcOp> tc_ops;
+    std::vector<int> tc_begin;
+    int tc_n_dense = 0;
+    TcOp* d_tcops = nullptr;
+    int* d_tcdense = nullptr;
     ~DevPlan();
 };
 
@@ -105,6 +112,9 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
                      long long item_stride = -1);
 
 // Synchronous upload of a host vector (used once per structure); throws bad_alloc.
+tcng_status run_plan_tc(DevPlan* dp, float2* state, const long long* d_item_off, int items,
+                        const double* params, cudaStream_t s, void* tma_base, long long item_stride);
+
 template <typename T>
 T* dev_copy(const std::vector<T>& v) {
     if (v.empty()) return nullptr;

@@ -87,6 +87,16 @@ struct DevPass {
     int32_t mat_count;
 };
 
+// ---- tensor-core tile passes -------------------------------------------------
+struct TcOp {                 // one block of a tensor-core pass, in plan order
+    uint8_t kind;             // K_DENSE or K_DIAG
+    uint8_t k;
+    uint8_t tb[5];            // dense: tile bits (ascending); diag: qubit sources (DevOp::src)
+    uint8_t pad;
+    int32_t slot;             // dense: B-operand slot
+    int32_t mat;              // complex offset of the block's matrix in the item's table
+};
+
 // ---- matrix-builder prologue -----------------------------------------------
 struct BuildOp {             // one gate inside a block (40 bytes)
     uint8_t code;            // tcng_op
@@ -139,6 +149,7 @@ struct PlanOptions {
     int chunk_bits = 7;          // c (lowest contiguous bits)
     int adjoint = 0;             // parameterised gates stay single blocks
     int unfused = 0;             // one block per gate, no passes
+    int tc = 0;                  // dense blocks applied on the tensor cores (complex64)
 };
 
 struct Plan {

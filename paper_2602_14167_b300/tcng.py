@@ -24,7 +24,7 @@ PAULI_DTYPE = np.dtype([("xmask", "<u8"), ("zmask", "<u8"), ("coeff", "<f8")], a
 assert GATE_DTYPE.itemsize == 56 and PAULI_DTYPE.itemsize == 24
 
 C64, C128 = 0, 1
-OPT_FUSE_WIDTH, OPT_TILE_BITS, OPT_CHUNK_BITS, OPT_USE_GRAPHS, OPT_UNFUSED = range(5)
+OPT_FUSE_WIDTH, OPT_TILE_BITS, OPT_CHUNK_BITS, OPT_USE_GRAPHS, OPT_UNFUSED, OPT_TENSOR_CORES = range(6)
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSUPPORTED", 5: "ETIMEOUT"}
 
 

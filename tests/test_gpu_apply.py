@@ -28,7 +28,7 @@ def T():
 
 @pytest.fixture(autouse=True)
 def default_options(T):
-    saved = {o: T.tcng_get_option(o) for o in range(5)}
+    saved = {o: T.tcng_get_option(o) for o in range(6)}
     yield
     for o, v in saved.items():
         T.tcng_set_option(o, v)
@@ -209,3 +209,29 @@ def test_invalid_arguments_are_rejected(T):
     with pytest.raises(T.TcngError):
         st.expect(np.array([(1 << 6, 0, 1.0)], dtype=T.PAULI_DTYPE))
     T.tcng_sync_status()
+
+
+@pytest.mark.parametrize("n,depth,width", [(13, 6, 4), (16, 8, 4), (19, 6, 3), (21, 5, 2)])
+def test_tensor_core_tile_passes(T, n, depth, width):
+    """complex64 tile passes with blocks on the tensor cores vs the oracle and vs the SIMT passes."""
+    c, th = gen.su4_brickwork(n, depth, "RZ", seed=n)
+    g, p = c.to_ir()
+    ref = sv.apply(n, g, p, th)
+    T.tcng_set_option(T.OPT_FUSE_WIDTH, width)
+    T.tcng_set_option(T.OPT_TENSOR_CORES, 1)
+    st = run(n, g, p, th, "c64")
+    tc = st.amplitudes(0).cpu().numpy()
+    check_state(tc, ref, "c64")
+    T.tcng_set_option(T.OPT_TENSOR_CORES, 0)
+    st2 = run(n, g, p, th, "c64")
+    check_state(st2.amplitudes(0).cpu().numpy(), ref, "c64")
+
+
+def test_tensor_core_passes_with_diagonal_and_random_ops(T):
+    n = 15
+    c, th = gen.random_circuit(n, 200, seed=77,
+                               kinds=["H", "RX", "RY", "RZ", "CX", "CZ", "CP", "RZZ", "U1", "U2", "U3", "U4", "T", "S"])
+    g, p = c.to_ir()
+    T.tcng_set_option(T.OPT_TENSOR_CORES, 1)
+    st = run(n, g, p, th, "c64")
+    check_state(st.amplitudes(0).cpu().numpy(), sv.apply(n, g, p, th), "c64")

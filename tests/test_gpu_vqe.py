@@ -97,7 +97,7 @@ def test_graph_and_eager_runs_agree(T):
 
 def test_autotune_sets_options_and_caches(T, tmp_path):
     cache = str(tmp_path / "tune.txt")
-    saved = {o: T.tcng_get_option(o) for o in range(5)}
+    saved = {o: T.tcng_get_option(o) for o in range(6)}
     try:
         T.tcng_autotune(18, T.C64, 1, cache)
         fw, tb, cb = (T.tcng_get_option(o) for o in (T.OPT_FUSE_WIDTH, T.OPT_TILE_BITS, T.OPT_CHUNK_BITS))
