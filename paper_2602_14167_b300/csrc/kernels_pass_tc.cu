@@ -320,6 +320,13 @@ tcng_status run_plan_tc(DevPlan* dp, float2* state, const long long* d_item_off,
         dp->d_tcops = dev_copy(ops);
         dp->d_tcdense = dev_copy(dense);
     }
+    // every pass needs a tile tensor map: check them all before launching anything,
+    // so that an unsupported plan falls back with the state untouched
+    std::vector<TmaTile> maps(pl.passes.size());
+    for (size_t pi = 0; pi < pl.passes.size(); ++pi) {
+        maps[pi] = make_tma_tile(tma_base, pl.n, 8, pl.passes[pi], items, item_stride);
+        if (!maps[pi].rank) return fail(TCNG_EUNSUPPORTED, "tensor-core pass needs a tile tensor map");
+    }
     float2* table = static_cast<float2*>(plan_table(dp, sizeof(float2), 1));
     if (!table) return fail(TCNG_ENOMEM, "matrix table allocation failed");
     cudaError_t e;
@@ -339,8 +346,7 @@ tcng_status run_plan_tc(DevPlan* dp, float2* state, const long long* d_item_off,
     if (e != cudaSuccess) return cuda_fail(e, "B operand prologue");
     for (size_t pi = 0; pi < pl.passes.size(); ++pi) {
         const DevPass& P = pl.passes[pi];
-        TmaTile tma = make_tma_tile(tma_base, pl.n, 8, P, items, item_stride);
-        if (!tma.rank) return fail(TCNG_EUNSUPPORTED, "tensor-core pass needs a tile tensor map");
+        const TmaTile& tma = maps[pi];
         PassTcArgs a{};
         a.state = state;
         a.item_off = d_item_off;
