@@ -300,7 +300,8 @@ typedef enum {
     TCNG_OPT_USE_GRAPHS = 3,   /* 1: replay CUDA graphs per structure (default 1) */
     TCNG_OPT_UNFUSED = 4,      /* 1: one pair/quartet kernel launch per gate (default 0) */
     TCNG_OPT_TENSOR_CORES = 5  /* 1: complex64 tile passes apply fused blocks (<= 4 qubits) on the
-                                  tensor cores when all items share one parameter set (default 1) */
+                                  tensor cores when all items share one parameter set (default 0:
+                                  slower than the FP32 register passes in this build) */
 } tcng_option;
 
 tcng_status tcng_set_option(tcng_option opt, int value);

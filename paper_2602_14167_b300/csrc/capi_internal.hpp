@@ -40,7 +40,7 @@ struct Options {
     int chunk_bits = 7;
     int use_graphs = 1;
     int unfused = 0;
-    int tensor_cores = 1;
+    int tensor_cores = 0;
 };
 extern Options g_opt;
 extern std::mutex g_mu;
