@@ -154,6 +154,16 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(value, dist, device=None):
+    """Max of a per-rank float over all ranks (identity without a process group)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
 def run_vqe_only(args):
     import torch
     dev = torch.device("cuda", 0)
@@ -227,10 +237,7 @@ def run_gpu(args):
     ms = ev0.elapsed_time(ev1)
     prof = T.tcng_profile_read(reset=True)
     T.tcng_profile_enable(False)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t[0])
+    ms = max_over_ranks(ms, dist, dev)
     ms_step = ms / args.steps
     value = world * step_bytes * args.steps / (ms * 1e-3) / 1e9
 
@@ -249,10 +256,7 @@ def run_gpu(args):
         e_host.copy_(energy, non_blocking=True)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t[0])
+    t_e2e = max_over_ranks(t_e2e, dist, dev)
     e2e = world * step_bytes * args.steps / t_e2e / 1e9
 
     peak, peak_kind = peaks()
@@ -331,10 +335,7 @@ def vqe_bench(args, dev, dist, world):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t[0])
+    ms = max_over_ranks(ms, dist, dev)
     res[f"n16_b{B}"] = {"evals_per_s": world * B / (ms * 1e-3), "ms_per_batch": ms,
                         "params_per_item": vb.P}
     del vb
