@@ -384,6 +384,13 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
 // ==================================================== Pauli expectation ==
 // One pass over the state evaluates every term whose X bits lie in the tile:
 // sum_x conj(psi[x ^ m]) i^{#Y} (-1)^{popc(x & z)} psi[x] (real part).
+// acc[j] += v for a runtime j without indexing a register array dynamically.
+__device__ __forceinline__ void acc_dyn(double (&acc)[kExpTermsPerPass], int j, double v) {
+#pragma unroll
+    for (int q = 0; q < kExpTermsPerPass; ++q)
+        if (q == j) acc[q] += v;
+}
+
 template <typename C>
 __global__ void __launch_bounds__(512) expect_pass_kernel(const C* __restrict__ state,
                                                           const long long* __restrict__ item_off,
@@ -428,6 +435,38 @@ __global__ void __launch_bounds__(512) expect_pass_kernel(const C* __restrict__ 
         __syncthreads();
         if (s_abort) break;
         const long long gbase = tile_global_base(p, t % tc.tiles_per_item);
+        if (tile_elems == kExpThreads * kExpSlots && blockDim.x == kExpThreads) {
+            // fast path: 16 amplitudes per thread held in registers for every term
+            C a[kExpSlots];
+#pragma unroll
+            for (int i = 0; i < kExpSlots; ++i) a[i] = buf[tid + kExpThreads * i];
+#pragma unroll 1
+            for (int j = 0; j < ep.nterms; ++j) {
+                const ExpTerm& T = ep.t[j];
+                // sign of slot i: parity((tid + 512 i) & zm) ^ parity(gbase & zm_glob)
+                const int pt = (__popc((unsigned)tid & T.zm_tile & (kExpThreads - 1)) +
+                                __popcll((unsigned long long)gbase & T.zm_glob)) & 1;
+                const unsigned zhi = T.zm_tile >> 9;   // tile bits 9..12 select the slot
+                R sr = 0, si = 0;
+#pragma unroll
+                for (int i = 0; i < kExpSlots; ++i) {
+                    const C b = buf[(tid + kExpThreads * i) ^ (int)T.xm_tile];
+                    const R wr = b.x * a[i].x + b.y * a[i].y;   // conj(b) * a
+                    const R wi = b.x * a[i].y - b.y * a[i].x;
+                    const bool neg = ((__popc((unsigned)i & zhi) + pt) & 1) != 0;
+                    sr += neg ? -wr : wr;
+                    si += neg ? -wi : wi;
+                }
+                R v;
+                switch (T.ny & 3) {   // Re(i^ny (sr + i si))
+                case 0: v = sr; break;
+                case 1: v = -si; break;
+                case 2: v = -sr; break;
+                default: v = si; break;
+                }
+                acc_dyn(acc, j, (double)v);
+            }
+        } else {
 #pragma unroll
         for (int j = 0; j < kExpTermsPerPass; ++j) {
             if (j < ep.nterms) {
@@ -451,6 +490,7 @@ __global__ void __launch_bounds__(512) expect_pass_kernel(const C* __restrict__ 
                 }
                 acc[j] += (double)part;
             }
+        }
         }
         __syncthreads();  // everyone done reading buf before it is refilled
         if (warp == 0) {

@@ -18,6 +18,11 @@ struct ExpTerm {
     int32_t ny;         // number of Y factors mod 4
     int32_t out;        // output column
 };
+// Expectation tiles are read by 512 threads, 16 amplitudes each: element i of
+// thread t is tile offset t + 512 i, so the Z parity of an element splits into
+// a per-thread part (zm_tile & 511) and a per-slot part (bit i of slot_sign).
+constexpr int kExpThreads = 512;
+constexpr int kExpSlots = 16;
 constexpr int kExpTermsPerPass = 16;
 struct ExpPass {
     int nterms;
