@@ -179,11 +179,15 @@ __global__ void __launch_bounds__(PT_THREADS, 1) pass_tc_kernel(const __grid_con
                     const uint32_t bhi = smem_u32(bbuf), blo = bhi + PT_B_BYTES;
                     const uint32_t acc = tmem + (uint32_t)(i & 1) * PT_N;
                     const int ksteps = (2 * D + 7) / 8;
+                    // cross terms first, hi*hi last (fewer full-magnitude round-toward-zero steps)
                     for (int kk = 0; kk < ksteps; ++kk) {
                         const uint32_t ko = (uint32_t)kk * 32u;
-                        tc_mma(acc, sw128_desc(ahi + ko), sw128_desc(bhi + ko), idesc, kk ? 1 : 0);
-                        tc_mma(acc, sw128_desc(ahi + ko), sw128_desc(blo + ko), idesc, 1);
+                        tc_mma(acc, sw128_desc(ahi + ko), sw128_desc(blo + ko), idesc, kk ? 1 : 0);
                         tc_mma(acc, sw128_desc(alo + ko), sw128_desc(bhi + ko), idesc, 1);
+                    }
+                    for (int kk = 0; kk < ksteps; ++kk) {
+                        const uint32_t ko = (uint32_t)kk * 32u;
+                        tc_mma(acc, sw128_desc(ahi + ko), sw128_desc(bhi + ko), idesc, 1);
                     }
                     tc_commit(&mma_bar[i & 1]);
                 }

@@ -123,19 +123,24 @@ __global__ void __launch_bounds__(128) shared_unitary_tc_kernel(TcArgs a) {
         tc_fence_after();
         // ---- 3-term TF32 product on the tensor cores ----
         if (tid == 0) {
+            // small cross terms first, the large hi*hi products last: the tensor-core
+            // accumulator rounds toward zero, so each full-magnitude accumulation costs
+            // up to an ulp; this order has 4 of them per output instead of 12
             int first = 1;
             for (int kb = 0; kb < TC_KBLK; ++kb)
                 for (int kk = 0; kk < 4; ++kk) {
                     const uint32_t ka = (uint32_t)kb * TC_M * TC_ROWB + kk * 32u;
                     const uint32_t kbb = (uint32_t)kb * TC_N * TC_ROWB + kk * 32u;
-                    const uint64_t dah = sw128_desc(smem_u32(a_hi) + ka);
-                    const uint64_t dal = sw128_desc(smem_u32(a_lo) + ka);
-                    const uint64_t dbh = sw128_desc(smem_u32(b_hi) + kbb);
-                    const uint64_t dbl = sw128_desc(smem_u32(b_lo) + kbb);
-                    tc_mma(tmem, dah, dbh, idesc, first ? 0 : 1);
-                    tc_mma(tmem, dah, dbl, idesc, 1);
-                    tc_mma(tmem, dal, dbh, idesc, 1);
+                    tc_mma(tmem, sw128_desc(smem_u32(a_hi) + ka), sw128_desc(smem_u32(b_lo) + kbb), idesc,
+                           first ? 0 : 1);
+                    tc_mma(tmem, sw128_desc(smem_u32(a_lo) + ka), sw128_desc(smem_u32(b_hi) + kbb), idesc, 1);
                     first = 0;
+                }
+            for (int kb = 0; kb < TC_KBLK; ++kb)
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint32_t ka = (uint32_t)kb * TC_M * TC_ROWB + kk * 32u;
+                    const uint32_t kbb = (uint32_t)kb * TC_N * TC_ROWB + kk * 32u;
+                    tc_mma(tmem, sw128_desc(smem_u32(a_hi) + ka), sw128_desc(smem_u32(b_hi) + kbb), idesc, 1);
                 }
             tc_commit(&bar);
         }
