@@ -104,8 +104,7 @@ DevPlan::~DevPlan() {
     cudaFree(d_table);
     cudaFree(d_gparam);
     cudaFree(d_gscale);
-    cudaFree(d_tcops);
-    cudaFree(d_tcdense);
+    cudaFree(d_tcs);
 }
 
 TermSet::~TermSet() {
@@ -230,10 +229,40 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
             if (e != cudaSuccess) return cuda_fail(e, "gate kernel");
         }
     } else {
-        for (const DevPass& p : pl.passes) {
+        // complex64 register stages on the tensor cores (when enabled): W operands
+        // from an FP64 table of the same blocks
+        const float* wops = nullptr;
+        long long w_stride = 0;
+        if (sizeof(C) == 8 && g_opt.tensor_cores) {
+            plan_tensor_stages(dp);
+            if (dp->n_tc) {
+                DeviceCtx& c = ctx();
+                double2* dtab = static_cast<double2*>(
+                    c.scratch("tc_table", sizeof(double2) * std::max(1, pl.table_size) * tab_items));
+                float* w = static_cast<float*>(
+                    c.scratch("tc_w", sizeof(float) * 2048 * (size_t)dp->n_tc * tab_items));
+                if (!dtab || !w) return fail(TCNG_ENOMEM, "tensor-core operand scratch");
+                ProfScope ps("build_stage_w", s);
+                e = launch_build_matrices<double2>(dp->d_bblocks, (int)pl.bblocks.size(), dp->d_bops,
+                                                   dp->d_pool, pl.P > 0 ? params : nullptr, pl.P, dtab,
+                                                   pl.table_size, tab_items, s);
+                if (e == cudaSuccess) e = launch_build_stage_w(dp, dtab, stride, tab_items, w, s);
+                if (e != cudaSuccess) return cuda_fail(e, "tensor-core operand prologue");
+                wops = w;
+                w_stride = pl.P > 0 ? 2048ll * dp->n_tc : 0;
+            }
+        }
+        for (size_t pi = 0; pi < pl.passes.size(); ++pi) {
+            const DevPass& p = pl.passes[pi];
             TmaTile tma{};
             if (tma_base && (items == 1 || item_stride > 0))
                 tma = make_tma_tile(tma_base, pl.n, (int)sizeof(C), p, items, item_stride);
+            if (wops && dp->tc_pass[pi] && tma.rank) {
+                ProfScope ps("pass_tcs_kernel_c64", s);
+                e = launch_pass_tcs(dp, (int)pi, items, wops, w_stride, ctx().err, tma, s);
+                if (e != cudaSuccess) return cuda_fail(e, "tensor-core pass kernel");
+                continue;
+            }
             ProfScope ps(sizeof(C) == 8 ? "pass_kernel_c64" : "pass_kernel_c128", s);
             e = launch_pass<C>(state, d_item_off, items, pl.n, p, pl.stages.data(), dp->d_stages,
                                dp->d_dops, table, stride, ctx().err, s, &tma);
@@ -471,20 +500,6 @@ tcng_status tcng_apply_circuit(tcng_state* st, const tcng_gate* ops, size_t n_op
             void* tb = nullptr;
             long long ts = -1;
             group_span(st, kv.second.items, &tb, &ts);
-            // tensor-core passes: complex64, one parameter set (or none) for all items
-            if (st->dt == TCNG_C64 && g_opt.tensor_cores && !g_opt.unfused && n >= 11 &&
-                (P == 0 || items == 1) && (items == 1 || ts > 0)) {
-                PlanOptions ot = o;
-                ot.tc = 1;
-                ot.fuse_width = std::min(4, std::max(2, g_opt.fuse_width == 2 ? 4 : g_opt.fuse_width));
-                DevPlan* dpt = get_plan(n, ops, n_ops, mat_pool, n_mat, P, ot);
-                tcng_status r = run_plan_tc(dpt, static_cast<float2*>(st->buf), kv.second.d_off, items,
-                                            static_cast<const double*>(params_dev), s, tb, ts);
-                if (r != TCNG_EUNSUPPORTED) {
-                    if (r) return r;
-                    continue;
-                }
-            }
             DevPlan* dp = get_plan(n, ops, n_ops, mat_pool, n_mat, P, o);
             // Parameters are indexed by position inside the group, so a ragged
             // batch with parameters needs the items of one n to be contiguous.

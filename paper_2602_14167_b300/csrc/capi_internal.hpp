@@ -56,12 +56,12 @@ struct DevPlan {
     double* d_gscale = nullptr;
     void* d_table = nullptr;
     size_t table_bytes = 0;
-    // tensor-core passes
-    std::vector<TcOp> tc_ops;
-    std::vector<int> tc_begin;
-    int tc_n_dense = 0;
-    TcOp* d_tcops = nullptr;
-    int* d_tcdense = nullptr;
+    // tensor-core register stages (complex64)
+    bool tc_ready = false;
+    std::vector<TcsStage> tcs;        // per plan stage
+    std::vector<char> tc_pass;        // per pass: 1 = run on the tensor cores
+    int n_tc = 0;                     // tensor-core stages (W operands per item)
+    TcsStage* d_tcs = nullptr;
     ~DevPlan();
 };
 
@@ -111,9 +111,14 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
                      const double* params, cudaStream_t s, void* tma_base = nullptr,
                      long long item_stride = -1);
 
+// Tensor-core register stages (kernels_pass_tc.cu).
+void plan_tensor_stages(DevPlan* dp);
+cudaError_t launch_build_stage_w(const DevPlan* dp, const double2* table, long long table_stride,
+                                 int items, float* wops, cudaStream_t s);
+cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float* wops,
+                            long long w_item_stride, unsigned* err, const TmaTile& tma, cudaStream_t s);
+
 // Synchronous upload of a host vector (used once per structure); throws bad_alloc.
-tcng_status run_plan_tc(DevPlan* dp, float2* state, const long long* d_item_off, int items,
-                        const double* params, cudaStream_t s, void* tma_base, long long item_stride);
 
 template <typename T>
 T* dev_copy(const std::vector<T>& v) {

@@ -87,15 +87,18 @@ struct DevPass {
     int32_t mat_count;
 };
 
-// ---- tensor-core tile passes -------------------------------------------------
-struct TcOp {                 // one block of a tensor-core pass, in plan order
-    uint8_t kind;             // K_DENSE or K_DIAG
-    uint8_t k;
-    uint8_t tb[5];            // dense: tile bits (ascending); diag: qubit sources (DevOp::src)
-    uint8_t pad;
-    int32_t slot;             // dense: B-operand slot
-    int32_t mat;              // complex offset of the block's matrix in the item's table
+// ---- tensor-core register stages ----------------------------------------------
+struct TcsStage {             // one register stage run as a 16x16 GEMM (24 bytes)
+    uint8_t rbit[4];          // tile bit of register bit i (ascending)
+    uint8_t nj;               // register bits 0..nj-1 lie on tile bits 0..3 (XOR-rotated reads)
+    uint8_t renorm;           // 1: every gate is unitary, restore the tile norm after the pass
+    uint16_t pad;
+    int32_t op_begin;         // the stage's ops (DevOp) for the matrix prologue
+    int32_t op_count;
+    int32_t mat_begin;        // the pass's matrix window in the item's table
+    int32_t tc_index;         // W operand index, -1: not a tensor-core stage
 };
+static_assert(sizeof(TcsStage) == 24, "TcsStage layout");
 
 // ---- matrix-builder prologue -----------------------------------------------
 struct BuildOp {             // one gate inside a block (40 bytes)
@@ -127,6 +130,7 @@ struct HostOp {
     double scale, angle0;
     int64_t mat_off;
     bool diag;
+    bool unitary;                // explicit matrices: checked on import; named gates: true
 };
 
 struct Block {
@@ -149,7 +153,6 @@ struct PlanOptions {
     int chunk_bits = 7;          // c (lowest contiguous bits)
     int adjoint = 0;             // parameterised gates stay single blocks
     int unfused = 0;             // one block per gate, no passes
-    int tc = 0;                  // dense blocks applied on the tensor cores (complex64)
 };
 
 struct Plan {
@@ -170,6 +173,7 @@ struct Plan {
     std::vector<int> grad_param;       // slot -> param index
     std::vector<double> grad_scale;    // slot -> factor * scale
     int P = 0;
+    bool all_unitary = true;           // every op's matrix is unitary
 };
 
 // Validate the IR and build HostOps (throws std::invalid_argument).

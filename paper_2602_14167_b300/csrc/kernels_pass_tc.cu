@@ -1,16 +1,31 @@
-// Tile passes with the fused blocks applied on the tensor cores (complex64).
+// Tile passes whose register stages run on the tensor cores (complex64).
 //
-// Same tiles as pass_kernel (2^13 amplitudes, one TMA tensor copy in and out),
-// but a dense block on k <= 4 tile bits is applied as a real GEMM over the
-// tile's 2^(13-k) rows: row = the block's 2^k amplitudes as (re, im) pairs,
-// times W (the real form of U^T, see kernels_tc.cu), in 128-row slices with
-// tcgen05.mma kind::tf32 (M=128, N=32, K=8) and a 3-term TF32 split for fp32
-// accuracy.  The slices are software-pipelined: while the tensor cores work on
-// slice i, the CTA gathers and splits slice i+1 and writes slice i-1 back from
-// TMEM.  Diagonal blocks are elementwise phase multiplies.
+// A register stage (the fused gate applications of Sec. II) moves every
+// thread's 16 amplitudes -- one value of the 9 tile bits outside the stage's 4
+// register bits -- through all the stage's gates.  Those gates compose to one
+// 16x16 unitary U_s, so the stage is a real GEMM: the tile's 512 rows of 32
+// reals (re, im of the 16 amplitudes) times W_s, the 32x32 real form of U_s^T.
+//
+// Per stage and 128-row slice (four warps, one per TMEM lane quarter):
+//   * each thread reads its row from the shared-memory tile, splits it into
+//     TF32 hi + lo parts (Veltkamp) and writes both into TMEM (the A operand);
+//   * one thread issues 12 tcgen05.mma kind::tf32 (M=128, N=32, K=8):
+//     a_hi*w_lo + a_lo*w_hi first, a_hi*w_hi last (the accumulator rounds
+//     toward zero; issuing the large products last keeps the full-magnitude
+//     accumulation steps to 4);
+//   * the row is read back from TMEM (tcgen05.ld) and written back to the tile.
+// When every gate of the plan is unitary the pass is unitary on each tile, so
+// after the last stage the tile's norm is restored to its norm before the pass:
+// this removes the systematic shrink of the round-toward-zero accumulation.
+// W_s (hi and lo, 128-byte swizzled, K-major) streams from global memory (L2)
+// through a three-slot ring, two stages ahead.  Rows whose register bits
+// include tile bits 0..3 read their slots XOR-rotated (bank-conflict free) and
+// undo the rotation in registers around the MMA.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <vector>
 
 #include "capi_internal.hpp"
 #include "device.cuh"
@@ -18,84 +33,191 @@
 
 namespace tcng {
 
-constexpr int PT_M = 128;
-constexpr int PT_K = 32;                               // real K = 2 * 2^k padded to 32 (k <= 4)
-constexpr int PT_N = 32;
-constexpr uint32_t PT_A_BYTES = PT_M * PT_K * 4;       // 16 KiB per split part
-constexpr uint32_t PT_B_BYTES = PT_N * PT_K * 4;       // 4 KiB per split part
-constexpr uint32_t PT_B_FLOATS = 2 * PT_N * PT_K;      // hi + lo of one block
-constexpr int PT_THREADS = 256;
+constexpr int TS_THREADS = 512;
+constexpr int TS_TILE_BITS = 13;
+constexpr int TS_NBUF = 3;                         // tile buffers
+constexpr int TS_NB = 3;                           // W ring slots
+constexpr uint32_t TS_W_FLOATS = 2 * 32 * 32;      // hi + lo
+constexpr uint32_t TS_W_BYTES = TS_W_FLOATS * 4;   // 8 KiB
+constexpr uint32_t TS_TMEM_COLS = 512;             // 4 slices x (A hi 32 + A lo 32 + D 32)
+constexpr int TS_MAX_STAGES = 64;                  // stages per pass held in shared memory
 
-// W^T (rows = output column 2j+b, cols = input 2l+a) of every dense block, split
-// into TF32 hi/lo, in the 128-byte-swizzled K-major layout.  One CTA per block.
-__global__ void build_b_operands_kernel(const TcOp* __restrict__ ops, const int* __restrict__ dense,
-                                       const float2* __restrict__ table, float* __restrict__ bops) {
-    const TcOp op = ops[dense[blockIdx.x]];
-    const int D = 1 << op.k;
-    const float2* U = table + op.mat;
-    unsigned char* out = reinterpret_cast<unsigned char*>(bops + (size_t)op.slot * PT_B_FLOATS);
-    for (int e = threadIdx.x; e < PT_N * PT_K; e += blockDim.x) {
-        const int nn = e / PT_K, kk = e % PT_K;
-        float w = 0.f;
-        if (nn < 2 * D && kk < 2 * D) {
-            const int j = nn >> 1, b = nn & 1, l = kk >> 1, a = kk & 1;
-            const float2 u = U[j * D + l];
-            w = (a == b) ? u.x : (a ? -u.y : u.y);
+struct StageSm {            // per-stage constants, shared memory
+    int sr[4];              // 1 << register tile bit i
+    int hm[4];              // ~((1 << register tile bit i) - 1): insert a zero bit (ascending)
+    int nj, renorm, tc_index, pad;
+};
+
+// ------------------------------------------------------------- prologue --
+// W_s of every tensor-core stage and item: U_s = product of the stage's ops
+// (FP64, from the FP64 matrix table), then the real form, TF32 hi/lo.
+__global__ void build_stage_w_kernel(const TcsStage* __restrict__ tcs, const DevOp* __restrict__ ops,
+                                     const double2* __restrict__ table, long long table_stride,
+                                     float* __restrict__ wops, int n_tc) {
+    const TcsStage S = tcs[blockIdx.x];
+    if (S.tc_index < 0) return;
+    const int item = blockIdx.y;
+    __shared__ double2 U[16][16];
+    const int tid = threadIdx.x, r = tid >> 4, c = tid & 15;
+    U[r][c] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+    __syncthreads();
+    const double2* tab = table + (long long)item * table_stride + S.mat_begin;
+    for (int oi = 0; oi < S.op_count; ++oi) {
+        const DevOp op = ops[S.op_begin + oi];
+        const double2* M = tab + op.mat;
+        double2 nv;
+        if (op.kind == K_DENSE) {
+            const int D = 1 << op.k, mask = op.mask;
+            int lr = 0, j = 0;   // local index of row r
+            for (int i = 0; i < 4; ++i)
+                if ((mask >> i) & 1) lr |= ((r >> i) & 1) << j++;
+            nv = make_double2(0.0, 0.0);
+            for (int l = 0; l < D; ++l) {
+                int rr = r & ~mask, jj = 0;
+                for (int i = 0; i < 4; ++i)
+                    if ((mask >> i) & 1) rr |= ((l >> jj++) & 1) << i;
+                const double2 m = M[lr * D + l], u = U[rr][c];
+                nv.x += m.x * u.x - m.y * u.y;
+                nv.y += m.x * u.y + m.y * u.x;
+            }
+        } else {
+            const int nib = op.mask | (op.pad << 8);
+            int idx = 0;
+            for (int i = 0; i < 4; ++i) {
+                const int jj = (nib >> (4 * i)) & 15;
+                if (jj) idx |= ((r >> i) & 1) << (jj - 1);
+            }
+            const double2 d = M[idx], u = U[r][c];
+            nv = make_double2(d.x * u.x - d.y * u.y, d.x * u.y + d.y * u.x);
         }
-        const float h = tf32_round(w);
-        const uint32_t off = sw128_offset(nn, kk, PT_N);
+        __syncthreads();
+        U[r][c] = nv;
+        __syncthreads();
+    }
+    // B operand row nn = output real 2j+b, column kk = input real 2l+a:
+    // W[kk][nn] of  y_j = sum_l U[j][l] x_l  in (re, im) pairs.
+    unsigned char* out = reinterpret_cast<unsigned char*>(
+        wops + ((long long)item * n_tc + S.tc_index) * TS_W_FLOATS);
+    for (int e = tid; e < 32 * 32; e += blockDim.x) {
+        const int nn = e >> 5, kk = e & 31;
+        const int j = nn >> 1, b = nn & 1, l = kk >> 1, a = kk & 1;
+        const double2 u = U[j][l];
+        const double w = (a == b) ? u.x : (a ? -u.y : u.y);
+        const float h = tf32_round((float)w);
+        const uint32_t off = sw128_offset(nn, kk, 32);
         *reinterpret_cast<float*>(out + off) = h;
-        *reinterpret_cast<float*>(out + PT_B_BYTES + off) = tf32_round(w - h);
+        *reinterpret_cast<float*>(out + 4096 + off) = tf32_round((float)(w - (double)h));
     }
 }
 
-struct PassTcArgs {
-    float2* state;
-    const long long* item_off;
-    const TcOp* ops;          // this pass's blocks
-    int n_ops;
-    const float2* table;      // item 0's matrix table (diagonal phases)
-    const float* bops;        // B operands (8 KiB per dense block)
+// ------------------------------------------------------------ helpers ----
+// Veltkamp split of x into hi (11 significant bits: exact in TF32) and the
+// exact rest x - hi (the tensor core keeps its leading 11 bits), on the FMA
+// pipe; the _rn intrinsics keep the compiler from contracting the steps.
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+    const float c = __fmul_rn(x, 8193.0f);   // 2^13 + 1
+    const float h = __fsub_rn(c, __fsub_rn(c, x));
+    hi = __float_as_uint(h);
+    lo = __float_as_uint(__fsub_rn(x, h));
+}
+
+__device__ __forceinline__ void tc_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+        "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+        "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+// D (TMEM) += A (TMEM) * B (shared-memory descriptor)
+__device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                          int accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+// a[s] holds register value s ^ tau (tau only on slots 0..nj-1): permute so
+// that a[v] holds value v (the permutation is its own inverse).
+__device__ __forceinline__ void unrotate(float2 (&a)[16], int tau, int nj) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (k < nj) {
+            const bool sw = (tau >> k) & 1;
+#pragma unroll
+            for (int s = 0; s < 16; ++s)
+                if (!(s & (1 << k))) {
+                    const float2 x = a[s], y = a[s | (1 << k)];
+                    a[s] = sw ? y : x;
+                    a[s | (1 << k)] = sw ? x : y;
+                }
+        }
+    }
+}
+
+struct PassTcsArgs {
+    const TcsStage* tcs;      // this pass's stages
+    const float* wops;        // W operands, [item][tensor-core stage]
+    long long w_item_stride;  // floats per item (0: one set for all items)
     long long tiles_per_item;
     long long total_tiles;
-    uint32_t tile_bytes;
     unsigned* err;
 };
 
-__device__ __forceinline__ int insert_zeros_bits(int r, const uint8_t* tb, int k) {
-    for (int j = 0; j < k; ++j) r = ((r >> tb[j]) << (tb[j] + 1)) | (r & ((1 << tb[j]) - 1));
-    return r;
+__device__ __forceinline__ void tcs_load_tile(const TmaTile& tma, const PassTcsArgs& a, long long t,
+                                              float2* dst, uint64_t* bar) {
+    int c[5];
+    tma_tile_coords(tma, t % a.tiles_per_item, (int)(t / a.tiles_per_item), c);
+    mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(float2) << TS_TILE_BITS));
+    tma_load_tile(tma, dst, bar, c);
 }
 
-__global__ void __launch_bounds__(PT_THREADS, 1) pass_tc_kernel(const __grid_constant__ DevPass p,
-                                                                const PassTcArgs a,
-                                                                const __grid_constant__ TmaTile tma) {
+// ------------------------------------------------------------- kernel ----
+__global__ void __launch_bounds__(TS_THREADS, 1)
+    pass_tcs_kernel(const __grid_constant__ DevPass p, const PassTcsArgs a,
+                    const __grid_constant__ TmaTile tma) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    const int tile_elems = 1 << p.m;
-    float2* tiles = reinterpret_cast<float2*>(base);                       // 2 x tile
-    unsigned char* abuf = base + 2 * (size_t)tile_elems * sizeof(float2);  // 2 x (hi, lo)
-    unsigned char* bbuf = abuf + 4 * PT_A_BYTES;                            // hi, lo
-    __shared__ uint64_t tile_bar[2], mma_bar[2], b_bar;
+    unsigned char* wring = base;                                            // TS_NB x 8 KiB
+    float2* bufs = reinterpret_cast<float2*>(base + TS_NB * TS_W_BYTES);    // TS_NBUF tiles
+    constexpr int tile_elems = 1 << TS_TILE_BITS;
+    __shared__ uint64_t tile_bar[TS_NBUF], w_bar[TS_NB], mma_bar[4];
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // zero the A operands once: columns beyond a block's 2^(k+1) stay 0
-    for (uint32_t i = tid; i < 4 * PT_A_BYTES / 16; i += PT_THREADS)
-        reinterpret_cast<float4*>(abuf)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __shared__ float2 red[TS_THREADS / 32];
+    __shared__ StageSm sst[TS_MAX_STAGES];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int quarter = warp & 3, slice = warp >> 2;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base)),
-                     "r"(2 * PT_N)
+                     "r"(TS_TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    for (int i = tid; i < p.stage_count; i += TS_THREADS) {
+        const TcsStage S = a.tcs[i];
+        StageSm d;
+        for (int r = 0; r < 4; ++r) {
+            d.sr[r] = 1 << S.rbit[r];
+            d.hm[r] = ~((1 << S.rbit[r]) - 1);
+        }
+        d.nj = S.nj;
+        d.renorm = S.renorm;
+        d.tc_index = S.tc_index;
+        d.pad = 0;
+        sst[i] = d;
+    }
     if (tid == 0) {
-        mbar_init(&tile_bar[0], 1);
-        mbar_init(&tile_bar[1], 1);
-        mbar_init(&mma_bar[0], 1);
-        mbar_init(&mma_bar[1], 1);
-        mbar_init(&b_bar, 1);
+        for (int i = 0; i < TS_NBUF; ++i) mbar_init(&tile_bar[i], 1);
+        for (int i = 0; i < TS_NB; ++i) mbar_init(&w_bar[i], 1);
+        for (int i = 0; i < 4; ++i) mbar_init(&mma_bar[i], 1);
         fence_mbar_init();
         s_abort = 0;
     }
@@ -103,270 +225,266 @@ __global__ void __launch_bounds__(PT_THREADS, 1) pass_tc_kernel(const __grid_con
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = tf32_idesc(PT_M, PT_N);
-    uint32_t mph[2] = {0u, 0u}, bph = 0u;
+    const uint32_t col_ahi = (uint32_t)slice * 96u, col_alo = col_ahi + 32u, col_d = col_ahi + 64u;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
+    const uint32_t idesc = tf32_idesc(128, 32);
+    const int nst = p.stage_count;
     const long long first = blockIdx.x, stride = gridDim.x;
-    auto tile_coords = [&](long long t, int (&c)[5]) {
-        tma_tile_coords(tma, t % a.tiles_per_item, (int)(t / a.tiles_per_item), c);
-    };
-    if (tid == 0)
-        for (int i = 0; i < 2; ++i) {
-            const long long t = first + i * stride;
-            if (t < a.total_tiles) {
-                int c[5];
-                tile_coords(t, c);
-                mbar_arrive_expect_tx(&tile_bar[i], a.tile_bytes);
-                tma_load_tile(tma, tiles + (size_t)i * tile_elems, &tile_bar[i], c);
-            }
+    const long long my_tiles = first < a.total_tiles ? (a.total_tiles - first + stride - 1) / stride : 0;
+    const long long total_q = my_tiles * nst;
+    // producer state (thread 0 only): loads issued so far; the next W operand is
+    // stage w_s of the CTA's tile w_t
+    long long tiles_issued = 0, w_issued = 0, w_t = 0;
+    int w_s = 0;
+    auto issue_w = [&]() {
+        const long long item = (first + w_t * stride) / a.tiles_per_item;
+        const float* src = a.wops + item * a.w_item_stride + (long long)sst[w_s].tc_index * TS_W_FLOATS;
+        const int slot = (int)(w_issued % TS_NB);
+        mbar_arrive_expect_tx(&w_bar[slot], TS_W_BYTES);
+        bulk_g2s(wring + (size_t)slot * TS_W_BYTES, src, TS_W_BYTES, &w_bar[slot]);
+        ++w_issued;
+        if (++w_s == nst) {
+            w_s = 0;
+            ++w_t;
         }
-    int it = 0;
+    };
+    if (tid == 0) {
+        for (; tiles_issued < TS_NBUF - 1 && tiles_issued < my_tiles; ++tiles_issued)
+            tcs_load_tile(tma, a, first + tiles_issued * stride, bufs + tiles_issued * tile_elems,
+                          &tile_bar[tiles_issued]);
+        while (w_issued < TS_NB - 1 && w_issued < total_q) issue_w();
+    }
+    long long q = 0;
+    long long it = 0;
     for (long long t = first; t < a.total_tiles; t += stride, ++it) {
-        const int bsel = it & 1;
-        float2* buf = tiles + (size_t)bsel * tile_elems;
-        if (!mbar_wait_bounded(&tile_bar[bsel], (uint32_t)((it >> 1) & 1), a.err)) s_abort = 1;
+        const int b = (int)(it % TS_NBUF);
+        float2* buf = bufs + (size_t)b * tile_elems;
+        if (!mbar_wait_bounded(&tile_bar[b], (uint32_t)((it / TS_NBUF) & 1), a.err)) s_abort = 1;
         __syncthreads();
         if (s_abort) break;
-        const long long gbase = tile_global_base(p, t % a.tiles_per_item);
-        for (int oi = 0; oi < a.n_ops && !s_abort; ++oi) {
-            const TcOp op = a.ops[oi];
-            if (op.kind == K_DIAG) {
-                const float2* M = a.table + op.mat;
-                for (int L = tid; L < tile_elems; L += PT_THREADS) {
-                    int idx = 0;
-                    for (int j = 0; j < op.k; ++j) idx |= src_bit(op.tb[j], L, gbase) << j;
-                    buf[L] = cmul(M[idx], buf[L]);
+        float nin = 0.f;   // this thread's share of the tile norm before the pass
+        for (int s = 0; s < nst; ++s, ++q) {
+            if (tid == 0 && w_issued < total_q && w_issued < q + TS_NB) issue_w();
+            const StageSm& S = sst[s];
+            // this thread's row is group g = tid; slot v is read at register value v ^ tau,
+            // tau = the group bits that land on tile bits >= 4 (bank-conflict-free reads)
+            const int tau = S.nj ? (tid & 15) >> (4 - S.nj) : 0;
+            int L[16];
+            {
+                int g = tid;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) g += g & S.hm[i];
+                int sr[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) sr[i] = S.sr[i];
+                int stau = 0;
+                if (S.nj) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) stau |= ((tau >> i) & 1) ? sr[i] : 0;
                 }
-                __syncthreads();
-                continue;
+                L[0] = g | stau;
+#pragma unroll
+                for (int v = 1; v < 16; ++v)
+                    L[v] = L[v & (v - 1)] ^ ((v & 1) ? sr[0] : (v & 2) ? sr[1] : (v & 4) ? sr[2] : sr[3]);
             }
-            // ---- dense block: GEMM over the tile's rows, 128 at a time ----
-            const int k = op.k, D = 1 << k;
-            const int rows = tile_elems >> k;
-            const int nmt = (rows + PT_M - 1) / PT_M;
-            if (tid == 0) {   // this block's B operand (8 KiB) into shared memory
-                mbar_arrive_expect_tx(&b_bar, 2 * PT_B_BYTES);
-                bulk_g2s(bbuf, a.bops + (size_t)op.slot * PT_B_FLOATS, 2 * PT_B_BYTES, &b_bar);
+            float2 x[16];
+#pragma unroll
+            for (int v = 0; v < 16; ++v) x[v] = buf[L[v]];
+            if (S.nj) unrotate(x, tau, S.nj);
+            if (S.renorm && s == 0) {   // tile norm before the pass (unitary on the tile)
+                float p4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int v = 0; v < 16; ++v) p4[v & 3] = fmaf(x[v].x, x[v].x, fmaf(x[v].y, x[v].y, p4[v & 3]));
+                nin = (p4[0] + p4[1]) + (p4[2] + p4[3]);
             }
-            for (int i = 0; i <= nmt; ++i) {
-                if (i < nmt) {   // gather + split slice i into A[i & 1]
-                    unsigned char* ahi = abuf + (size_t)(i & 1) * 2 * PT_A_BYTES;
-                    unsigned char* alo = ahi + PT_A_BYTES;
-                    for (int e = tid; e < PT_M * D; e += PT_THREADS) {
-                        const int l = e / PT_M, row = e % PT_M;
-                        const int r = i * PT_M + row;
-                        if (r >= rows) continue;
-                        int x = insert_zeros_bits(r, op.tb, k);
-                        for (int j = 0; j < k; ++j)
-                            if ((l >> j) & 1) x |= 1 << op.tb[j];
-                        const float2 v = buf[x];
-                        const float hr = tf32_round(v.x), hm = tf32_round(v.y);
-                        const uint32_t o = sw128_offset(row, 2 * l, PT_M);   // re, im share a 16-B chunk
-                        *reinterpret_cast<float2*>(ahi + o) = make_float2(hr, hm);
-                        *reinterpret_cast<float2*>(alo + o) = make_float2(tf32_round(v.x - hr), tf32_round(v.y - hm));
-                    }
+            {
+                uint32_t hi[32], lo[32];
+#pragma unroll
+                for (int v = 0; v < 16; ++v) {
+                    split_tf32(x[v].x, hi[2 * v], lo[2 * v]);
+                    split_tf32(x[v].y, hi[2 * v + 1], lo[2 * v + 1]);
                 }
-                fence_proxy_async_smem();
-                tc_fence_before();
-                __syncthreads();
+                tc_st32(lane_base + col_ahi, hi);
+                tc_st32(lane_base + col_alo, lo);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            }
+            tc_fence_before();
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + slice), "r"(128) : "memory");
+            if ((tid & 127) == 0) {
                 tc_fence_after();
-                if (i < nmt && tid == 0) {
-                    if (i == 0) {
-                        if (!mbar_wait_bounded(&b_bar, bph, a.err)) s_abort = 1;
-                        bph ^= 1u;
-                    }
-                    const uint32_t ahi = smem_u32(abuf) + (uint32_t)(i & 1) * 2 * PT_A_BYTES;
-                    const uint32_t alo = ahi + PT_A_BYTES;
-                    const uint32_t bhi = smem_u32(bbuf), blo = bhi + PT_B_BYTES;
-                    const uint32_t acc = tmem + (uint32_t)(i & 1) * PT_N;
-                    const int ksteps = (2 * D + 7) / 8;
-                    // cross terms first, hi*hi last (fewer full-magnitude round-toward-zero steps)
-                    for (int kk = 0; kk < ksteps; ++kk) {
-                        const uint32_t ko = (uint32_t)kk * 32u;
-                        tc_mma(acc, sw128_desc(ahi + ko), sw128_desc(blo + ko), idesc, kk ? 1 : 0);
-                        tc_mma(acc, sw128_desc(alo + ko), sw128_desc(bhi + ko), idesc, 1);
-                    }
-                    for (int kk = 0; kk < ksteps; ++kk) {
-                        const uint32_t ko = (uint32_t)kk * 32u;
-                        tc_mma(acc, sw128_desc(ahi + ko), sw128_desc(bhi + ko), idesc, 1);
-                    }
-                    tc_commit(&mma_bar[i & 1]);
-                }
-                if (i >= 1) {   // epilogue of slice i-1
-                    const int s = (i - 1) & 1;
-                    if (!mbar_wait_bounded(&mma_bar[s], mph[s], a.err)) s_abort = 1;
-                    mph[s] ^= 1u;
-                    tc_fence_after();
-                    const int q = warp & 3, half = warp >> 2;     // lane quarter, output half
-                    float v[16];
-                    uint32_t rr[16];
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                        : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]),
-                          "=r"(rr[6]), "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]),
-                          "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]), "=r"(rr[15])
-                        : "r"(tmem + (uint32_t)s * PT_N + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * half))
-                        : "memory");
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int slot = (int)(q % TS_NB);
+                if (mbar_wait_bounded(&w_bar[slot], (uint32_t)((q / TS_NB) & 1), a.err)) {
+                    const uint32_t whi = smem_u32(wring) + (uint32_t)slot * TS_W_BYTES, wlo = whi + 4096u;
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(rr[c]);
-                    const int row = 32 * q + lane;
-                    const int r = (i - 1) * PT_M + row;
-                    if (r < rows) {
-                        const int x = insert_zeros_bits(r, op.tb, k);
-#pragma unroll
-                        for (int jj = 0; jj < 8; ++jj) {
-                            const int j = 8 * half + jj;
-                            if (j < D) {
-                                int y = x;
-                                for (int b = 0; b < k; ++b)
-                                    if ((j >> b) & 1) y |= 1 << op.tb[b];
-                                buf[y] = make_float2(v[2 * jj], v[2 * jj + 1]);
-                            }
-                        }
+                    for (int kk = 0; kk < 4; ++kk) {
+                        tc_mma_ts(tmem + col_d, tmem + col_ahi + 8u * kk, sw128_desc(wlo + 32u * kk), idesc, kk);
+                        tc_mma_ts(tmem + col_d, tmem + col_alo + 8u * kk, sw128_desc(whi + 32u * kk), idesc, 1);
                     }
-                    tc_fence_before();
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc_mma_ts(tmem + col_d, tmem + col_ahi + 8u * kk, sw128_desc(whi + 32u * kk), idesc, 1);
+                } else {
+                    s_abort = 1;
                 }
+                tc_commit(&mma_bar[slice]);
             }
-            __syncthreads();   // block done: the next op sees the updated tile
+            if (!mbar_wait_bounded(&mma_bar[slice], (uint32_t)(q & 1), a.err)) s_abort = 1;
+            tc_fence_after();
+            {
+                float y[32];
+                tc_ld32(lane_base + col_d, y);
+#pragma unroll
+                for (int v = 0; v < 16; ++v) x[v] = make_float2(y[2 * v], y[2 * v + 1]);
+            }
+            if (S.renorm && s == nst - 1) {   // restore the tile norm after the last stage
+                float p4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int v = 0; v < 16; ++v) p4[v & 3] = fmaf(x[v].x, x[v].x, fmaf(x[v].y, x[v].y, p4[v & 3]));
+                float nout = (p4[0] + p4[1]) + (p4[2] + p4[3]);
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    nin += __shfl_xor_sync(0xffffffffu, nin, o);
+                    nout += __shfl_xor_sync(0xffffffffu, nout, o);
+                }
+                if ((tid & 31) == 0) red[warp] = make_float2(nin, nout);
+                __syncthreads();
+                float ti = 0.f, to = 0.f;
+#pragma unroll
+                for (int w = 0; w < TS_THREADS / 32; ++w) {
+                    const float2 r = red[w];
+                    ti += r.x;
+                    to += r.y;
+                }
+                const float f = to > 0.f ? sqrtf(ti / to) : 1.f;
+#pragma unroll
+                for (int v = 0; v < 16; ++v) x[v] = make_float2(x[v].x * f, x[v].y * f);
+                nin = 0.f;
+            }
+            if (S.nj) unrotate(x, tau, S.nj);
+#pragma unroll
+            for (int v = 0; v < 16; ++v) buf[L[v]] = x[v];
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (s_abort) break;
         }
         if (s_abort) break;
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
             int c[5];
-            tile_coords(t, c);
+            tma_tile_coords(tma, t % a.tiles_per_item, (int)(t / a.tiles_per_item), c);
             tma_store_tile(tma, buf, c);
             bulk_commit();
-            const long long tn = t + 2 * stride;
-            if (tn < a.total_tiles) {
-                bulk_wait_read<0>();
-                tile_coords(tn, c);
-                mbar_arrive_expect_tx(&tile_bar[bsel], a.tile_bytes);
-                tma_load_tile(tma, buf, &tile_bar[bsel], c);
+            if (tiles_issued < my_tiles) {   // the next load reuses the buffer stored one tile ago
+                bulk_wait_read<1>();
+                const int bn = (int)(tiles_issued % TS_NBUF);
+                tcs_load_tile(tma, a, first + tiles_issued * stride, bufs + (size_t)bn * tile_elems,
+                              &tile_bar[bn]);
+                ++tiles_issued;
             }
         }
     }
-    if (tid == 0) bulk_wait<0>();
+    if (tid == 0) {
+        bulk_wait<0>();
+        if (s_abort) {   // drain the loads still in flight before the shared memory goes away
+            for (long long i = it; i < tiles_issued; ++i)
+                mbar_wait_bounded(&tile_bar[i % TS_NBUF], (uint32_t)((i / TS_NBUF) & 1), a.err);
+            for (long long i = q; i < w_issued; ++i)
+                mbar_wait_bounded(&w_bar[i % TS_NB], (uint32_t)((i / TS_NB) & 1), a.err);
+        }
+    }
     tc_fence_before();
     __syncthreads();
+    tc_fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * PT_N)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TS_TMEM_COLS)
                      : "memory");
 }
 
-size_t pass_tc_smem_bytes(int m) {
-    return 1024 + 2 * (sizeof(float2) << m) + 4 * PT_A_BYTES + 2 * PT_B_BYTES;
+// ------------------------------------------------------------ host side --
+static size_t pass_tcs_smem_bytes() {
+    return 1024 + TS_NB * TS_W_BYTES + TS_NBUF * (sizeof(float2) << TS_TILE_BITS);
 }
 
-cudaError_t launch_build_b_operands(const TcOp* ops, const int* dense, int n_dense, const float2* table,
-                                    float* bops, cudaStream_t s) {
-    if (!n_dense) return cudaSuccess;
-    build_b_operands_kernel<<<n_dense, 256, 0, s>>>(ops, dense, table, bops);
+// Which passes run their stages on the tensor cores, and the per-stage data.
+void plan_tensor_stages(DevPlan* dp) {
+    if (dp->tc_ready) return;
+    Plan& pl = dp->plan;
+    dp->tcs.assign(pl.stages.size(), TcsStage{});
+    for (auto& s : dp->tcs) s.tc_index = -1;
+    dp->tc_pass.assign(pl.passes.size(), 0);
+    dp->n_tc = 0;
+    if (!pl.opt.unfused && !pl.opt.adjoint) {
+        for (size_t pi = 0; pi < pl.passes.size(); ++pi) {
+            const DevPass& P = pl.passes[pi];
+            bool ok = P.m == TS_TILE_BITS && P.stage_count > 0 && P.stage_count <= TS_MAX_STAGES;
+            for (int si = 0; ok && si < P.stage_count; ++si) {
+                const DevStage& st = pl.stages[P.stage_begin + si];
+                if (st.nreg != 4) ok = false;
+                for (uint32_t oi = 0; ok && oi < st.op_count; ++oi) {
+                    const DevOp& o = pl.dops[st.op_begin + oi];
+                    if (o.kind == K_DIAG) {   // foldable only if every source is a register bit
+                        const int nib = o.mask | (o.pad << 8);
+                        int srcs = 0;
+                        for (int i = 0; i < 4; ++i) srcs += ((nib >> (4 * i)) & 15) ? 1 : 0;
+                        if (srcs != o.k) ok = false;
+                    }
+                }
+            }
+            if (!ok) continue;
+            dp->tc_pass[pi] = 1;
+            for (int si = 0; si < P.stage_count; ++si) {
+                const DevStage& st = pl.stages[P.stage_begin + si];
+                TcsStage& t = dp->tcs[P.stage_begin + si];
+                int nj = 0;
+                for (int i = 0; i < 4; ++i) {
+                    t.rbit[i] = st.rbit[i];
+                    if (st.rbit[i] < 4) ++nj;
+                }
+                t.nj = (uint8_t)nj;
+                t.renorm = pl.all_unitary ? 1 : 0;
+                t.op_begin = (int32_t)st.op_begin;
+                t.op_count = (int32_t)st.op_count;
+                t.mat_begin = P.mat_begin;
+                t.tc_index = dp->n_tc++;
+            }
+        }
+    }
+    if (dp->n_tc) dp->d_tcs = dev_copy(dp->tcs);
+    dp->tc_ready = true;
+}
+
+cudaError_t launch_build_stage_w(const DevPlan* dp, const double2* table, long long table_stride,
+                                 int items, float* wops, cudaStream_t s) {
+    if (!dp->n_tc) return cudaSuccess;
+    dim3 grid((unsigned)dp->tcs.size(), (unsigned)items);
+    build_stage_w_kernel<<<grid, 256, 0, s>>>(dp->d_tcs, dp->d_dops, table, table_stride, wops, dp->n_tc);
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_pass_tc(const DevPass& p, const PassTcArgs& a, const TmaTile& tma, cudaStream_t s) {
-    const size_t smem = pass_tc_smem_bytes(p.m);
+cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float* wops,
+                            long long w_item_stride, unsigned* err, const TmaTile& tma, cudaStream_t s) {
+    const DevPass& P = dp->plan.passes[pass];
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(pass_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)pass_tc_smem_bytes(13));
+        cudaError_t e = cudaFuncSetAttribute(pass_tcs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)pass_tcs_smem_bytes());
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    PassTcsArgs a{};
+    a.tcs = dp->d_tcs + P.stage_begin;
+    a.wops = wops;
+    a.w_item_stride = w_item_stride;
+    a.tiles_per_item = 1ll << (dp->plan.n - P.m);
+    a.total_tiles = a.tiles_per_item * items;
+    a.err = err;
     const long long grid = std::min<long long>(a.total_tiles, num_sms());
-    pass_tc_kernel<<<(unsigned)grid, PT_THREADS, smem, s>>>(p, a, tma);
+    pass_tcs_kernel<<<(unsigned)grid, TS_THREADS, pass_tcs_smem_bytes(), s>>>(P, a, tma);
     count_launch();
     return cudaGetLastError();
-}
-
-// ------------------------------------------------------------ host driver --
-// Run a tensor-core plan (c64, one parameter set for all items).
-tcng_status run_plan_tc(DevPlan* dp, float2* state, const long long* d_item_off, int items,
-                        const double* params, cudaStream_t s, void* tma_base, long long item_stride) {
-    Plan& pl = dp->plan;
-    DeviceCtx& c = ctx();
-    // host list of blocks per pass, built once
-    if (dp->tc_ops.empty() && !pl.passes.empty()) {
-        std::vector<TcOp> ops;
-        std::vector<int> dense;
-        int slot = 0;
-        for (const DevPass& P : pl.passes) {
-            dp->tc_begin.push_back((int)ops.size());
-            for (int si = 0; si < P.stage_count; ++si) {
-                const DevStage& st = pl.stages[P.stage_begin + si];
-                for (uint32_t oi = 0; oi < st.op_count; ++oi) {
-                    const DevOp& o = pl.dops[st.op_begin + oi];
-                    TcOp t{};
-                    t.kind = o.kind;
-                    t.k = o.k;
-                    t.mat = P.mat_begin + (int)o.mat;
-                    if (o.kind == K_DENSE) {
-                        if (o.k > 4) return fail(TCNG_EUNSUPPORTED, "5-qubit block: use the SIMT passes");
-                        int j = 0;
-                        for (int r = 0; r < st.nreg; ++r)
-                            if ((o.mask >> r) & 1) t.tb[j++] = st.rbit[r];
-                        t.slot = slot++;
-                        dense.push_back((int)ops.size());
-                    } else {
-                        for (int j = 0; j < o.k; ++j) t.tb[j] = o.src[j];
-                        t.slot = -1;
-                    }
-                    ops.push_back(t);
-                }
-            }
-        }
-        dp->tc_begin.push_back((int)ops.size());
-        dp->tc_ops = ops;
-        dp->tc_n_dense = slot;
-        dp->d_tcops = dev_copy(ops);
-        dp->d_tcdense = dev_copy(dense);
-    }
-    // every pass needs a tile tensor map: check them all before launching anything,
-    // so that an unsupported plan falls back with the state untouched
-    std::vector<TmaTile> maps(pl.passes.size());
-    for (size_t pi = 0; pi < pl.passes.size(); ++pi) {
-        maps[pi] = make_tma_tile(tma_base, pl.n, 8, pl.passes[pi], items, item_stride);
-        if (!maps[pi].rank) return fail(TCNG_EUNSUPPORTED, "tensor-core pass needs a tile tensor map");
-    }
-    float2* table = static_cast<float2*>(plan_table(dp, sizeof(float2), 1));
-    if (!table) return fail(TCNG_ENOMEM, "matrix table allocation failed");
-    cudaError_t e;
-    {
-        ProfScope ps("build_matrices", s);
-        e = launch_build_matrices<float2>(dp->d_bblocks, (int)pl.bblocks.size(), dp->d_bops, dp->d_pool,
-                                          pl.P > 0 ? params : nullptr, pl.P, table, pl.table_size, 1, s);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "matrix prologue");
-    float* bops = static_cast<float*>(c.scratch("tc_bops", sizeof(float) * PT_B_FLOATS * std::max(1, dp->tc_n_dense)));
-    if (!bops) return fail(TCNG_ENOMEM, "B operand scratch");
-    {
-        ProfScope ps("build_b_operands", s);
-        e = launch_build_b_operands(reinterpret_cast<const TcOp*>(dp->d_tcops), dp->d_tcdense,
-                                    dp->tc_n_dense, table, bops, s);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "B operand prologue");
-    for (size_t pi = 0; pi < pl.passes.size(); ++pi) {
-        const DevPass& P = pl.passes[pi];
-        const TmaTile& tma = maps[pi];
-        PassTcArgs a{};
-        a.state = state;
-        a.item_off = d_item_off;
-        a.ops = reinterpret_cast<const TcOp*>(dp->d_tcops) + dp->tc_begin[pi];
-        a.n_ops = dp->tc_begin[pi + 1] - dp->tc_begin[pi];
-        a.table = table;
-        a.bops = bops;
-        a.tiles_per_item = 1ll << (pl.n - P.m);
-        a.total_tiles = a.tiles_per_item * items;
-        a.tile_bytes = (uint32_t)(sizeof(float2) << P.m);
-        a.err = c.err;
-        ProfScope ps("pass_tc_kernel_c64", s);
-        e = launch_pass_tc(P, a, tma, s);
-        if (e != cudaSuccess) return cuda_fail(e, "tensor-core pass");
-    }
-    return TCNG_OK;
 }
 
 }  // namespace tcng

@@ -65,6 +65,7 @@ std::vector<HostOp> import_ops(int n, const tcng_gate* ops, size_t n_ops, size_t
         if (!std::isfinite(g.scale) || !std::isfinite(g.angle0))
             throw std::invalid_argument(where.str() + "non-finite angle");
         h.mat_off = -1;
+        h.unitary = true;
         if (g.op == TCNG_U1 || g.op == TCNG_U2 || g.op == TCNG_UK) {
             int64_t need = int64_t(1) << (2 * h.k);
             if (g.mat_off < 0 || size_t(g.mat_off + need) > n_mat)
@@ -87,6 +88,20 @@ std::vector<HostOp> import_ops(int n, const tcng_gate* ops, size_t n_ops, size_t
                         break;
                     }
             h.diag = dg;
+            // unitary to 1e-9 (U^dagger U = I); only then may row norms be restored
+            double dev = 0.0;
+            for (int r = 0; r < d; ++r)
+                for (int c = 0; c < d; ++c) {
+                    double re = 0.0, im = 0.0;
+                    for (int l = 0; l < d; ++l) {
+                        const double* a = pool + 2 * (h.mat_off + l * d + r);
+                        const double* b = pool + 2 * (h.mat_off + l * d + c);
+                        re += a[0] * b[0] + a[1] * b[1];
+                        im += a[0] * b[1] - a[1] * b[0];
+                    }
+                    dev = std::max(dev, std::hypot(re - (r == c ? 1.0 : 0.0), im));
+                }
+            h.unitary = dev < 1e-9;
             break;
         }
         default:
@@ -242,6 +257,8 @@ static int pass_work(const Plan& plan, const std::vector<int>& taken) {
 void build_plan(Plan& plan) {
     const PlanOptions& o = plan.opt;
     const int n = plan.n;
+    plan.all_unitary = true;
+    for (const HostOp& h : plan.ops) plan.all_unitary = plan.all_unitary && h.unitary;
     fuse(plan);
     plan.passes.clear();
     plan.stages.clear();
@@ -495,7 +512,14 @@ std::string describe_plan(const Plan& plan) {
         const DevPass& d = plan.passes[p];
         s << " pass " << p << ": m=" << d.m << " chunk=" << d.chunk << " gather=[";
         for (int i = 0; i < d.ngather; ++i) s << (i ? "," : "") << int(d.gather[i]);
-        s << "] stages=" << d.stage_count << " mats=" << d.mat_count << "\n";
+        s << "] stages=" << d.stage_count << " mats=" << d.mat_count << " regs=";
+        for (int i = 0; i < d.stage_count; ++i) {   // register tile bits and op count per stage
+            const DevStage& st = plan.stages[d.stage_begin + i];
+            s << (i ? " " : "") << "{";
+            for (int r = 0; r < st.nreg; ++r) s << (r ? "," : "") << int(st.rbit[r]);
+            s << "}x" << st.op_count;
+        }
+        s << "\n";
     }
     return s.str();
 }

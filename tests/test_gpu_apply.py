@@ -211,27 +211,79 @@ def test_invalid_arguments_are_rejected(T):
     T.tcng_sync_status()
 
 
-@pytest.mark.parametrize("n,depth,width", [(13, 6, 4), (16, 8, 4), (19, 6, 3), (21, 5, 2)])
-def test_tensor_core_tile_passes(T, n, depth, width):
-    """complex64 tile passes with blocks on the tensor cores vs the oracle and vs the SIMT passes."""
+def tc_run(T, n, g, p, th, batch=1):
+    """complex64 run with register stages on the tensor cores; returns (state, tc launches)."""
+    T.tcng_set_option(T.OPT_TENSOR_CORES, 1)
+    T.tcng_profile_enable(True)
+    T.tcng_profile_read(reset=True)
+    try:
+        st = run(n, g, p, th, "c64", batch=batch)
+        prof = T.tcng_profile_read(reset=True)
+    finally:
+        T.tcng_profile_enable(False)
+    return st, prof.get("pass_tcs_kernel_c64", (0, 0.0))[0]
+
+
+@pytest.mark.parametrize("n,depth,width", [(13, 6, 4), (16, 8, 4), (19, 6, 3), (21, 5, 2), (22, 6, 2)])
+def test_tensor_core_stages(T, n, depth, width):
+    """complex64 register stages on the tensor cores vs the oracle and vs the SIMT stages."""
     c, th = gen.su4_brickwork(n, depth, "RZ", seed=n)
     g, p = c.to_ir()
     ref = sv.apply(n, g, p, th)
     T.tcng_set_option(T.OPT_FUSE_WIDTH, width)
-    T.tcng_set_option(T.OPT_TENSOR_CORES, 1)
-    st = run(n, g, p, th, "c64")
-    tc = st.amplitudes(0).cpu().numpy()
-    check_state(tc, ref, "c64")
+    st, launches = tc_run(T, n, g, p, th)
+    assert launches > 0
+    check_state(st.amplitudes(0).cpu().numpy(), ref, "c64")
     T.tcng_set_option(T.OPT_TENSOR_CORES, 0)
     st2 = run(n, g, p, th, "c64")
     check_state(st2.amplitudes(0).cpu().numpy(), ref, "c64")
 
 
-def test_tensor_core_passes_with_diagonal_and_random_ops(T):
+def test_tensor_core_stages_with_diagonal_and_random_ops(T):
     n = 15
     c, th = gen.random_circuit(n, 200, seed=77,
                                kinds=["H", "RX", "RY", "RZ", "CX", "CZ", "CP", "RZZ", "U1", "U2", "U3", "U4", "T", "S"])
     g, p = c.to_ir()
-    T.tcng_set_option(T.OPT_TENSOR_CORES, 1)
-    st = run(n, g, p, th, "c64")
+    st, launches = tc_run(T, n, g, p, th)
+    assert launches > 0
     check_state(st.amplitudes(0).cpu().numpy(), sv.apply(n, g, p, th), "c64")
+
+
+def test_tensor_core_stages_config2(T):
+    """n=24 depth-20 SU(4) brickwork + RX: the longest circuit of the parity set."""
+    n = 24
+    c, th = gen.su4_brickwork(n, 20, "RX", seed=0)
+    g, p = c.to_ir()
+    st, launches = tc_run(T, n, g, p, th)
+    assert launches > 0
+    check_state(st.amplitudes(0).cpu().numpy(), sv.apply(n, g, p, th), "c64")
+
+
+def test_tensor_core_stages_batch_per_item_params(T):
+    n, B = 14, 3
+    c = gen.hea_ring(n, 2)
+    g, p = c.to_ir()
+    th = gen.random_thetas((B, c.n_params), seed=5)
+    st, launches = tc_run(T, n, g, p, th, batch=B)
+    assert launches > 0
+    for b in range(B):
+        check_state(st.amplitudes(b).cpu().numpy(), sv.apply(n, g, p, th[b]), "c64")
+
+
+def test_tensor_core_stages_non_unitary_matrix(T):
+    """An explicit non-unitary block (a projector times a scale) must not be renormalised."""
+    from workloads import Circuit
+    n = 14
+    c = Circuit(n)
+    for q in range(n):
+        c.h(q)
+    c.unitary((3, 4), np.diag([1.0, 0.0, 0.0, 0.5]).astype(np.complex128))
+    c.unitary((9, 11), np.array([[1, 1, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0.5j], [0, 0, 0, 0.5]],
+                                dtype=np.complex128))
+    for q in range(0, n - 1, 2):
+        c.cx(q, q + 1)
+    g, p = c.to_ir()
+    st, launches = tc_run(T, n, g, p, None)
+    ref = sv.apply(n, g, p, None)
+    psi = st.amplitudes(0).cpu().numpy()
+    assert relerr(psi, ref) < TOL["c64"], relerr(psi, ref)
