@@ -550,11 +550,15 @@ static tcng_status expect_impl(const tcng_state* st, const tcng_pauli* terms, si
         double* partial = static_cast<double*>(
             c.scratch("exp_partial", sizeof(double) * (size_t)items * n_terms * nblk));
         if (!partial) return fail(TCNG_ENOMEM, "expectation scratch");
+        void* tbase = nullptr;
+        long long tstride = -1;
+        group_span(st, st->groups.begin()->second.items, &tbase, &tstride);
         for (size_t i = 0; i < passes.size(); ++i) {
             cudaError_t e;
-            // Expectation tiles gather scattered X bits: per-chunk bulk copies measured faster
-            // than many-dimensional tensor copies here, so no tensor map.
+            // one tensor copy per tile where the pass's bit runs fit a tensor map
             TmaTile tma{};
+            if (items == 1 || tstride > 0)
+                tma = make_tma_tile(tbase, n, st->dt == TCNG_C64 ? 8 : 16, passes[i], items, tstride);
             ProfScope ps(st->dt == TCNG_C64 ? "expect_pass_c64" : "expect_pass_c128", s);
             if (st->dt == TCNG_C64)
                 e = launch_expect_pass<float2>(static_cast<const float2*>(st->buf), st->d_off, items, n,

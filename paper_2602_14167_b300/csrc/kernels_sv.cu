@@ -383,16 +383,30 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
 
 // ==================================================== Pauli expectation ==
 // One pass over the state evaluates every term whose X bits lie in the tile:
-// sum_x conj(psi[x ^ m]) i^{#Y} (-1)^{popc(x & z)} psi[x] (real part).
-// acc[j] += v for a runtime j without indexing a register array dynamically.
-__device__ __forceinline__ void acc_dyn(double (&acc)[kExpTermsPerPass], int j, double v) {
+// <P> = sum_x conj(psi[x ^ m]) i^{#Y} (-1)^{popc(x & z)} psi[x] (real part).
+//
+// complex64 tiles of 2^13 amplitudes: thread t holds tile offsets t + 512 i
+// (i = 0..15) in registers, so a term's Z parity splits into a per-thread part
+// (tile bits 0..8 and the tile's global bits) and a per-slot part (tile bits
+// 9..12, applied by a butterfly with runtime signs); the partner amplitude of
+// slot i is buf[(t ^ x) ^ 512 i].  Per term and tile each thread forms an FP32
+// sum, the warp reduces it, and lane 0 adds it to an FP64 accumulator in shared
+// memory (FP64 arithmetic stays out of the per-thread loop).
+
+// sum_i (-1)^{popc(i & zhi)} w_i as a 4-level butterfly over the slot bits,
+// sg[b] = (-1)^{bit b of zhi}: no branch on the Z pattern.
+__device__ __forceinline__ float exp_butterfly(float (&w)[kExpSlots], const float (&sg)[4]) {
 #pragma unroll
-    for (int q = 0; q < kExpTermsPerPass; ++q)
-        if (q == j) acc[q] += v;
+    for (int k = 0; k < 8; ++k) w[k] = fmaf(sg[0], w[2 * k + 1], w[2 * k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w[k] = fmaf(sg[1], w[2 * k + 1], w[2 * k]);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) w[k] = fmaf(sg[2], w[2 * k + 1], w[2 * k]);
+    return fmaf(sg[3], w[1], w[0]);
 }
 
 template <typename C>
-__global__ void __launch_bounds__(512) expect_pass_kernel(const C* __restrict__ state,
+__global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict__ state,
                                                           const long long* __restrict__ item_off,
                                                           const __grid_constant__ DevPass p,
                                                           const __grid_constant__ ExpPass ep,
@@ -405,9 +419,12 @@ __global__ void __launch_bounds__(512) expect_pass_kernel(const C* __restrict__ 
     C* bufs = reinterpret_cast<C*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     uint64_t* bars = reinterpret_cast<uint64_t*>(bufs + (long long)tc.nbuf * tile_elems);
     __shared__ double red[32][kExpTermsPerPass];
+    __shared__ ExpTerm sterm[kExpTermsPerPass];   // the pass's terms, read per tile
     __shared__ int s_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int item = blockIdx.y;
+    for (int i = tid; i < 32 * kExpTermsPerPass; i += blockDim.x) (&red[0][0])[i] = 0.0;
+    if (tid < ep.nterms) sterm[tid] = ep.t[tid];
     if (tid == 0) {
         for (int i = 0; i < tc.nbuf; ++i) mbar_init(&bars[i], 1);
         fence_mbar_init();
@@ -423,9 +440,27 @@ __global__ void __launch_bounds__(512) expect_pass_kernel(const C* __restrict__ 
             const long long t = first + i * stride;
             if (t < t1) issue_tile_load(state, item_off, p, tc, t, bufs + (long long)i * tile_elems, &bars[i], lane, tma);
         }
+    const bool fast = std::is_same<C, float2>::value && tile_elems == kExpThreads * kExpSlots &&
+                      blockDim.x == kExpThreads;
     double acc[kExpTermsPerPass];
+    float acc32[kExpTermsPerPass];
 #pragma unroll
-    for (int j = 0; j < kExpTermsPerPass; ++j) acc[j] = 0.0;
+    for (int j = 0; j < kExpTermsPerPass; ++j) {
+        acc[j] = 0.0;
+        acc32[j] = 0.f;
+    }
+    auto flush32 = [&]() {   // warp sums in a fixed order, lane 0 adds into the FP64 sums
+#pragma unroll
+        for (int j = 0; j < kExpTermsPerPass; ++j) {
+            if (j < ep.nterms) {
+                float v = acc32[j];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) red[warp][j] += (double)v;
+            }
+            acc32[j] = 0.f;
+        }
+    };
     int it = 0;
     for (long long t = first; t < t1; t += stride, ++it) {
         const int b = it % tc.nbuf;
@@ -435,38 +470,61 @@ __global__ void __launch_bounds__(512) expect_pass_kernel(const C* __restrict__ 
         __syncthreads();
         if (s_abort) break;
         const long long gbase = tile_global_base(p, t % tc.tiles_per_item);
-        if (tile_elems == kExpThreads * kExpSlots && blockDim.x == kExpThreads) {
-            // fast path: 16 amplitudes per thread held in registers for every term
-            C a[kExpSlots];
-#pragma unroll
-            for (int i = 0; i < kExpSlots; ++i) a[i] = buf[tid + kExpThreads * i];
-#pragma unroll 1
-            for (int j = 0; j < ep.nterms; ++j) {
-                const ExpTerm& T = ep.t[j];
-                // sign of slot i: parity((tid + 512 i) & zm) ^ parity(gbase & zm_glob)
-                const int pt = (__popc((unsigned)tid & T.zm_tile & (kExpThreads - 1)) +
-                                __popcll((unsigned long long)gbase & T.zm_glob)) & 1;
-                const unsigned zhi = T.zm_tile >> 9;   // tile bits 9..12 select the slot
-                R sr = 0, si = 0;
+        if constexpr (std::is_same<C, float2>::value) {
+            if (fast) {
+                float2 a[kExpSlots];
+                float pz[kExpSlots];   // |a_i|^2 for the Z-only terms
 #pragma unroll
                 for (int i = 0; i < kExpSlots; ++i) {
-                    const C b = buf[(tid + kExpThreads * i) ^ (int)T.xm_tile];
-                    const R wr = b.x * a[i].x + b.y * a[i].y;   // conj(b) * a
-                    const R wi = b.x * a[i].y - b.y * a[i].x;
-                    const bool neg = ((__popc((unsigned)i & zhi) + pt) & 1) != 0;
-                    sr += neg ? -wr : wr;
-                    si += neg ? -wi : wi;
+                    a[i] = buf[tid + kExpThreads * i];
+                    pz[i] = fmaf(a[i].x, a[i].x, a[i].y * a[i].y);
                 }
-                R v;
-                switch (T.ny & 3) {   // Re(i^ny (sr + i si))
-                case 0: v = sr; break;
-                case 1: v = -si; break;
-                case 2: v = -sr; break;
-                default: v = si; break;
+#pragma unroll 1
+                for (int j = 0; j < ep.nterms; ++j) {
+                    const ExpTerm T = sterm[j];
+                    float sg[4];
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) sg[bb] = ((T.zm_tile >> (9 + bb)) & 1) ? -1.f : 1.f;
+                    float w[kExpSlots];
+                    if (T.xm_tile == 0) {
+#pragma unroll
+                        for (int i = 0; i < kExpSlots; ++i) w[i] = pz[i];
+                    } else {
+                        // partner of slot i: tile offset (tid ^ xm) ^ 512 i
+                        if (T.ny & 1) {   // Im(conj(b) a)
+#pragma unroll
+                            for (int i = 0; i < kExpSlots; ++i) {
+                                const float2 b = buf[(tid ^ (int)T.xm_tile) ^ (i << 9)];
+                                w[i] = fmaf(b.x, a[i].y, -b.y * a[i].x);
+                            }
+                        } else {          // Re(conj(b) a)
+#pragma unroll
+                            for (int i = 0; i < kExpSlots; ++i) {
+                                const float2 b = buf[(tid ^ (int)T.xm_tile) ^ (i << 9)];
+                                w[i] = fmaf(b.x, a[i].x, b.y * a[i].y);
+                            }
+                        }
+                    }
+                    float v = exp_butterfly(w, sg);
+                    // per-thread Z parity, and Re(i^ny s): ny = 1, 2 flip the sign
+                    const int flip = (__popc((unsigned)tid & T.zm_tile & (kExpThreads - 1)) +
+                                      __popcll((unsigned long long)gbase & T.zm_glob) +
+                                      ((T.ny & 3) == 1 || (T.ny & 3) == 2)) & 1;
+                    v = flip ? -v : v;
+                    switch (j) {   // uniform branch: a static register per term
+#define TCNG_ACASE(q) case q: acc32[q] += v; break;
+                    TCNG_ACASE(0) TCNG_ACASE(1) TCNG_ACASE(2) TCNG_ACASE(3) TCNG_ACASE(4) TCNG_ACASE(5)
+                    TCNG_ACASE(6) TCNG_ACASE(7) TCNG_ACASE(8) TCNG_ACASE(9) TCNG_ACASE(10)
+                    TCNG_ACASE(11) TCNG_ACASE(12) TCNG_ACASE(13) TCNG_ACASE(14)
+                    default: acc32[15] += v; break;
+#undef TCNG_ACASE
+                    }
                 }
-                acc_dyn(acc, j, (double)v);
+                // every 64 tiles (and at the end) fold the FP32 sums into FP64
+                if ((it & 63) == 63 || t + stride >= t1) flush32();
             }
-        } else {
+        }
+        if (!fast) {
 #pragma unroll
         for (int j = 0; j < kExpTermsPerPass; ++j) {
             if (j < ep.nterms) {
@@ -500,12 +558,14 @@ __global__ void __launch_bounds__(512) expect_pass_kernel(const C* __restrict__ 
         }
     }
     // deterministic block reduction: warp tree, then warps in order
+    if (!fast) {
 #pragma unroll
-    for (int j = 0; j < kExpTermsPerPass; ++j) {
-        double v = acc[j];
+        for (int j = 0; j < kExpTermsPerPass; ++j) {
+            double v = acc[j];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][j] = v;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][j] = v;
+        }
     }
     __syncthreads();
     if (tid < ep.nterms) {
@@ -735,7 +795,7 @@ template <typename C>
 cudaError_t launch_expect_pass(const C* state, const long long* item_off, int items, int n,
                                const DevPass& p, const ExpPass& ep, double* partial, int n_out,
                                int nblk, unsigned* err, cudaStream_t s, const TmaTile* tma) {
-    const int nbuf = 2;
+    const int nbuf = 3;
     const size_t smem = 128 + (size_t)nbuf * (sizeof(C) << p.m) + 8 * nbuf;
     static bool done = false;
     static size_t lim = 0;
