@@ -299,9 +299,11 @@ typedef enum {
     TCNG_OPT_CHUNK_BITS = 2,   /* log2 contiguous amplitudes per copied chunk (default 7) */
     TCNG_OPT_USE_GRAPHS = 3,   /* 1: replay CUDA graphs per structure (default 1) */
     TCNG_OPT_UNFUSED = 4,      /* 1: one pair/quartet kernel launch per gate (default 0) */
-    TCNG_OPT_TENSOR_CORES = 5  /* 1: complex64 tile passes apply fused blocks (<= 4 qubits) on the
-                                  tensor cores when all items share one parameter set (default 0:
-                                  slower than the FP32 register passes in this build) */
+    TCNG_OPT_TENSOR_CORES = 5  /* complex64 register stages as 16x16 GEMMs on the tensor cores
+                                  (TF32 hi/lo split, ~1e-6 relative error per circuit):
+                                  0 off, 1 on, 2 auto (default): on when all items share one
+                                  parameter set and the state spans at least one 2^13-amplitude
+                                  tile per SM, or spans 32 tiles per SM */
 } tcng_option;
 
 tcng_status tcng_set_option(tcng_option opt, int value);

@@ -233,7 +233,12 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
         // from an FP64 table of the same blocks
         const float* wops = nullptr;
         long long w_stride = 0;
-        if (sizeof(C) == 8 && g_opt.tensor_cores) {
+        // auto: the W prologue is per item when items carry their own parameters, and
+        // fewer tiles than SMs leave the tensor-core pipeline latency-bound (measured
+        // slower than the SIMT stages there)
+        const long long tiles = (pl.n >= 13 ? (1ll << (pl.n - 13)) : 0) * items;
+        const bool tc_auto = (tab_items == 1 && tiles >= num_sms()) || tiles >= 32ll * num_sms();
+        if (sizeof(C) == 8 && (g_opt.tensor_cores == 1 || (g_opt.tensor_cores == 2 && tc_auto))) {
             plan_tensor_stages(dp);
             if (dp->n_tc) {
                 DeviceCtx& c = ctx();
@@ -636,7 +641,8 @@ tcng_status tcng_set_option(tcng_option opt, int value) {
         g_opt.unfused = value ? 1 : 0;
         return TCNG_OK;
     case TCNG_OPT_TENSOR_CORES:
-        g_opt.tensor_cores = value ? 1 : 0;
+        if (value < 0 || value > 2) return fail(TCNG_EINVAL, "tensor-core option is 0, 1 or 2");
+        g_opt.tensor_cores = value;
         return TCNG_OK;
     }
     return fail(TCNG_EINVAL, "unknown option");

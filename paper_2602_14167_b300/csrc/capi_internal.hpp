@@ -40,7 +40,7 @@ struct Options {
     int chunk_bits = 7;
     int use_graphs = 1;
     int unfused = 0;
-    int tensor_cores = 0;
+    int tensor_cores = 2;     // 0 off, 1 on, 2 auto
 };
 extern Options g_opt;
 extern std::mutex g_mu;
@@ -60,6 +60,7 @@ struct DevPlan {
     bool tc_ready = false;
     std::vector<TcsStage> tcs;        // per plan stage
     std::vector<char> tc_pass;        // per pass: 1 = run on the tensor cores
+    std::vector<int> tc_group;        // per pass: slice tile bits (b0 | b1 << 8), -1 = none
     int n_tc = 0;                     // tensor-core stages (W operands per item)
     TcsStage* d_tcs = nullptr;
     ~DevPlan();

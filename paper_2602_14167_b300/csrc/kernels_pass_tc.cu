@@ -9,14 +9,15 @@
 // Per stage and 128-row slice (four warps, one per TMEM lane quarter):
 //   * each thread reads its row from the shared-memory tile, splits it into
 //     TF32 hi + lo parts (Veltkamp) and writes both into TMEM (the A operand);
-//   * one thread issues 12 tcgen05.mma kind::tf32 (M=128, N=32, K=8):
-//     a_hi*w_lo + a_lo*w_hi first, a_hi*w_hi last (the accumulator rounds
-//     toward zero; issuing the large products last keeps the full-magnitude
-//     accumulation steps to 4);
+//   * one thread issues 8 tcgen05.mma kind::tf32 (M=128, K=8): per K step one
+//     N=64 MMA against [W_hi | W_lo] (a_hi*w_hi and a_hi*w_lo side by side)
+//     and one N=32 MMA adding a_lo*w_hi to the small half; the halves are
+//     summed in registers, so the large products accumulate on their own;
 //   * the row is read back from TMEM (tcgen05.ld) and written back to the tile.
-// When every gate of the plan is unitary the pass is unitary on each tile, so
-// after the last stage the tile's norm is restored to its norm before the pass:
-// this removes the systematic shrink of the round-toward-zero accumulation.
+// When every gate of the plan is unitary the pass is unitary on each tile (and,
+// in a grouped pass, on each slice), so after the last stage the tile's (slice's)
+// norm is restored to its norm before the pass: this removes the systematic
+// shrink of the round-toward-zero accumulation.
 // W_s (hi and lo, 128-byte swizzled, K-major) streams from global memory (L2)
 // through a three-slot ring, two stages ahead.  Rows whose register bits
 // include tile bits 0..3 read their slots XOR-rotated (bank-conflict free) and
@@ -39,12 +40,13 @@ constexpr int TS_NBUF = 3;                         // tile buffers
 constexpr int TS_NB = 3;                           // W ring slots
 constexpr uint32_t TS_W_FLOATS = 2 * 32 * 32;      // hi + lo
 constexpr uint32_t TS_W_BYTES = TS_W_FLOATS * 4;   // 8 KiB
-constexpr uint32_t TS_TMEM_COLS = 512;             // 4 slices x (A hi 32 + A lo 32 + D 32)
+constexpr uint32_t TS_TMEM_COLS = 512;             // 4 slices x (A hi 32 + A lo 32 + D 64)
 constexpr int TS_MAX_STAGES = 64;                  // stages per pass held in shared memory
 
 struct StageSm {            // per-stage constants, shared memory
     int sr[4];              // 1 << register tile bit i
-    int hm[4];              // ~((1 << register tile bit i) - 1): insert a zero bit (ascending)
+    int hm[6];              // ~((1 << b) - 1) for the bits the row index skips (ascending)
+    int gb0, gb1;           // grouped passes: tile bits fixed per 128-row slice
     int nj, renorm, tc_index, pad;
 };
 
@@ -162,6 +164,8 @@ __device__ __forceinline__ void unrotate(float2 (&a)[16], int tau, int nj) {
 }
 
 struct PassTcsArgs {
+    int grouped;              // 1: slices run independently (see plan_tensor_stages)
+    int gb0, gb1;             // their fixed tile bits
     const TcsStage* tcs;      // this pass's stages
     const float* wops;        // W operands, [item][tensor-core stage]
     long long w_item_stride;  // floats per item (0: one set for all items)
@@ -204,10 +208,24 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
     for (int i = tid; i < p.stage_count; i += TS_THREADS) {
         const TcsStage S = a.tcs[i];
         StageSm d;
+        int skip[6], ns = 0;   // register bits (+ the slice bits of a grouped pass), ascending
         for (int r = 0; r < 4; ++r) {
             d.sr[r] = 1 << S.rbit[r];
-            d.hm[r] = ~((1 << S.rbit[r]) - 1);
+            skip[ns++] = S.rbit[r];
         }
+        if (a.grouped) {
+            skip[ns++] = a.gb0;
+            skip[ns++] = a.gb1;
+        }
+        for (int x = 1; x < ns; ++x)
+            for (int y = x; y > 0 && skip[y - 1] > skip[y]; --y) {
+                const int tmp = skip[y];
+                skip[y] = skip[y - 1];
+                skip[y - 1] = tmp;
+            }
+        for (int k = 0; k < 6; ++k) d.hm[k] = k < ns ? ~((1 << skip[k]) - 1) : 0;
+        d.gb0 = a.gb0;
+        d.gb1 = a.gb1;
         d.nj = S.nj;
         d.renorm = S.renorm;
         d.tc_index = S.tc_index;
@@ -225,9 +243,9 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t col_ahi = (uint32_t)slice * 96u, col_alo = col_ahi + 32u, col_d = col_ahi + 64u;
+    const uint32_t col_ahi = (uint32_t)slice * 128u, col_alo = col_ahi + 32u, col_d = col_ahi + 64u;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
-    const uint32_t idesc = tf32_idesc(128, 32);
+    const uint32_t idesc64 = tf32_idesc(128, 64), idesc32 = tf32_idesc(128, 32);
     const int nst = p.stage_count;
     const long long first = blockIdx.x, stride = gridDim.x;
     const long long my_tiles = first < a.total_tiles ? (a.total_tiles - first + stride - 1) / stride : 0;
@@ -252,7 +270,15 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
         for (; tiles_issued < TS_NBUF - 1 && tiles_issued < my_tiles; ++tiles_issued)
             tcs_load_tile(tma, a, first + tiles_issued * stride, bufs + tiles_issued * tile_elems,
                           &tile_bar[tiles_issued]);
-        while (w_issued < TS_NB - 1 && w_issued < total_q) issue_w();
+        if (a.grouped) {   // every stage's W stays resident (one set for all items)
+            for (int st = 0; st < nst && my_tiles > 0; ++st) {
+                mbar_arrive_expect_tx(&w_bar[st], TS_W_BYTES);
+                bulk_g2s(wring + (size_t)st * TS_W_BYTES, a.wops + (long long)sst[st].tc_index * TS_W_FLOATS,
+                         TS_W_BYTES, &w_bar[st]);
+            }
+        } else {
+            while (w_issued < TS_NB - 1 && w_issued < total_q) issue_w();
+        }
     }
     long long q = 0;
     long long it = 0;
@@ -264,16 +290,24 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
         if (s_abort) break;
         float nin = 0.f;   // this thread's share of the tile norm before the pass
         for (int s = 0; s < nst; ++s, ++q) {
-            if (tid == 0 && w_issued < total_q && w_issued < q + TS_NB) issue_w();
+            if (!a.grouped && tid == 0 && w_issued < total_q && w_issued < q + TS_NB) issue_w();
             const StageSm& S = sst[s];
             // this thread's row is group g = tid; slot v is read at register value v ^ tau,
             // tau = the group bits that land on tile bits >= 4 (bank-conflict-free reads)
             const int tau = S.nj ? (tid & 15) >> (4 - S.nj) : 0;
             int L[16];
             {
-                int g = tid;
+                int g;
+                if (a.grouped) {   // slice bits of tid -> the pass's fixed tile bits
+                    g = tid & 127;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) g += g & S.hm[i];
+                    for (int i = 0; i < 6; ++i) g += g & S.hm[i];
+                    g |= (((tid >> 7) & 1) << S.gb0) | (((tid >> 8) & 1) << S.gb1);
+                } else {
+                    g = tid;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) g += g & S.hm[i];
+                }
                 int sr[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) sr[i] = S.sr[i];
@@ -312,17 +346,18 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
             asm volatile("bar.sync %0, %1;" ::"r"(1 + slice), "r"(128) : "memory");
             if ((tid & 127) == 0) {
                 tc_fence_after();
-                const int slot = (int)(q % TS_NB);
-                if (mbar_wait_bounded(&w_bar[slot], (uint32_t)((q / TS_NB) & 1), a.err)) {
-                    const uint32_t whi = smem_u32(wring) + (uint32_t)slot * TS_W_BYTES, wlo = whi + 4096u;
+                const int slot = a.grouped ? s : (int)(q % TS_NB);
+                const uint32_t wpar = a.grouped ? 0u : (uint32_t)((q / TS_NB) & 1);
+                if (mbar_wait_bounded(&w_bar[slot], wpar, a.err)) {
+                    // W slot = [W_hi (32 rows) | W_lo (32 rows)]: one N=64 MMA gives
+                    // a_hi*w_hi in D[0:32] and a_hi*w_lo in D[32:64]; a_lo*w_hi joins
+                    // D[32:64]; the two halves are added in registers afterwards
+                    const uint64_t dw = sw128_desc(smem_u32(wring) + (uint32_t)slot * TS_W_BYTES);
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        tc_mma_ts(tmem + col_d, tmem + col_ahi + 8u * kk, sw128_desc(wlo + 32u * kk), idesc, kk);
-                        tc_mma_ts(tmem + col_d, tmem + col_alo + 8u * kk, sw128_desc(whi + 32u * kk), idesc, 1);
+                    for (int kk = 0; kk < 4; ++kk) {   // K step kk: +32 bytes = +2 in the start field
+                        tc_mma_ts(tmem + col_d, tmem + col_ahi + 8u * kk, dw + 2u * kk, idesc64, kk);
+                        tc_mma_ts(tmem + col_d + 32u, tmem + col_alo + 8u * kk, dw + 2u * kk, idesc32, 1);
                     }
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        tc_mma_ts(tmem + col_d, tmem + col_ahi + 8u * kk, sw128_desc(whi + 32u * kk), idesc, 1);
                 } else {
                     s_abort = 1;
                 }
@@ -331,10 +366,11 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
             if (!mbar_wait_bounded(&mma_bar[slice], (uint32_t)(q & 1), a.err)) s_abort = 1;
             tc_fence_after();
             {
-                float y[32];
+                float y[32], z[32];
                 tc_ld32(lane_base + col_d, y);
+                tc_ld32(lane_base + col_d + 32u, z);
 #pragma unroll
-                for (int v = 0; v < 16; ++v) x[v] = make_float2(y[2 * v], y[2 * v + 1]);
+                for (int v = 0; v < 16; ++v) x[v] = make_float2(y[2 * v] + z[2 * v], y[2 * v + 1] + z[2 * v + 1]);
             }
             if (S.renorm && s == nst - 1) {   // restore the tile norm after the last stage
                 float p4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -347,13 +383,23 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                     nout += __shfl_xor_sync(0xffffffffu, nout, o);
                 }
                 if ((tid & 31) == 0) red[warp] = make_float2(nin, nout);
-                __syncthreads();
                 float ti = 0.f, to = 0.f;
+                if (a.grouped) {   // the slice's rows are closed under the pass: its own norm
+                    asm volatile("bar.sync %0, %1;" ::"r"(1 + slice), "r"(128) : "memory");
 #pragma unroll
-                for (int w = 0; w < TS_THREADS / 32; ++w) {
-                    const float2 r = red[w];
-                    ti += r.x;
-                    to += r.y;
+                    for (int w = 0; w < 4; ++w) {
+                        const float2 r = red[4 * slice + w];
+                        ti += r.x;
+                        to += r.y;
+                    }
+                } else {
+                    __syncthreads();
+#pragma unroll
+                    for (int w = 0; w < TS_THREADS / 32; ++w) {
+                        const float2 r = red[w];
+                        ti += r.x;
+                        to += r.y;
+                    }
                 }
                 const float f = to > 0.f ? sqrtf(ti / to) : 1.f;
 #pragma unroll
@@ -364,9 +410,13 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
 #pragma unroll
             for (int v = 0; v < 16; ++v) buf[L[v]] = x[v];
             tc_fence_before();
-            __syncthreads();
+            if (a.grouped) {   // the next stage reads only this slice's rows
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + slice), "r"(128) : "memory");
+            } else {
+                __syncthreads();
+            }
             tc_fence_after();
-            if (s_abort) break;
+            if (!a.grouped && s_abort) break;
         }
         if (s_abort) break;
         fence_proxy_async_smem();
@@ -390,8 +440,12 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
         if (s_abort) {   // drain the loads still in flight before the shared memory goes away
             for (long long i = it; i < tiles_issued; ++i)
                 mbar_wait_bounded(&tile_bar[i % TS_NBUF], (uint32_t)((i / TS_NBUF) & 1), a.err);
-            for (long long i = q; i < w_issued; ++i)
-                mbar_wait_bounded(&w_bar[i % TS_NB], (uint32_t)((i / TS_NB) & 1), a.err);
+            if (a.grouped) {
+                for (int st = 0; st < nst; ++st) mbar_wait_bounded(&w_bar[st], 0u, a.err);
+            } else {
+                for (long long i = q; i < w_issued; ++i)
+                    mbar_wait_bounded(&w_bar[i % TS_NB], (uint32_t)((i / TS_NB) & 1), a.err);
+            }
         }
     }
     tc_fence_before();
@@ -414,6 +468,7 @@ void plan_tensor_stages(DevPlan* dp) {
     dp->tcs.assign(pl.stages.size(), TcsStage{});
     for (auto& s : dp->tcs) s.tc_index = -1;
     dp->tc_pass.assign(pl.passes.size(), 0);
+    dp->tc_group.assign(pl.passes.size(), -1);
     dp->n_tc = 0;
     if (!pl.opt.unfused && !pl.opt.adjoint) {
         for (size_t pi = 0; pi < pl.passes.size(); ++pi) {
@@ -434,6 +489,20 @@ void plan_tensor_stages(DevPlan* dp) {
             }
             if (!ok) continue;
             dp->tc_pass[pi] = 1;
+            // two tile bits that no stage of the pass touches (>= 5, so the lanes keep the
+            // low bits): rows with fixed values of them never leave their 128-row slice
+            {
+                uint32_t U = 0;
+                for (int si = 0; si < P.stage_count; ++si)
+                    for (int i = 0; i < 4; ++i) U |= 1u << pl.stages[P.stage_begin + si].rbit[i];
+                int g1 = -1, g0 = -1;
+                for (int b = TS_TILE_BITS - 1; b >= 5 && g0 < 0; --b)
+                    if (!((U >> b) & 1)) {
+                        if (g1 < 0) g1 = b;
+                        else g0 = b;
+                    }
+                if (g0 >= 0 && P.stage_count <= TS_NB) dp->tc_group[pi] = g0 | (g1 << 8);
+            }
             for (int si = 0; si < P.stage_count; ++si) {
                 const DevStage& st = pl.stages[P.stage_begin + si];
                 TcsStage& t = dp->tcs[P.stage_begin + si];
@@ -475,6 +544,10 @@ cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float*
         attr = true;
     }
     PassTcsArgs a{};
+    const int grp = dp->tc_group[pass];
+    a.grouped = (grp >= 0 && (w_item_stride == 0 || items == 1)) ? 1 : 0;   // one W set per CTA
+    a.gb0 = a.grouped ? (grp & 255) : 0;
+    a.gb1 = a.grouped ? (grp >> 8) : 0;
     a.tcs = dp->d_tcs + P.stage_begin;
     a.wops = wops;
     a.w_item_stride = w_item_stride;
