@@ -385,13 +385,35 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
 // One pass over the state evaluates every term whose X bits lie in the tile:
 // <P> = sum_x conj(psi[x ^ m]) i^{#Y} (-1)^{popc(x & z)} psi[x] (real part).
 //
-// complex64 tiles of 2^13 amplitudes: thread t holds tile offsets t + 512 i
-// (i = 0..15) in registers, so a term's Z parity splits into a per-thread part
-// (tile bits 0..8 and the tile's global bits) and a per-slot part (tile bits
-// 9..12, applied by a butterfly with runtime signs); the partner amplitude of
-// slot i is buf[(t ^ x) ^ 512 i].  Per term and tile each thread forms an FP32
+// complex64 tiles of 2^13 amplitudes: thread t holds tile offsets
+// e + 2t + 1024 i (e = 0, 1; i = 0..7) in registers, read as 16-byte pairs, so
+// a term's Z parity splits into a per-thread part (tile bits 1..9 and the
+// tile's global bits) and a per-register part (tile bits 0, 10, 11, 12,
+// applied by a butterfly with runtime signs); the partner pair of pair i is
+// float4 (t ^ (x >> 1)) ^ 512 i, with its halves swapped when x has bit 0.  Per term and tile each thread forms an FP32
 // sum, the warp reduces it, and lane 0 adds it to an FP64 accumulator in shared
 // memory (FP64 arithmetic stays out of the per-thread loop).
+
+// w_r = Re (or Im) of conj(partner) * a_r for the 8 register pairs: partner
+// pair i is buf4[B ^ (i << 9)]; SWAP exchanges the pair's two amplitudes.
+template <bool SWAP, bool IM>
+__device__ __forceinline__ void exp_pairs(const float2 (&a)[kExpSlots], const float4* __restrict__ buf4,
+                                          int B, float (&w)[kExpSlots]) {
+#pragma unroll
+    for (int i = 0; i < kExpSlots / 2; ++i) {
+        const float4 q = buf4[B ^ (i << 9)];
+        const float2 b0 = SWAP ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+        const float2 b1 = SWAP ? make_float2(q.x, q.y) : make_float2(q.z, q.w);
+        const float2 a0 = a[2 * i], a1 = a[2 * i + 1];
+        if (!IM) {
+            w[2 * i] = fmaf(b0.x, a0.x, b0.y * a0.y);
+            w[2 * i + 1] = fmaf(b1.x, a1.x, b1.y * a1.y);
+        } else {
+            w[2 * i] = fmaf(b0.x, a0.y, -b0.y * a0.x);
+            w[2 * i + 1] = fmaf(b1.x, a1.y, -b1.y * a1.x);
+        }
+    }
+}
 
 // sum_i (-1)^{popc(i & zhi)} w_i as a 4-level butterfly over the slot bits,
 // sg[b] = (-1)^{bit b of zhi}: no branch on the Z pattern.
@@ -472,42 +494,45 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
         const long long gbase = tile_global_base(p, t % tc.tiles_per_item);
         if constexpr (std::is_same<C, float2>::value) {
             if (fast) {
+                // register r = e + 2 i holds tile offset e + 2 tid + 1024 i (pairs of
+                // adjacent amplitudes read as one 16-byte load)
+                const float4* buf4 = reinterpret_cast<const float4*>(buf);
                 float2 a[kExpSlots];
-                float pz[kExpSlots];   // |a_i|^2 for the Z-only terms
+                float pz[kExpSlots];   // |a_r|^2 for the Z-only terms
 #pragma unroll
-                for (int i = 0; i < kExpSlots; ++i) {
-                    a[i] = buf[tid + kExpThreads * i];
-                    pz[i] = fmaf(a[i].x, a[i].x, a[i].y * a[i].y);
+                for (int i = 0; i < kExpSlots / 2; ++i) {
+                    const float4 q = buf4[tid + kExpThreads * i];
+                    a[2 * i] = make_float2(q.x, q.y);
+                    a[2 * i + 1] = make_float2(q.z, q.w);
                 }
+#pragma unroll
+                for (int r = 0; r < kExpSlots; ++r) pz[r] = fmaf(a[r].x, a[r].x, a[r].y * a[r].y);
 #pragma unroll 1
                 for (int j = 0; j < ep.nterms; ++j) {
                     const ExpTerm T = sterm[j];
+                    // register bits: tile bit 0, then tile bits 10, 11, 12
                     float sg[4];
+                    sg[0] = (T.zm_tile & 1) ? -1.f : 1.f;
 #pragma unroll
-                    for (int bb = 0; bb < 4; ++bb) sg[bb] = ((T.zm_tile >> (9 + bb)) & 1) ? -1.f : 1.f;
+                    for (int bb = 1; bb < 4; ++bb) sg[bb] = ((T.zm_tile >> (9 + bb)) & 1) ? -1.f : 1.f;
                     float w[kExpSlots];
                     if (T.xm_tile == 0) {
 #pragma unroll
-                        for (int i = 0; i < kExpSlots; ++i) w[i] = pz[i];
+                        for (int r = 0; r < kExpSlots; ++r) w[r] = pz[r];
                     } else {
-                        // partner of slot i: tile offset (tid ^ xm) ^ 512 i
-                        if (T.ny & 1) {   // Im(conj(b) a)
-#pragma unroll
-                            for (int i = 0; i < kExpSlots; ++i) {
-                                const float2 b = buf[(tid ^ (int)T.xm_tile) ^ (i << 9)];
-                                w[i] = fmaf(b.x, a[i].y, -b.y * a[i].x);
-                            }
-                        } else {          // Re(conj(b) a)
-#pragma unroll
-                            for (int i = 0; i < kExpSlots; ++i) {
-                                const float2 b = buf[(tid ^ (int)T.xm_tile) ^ (i << 9)];
-                                w[i] = fmaf(b.x, a[i].x, b.y * a[i].y);
-                            }
+                        // partner pair of register pair i: float4 (tid ^ (x >> 1)) ^ 512 i;
+                        // x bit 0 swaps the two amplitudes of the pair
+                        const int B = tid ^ (int)(T.xm_tile >> 1);
+                        switch ((T.xm_tile & 1) | ((T.ny & 1) << 1)) {
+                        case 0: exp_pairs<false, false>(a, buf4, B, w); break;
+                        case 1: exp_pairs<true, false>(a, buf4, B, w); break;
+                        case 2: exp_pairs<false, true>(a, buf4, B, w); break;
+                        default: exp_pairs<true, true>(a, buf4, B, w); break;
                         }
                     }
                     float v = exp_butterfly(w, sg);
                     // per-thread Z parity, and Re(i^ny s): ny = 1, 2 flip the sign
-                    const int flip = (__popc((unsigned)tid & T.zm_tile & (kExpThreads - 1)) +
+                    const int flip = (__popc(((unsigned)tid << 1) & T.zm_tile & 0x3feu) +
                                       __popcll((unsigned long long)gbase & T.zm_glob) +
                                       ((T.ny & 3) == 1 || (T.ny & 3) == 2)) & 1;
                     v = flip ? -v : v;

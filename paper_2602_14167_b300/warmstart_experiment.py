@@ -23,7 +23,7 @@ import numpy as np
 import torch
 
 from . import tcng as T  # noqa: F401  (loads the library: fails loudly without it)
-from .warmstart import MLP, RaggedVQE, features, predict_init, steps_to_reach, targets_for
+from .warmstart import MLP, RaggedVQE, features, predict_init, targets_for
 
 
 def run(train=1024, held=32, restarts=16, n_min=14, n_max=20, layers=12, steps=200, lr=0.05,
@@ -36,14 +36,13 @@ def run(train=1024, held=32, restarts=16, n_min=14, n_max=20, layers=12, steps=2
     common = np.random.default_rng(seed + 5).uniform(-0.3, 0.3, 3 * n_max * layers)
 
     # 1. targets: converged angles from the common start, in chunks of `chunk` chains
-    thetas, final_e = [], []
+    thetas = []
     for c0 in range(0, train, chunk):
         part = tr[c0:c0 + chunk]
         rv = RaggedVQE(part, gen.chain_terms, layers=layers)
         th0 = [common[:3 * c["n"] * layers] for c in part]
-        th, hist = rv.optimize(rv.pack(th0), steps=steps, lr=lr)
+        th, _ = rv.optimize(rv.pack(th0), steps=steps, lr=lr)
         thetas += rv.unpack(th)
-        final_e.append(hist[-1].cpu().numpy())
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
 
