@@ -355,10 +355,9 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
             for (int i = tid; i < p.mat_count; i += blockDim.x) mats[i] = src[i];
             cur_item = item;
         }
-        const bool ok = mbar_wait_bounded(&bars[b], (uint32_t)((it / tc.nbuf) & 1), err);
-        if (!ok) s_abort = 1;
-        __syncthreads();
-        if (s_abort) break;
+        // no CTA barrier per tile: every thread waits for the tile itself, and each
+        // warp releases the buffer on its own (warp 0 refills it once all have)
+        if (!mbar_wait_bounded(&bars[b], (uint32_t)((it / tc.nbuf) & 1), err)) s_abort = 1;
         const long long gbase = tile_global_base(p, t % tc.tiles_per_item);
         for (int s = 0; s < p.stage_count; ++s) {
             const DevStage st = stages[p.stage_begin + s];
@@ -440,6 +439,7 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
     const int tile_elems = 1 << p.m;
     C* bufs = reinterpret_cast<C*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     uint64_t* bars = reinterpret_cast<uint64_t*>(bufs + (long long)tc.nbuf * tile_elems);
+    uint64_t* ebars = bars + tc.nbuf;   // buffer released by every warp
     __shared__ double red[32][kExpTermsPerPass];
     __shared__ ExpTerm sterm[kExpTermsPerPass];   // the pass's terms, read per tile
     __shared__ int s_abort;
@@ -447,8 +447,12 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
     const int item = blockIdx.y;
     for (int i = tid; i < 32 * kExpTermsPerPass; i += blockDim.x) (&red[0][0])[i] = 0.0;
     if (tid < ep.nterms) sterm[tid] = ep.t[tid];
+    const int nwarps = (int)(blockDim.x >> 5);
     if (tid == 0) {
-        for (int i = 0; i < tc.nbuf; ++i) mbar_init(&bars[i], 1);
+        for (int i = 0; i < tc.nbuf; ++i) {
+            mbar_init(&bars[i], 1);
+            mbar_init(&ebars[i], (uint32_t)nwarps);
+        }
         fence_mbar_init();
         s_abort = 0;
     }
@@ -487,10 +491,9 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
     for (long long t = first; t < t1; t += stride, ++it) {
         const int b = it % tc.nbuf;
         const C* buf = bufs + (long long)b * tile_elems;
-        const bool ok = mbar_wait_bounded(&bars[b], (uint32_t)((it / tc.nbuf) & 1), err);
-        if (!ok) s_abort = 1;
-        __syncthreads();
-        if (s_abort) break;
+        // no CTA barrier per tile: every thread waits for the tile itself, and each
+        // warp releases the buffer on its own (warp 0 refills it once all have)
+        if (!mbar_wait_bounded(&bars[b], (uint32_t)((it / tc.nbuf) & 1), err)) s_abort = 1;
         const long long gbase = tile_global_base(p, t % tc.tiles_per_item);
         if constexpr (std::is_same<C, float2>::value) {
             if (fast) {
@@ -575,11 +578,22 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
             }
         }
         }
-        __syncthreads();  // everyone done reading buf before it is refilled
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ebars[b]);   // this warp is done with buf
         if (warp == 0) {
             const long long tn = t + (long long)tc.nbuf * stride;
-            if (tn < t1) issue_tile_load(state, item_off, p, tc, tn, bufs + (long long)b * tile_elems,
-                                         &bars[b], lane, tma);
+            if (tn < t1) {
+                if (!mbar_wait_bounded(&ebars[b], (uint32_t)((it / tc.nbuf) & 1), err)) s_abort = 1;
+                __syncwarp();
+                issue_tile_load(state, item_off, p, tc, tn, bufs + (long long)b * tile_elems, &bars[b], lane, tma);
+            }
+        }
+        if (s_abort) break;
+    }
+    if (s_abort && tid == 0) {   // drain loads still in flight before the shared memory goes away
+        for (int i = 0; i < tc.nbuf; ++i) {
+            const long long ti = first + (long long)(it + 1 + i) * stride;
+            if (ti < t1) mbar_wait_bounded(&bars[(it + 1 + i) % tc.nbuf], (uint32_t)(((it + 1 + i) / tc.nbuf) & 1), err);
         }
     }
     // deterministic block reduction: warp tree, then warps in order
@@ -821,7 +835,7 @@ cudaError_t launch_expect_pass(const C* state, const long long* item_off, int it
                                const DevPass& p, const ExpPass& ep, double* partial, int n_out,
                                int nblk, unsigned* err, cudaStream_t s, const TmaTile* tma) {
     const int nbuf = 3;
-    const size_t smem = 128 + (size_t)nbuf * (sizeof(C) << p.m) + 8 * nbuf;
+    const size_t smem = 128 + (size_t)nbuf * (sizeof(C) << p.m) + 16 * nbuf;
     static bool done = false;
     static size_t lim = 0;
     if (smem > dyn_smem_limit(expect_pass_kernel<C>, &done, &lim)) return cudaErrorInvalidConfiguration;
