@@ -355,9 +355,10 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
             for (int i = tid; i < p.mat_count; i += blockDim.x) mats[i] = src[i];
             cur_item = item;
         }
-        // no CTA barrier per tile: every thread waits for the tile itself, and each
-        // warp releases the buffer on its own (warp 0 refills it once all have)
-        if (!mbar_wait_bounded(&bars[b], (uint32_t)((it / tc.nbuf) & 1), err)) s_abort = 1;
+        const bool ok = mbar_wait_bounded(&bars[b], (uint32_t)((it / tc.nbuf) & 1), err);
+        if (!ok) s_abort = 1;
+        __syncthreads();   // also orders the matrix window reload above before the stages
+        if (s_abort) break;
         const long long gbase = tile_global_base(p, t % tc.tiles_per_item);
         for (int s = 0; s < p.stage_count; ++s) {
             const DevStage st = stages[p.stage_begin + s];
@@ -389,9 +390,12 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
 // a term's Z parity splits into a per-thread part (tile bits 1..9 and the
 // tile's global bits) and a per-register part (tile bits 0, 10, 11, 12,
 // applied by a butterfly with runtime signs); the partner pair of pair i is
-// float4 (t ^ (x >> 1)) ^ 512 i, with its halves swapped when x has bit 0.  Per term and tile each thread forms an FP32
-// sum, the warp reduces it, and lane 0 adds it to an FP64 accumulator in shared
-// memory (FP64 arithmetic stays out of the per-thread loop).
+// float4 (t ^ (x >> 1)) ^ 512 i, with its halves swapped when x has bit 0.
+// Each thread keeps one FP32 sum per term in a register (the term loop is
+// unrolled so the index is static) and every 64 tiles the warp folds them into
+// FP64 sums in shared memory: FP64 arithmetic stays out of the per-tile loop.
+// The tile buffers form a ring: each warp releases a buffer through an
+// mbarrier, and warp 0 refills it once every warp has.
 
 // w_r = Re (or Im) of conj(partner) * a_r for the 8 register pairs: partner
 // pair i is buf4[B ^ (i << 9)]; SWAP exchanges the pair's two amplitudes.
@@ -416,17 +420,26 @@ __device__ __forceinline__ void exp_pairs(const float2 (&a)[kExpSlots], const fl
 
 // sum_i (-1)^{popc(i & zhi)} w_i as a 4-level butterfly over the slot bits,
 // sg[b] = (-1)^{bit b of zhi}: no branch on the Z pattern.
-__device__ __forceinline__ float exp_butterfly(float (&w)[kExpSlots], const float (&sg)[4]) {
+__device__ __forceinline__ float exp_butterfly(const float (&w)[kExpSlots], const float4 sg) {
+    float u[8], v[4];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) w[k] = fmaf(sg[0], w[2 * k + 1], w[2 * k]);
+    for (int k = 0; k < 8; ++k) u[k] = fmaf(sg.x, w[2 * k + 1], w[2 * k]);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) w[k] = fmaf(sg[1], w[2 * k + 1], w[2 * k]);
-#pragma unroll
-    for (int k = 0; k < 2; ++k) w[k] = fmaf(sg[2], w[2 * k + 1], w[2 * k]);
-    return fmaf(sg[3], w[1], w[0]);
+    for (int k = 0; k < 4; ++k) v[k] = fmaf(sg.y, u[2 * k + 1], u[2 * k]);
+    return fmaf(sg.w, fmaf(sg.z, v[3], v[2]), fmaf(sg.z, v[1], v[0]));
 }
 
-template <typename C>
+// A term of a complex64 fast-path pass, prepared once per CTA.
+struct ExpTermSm {
+    float4 sg;          // (-1)^{z bit} for register bits: tile bits 0, 10, 11, 12
+    uint64_t zg;        // Z mask on global bits outside the tile
+    uint32_t xm;        // X mask in tile bits
+    int32_t var;        // 0: Z only; 1 + (x bit 0) + 2 (ny odd): partner variant
+    int32_t flip0;      // Re(i^ny s) = -s for ny = 1, 2
+    int32_t pad;
+};
+
+template <typename C, bool FAST>
 __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict__ state,
                                                           const long long* __restrict__ item_off,
                                                           const __grid_constant__ DevPass p,
@@ -442,11 +455,29 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
     uint64_t* ebars = bars + tc.nbuf;   // buffer released by every warp
     __shared__ double red[32][kExpTermsPerPass];
     __shared__ ExpTerm sterm[kExpTermsPerPass];   // the pass's terms, read per tile
+    __shared__ ExpTermSm sx[kExpTermsPerPass];
     __shared__ int s_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int item = blockIdx.y;
     for (int i = tid; i < 32 * kExpTermsPerPass; i += blockDim.x) (&red[0][0])[i] = 0.0;
-    if (tid < ep.nterms) sterm[tid] = ep.t[tid];
+    if (tid < ep.nterms) {
+        const ExpTerm T = ep.t[tid];
+        sterm[tid] = T;
+        ExpTermSm x;
+        x.sg = make_float4((T.zm_tile & 1) ? -1.f : 1.f, ((T.zm_tile >> 10) & 1) ? -1.f : 1.f,
+                           ((T.zm_tile >> 11) & 1) ? -1.f : 1.f, ((T.zm_tile >> 12) & 1) ? -1.f : 1.f);
+        x.zg = T.zm_glob;
+        x.xm = T.xm_tile;
+        x.var = T.xm_tile == 0 ? 0 : 1 + (int)(T.xm_tile & 1) + 2 * (T.ny & 1);
+        x.flip0 = ((T.ny & 3) == 1 || (T.ny & 3) == 2) ? 1 : 0;
+        x.pad = 0;
+        sx[tid] = x;
+    }
+    // per-thread Z parity of every term over tile bits 1..9 (fast-path layout)
+    uint32_t tpar = 0;
+    if constexpr (FAST)
+        for (int j = 0; j < ep.nterms; ++j)
+            tpar |= (uint32_t)(__popc(((unsigned)tid << 1) & ep.t[j].zm_tile & 0x3feu) & 1) << j;
     const int nwarps = (int)(blockDim.x >> 5);
     if (tid == 0) {
         for (int i = 0; i < tc.nbuf; ++i) {
@@ -466,8 +497,8 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
             const long long t = first + i * stride;
             if (t < t1) issue_tile_load(state, item_off, p, tc, t, bufs + (long long)i * tile_elems, &bars[i], lane, tma);
         }
-    const bool fast = std::is_same<C, float2>::value && tile_elems == kExpThreads * kExpSlots &&
-                      blockDim.x == kExpThreads;
+    // FAST: complex64, 2^13 tiles, kExpThreads threads (chosen by the launcher)
+    constexpr bool fast = FAST && std::is_same<C, float2>::value;
     double acc[kExpTermsPerPass];
     float acc32[kExpTermsPerPass];
 #pragma unroll
@@ -495,8 +526,8 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
         // warp releases the buffer on its own (warp 0 refills it once all have)
         if (!mbar_wait_bounded(&bars[b], (uint32_t)((it / tc.nbuf) & 1), err)) s_abort = 1;
         const long long gbase = tile_global_base(p, t % tc.tiles_per_item);
-        if constexpr (std::is_same<C, float2>::value) {
-            if (fast) {
+        if constexpr (fast) {
+            {
                 // register r = e + 2 i holds tile offset e + 2 tid + 1024 i (pairs of
                 // adjacent amplitudes read as one 16-byte load)
                 const float4* buf4 = reinterpret_cast<const float4*>(buf);
@@ -510,49 +541,36 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
                 }
 #pragma unroll
                 for (int r = 0; r < kExpSlots; ++r) pz[r] = fmaf(a[r].x, a[r].x, a[r].y * a[r].y);
-#pragma unroll 1
-                for (int j = 0; j < ep.nterms; ++j) {
-                    const ExpTerm T = sterm[j];
-                    // register bits: tile bit 0, then tile bits 10, 11, 12
-                    float sg[4];
-                    sg[0] = (T.zm_tile & 1) ? -1.f : 1.f;
+                const int nt = ep.nterms;
 #pragma unroll
-                    for (int bb = 1; bb < 4; ++bb) sg[bb] = ((T.zm_tile >> (9 + bb)) & 1) ? -1.f : 1.f;
-                    float w[kExpSlots];
-                    if (T.xm_tile == 0) {
-#pragma unroll
-                        for (int r = 0; r < kExpSlots; ++r) w[r] = pz[r];
-                    } else {
-                        // partner pair of register pair i: float4 (tid ^ (x >> 1)) ^ 512 i;
-                        // x bit 0 swaps the two amplitudes of the pair
-                        const int B = tid ^ (int)(T.xm_tile >> 1);
-                        switch ((T.xm_tile & 1) | ((T.ny & 1) << 1)) {
-                        case 0: exp_pairs<false, false>(a, buf4, B, w); break;
-                        case 1: exp_pairs<true, false>(a, buf4, B, w); break;
-                        case 2: exp_pairs<false, true>(a, buf4, B, w); break;
-                        default: exp_pairs<true, true>(a, buf4, B, w); break;
+                for (int j = 0; j < kExpTermsPerPass; ++j) {   // static j: acc32[j] is a register
+                    if (j >= nt) break;   // one jump past the unused terms
+                    {
+                        const ExpTermSm X = sx[j];
+                        float v;
+                        if (X.var == 0) {
+                            v = exp_butterfly(pz, X.sg);
+                        } else {
+                            // partner pair of register pair i: float4 (tid ^ (x >> 1)) ^ 512 i;
+                            // x bit 0 swaps the two amplitudes of the pair
+                            const int B = tid ^ (int)(X.xm >> 1);
+                            float w[kExpSlots];
+                            if (X.var == 1) exp_pairs<false, false>(a, buf4, B, w);
+                            else if (X.var == 2) exp_pairs<true, false>(a, buf4, B, w);
+                            else if (X.var == 3) exp_pairs<false, true>(a, buf4, B, w);
+                            else exp_pairs<true, true>(a, buf4, B, w);
+                            v = exp_butterfly(w, X.sg);
                         }
-                    }
-                    float v = exp_butterfly(w, sg);
-                    // per-thread Z parity, and Re(i^ny s): ny = 1, 2 flip the sign
-                    const int flip = (__popc(((unsigned)tid << 1) & T.zm_tile & 0x3feu) +
-                                      __popcll((unsigned long long)gbase & T.zm_glob) +
-                                      ((T.ny & 3) == 1 || (T.ny & 3) == 2)) & 1;
-                    v = flip ? -v : v;
-                    switch (j) {   // uniform branch: a static register per term
-#define TCNG_ACASE(q) case q: acc32[q] += v; break;
-                    TCNG_ACASE(0) TCNG_ACASE(1) TCNG_ACASE(2) TCNG_ACASE(3) TCNG_ACASE(4) TCNG_ACASE(5)
-                    TCNG_ACASE(6) TCNG_ACASE(7) TCNG_ACASE(8) TCNG_ACASE(9) TCNG_ACASE(10)
-                    TCNG_ACASE(11) TCNG_ACASE(12) TCNG_ACASE(13) TCNG_ACASE(14)
-                    default: acc32[15] += v; break;
-#undef TCNG_ACASE
+                        const int f = (int)((tpar >> j) ^ (uint32_t)__popcll((unsigned long long)gbase & X.zg) ^
+                                            (uint32_t)X.flip0) & 1;
+                        acc32[j] += f ? -v : v;
                     }
                 }
                 // every 64 tiles (and at the end) fold the FP32 sums into FP64
                 if ((it & 63) == 63 || t + stride >= t1) flush32();
             }
         }
-        if (!fast) {
+        if constexpr (!fast) {
 #pragma unroll
         for (int j = 0; j < kExpTermsPerPass; ++j) {
             if (j < ep.nterms) {
@@ -597,7 +615,7 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
         }
     }
     // deterministic block reduction: warp tree, then warps in order
-    if (!fast) {
+    if constexpr (!fast) {
 #pragma unroll
         for (int j = 0; j < kExpTermsPerPass; ++j) {
             double v = acc[j];
@@ -836,15 +854,23 @@ cudaError_t launch_expect_pass(const C* state, const long long* item_off, int it
                                int nblk, unsigned* err, cudaStream_t s, const TmaTile* tma) {
     const int nbuf = 3;
     const size_t smem = 128 + (size_t)nbuf * (sizeof(C) << p.m) + 16 * nbuf;
-    static bool done = false;
-    static size_t lim = 0;
-    if (smem > dyn_smem_limit(expect_pass_kernel<C>, &done, &lim)) return cudaErrorInvalidConfiguration;
     TileCtx tc = make_ctx(p, n, items, sizeof(C), nbuf);
-    const int threads = std::min(512, std::max(32, 1 << p.m));
     dim3 grid((unsigned)nblk, (unsigned)items);
     const TmaTile t0{};
-    expect_pass_kernel<C><<<grid, threads, smem, s>>>(state, item_off, p, ep, tc, partial, n_out, err,
-                                                      tma ? *tma : t0);
+    if (sizeof(C) == 8 && p.m == 13) {   // complex64 fast path: 512 threads x 16 amplitudes
+        auto kern = expect_pass_kernel<C, true>;
+        static bool done = false;
+        static size_t lim = 0;
+        if (smem > dyn_smem_limit(kern, &done, &lim)) return cudaErrorInvalidConfiguration;
+        kern<<<grid, kExpThreads, smem, s>>>(state, item_off, p, ep, tc, partial, n_out, err, tma ? *tma : t0);
+    } else {
+        auto kern = expect_pass_kernel<C, false>;
+        static bool done = false;
+        static size_t lim = 0;
+        if (smem > dyn_smem_limit(kern, &done, &lim)) return cudaErrorInvalidConfiguration;
+        const int threads = std::min(512, std::max(32, 1 << p.m));
+        kern<<<grid, threads, smem, s>>>(state, item_off, p, ep, tc, partial, n_out, err, tma ? *tma : t0);
+    }
     count_launch();
     return cudaGetLastError();
 }
