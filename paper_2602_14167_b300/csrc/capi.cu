@@ -562,8 +562,13 @@ static tcng_status expect_impl(const tcng_state* st, const tcng_pauli* terms, si
             cudaError_t e;
             // one tensor copy per tile where the pass's bit runs fit a tensor map
             TmaTile tma{};
-            if (items == 1 || tstride > 0)
-                tma = make_tma_tile(tbase, n, st->dt == TCNG_C64 ? 8 : 16, passes[i], items, tstride);
+            const int es = st->dt == TCNG_C64 ? 8 : 16;
+            if (items == 1 || tstride > 0) {
+                tma = make_tma_tile(tbase, n, es, passes[i], items, tstride);
+                if (!tma.rank)   // scattered gather bits: four chunks per gather4 copy
+                    tma = make_tma_gather4(tbase, st->off[st->groups.begin()->second.items[0]], n, es,
+                                           passes[i], items, tstride);
+            }
             ProfScope ps(st->dt == TCNG_C64 ? "expect_pass_c64" : "expect_pass_c128", s);
             if (st->dt == TCNG_C64)
                 e = launch_expect_pass<float2>(static_cast<const float2*>(st->buf), st->d_off, items, n,

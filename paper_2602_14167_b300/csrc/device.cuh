@@ -163,6 +163,16 @@ __device__ __forceinline__ void tma_load_tile(const TmaTile& t, void* dst, uint6
         break;
     }
 }
+// Four rows (r0..r3, one box each) of a 2D tensor map into consecutive shared memory.
+__device__ __forceinline__ void tma_gather4(const TmaTile& t, void* dst, uint64_t* bar, int r0, int r1, int r2,
+                                            int r3) {
+    const uint64_t map = reinterpret_cast<uint64_t>(&t.map);
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_u32(bar))
+        : "memory");
+}
 __device__ __forceinline__ void tma_store_tile(const TmaTile& t, const void* src, const int (&c)[5]) {
     const uint64_t map = reinterpret_cast<uint64_t>(&t.map);
     const uint32_t sp = smem_u32(src);

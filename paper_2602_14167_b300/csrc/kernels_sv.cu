@@ -285,6 +285,22 @@ __device__ __forceinline__ void issue_tile_load(const C* state, const long long*
         return;
     }
     const long long base = tile_global_base(p, tile % tc.tiles_per_item);
+    if (tma.g4) {   // four rows of 2^g4rb amplitudes per tile::gather4 copy, in tile order
+        const long long b0 = item_off[item] - tma.g4base + base;
+        const int rb = tma.g4rb, sub = p.chunk - rb;   // rows per chunk: 2^sub
+        if (lane == 0) mbar_arrive_expect_tx(bar, tc.tile_bytes);
+        __syncwarp();
+        for (int k = lane; k < ((1 << p.m) >> (rb + 2)); k += 32) {
+            int r[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = 4 * k + q;   // chunk row >> sub, piece row & (2^sub - 1)
+                r[q] = (int)((b0 + chunk_offset(p, row >> sub) + ((long long)(row & ((1 << sub) - 1)) << rb)) >> rb);
+            }
+            tma_gather4(tma, buf + ((long long)(4 * k) << rb), bar, r[0], r[1], r[2], r[3]);
+        }
+        return;
+    }
     const C* src = state + item_off[item] + base;
     if (lane == 0) mbar_arrive_expect_tx(bar, tc.tile_bytes);
     __syncwarp();

@@ -33,17 +33,26 @@ struct ExpPass {
 // index are box-1 dimensions addressed by coordinates.
 struct alignas(64) TmaTile {
     CUtensorMap map;
-    int32_t rank;              // 0: not usable (fall back to per-chunk bulk copies)
+    int32_t rank;              // 0: no tile map (gather4 map or per-chunk bulk copies)
     int8_t kind[5];            // 0 tile run (coordinate 0), 1 rest run, 2 item
     int8_t shift[5];           // rest run: first bit of the tile number it takes
     int8_t len[5];             // rest run: number of bits
-    int8_t pad;
+    int8_t g4;                 // rank 0: map is a 2D [rows x 2^g4rb] gather4 map
+    long long g4base;          // gather4: element offset of the map's first row
+    int32_t g4rb;              // gather4: log2 amplitudes per row (<= chunk)
 };
 
 // Build the tensor map of a pass (returns rank 0 if the pass needs > 5 dims or
 // the encoder rejects it).  items > 1 needs equally spaced items (stride bytes).
 TmaTile make_tma_tile(void* base, int n, int elem_bytes, const DevPass& p, int items,
                       long long item_stride_bytes);
+// A pass's tiles as rows of one chunk (2^chunk amplitudes, at most 256 8-byte
+// elements), four arbitrary rows per tile::gather4 copy (for passes whose bit
+// runs need more than five tensor dimensions).  base_elems: element offset of
+// base within the state buffer.  Returns g4 = 0 if the pass does not fit
+// (larger chunks, fewer than 4 chunks per tile, unequal item spacing).
+TmaTile make_tma_gather4(void* base, long long base_elems, int n, int elem_bytes, const DevPass& p,
+                         int items, long long item_stride_bytes);
 
 struct HTerm {
     uint64_t xm, zm;

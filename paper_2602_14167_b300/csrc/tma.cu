@@ -88,4 +88,32 @@ TmaTile make_tma_tile(void* base, int n, int elem_bytes, const DevPass& p, int i
     return t;
 }
 
+TmaTile make_tma_gather4(void* base, long long base_elems, int n, int elem_bytes, const DevPass& p,
+                         int items, long long item_stride_bytes) {
+    TmaTile t;
+    std::memset(&t, 0, sizeof t);
+    auto fn = encode_fn();
+    const int e = elem_bytes / 8;
+    // one chunk per row, at most 256 8-byte elements (measured: splitting larger
+    // chunks into several gathered rows is slower than their per-chunk bulk copies)
+    const int rb = p.chunk;
+    const long long row_elems = 1ll << rb;
+    if (!fn || row_elems * e > 256 || (p.m - rb) < 2) return t;
+    if (items > 1 && (item_stride_bytes <= 0 || item_stride_bytes % (row_elems * elem_bytes))) return t;
+    const long long span = (items > 1 ? (long long)(items - 1) * (item_stride_bytes / elem_bytes) : 0) + (1ll << n);
+    cuuint64_t gdim[2] = {(cuuint64_t)(row_elems * e), (cuuint64_t)(span / row_elems)};
+    cuuint64_t gstride[1] = {(cuuint64_t)(row_elems * elem_bytes)};
+    cuuint32_t box[2] = {(cuuint32_t)(row_elems * e), 1};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(&t.map, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, base, gdim, gstride, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return TmaTile{};
+    t.rank = 0;
+    t.g4 = 1;
+    t.g4base = base_elems;
+    t.g4rb = rb;
+    return t;
+}
+
 }  // namespace tcng
