@@ -348,7 +348,8 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                 tc_fence_after();
                 const int slot = a.grouped ? s : (int)(q % TS_NB);
                 const uint32_t wpar = a.grouped ? 0u : (uint32_t)((q / TS_NB) & 1);
-                if (mbar_wait_bounded(&w_bar[slot], wpar, a.err)) {
+                // grouped: W stays resident, so only the first tile waits for it
+                if ((a.grouped && it > 0) || mbar_wait_bounded(&w_bar[slot], wpar, a.err)) {
                     // W slot = [W_hi (32 rows) | W_lo (32 rows)]: one N=64 MMA gives
                     // a_hi*w_hi in D[0:32] and a_hi*w_lo in D[32:64]; a_lo*w_hi joins
                     // D[32:64]; the two halves are added in registers afterwards
