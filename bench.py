@@ -40,6 +40,10 @@ REF_GATES = 4       # gates per reference step
 
 
 PASS_KERNELS = ("pass_kernel_c64", "pass_tcs_kernel_c64")
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one 28-qubit
+# launch from an ncu capture of this kernel, scaled by the state size; a kernel
+# changed since its capture has no entry.
+TRAFFIC_28Q = {"pass_tcs_kernel_c64": 2.147555e9 + 2.087492e9}
 
 
 def workload(n=N_QUBITS, depth=DEPTH):
@@ -287,7 +291,8 @@ def run_gpu(args):
                       "l2": "inputs larger than L2 (32 GiB state), no flush",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": (achieved / peak) if achieved else None, "traffic": None,
+                        "frac": (achieved / peak) if achieved else None,
+                        "traffic": (TRAFFIC_28Q[pk_name] * 2.0 ** (NQ - 28)) if pk_name in TRAFFIC_28Q else None,
                         "kernel": pk_name, "peak_kind": peak_kind,
                         "algorithmic_bytes_per_launch": 2 * S,
                         "avg_launch_ms": avg_pass_ms},
