@@ -63,7 +63,7 @@ static AdjLayout* get_layout(const tcng_problem* probs, int n_probs, const int* 
                              int batch, tcng_dtype dt, const long long* psi_off) {
     const PlanOptions base = plan_options(dt, true);
     const int res_bits = dt == TCNG_C64 ? 13 : 12;
-    const int stream_tile = res_bits - 1;
+    const int stream_tile = res_bits;   // streamed psi and lambda tiles use the two resident buffers
     uint64_t h = 1469598103934665603ULL;
     std::vector<uint64_t> shash(n_probs);
     for (int s = 0; s < n_probs; ++s) {

@@ -13,7 +13,8 @@
 // Each CTA pops items from a global counter (largest n first).  States of up to
 // 2^13 (complex64) / 2^12 (complex128) amplitudes live in shared memory for the
 // whole item ("resident"); larger ones stream through per-CTA global scratch in
-// 2^12 / 2^11-amplitude tiles with bulk asynchronous copies.
+// tiles of the same size (psi and lambda tiles in the two resident buffers)
+// with bulk asynchronous copies.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -208,8 +209,13 @@ __device__ void tile_store(const DevPass& p, long long tile, C* const* gptr, C* 
 }
 
 // ------------------------------------------------------------------ kernel --
+// complex64: 512 threads, one per register group of a 2^13 tile (128 registers);
+// complex128 keeps 256 threads (its FP64 stages spill heavily at 128 registers).
 template <typename C>
-__global__ void __launch_bounds__(256, 1) adjoint_kernel(AdjArgs a) {
+constexpr int adjoint_threads() { return sizeof(C) == 8 ? 512 : 256; }
+
+template <typename C>
+__global__ void __launch_bounds__(adjoint_threads<C>(), 1) adjoint_kernel(AdjArgs a) {
     using T = typename Real<C>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x;
@@ -296,11 +302,11 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(AdjArgs a) {
         }
         // ---------------- lambda = H psi, E = Re <psi|lambda> ----------------
         // Resident: psi is in shared memory.  Streamed: psi is read tile by tile
-        // (2^(res_bits-1) contiguous amplitudes) into shared memory; partners
+        // (2^res_bits contiguous amplitudes) into shared memory; partners
         // outside the tile come from global memory.
         double e_part = 0.0;
         {
-            const int tb = resident ? n : a.res_bits - 1;
+            const int tb = resident ? n : a.res_bits;
             const long long tn = 1ll << tb;
             const long long ntile = resident ? 1 : (N >> tb);
             for (long long t = 0; t < ntile; ++t) {
@@ -362,7 +368,7 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(AdjArgs a) {
                 __syncthreads();
                 const long long ntiles = resident ? 1 : (1ll << (n - P.m));
                 C* tp = sp;
-                C* tl = resident ? sl : sp + (1 << P.m);
+                C* tl = sl;
                 for (long long t = 0; t < ntiles; ++t) {
                     if (!resident) {
                         C* gptr[2] = {gp, gl};
@@ -435,7 +441,7 @@ cudaError_t launch_adjoint(const AdjArgs& a, int grid, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         set_bytes = smem;
     }
-    kern<<<grid, 256, smem, s>>>(a);
+    kern<<<grid, adjoint_threads<C>(), smem, s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
