@@ -192,6 +192,8 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
     float2* bufs = reinterpret_cast<float2*>(base + TS_NB * TS_W_BYTES);    // TS_NBUF tiles
     constexpr int tile_elems = 1 << TS_TILE_BITS;
     __shared__ uint64_t tile_bar[TS_NBUF], w_bar[TS_NB], mma_bar[4];
+    __shared__ uint64_t done_bar[TS_NBUF];   // grouped: slices 1..3 finished a tile
+    __shared__ uint64_t stag_bar;            // grouped: slices 2, 3 started (once)
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
     __shared__ float2 red[TS_THREADS / 32];
@@ -236,6 +238,8 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
         for (int i = 0; i < TS_NBUF; ++i) mbar_init(&tile_bar[i], 1);
         for (int i = 0; i < TS_NB; ++i) mbar_init(&w_bar[i], 1);
         for (int i = 0; i < 4; ++i) mbar_init(&mma_bar[i], 1);
+        for (int i = 0; i < TS_NBUF; ++i) mbar_init(&done_bar[i], 3);
+        mbar_init(&stag_bar, 2);
         fence_mbar_init();
         s_abort = 0;
     }
@@ -285,9 +289,28 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
     for (long long t = first; t < a.total_tiles; t += stride, ++it) {
         const int b = (int)(it % TS_NBUF);
         float2* buf = bufs + (size_t)b * tile_elems;
-        if (!mbar_wait_bounded(&tile_bar[b], (uint32_t)((it / TS_NBUF) & 1), a.err)) s_abort = 1;
-        __syncthreads();
-        if (s_abort) break;
+        const bool tile_ok = mbar_wait_bounded(&tile_bar[b], (uint32_t)((it / TS_NBUF) & 1), a.err);
+        if (a.grouped) {
+            // slices run through the tiles independently: a slice-uniform abort check
+            uint32_t stop;
+            asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+                         "bar.red.or.pred p, %2, 128, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                         : "=r"(stop)
+                         : "r"((uint32_t)(!tile_ok || s_abort)), "r"(1 + slice)
+                         : "memory");
+            if (stop) {
+                s_abort = 1;
+                break;
+            }
+            // once: slices 0 and 1 start after 2 and 3 have issued their first MMAs, so
+            // the two pairs stay half a stage apart (one pair's shared-memory phases
+            // overlap the other's tensor-core phase)
+            if (it == 0 && slice < 2) mbar_wait_bounded(&stag_bar, 0u, a.err);
+        } else {
+            if (!tile_ok) s_abort = 1;
+            __syncthreads();
+            if (s_abort) break;
+        }
         float nin = 0.f;   // this thread's share of the tile norm before the pass
         for (int s = 0; s < nst; ++s, ++q) {
             if (!a.grouped && tid == 0 && w_issued < total_q && w_issued < q + TS_NB) issue_w();
@@ -363,6 +386,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                     s_abort = 1;
                 }
                 tc_commit(&mma_bar[slice]);
+                if (a.grouped && it == 0 && s == 0 && slice >= 2) mbar_arrive(&stag_bar);
             }
             if (!mbar_wait_bounded(&mma_bar[slice], (uint32_t)(q & 1), a.err)) s_abort = 1;
             tc_fence_after();
@@ -419,9 +443,17 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
             tc_fence_after();
             if (!a.grouped && s_abort) break;
         }
-        if (s_abort) break;
-        fence_proxy_async_smem();
-        __syncthreads();
+        fence_proxy_async_smem();   // this thread's tile writes before the tensor store reads them
+        if (a.grouped) {
+            // slices 1..3 report; thread 0 (slice 0) stores once all four are done
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + slice), "r"(128) : "memory");
+            if ((tid & 127) == 0 && slice > 0) mbar_arrive(&done_bar[b]);
+            if (tid == 0 && !mbar_wait_bounded(&done_bar[b], (uint32_t)((it / TS_NBUF) & 1), a.err))
+                s_abort = 1;
+        } else {
+            if (s_abort) break;
+            __syncthreads();
+        }
         if (tid == 0) {
             int c[5];
             tma_tile_coords(tma, t % a.tiles_per_item, (int)(t / a.tiles_per_item), c);
