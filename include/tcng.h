@@ -134,8 +134,10 @@ tcng_status tcng_apply_circuit(tcng_state* st, const tcng_gate* ops, size_t n_op
  * expectation_ps, Sec. I.B; coefficients are NOT applied).
  *   terms     host array [n_terms <= 4096] of Pauli strings (masks < 2^n);
  *   out_dev   device double [batch][n_terms].
- * All items must have the same n.  Sums accumulate in FP64 in a fixed order
- * (bitwise reproducible).  Errors: EINVAL, ENOMEM, EUNSUPPORTED (ragged), ECUDA.
+ * All items must have the same n.  A term may have at most tile_bits - 1 X/Y
+ * factors above qubit 0 (12 for complex64, 11 for complex128 at the default
+ * tile bits), else EINVAL.  Sums accumulate in FP64 in a fixed order (bitwise
+ * reproducible).  Errors: EINVAL, ENOMEM, EUNSUPPORTED (ragged), ECUDA.
  */
 tcng_status tcng_expect_pauli(const tcng_state* st, const tcng_pauli* terms, size_t n_terms,
                               double* out_dev, void* stream);

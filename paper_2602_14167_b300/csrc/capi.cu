@@ -303,12 +303,30 @@ void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
         if ((terms[t].xmask & ~lim) || (terms[t].zmask & ~lim))
             throw std::invalid_argument("Pauli mask outside the register");
     m = std::min(m, n);
-    low = std::min(low, m);
-    const int gmax = m - low;
-    const uint64_t lowmask = (low >= 64) ? ~0ULL : ((1ULL << low) - 1);
+    const int low0 = std::min(low, m);
+    auto mask_below = [](int b) { return b >= 64 ? ~0ULL : ((1ULL << b) - 1); };
+    // a tile keeps at least its lowest qubit contiguous (16-byte copies), so a term
+    // may have at most m - 1 X/Y factors above qubit 0
+    if (n > m)
+        for (size_t t = 0; t < T; ++t)
+            if (__builtin_popcountll(terms[t].xmask & ~1ULL) > m - 1)
+                throw std::invalid_argument("Pauli term " + std::to_string(t) + ": more than " +
+                                            std::to_string(m - 1) + " X/Y factors above qubit 0");
     std::vector<char> done(T, 0);
     size_t left = T;
     while (left) {
+        // contiguous low bits of this pass: the default, or fewer when the first open
+        // term has more X bits above them than the tile can gather
+        int lowp = low0;
+        if (n > m)
+            for (size_t t = 0; t < T; ++t)
+                if (!done[t]) {
+                    while (lowp > 1 && __builtin_popcountll(terms[t].xmask & ~mask_below(lowp)) > m - lowp)
+                        --lowp;
+                    break;
+                }
+        const int gmax = m - lowp;
+        const uint64_t lowmask = mask_below(lowp);
         uint64_t G = 0;
         ExpPass ep{};
         std::vector<int> sel;
@@ -319,12 +337,13 @@ void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
             G |= hi;
             sel.push_back((int)t);
         }
+        if (sel.empty()) throw std::logic_error("expectation planner: no term fits a tile");
         uint64_t S;
         if (n <= m) {
             S = lim;
         } else {
             S = lowmask | G;
-            for (int q = low; q < n && __builtin_popcountll(S) < m; ++q) S |= 1ULL << q;
+            for (int q = lowp; q < n && __builtin_popcountll(S) < m; ++q) S |= 1ULL << q;
         }
         DevPass dp{};
         dp.m = __builtin_popcountll(S);

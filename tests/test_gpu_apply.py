@@ -161,6 +161,38 @@ def test_expectations_random_strings(T, n, dtype):
     assert np.max(np.abs(vals - vref)) < (1e-6 if dtype == "c64" else 1e-12)
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_expectations_scattered_gathers(T, dtype):
+    """Terms whose X bits scatter over the high qubits: tiles that need more than five
+    tensor-map dimensions (gather4 rows for 2^7 chunks, bulk copies for wider chunks)."""
+    n = 20
+    psi0 = gen.random_state(n, seed=21)
+    from paper_2602_14167_b300 import StateBatch
+    from workloads import pauli_terms
+    st = StateBatch(n, dtype=dtype)
+    st.amplitudes(0).copy_(torch.tensor(psi0, dtype=st.cdtype, device="cuda"))
+    strings = pauli_terms([{8: "X", 10: "X", 12: "Y", 14: "X", 16: "X", 18: "Y"},   # 2^7 chunk rows
+                           {8: "X", 11: "Y", 14: "X", 17: "Z", 19: "X"},
+                           {8: "Y", 11: "X", 14: "Y", 17: "X", 19: "Y", 2: "Z"},
+                           {9: "X", 12: "X", 15: "Y", 18: "X", 0: "Y"},
+                           {10: "X", 16: "Y", 19: "Z", 3: "X"}])
+    vals = st.expect(strings)[0].cpu().numpy()
+    ref_psi = st.amplitudes(0).cpu().numpy().astype(np.complex128)
+    vref = sv.expect(n, ref_psi, strings).real
+    assert np.max(np.abs(vals - vref)) < (1e-6 if dtype == "c64" else 1e-12)
+
+
+def test_expectation_term_wider_than_a_tile_is_rejected(T):
+    from paper_2602_14167_b300 import StateBatch
+    from workloads import pauli_terms
+    st = StateBatch(16, dtype="c128")   # 12 tile bits: at most 11 X/Y factors above qubit 0
+    with pytest.raises(T.TcngError):
+        st.expect(pauli_terms([{q: "X" for q in range(1, 13)}]))
+    T.tcng_sync_status()
+    vals = st.expect(pauli_terms([{q: "X" for q in range(1, 12)}]))   # 11 fit
+    assert vals.shape == (1, 1)
+
+
 def test_energy_per_item_coefficients(T):
     n, B = 12, 4
     b = gen.tfim_batch(n, B, layers=2, seed=3)
@@ -268,6 +300,29 @@ def test_tensor_core_stages_batch_per_item_params(T):
     assert launches > 0
     for b in range(B):
         check_state(st.amplitudes(b).cpu().numpy(), sv.apply(n, g, p, th[b]), "c64")
+
+
+def test_tensor_core_stages_shared_params_batch(T):
+    """Several items, one parameter set: every item runs the same W operands."""
+    n, B = 15, 4
+    c, th = gen.su4_brickwork(n, 5, "RZ", seed=3)
+    g, p = c.to_ir()
+    from paper_2602_14167_b300 import StateBatch
+    T.tcng_set_option(T.OPT_TENSOR_CORES, 1)
+    st = StateBatch(n, batch=B, dtype="c64")
+    prm = torch.tensor(th, dtype=torch.float64, device="cuda").reshape(1, -1).expand(B, -1).contiguous()
+    st.apply(g, p, prm)
+    ref = sv.apply(n, g, p, th)
+    for b in range(B):
+        check_state(st.amplitudes(b).cpu().numpy(), ref, "c64")
+
+
+def test_tensor_core_option_values(T):
+    for v in (0, 1, 2):
+        T.tcng_set_option(T.OPT_TENSOR_CORES, v)
+        assert T.tcng_get_option(T.OPT_TENSOR_CORES) == v
+    with pytest.raises(T.TcngError):
+        T.tcng_set_option(T.OPT_TENSOR_CORES, 3)
 
 
 def test_tensor_core_stages_non_unitary_matrix(T):
