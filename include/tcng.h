@@ -170,6 +170,17 @@ tcng_status tcng_expect_pauli_noalloc(const void* psi_dev, int n, tcng_dtype dt,
                                       void* stream);
 
 /*
+ * tcng_expect_energy -- both of the above from one plan: out_dev[b][t] =
+ * <psi_b|P_t|psi_b> for every term and energy_dev[b] = sum_t c[b][t] out_dev[b][t]
+ * (coefficients as in tcng_energy; give a term coefficient 0 to report it without
+ * weighting it).  Planning all terms together packs them into fewer passes over
+ * the state than separate calls.  Errors: as tcng_expect_pauli.
+ */
+tcng_status tcng_expect_energy(const tcng_state* st, const tcng_pauli* terms, size_t n_terms,
+                               const double* coeffs_dev, double* out_dev, double* energy_dev,
+                               void* stream);
+
+/*
  * tcng_energy -- energy_dev[b] = sum_t c[b][t] <psi_b|P_t|psi_b>, the TFIM (or
  * any Pauli-sum) energy of Sec. I.B.  coeffs_dev: device double [batch][n_terms],
  * or NULL to use terms[t].coeff for every item.  Errors: as tcng_expect_pauli.

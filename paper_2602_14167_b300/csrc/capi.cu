@@ -312,6 +312,14 @@ void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
             if (__builtin_popcountll(terms[t].xmask & ~1ULL) > m - 1)
                 throw std::invalid_argument("Pauli term " + std::to_string(t) + ": more than " +
                                             std::to_string(m - 1) + " X/Y factors above qubit 0");
+    // most constrained terms first (most X bits above the default contiguous bits):
+    // the greedy packing then fills passes around them (results keep the input order)
+    std::vector<size_t> order(T);
+    for (size_t t = 0; t < T; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        return __builtin_popcountll(terms[a].xmask & ~mask_below(low0)) >
+               __builtin_popcountll(terms[b].xmask & ~mask_below(low0));
+    });
     std::vector<char> done(T, 0);
     size_t left = T;
     while (left) {
@@ -319,7 +327,7 @@ void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
         // term has more X bits above them than the tile can gather
         int lowp = low0;
         if (n > m)
-            for (size_t t = 0; t < T; ++t)
+            for (size_t t : order)
                 if (!done[t]) {
                     while (lowp > 1 && __builtin_popcountll(terms[t].xmask & ~mask_below(lowp)) > m - lowp)
                         --lowp;
@@ -330,7 +338,8 @@ void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
         uint64_t G = 0;
         ExpPass ep{};
         std::vector<int> sel;
-        for (size_t t = 0; t < T && (int)sel.size() < kExpTermsPerPass; ++t) {
+        for (size_t t : order) {
+            if ((int)sel.size() >= kExpTermsPerPass) break;
             if (done[t]) continue;
             const uint64_t hi = (n <= m) ? 0 : (terms[t].xmask & ~lowmask);
             if (__builtin_popcountll(G | hi) > gmax) continue;
@@ -609,6 +618,14 @@ tcng_status tcng_expect_pauli(const tcng_state* st, const tcng_pauli* terms, siz
                               double* out_dev, void* stream) {
     if (!out_dev) return fail(TCNG_EINVAL, "out_dev is NULL");
     return expect_impl(st, terms, n_terms, out_dev, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+tcng_status tcng_expect_energy(const tcng_state* st, const tcng_pauli* terms, size_t n_terms,
+                               const double* coeffs_dev, double* out_dev, double* energy_dev,
+                               void* stream) {
+    if (!out_dev || !energy_dev) return fail(TCNG_EINVAL, "out_dev or energy_dev is NULL");
+    return expect_impl(st, terms, n_terms, out_dev, coeffs_dev, energy_dev,
+                       static_cast<cudaStream_t>(stream));
 }
 
 tcng_status tcng_energy(const tcng_state* st, const tcng_pauli* terms, size_t n_terms,

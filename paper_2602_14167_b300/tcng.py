@@ -62,6 +62,7 @@ def lib():
             "tcng_expect_pauli": [vp, vp, sz, vp, vp],
             "tcng_expect_pauli_noalloc": [vp, i32, i32, vp, sz, vp, vp],
             "tcng_energy": [vp, vp, sz, vp, vp, vp],
+            "tcng_expect_energy": [vp, vp, sz, vp, vp, vp, vp],
             "tcng_hamiltonian_apply": [vp, vp, sz, vp, vp, vp],
             "tcng_energy_grad": [vp, vp, sz, vp, sz, vp, i32, vp, sz, vp, vp, vp, vp],
             "tcng_energy_grad_ragged": [vp, i32, vp, i32, vp, vp, vp, vp, vp],
@@ -196,6 +197,12 @@ def tcng_energy(handle, terms, coeffs_dev, energy_dev, stream=None):
                              _stream(stream)))
 
 
+def tcng_expect_energy(handle, terms, coeffs_dev, out_dev, energy_dev, stream=None):
+    t = _terms(terms)
+    _check(lib().tcng_expect_energy(handle, t.ctypes.data, len(t), _ptr(coeffs_dev), _ptr(out_dev),
+                                    _ptr(energy_dev), _stream(stream)))
+
+
 def tcng_hamiltonian_apply(handle, terms, coeffs_dev, out_handle, stream=None):
     t = _terms(terms)
     _check(lib().tcng_hamiltonian_apply(handle, t.ctypes.data, len(t), _ptr(coeffs_dev), out_handle,
@@ -315,7 +322,8 @@ def tcng_version():
 
 EXPORTED = [
     "tcng_state_init", "tcng_state_bytes", "tcng_state_free", "tcng_state_ptr", "tcng_state_reset",
-    "tcng_apply_circuit", "tcng_expect_pauli", "tcng_expect_pauli_noalloc", "tcng_energy", "tcng_hamiltonian_apply",
+    "tcng_apply_circuit", "tcng_expect_pauli", "tcng_expect_pauli_noalloc", "tcng_energy", "tcng_expect_energy",
+    "tcng_hamiltonian_apply",
     "tcng_energy_grad", "tcng_energy_grad_ragged", "tcng_apply_shared_unitary", "tcng_adam_step",
     "tcng_adam_step_f32", "tcng_mlp_forward", "tcng_mlp_backward", "tcng_set_option",
     "tcng_get_option", "tcng_autotune", "tcng_sync_status", "tcng_describe_plan",

@@ -205,6 +205,28 @@ def test_energy_per_item_coefficients(T):
         assert abs(e[i] - e_ref) < 1e-11
 
 
+def test_expect_energy_matches_separate_calls(T):
+    """One plan for strings + Hamiltonian: same values and energy as two calls."""
+    n = 18
+    c, th = gen.su4_brickwork(n, 4, "RZ", seed=9)
+    g, p = c.to_ir()
+    st = run(n, g, p, th, "c64")
+    strings = gen.random_pauli_strings(n, 24, 4, seed=10)
+    ham = gen.tfim_terms(n, 1.0, 0.8)
+    terms = np.concatenate([strings, ham])
+    terms["coeff"][:len(strings)] = 0.0
+    vals = torch.empty((1, len(terms)), dtype=torch.float64, device="cuda")
+    e = torch.empty(1, dtype=torch.float64, device="cuda")
+    T.tcng_expect_energy(st.handle, terms, None, vals, e)
+    v_sep = st.expect(strings)[0].cpu().numpy()
+    e_sep = float(st.energy(ham)[0])
+    v = vals[0].cpu().numpy()
+    assert np.max(np.abs(v[:len(strings)] - v_sep)) < 1e-6
+    assert abs(float(e[0]) - e_sep) < 1e-6 * np.abs(ham["coeff"]).sum()
+    ref = sv.apply(n, g, p, th)
+    assert abs(float(e[0]) - float(np.dot(ham["coeff"], sv.expect(n, ref, ham).real))) < 1e-5 * np.abs(ham["coeff"]).sum()
+
+
 def test_hamiltonian_apply(T):
     n = 10
     from paper_2602_14167_b300 import StateBatch
