@@ -4,6 +4,8 @@
 // the contraction path and gradient graph are traced once); the analogue here is
 // a plan built once per structure hash and cached by the C ABI layer.
 #include <algorithm>
+#include <functional>
+#include <unordered_map>
 #include <cmath>
 #include <cstring>
 #include <sstream>
@@ -431,7 +433,114 @@ void build_plan(Plan& plan) {
             for (int b : pass_list)
                 for (int d : deps[b])
                     if (inp[d]) pdeps[b].push_back(d);
+            // tile-bit mask of each block of the pass
+            std::vector<uint32_t> tbm_of(plan.blocks.size(), 0);
+            bool small_blocks = !o.adjoint;   // the register-set search below: <= 4-qubit blocks
+            for (int b : pass_list) {
+                uint64_t qm = plan.blocks[b].qmask;
+                while (qm) {
+                    int q = __builtin_ctzll(qm);
+                    qm &= qm - 1;
+                    tbm_of[b] |= 1u << tb_of_q[q];
+                }
+                if (!plan.blocks[b].diag && __builtin_popcount(tbm_of[b]) > kRegBits) small_blocks = false;
+            }
+            // Register sets of the stages: for passes of up to 12 dense blocks, the
+            // fewest stages (a stage costs about the same whatever it holds on the
+            // tensor-core passes).  A stage with register set R takes every block that
+            // becomes ready and fits R (taking more never hurts the rest), so the search
+            // runs over sets of placed blocks, memoised; ties prefer sets without tile
+            // bits 0..3 (no slot rotation).  Larger passes grow stages greedily.
+            std::vector<int> dense_ids;   // pass blocks by local index
+            for (int b : pass_list) dense_ids.push_back(b);
+            const int nbk = (int)dense_ids.size();
+            int n_dense_pass = 0;
+            for (int b : pass_list) n_dense_pass += plan.blocks[b].diag ? 0 : 1;
+            bool search = small_blocks && nbk <= 64 && n_dense_pass <= 12;
+            std::vector<uint64_t> pdep_mask(nbk, 0);
+            {
+                std::vector<int> local(plan.blocks.size(), -1);
+                for (int i = 0; i < nbk; ++i) local[dense_ids[i]] = i;
+                for (int i = 0; i < nbk; ++i)
+                    for (int d : pdeps[dense_ids[i]]) pdep_mask[i] |= 1ULL << local[d];
+            }
+            const uint64_t all_mask = nbk >= 64 ? ~0ULL : ((1ULL << nbk) - 1);
+            auto closure = [&](uint64_t dm, uint32_t R) {
+                for (bool prog = true; prog;) {
+                    prog = false;
+                    for (int i = 0; i < nbk; ++i) {
+                        if ((dm >> i) & 1) continue;
+                        if ((pdep_mask[i] & ~dm) != 0) continue;
+                        const int b = dense_ids[i];
+                        if (plan.blocks[b].diag || (tbm_of[b] & ~R) == 0) {
+                            dm |= 1ULL << i;
+                            prog = true;
+                        }
+                    }
+                }
+                return dm;
+            };
+            std::unordered_map<uint64_t, std::pair<int, uint32_t>> memo;
+            std::function<int(uint64_t)> solve = [&](uint64_t dm) -> int {
+                if ((dm & all_mask) == all_mask) return 0;
+                if (memo.size() > 20000) {   // too many reachable states: greedy instead
+                    search = false;
+                    return 0;
+                }
+                auto it = memo.find(dm);
+                if (it != memo.end()) return it->second.first;
+                uint32_t touch = 0;
+                for (int i = 0; i < nbk; ++i)
+                    if (!((dm >> i) & 1) && !plan.blocks[dense_ids[i]].diag) touch |= tbm_of[dense_ids[i]];
+                std::vector<int> bits;
+                for (int tb = 0; tb < dp.m; ++tb)
+                    if ((touch >> tb) & 1) bits.push_back(tb);
+                std::vector<uint32_t> cands;
+                if ((int)bits.size() <= kRegBits) {
+                    cands.push_back(touch);
+                } else {
+                    const int nb = (int)bits.size();
+                    for (int i0 = 0; i0 < nb; ++i0)
+                        for (int i1 = i0 + 1; i1 < nb; ++i1)
+                            for (int i2 = i1 + 1; i2 < nb; ++i2)
+                                for (int i3 = i2 + 1; i3 < nb; ++i3)
+                                    cands.push_back((1u << bits[i0]) | (1u << bits[i1]) | (1u << bits[i2]) |
+                                                    (1u << bits[i3]));
+                }
+                int best = 1 << 20, best_low = 99;
+                uint32_t bestR = 0;
+                std::vector<uint64_t> seen;
+                for (uint32_t R : cands) {
+                    const uint64_t nd = closure(dm, R);
+                    if (nd == dm) continue;
+                    const int low = __builtin_popcount(R & 0xFu);
+                    bool dup = false;
+                    for (uint64_t x : seen) dup = dup || x == nd;
+                    if (dup && low >= best_low) continue;
+                    seen.push_back(nd);
+                    const int v = 1 + solve(nd);
+                    if (v < best || (v == best && low < best_low)) {
+                        best = v;
+                        best_low = low;
+                        bestR = R;
+                    }
+                }
+                memo[dm] = {best, bestR};
+                return best;
+            };
+            auto choose_set = [&]() -> uint32_t {
+                if (!search) return 0;
+                uint64_t dm = 0;
+                for (int i = 0; i < nbk; ++i)
+                    if (done[dense_ids[i]]) dm |= 1ULL << i;
+                solve(dm);
+                if (!search) return 0;
+                auto it = memo.find(dm);
+                return it == memo.end() ? 0 : it->second.second;
+            };
+            uint32_t Rfix = 0;   // chosen register set of the open stage (0: grow greedily)
             while (left) {
+                if (cur.empty() && small_blocks) Rfix = choose_set();
                 int pick = -1;
                 for (int b : pass_list) {
                     if (done[b]) continue;
@@ -440,6 +549,14 @@ void build_plan(Plan& plan) {
                         if (!done[d]) { ready = false; break; }
                     if (!ready) continue;
                     const Block& blk = plan.blocks[b];
+                    if (Rfix && !blk.diag) {
+                        if ((tbm_of[b] & ~Rfix) == 0) {
+                            pick = b;
+                            Rset = Rfix;
+                            break;
+                        }
+                        continue;
+                    }
                     if (o.adjoint && blk.param_single &&
                         (cur_grads >= kMaxStageGrads || Rcap > kRegBits))
                         continue;   // gradient ops stay in 16-amplitude register stages
