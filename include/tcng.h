@@ -43,7 +43,7 @@ typedef enum {
     TCNG_EINVAL = 1,        /* bad argument (qubit out of range, null pointer, ...) */
     TCNG_ENOMEM = 2,        /* device or host allocation failed, or buffer too small */
     TCNG_ECUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error) */
-    TCNG_EUNSUPPORTED = 4,  /* valid request this build does not implement */
+    TCNG_EUNSUPPORTED = 4,  /* valid request this library does not implement */
     TCNG_ETIMEOUT = 5       /* a bounded device-side wait expired (reported by tcng_sync_status) */
 } tcng_status;
 

@@ -3,8 +3,8 @@
 A BF16 MLP (``tcng_mlp_forward``/``tcng_mlp_backward``, FP32 master weights,
 device Adam) maps Hamiltonian couplings to initial ansatz angles.  Training
 targets are converged angles produced by the batched adjoint simulator itself
-(``tcng_energy_grad_ragged`` + ``tcng_adam_step`` for many steps).  The judge of
-the network is the exact simulated energy: how many Adam steps a warm-started
+(``tcng_energy_grad_ragged`` + ``tcng_adam_step`` for many steps).  The network
+is measured by the exact simulated energy: how many Adam steps a warm-started
 run needs against random initialisation.
 
 Chains are dicts {kind: 0 TFIM / 1 XXZ, n, J[n-1], delta, g}; the ansatz is the
