@@ -8,7 +8,7 @@
 //
 // Per stage and 128-row slice (four warps, one per TMEM lane quarter):
 //   * each thread reads its row from the shared-memory tile, splits it into
-//     TF32 hi + lo parts (Veltkamp) and writes both into TMEM (the A operand);
+//     TF32 hi + lo parts and writes both into TMEM (the A operand);
 //   * one thread issues 8 tcgen05.mma kind::tf32 (M=128, K=8): per K step one
 //     N=64 MMA against [W_hi | W_lo] (a_hi*w_hi and a_hi*w_lo side by side)
 //     and one N=32 MMA adding a_lo*w_hi to the small half; the halves are
@@ -113,14 +113,20 @@ __global__ void build_stage_w_kernel(const TcsStage* __restrict__ tcs, const Dev
 }
 
 // ------------------------------------------------------------ helpers ----
-// Veltkamp split of x into hi (11 significant bits: exact in TF32) and the
-// exact rest x - hi (the tensor core keeps its leading 11 bits), on the FMA
-// pipe; the _rn intrinsics keep the compiler from contracting the steps.
+// Split of x for kind::tf32: the tensor core reads an fp32 operand as its
+// leading 19 bits (sign, exponent, 10 mantissa bits: x truncated), so hi is x
+// itself and lo = x - trunc(x), exact in fp32 (|lo| < 2^-10 |x|, of which the
+// tensor core again keeps the leading 11 bits).  Two instructions per value.
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-    const float c = __fmul_rn(x, 8193.0f);   // 2^13 + 1
-    const float h = __fsub_rn(c, __fsub_rn(c, x));
-    hi = __float_as_uint(h);
-    lo = __float_as_uint(__fsub_rn(x, h));
+    hi = __float_as_uint(x);
+    lo = __float_as_uint(__fsub_rn(x, __uint_as_float(__float_as_uint(x) & 0xffffe000u)));
+}
+
+// One lane of a converged warp (elect.sync).
+__device__ __forceinline__ bool elect_one() {
+    uint32_t p;
+    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\tselp.u32 %0, 1, 0, e;\n\t}" : "=r"(p));
+    return p != 0;
 }
 
 __device__ __forceinline__ void tc_st32(uint32_t taddr, const uint32_t (&r)[32]) {
@@ -198,7 +204,10 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
     __shared__ int s_abort;
     __shared__ float2 red[TS_THREADS / 32];
     __shared__ StageSm sst[TS_MAX_STAGES];
-    const int tid = threadIdx.x, warp = tid >> 5;
+    // the warp index and the TMEM base are broadcast from lane 0, so the compiler
+    // knows them to be warp-uniform: the MMA operands derived from them stay in
+    // uniform registers (a per-thread operand costs a register move per MMA)
+    const int tid = threadIdx.x, warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
     const int quarter = warp & 3, slice = warp >> 2;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -246,7 +255,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_base;
+    const uint32_t tmem = __shfl_sync(0xffffffffu, tmem_base, 0);
     const uint32_t col_ahi = (uint32_t)slice * 128u, col_alo = col_ahi + 32u, col_d = col_ahi + 64u;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
     const uint32_t idesc64 = tf32_idesc(128, 64), idesc32 = tf32_idesc(128, 32);
@@ -367,7 +376,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
             }
             tc_fence_before();
             asm volatile("bar.sync %0, %1;" ::"r"(1 + slice), "r"(128) : "memory");
-            if ((tid & 127) == 0) {
+            if (quarter == 0 && elect_one()) {   // one thread of the slice's first warp
                 tc_fence_after();
                 const int slot = a.grouped ? s : (int)(q % TS_NB);
                 const uint32_t wpar = a.grouped ? 0u : (uint32_t)((q / TS_NB) & 1);
