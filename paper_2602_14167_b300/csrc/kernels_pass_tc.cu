@@ -122,12 +122,6 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) 
     lo = __float_as_uint(__fsub_rn(x, __uint_as_float(__float_as_uint(x) & 0xffffe000u)));
 }
 
-// One lane of a converged warp (elect.sync).
-__device__ __forceinline__ bool elect_one() {
-    uint32_t p;
-    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\tselp.u32 %0, 1, 0, e;\n\t}" : "=r"(p));
-    return p != 0;
-}
 
 __device__ __forceinline__ void tc_st32(uint32_t taddr, const uint32_t (&r)[32]) {
     asm volatile(
@@ -175,7 +169,8 @@ struct PassTcsArgs {
     const TcsStage* tcs;      // this pass's stages
     const float* wops;        // W operands, [item][tensor-core stage]
     long long w_item_stride;  // floats per item (0: one set for all items)
-    long long tiles_per_item;
+    long long tiles_per_item;   // a power of two: 2^tpi_log
+    int tpi_log;
     long long total_tiles;
     unsigned* err;
 };
@@ -183,7 +178,7 @@ struct PassTcsArgs {
 __device__ __forceinline__ void tcs_load_tile(const TmaTile& tma, const PassTcsArgs& a, long long t,
                                               float2* dst, uint64_t* bar) {
     int c[5];
-    tma_tile_coords(tma, t % a.tiles_per_item, (int)(t / a.tiles_per_item), c);
+    tma_tile_coords(tma, (t & (a.tiles_per_item - 1)), (int)(t >> a.tpi_log), c);
     mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(float2) << TS_TILE_BITS));
     tma_load_tile(tma, dst, bar, c);
 }
@@ -268,7 +263,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
     long long tiles_issued = 0, w_issued = 0, w_t = 0;
     int w_s = 0;
     auto issue_w = [&]() {
-        const long long item = (first + w_t * stride) / a.tiles_per_item;
+        const long long item = (first + w_t * stride) >> a.tpi_log;
         const float* src = a.wops + item * a.w_item_stride + (long long)sst[w_s].tc_index * TS_W_FLOATS;
         const int slot = (int)(w_issued % TS_NB);
         mbar_arrive_expect_tx(&w_bar[slot], TS_W_BYTES);
@@ -465,7 +460,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
         }
         if (tid == 0) {
             int c[5];
-            tma_tile_coords(tma, t % a.tiles_per_item, (int)(t / a.tiles_per_item), c);
+            tma_tile_coords(tma, (t & (a.tiles_per_item - 1)), (int)(t >> a.tpi_log), c);
             tma_store_tile(tma, buf, c);
             bulk_commit();
             if (tiles_issued < my_tiles) {   // the next load reuses the buffer stored one tile ago
@@ -594,6 +589,7 @@ cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float*
     a.wops = wops;
     a.w_item_stride = w_item_stride;
     a.tiles_per_item = 1ll << (dp->plan.n - P.m);
+    a.tpi_log = dp->plan.n - P.m;
     a.total_tiles = a.tiles_per_item * items;
     a.err = err;
     const long long grid = std::min<long long>(a.total_tiles, num_sms());

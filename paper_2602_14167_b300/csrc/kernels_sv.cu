@@ -266,7 +266,8 @@ struct TileCtx {
     int nchunks;
     uint32_t chunk_bytes;
     uint32_t tile_bytes;
-    long long tiles_per_item;
+    long long tiles_per_item;   // a power of two: 2^tpi_log
+    int tpi_log;
     long long total_tiles;
 };
 
@@ -274,17 +275,17 @@ template <typename C>
 __device__ __forceinline__ void issue_tile_load(const C* state, const long long* item_off,
                                                 const DevPass& p, const TileCtx& tc, long long tile,
                                                 C* buf, uint64_t* bar, int lane, const TmaTile& tma) {
-    const long long item = tile / tc.tiles_per_item;
+    const long long item = (tile >> tc.tpi_log);
     if (tma.rank) {   // one tensor copy for the whole tile
         if (lane == 0) {
             int c[5];
-            tma_tile_coords(tma, tile % tc.tiles_per_item, (int)item, c);
+            tma_tile_coords(tma, (tile & (tc.tiles_per_item - 1)), (int)item, c);
             mbar_arrive_expect_tx(bar, tc.tile_bytes);
             tma_load_tile(tma, buf, bar, c);
         }
         return;
     }
-    const long long base = tile_global_base(p, tile % tc.tiles_per_item);
+    const long long base = tile_global_base(p, (tile & (tc.tiles_per_item - 1)));
     if (tma.g4) {   // four rows of 2^g4rb amplitudes per tile::gather4 copy, in tile order
         const long long b0 = item_off[item] - tma.g4base + base;
         const int rb = tma.g4rb, sub = p.chunk - rb;   // rows per chunk: 2^sub
@@ -312,17 +313,17 @@ template <typename C>
 __device__ __forceinline__ void issue_tile_store(C* state, const long long* item_off, const DevPass& p,
                                                  const TileCtx& tc, long long tile, const C* buf,
                                                  int lane, const TmaTile& tma) {
-    const long long item = tile / tc.tiles_per_item;
+    const long long item = (tile >> tc.tpi_log);
     if (tma.rank) {
         if (lane == 0) {
             int c[5];
-            tma_tile_coords(tma, tile % tc.tiles_per_item, (int)item, c);
+            tma_tile_coords(tma, (tile & (tc.tiles_per_item - 1)), (int)item, c);
             tma_store_tile(tma, buf, c);
         }
         bulk_commit();
         return;
     }
-    const long long base = tile_global_base(p, tile % tc.tiles_per_item);
+    const long long base = tile_global_base(p, (tile & (tc.tiles_per_item - 1)));
     C* dst = state + item_off[item] + base;
     for (int j = lane; j < tc.nchunks; j += 32)
         bulk_s2g(dst + chunk_offset(p, j), buf + ((long long)j << p.chunk), tc.chunk_bytes);
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
     for (long long t = first; t < tc.total_tiles; t += stride, ++it) {
         const int b = it % tc.nbuf;
         C* buf = bufs + (long long)b * tile_elems;
-        const long long item = t / tc.tiles_per_item;
+        const long long item = (t >> tc.tpi_log);
         if (item != cur_item) {  // (re)load the matrix window of this item
             const C* src = table + item * table_stride + p.mat_begin;
             for (int i = tid; i < p.mat_count; i += blockDim.x) mats[i] = src[i];
@@ -375,7 +376,7 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
         if (!ok) s_abort = 1;
         __syncthreads();   // also orders the matrix window reload above before the stages
         if (s_abort) break;
-        const long long gbase = tile_global_base(p, t % tc.tiles_per_item);
+        const long long gbase = tile_global_base(p, (t & (tc.tiles_per_item - 1)));
         for (int s = 0; s < p.stage_count; ++s) {
             const DevStage st = stages[p.stage_begin + s];
             run_stage<C>(buf, st, ops, mats, p.m, gbase);
@@ -541,7 +542,7 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
         // no CTA barrier per tile: every thread waits for the tile itself, and each
         // warp releases the buffer on its own (warp 0 refills it once all have)
         if (!mbar_wait_bounded(&bars[b], (uint32_t)((it / tc.nbuf) & 1), err)) s_abort = 1;
-        const long long gbase = tile_global_base(p, t % tc.tiles_per_item);
+        const long long gbase = tile_global_base(p, (t & (tc.tiles_per_item - 1)));
         if constexpr (fast) {
             {
                 // register r = e + 2 i holds tile offset e + 2 tid + 1024 i (pairs of
@@ -807,6 +808,7 @@ static TileCtx make_ctx(const DevPass& p, int n, int items, int elem_bytes, int 
     tc.chunk_bytes = (uint32_t)(elem_bytes << p.chunk);
     tc.tile_bytes = (uint32_t)(elem_bytes << p.m);
     tc.tiles_per_item = 1ll << (n - p.m);
+    tc.tpi_log = n - p.m;
     tc.total_tiles = tc.tiles_per_item * items;
     return tc;
 }

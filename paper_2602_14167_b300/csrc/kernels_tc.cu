@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(128) shared_unitary_tc_kernel(TcArgs a) {
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // warp index and TMEM base broadcast from lane 0: warp-uniform for the compiler
+    const int tid = threadIdx.x, warp = __shfl_sync(0xffffffffu, tid >> 5, 0), lane = tid & 31;
     const int kq = a.k, D = 1 << kq;
     int qs[TCNG_MAX_FUSE];
     {
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(128) shared_unitary_tc_kernel(TcArgs a) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_base;
+    const uint32_t tmem = __shfl_sync(0xffffffffu, tmem_base, 0);
     const long long rows_per_item = 1ll << (a.n - kq);
     const long long total_rows = rows_per_item * a.items;
     const long long ntiles = (total_rows + TC_M - 1) / TC_M;
@@ -103,8 +104,8 @@ __global__ void __launch_bounds__(128) shared_unitary_tc_kernel(TcArgs a) {
             const long long r = r0 + row;
             float2 v = make_float2(0.f, 0.f);
             if (r < total_rows) {
-                const long long item = r / rows_per_item;
-                long long x = r % rows_per_item;
+                const long long item = r >> (a.n - kq);
+                long long x = r & (rows_per_item - 1);
                 for (int j = 0; j < kq; ++j) x = ((x >> qs[j]) << (qs[j] + 1)) | (x & ((1ll << qs[j]) - 1));
                 for (int j = 0; j < kq; ++j)
                     if ((l >> j) & 1) x |= 1ll << qs[j];
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(128) shared_unitary_tc_kernel(TcArgs a) {
         __syncthreads();
         tc_fence_after();
         // ---- 3-term TF32 product on the tensor cores ----
-        if (tid == 0) {
+        if (warp == 0 && elect_one()) {
             // small cross terms first, the large hi*hi products last: the tensor-core
             // accumulator rounds toward zero, so each full-magnitude accumulation costs
             // up to an ulp; this order has 4 of them per output instead of 12
@@ -157,8 +158,8 @@ __global__ void __launch_bounds__(128) shared_unitary_tc_kernel(TcArgs a) {
             tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 0u, v[0]);
             tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32u, v[1]);
             if (r < total_rows) {
-                const long long item = r / rows_per_item;
-                long long x = r % rows_per_item;
+                const long long item = r >> (a.n - kq);
+                long long x = r & (rows_per_item - 1);
                 for (int j = 0; j < kq; ++j) x = ((x >> qs[j]) << (qs[j] + 1)) | (x & ((1ll << qs[j]) - 1));
                 float2* psi = a.state + a.item_off[item];
 #pragma unroll

@@ -59,6 +59,14 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, ui
         "l"(a), "l"(b), "r"(idesc), "r"(accum)
         : "memory");
 }
+// One lane of a converged warp (elect.sync).  Issuing MMAs from an elected lane
+// of a warp-uniform branch, with warp-uniform operands, keeps those operands in
+// uniform registers.
+__device__ __forceinline__ bool elect_one() {
+    uint32_t p;
+    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\tselp.u32 %0, 1, 0, e;\n\t}" : "=r"(p));
+    return p != 0;
+}
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
