@@ -19,7 +19,9 @@
 // norm is restored to its norm before the pass: this removes the systematic
 // shrink of the round-toward-zero accumulation.
 // W_s (hi and lo, 128-byte swizzled, K-major) streams from global memory (L2)
-// through a three-slot ring, two stages ahead.  Rows whose register bits
+// through a three-slot ring, two stages ahead.  A seventeenth warp only moves
+// tiles: it stores a tile once all four slices report it done and loads the tile
+// two ahead into the freed buffer, so no compute warp waits on a TMA issue.  Rows whose register bits
 // include tile bits 0..3 read their slots XOR-rotated (bank-conflict free) and
 // undo the rotation in registers around the MMA.
 #include <cuda_runtime.h>
@@ -34,7 +36,9 @@
 
 namespace tcng {
 
-constexpr int TS_THREADS = 512;
+constexpr int TS_THREADS = 512;                    // compute threads: 4 slices x 4 warps
+constexpr int TS_CTA_THREADS = TS_THREADS + 32;    // + one producer warp (tile loads, stores)
+constexpr int TS_PRODUCER_WARP = TS_THREADS / 32;
 constexpr int TS_TILE_BITS = 13;
 constexpr int TS_NBUF = 3;                         // tile buffers
 constexpr int TS_NB = 3;                           // W ring slots
@@ -145,6 +149,11 @@ __device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint
         : "memory");
 }
 
+// Barrier of the 512 compute threads (the producer warp never joins it).
+__device__ __forceinline__ void compute_sync() {
+    asm volatile("bar.sync 5, %0;" ::"n"(TS_THREADS) : "memory");
+}
+
 // a[s] holds register value s ^ tau (tau only on slots 0..nj-1): permute so
 // that a[v] holds value v (the permutation is its own inverse).
 __device__ __forceinline__ void unrotate(float2 (&a)[16], int tau, int nj) {
@@ -184,7 +193,7 @@ __device__ __forceinline__ void tcs_load_tile(const TmaTile& tma, const PassTcsA
 }
 
 // ------------------------------------------------------------- kernel ----
-__global__ void __launch_bounds__(TS_THREADS, 1)
+__global__ void __launch_bounds__(TS_CTA_THREADS, 1)
     pass_tcs_kernel(const __grid_constant__ DevPass p, const PassTcsArgs a,
                     const __grid_constant__ TmaTile tma) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -193,7 +202,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
     float2* bufs = reinterpret_cast<float2*>(base + TS_NB * TS_W_BYTES);    // TS_NBUF tiles
     constexpr int tile_elems = 1 << TS_TILE_BITS;
     __shared__ uint64_t tile_bar[TS_NBUF], w_bar[TS_NB], mma_bar[4];
-    __shared__ uint64_t done_bar[TS_NBUF];   // grouped: slices 1..3 finished a tile
+    __shared__ uint64_t done_bar[TS_NBUF];   // the four slices finished a tile
     __shared__ uint64_t stag_bar;            // grouped: slices 2, 3 started (once)
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
@@ -211,7 +220,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int i = tid; i < p.stage_count; i += TS_THREADS) {
+    for (int i = tid; i < p.stage_count; i += TS_CTA_THREADS) {
         const TcsStage S = a.tcs[i];
         StageSm d;
         int skip[6], ns = 0;   // register bits (+ the slice bits of a grouped pass), ascending
@@ -242,7 +251,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
         for (int i = 0; i < TS_NBUF; ++i) mbar_init(&tile_bar[i], 1);
         for (int i = 0; i < TS_NB; ++i) mbar_init(&w_bar[i], 1);
         for (int i = 0; i < 4; ++i) mbar_init(&mma_bar[i], 1);
-        for (int i = 0; i < TS_NBUF; ++i) mbar_init(&done_bar[i], 3);
+        for (int i = 0; i < TS_NBUF; ++i) mbar_init(&done_bar[i], 4);
         mbar_init(&stag_bar, 2);
         fence_mbar_init();
         s_abort = 0;
@@ -258,9 +267,52 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
     const long long first = blockIdx.x, stride = gridDim.x;
     const long long my_tiles = first < a.total_tiles ? (a.total_tiles - first + stride - 1) / stride : 0;
     const long long total_q = my_tiles * nst;
-    // producer state (thread 0 only): loads issued so far; the next W operand is
-    // stage w_s of the CTA's tile w_t
-    long long tiles_issued = 0, w_issued = 0, w_t = 0;
+    if (warp == TS_PRODUCER_WARP) {   // ---------------------------- tile mover --
+        if ((tid & 31) == 0) {
+            long long issued = 0;
+            for (; issued < TS_NBUF - 1 && issued < my_tiles; ++issued)
+                tcs_load_tile(tma, a, first + issued * stride, bufs + issued * tile_elems, &tile_bar[issued]);
+            for (long long i = 0; i < my_tiles; ++i) {
+                const int b = (int)(i % TS_NBUF);
+                // wait for the four slices (or give up when they abort)
+                bool done = mbar_try_wait(&done_bar[b], (uint32_t)((i / TS_NBUF) & 1));
+                const unsigned long long t0 = global_ns();
+                for (uint32_t k = 1; !done; ++k) {
+                    if (*reinterpret_cast<volatile int*>(&s_abort)) break;
+                    done = mbar_try_wait(&done_bar[b], (uint32_t)((i / TS_NBUF) & 1));
+                    if (!done && (k & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
+                        atomicOr(a.err, ERR_TIMEOUT);
+                        s_abort = 1;
+                        break;
+                    }
+                }
+                if (!done) break;
+                const long long t = first + i * stride;
+                int c[5];
+                tma_tile_coords(tma, (t & (a.tiles_per_item - 1)), (int)(t >> a.tpi_log), c);
+                tma_store_tile(tma, bufs + (size_t)b * tile_elems, c);
+                bulk_commit();
+                if (issued < my_tiles) {   // the next load reuses the buffer stored one tile ago
+                    bulk_wait_read<1>();
+                    const int bn = (int)(issued % TS_NBUF);
+                    tcs_load_tile(tma, a, first + issued * stride, bufs + (size_t)bn * tile_elems, &tile_bar[bn]);
+                    ++issued;
+                }
+            }
+            bulk_wait<0>();
+            // after an abort: the last loads (at most one per buffer) may still be in
+            // flight; wait for them before the shared memory goes away
+            for (long long i = issued > TS_NBUF ? issued - TS_NBUF : 0; i < issued; ++i)
+                mbar_wait_bounded(&tile_bar[i % TS_NBUF], (uint32_t)((i / TS_NBUF) & 1), a.err);
+        }
+        __syncwarp();
+        tc_fence_before();
+        __syncthreads();
+        return;
+    }
+    // W operand producer state (thread 0): the next W operand is stage w_s of the
+    // CTA's tile w_t
+    long long w_issued = 0, w_t = 0;
     int w_s = 0;
     auto issue_w = [&]() {
         const long long item = (first + w_t * stride) >> a.tpi_log;
@@ -275,9 +327,6 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
         }
     };
     if (tid == 0) {
-        for (; tiles_issued < TS_NBUF - 1 && tiles_issued < my_tiles; ++tiles_issued)
-            tcs_load_tile(tma, a, first + tiles_issued * stride, bufs + tiles_issued * tile_elems,
-                          &tile_bar[tiles_issued]);
         if (a.grouped) {   // every stage's W stays resident (one set for all items)
             for (int st = 0; st < nst && my_tiles > 0; ++st) {
                 mbar_arrive_expect_tx(&w_bar[st], TS_W_BYTES);
@@ -312,7 +361,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
             if (it == 0 && slice < 2) mbar_wait_bounded(&stag_bar, 0u, a.err);
         } else {
             if (!tile_ok) s_abort = 1;
-            __syncthreads();
+            compute_sync();
             if (s_abort) break;
         }
         float nin = 0.f;   // this thread's share of the tile norm before the pass
@@ -422,7 +471,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                         to += r.y;
                     }
                 } else {
-                    __syncthreads();
+                    compute_sync();
 #pragma unroll
                     for (int w = 0; w < TS_THREADS / 32; ++w) {
                         const float2 r = red[w];
@@ -442,41 +491,19 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
             if (a.grouped) {   // the next stage reads only this slice's rows
                 asm volatile("bar.sync %0, %1;" ::"r"(1 + slice), "r"(128) : "memory");
             } else {
-                __syncthreads();
+                compute_sync();
             }
             tc_fence_after();
             if (!a.grouped && s_abort) break;
         }
         fence_proxy_async_smem();   // this thread's tile writes before the tensor store reads them
-        if (a.grouped) {
-            // slices 1..3 report; thread 0 (slice 0) stores once all four are done
-            asm volatile("bar.sync %0, %1;" ::"r"(1 + slice), "r"(128) : "memory");
-            if ((tid & 127) == 0 && slice > 0) mbar_arrive(&done_bar[b]);
-            if (tid == 0 && !mbar_wait_bounded(&done_bar[b], (uint32_t)((it / TS_NBUF) & 1), a.err))
-                s_abort = 1;
-        } else {
-            if (s_abort) break;
-            __syncthreads();
-        }
-        if (tid == 0) {
-            int c[5];
-            tma_tile_coords(tma, (t & (a.tiles_per_item - 1)), (int)(t >> a.tpi_log), c);
-            tma_store_tile(tma, buf, c);
-            bulk_commit();
-            if (tiles_issued < my_tiles) {   // the next load reuses the buffer stored one tile ago
-                bulk_wait_read<1>();
-                const int bn = (int)(tiles_issued % TS_NBUF);
-                tcs_load_tile(tma, a, first + tiles_issued * stride, bufs + (size_t)bn * tile_elems,
-                              &tile_bar[bn]);
-                ++tiles_issued;
-            }
-        }
+        if (!a.grouped && s_abort) break;
+        // each slice reports the tile; the producer warp stores it once all four have
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + slice), "r"(128) : "memory");
+        if ((tid & 127) == 0) mbar_arrive(&done_bar[b]);
     }
     if (tid == 0) {
-        bulk_wait<0>();
-        if (s_abort) {   // drain the loads still in flight before the shared memory goes away
-            for (long long i = it; i < tiles_issued; ++i)
-                mbar_wait_bounded(&tile_bar[i % TS_NBUF], (uint32_t)((i / TS_NBUF) & 1), a.err);
+        if (s_abort) {   // drain the W loads still in flight before the shared memory goes away
             if (a.grouped) {
                 for (int st = 0; st < nst; ++st) mbar_wait_bounded(&w_bar[st], 0u, a.err);
             } else {
@@ -593,7 +620,7 @@ cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float*
     a.total_tiles = a.tiles_per_item * items;
     a.err = err;
     const long long grid = std::min<long long>(a.total_tiles, num_sms());
-    pass_tcs_kernel<<<(unsigned)grid, TS_THREADS, pass_tcs_smem_bytes(), s>>>(P, a, tma);
+    pass_tcs_kernel<<<(unsigned)grid, TS_CTA_THREADS, pass_tcs_smem_bytes(), s>>>(P, a, tma);
     count_launch();
     return cudaGetLastError();
 }
