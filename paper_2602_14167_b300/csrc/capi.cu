@@ -262,9 +262,10 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
             TmaTile tma{};
             if (tma_base && (items == 1 || item_stride > 0))
                 tma = make_tma_tile(tma_base, pl.n, (int)sizeof(C), p, items, item_stride);
-            if (wops && dp->tc_pass[pi] && tma.rank) {
+            if (wops && dp->tc_pass[pi]) {   // tile map, else one bulk copy per chunk
                 ProfScope ps("pass_tcs_kernel_c64", s);
-                e = launch_pass_tcs(dp, (int)pi, items, wops, w_stride, ctx().err, tma, s);
+                e = launch_pass_tcs(dp, (int)pi, items, wops, w_stride, ctx().err, tma,
+                                    reinterpret_cast<float2*>(state), d_item_off, s);
                 if (e != cudaSuccess) return cuda_fail(e, "tensor-core pass kernel");
                 continue;
             }

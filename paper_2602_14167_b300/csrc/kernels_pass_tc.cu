@@ -33,6 +33,7 @@
 #include "capi_internal.hpp"
 #include "device.cuh"
 #include "tc.cuh"
+#include "tile_io.cuh"
 
 namespace tcng {
 
@@ -182,15 +183,11 @@ struct PassTcsArgs {
     int tpi_log;
     long long total_tiles;
     unsigned* err;
+    float2* state;              // tile copies: state + item_off[item], in the pass's copy form
+    const long long* item_off;
+    TileCtx tc;
 };
 
-__device__ __forceinline__ void tcs_load_tile(const TmaTile& tma, const PassTcsArgs& a, long long t,
-                                              float2* dst, uint64_t* bar) {
-    int c[5];
-    tma_tile_coords(tma, (t & (a.tiles_per_item - 1)), (int)(t >> a.tpi_log), c);
-    mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(float2) << TS_TILE_BITS));
-    tma_load_tile(tma, dst, bar, c);
-}
 
 // ------------------------------------------------------------- kernel ----
 __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
@@ -268,14 +265,18 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
     const long long my_tiles = first < a.total_tiles ? (a.total_tiles - first + stride - 1) / stride : 0;
     const long long total_q = my_tiles * nst;
     if (warp == TS_PRODUCER_WARP) {   // ---------------------------- tile mover --
-        if ((tid & 31) == 0) {
-            long long issued = 0;
-            for (; issued < TS_NBUF - 1 && issued < my_tiles; ++issued)
-                tcs_load_tile(tma, a, first + issued * stride, bufs + issued * tile_elems, &tile_bar[issued]);
-            for (long long i = 0; i < my_tiles; ++i) {
-                const int b = (int)(i % TS_NBUF);
-                // wait for the four slices (or give up when they abort)
-                bool done = mbar_try_wait(&done_bar[b], (uint32_t)((i / TS_NBUF) & 1));
+        // the whole warp issues the copies (the gather4 and per-chunk forms use every lane)
+        const int lane = tid & 31;
+        long long issued = 0;
+        for (; issued < TS_NBUF - 1 && issued < my_tiles; ++issued)
+            issue_tile_load(a.state, a.item_off, p, a.tc, first + issued * stride, bufs + issued * tile_elems,
+                            &tile_bar[issued], lane, tma);
+        for (long long i = 0; i < my_tiles; ++i) {
+            const int b = (int)(i % TS_NBUF);
+            // lane 0 waits for the four slices (or gives up when they abort)
+            uint32_t done = 0;
+            if (lane == 0) {
+                done = mbar_try_wait(&done_bar[b], (uint32_t)((i / TS_NBUF) & 1));
                 const unsigned long long t0 = global_ns();
                 for (uint32_t k = 1; !done; ++k) {
                     if (*reinterpret_cast<volatile int*>(&s_abort)) break;
@@ -286,25 +287,25 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
                         break;
                     }
                 }
-                if (!done) break;
-                const long long t = first + i * stride;
-                int c[5];
-                tma_tile_coords(tma, (t & (a.tiles_per_item - 1)), (int)(t >> a.tpi_log), c);
-                tma_store_tile(tma, bufs + (size_t)b * tile_elems, c);
-                bulk_commit();
-                if (issued < my_tiles) {   // the next load reuses the buffer stored one tile ago
-                    bulk_wait_read<1>();
-                    const int bn = (int)(issued % TS_NBUF);
-                    tcs_load_tile(tma, a, first + issued * stride, bufs + (size_t)bn * tile_elems, &tile_bar[bn]);
-                    ++issued;
-                }
             }
-            bulk_wait<0>();
-            // after an abort: the last loads (at most one per buffer) may still be in
-            // flight; wait for them before the shared memory goes away
+            if (!__shfl_sync(0xffffffffu, done, 0)) break;
+            issue_tile_store(a.state, a.item_off, p, a.tc, first + i * stride, bufs + (size_t)b * tile_elems,
+                             lane, tma);
+            if (issued < my_tiles) {   // the next load reuses the buffer stored one tile ago
+                bulk_wait_read<1>();
+                __syncwarp();
+                const int bn = (int)(issued % TS_NBUF);
+                issue_tile_load(a.state, a.item_off, p, a.tc, first + issued * stride,
+                                bufs + (size_t)bn * tile_elems, &tile_bar[bn], lane, tma);
+                ++issued;
+            }
+        }
+        bulk_wait<0>();
+        // after an abort: the last loads (at most one per buffer) may still be in
+        // flight; wait for them before the shared memory goes away
+        if (lane == 0)
             for (long long i = issued > TS_NBUF ? issued - TS_NBUF : 0; i < issued; ++i)
                 mbar_wait_bounded(&tile_bar[i % TS_NBUF], (uint32_t)((i / TS_NBUF) & 1), a.err);
-        }
         __syncwarp();
         tc_fence_before();
         __syncthreads();
@@ -598,7 +599,8 @@ cudaError_t launch_build_stage_w(const DevPlan* dp, const double2* table, long l
 }
 
 cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float* wops,
-                            long long w_item_stride, unsigned* err, const TmaTile& tma, cudaStream_t s) {
+                            long long w_item_stride, unsigned* err, const TmaTile& tma, float2* state,
+                            const long long* item_off, cudaStream_t s) {
     const DevPass& P = dp->plan.passes[pass];
     static bool attr = false;
     if (!attr) {
@@ -619,6 +621,15 @@ cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float*
     a.tpi_log = dp->plan.n - P.m;
     a.total_tiles = a.tiles_per_item * items;
     a.err = err;
+    a.state = state;
+    a.item_off = item_off;
+    a.tc.nbuf = TS_NBUF;
+    a.tc.nchunks = 1 << P.ngather;
+    a.tc.chunk_bytes = (uint32_t)(sizeof(float2) << P.chunk);
+    a.tc.tile_bytes = (uint32_t)(sizeof(float2) << P.m);
+    a.tc.tiles_per_item = a.tiles_per_item;
+    a.tc.tpi_log = a.tpi_log;
+    a.tc.total_tiles = a.total_tiles;
     const long long grid = std::min<long long>(a.total_tiles, num_sms());
     pass_tcs_kernel<<<(unsigned)grid, TS_CTA_THREADS, pass_tcs_smem_bytes(), s>>>(P, a, tma);
     count_launch();
