@@ -190,6 +190,9 @@ struct PassTcsArgs {
 
 
 // ------------------------------------------------------------- kernel ----
+// ROT: some stage has register bits on tile bits 0..3 (XOR-rotated reads); the
+// passes without such stages get an instance without the un-rotation code.
+template <bool ROT>
 __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
     pass_tcs_kernel(const __grid_constant__ DevPass p, const PassTcsArgs a,
                     const __grid_constant__ TmaTile tma) {
@@ -371,7 +374,7 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
             const StageSm& S = sst[s];
             // this thread's row is group g = tid; slot v is read at register value v ^ tau,
             // tau = the group bits that land on tile bits >= 4 (bank-conflict-free reads)
-            const int tau = S.nj ? (tid & 15) >> (4 - S.nj) : 0;
+            const int tau = (ROT && S.nj) ? (tid & 15) >> (4 - S.nj) : 0;
             int L[16];
             {
                 int g;
@@ -389,7 +392,7 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
 #pragma unroll
                 for (int i = 0; i < 4; ++i) sr[i] = S.sr[i];
                 int stau = 0;
-                if (S.nj) {
+                if (ROT && S.nj) {
 #pragma unroll
                     for (int i = 0; i < 4; ++i) stau |= ((tau >> i) & 1) ? sr[i] : 0;
                 }
@@ -401,7 +404,7 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
             float2 x[16];
 #pragma unroll
             for (int v = 0; v < 16; ++v) x[v] = buf[L[v]];
-            if (S.nj) unrotate(x, tau, S.nj);
+            if (ROT && S.nj) unrotate(x, tau, S.nj);
             if (S.renorm && s == 0) {   // tile norm before the pass (unitary on the tile)
                 float p4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -485,7 +488,7 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
                 for (int v = 0; v < 16; ++v) x[v] = make_float2(x[v].x * f, x[v].y * f);
                 nin = 0.f;
             }
-            if (S.nj) unrotate(x, tau, S.nj);
+            if (ROT && S.nj) unrotate(x, tau, S.nj);
 #pragma unroll
             for (int v = 0; v < 16; ++v) buf[L[v]] = x[v];
             tc_fence_before();
@@ -604,11 +607,16 @@ cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float*
     const DevPass& P = dp->plan.passes[pass];
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(pass_tcs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(pass_tcs_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)pass_tcs_smem_bytes());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(pass_tcs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)pass_tcs_smem_bytes());
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    bool rot = false;
+    for (int si = 0; si < P.stage_count; ++si) rot = rot || dp->tcs[P.stage_begin + si].nj > 0;
     PassTcsArgs a{};
     const int grp = dp->tc_group[pass];
     a.grouped = (grp >= 0 && (w_item_stride == 0 || items == 1)) ? 1 : 0;   // one W set per CTA
@@ -631,7 +639,10 @@ cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float*
     a.tc.tpi_log = a.tpi_log;
     a.tc.total_tiles = a.total_tiles;
     const long long grid = std::min<long long>(a.total_tiles, num_sms());
-    pass_tcs_kernel<<<(unsigned)grid, TS_CTA_THREADS, pass_tcs_smem_bytes(), s>>>(P, a, tma);
+    if (rot)
+        pass_tcs_kernel<true><<<(unsigned)grid, TS_CTA_THREADS, pass_tcs_smem_bytes(), s>>>(P, a, tma);
+    else
+        pass_tcs_kernel<false><<<(unsigned)grid, TS_CTA_THREADS, pass_tcs_smem_bytes(), s>>>(P, a, tma);
     count_launch();
     return cudaGetLastError();
 }
