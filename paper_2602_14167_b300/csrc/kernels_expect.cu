@@ -1,0 +1,253 @@
+// Pauli-string expectations of complex64 states, 2^13-amplitude tiles (the fast
+// form of the expectation pass; Sec. I.B, expectation_ps).
+//
+// One pass over the state evaluates every term whose X bits lie in the tile:
+// <P> = sum_x Re( i^{#Y} conj(psi[x ^ m]) (-1)^{popc(x & z)} psi[x] ).
+//
+// Thread t of 512 holds tile offsets e + 2t + 1024 i (e = 0, 1; i = 0..7) in
+// registers r = e + 2i, read as eight 16-byte pairs.  For a term with X mask m:
+//   * m's bits 1..9 (xt) name the partner thread, m's bits 10..12 (XR) permute
+//     the pairs, m's bit 0 swaps the two amplitudes of a pair;
+//   * the Z parity splits into the thread's part (tile bits 1..9, a bit per term
+//     prepared once per pass), the tile's part (global bits, one ballot per tile
+//     for all terms) and the register part (tile bits 0, 10, 11, 12: a butterfly
+//     with +-1 factors).
+// The term loop runs over the pass's terms at run time; each term jumps to a
+// form specialised for its (XR, swap, Re/Im), so the partner pairs are read at
+// fixed offsets from one base.  Per term and tile, lane pairs add
+// their values and the even lanes accumulate them in FP32 in shared memory;
+// every 64 tiles the warps fold those sums into FP64 in a fixed order.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "launch.hpp"
+#include "tile_io.cuh"
+
+namespace tcng {
+
+namespace {
+
+constexpr int kEfTileBits = 13;
+constexpr int kEfNbuf = 3;
+constexpr int kEfAccCols = kExpThreads / 2;   // one FP32 sum per lane pair and term
+
+struct EfTerm {          // a term of the pass, prepared once per CTA
+    float4 sg;           // (-1)^{z bit} of the register bits: tile bits 0, 10, 11, 12
+    int32_t xt;          // X mask on tile bits 1..9 as a thread offset (partner thread t ^ xt)
+    int32_t var;         // 0: Z only; else 1 + 4 XR + 2 swap + im
+    int32_t pad0, pad1;
+};
+
+// sum_r (-1)^{popc(r & zr)} w_r over the 16 registers: 4-level butterfly, no branch.
+__device__ __forceinline__ float ef_butterfly(const float (&w)[kExpSlots], const float4 sg) {
+    float u[8], v[4];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) u[k] = fmaf(sg.x, w[2 * k + 1], w[2 * k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = fmaf(sg.y, u[2 * k + 1], u[2 * k]);
+    return fmaf(sg.w, fmaf(sg.z, v[3], v[2]), fmaf(sg.z, v[1], v[0]));
+}
+
+// Term with X bits: w_r = Re (IM: Im) of conj(partner) * a_r.  The partner of
+// register pair i is pair i ^ XR of thread t ^ xt: pb[512 (i ^ XR)] with pb the
+// partner thread's first pair.  (Taking the partner from the thread's own
+// registers when xt = 0 is left out: those forms raise the register count of
+// the whole term loop past the limit.)
+template <int XR, bool SWAP, bool IM>
+__device__ __forceinline__ float ef_xterm(const float2 (&a)[kExpSlots], const float4* __restrict__ pb,
+                                          const float4 sg) {
+    float w[kExpSlots];
+#pragma unroll
+    for (int i = 0; i < kExpSlots / 2; ++i) {
+        const float4 q = pb[kExpThreads * (i ^ XR)];
+        float2 b0 = make_float2(q.x, q.y), b1 = make_float2(q.z, q.w);
+        if (SWAP) {
+            const float2 tmp = b0;
+            b0 = b1;
+            b1 = tmp;
+        }
+        const float2 a0 = a[2 * i], a1 = a[2 * i + 1];
+        if (!IM) {
+            w[2 * i] = fmaf(b0.x, a0.x, b0.y * a0.y);
+            w[2 * i + 1] = fmaf(b1.x, a1.x, b1.y * a1.y);
+        } else {
+            w[2 * i] = fmaf(b0.x, a0.y, -b0.y * a0.x);
+            w[2 * i + 1] = fmaf(b1.x, a1.y, -b1.y * a1.x);
+        }
+    }
+    return ef_butterfly(w, sg);
+}
+
+__global__ void __launch_bounds__(kExpThreads, 1)
+    expect_fast_kernel(const float2* __restrict__ state, const long long* __restrict__ item_off,
+                       const __grid_constant__ DevPass p, const __grid_constant__ ExpPass ep, TileCtx tc,
+                       double* __restrict__ partial, int n_out, unsigned* __restrict__ err,
+                       const __grid_constant__ TmaTile tma) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int tile_elems = 1 << kEfTileBits;
+    float2* bufs = reinterpret_cast<float2*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(bufs + (size_t)kEfNbuf * tile_elems);
+    uint64_t* ebars = bars + kEfNbuf;                             // buffer released by every warp
+    float* acc = reinterpret_cast<float*>(ebars + kEfNbuf);      // [term][lane pair]
+    __shared__ double red[kExpThreads / 32][kExpTermsPerPass];
+    __shared__ EfTerm sx[kExpTermsPerPass];
+    __shared__ unsigned long long szg[kExpTermsPerPass];         // Z mask on global bits
+    __shared__ int s_abort, s_hasz;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int item = blockIdx.y;
+    const int nt = ep.nterms;
+    for (int i = tid; i < (kExpThreads / 32) * kExpTermsPerPass; i += kExpThreads) (&red[0][0])[i] = 0.0;
+    for (int i = tid; i < kExpTermsPerPass * kEfAccCols; i += kExpThreads) acc[i] = 0.f;
+    if (tid == 0) s_hasz = 0;
+    __syncthreads();
+    if (tid < nt) {
+        const ExpTerm T = ep.t[tid];
+        EfTerm x;
+        x.sg = make_float4((T.zm_tile & 1) ? -1.f : 1.f, ((T.zm_tile >> 10) & 1) ? -1.f : 1.f,
+                           ((T.zm_tile >> 11) & 1) ? -1.f : 1.f, ((T.zm_tile >> 12) & 1) ? -1.f : 1.f);
+        x.xt = (int)((T.xm_tile >> 1) & 511u);
+        x.var = T.xm_tile == 0 ? 0
+                               : 1 + 4 * (int)((T.xm_tile >> 10) & 7u) +
+                                     2 * (int)(T.xm_tile & 1u) + (T.ny & 1);
+        x.pad0 = x.pad1 = 0;
+        sx[tid] = x;
+        szg[tid] = T.zm_glob;
+        if (T.xm_tile == 0) s_hasz = 1;
+    }
+    // per thread and term: Z parity over tile bits 1..9, xor Re(i^ny s) = -s for ny = 1, 2
+    uint32_t fm0 = 0;
+    for (int j = 0; j < nt; ++j) {
+        const ExpTerm& T = ep.t[j];
+        const uint32_t f = (uint32_t)(__popc(((unsigned)tid << 1) & T.zm_tile & 0x3feu) & 1) ^
+                           (((T.ny & 3) == 1 || (T.ny & 3) == 2) ? 1u : 0u);
+        fm0 |= f << j;
+    }
+    if (tid == 0) {
+        for (int i = 0; i < kEfNbuf; ++i) {
+            mbar_init(&bars[i], 1);
+            mbar_init(&ebars[i], (uint32_t)(kExpThreads / 32));
+        }
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    const bool hasz = s_hasz != 0;
+    const long long t0 = (long long)item * tc.tiles_per_item;
+    const long long t1 = t0 + tc.tiles_per_item;
+    const long long first = t0 + blockIdx.x;
+    const long long stride = gridDim.x;
+    if (warp == 0)
+        for (int i = 0; i < kEfNbuf; ++i) {
+            const long long t = first + i * stride;
+            if (t < t1) issue_tile_load(state, item_off, p, tc, t, bufs + (size_t)i * tile_elems, &bars[i], lane, tma);
+        }
+    const unsigned long long lane_zg = lane < nt ? szg[lane] : 0ull;
+    auto flush = [&]() {   // even lanes' FP32 sums -> warp sum (fixed order) -> FP64
+        for (int j = 0; j < nt; ++j) {
+            float v = 0.f;
+            if (!(lane & 1)) {
+                v = acc[j * kEfAccCols + (tid >> 1)];
+                acc[j * kEfAccCols + (tid >> 1)] = 0.f;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][j] += (double)v;
+        }
+    };
+    int it = 0;
+    for (long long t = first; t < t1; t += stride, ++it) {
+        const int b = it % kEfNbuf;
+        const float2* buf = bufs + (size_t)b * tile_elems;
+        if (!mbar_wait_bounded(&bars[b], (uint32_t)((it / kEfNbuf) & 1), err)) s_abort = 1;
+        const long long gbase = tile_global_base(p, t & (tc.tiles_per_item - 1));
+        // the tile's part of every term's Z parity: one term per lane, one ballot
+        const uint32_t fm =
+            fm0 ^ __ballot_sync(0xffffffffu, (__popcll((unsigned long long)gbase & lane_zg) & 1) != 0);
+        const float4* buf4 = reinterpret_cast<const float4*>(buf);
+        float2 a[kExpSlots];
+#pragma unroll
+        for (int i = 0; i < kExpSlots / 2; ++i) {
+            const float4 q = buf4[tid + kExpThreads * i];
+            a[2 * i] = make_float2(q.x, q.y);
+            a[2 * i + 1] = make_float2(q.z, q.w);
+        }
+        float pz[kExpSlots];   // |a_r|^2 for the Z-only terms
+        if (hasz) {
+#pragma unroll
+            for (int r = 0; r < kExpSlots; ++r) pz[r] = fmaf(a[r].x, a[r].x, a[r].y * a[r].y);
+        }
+        for (int j = 0; j < nt; ++j) {
+            const EfTerm T = sx[j];
+            float v = 0.f;
+            if (T.var == 0) {
+                v = ef_butterfly(pz, T.sg);
+            } else {
+                const float4* pb = buf4 + (tid ^ T.xt);
+                switch (T.var) {
+#define TCNG_EF1(XR, SW, IM) \
+    case 1 + 4 * (XR) + 2 * (SW) + (IM): v = ef_xterm<XR, SW, IM>(a, pb, T.sg); break;
+#define TCNG_EF4(XR) TCNG_EF1(XR, 0, 0) TCNG_EF1(XR, 0, 1) TCNG_EF1(XR, 1, 0) TCNG_EF1(XR, 1, 1)
+                    TCNG_EF4(0) TCNG_EF4(1) TCNG_EF4(2) TCNG_EF4(3)
+                    TCNG_EF4(4) TCNG_EF4(5) TCNG_EF4(6) TCNG_EF4(7)
+#undef TCNG_EF4
+#undef TCNG_EF1
+                default: break;
+                }
+            }
+            v = __uint_as_float(__float_as_uint(v) ^ (((fm >> j) & 1u) << 31));
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            if (!(lane & 1)) acc[j * kEfAccCols + (tid >> 1)] += v;
+        }
+        if ((it & 63) == 63 || t + stride >= t1) flush();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ebars[b]);   // this warp is done with buf
+        if (warp == 0) {
+            const long long tn = t + (long long)kEfNbuf * stride;
+            if (tn < t1) {
+                if (!mbar_wait_bounded(&ebars[b], (uint32_t)((it / kEfNbuf) & 1), err)) s_abort = 1;
+                __syncwarp();
+                issue_tile_load(state, item_off, p, tc, tn, bufs + (size_t)b * tile_elems, &bars[b], lane, tma);
+            }
+        }
+        if (s_abort) break;
+    }
+    if (s_abort && tid == 0) {   // drain loads still in flight before the shared memory goes away
+        for (int i = 0; i < kEfNbuf; ++i) {
+            const long long ti = first + (long long)(it + 1 + i) * stride;
+            if (ti < t1) mbar_wait_bounded(&bars[(it + 1 + i) % kEfNbuf], (uint32_t)(((it + 1 + i) / kEfNbuf) & 1), err);
+        }
+    }
+    __syncthreads();
+    if (tid < nt) {   // warps in order
+        double s = 0;
+        for (int w = 0; w < kExpThreads / 32; ++w) s += red[w][tid];
+        partial[((long long)item * n_out + ep.t[tid].out) * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+}  // namespace
+
+size_t expect_fast_smem_bytes() {
+    return 128 + (size_t)kEfNbuf * (sizeof(float2) << kEfTileBits) + 16 * kEfNbuf +
+           sizeof(float) * kExpTermsPerPass * kEfAccCols;
+}
+
+cudaError_t launch_expect_fast(const float2* state, const long long* item_off, int items, const DevPass& p,
+                               const ExpPass& ep, const TileCtx& tc, double* partial, int n_out, int nblk,
+                               unsigned* err, cudaStream_t s, const TmaTile& tma) {
+    if (p.m != kEfTileBits || tc.nbuf != kEfNbuf) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(expect_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)expect_fast_smem_bytes());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((unsigned)nblk, (unsigned)items);
+    expect_fast_kernel<<<grid, kExpThreads, expect_fast_smem_bytes(), s>>>(state, item_off, p, ep, tc, partial,
+                                                                           n_out, err, tma);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace tcng

@@ -808,13 +808,12 @@ cudaError_t launch_expect_pass(const C* state, const long long* item_off, int it
     TileCtx tc = make_ctx(p, n, items, sizeof(C), nbuf);
     dim3 grid((unsigned)nblk, (unsigned)items);
     const TmaTile t0{};
-    if (sizeof(C) == 8 && p.m == 13) {   // complex64 fast path: 512 threads x 16 amplitudes
-        auto kern = expect_pass_kernel<C, true>;
-        static bool done = false;
-        static size_t lim = 0;
-        if (smem > dyn_smem_limit(kern, &done, &lim)) return cudaErrorInvalidConfiguration;
-        kern<<<grid, kExpThreads, smem, s>>>(state, item_off, p, ep, tc, partial, n_out, err, tma ? *tma : t0);
-    } else {
+    if constexpr (std::is_same<C, float2>::value) {   // complex64, 2^13 tiles: kernels_expect.cu
+        if (p.m == 13)
+            return launch_expect_fast(state, item_off, items, p, ep, tc, partial, n_out, nblk, err, s,
+                                      tma ? *tma : t0);
+    }
+    {
         auto kern = expect_pass_kernel<C, false>;
         static bool done = false;
         static size_t lim = 0;

@@ -80,4 +80,10 @@ __device__ __forceinline__ void issue_tile_store(C* state, const long long* item
     bulk_commit();
 }
 
+// The complex64 expectation pass over 2^13-amplitude tiles (kernels_expect.cu).
+size_t expect_fast_smem_bytes();
+cudaError_t launch_expect_fast(const float2* state, const long long* item_off, int items, const DevPass& p,
+                               const ExpPass& ep, const TileCtx& tc, double* partial, int n_out, int nblk,
+                               unsigned* err, cudaStream_t s, const TmaTile& tma);
+
 }  // namespace tcng
