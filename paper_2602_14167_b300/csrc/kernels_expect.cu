@@ -14,7 +14,12 @@
 //     with +-1 factors).
 // The term loop runs over the pass's terms at run time; each term jumps to a
 // form specialised for its (XR, swap, Re/Im), so the partner pairs are read at
-// fixed offsets from one base.  Per term and tile, lane pairs add
+// fixed offsets from one base.  A Pauli string is Hermitian, so the terms of x
+// and x ^ m are complex conjugates: one member of each pair, doubled, gives
+// the same sum.  With XR != 0 only the register pairs with XR's top bit clear
+// are evaluated (four partner loads instead of eight); otherwise, with X bits on
+// tile bits 6..9 (warp bits), the warps with the lowest such bit set skip the
+// term.  Partner reads from shared memory are what bound this kernel.  Per term and tile, lane pairs add
 // their values and the even lanes accumulate them in FP32 in shared memory;
 // every 64 tiles the warps fold those sums into FP64 in a fixed order.
 #include <cuda_runtime.h>
@@ -35,7 +40,8 @@ struct EfTerm {          // a term of the pass, prepared once per CTA
     float4 sg;           // (-1)^{z bit} of the register bits: tile bits 0, 10, 11, 12
     int32_t xt;          // X mask on tile bits 1..9 as a thread offset (partner thread t ^ xt)
     int32_t var;         // 0: Z only; else 1 + 4 XR + 2 swap + im
-    int32_t pad0, pad1;
+    int32_t wskip;       // >= 0: warps with this bit set skip the term (X on tile bit 6 + wskip)
+    int32_t pad1;
 };
 
 // sum_r (-1)^{popc(r & zr)} w_r over the 16 registers: 4-level butterfly, no branch.
@@ -48,14 +54,54 @@ __device__ __forceinline__ float ef_butterfly(const float (&w)[kExpSlots], const
     return fmaf(sg.w, fmaf(sg.z, v[3], v[2]), fmaf(sg.z, v[1], v[0]));
 }
 
+// The same over the 8 registers whose pair index i has bit K clear: the pair
+// bit (sg.x), then the two other pair bits in ascending order (sg.y, sg.z, sg.w
+// are the signs of pair bits 0, 1, 2).
+template <int K>
+__device__ __forceinline__ float ef_butterfly_half(const float (&w)[kExpSlots / 2], const float4 sg) {
+    const float s1 = K == 0 ? sg.z : sg.y, s2 = K == 2 ? sg.z : sg.w;
+    float u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) u[k] = fmaf(sg.x, w[2 * k + 1], w[2 * k]);
+    return fmaf(s2, fmaf(s1, u[3], u[2]), fmaf(s1, u[1], u[0]));
+}
+
+template <bool SWAP, bool IM>
+__device__ __forceinline__ void ef_pair(const float4 q, const float2 a0, const float2 a1, float& w0, float& w1) {
+    float2 b0 = make_float2(q.x, q.y), b1 = make_float2(q.z, q.w);
+    if (SWAP) {
+        const float2 tmp = b0;
+        b0 = b1;
+        b1 = tmp;
+    }
+    if (!IM) {
+        w0 = fmaf(b0.x, a0.x, b0.y * a0.y);
+        w1 = fmaf(b1.x, a1.x, b1.y * a1.y);
+    } else {
+        w0 = fmaf(b0.x, a0.y, -b0.y * a0.x);
+        w1 = fmaf(b1.x, a1.y, -b1.y * a1.x);
+    }
+}
+
 // Term with X bits: w_r = Re (IM: Im) of conj(partner) * a_r.  The partner of
 // register pair i is pair i ^ XR of thread t ^ xt: pb[512 (i ^ XR)] with pb the
-// partner thread's first pair.  (Taking the partner from the thread's own
+// partner thread's first pair.  XR != 0: the half form (pairs with bit K of i
+// clear, K = XR's top bit), doubled.  (Taking the partner from the thread's own
 // registers when xt = 0 is left out: those forms raise the register count of
 // the whole term loop past the limit.)
 template <int XR, bool SWAP, bool IM>
 __device__ __forceinline__ float ef_xterm(const float2 (&a)[kExpSlots], const float4* __restrict__ pb,
                                           const float4 sg) {
+    if constexpr (XR != 0) {
+        constexpr int K = XR >= 4 ? 2 : (XR >= 2 ? 1 : 0);
+        float w[kExpSlots / 2];
+#pragma unroll
+        for (int jj = 0; jj < kExpSlots / 4; ++jj) {
+            const int i = ((jj >> K) << (K + 1)) | (jj & ((1 << K) - 1));   // jj with a 0 inserted at bit K
+            ef_pair<SWAP, IM>(pb[kExpThreads * (i ^ XR)], a[2 * i], a[2 * i + 1], w[2 * jj], w[2 * jj + 1]);
+        }
+        return 2.f * ef_butterfly_half<K>(w, sg);
+    }
     float w[kExpSlots];
 #pragma unroll
     for (int i = 0; i < kExpSlots / 2; ++i) {
@@ -109,7 +155,10 @@ __global__ void __launch_bounds__(kExpThreads, 1)
         x.var = T.xm_tile == 0 ? 0
                                : 1 + 4 * (int)((T.xm_tile >> 10) & 7u) +
                                      2 * (int)(T.xm_tile & 1u) + (T.ny & 1);
-        x.pad0 = x.pad1 = 0;
+        // warp form: X on tile bits 6..9 (thread bits 5..8 = warp bits 0..3), none on 10..12
+        const uint32_t xw = (T.xm_tile >> 6) & 15u;
+        x.wskip = (((T.xm_tile >> 10) & 7u) == 0 && xw) ? __ffs(xw) - 1 : -1;
+        x.pad1 = 0;
         sx[tid] = x;
         szg[tid] = T.zm_glob;
         if (T.xm_tile == 0) s_hasz = 1;
@@ -181,6 +230,8 @@ __global__ void __launch_bounds__(kExpThreads, 1)
             float v = 0.f;
             if (T.var == 0) {
                 v = ef_butterfly(pz, T.sg);
+            } else if (T.wskip >= 0 && ((warp >> T.wskip) & 1)) {
+                v = 0.f;   // the warps with this bit clear carry the term (doubled)
             } else {
                 const float4* pb = buf4 + (tid ^ T.xt);
                 switch (T.var) {
@@ -193,6 +244,7 @@ __global__ void __launch_bounds__(kExpThreads, 1)
 #undef TCNG_EF1
                 default: break;
                 }
+                if (T.wskip >= 0) v *= 2.f;
             }
             v = __uint_as_float(__float_as_uint(v) ^ (((fm >> j) & 1u) << 31));
             v += __shfl_xor_sync(0xffffffffu, v, 1);
