@@ -334,62 +334,11 @@ __global__ void __launch_bounds__(512, 1) pass_kernel(C* __restrict__ state,
 // ==================================================== Pauli expectation ==
 // One pass over the state evaluates every term whose X bits lie in the tile:
 // <P> = sum_x conj(psi[x ^ m]) i^{#Y} (-1)^{popc(x & z)} psi[x] (real part).
-//
-// complex64 tiles of 2^13 amplitudes: thread t holds tile offsets
-// e + 2t + 1024 i (e = 0, 1; i = 0..7) in registers, read as 16-byte pairs, so
-// a term's Z parity splits into a per-thread part (tile bits 1..9 and the
-// tile's global bits) and a per-register part (tile bits 0, 10, 11, 12,
-// applied by a butterfly with runtime signs); the partner pair of pair i is
-// float4 (t ^ (x >> 1)) ^ 512 i, with its halves swapped when x has bit 0.
-// Each thread keeps one FP32 sum per term in a register (the term loop is
-// unrolled so the index is static) and every 64 tiles the warp folds them into
-// FP64 sums in shared memory: FP64 arithmetic stays out of the per-tile loop.
+// This is the general form (complex128, or tiles other than 2^13); complex64
+// passes over 2^13-amplitude tiles use expect_fast_kernel (kernels_expect.cu).
 // The tile buffers form a ring: each warp releases a buffer through an
 // mbarrier, and warp 0 refills it once every warp has.
-
-// w_r = Re (or Im) of conj(partner) * a_r for the 8 register pairs: partner
-// pair i is buf4[B ^ (i << 9)]; SWAP exchanges the pair's two amplitudes.
-template <bool SWAP, bool IM>
-__device__ __forceinline__ void exp_pairs(const float2 (&a)[kExpSlots], const float4* __restrict__ buf4,
-                                          int B, float (&w)[kExpSlots]) {
-#pragma unroll
-    for (int i = 0; i < kExpSlots / 2; ++i) {
-        const float4 q = buf4[B ^ (i << 9)];
-        const float2 b0 = SWAP ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
-        const float2 b1 = SWAP ? make_float2(q.x, q.y) : make_float2(q.z, q.w);
-        const float2 a0 = a[2 * i], a1 = a[2 * i + 1];
-        if (!IM) {
-            w[2 * i] = fmaf(b0.x, a0.x, b0.y * a0.y);
-            w[2 * i + 1] = fmaf(b1.x, a1.x, b1.y * a1.y);
-        } else {
-            w[2 * i] = fmaf(b0.x, a0.y, -b0.y * a0.x);
-            w[2 * i + 1] = fmaf(b1.x, a1.y, -b1.y * a1.x);
-        }
-    }
-}
-
-// sum_i (-1)^{popc(i & zhi)} w_i as a 4-level butterfly over the slot bits,
-// sg[b] = (-1)^{bit b of zhi}: no branch on the Z pattern.
-__device__ __forceinline__ float exp_butterfly(const float (&w)[kExpSlots], const float4 sg) {
-    float u[8], v[4];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) u[k] = fmaf(sg.x, w[2 * k + 1], w[2 * k]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = fmaf(sg.y, u[2 * k + 1], u[2 * k]);
-    return fmaf(sg.w, fmaf(sg.z, v[3], v[2]), fmaf(sg.z, v[1], v[0]));
-}
-
-// A term of a complex64 fast-path pass, prepared once per CTA.
-struct ExpTermSm {
-    float4 sg;          // (-1)^{z bit} for register bits: tile bits 0, 10, 11, 12
-    uint64_t zg;        // Z mask on global bits outside the tile
-    uint32_t xm;        // X mask in tile bits
-    int32_t var;        // 0: Z only; 1 + (x bit 0) + 2 (ny odd): partner variant
-    int32_t flip0;      // Re(i^ny s) = -s for ny = 1, 2
-    int32_t pad;
-};
-
-template <typename C, bool FAST>
+template <typename C>
 __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict__ state,
                                                           const long long* __restrict__ item_off,
                                                           const __grid_constant__ DevPass p,
@@ -405,29 +354,11 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
     uint64_t* ebars = bars + tc.nbuf;   // buffer released by every warp
     __shared__ double red[32][kExpTermsPerPass];
     __shared__ ExpTerm sterm[kExpTermsPerPass];   // the pass's terms, read per tile
-    __shared__ ExpTermSm sx[kExpTermsPerPass];
     __shared__ int s_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int item = blockIdx.y;
     for (int i = tid; i < 32 * kExpTermsPerPass; i += blockDim.x) (&red[0][0])[i] = 0.0;
-    if (tid < ep.nterms) {
-        const ExpTerm T = ep.t[tid];
-        sterm[tid] = T;
-        ExpTermSm x;
-        x.sg = make_float4((T.zm_tile & 1) ? -1.f : 1.f, ((T.zm_tile >> 10) & 1) ? -1.f : 1.f,
-                           ((T.zm_tile >> 11) & 1) ? -1.f : 1.f, ((T.zm_tile >> 12) & 1) ? -1.f : 1.f);
-        x.zg = T.zm_glob;
-        x.xm = T.xm_tile;
-        x.var = T.xm_tile == 0 ? 0 : 1 + (int)(T.xm_tile & 1) + 2 * (T.ny & 1);
-        x.flip0 = ((T.ny & 3) == 1 || (T.ny & 3) == 2) ? 1 : 0;
-        x.pad = 0;
-        sx[tid] = x;
-    }
-    // per-thread Z parity of every term over tile bits 1..9 (fast-path layout)
-    uint32_t tpar = 0;
-    if constexpr (FAST)
-        for (int j = 0; j < ep.nterms; ++j)
-            tpar |= (uint32_t)(__popc(((unsigned)tid << 1) & ep.t[j].zm_tile & 0x3feu) & 1) << j;
+    if (tid < ep.nterms) sterm[tid] = ep.t[tid];
     const int nwarps = (int)(blockDim.x >> 5);
     if (tid == 0) {
         for (int i = 0; i < tc.nbuf; ++i) {
@@ -447,27 +378,9 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
             const long long t = first + i * stride;
             if (t < t1) issue_tile_load(state, item_off, p, tc, t, bufs + (long long)i * tile_elems, &bars[i], lane, tma);
         }
-    // FAST: complex64, 2^13 tiles, kExpThreads threads (chosen by the launcher)
-    constexpr bool fast = FAST && std::is_same<C, float2>::value;
     double acc[kExpTermsPerPass];
-    float acc32[kExpTermsPerPass];
 #pragma unroll
-    for (int j = 0; j < kExpTermsPerPass; ++j) {
-        acc[j] = 0.0;
-        acc32[j] = 0.f;
-    }
-    auto flush32 = [&]() {   // warp sums in a fixed order, lane 0 adds into the FP64 sums
-#pragma unroll
-        for (int j = 0; j < kExpTermsPerPass; ++j) {
-            if (j < ep.nterms) {
-                float v = acc32[j];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) red[warp][j] += (double)v;
-            }
-            acc32[j] = 0.f;
-        }
-    };
+    for (int j = 0; j < kExpTermsPerPass; ++j) acc[j] = 0.0;
     int it = 0;
     for (long long t = first; t < t1; t += stride, ++it) {
         const int b = it % tc.nbuf;
@@ -476,51 +389,6 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
         // warp releases the buffer on its own (warp 0 refills it once all have)
         if (!mbar_wait_bounded(&bars[b], (uint32_t)((it / tc.nbuf) & 1), err)) s_abort = 1;
         const long long gbase = tile_global_base(p, (t & (tc.tiles_per_item - 1)));
-        if constexpr (fast) {
-            {
-                // register r = e + 2 i holds tile offset e + 2 tid + 1024 i (pairs of
-                // adjacent amplitudes read as one 16-byte load)
-                const float4* buf4 = reinterpret_cast<const float4*>(buf);
-                float2 a[kExpSlots];
-                float pz[kExpSlots];   // |a_r|^2 for the Z-only terms
-#pragma unroll
-                for (int i = 0; i < kExpSlots / 2; ++i) {
-                    const float4 q = buf4[tid + kExpThreads * i];
-                    a[2 * i] = make_float2(q.x, q.y);
-                    a[2 * i + 1] = make_float2(q.z, q.w);
-                }
-#pragma unroll
-                for (int r = 0; r < kExpSlots; ++r) pz[r] = fmaf(a[r].x, a[r].x, a[r].y * a[r].y);
-                const int nt = ep.nterms;
-#pragma unroll
-                for (int j = 0; j < kExpTermsPerPass; ++j) {   // static j: acc32[j] is a register
-                    if (j >= nt) break;   // one jump past the unused terms
-                    {
-                        const ExpTermSm X = sx[j];
-                        float v;
-                        if (X.var == 0) {
-                            v = exp_butterfly(pz, X.sg);
-                        } else {
-                            // partner pair of register pair i: float4 (tid ^ (x >> 1)) ^ 512 i;
-                            // x bit 0 swaps the two amplitudes of the pair
-                            const int B = tid ^ (int)(X.xm >> 1);
-                            float w[kExpSlots];
-                            if (X.var == 1) exp_pairs<false, false>(a, buf4, B, w);
-                            else if (X.var == 2) exp_pairs<true, false>(a, buf4, B, w);
-                            else if (X.var == 3) exp_pairs<false, true>(a, buf4, B, w);
-                            else exp_pairs<true, true>(a, buf4, B, w);
-                            v = exp_butterfly(w, X.sg);
-                        }
-                        const int f = (int)((tpar >> j) ^ (uint32_t)__popcll((unsigned long long)gbase & X.zg) ^
-                                            (uint32_t)X.flip0) & 1;
-                        acc32[j] += f ? -v : v;
-                    }
-                }
-                // every 64 tiles (and at the end) fold the FP32 sums into FP64
-                if ((it & 63) == 63 || t + stride >= t1) flush32();
-            }
-        }
-        if constexpr (!fast) {
 #pragma unroll
         for (int j = 0; j < kExpTermsPerPass; ++j) {
             if (j < ep.nterms) {
@@ -545,7 +413,6 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
                 acc[j] += (double)part;
             }
         }
-        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&ebars[b]);   // this warp is done with buf
         if (warp == 0) {
@@ -565,14 +432,12 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
         }
     }
     // deterministic block reduction: warp tree, then warps in order
-    if constexpr (!fast) {
 #pragma unroll
-        for (int j = 0; j < kExpTermsPerPass; ++j) {
-            double v = acc[j];
+    for (int j = 0; j < kExpTermsPerPass; ++j) {
+        double v = acc[j];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) red[warp][j] = v;
-        }
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][j] = v;
     }
     __syncthreads();
     if (tid < ep.nterms) {
@@ -814,7 +679,7 @@ cudaError_t launch_expect_pass(const C* state, const long long* item_off, int it
                                       tma ? *tma : t0);
     }
     {
-        auto kern = expect_pass_kernel<C, false>;
+        auto kern = expect_pass_kernel<C>;
         static bool done = false;
         static size_t lim = 0;
         if (smem > dyn_smem_limit(kern, &done, &lim)) return cudaErrorInvalidConfiguration;
