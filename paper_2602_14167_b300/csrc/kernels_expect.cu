@@ -18,10 +18,11 @@
 // and x ^ m are complex conjugates: one member of each pair, doubled, gives
 // the same sum.  With XR != 0 only the register pairs with XR's top bit clear
 // are evaluated (four partner loads instead of eight); otherwise, with X bits on
-// tile bits 6..9 (warp bits), the warps with the lowest such bit set skip the
-// term.  Partner reads from shared memory are what bound this kernel.  Per term and tile, lane pairs add
-// their values and the even lanes accumulate them in FP32 in shared memory;
-// every 64 tiles the warps fold those sums into FP64 in a fixed order.
+// tile bits 6..9 (warp bits), the warps on one side of the lowest such bit
+// (alternating per tile) skip the term.  Partner reads from shared memory
+// bound this kernel.  Per term and tile, lane pairs add their values and the
+// even lanes accumulate them in FP32 in shared memory; every 64 tiles the
+// warps fold those sums into FP64 in a fixed order.
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -40,7 +41,7 @@ struct EfTerm {          // a term of the pass, prepared once per CTA
     float4 sg;           // (-1)^{z bit} of the register bits: tile bits 0, 10, 11, 12
     int32_t xt;          // X mask on tile bits 1..9 as a thread offset (partner thread t ^ xt)
     int32_t var;         // 0: Z only; else 1 + 4 XR + 2 swap + im
-    int32_t wskip;       // >= 0: warps with this bit set skip the term (X on tile bit 6 + wskip)
+    int32_t wskip;       // >= 0: warps with this bit (xor tile parity) set skip the term (X on tile bit 6 + wskip)
     int32_t pad1;
 };
 
@@ -230,8 +231,10 @@ __global__ void __launch_bounds__(kExpThreads, 1)
             float v = 0.f;
             if (T.var == 0) {
                 v = ef_butterfly(pz, T.sg);
-            } else if (T.wskip >= 0 && ((warp >> T.wskip) & 1)) {
-                v = 0.f;   // the warps with this bit clear carry the term (doubled)
+            } else if (T.wskip >= 0 && (((warp >> T.wskip) ^ it) & 1)) {
+                // one half of the warps carries the term (doubled); the halves take
+                // turns tile by tile, so no warp runs ahead of the others
+                v = 0.f;
             } else {
                 const float4* pb = buf4 + (tid ^ T.xt);
                 switch (T.var) {
