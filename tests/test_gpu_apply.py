@@ -162,6 +162,42 @@ def test_expectations_random_strings(T, n, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_expectation_forms(T, dtype):
+    """Every specialised form of the complex64 expectation pass (2^13 tiles over
+    qubits 0..12): X on register qubits 10..12 (all 8 patterns; the half-pair forms
+    for the non-zero ones), with and without X on qubit 0 (swapped pairs), an even
+    or odd number of Y factors, the partner on a lane bit (qubit 3), a warp bit
+    (qubit 7; the alternating warp-half form), both, or the thread itself; random Z
+    factors on the tile and on qubits 13..15 (the tile's global sign)."""
+    n = 16
+    psi0 = gen.random_state(n, seed=31)
+    from paper_2602_14167_b300 import StateBatch
+    from workloads import pauli_terms
+    rng = np.random.default_rng(5)
+    specs = []
+    for xr in range(8):
+        for sw in (0, 1):
+            for part in ((), (3,), (7,), (3, 7)):
+                for im in (0, 1):
+                    xq = [10 + k for k in range(3) if (xr >> k) & 1] + ([0] if sw else []) + list(part)
+                    if not xq:
+                        continue
+                    d = {q: "X" for q in xq}
+                    if im:
+                        d[xq[0]] = "Y"
+                    for q in rng.choice([q for q in range(n) if q not in d], size=3, replace=False):
+                        d[int(q)] = "Z"
+                    specs.append(d)
+    strings = pauli_terms(specs)
+    st = StateBatch(n, dtype=dtype)
+    st.amplitudes(0).copy_(torch.tensor(psi0, dtype=st.cdtype, device="cuda"))
+    vals = st.expect(strings)[0].cpu().numpy()
+    ref_psi = st.amplitudes(0).cpu().numpy().astype(np.complex128)
+    vref = sv.expect(n, ref_psi, strings).real
+    assert np.max(np.abs(vals - vref)) < (1e-6 if dtype == "c64" else 1e-12)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
 def test_expectations_scattered_gathers(T, dtype):
     """Terms whose X bits scatter over the high qubits: tiles that need more than five
     tensor-map dimensions (gather4 rows for 2^7 chunks, bulk copies for wider chunks)."""
