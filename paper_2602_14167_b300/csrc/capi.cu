@@ -263,8 +263,18 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
             if (tma_base && (items == 1 || item_stride > 0))
                 tma = make_tma_tile(tma_base, pl.n, (int)sizeof(C), p, items, item_stride);
             if (wops && dp->tc_pass[pi]) {   // tile map, else one bulk copy per chunk
+                // stages on tile bits 0..3 read conflict-free from a 128-byte swizzled tile
+                bool rot = false, swz = false;
+                for (int si = 0; si < p.stage_count; ++si) rot = rot || dp->tcs[p.stage_begin + si].nj > 0;
+                if (rot && p.chunk >= 4 && tma.rank) {
+                    const TmaTile ts = make_tma_tile(tma_base, pl.n, (int)sizeof(C), p, items, item_stride, true);
+                    if (ts.rank) {
+                        tma = ts;
+                        swz = true;
+                    }
+                }
                 ProfScope ps("pass_tcs_kernel_c64", s);
-                e = launch_pass_tcs(dp, (int)pi, items, wops, w_stride, ctx().err, tma,
+                e = launch_pass_tcs(dp, (int)pi, items, wops, w_stride, ctx().err, tma, swz,
                                     reinterpret_cast<float2*>(state), d_item_off, s);
                 if (e != cudaSuccess) return cuda_fail(e, "tensor-core pass kernel");
                 continue;

@@ -117,8 +117,8 @@ void plan_tensor_stages(DevPlan* dp);
 cudaError_t launch_build_stage_w(const DevPlan* dp, const double2* table, long long table_stride,
                                  int items, float* wops, cudaStream_t s);
 cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float* wops,
-                            long long w_item_stride, unsigned* err, const TmaTile& tma, float2* state,
-                            const long long* item_off, cudaStream_t s);
+                            long long w_item_stride, unsigned* err, const TmaTile& tma, bool swizzled,
+                            float2* state, const long long* item_off, cudaStream_t s);
 
 // Synchronous upload of a host vector (used once per structure); throws bad_alloc.
 

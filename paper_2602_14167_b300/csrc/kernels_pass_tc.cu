@@ -183,6 +183,7 @@ struct PassTcsArgs {
     int tpi_log;
     long long total_tiles;
     unsigned* err;
+    int swz;                  // 1: the tile is 128-byte swizzled in shared memory (TMA)
     float2* state;              // tile copies: state + item_off[item], in the pass's copy form
     const long long* item_off;
     TileCtx tc;
@@ -391,6 +392,11 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
                 int sr[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) sr[i] = S.sr[i];
+                if (a.swz) {   // slot offset o lies at o ^ ((o >> 3) & 0xE) (linear in o)
+                    g ^= (g >> 3) & 0xe;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) sr[i] ^= (sr[i] >> 3) & 0xe;
+                }
                 int stau = 0;
                 if (ROT && S.nj) {
 #pragma unroll
@@ -602,8 +608,8 @@ cudaError_t launch_build_stage_w(const DevPlan* dp, const double2* table, long l
 }
 
 cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float* wops,
-                            long long w_item_stride, unsigned* err, const TmaTile& tma, float2* state,
-                            const long long* item_off, cudaStream_t s) {
+                            long long w_item_stride, unsigned* err, const TmaTile& tma, bool swizzled,
+                            float2* state, const long long* item_off, cudaStream_t s) {
     const DevPass& P = dp->plan.passes[pass];
     static bool attr = false;
     if (!attr) {
@@ -615,8 +621,9 @@ cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float*
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    bool rot = false;
+    bool rot = false;   // XOR-rotated slot reads (not needed on a swizzled tile)
     for (int si = 0; si < P.stage_count; ++si) rot = rot || dp->tcs[P.stage_begin + si].nj > 0;
+    rot = rot && !swizzled;
     PassTcsArgs a{};
     const int grp = dp->tc_group[pass];
     a.grouped = (grp >= 0 && (w_item_stride == 0 || items == 1)) ? 1 : 0;   // one W set per CTA
@@ -629,6 +636,7 @@ cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float*
     a.tpi_log = dp->plan.n - P.m;
     a.total_tiles = a.tiles_per_item * items;
     a.err = err;
+    a.swz = swizzled ? 1 : 0;
     a.state = state;
     a.item_off = item_off;
     a.tc.nbuf = TS_NBUF;

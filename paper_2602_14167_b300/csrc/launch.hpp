@@ -44,8 +44,11 @@ struct alignas(64) TmaTile {
 
 // Build the tensor map of a pass (returns rank 0 if the pass needs > 5 dims or
 // the encoder rejects it).  items > 1 needs equally spaced items (stride bytes).
+// sw128: the tile lands in shared memory with the 128-byte swizzle (rows of 128
+// bytes whose 16-byte chunk index is XORed with the row index mod 8); needs a
+// 1024-byte aligned destination and a low chunk of at least 128 bytes.
 TmaTile make_tma_tile(void* base, int n, int elem_bytes, const DevPass& p, int items,
-                      long long item_stride_bytes);
+                      long long item_stride_bytes, bool sw128 = false);
 // A pass's tiles as rows of one chunk (2^chunk amplitudes, at most 256 8-byte
 // elements), four arbitrary rows per tile::gather4 copy (for passes whose bit
 // runs need more than five tensor dimensions).  base_elems: element offset of

@@ -29,7 +29,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 TmaTile make_tma_tile(void* base, int n, int elem_bytes, const DevPass& p, int items,
-                      long long item_stride_bytes) {
+                      long long item_stride_bytes, bool sw128) {
     TmaTile t;
     std::memset(&t, 0, sizeof t);
     auto fn = encode_fn();
@@ -51,7 +51,8 @@ TmaTile make_tma_tile(void* base, int n, int elem_bytes, const DevPass& p, int i
         while (done < len) {
             int piece = len - done;
             if (tile) {
-                const int cap = (rank == 0) ? (e == 1 ? 8 : 7) : 8;
+                // sw128: the innermost box dimension is one 128-byte swizzle row
+                const int cap = (rank == 0) ? (sw128 ? (e == 1 ? 4 : 3) : (e == 1 ? 8 : 7)) : 8;
                 if (piece > cap) piece = cap;
             }
             if (rank == 5) return TmaTile{};   // too many dimensions
@@ -81,7 +82,7 @@ TmaTile make_tma_tile(void* base, int n, int elem_bytes, const DevPass& p, int i
         ++rank;
     }
     CUresult r = fn(&t.map, CU_TENSOR_MAP_DATA_TYPE_INT64, (cuuint32_t)rank, base, gdim, gstride, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, sw128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return TmaTile{};
     t.rank = rank;
