@@ -183,7 +183,6 @@ struct PassTcsArgs {
     int tpi_log;
     long long total_tiles;
     unsigned* err;
-    int swz;                  // 1: the tile is 128-byte swizzled in shared memory (TMA)
     float2* state;              // tile copies: state + item_off[item], in the pass's copy form
     const long long* item_off;
     TileCtx tc;
@@ -191,9 +190,10 @@ struct PassTcsArgs {
 
 
 // ------------------------------------------------------------- kernel ----
-// ROT: some stage has register bits on tile bits 0..3 (XOR-rotated reads); the
-// passes without such stages get an instance without the un-rotation code.
-template <bool ROT>
+// ROT: some stage has register bits on tile bits 0..3 (XOR-rotated reads); SWZ:
+// the tile is 128-byte swizzled instead (no rotation).  The passes without such
+// stages get an instance with neither.
+template <bool ROT, bool SWZ>
 __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
     pass_tcs_kernel(const __grid_constant__ DevPass p, const PassTcsArgs a,
                     const __grid_constant__ TmaTile tma) {
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
                 int sr[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) sr[i] = S.sr[i];
-                if (a.swz) {   // slot offset o lies at o ^ ((o >> 3) & 0xE) (linear in o)
+                if (SWZ) {   // slot offset o lies at o ^ ((o >> 3) & 0xE) (linear in o)
                     g ^= (g >> 3) & 0xe;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) sr[i] ^= (sr[i] >> 3) & 0xe;
@@ -613,10 +613,13 @@ cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float*
     const DevPass& P = dp->plan.passes[pass];
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(pass_tcs_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)pass_tcs_smem_bytes());
+        cudaError_t e = cudaFuncSetAttribute(pass_tcs_kernel<true, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_tcs_smem_bytes());
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(pass_tcs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(pass_tcs_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)pass_tcs_smem_bytes());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(pass_tcs_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)pass_tcs_smem_bytes());
         if (e != cudaSuccess) return e;
         attr = true;
@@ -636,7 +639,6 @@ cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float*
     a.tpi_log = dp->plan.n - P.m;
     a.total_tiles = a.tiles_per_item * items;
     a.err = err;
-    a.swz = swizzled ? 1 : 0;
     a.state = state;
     a.item_off = item_off;
     a.tc.nbuf = TS_NBUF;
@@ -647,10 +649,13 @@ cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float*
     a.tc.tpi_log = a.tpi_log;
     a.tc.total_tiles = a.total_tiles;
     const long long grid = std::min<long long>(a.total_tiles, num_sms());
+    const size_t sm = pass_tcs_smem_bytes();
     if (rot)
-        pass_tcs_kernel<true><<<(unsigned)grid, TS_CTA_THREADS, pass_tcs_smem_bytes(), s>>>(P, a, tma);
+        pass_tcs_kernel<true, false><<<(unsigned)grid, TS_CTA_THREADS, sm, s>>>(P, a, tma);
+    else if (swizzled)
+        pass_tcs_kernel<false, true><<<(unsigned)grid, TS_CTA_THREADS, sm, s>>>(P, a, tma);
     else
-        pass_tcs_kernel<false><<<(unsigned)grid, TS_CTA_THREADS, pass_tcs_smem_bytes(), s>>>(P, a, tma);
+        pass_tcs_kernel<false, false><<<(unsigned)grid, TS_CTA_THREADS, sm, s>>>(P, a, tma);
     count_launch();
     return cudaGetLastError();
 }
