@@ -314,7 +314,12 @@ void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
         if ((terms[t].xmask & ~lim) || (terms[t].zmask & ~lim))
             throw std::invalid_argument("Pauli mask outside the register");
     m = std::min(m, n);
-    const int low0 = std::min(low, m);
+    // at most 6 contiguous low bits: a pass then gathers up to m - 6 high qubits, so
+    // fewer passes hold the same terms (32 qubits, 64 weight-4 strings + TFIM: 13
+    // passes instead of 16 with 7 bits, a 1.7 % faster step; 5 bits: slower, the
+    // 256-byte rows stream less well)
+    constexpr int kExpLowBits = 6;
+    const int low0 = std::min(std::min(low, m), kExpLowBits);
     auto mask_below = [](int b) { return b >= 64 ? ~0ULL : ((1ULL << b) - 1); };
     // a tile keeps at least its lowest qubit contiguous (16-byte copies), so a term
     // may have at most m - 1 X/Y factors above qubit 0
