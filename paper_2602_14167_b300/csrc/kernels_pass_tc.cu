@@ -19,11 +19,14 @@
 // norm is restored to its norm before the pass: this removes the systematic
 // shrink of the round-toward-zero accumulation.
 // W_s (hi and lo, 128-byte swizzled, K-major) streams from global memory (L2)
-// through a three-slot ring, two stages ahead.  A seventeenth warp only moves
-// tiles: it stores a tile once all four slices report it done and loads the tile
-// two ahead into the freed buffer, so no compute warp waits on a TMA issue.  Rows whose register bits
-// include tile bits 0..3 read their slots XOR-rotated (bank-conflict free) and
-// undo the rotation in registers around the MMA.
+// through a three-slot ring, two stages ahead (or stays resident for passes of
+// at most three stages).  A seventeenth warp only moves tiles: it stores a tile
+// once all four slices report it done and loads the tile two ahead into the
+// freed buffer, so no compute warp waits on a TMA issue.  Rows whose register
+// bits include tile bits 0..3 would put all 32 lanes on one bank: such passes
+// either load the tile 128-byte swizzled (TMA) and address it through the same
+// XOR map, or read their slots XOR-rotated per lane and undo the rotation in
+// registers around the MMA (a separate kernel instance each).
 #include <cuda_runtime.h>
 
 #include <algorithm>
