@@ -345,6 +345,22 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
             while (w_issued < TS_NB - 1 && w_issued < total_q) issue_w();
         }
     }
+    // row base of each stage (fixed per thread for the whole pass), computed once in
+    // the plain instance for independent-slice passes of up to three stages
+    int gpre0 = 0, gpre1 = 0, gpre2 = 0;
+    const bool use_gpre = !ROT && !SWZ && a.grouped && nst <= 3;
+    if (use_gpre) {
+        for (int s = 0; s < nst; ++s) {
+            const StageSm& S = sst[s];
+            int g = tid & 127;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) g += g & S.hm[i];
+            g |= (((tid >> 7) & 1) << S.gb0) | (((tid >> 8) & 1) << S.gb1);
+            if (s == 0) gpre0 = g;
+            else if (s == 1) gpre1 = g;
+            else gpre2 = g;
+        }
+    }
     long long q = 0;
     long long it = 0;
     for (long long t = first; t < a.total_tiles; t += stride, ++it) {
@@ -382,7 +398,9 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
             int L[16];
             {
                 int g;
-                if (a.grouped) {   // slice bits of tid -> the pass's fixed tile bits
+                if (use_gpre) {
+                    g = s == 0 ? gpre0 : (s == 1 ? gpre1 : gpre2);
+                } else if (a.grouped) {   // slice bits of tid -> the pass's fixed tile bits
                     g = tid & 127;
 #pragma unroll
                     for (int i = 0; i < 6; ++i) g += g & S.hm[i];
@@ -492,7 +510,7 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
                         to += r.y;
                     }
                 }
-                const float f = to > 0.f ? sqrtf(ti / to) : 1.f;
+                const float f = (to > 0.f && ti > 0.f) ? ti * rsqrtf(ti * to) : 1.f;   // sqrt(ti / to)
 #pragma unroll
                 for (int v = 0; v < 16; ++v) x[v] = make_float2(x[v].x * f, x[v].y * f);
                 nin = 0.f;
