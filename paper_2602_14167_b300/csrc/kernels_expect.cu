@@ -23,6 +23,12 @@
 // bound this kernel.  Per term and tile, lane pairs add their values and the
 // even lanes accumulate them in FP32 in shared memory; every 64 tiles the
 // warps fold those sums into FP64 in a fixed order.
+// Tiles whose bit runs fit a tensor map arrive by one TMA copy (warp 0 refills a
+// buffer once every warp has released it).  Others (gathered qubits scattered
+// over more than five dimensions) are copied by all 512 threads with 16-byte
+// cp.async pieces, which stream these scattered rows at the contiguous rate
+// where per-row TMA copies do not; each warp loads its share of tile i + 2 at
+// the end of tile i, once every warp has left tile i - 1.
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -32,6 +38,21 @@
 namespace tcng {
 
 namespace {
+
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src_gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src_gmem) : "memory");
+}
+// The mbarrier counts one arrival when all of this thread's earlier cp.async copies land.
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Global element offset (from the tile base) of tile element x: the low chunk
+// bits stay, the row bits land on the gathered qubits.  Linear in x (an OR of
+// per-bit parts), so disjoint parts of x can be mapped separately.
+__device__ __forceinline__ long long ef_tile_offset(const DevPass& p, int x) {
+    return (long long)(x & ((1 << p.chunk) - 1)) | chunk_offset(p, x >> p.chunk);
+}
 
 constexpr int kEfTileBits = 13;
 constexpr int kEfNbuf = 3;
@@ -140,6 +161,7 @@ __global__ void __launch_bounds__(kExpThreads, 1)
     __shared__ EfTerm sx[kExpTermsPerPass];
     __shared__ unsigned long long szg[kExpTermsPerPass];         // Z mask on global bits
     __shared__ int s_abort, s_hasz;
+    __shared__ long long s_koff[3];   // cp.async form: offsets of tile elements 1024, 2048, 4096
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int item = blockIdx.y;
     const int nt = ep.nterms;
@@ -172,11 +194,13 @@ __global__ void __launch_bounds__(kExpThreads, 1)
                            (((T.ny & 3) == 1 || (T.ny & 3) == 2) ? 1u : 0u);
         fm0 |= f << j;
     }
+    const bool simt = tma.rank == 0;   // no tile map: cp.async pieces by every thread
     if (tid == 0) {
         for (int i = 0; i < kEfNbuf; ++i) {
-            mbar_init(&bars[i], 1);
+            mbar_init(&bars[i], simt ? (uint32_t)kExpThreads : 1u);
             mbar_init(&ebars[i], (uint32_t)(kExpThreads / 32));
         }
+        for (int k = 0; k < 3; ++k) s_koff[k] = ef_tile_offset(p, 1024 << k);
         fence_mbar_init();
         s_abort = 0;
     }
@@ -186,11 +210,30 @@ __global__ void __launch_bounds__(kExpThreads, 1)
     const long long t1 = t0 + tc.tiles_per_item;
     const long long first = t0 + blockIdx.x;
     const long long stride = gridDim.x;
-    if (warp == 0)
+    // cp.async form: this thread copies pieces tid + 512 k (elements 2 tid + 1024 k, k = 0..7)
+    const long long my_off = ef_tile_offset(p, 2 * tid);
+    const float2* item_state = state + item_off[item];
+    auto simt_load = [&](long long t, int bb) {
+        const long long gb = tile_global_base(p, t & (tc.tiles_per_item - 1));
+        float2* dst = bufs + (size_t)bb * tile_elems + 2 * tid;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const long long ko = ((k & 1) ? s_koff[0] : 0) | ((k & 2) ? s_koff[1] : 0) | ((k & 4) ? s_koff[2] : 0);
+            cp_async16(dst + 1024 * k, item_state + (gb + (my_off | ko)));
+        }
+        cp_async_arrive(&bars[bb]);
+    };
+    if (simt) {
+        for (int i = 0; i < 2; ++i) {
+            const long long t = first + i * stride;
+            if (t < t1) simt_load(t, i);
+        }
+    } else if (warp == 0) {
         for (int i = 0; i < kEfNbuf; ++i) {
             const long long t = first + i * stride;
             if (t < t1) issue_tile_load(state, item_off, p, tc, t, bufs + (size_t)i * tile_elems, &bars[i], lane, tma);
         }
+    }
     const unsigned long long lane_zg = lane < nt ? szg[lane] : 0ull;
     auto flush = [&]() {   // even lanes' FP32 sums -> warp sum (fixed order) -> FP64
         for (int j = 0; j < nt; ++j) {
@@ -256,7 +299,14 @@ __global__ void __launch_bounds__(kExpThreads, 1)
         if ((it & 63) == 63 || t + stride >= t1) flush();
         __syncwarp();
         if (lane == 0) mbar_arrive(&ebars[b]);   // this warp is done with buf
-        if (warp == 0) {
+        if (simt) {   // this warp's share of tile it + 2, into the buffer of tile it - 1
+            const long long tn = t + 2 * stride;
+            if (tn < t1) {
+                if (it >= 1 && !mbar_wait_bounded(&ebars[(it + 2) % kEfNbuf], (uint32_t)(((it - 1) / kEfNbuf) & 1), err))
+                    s_abort = 1;
+                simt_load(tn, (it + 2) % kEfNbuf);
+            }
+        } else if (warp == 0) {
             const long long tn = t + (long long)kEfNbuf * stride;
             if (tn < t1) {
                 if (!mbar_wait_bounded(&ebars[b], (uint32_t)((it / kEfNbuf) & 1), err)) s_abort = 1;
@@ -266,7 +316,8 @@ __global__ void __launch_bounds__(kExpThreads, 1)
         }
         if (s_abort) break;
     }
-    if (s_abort && tid == 0) {   // drain loads still in flight before the shared memory goes away
+    asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's copies (cp.async form)
+    if (s_abort && tid == 0 && !simt) {   // drain loads still in flight before the shared memory goes away
         for (int i = 0; i < kEfNbuf; ++i) {
             const long long ti = first + (long long)(it + 1 + i) * stride;
             if (ti < t1) mbar_wait_bounded(&bars[(it + 1 + i) % kEfNbuf], (uint32_t)(((it + 1 + i) / kEfNbuf) & 1), err);
