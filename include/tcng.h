@@ -310,7 +310,7 @@ typedef enum {
     TCNG_OPT_FUSE_WIDTH = 0,   /* max qubits of a fused block, 1..5 (default 2) */
     TCNG_OPT_TILE_BITS = 1,    /* log2 amplitudes per shared-memory tile, 5..13 (default 13) */
     TCNG_OPT_CHUNK_BITS = 2,   /* log2 contiguous amplitudes per copied chunk (default 7;
-                                  expectation passes use at most 6) */
+                                  expectation passes use at most 3) */
     TCNG_OPT_USE_GRAPHS = 3,   /* 1: replay CUDA graphs per structure (default 1) */
     TCNG_OPT_UNFUSED = 4,      /* 1: one pair/quartet kernel launch per gate (default 0) */
     TCNG_OPT_TENSOR_CORES = 5  /* complex64 register stages as 16x16 GEMMs on the tensor cores

@@ -314,11 +314,12 @@ void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
         if ((terms[t].xmask & ~lim) || (terms[t].zmask & ~lim))
             throw std::invalid_argument("Pauli mask outside the register");
     m = std::min(m, n);
-    // at most 6 contiguous low bits: a pass then gathers up to m - 6 high qubits, so
-    // fewer passes hold the same terms (32 qubits, 64 weight-4 strings + TFIM: 13
-    // passes instead of 16 with 7 bits, a 1.7 % faster step; 5 bits: slower, the
-    // 256-byte rows stream less well)
-    constexpr int kExpLowBits = 6;
+    // at most 3 contiguous low bits: a pass then gathers up to m - 3 high qubits, so
+    // fewer passes hold the same terms.  The scattered rows stream well through the
+    // complex64 kernel's cp.async copies (32 qubits, 64 weight-4 strings + TFIM: 8
+    // passes and a 586 ms step with 3 bits; 626 ms with 6, 650 ms with 7, 602 ms
+    // with 2 (10 passes))
+    constexpr int kExpLowBits = 3;
     const int low0 = std::min(std::min(low, m), kExpLowBits);
     auto mask_below = [](int b) { return b >= 64 ? ~0ULL : ((1ULL << b) - 1); };
     // a tile keeps at least its lowest qubit contiguous (16-byte copies), so a term
