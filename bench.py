@@ -43,7 +43,7 @@ PASS_KERNELS = ("pass_kernel_c64", "pass_tcs_kernel_c64")
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one 28-qubit
 # launch from an ncu capture of this kernel, scaled by the state size; a kernel
 # changed since its capture has no entry.
-TRAFFIC_28Q = {"pass_tcs_kernel_c64": 2.148048e9 + 2.087302e9}
+TRAFFIC_28Q = {"pass_tcs_kernel_c64": 4.234933e9}
 
 
 def workload(n=N_QUBITS, depth=DEPTH):
@@ -291,7 +291,8 @@ def run_gpu(args):
                       "chunk_bits": T.tcng_get_option(T.OPT_CHUNK_BITS),
                       "tensor_cores": T.tcng_get_option(T.OPT_TENSOR_CORES),
                       "ms_per_layer": ms_step / DP,
-                      "l2": "inputs larger than L2 (32 GiB state), no flush",
+                      "l2": (f"inputs larger than L2 ({S / 2**30:g} GiB state), no flush" if S > 126e6
+                             else f"state ({S / 2**20:g} MiB) fits in L2, no flush"),
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": (achieved / peak) if achieved else None,

@@ -18,11 +18,13 @@
 // in a grouped pass, on each slice), so after the last stage the tile's (slice's)
 // norm is restored to its norm before the pass: this removes the systematic
 // shrink of the round-toward-zero accumulation.
-// W_s (hi and lo, 128-byte swizzled, K-major) streams from global memory (L2)
-// through a three-slot ring, two stages ahead (or stays resident for passes of
-// at most three stages).  A seventeenth warp only moves tiles: it stores a tile
-// once all four slices report it done and loads the tile two ahead into the
-// freed buffer, so no compute warp waits on a TMA issue.  Rows whose register
+// W_s (hi and lo, 128-byte swizzled, K-major) is loaded once per CTA when one W
+// set serves every tile: into the three ring slots for passes of up to three
+// stages, else into an 11-slot layout with two tile buffers instead of three;
+// per-item W streams from global memory (L2) through the three-slot ring, two
+// stages ahead.  A seventeenth warp only moves tiles: it stores a tile once all
+// four slices report it done and loads the tile two ahead into a freed buffer,
+// so no compute warp waits on a TMA issue.  Rows whose register
 // bits include tile bits 0..3 would put all 32 lanes on one bank: such passes
 // either load the tile 128-byte swizzled (TMA) and address it through the same
 // XOR map, or read their slots XOR-rotated per lane and undo the rotation in
@@ -46,6 +48,10 @@ constexpr int TS_PRODUCER_WARP = TS_THREADS / 32;
 constexpr int TS_TILE_BITS = 13;
 constexpr int TS_NBUF = 3;                         // tile buffers
 constexpr int TS_NB = 3;                           // W ring slots
+// the resident-W configuration: two tile buffers and room for the W operands of
+// every stage of a pass of up to 11 stages (one W set shared by all tiles)
+constexpr int TS_NBUF_RES = 2;
+constexpr int TS_NB_RES = 11;
 constexpr uint32_t TS_W_FLOATS = 2 * 32 * 32;      // hi + lo
 constexpr uint32_t TS_W_BYTES = TS_W_FLOATS * 4;   // 8 KiB
 constexpr uint32_t TS_TMEM_COLS = 512;             // 4 slices x (A hi 32 + A lo 32 + D 64)
@@ -178,6 +184,7 @@ __device__ __forceinline__ void unrotate(float2 (&a)[16], int tau, int nj) {
 
 struct PassTcsArgs {
     int grouped;              // 1: slices run independently (see plan_tensor_stages)
+    int wres;                 // 1: every stage's W loaded once (one W set for all tiles)
     int gb0, gb1;             // their fixed tile bits
     const TcsStage* tcs;      // this pass's stages
     const float* wops;        // W operands, [item][tensor-core stage]
@@ -196,17 +203,18 @@ struct PassTcsArgs {
 // ROT: some stage has register bits on tile bits 0..3 (XOR-rotated reads); SWZ:
 // the tile is 128-byte swizzled instead (no rotation).  The passes without such
 // stages get an instance with neither.
-template <bool ROT, bool SWZ>
+// NBUF tile buffers, NB W slots (a ring, or every stage's W resident when a.wres).
+template <bool ROT, bool SWZ, int NBUF, int NB>
 __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
     pass_tcs_kernel(const __grid_constant__ DevPass p, const PassTcsArgs a,
                     const __grid_constant__ TmaTile tma) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    unsigned char* wring = base;                                            // TS_NB x 8 KiB
-    float2* bufs = reinterpret_cast<float2*>(base + TS_NB * TS_W_BYTES);    // TS_NBUF tiles
+    unsigned char* wring = base;                                            // NB x 8 KiB
+    float2* bufs = reinterpret_cast<float2*>(base + NB * TS_W_BYTES);    // NBUF tiles
     constexpr int tile_elems = 1 << TS_TILE_BITS;
-    __shared__ uint64_t tile_bar[TS_NBUF], w_bar[TS_NB], mma_bar[4];
-    __shared__ uint64_t done_bar[TS_NBUF];   // the four slices finished a tile
+    __shared__ uint64_t tile_bar[NBUF], w_bar[NB], mma_bar[4];
+    __shared__ uint64_t done_bar[NBUF];   // the four slices finished a tile
     __shared__ uint64_t stag_bar;            // grouped: slices 2, 3 started (once)
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
@@ -252,10 +260,10 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
         sst[i] = d;
     }
     if (tid == 0) {
-        for (int i = 0; i < TS_NBUF; ++i) mbar_init(&tile_bar[i], 1);
-        for (int i = 0; i < TS_NB; ++i) mbar_init(&w_bar[i], 1);
+        for (int i = 0; i < NBUF; ++i) mbar_init(&tile_bar[i], 1);
+        for (int i = 0; i < NB; ++i) mbar_init(&w_bar[i], 1);
         for (int i = 0; i < 4; ++i) mbar_init(&mma_bar[i], 1);
-        for (int i = 0; i < TS_NBUF; ++i) mbar_init(&done_bar[i], 4);
+        for (int i = 0; i < NBUF; ++i) mbar_init(&done_bar[i], 4);
         mbar_init(&stag_bar, 2);
         fence_mbar_init();
         s_abort = 0;
@@ -274,20 +282,23 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
     if (warp == TS_PRODUCER_WARP) {   // ---------------------------- tile mover --
         // the whole warp issues the copies (the gather4 and per-chunk forms use every lane)
         const int lane = tid & 31;
+        // loads run two tiles ahead: with three buffers into the one stored a tile
+        // ago, with two into the one just stored (once its store has read it)
+        constexpr int ahead = NBUF == 2 ? 2 : NBUF - 1;
         long long issued = 0;
-        for (; issued < TS_NBUF - 1 && issued < my_tiles; ++issued)
+        for (; issued < ahead && issued < my_tiles; ++issued)
             issue_tile_load(a.state, a.item_off, p, a.tc, first + issued * stride, bufs + issued * tile_elems,
                             &tile_bar[issued], lane, tma);
         for (long long i = 0; i < my_tiles; ++i) {
-            const int b = (int)(i % TS_NBUF);
+            const int b = (int)(i % NBUF);
             // lane 0 waits for the four slices (or gives up when they abort)
             uint32_t done = 0;
             if (lane == 0) {
-                done = mbar_try_wait(&done_bar[b], (uint32_t)((i / TS_NBUF) & 1));
+                done = mbar_try_wait(&done_bar[b], (uint32_t)((i / NBUF) & 1));
                 const unsigned long long t0 = global_ns();
                 for (uint32_t k = 1; !done; ++k) {
                     if (*reinterpret_cast<volatile int*>(&s_abort)) break;
-                    done = mbar_try_wait(&done_bar[b], (uint32_t)((i / TS_NBUF) & 1));
+                    done = mbar_try_wait(&done_bar[b], (uint32_t)((i / NBUF) & 1));
                     if (!done && (k & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
                         atomicOr(a.err, ERR_TIMEOUT);
                         s_abort = 1;
@@ -298,10 +309,13 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
             if (!__shfl_sync(0xffffffffu, done, 0)) break;
             issue_tile_store(a.state, a.item_off, p, a.tc, first + i * stride, bufs + (size_t)b * tile_elems,
                              lane, tma);
-            if (issued < my_tiles) {   // the next load reuses the buffer stored one tile ago
-                bulk_wait_read<1>();
+            if (issued < my_tiles) {
+                if (NBUF == 2)
+                    bulk_wait_read<0>();
+                else
+                    bulk_wait_read<1>();
                 __syncwarp();
-                const int bn = (int)(issued % TS_NBUF);
+                const int bn = (int)(issued % NBUF);
                 issue_tile_load(a.state, a.item_off, p, a.tc, first + issued * stride,
                                 bufs + (size_t)bn * tile_elems, &tile_bar[bn], lane, tma);
                 ++issued;
@@ -311,8 +325,8 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
         // after an abort: the last loads (at most one per buffer) may still be in
         // flight; wait for them before the shared memory goes away
         if (lane == 0)
-            for (long long i = issued > TS_NBUF ? issued - TS_NBUF : 0; i < issued; ++i)
-                mbar_wait_bounded(&tile_bar[i % TS_NBUF], (uint32_t)((i / TS_NBUF) & 1), a.err);
+            for (long long i = issued > NBUF ? issued - NBUF : 0; i < issued; ++i)
+                mbar_wait_bounded(&tile_bar[i % NBUF], (uint32_t)((i / NBUF) & 1), a.err);
         __syncwarp();
         tc_fence_before();
         __syncthreads();
@@ -325,7 +339,7 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
     auto issue_w = [&]() {
         const long long item = (first + w_t * stride) >> a.tpi_log;
         const float* src = a.wops + item * a.w_item_stride + (long long)sst[w_s].tc_index * TS_W_FLOATS;
-        const int slot = (int)(w_issued % TS_NB);
+        const int slot = (int)(w_issued % NB);
         mbar_arrive_expect_tx(&w_bar[slot], TS_W_BYTES);
         bulk_g2s(wring + (size_t)slot * TS_W_BYTES, src, TS_W_BYTES, &w_bar[slot]);
         ++w_issued;
@@ -335,14 +349,14 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
         }
     };
     if (tid == 0) {
-        if (a.grouped) {   // every stage's W stays resident (one set for all items)
+        if (a.wres) {   // every stage's W stays resident (one set for all items)
             for (int st = 0; st < nst && my_tiles > 0; ++st) {
                 mbar_arrive_expect_tx(&w_bar[st], TS_W_BYTES);
                 bulk_g2s(wring + (size_t)st * TS_W_BYTES, a.wops + (long long)sst[st].tc_index * TS_W_FLOATS,
                          TS_W_BYTES, &w_bar[st]);
             }
         } else {
-            while (w_issued < TS_NB - 1 && w_issued < total_q) issue_w();
+            while (w_issued < NB - 1 && w_issued < total_q) issue_w();
         }
     }
     // row base of each stage (fixed per thread for the whole pass), computed once in
@@ -364,9 +378,9 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
     long long q = 0;
     long long it = 0;
     for (long long t = first; t < a.total_tiles; t += stride, ++it) {
-        const int b = (int)(it % TS_NBUF);
+        const int b = (int)(it % NBUF);
         float2* buf = bufs + (size_t)b * tile_elems;
-        const bool tile_ok = mbar_wait_bounded(&tile_bar[b], (uint32_t)((it / TS_NBUF) & 1), a.err);
+        const bool tile_ok = mbar_wait_bounded(&tile_bar[b], (uint32_t)((it / NBUF) & 1), a.err);
         if (a.grouped) {
             // slices run through the tiles independently: a slice-uniform abort check
             uint32_t stop;
@@ -390,7 +404,7 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
         }
         float nin = 0.f;   // this thread's share of the tile norm before the pass
         for (int s = 0; s < nst; ++s, ++q) {
-            if (!a.grouped && tid == 0 && w_issued < total_q && w_issued < q + TS_NB) issue_w();
+            if (!a.wres && tid == 0 && w_issued < total_q && w_issued < q + NB) issue_w();
             const StageSm& S = sst[s];
             // this thread's row is group g = tid; slot v is read at register value v ^ tau,
             // tau = the group bits that land on tile bits >= 4 (bank-conflict-free reads)
@@ -453,10 +467,10 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
             asm volatile("bar.sync %0, %1;" ::"r"(1 + slice), "r"(128) : "memory");
             if (quarter == 0 && elect_one()) {   // one thread of the slice's first warp
                 tc_fence_after();
-                const int slot = a.grouped ? s : (int)(q % TS_NB);
-                const uint32_t wpar = a.grouped ? 0u : (uint32_t)((q / TS_NB) & 1);
-                // grouped: W stays resident, so only the first tile waits for it
-                if ((a.grouped && it > 0) || mbar_wait_bounded(&w_bar[slot], wpar, a.err)) {
+                const int slot = a.wres ? s : (int)(q % NB);
+                const uint32_t wpar = a.wres ? 0u : (uint32_t)((q / NB) & 1);
+                // resident W: only the first tile waits for it
+                if ((a.wres && it > 0) || mbar_wait_bounded(&w_bar[slot], wpar, a.err)) {
                     // W slot = [W_hi (32 rows) | W_lo (32 rows)]: one N=64 MMA gives
                     // a_hi*w_hi in D[0:32] and a_hi*w_lo in D[32:64]; a_lo*w_hi joins
                     // D[32:64]; the two halves are added in registers afterwards
@@ -535,11 +549,11 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
     }
     if (tid == 0) {
         if (s_abort) {   // drain the W loads still in flight before the shared memory goes away
-            if (a.grouped) {
+            if (a.wres) {
                 for (int st = 0; st < nst; ++st) mbar_wait_bounded(&w_bar[st], 0u, a.err);
             } else {
                 for (long long i = q; i < w_issued; ++i)
-                    mbar_wait_bounded(&w_bar[i % TS_NB], (uint32_t)((i / TS_NB) & 1), a.err);
+                    mbar_wait_bounded(&w_bar[i % NB], (uint32_t)((i / NB) & 1), a.err);
             }
         }
     }
@@ -552,8 +566,35 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
 }
 
 // ------------------------------------------------------------ host side --
-static size_t pass_tcs_smem_bytes() {
-    return 1024 + TS_NB * TS_W_BYTES + TS_NBUF * (sizeof(float2) << TS_TILE_BITS);
+static size_t pass_tcs_smem_bytes(int nbuf, int nb) {
+    return 1024 + (size_t)nb * TS_W_BYTES + (size_t)nbuf * (sizeof(float2) << TS_TILE_BITS);
+}
+
+template <int NBUF, int NB>
+static cudaError_t set_pass_tcs_smem() {
+    const int sm = (int)pass_tcs_smem_bytes(NBUF, NB);
+    cudaError_t e = cudaFuncSetAttribute(pass_tcs_kernel<true, false, NBUF, NB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pass_tcs_kernel<false, false, NBUF, NB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pass_tcs_kernel<false, true, NBUF, NB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return e;
+}
+
+template <int NBUF, int NB>
+static void launch_pass_tcs_cfg(bool rot, bool swizzled, unsigned grid, const DevPass& P, PassTcsArgs a,
+                                const TmaTile& tma, cudaStream_t s) {
+    const size_t sm = pass_tcs_smem_bytes(NBUF, NB);
+    a.tc.nbuf = NBUF;
+    if (rot)
+        pass_tcs_kernel<true, false, NBUF, NB><<<grid, TS_CTA_THREADS, sm, s>>>(P, a, tma);
+    else if (swizzled)
+        pass_tcs_kernel<false, true, NBUF, NB><<<grid, TS_CTA_THREADS, sm, s>>>(P, a, tma);
+    else
+        pass_tcs_kernel<false, false, NBUF, NB><<<grid, TS_CTA_THREADS, sm, s>>>(P, a, tma);
 }
 
 // Which passes run their stages on the tensor cores, and the per-stage data.
@@ -634,14 +675,8 @@ cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float*
     const DevPass& P = dp->plan.passes[pass];
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(pass_tcs_kernel<true, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_tcs_smem_bytes());
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(pass_tcs_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)pass_tcs_smem_bytes());
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(pass_tcs_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)pass_tcs_smem_bytes());
+        cudaError_t e = set_pass_tcs_smem<TS_NBUF, TS_NB>();
+        if (e == cudaSuccess) e = set_pass_tcs_smem<TS_NBUF_RES, TS_NB_RES>();
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -650,7 +685,12 @@ cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float*
     rot = rot && !swizzled;
     PassTcsArgs a{};
     const int grp = dp->tc_group[pass];
-    a.grouped = (grp >= 0 && (w_item_stride == 0 || items == 1)) ? 1 : 0;   // one W set per CTA
+    const bool w_shared = w_item_stride == 0 || items == 1;   // one W set for every tile
+    a.grouped = (grp >= 0 && w_shared) ? 1 : 0;
+    // lock-step passes of 4..11 stages keep every W resident with two tile buffers;
+    // passes of up to three stages keep them in the ring's slots
+    const bool res_cfg = w_shared && !a.grouped && P.stage_count > TS_NB && P.stage_count <= TS_NB_RES;
+    a.wres = (w_shared && (P.stage_count <= TS_NB || res_cfg)) ? 1 : 0;
     a.gb0 = a.grouped ? (grp & 255) : 0;
     a.gb1 = a.grouped ? (grp >> 8) : 0;
     a.tcs = dp->d_tcs + P.stage_begin;
@@ -662,21 +702,17 @@ cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float*
     a.err = err;
     a.state = state;
     a.item_off = item_off;
-    a.tc.nbuf = TS_NBUF;
     a.tc.nchunks = 1 << P.ngather;
     a.tc.chunk_bytes = (uint32_t)(sizeof(float2) << P.chunk);
     a.tc.tile_bytes = (uint32_t)(sizeof(float2) << P.m);
     a.tc.tiles_per_item = a.tiles_per_item;
     a.tc.tpi_log = a.tpi_log;
     a.tc.total_tiles = a.total_tiles;
-    const long long grid = std::min<long long>(a.total_tiles, num_sms());
-    const size_t sm = pass_tcs_smem_bytes();
-    if (rot)
-        pass_tcs_kernel<true, false><<<(unsigned)grid, TS_CTA_THREADS, sm, s>>>(P, a, tma);
-    else if (swizzled)
-        pass_tcs_kernel<false, true><<<(unsigned)grid, TS_CTA_THREADS, sm, s>>>(P, a, tma);
+    const unsigned grid = (unsigned)std::min<long long>(a.total_tiles, num_sms());
+    if (res_cfg)
+        launch_pass_tcs_cfg<TS_NBUF_RES, TS_NB_RES>(rot, swizzled, grid, P, a, tma, s);
     else
-        pass_tcs_kernel<false, false><<<(unsigned)grid, TS_CTA_THREADS, sm, s>>>(P, a, tma);
+        launch_pass_tcs_cfg<TS_NBUF, TS_NB>(rot, swizzled, grid, P, a, tma, s);
     count_launch();
     return cudaGetLastError();
 }
