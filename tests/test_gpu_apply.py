@@ -167,7 +167,8 @@ def test_expectation_forms(T, dtype):
     qubits 0..12): X on register qubits 10..12 (all 8 patterns; the half-pair forms
     for the non-zero ones), with and without X on qubit 0 (swapped pairs), an even
     or odd number of Y factors, the partner on a lane bit (qubit 3), a warp bit
-    (qubit 7; the alternating warp-half form), both, or the thread itself; random Z
+    (qubit 7; the alternating warp-half form), both, or the thread itself, the top
+    X bit on qubit 4 or 5 (lane bits 3, 4), alone or with lower X bits; random Z
     factors on the tile and on qubits 13..15 (the tile's global sign)."""
     n = 16
     psi0 = gen.random_state(n, seed=31)
@@ -177,7 +178,7 @@ def test_expectation_forms(T, dtype):
     specs = []
     for xr in range(8):
         for sw in (0, 1):
-            for part in ((), (3,), (7,), (3, 7)):
+            for part in ((), (3,), (7,), (3, 7), (4,), (5,), (1, 5), (2, 3, 4)):
                 for im in (0, 1):
                     xq = [10 + k for k in range(3) if (xr >> k) & 1] + ([0] if sw else []) + list(part)
                     if not xq:
