@@ -276,6 +276,71 @@ __device__ __forceinline__ void dense_apply(C (&a)[1 << R], const C* __restrict_
     }
 }
 
+// The same matrix on two groups at once (the adjoint sweep's psi and lambda):
+// one dispatch and one decode of the matrix for both.
+template <typename C, int R, int MASK, bool DAG>
+__device__ __forceinline__ void dense_apply2(C (&a)[1 << R], C (&b)[1 << R], const C* __restrict__ M, int tau) {
+    constexpr int K = cpopc(MASK);
+    if constexpr (K <= 2) {
+        constexpr int D = 1 << K;
+        constexpr int OMASK = ((1 << R) - 1) & ~MASK;
+        constexpr int NOUT = (1 << R) >> K;
+        const int t = pext4(tau, MASK);
+        C m[D][D];
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                if constexpr (DAG) m[r][c] = cconj(M[((c ^ t) << K) | (r ^ t)]);
+                else m[r][c] = M[((r ^ t) << K) | (c ^ t)];
+            }
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) {
+            const int base = cscatter(o, OMASK);
+            C va[D], vb[D];
+#pragma unroll
+            for (int s = 0; s < D; ++s) {
+                va[s] = a[base | cscatter(s, MASK)];
+                vb[s] = b[base | cscatter(s, MASK)];
+            }
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                C acc_a = cmk<C>(0, 0), acc_b = cmk<C>(0, 0);
+#pragma unroll
+                for (int s = 0; s < D; ++s) {
+                    cfma(acc_a, m[r][s], va[s]);
+                    cfma(acc_b, m[r][s], vb[s]);
+                }
+                a[base | cscatter(r, MASK)] = acc_a;
+                b[base | cscatter(r, MASK)] = acc_b;
+            }
+        }
+    } else {
+        dense_apply<C, R, MASK, DAG>(a, M, tau);
+        dense_apply<C, R, MASK, DAG>(b, M, tau);
+    }
+}
+
+template <typename C, int R, bool DAG, int MASK>
+__device__ __forceinline__ void dense_case2(C (&a)[1 << R], C (&b)[1 << R], const C* M, int tau) {
+    if constexpr (MASK < (1 << R)) dense_apply2<C, R, MASK, DAG>(a, b, M, tau);
+}
+
+template <typename C, int R, bool DAG>
+__device__ __forceinline__ void dense_dispatch2(int mask, C (&a)[1 << R], C (&b)[1 << R], const C* M, int tau) {
+    switch (mask) {
+#define TCNG_CASE(m) case m: dense_case2<C, R, DAG, m>(a, b, M, tau); break;
+        TCNG_CASE(1) TCNG_CASE(2) TCNG_CASE(3) TCNG_CASE(4) TCNG_CASE(5) TCNG_CASE(6)
+        TCNG_CASE(7) TCNG_CASE(8) TCNG_CASE(9) TCNG_CASE(10) TCNG_CASE(11) TCNG_CASE(12)
+        TCNG_CASE(13) TCNG_CASE(14) TCNG_CASE(15) TCNG_CASE(16) TCNG_CASE(17) TCNG_CASE(18)
+        TCNG_CASE(19) TCNG_CASE(20) TCNG_CASE(21) TCNG_CASE(22) TCNG_CASE(23) TCNG_CASE(24)
+        TCNG_CASE(25) TCNG_CASE(26) TCNG_CASE(27) TCNG_CASE(28) TCNG_CASE(29) TCNG_CASE(30)
+        TCNG_CASE(31)
+#undef TCNG_CASE
+        default: break;
+    }
+}
+
 template <typename C, int R, bool DAG, int MASK>
 __device__ __forceinline__ void dense_case(C (&a)[1 << R], const C* M, int tau) {
     if constexpr (MASK < (1 << R)) dense_apply<C, R, MASK, DAG>(a, M, tau);
@@ -335,6 +400,19 @@ __device__ __forceinline__ void diag_apply(C (&a)[1 << R], const DevOp& op, cons
         C d = M[idx[s]];
         if constexpr (DAG) d = cconj(d);
         a[s] = cmul(d, a[s]);
+    }
+}
+
+// Diagonal op on two groups with the same slot indices (psi and lambda).
+template <typename C, int R, bool DAG>
+__device__ __forceinline__ void diag_apply2(C (&a)[1 << R], C (&b)[1 << R], const C* __restrict__ M,
+                                            const int (&idx)[1 << R]) {
+#pragma unroll
+    for (int s = 0; s < (1 << R); ++s) {
+        C d = M[idx[s]];
+        if constexpr (DAG) d = cconj(d);
+        a[s] = cmul(d, a[s]);
+        b[s] = cmul(d, b[s]);
     }
 }
 

@@ -66,36 +66,41 @@ __device__ __forceinline__ typename Real<C>::T grad_xy(bool is_y, const C (&p)[1
     return acc;
 }
 
-// Gradient contribution Im<lambda|G|psi> of one group, for a lone parameterised op.
+// Gradient contribution Im<lambda|G|psi> of one group, for a lone parameterised
+// dense op (generator X or Y on one register bit).
 template <typename C, int R>
-__device__ __forceinline__ typename Real<C>::T grad_part(const DevOp& op, const C (&p)[1 << R],
-                                                        const C (&l)[1 << R], int tau,
-                                                        const int (&L)[1 << R], long long gbase) {
+__device__ __forceinline__ typename Real<C>::T grad_part_xy(const DevOp& op, const C (&p)[1 << R],
+                                                           const C (&l)[1 << R], int tau) {
     using T = typename Real<C>::T;
     T acc = 0;
-    if (op.grad == G_X || op.grad == G_Y) {
-        const int bit = __ffs(op.mask) - 1;          // register bit of the gate
-        const int flip = (tau >> bit) & 1;            // slot with bit 0 holds logical `flip`
-        const bool is_y = op.grad == G_Y;
-        switch (bit) {
-        case 0: acc = grad_xy<C, R, 0>(is_y, p, l, flip); break;
-        case 1: acc = grad_xy<C, R, 1>(is_y, p, l, flip); break;
-        case 2: acc = grad_xy<C, R, 2>(is_y, p, l, flip); break;
-        case 3: acc = grad_xy<C, R, 3>(is_y, p, l, flip); break;
-        default: acc = grad_xy<C, R, 4>(is_y, p, l, flip); break;
-        }
-    } else {
-        int idx[1 << R];
-        diag_index<R>(op, L, gbase, idx);
+    const int bit = __ffs(op.mask) - 1;          // register bit of the gate
+    const int flip = (tau >> bit) & 1;            // slot with bit 0 holds logical `flip`
+    const bool is_y = op.grad == G_Y;
+    switch (bit) {
+    case 0: acc = grad_xy<C, R, 0>(is_y, p, l, flip); break;
+    case 1: acc = grad_xy<C, R, 1>(is_y, p, l, flip); break;
+    case 2: acc = grad_xy<C, R, 2>(is_y, p, l, flip); break;
+    case 3: acc = grad_xy<C, R, 3>(is_y, p, l, flip); break;
+    default: acc = grad_xy<C, R, 4>(is_y, p, l, flip); break;
+    }
+    return acc;
+}
+
+// The same for a diagonal op (generator Z, ZZ or the |11><11| projector), from
+// the op's phase-table index of every slot.
+template <typename C, int R>
+__device__ __forceinline__ typename Real<C>::T grad_part_diag(const DevOp& op, const C (&p)[1 << R],
+                                                             const C (&l)[1 << R], const int (&idx)[1 << R]) {
+    using T = typename Real<C>::T;
+    T acc = 0;
 #pragma unroll
-        for (int s = 0; s < (1 << R); ++s) {
-            const int b = idx[s];   // bit j = value of source j (ascending qubits)
-            T w;
-            if (op.grad == G_Z) w = (b & 1) ? T(-1) : T(1);
-            else if (op.grad == G_ZZ) w = (__popc(b & 3) & 1) ? T(-1) : T(1);
-            else w = (b == 3) ? T(1) : T(0);
-            acc += w * im_conj_mul(l[s].x, l[s].y, p[s].x, p[s].y);
-        }
+    for (int s = 0; s < (1 << R); ++s) {
+        const int b = idx[s];   // bit j = value of source j (ascending qubits)
+        T w;
+        if (op.grad == G_Z) w = (b & 1) ? T(-1) : T(1);
+        else if (op.grad == G_ZZ) w = (__popc(b & 3) & 1) ? T(-1) : T(1);
+        else w = (b == 3) ? T(1) : T(0);
+        acc += w * im_conj_mul(l[s].x, l[s].y, p[s].x, p[s].y);
     }
     return acc;
 }
@@ -130,24 +135,30 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
                 l[s] = cmk<C>(0, 0);
             }
         }
+        // per op: one dispatch and one decode (matrix, or diagonal slot indices)
+        // serve the gradient term and the uncompute of both states
         int j = 0;
         for (int i = (int)st.op_count - 1; i >= 0; --i) {
             const DevOp op = ops[st.op_begin + i];
             const C* M = mats + op.mat;
-            if (op.grad != G_NONE) {
-                T v = active ? grad_part<C, R>(op, p, l, tau, L, gbase) : T(0);
-                const T w = warp_sum(v);
-                if (lane == 0) red[warp * kMaxStageGrads + j] += w;
-                ++j;
-            }
-            if (active) {
-                if (op.kind == K_DENSE) {
-                    dense_dispatch<C, R, true>(op.mask, p, M, tau);
-                    dense_dispatch<C, R, true>(op.mask, l, M, tau);
-                } else {
-                    diag_apply<C, R, true>(p, op, M, L, gbase);
-                    diag_apply<C, R, true>(l, op, M, L, gbase);
+            if (op.kind == K_DENSE) {
+                if (op.grad != G_NONE) {
+                    T v = active ? grad_part_xy<C, R>(op, p, l, tau) : T(0);
+                    const T w = warp_sum(v);
+                    if (lane == 0) red[warp * kMaxStageGrads + j] += w;
+                    ++j;
                 }
+                if (active) dense_dispatch2<C, R, true>(op.mask, p, l, M, tau);
+            } else {
+                int idx[1 << R];
+                diag_index<R>(op, L, gbase, idx);
+                if (op.grad != G_NONE) {
+                    T v = active ? grad_part_diag<C, R>(op, p, l, idx) : T(0);
+                    const T w = warp_sum(v);
+                    if (lane == 0) red[warp * kMaxStageGrads + j] += w;
+                    ++j;
+                }
+                if (active) diag_apply2<C, R, true>(p, l, M, idx);
             }
         }
         if (active) {
