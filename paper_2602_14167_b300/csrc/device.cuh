@@ -373,7 +373,10 @@ template <int R>
 __device__ __forceinline__ void diag_index(const DevOp& op, const int (&L)[1 << R], long long gbase,
                                            int (&idx)[1 << R]) {
     int i0 = 0;
-    for (int j = 0; j < op.k; ++j) i0 |= src_bit(op.src[j], L[0], gbase) << j;
+    // unrolled to the 5 source slots (compile-time indices keep op in registers)
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+        if (j < op.k) i0 |= src_bit(op.src[j], L[0], gbase) << j;
     const int nib = op.mask | (op.pad << 8);
     int e[R];
 #pragma unroll
@@ -515,7 +518,9 @@ __device__ void run_stage_smem(C* __restrict__ buf, const DevStage& st, const De
         } else {
             for (int L = threadIdx.x; L < N; L += blockDim.x) {
                 int idx = 0;
-                for (int j = 0; j < op.k; ++j) idx |= src_bit(op.src[j], L, gbase) << j;
+#pragma unroll
+                for (int j = 0; j < 5; ++j)
+                    if (j < op.k) idx |= src_bit(op.src[j], L, gbase) << j;
                 C d = M[idx];
                 if (DAG) d = cconj(d);
                 buf[L] = cmul(d, buf[L]);
