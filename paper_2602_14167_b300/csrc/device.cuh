@@ -369,14 +369,14 @@ __device__ __forceinline__ int src_bit(uint8_t src, int L, long long gbase) {
 // Phase-table index of every slot for a diagonal op: the index of slot 0 from its
 // tile offset, then one XOR per slot -- flipping register bit i flips index bit
 // e_i (the source fed by that register bit, from the planner's nibbles).
+// L0: tile offset of slot 0.
 template <int R>
-__device__ __forceinline__ void diag_index(const DevOp& op, const int (&L)[1 << R], long long gbase,
-                                           int (&idx)[1 << R]) {
+__device__ __forceinline__ void diag_index0(const DevOp& op, int L0, long long gbase, int (&idx)[1 << R]) {
     int i0 = 0;
     // unrolled to the 5 source slots (compile-time indices keep op in registers)
 #pragma unroll
     for (int j = 0; j < 5; ++j)
-        if (j < op.k) i0 |= src_bit(op.src[j], L[0], gbase) << j;
+        if (j < op.k) i0 |= src_bit(op.src[j], L0, gbase) << j;
     const int nib = op.mask | (op.pad << 8);
     int e[R];
 #pragma unroll
@@ -390,6 +390,12 @@ __device__ __forceinline__ void diag_index(const DevOp& op, const int (&L)[1 << 
         const int low = cctz(s);                   // compile-time after unrolling
         idx[s] = idx[s & (s - 1)] ^ e[low];
     }
+}
+
+template <int R>
+__device__ __forceinline__ void diag_index(const DevOp& op, const int (&L)[1 << R], long long gbase,
+                                           int (&idx)[1 << R]) {
+    diag_index0<R>(op, L[0], gbase, idx);
 }
 
 // Diagonal op: multiply slot s by M[idx(s)].

@@ -117,20 +117,21 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
     for (int g0 = 0; g0 < ngroups; g0 += blockDim.x) {
         const int g = g0 + threadIdx.x;
         const bool active = g < ngroups;
-        int L[1 << R];
         C p[1 << R], l[1 << R];
         const int tau = st.rotate ? (g & ((1 << R) - 1)) : 0;
+        int L0 = 0;   // slot 0's offset (the diagonal ops' index); the others are recomputed for the store
         if (active) {
+            int L[1 << R];
             group_offsets<R>(g, tau, st.rbit, L);
 #pragma unroll
             for (int s = 0; s < (1 << R); ++s) {
                 p[s] = pbuf[L[s]];
                 l[s] = lbuf[L[s]];
             }
+            L0 = L[0];
         } else {
 #pragma unroll
             for (int s = 0; s < (1 << R); ++s) {
-                L[s] = 0;
                 p[s] = cmk<C>(0, 0);
                 l[s] = cmk<C>(0, 0);
             }
@@ -151,7 +152,7 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
                 if (active) dense_dispatch2<C, R, true>(op.mask, p, l, M, tau);
             } else {
                 int idx[1 << R];
-                diag_index<R>(op, L, gbase, idx);
+                diag_index0<R>(op, L0, gbase, idx);
                 if (op.grad != G_NONE) {
                     T v = active ? grad_part_diag<C, R>(op, p, l, idx) : T(0);
                     const T w = warp_sum(v);
@@ -162,6 +163,8 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
             }
         }
         if (active) {
+            int L[1 << R];
+            group_offsets<R>(g, tau, st.rbit, L);
 #pragma unroll
             for (int s = 0; s < (1 << R); ++s) {
                 pbuf[L[s]] = p[s];
