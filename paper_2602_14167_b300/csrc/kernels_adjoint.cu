@@ -66,28 +66,35 @@ __device__ __forceinline__ typename Real<C>::T grad_xy(bool is_y, const C (&p)[1
     return acc;
 }
 
-// Gradient contribution Im<lambda|G|psi> of one group, for a lone parameterised
-// dense op (generator X or Y on one register bit).
+// Gradient term of a parameterised dense op, then its uncompute on both groups,
+// under one dispatch on the op's register bit.
 template <typename C, int R>
-__device__ __forceinline__ typename Real<C>::T grad_part_xy(const DevOp& op, const C (&p)[1 << R],
-                                                           const C (&l)[1 << R], int tau) {
+__device__ __forceinline__ typename Real<C>::T grad_apply_xy(const DevOp& op, C (&p)[1 << R], C (&l)[1 << R],
+                                                            const C* __restrict__ M, int tau) {
     using T = typename Real<C>::T;
     T acc = 0;
-    const int bit = __ffs(op.mask) - 1;          // register bit of the gate
-    const int flip = (tau >> bit) & 1;            // slot with bit 0 holds logical `flip`
+    const int bit = __ffs(op.mask) - 1;
+    const int flip = (tau >> bit) & 1;
     const bool is_y = op.grad == G_Y;
     switch (bit) {
-    case 0: acc = grad_xy<C, R, 0>(is_y, p, l, flip); break;
-    case 1: acc = grad_xy<C, R, 1>(is_y, p, l, flip); break;
-    case 2: acc = grad_xy<C, R, 2>(is_y, p, l, flip); break;
-    case 3: acc = grad_xy<C, R, 3>(is_y, p, l, flip); break;
-    default: acc = grad_xy<C, R, 4>(is_y, p, l, flip); break;
+#define TCNG_GA(B)                                              \
+    case B:                                                     \
+        acc = grad_xy<C, R, B>(is_y, p, l, flip);               \
+        dense_case2<C, R, true, 1 << B>(p, l, M, tau);          \
+        break;
+        TCNG_GA(0) TCNG_GA(1) TCNG_GA(2) TCNG_GA(3)
+#undef TCNG_GA
+    default:
+        acc = grad_xy<C, R, 4>(is_y, p, l, flip);
+        dense_case2<C, R, true, 16>(p, l, M, tau);
+        break;
     }
     return acc;
 }
 
-// The same for a diagonal op (generator Z, ZZ or the |11><11| projector), from
-// the op's phase-table index of every slot.
+// Gradient contribution Im<lambda|G|psi> of one group for a parameterised
+// diagonal op (generator Z, ZZ or the |11><11| projector), from the op's
+// phase-table index of every slot.
 template <typename C, int R>
 __device__ __forceinline__ typename Real<C>::T grad_part_diag(const DevOp& op, const C (&p)[1 << R],
                                                              const C (&l)[1 << R], const int (&idx)[1 << R]) {
@@ -144,12 +151,13 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
             const C* M = mats + op.mat;
             if (op.kind == K_DENSE) {
                 if (op.grad != G_NONE) {
-                    T v = active ? grad_part_xy<C, R>(op, p, l, tau) : T(0);
+                    T v = active ? grad_apply_xy<C, R>(op, p, l, M, tau) : T(0);
                     const T w = warp_sum(v);
                     if (lane == 0) red[warp * kMaxStageGrads + j] += w;
                     ++j;
+                } else if (active) {
+                    dense_dispatch2<C, R, true>(op.mask, p, l, M, tau);
                 }
-                if (active) dense_dispatch2<C, R, true>(op.mask, p, l, M, tau);
             } else {
                 int idx[1 << R];
                 diag_index0<R>(op, L0, gbase, idx);
