@@ -66,8 +66,36 @@ __device__ __forceinline__ typename Real<C>::T grad_xy(bool is_y, const C (&p)[1
     return acc;
 }
 
-// Gradient term of a parameterised dense op, then its uncompute on both groups,
-// under one dispatch on the op's register bit.
+// U^dag of a lone RX (IS_Y false) or RY (IS_Y true) on register bit BIT, on both
+// groups: U = cos(t/2) I - i sin(t/2) G, so U^dag needs c = cos(t/2) and s =
+// sin(t/2) only (half the products of a general 2x2 complex matrix).  For RY the
+// caller passes -s when the slot order on BIT is flipped (RX is symmetric).
+template <typename C, int R, int BIT, bool IS_Y>
+__device__ __forceinline__ void rot_dag2(C (&p)[1 << R], C (&l)[1 << R], typename Real<C>::T c,
+                                         typename Real<C>::T s) {
+    if constexpr (BIT < R) {
+#pragma unroll
+        for (int k = 0; k < (1 << R); ++k) {
+            if ((k >> BIT) & 1) continue;
+            const int k1 = k | (1 << BIT);
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                C* a = w ? l : p;
+                const C a0 = a[k], a1 = a[k1];
+                if constexpr (!IS_Y) {   // [[c, i s], [i s, c]]
+                    a[k] = cmk<C>(c * a0.x - s * a1.y, c * a0.y + s * a1.x);
+                    a[k1] = cmk<C>(c * a1.x - s * a0.y, c * a1.y + s * a0.x);
+                } else {                 // [[c, s], [-s, c]]
+                    a[k] = cmk<C>(c * a0.x + s * a1.x, c * a0.y + s * a1.y);
+                    a[k1] = cmk<C>(c * a1.x - s * a0.x, c * a1.y - s * a0.y);
+                }
+            }
+        }
+    }
+}
+
+// Gradient term of a parameterised dense op (a lone RX or RY), then its uncompute
+// on both groups, under one dispatch on the op's register bit.
 template <typename C, int R>
 __device__ __forceinline__ typename Real<C>::T grad_apply_xy(const DevOp& op, C (&p)[1 << R], C (&l)[1 << R],
                                                             const C* __restrict__ M, int tau) {
@@ -76,17 +104,22 @@ __device__ __forceinline__ typename Real<C>::T grad_apply_xy(const DevOp& op, C 
     const int bit = __ffs(op.mask) - 1;
     const int flip = (tau >> bit) & 1;
     const bool is_y = op.grad == G_Y;
+    // the op's matrix: RX [[c, -i s], [-i s, c]], RY [[c, -s], [s, c]] (row-major)
+    const T c = M[0].x;
+    const T s = is_y ? (flip ? -M[2].x : M[2].x) : -M[1].y;
     switch (bit) {
 #define TCNG_GA(B)                                              \
     case B:                                                     \
         acc = grad_xy<C, R, B>(is_y, p, l, flip);               \
-        dense_case2<C, R, true, 1 << B>(p, l, M, tau);          \
+        if (is_y) rot_dag2<C, R, B, true>(p, l, c, s);          \
+        else rot_dag2<C, R, B, false>(p, l, c, s);              \
         break;
         TCNG_GA(0) TCNG_GA(1) TCNG_GA(2) TCNG_GA(3)
 #undef TCNG_GA
     default:
         acc = grad_xy<C, R, 4>(is_y, p, l, flip);
-        dense_case2<C, R, true, 16>(p, l, M, tau);
+        if (is_y) rot_dag2<C, R, 4, true>(p, l, c, s);
+        else rot_dag2<C, R, 4, false>(p, l, c, s);
         break;
     }
     return acc;
