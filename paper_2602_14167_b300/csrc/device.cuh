@@ -425,6 +425,50 @@ __device__ __forceinline__ void diag_apply2(C (&a)[1 << R], C (&b)[1 << R], cons
     }
 }
 
+// A lone RX (IS_Y false) or RY (IS_Y true) on register bit BIT, from c = cos(t/2)
+// and s = sin(t/2): U = c I - i s G (adjoint plans mark such ops with their
+// generator), half the products of a general 2x2 complex matrix.  For RY a
+// flipped slot order on BIT negates s (RX is symmetric under the flip).
+template <typename C, int R, int BIT, bool IS_Y>
+__device__ __forceinline__ void rot_apply(C (&a)[1 << R], typename Real<C>::T c, typename Real<C>::T s) {
+    if constexpr (BIT < R) {
+#pragma unroll
+        for (int k = 0; k < (1 << R); ++k) {
+            if ((k >> BIT) & 1) continue;
+            const int k1 = k | (1 << BIT);
+            const C a0 = a[k], a1 = a[k1];
+            if constexpr (!IS_Y) {   // [[c, -i s], [-i s, c]]
+                a[k] = cmk<C>(c * a0.x + s * a1.y, c * a0.y - s * a1.x);
+                a[k1] = cmk<C>(c * a1.x + s * a0.y, c * a1.y - s * a0.x);
+            } else {                 // [[c, -s], [s, c]]
+                a[k] = cmk<C>(c * a0.x - s * a1.x, c * a0.y - s * a1.y);
+                a[k1] = cmk<C>(c * a1.x + s * a0.x, c * a1.y + s * a0.y);
+            }
+        }
+    }
+}
+
+// The same dispatched on the op's register bit; c and s from its matrix
+// (RX [[c, -i s], [-i s, c]], RY [[c, -s], [s, c]], row-major).
+template <typename C, int R>
+__device__ __forceinline__ void rot_dispatch(const DevOp& op, C (&a)[1 << R], const C* __restrict__ M, int tau) {
+    using T = typename Real<C>::T;
+    const int bit = __ffs(op.mask) - 1;
+    const bool is_y = op.grad == G_Y;
+    const T c = M[0].x;
+    const T s = is_y ? (((tau >> bit) & 1) ? -M[2].x : M[2].x) : -M[1].y;
+    switch (bit) {
+#define TCNG_RA(B)                                        \
+    case B:                                               \
+        if (is_y) rot_apply<C, R, B, true>(a, c, s);      \
+        else rot_apply<C, R, B, false>(a, c, s);          \
+        break;
+        TCNG_RA(0) TCNG_RA(1) TCNG_RA(2) TCNG_RA(3) TCNG_RA(4)
+#undef TCNG_RA
+    default: break;
+    }
+}
+
 // Insert a zero bit at each of the R register positions (ascending) into g.
 template <int R>
 __device__ __forceinline__ int insert_zero_bits(int g, const uint8_t* rbit) {
@@ -473,8 +517,12 @@ __device__ __forceinline__ void run_stage_group(C* __restrict__ buf, const DevSt
     for (uint32_t i = 0; i < st.op_count; ++i) {
         const DevOp op = ops[st.op_begin + i];
         const C* M = mats + op.mat;
-        if (op.kind == K_DENSE) dense_dispatch<C, R, false>(op.mask, a, M, tau);
-        else diag_apply<C, R, false>(a, op, M, L, gbase);
+        if (op.kind == K_DENSE) {
+            if (op.grad == G_X || op.grad == G_Y) rot_dispatch<C, R>(op, a, M, tau);   // lone RX / RY
+            else dense_dispatch<C, R, false>(op.mask, a, M, tau);
+        } else {
+            diag_apply<C, R, false>(a, op, M, L, gbase);
+        }
     }
 #pragma unroll
     for (int s = 0; s < (1 << R); ++s) buf[L[s]] = a[s];
