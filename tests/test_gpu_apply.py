@@ -398,6 +398,38 @@ def test_tensor_core_stages_shared_params_batch(T):
         check_state(st.amplitudes(b).cpu().numpy(), ref, "c64")
 
 
+def test_tensor_core_stages_parameter_free_batch(T):
+    """A circuit without parameters (angles fixed in the gates) on three different
+    states: one W set serves every tile of every item, and the lock-step pass over
+    the 13 lowest qubits (10 register stages) keeps it resident; each item against
+    the oracle."""
+    n, B = 15, 3
+    c, th = gen.su4_brickwork(n, 6, "RZ", seed=11)
+    g, p = c.to_ir()
+    g = g.copy()
+    sel = g["param"] >= 0
+    g["angle0"][sel] = g["angle0"][sel] + g["scale"][sel] * np.asarray(th, dtype=np.float64)[g["param"][sel]]
+    g["scale"][sel] = 0.0
+    g["param"][sel] = -1
+    from paper_2602_14167_b300 import StateBatch
+    psi0 = [gen.random_state(n, seed=60 + i) for i in range(B)]
+    T.tcng_set_option(T.OPT_TENSOR_CORES, 1)
+    T.tcng_profile_enable(True)
+    T.tcng_profile_read(reset=True)
+    try:
+        st = StateBatch(n, batch=B, dtype="c64")
+        for i in range(B):
+            st.amplitudes(i).copy_(torch.tensor(psi0[i], dtype=st.cdtype, device="cuda"))
+        st.apply(g, p)
+        torch.cuda.synchronize()
+        launches = T.tcng_profile_read(reset=True).get("pass_tcs_kernel_c64", (0, 0.0))[0]
+    finally:
+        T.tcng_profile_enable(False)
+    assert launches > 0
+    for i in range(B):
+        check_state(st.amplitudes(i).cpu().numpy(), sv.apply(n, g, p, None, psi=psi0[i]), "c64")
+
+
 def test_tensor_core_option_values(T):
     for v in (0, 1, 2):
         T.tcng_set_option(T.OPT_TENSOR_CORES, v)
