@@ -360,17 +360,8 @@ def vqe_bench(args, dev, dist, world):
     # ragged batch, one persistent launch
     if args.vqe_only:
         return res
-    ns = gen.ragged_sizes(B, seed=0)
-    probs, sidx = [], {}
-    for nn in sorted(set(int(x) for x in ns)):
-        c = gen.hea_ring(nn, 12)
-        gg, pp = c.to_ir()
-        sidx[nn] = len(probs)
-        probs.append(dict(n=nn, gates=gg, pool=pp, P=c.n_params, terms=gen.tfim_terms(nn, 1.0, 1.0)))
-    item_problem = [sidx[int(x)] for x in ns]
-    rng = np.random.default_rng(1)
-    th = np.concatenate([rng.uniform(-np.pi, np.pi, probs[s]["P"]) for s in item_problem])
-    cf = np.concatenate([-rng.uniform(0.5, 1.5, 2 * probs[s]["n"] - 1) for s in item_problem])
+    probs, item_problem, th, cf, ns = gen.ragged_vqe_batch(B, layers=12)
+    sidx = {p["n"]: i for i, p in enumerate(probs)}
     prm = torch.tensor(th, device=dev)
     cfd = torch.tensor(cf, device=dev)
     en = torch.empty(B, dtype=torch.float64, device=dev)

@@ -27,6 +27,8 @@
  * calls that overlap on different streams and share a structure race on it.
  * No call synchronises the device except the first call of a new structure
  * (uploading its plan), scratch growth, tcng_autotune and tcng_sync_status.
+ * With TCNG_OPT_USE_GRAPHS on, the second call of a structure (same device
+ * pointers) also instantiates a CUDA graph (host work only).
  */
 #ifndef TCNG_PUBLIC_API_H_
 #define TCNG_PUBLIC_API_H_
@@ -130,6 +132,25 @@ tcng_status tcng_apply_circuit(tcng_state* st, const tcng_gate* ops, size_t n_op
                                const void* params_dev, int P, void* stream);
 
 /*
+ * tcng_apply_circuit_pooled -- tcng_apply_circuit where every item has its own
+ * explicit gate matrices: the trajectories of the paper's MIPT study draw an
+ * independent Haar SU(4) for every gate of every trajectory (Sec. VII.C).
+ *   mat_pool, n_mat   host complex128 pool with the same layout as every item's
+ *                     (the planner reads it to classify each matrix as diagonal
+ *                     or dense and as unitary or not; every item's matrices must
+ *                     share those properties with it);
+ *   item_pool_dev     device complex128 (re, im) [batch][pool_stride], 16-byte
+ *                     aligned: gate g of item b uses the matrix at
+ *                     item_pool_dev[b][g.mat_off ...];
+ *   pool_stride       complex entries per item (>= n_mat).
+ * All items must have the same n.  Errors: as tcng_apply_circuit, plus
+ * EUNSUPPORTED (ragged state).
+ */
+tcng_status tcng_apply_circuit_pooled(tcng_state* st, const tcng_gate* ops, size_t n_ops,
+                                      const double* mat_pool, size_t n_mat, const void* item_pool_dev,
+                                      size_t pool_stride, const void* params_dev, int P, void* stream);
+
+/*
  * tcng_expect_pauli -- out_dev[b][t] = <psi_b|P_t|psi_b> (real; the paper's
  * expectation_ps, Sec. I.B; coefficients are NOT applied).
  *   terms     host array [n_terms <= 4096] of Pauli strings (masks < 2^n);
@@ -146,10 +167,9 @@ tcng_status tcng_expect_pauli(const tcng_state* st, const tcng_pauli* terms, siz
  * tcng_expect_pauli_noalloc -- out_dev[t] = <psi|P_t|psi> for one state vector,
  * like tcng_expect_pauli, but without allocating any device memory.  The paper
  * has no counterpart; this is for callers that cannot let a library allocate:
- * an application whose own allocator already holds the GPU's free memory, a
+ * an application whose own allocator already holds the GPU's free memory, or a
  * serving loop where cudaMalloc/cudaFree (and the synchronisation cudaFree
- * implies) are banned from the hot path, or work recorded into a stream
- * capture, where cudaMalloc is illegal.
+ * implies) are banned from the hot path.
  *   psi_dev   device state, 2^n amplitudes of type dt, 256-byte aligned;
  *   terms     host array of n_terms Pauli strings (masks < 2^n);
  *   out_dev   device double [n_terms].
@@ -162,8 +182,10 @@ tcng_status tcng_expect_pauli(const tcng_state* st, const tcng_pauli* terms, siz
  * before any stream capture.  All calls share the array: calls that overlap
  * on the GPU (different streams, or different host threads) race on it and
  * must be serialised by the caller.  Each call writes every slot it reads, so
- * no state carries over between calls.  No device-side error word is kept for
- * this call (a timed-out wait just ends the kernel).
+ * no state carries over between calls.  The call takes the library's host lock
+ * like every other entry point.  No device-side error word is kept for this
+ * call: a bounded device-side wait that times out ends the pass early and the
+ * affected values of out_dev are NaN.
  */
 tcng_status tcng_expect_pauli_noalloc(const void* psi_dev, int n, tcng_dtype dt,
                                       const tcng_pauli* terms, size_t n_terms, double* out_dev,
@@ -249,6 +271,47 @@ tcng_status tcng_energy_grad_ragged(const tcng_problem* problems, int n_problems
                                     double* energy_dev, double* grad_dev, void* stream);
 
 /*
+ * tcng_marginal_probs -- out_dev[b][k] = sum of |psi_b(x)|^2 over the x whose
+ * bits at qubits[0..nk-1] spell k, with k = sum_j bit(x, qubits[j]) << (nk-1-j)
+ * (qubits[0] is the most significant bit of k): the diagonal of the reduced
+ * density matrix of those qubits, which the paper's QML pipeline reads out as
+ * class probabilities (Sec. VII.B, reduced_density_matrix over the first 7
+ * qubits), i.e. the Born probabilities of measuring them.
+ *   qubits    host int [nk], distinct, each < n; nk in 1..10;
+ *   out_dev   device double [batch][2^nk].
+ * All items must have the same n.  Sums accumulate per thread in the state's
+ * precision (folded into FP64 every 256 amplitudes) and then in FP64 in a
+ * fixed order (bitwise reproducible).  Errors: EINVAL, EUNSUPPORTED (ragged),
+ * ENOMEM, ECUDA.
+ */
+tcng_status tcng_marginal_probs(const tcng_state* st, const int* qubits, int nk, double* out_dev,
+                                void* stream);
+
+/*
+ * tcng_measure -- projective computational-basis (Z) measurement of the qubits
+ * in mask_dev[b] of every item b (the per-qubit measurements of the paper's MIPT
+ * trajectories, Sec. VII.C, and the bitstrings of its shadow snapshots,
+ * Sec. VII.A).  Qubits are measured in increasing order; the outcome of qubit q
+ * is 0 iff u_dev[b][q] < P(0 | the item's earlier outcomes of this call) (Born
+ * rule); the state is projected onto the outcomes and rescaled to unit norm.
+ *   mask_dev     device uint64 [batch]: bit q set = measure qubit q (0: the
+ *                item is left unchanged);
+ *   u_dev        device double [batch][n], uniforms in [0, 1) (only the
+ *                entries of measured qubits are read);
+ *   outcome_dev  device int8 [batch][n]: 0 or 1 written for each measured
+ *                qubit, other entries untouched;
+ *   logp_dev     device double [batch]: the natural log of the probability of
+ *                this call's outcomes is ADDED (a trajectory's log-probability
+ *                accumulates over calls); NULL to skip.
+ * Outcomes are sampled in rounds of up to 10 qubits from the joint Born
+ * probabilities of the round's qubits (summed in FP64, fixed order).  All
+ * items must have the same n.  Errors: EINVAL, EUNSUPPORTED (ragged), ENOMEM,
+ * ECUDA.
+ */
+tcng_status tcng_measure(tcng_state* st, const uint64_t* mask_dev, const double* u_dev, int8_t* outcome_dev,
+                         double* logp_dev, void* stream);
+
+/*
  * tcng_apply_shared_unitary -- apply one k-qubit unitary U (host complex128,
  * row-major, local index as in the gate list with qubits q[0..k-1]) to every
  * item of a complex64 batch: a complex GEMM [2^k x 2^k] x [2^k x batch*2^(n-k)]
@@ -311,7 +374,17 @@ typedef enum {
     TCNG_OPT_TILE_BITS = 1,    /* log2 amplitudes per shared-memory tile, 5..13 (default 13) */
     TCNG_OPT_CHUNK_BITS = 2,   /* log2 contiguous amplitudes per copied chunk (default 7;
                                   expectation passes use at most 3) */
-    TCNG_OPT_USE_GRAPHS = 3,   /* 1: replay CUDA graphs per structure (default 1) */
+    TCNG_OPT_USE_GRAPHS = 3,   /* 1 (default): tcng_apply_circuit, tcng_energy_grad and
+                                  tcng_energy_grad_ragged replay one CUDA graph per key
+                                  (structure, options, device pointers): the first call
+                                  of a key runs eagerly, the second records its launches
+                                  on a private stream and launches the graph, later
+                                  calls only launch it.  Parameters, coefficients and
+                                  states are read from device memory when the graph
+                                  runs, so new values need no new recording.  Calls on
+                                  a stream the caller is capturing, and calls while
+                                  tcng_profile_enable is on, run eagerly.  0: always
+                                  eager. */
     TCNG_OPT_UNFUSED = 4,      /* 1: one pair/quartet kernel launch per gate (default 0) */
     TCNG_OPT_TENSOR_CORES = 5  /* complex64 register stages as 16x16 GEMMs on the tensor cores
                                   (TF32 hi/lo split, ~1e-6 relative error per circuit):

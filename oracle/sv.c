@@ -17,7 +17,10 @@
  *   - (H psi)[y] = sum_j c_j i^{#Y_j} (-1)^{popc((y ^ m_j) & z_j)} psi[y ^ m_j];
  *   - dE/dtheta by the two-term parameter-shift rule (the "2k circuit
  *     evaluations" the paper contrasts with reverse-mode AD in Sec. I.B), and
- *     by central finite differences.
+ *     by central finite differences;
+ *   - Born probabilities of a subset of qubits (the QML readout of Sec. VII.B)
+ *     and single-qubit projective measurements (the MIPT trajectories of
+ *     Sec. VII.C, the shadow snapshots of Sec. VII.A).
  * Gate conventions: R_P(t) = exp(-i t P / 2); 2-qubit local index
  * r = 2*bit(q[0]) + bit(q[1]); CX(control, target); CP(phi) = diag(1,1,1,e^{i phi}).
  */
@@ -354,6 +357,58 @@ int orc_grad_fd(int n, const og_gate* ops, int64_t n_ops, const double* pool, in
         free(work);
     }
     return bad ? EBAD : OK;
+}
+
+/* Born probabilities of measuring qubits q[0..k-1] in the computational basis:
+ * out[j] = sum of |psi[x]|^2 over the x whose bits at q[0..k-1] spell j, with
+ * q[0] the most significant bit of j (the diagonal of the reduced density
+ * matrix of those qubits). */
+int orc_marginal_probs(int n, const double* psi_ri, const int32_t* q, int k, double* out) {
+    const int64_t N = (int64_t)1 << n;
+    const cx* psi = (const cx*)psi_ri;
+    if (k < 1 || k > 20) return EBAD;
+    for (int i = 0; i < k; ++i) {
+        if (q[i] < 0 || q[i] >= n) return EBAD;
+        for (int j = 0; j < i; ++j)
+            if (q[j] == q[i]) return EBAD;
+    }
+    long double* acc = (long double*)calloc((size_t)1 << k, sizeof(long double));
+    if (!acc) return EBAD;
+    for (int64_t x = 0; x < N; ++x) {
+        int64_t j = 0;
+        for (int i = 0; i < k; ++i) j = (j << 1) | ((x >> q[i]) & 1);
+        acc[j] += (long double)(creal(psi[x]) * creal(psi[x]) + cimag(psi[x]) * cimag(psi[x]));
+    }
+    for (int64_t j = 0; j < ((int64_t)1 << k); ++j) out[j] = (double)acc[j];
+    free(acc);
+    return OK;
+}
+
+/* Projective measurement of qubit q in the computational basis (Born rule).
+ * p0 = sum_{bit q of x = 0} |psi[x]|^2 / sum_x |psi[x]|^2; the outcome is 0 if
+ * u < p0, else 1 (forced = 0 or 1 imposes an outcome instead).  The amplitudes
+ * of the other outcome are set to zero and the rest rescaled to unit norm.
+ * Returns the outcome; *prob = its probability, *p0_out = p0. */
+int orc_measure_qubit(int n, double* psi_ri, int q, double u, int forced, double* prob, double* p0_out) {
+    const int64_t N = (int64_t)1 << n;
+    cx* psi = (cx*)psi_ri;
+    if (q < 0 || q >= n) return -1;
+    long double s0 = 0, s1 = 0;
+    for (int64_t x = 0; x < N; ++x) {
+        const long double a = (long double)(creal(psi[x]) * creal(psi[x]) + cimag(psi[x]) * cimag(psi[x]));
+        if ((x >> q) & 1) s1 += a; else s0 += a;
+    }
+    const double p0 = (double)(s0 / (s0 + s1));
+    const int out = forced >= 0 ? forced : (u < p0 ? 0 : 1);
+    const double pk = out ? 1.0 - p0 : p0;
+    const double scale = 1.0 / sqrt((double)(out ? s1 : s0));
+    for (int64_t x = 0; x < N; ++x) {
+        if ((int)((x >> q) & 1) == out) psi[x] *= scale;
+        else psi[x] = 0;
+    }
+    *prob = pk;
+    *p0_out = p0;
+    return out;
 }
 
 int orc_num_threads(void) {

@@ -49,7 +49,9 @@ def lib():
                                                dp, i64, dp]
             L.orc_grad_fd.argtypes = [C.c_int, vp, i64, dp, i64, dp, C.c_int, u64p, u64p, dp, i64,
                                       C.c_double, dp]
-            for f in ("orc_apply", "orc_gate_matrix", "orc_expect", "orc_hamiltonian_apply",
+            L.orc_marginal_probs.argtypes = [C.c_int, dp, C.POINTER(C.c_int32), C.c_int, dp]
+            L.orc_measure_qubit.argtypes = [C.c_int, dp, C.c_int, C.c_double, C.c_int, dp, dp]
+            for f in ("orc_marginal_probs", "orc_measure_qubit", "orc_apply", "orc_gate_matrix", "orc_expect", "orc_hamiltonian_apply",
                       "orc_energy", "orc_grad_param_shift", "orc_grad_fd"):
                 getattr(L, f).restype = C.c_int
             L.orc_num_threads.restype = C.c_int
@@ -167,6 +169,31 @@ def grad_fd(n, gates, pool, params, terms, coeffs=None, h=1e-5) -> np.ndarray:
     if rc:
         raise ValueError("oracle rejected the input")
     return g[:P]
+
+
+def marginal_probs(n, psi, qubits) -> np.ndarray:
+    """Born probabilities of measuring ``qubits`` (qubits[0] most significant bit
+    of the outcome index)."""
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    q = np.ascontiguousarray(qubits, dtype=np.int32)
+    out = np.zeros(1 << q.size)
+    rc = lib().orc_marginal_probs(n, _d(psi.view(np.float64)), q.ctypes.data_as(C.POINTER(C.c_int32)),
+                                  int(q.size), _d(out))
+    if rc:
+        raise ValueError("bad qubit list")
+    return out
+
+
+def measure_qubit(n, psi, q, u, forced=-1):
+    """Measure qubit q of psi in place (Born rule with uniform u, or the forced
+    outcome).  Returns (outcome, probability of the outcome, p0)."""
+    assert psi.dtype == np.complex128 and psi.flags.c_contiguous
+    prob = np.zeros(1)
+    p0 = np.zeros(1)
+    out = lib().orc_measure_qubit(n, _d(psi.view(np.float64)), int(q), float(u), int(forced), _d(prob), _d(p0))
+    if out < 0:
+        raise ValueError("bad qubit")
+    return out, float(prob[0]), float(p0[0])
 
 
 def num_threads() -> int:

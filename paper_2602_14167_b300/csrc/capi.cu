@@ -19,7 +19,13 @@
 namespace tcng {
 
 static std::atomic<uint64_t> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local int g_count_off = 0;
+void count_launch() {
+    if (!g_count_off) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void add_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+LaunchCountOff::LaunchCountOff() { ++g_count_off; }
+LaunchCountOff::~LaunchCountOff() { --g_count_off; }
 
 static thread_local std::string g_err;
 tcng_status fail(tcng_status s, const std::string& msg) {
@@ -41,6 +47,7 @@ struct ProfRec {
 };
 static bool g_prof = false;
 static std::mutex g_prof_mu;
+bool profiling_enabled() { return g_prof; }
 static std::vector<ProfRec> g_prof_recs;
 
 ProfScope::ProfScope(const char* nm, cudaStream_t st) : name(nm), s(st) {
@@ -86,6 +93,7 @@ void* DeviceCtx::scratch(const std::string& name, size_t bytes) {
             b.bytes = 0;
         }
         size_t cap = std::max(bytes, (size_t)256);
+        ++gen;
         if (cudaMalloc(&b.ptr, cap) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
@@ -196,6 +204,7 @@ void* plan_table(DevPlan* dp, size_t elem, int items) {
             dp->d_table = nullptr;
             dp->table_bytes = 0;
         }
+        ++ctx().gen;
         if (cudaMalloc(&dp->d_table, need) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
@@ -208,18 +217,23 @@ void* plan_table(DevPlan* dp, size_t elem, int items) {
 // Run a plan on a group of items (all with n == plan.n).
 template <typename C>
 tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int items,
-                     const double* params, cudaStream_t s, void* tma_base, long long item_stride) {
+                     const double* params, cudaStream_t s, void* tma_base, long long item_stride,
+                     const double2* item_pool, long long pool_stride) {
     Plan& pl = dp->plan;
-    const int tab_items = pl.P > 0 ? items : 1;
+    // per-item matrices: from per-item parameters, or from a per-item matrix pool
+    const bool per_item = pl.P > 0 || (item_pool && pool_stride > 0);
+    const double2* pool = item_pool ? item_pool : dp->d_pool;
+    const long long pstride = item_pool ? pool_stride : 0;
+    const int tab_items = per_item ? items : 1;
     C* table = static_cast<C*>(plan_table(dp, sizeof(C), tab_items));
     if (!table) return fail(TCNG_ENOMEM, "matrix table allocation failed");
-    const long long stride = pl.P > 0 ? pl.table_size : 0;
+    const long long stride = per_item ? pl.table_size : 0;
     cudaError_t e;
     {
     ProfScope ps("build_matrices", s);
     e = launch_build_matrices<C>(dp->d_bblocks, (int)pl.bblocks.size(), dp->d_bops,
-                                             dp->d_pool, pl.P > 0 ? params : nullptr, pl.P, table,
-                                             pl.table_size, tab_items, s);
+                                             pool, pl.P > 0 ? params : nullptr, pl.P, table,
+                                             pl.table_size, tab_items, s, pstride);
     }
     if (e != cudaSuccess) return cuda_fail(e, "matrix prologue");
     if (pl.opt.unfused) {
@@ -249,12 +263,12 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
                 if (!dtab || !w) return fail(TCNG_ENOMEM, "tensor-core operand scratch");
                 ProfScope ps("build_stage_w", s);
                 e = launch_build_matrices<double2>(dp->d_bblocks, (int)pl.bblocks.size(), dp->d_bops,
-                                                   dp->d_pool, pl.P > 0 ? params : nullptr, pl.P, dtab,
-                                                   pl.table_size, tab_items, s);
+                                                   pool, pl.P > 0 ? params : nullptr, pl.P, dtab,
+                                                   pl.table_size, tab_items, s, pstride);
                 if (e == cudaSuccess) e = launch_build_stage_w(dp, dtab, stride, tab_items, w, s);
                 if (e != cudaSuccess) return cuda_fail(e, "tensor-core operand prologue");
                 wops = w;
-                w_stride = pl.P > 0 ? 2048ll * dp->n_tc : 0;
+                w_stride = per_item ? 2048ll * dp->n_tc : 0;
             }
         }
         for (size_t pi = 0; pi < pl.passes.size(); ++pi) {
@@ -288,9 +302,9 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
     return TCNG_OK;
 }
 template tcng_status run_plan<float2>(DevPlan*, float2*, const long long*, int, const double*, cudaStream_t,
-                                      void*, long long);
+                                      void*, long long, const double2*, long long);
 template tcng_status run_plan<double2>(DevPlan*, double2*, const long long*, int, const double*, cudaStream_t,
-                                       void*, long long);
+                                       void*, long long, const double2*, long long);
 
 // Device address of a group's first item and the spacing of its items in bytes
 // (-1 if they are not equally spaced).
@@ -459,6 +473,7 @@ tcng_status tcng_state_free(tcng_state* st) {
     if (st->owned) cudaFree(st->buf);
     cudaFree(st->d_off);
     for (auto& kv : st->groups) cudaFree(kv.second.d_off);
+    for (auto& kv : st->pack) cudaFree(kv.second.first);
     delete st;
     return TCNG_OK;
 }
@@ -533,6 +548,39 @@ tcng_status tcng_state_ptr(const tcng_state* st, int item, void** dev_amp, size_
     return TCNG_OK;
 }
 
+}  // extern "C"
+
+namespace tcng {
+// A batch of states smaller than a tile that all see the same gates (no
+// per-item parameters) is stored back to back, so 2^(m-n) consecutive items
+// form one 2^m-amplitude tile of a virtual m-qubit state whose top m - n qubits
+// no gate touches (the QML batches of Sec. VII.B: B inputs, one circuit).
+// Every pass then runs on full tiles -- on the tensor cores for complex64, one
+// W set for the whole batch -- instead of one small tile per item.  Returns
+// the number of whole virtual items (0: not packable); items past
+// virtual * 2^(m-n) run the ordinary per-item path.
+static long long packed_items(tcng_state* st, int m, int P, long long** d_voff) {
+    if (st->groups.size() != 1 || P != 0) return 0;
+    const int n = st->groups.begin()->first;
+    const int es = st->dt == TCNG_C64 ? 8 : 16;
+    if (n >= m || (es << n) < 256) return 0;
+    for (int b = 0; b < st->batch; ++b)
+        if (st->off[b] != ((long long)b << n)) return 0;
+    const long long nv = ((long long)st->batch << n) >> m;
+    if (nv < 1) return 0;
+    auto it = st->pack.find(m);
+    if (it == st->pack.end()) {
+        std::vector<long long> v(nv);
+        for (long long i = 0; i < nv; ++i) v[i] = i << m;
+        it = st->pack.emplace(m, std::make_pair(dev_copy(v), nv)).first;
+    }
+    *d_voff = it->second.first;
+    return it->second.second;
+}
+}  // namespace tcng
+
+extern "C" {
+
 tcng_status tcng_apply_circuit(tcng_state* st, const tcng_gate* ops, size_t n_ops,
                                const double* mat_pool, size_t n_mat, const void* params_dev, int P,
                                void* stream) {
@@ -544,6 +592,44 @@ tcng_status tcng_apply_circuit(tcng_state* st, const tcng_gate* ops, size_t n_op
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     TCNG_TRY({
         const PlanOptions o = plan_options(st->dt, false);
+        // graph key: structure of every size class, options and every device pointer read
+        uint64_t key = key_mix(options_key(), 1);
+        key = key_mix(key, reinterpret_cast<uintptr_t>(st));
+        key = key_mix(key, reinterpret_cast<uintptr_t>(st->buf));
+        key = key_mix(key, reinterpret_cast<uintptr_t>(params_dev));
+        key = key_mix(key, (uint64_t)P);
+        for (auto& kv : st->groups)
+            key = key_mix(key, structure_hash(kv.first, ops, n_ops, mat_pool, n_mat, P, o));
+        return run_graphed(key, s, [&](cudaStream_t s) -> tcng_status {
+        long long* d_voff = nullptr;
+        const long long nv = o.unfused ? 0 : packed_items(st, o.tile_bits, P, &d_voff);
+        int first = 0;   // first item left for the per-item path
+        if (nv > 0) {
+            const int n = st->groups.begin()->first;
+            const int m = o.tile_bits;
+            // the n-qubit plan validates every qubit against n (the virtual m-qubit
+            // register would accept qubits of the neighbouring items)
+            DevPlan* dq = get_plan(n, ops, n_ops, mat_pool, n_mat, 0, o);
+            DevPlan* dp = get_plan(m, ops, n_ops, mat_pool, n_mat, 0, o);
+            const long long vstride = (long long)(st->dt == TCNG_C64 ? 8 : 16) << m;
+            tcng_status r;
+            if (st->dt == TCNG_C64)
+                r = run_plan<float2>(dp, static_cast<float2*>(st->buf), d_voff, (int)nv, nullptr, s, st->buf, vstride);
+            else
+                r = run_plan<double2>(dp, static_cast<double2*>(st->buf), d_voff, (int)nv, nullptr, s, st->buf, vstride);
+            if (r) return r;
+            first = (int)((nv << m) >> n);
+            if (first >= st->batch) return TCNG_OK;
+            const int rest = st->batch - first;
+            std::vector<int> items(rest);
+            for (int i = 0; i < rest; ++i) items[i] = first + i;
+            void* tb = nullptr;
+            long long ts = -1;
+            group_span(st, items, &tb, &ts);
+            if (st->dt == TCNG_C64)
+                return run_plan<float2>(dq, static_cast<float2*>(st->buf), st->d_off + first, rest, nullptr, s, tb, ts);
+            return run_plan<double2>(dq, static_cast<double2*>(st->buf), st->d_off + first, rest, nullptr, s, tb, ts);
+        }
         for (auto& kv : st->groups) {
             const int n = kv.first;
             const int items = (int)kv.second.items.size();
@@ -570,6 +656,46 @@ tcng_status tcng_apply_circuit(tcng_state* st, const tcng_gate* ops, size_t n_op
             if (r) return r;
         }
         return TCNG_OK;
+        });
+    })
+}
+
+tcng_status tcng_apply_circuit_pooled(tcng_state* st, const tcng_gate* ops, size_t n_ops,
+                                      const double* mat_pool, size_t n_mat, const void* item_pool_dev,
+                                      size_t pool_stride, const void* params_dev, int P, void* stream) {
+    if (!st) return fail(TCNG_EINVAL, "state is NULL");
+    if (P < 0) return fail(TCNG_EINVAL, "P < 0");
+    if (P > 0 && !params_dev) return fail(TCNG_EINVAL, "params_dev is NULL");
+    if (!item_pool_dev) return fail(TCNG_EINVAL, "item_pool_dev is NULL");
+    if (pool_stride < n_mat) return fail(TCNG_EINVAL, "pool_stride < n_mat");
+    if (reinterpret_cast<uintptr_t>(item_pool_dev) & 15) return fail(TCNG_EINVAL, "item_pool_dev not 16-byte aligned");
+    if (st->groups.size() != 1) return fail(TCNG_EUNSUPPORTED, "ragged state: call per size class");
+    if (n_ops == 0) return TCNG_OK;
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TCNG_TRY({
+        const PlanOptions o = plan_options(st->dt, false);
+        const int n = st->groups.begin()->first;
+        uint64_t key = key_mix(options_key(), 4);
+        for (const void* p : {(const void*)st, (const void*)st->buf, params_dev, item_pool_dev})
+            key = key_mix(key, reinterpret_cast<uintptr_t>(p));
+        key = key_mix(key, ((uint64_t)pool_stride << 16) ^ (uint64_t)P);
+        key = key_mix(key, structure_hash(n, ops, n_ops, mat_pool, n_mat, P, o));
+        return run_graphed(key, s, [&](cudaStream_t s) -> tcng_status {
+            const auto& g = st->groups.begin()->second;
+            const int items = (int)g.items.size();
+            void* tb = nullptr;
+            long long ts = -1;
+            group_span(st, g.items, &tb, &ts);
+            DevPlan* dp = get_plan(n, ops, n_ops, mat_pool, n_mat, P, o);
+            const double* prm = static_cast<const double*>(params_dev);
+            const double2* pool = static_cast<const double2*>(item_pool_dev);
+            if (st->dt == TCNG_C64)
+                return run_plan<float2>(dp, static_cast<float2*>(st->buf), g.d_off, items, prm, s, tb, ts, pool,
+                                        (long long)pool_stride);
+            return run_plan<double2>(dp, static_cast<double2*>(st->buf), g.d_off, items, prm, s, tb, ts, pool,
+                                     (long long)pool_stride);
+        });
     })
 }
 
@@ -786,6 +912,71 @@ const char* tcng_describe_plan(int n, const tcng_gate* ops, size_t n_ops, const 
         out = std::string("error: ") + ex.what();
     }
     return out.c_str();
+}
+
+tcng_status tcng_marginal_probs(const tcng_state* st, const int* qubits, int k, double* out_dev,
+                                void* stream) {
+    if (!st || !qubits || !out_dev) return fail(TCNG_EINVAL, "null argument");
+    if (k < 1 || k > 10) return fail(TCNG_EINVAL, "k must be 1..10");
+    if (st->groups.size() != 1) return fail(TCNG_EUNSUPPORTED, "ragged state: call per size class");
+    const int n = st->n[0];
+    uint64_t seen = 0;
+    for (int i = 0; i < k; ++i) {
+        if (qubits[i] < 0 || qubits[i] >= n) return fail(TCNG_EINVAL, "qubit out of range");
+        if ((seen >> qubits[i]) & 1) return fail(TCNG_EINVAL, "repeated qubit");
+        seen |= 1ull << qubits[i];
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    TCNG_TRY({
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const int items = st->batch;
+        const int splits = marginal_splits(items, n, k);
+        double* partial = nullptr;
+        if (splits > 1) {
+            partial = static_cast<double*>(
+                ctx().scratch("marginal", sizeof(double) * ((size_t)items << k) * splits));
+            if (!partial) return fail(TCNG_ENOMEM, "marginal scratch");
+        }
+        ProfScope ps("marginal_probs", s);
+        cudaError_t e;
+        if (st->dt == TCNG_C64)
+            e = launch_marginal<float2>(static_cast<const float2*>(st->buf), st->d_off, items, n, qubits, k,
+                                        out_dev, partial, splits, s);
+        else
+            e = launch_marginal<double2>(static_cast<const double2*>(st->buf), st->d_off, items, n, qubits, k,
+                                         out_dev, partial, splits, s);
+        if (e != cudaSuccess) return cuda_fail(e, "marginal kernel");
+        return TCNG_OK;
+    })
+}
+
+tcng_status tcng_measure(tcng_state* st, const uint64_t* mask_dev, const double* u_dev, int8_t* outcome_dev,
+                         double* logp_dev, void* stream) {
+    if (!st || !mask_dev || !u_dev || !outcome_dev) return fail(TCNG_EINVAL, "null argument");
+    if (st->groups.size() != 1) return fail(TCNG_EUNSUPPORTED, "ragged state: call per size class");
+    std::lock_guard<std::mutex> lk(g_mu);
+    TCNG_TRY({
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const int n = st->n[0];
+        const int items = st->batch;
+        const int splits = measure_splits(items, n);
+        DeviceCtx& c = ctx();
+        double* hist = static_cast<double*>(c.scratch("meas_hist", sizeof(double) * 1024 * (size_t)items * splits));
+        void* proj = c.scratch("meas_proj", measure_proj_bytes(items));
+        if (!hist || !proj) return fail(TCNG_ENOMEM, "measurement scratch");
+        ProfScope ps("measure", s);
+        cudaError_t e;
+        const auto* mk = reinterpret_cast<const unsigned long long*>(mask_dev);
+        auto* oc = reinterpret_cast<signed char*>(outcome_dev);
+        if (st->dt == TCNG_C64)
+            e = launch_measure<float2>(static_cast<float2*>(st->buf), st->d_off, items, n, mk, u_dev, oc, logp_dev,
+                                       hist, splits, proj, s);
+        else
+            e = launch_measure<double2>(static_cast<double2*>(st->buf), st->d_off, items, n, mk, u_dev, oc,
+                                        logp_dev, hist, splits, proj, s);
+        if (e != cudaSuccess) return cuda_fail(e, "measurement kernels");
+        return TCNG_OK;
+    })
 }
 
 }  // extern "C"

@@ -245,13 +245,20 @@ tcng_status tcng_energy_grad(tcng_state* st, const tcng_gate* ops, size_t n_ops,
         pr.n_terms = n_terms;
         std::vector<int> ip(st->batch, 0);
         AdjLayout* lay = get_layout(&pr, 1, ip.data(), st->batch, st->dt, st->off.data());
-        cudaStream_t s = static_cast<cudaStream_t>(stream);
         const double* prm = static_cast<const double*>(params_dev);
-        if (st->dt == TCNG_C64)
-            return run_adjoint<float2>(lay, st->batch, prm, coeffs_dev, energy_dev, grad_dev, st->buf,
-                                       P > 0, s);
-        return run_adjoint<double2>(lay, st->batch, prm, coeffs_dev, energy_dev, grad_dev, st->buf,
-                                    P > 0, s);
+        uint64_t key = key_mix(options_key(), 2);
+        for (const void* p : {(const void*)lay, (const void*)st->buf, params_dev, (const void*)coeffs_dev,
+                              (const void*)energy_dev, (const void*)grad_dev})
+            key = key_mix(key, reinterpret_cast<uintptr_t>(p));
+        key = key_mix(key, ((uint64_t)st->batch << 32) | (uint32_t)P);
+        const tcng_dtype dt = st->dt;
+        const int batch = st->batch;
+        void* buf = st->buf;
+        return run_graphed(key, static_cast<cudaStream_t>(stream), [&](cudaStream_t s) -> tcng_status {
+            if (dt == TCNG_C64)
+                return run_adjoint<float2>(lay, batch, prm, coeffs_dev, energy_dev, grad_dev, buf, P > 0, s);
+            return run_adjoint<double2>(lay, batch, prm, coeffs_dev, energy_dev, grad_dev, buf, P > 0, s);
+        });
     } catch (const std::invalid_argument& ex) {
         return fail(TCNG_EINVAL, ex.what());
     } catch (const std::bad_alloc&) {
@@ -273,8 +280,15 @@ tcng_status tcng_energy_grad_ragged(const tcng_problem* problems, int n_problems
     std::lock_guard<std::mutex> lk(g_mu);
     try {
         AdjLayout* lay = get_layout(problems, n_problems, item_problem, batch, TCNG_C64, nullptr);
-        return run_adjoint<float2>(lay, batch, params_dev, coeffs_dev, energy_dev, grad_dev, nullptr,
-                                   any_p, static_cast<cudaStream_t>(stream));
+        uint64_t key = key_mix(options_key(), 3);
+        for (const void* p : {(const void*)lay, (const void*)params_dev, (const void*)coeffs_dev,
+                              (const void*)energy_dev, (const void*)grad_dev})
+            key = key_mix(key, reinterpret_cast<uintptr_t>(p));
+        key = key_mix(key, (uint64_t)batch);
+        return run_graphed(key, static_cast<cudaStream_t>(stream), [&](cudaStream_t s) -> tcng_status {
+            return run_adjoint<float2>(lay, batch, params_dev, coeffs_dev, energy_dev, grad_dev, nullptr,
+                                       any_p, s);
+        });
     } catch (const std::invalid_argument& ex) {
         return fail(TCNG_EINVAL, ex.what());
     } catch (const std::bad_alloc&) {

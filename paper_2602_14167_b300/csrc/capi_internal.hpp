@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -28,6 +29,9 @@ struct tcng_state {
     bool owned = false;
     long long* d_off = nullptr;
     std::map<int, Group> groups;      // items by qubit count
+    // packed views of a batch of small states: tile bits m -> device offsets of the
+    // virtual 2^m-amplitude items (2^(m-n) consecutive items each) and their count
+    std::map<int, std::pair<long long*, long long>> pack;
 };
 
 namespace tcng {
@@ -84,6 +88,20 @@ struct DeviceCtx {
     std::unordered_map<uint64_t, std::unique_ptr<TermSet>> terms;
     std::map<std::string, Buf> bufs;
     void* scratch(const std::string& name, size_t bytes);
+    // allocation generation: bumped whenever a scratch buffer or matrix table
+    // moves, which invalidates every recorded graph
+    uint64_t gen = 0;
+    // recorded launch sequences (one CUDA graph per structure and pointer set)
+    struct GraphEntry {
+        int seen = 0;
+        bool bad = false;
+        cudaGraphExec_t exec = nullptr;
+        int kernels = 0;
+        ~GraphEntry();
+    };
+    std::unordered_map<uint64_t, std::unique_ptr<GraphEntry>> graphs;
+    uint64_t graph_gen = 0;
+    cudaStream_t capture_stream = nullptr;
 };
 
 // Event-timed scope around one kernel launch (active only when profiling is on).
@@ -96,6 +114,19 @@ struct ProfScope {
 };
 
 DeviceCtx& ctx();
+bool profiling_enabled();
+void add_launches(uint64_t k);
+// While alive, launches on this thread are not counted (they are being recorded).
+struct LaunchCountOff {
+    LaunchCountOff();
+    ~LaunchCountOff();
+};
+// CUDA graph per structure (graphs.cu): key_mix folds values into a key;
+// options_key() covers every option a launch sequence depends on; run_graphed
+// runs body eagerly, records it, or replays the recording (see graphs.cu).
+uint64_t key_mix(uint64_t h, uint64_t v);
+uint64_t options_key();
+tcng_status run_graphed(uint64_t key, cudaStream_t s, const std::function<tcng_status(cudaStream_t)>& body);
 tcng_status fail(tcng_status s, const std::string& msg);
 tcng_status cuda_fail(cudaError_t e, const char* where);
 PlanOptions plan_options(tcng_dtype dt, bool adjoint);
@@ -110,7 +141,8 @@ void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
 template <typename C>
 tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int items,
                      const double* params, cudaStream_t s, void* tma_base = nullptr,
-                     long long item_stride = -1);
+                     long long item_stride = -1, const double2* item_pool = nullptr,
+                     long long pool_stride = 0);
 
 // Tensor-core register stages (kernels_pass_tc.cu).
 void plan_tensor_stages(DevPlan* dp);

@@ -490,11 +490,13 @@ template <typename C>
 cudaError_t launch_adjoint(const AdjArgs& a, int grid, cudaStream_t s) {
     const size_t smem = adjoint_smem_bytes<C>(a.res_bits);
     auto kern = adjoint_kernel<C>;
-    static size_t set_bytes = 0;   // set once (the call is not legal inside every stream capture)
-    if (set_bytes < smem) {
+    // set once per device (the call is not legal inside every stream capture)
+    static size_t set_bytes[kMaxDeviceSlots] = {};
+    const int d = device_slot();
+    if (set_bytes[d] < smem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        set_bytes = smem;
+        set_bytes[d] = smem;
     }
     kern<<<grid, adjoint_threads<C>(), smem, s>>>(a);
     count_launch();

@@ -327,7 +327,8 @@ __global__ void __launch_bounds__(kExpThreads, 1)
     if (tid < nt) {   // warps in order
         double s = 0;
         for (int w = 0; w < kExpThreads / 32; ++w) s += red[w][tid];
-        partial[((long long)item * n_out + ep.t[tid].out) * gridDim.x + blockIdx.x] = s;
+        // a timed-out wait leaves the sum short: report NaN rather than a wrong value
+        partial[((long long)item * n_out + ep.t[tid].out) * gridDim.x + blockIdx.x] = s_abort ? __longlong_as_double(0x7ff8000000000000ll) : s;
     }
 }
 
@@ -342,12 +343,13 @@ cudaError_t launch_expect_fast(const float2* state, const long long* item_off, i
                                const ExpPass& ep, const TileCtx& tc, double* partial, int n_out, int nblk,
                                unsigned* err, cudaStream_t s, const TmaTile& tma) {
     if (p.m != kEfTileBits || tc.nbuf != kEfNbuf) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
+    static bool attr[kMaxDeviceSlots] = {};   // the attribute is per device
+    const int d = device_slot();
+    if (!attr[d]) {
         const cudaError_t e = cudaFuncSetAttribute(expect_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)expect_fast_smem_bytes());
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[d] = true;
     }
     dim3 grid((unsigned)nblk, (unsigned)items);
     expect_fast_kernel<<<grid, kExpThreads, expect_fast_smem_bytes(), s>>>(state, item_off, p, ep, tc, partial,

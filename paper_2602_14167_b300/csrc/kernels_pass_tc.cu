@@ -524,7 +524,10 @@ __global__ void __launch_bounds__(TS_CTA_THREADS, 1)
                         to += r.y;
                     }
                 }
-                const float f = (to > 0.f && ti > 0.f) ? ti * rsqrtf(ti * to) : 1.f;   // sqrt(ti / to)
+                // sqrt(ti / to); tiles of tiny norm keep their values (ti * to, or the
+                // squares themselves, would leave the FP32 range: a product state's
+                // far tiles have norms far below 1e-30)
+                const float f = (to > 1e-30f && ti > 1e-30f) ? sqrtf(ti) * rsqrtf(to) : 1.f;
 #pragma unroll
                 for (int v = 0; v < 16; ++v) x[v] = make_float2(x[v].x * f, x[v].y * f);
                 nin = 0.f;
@@ -673,12 +676,13 @@ cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float*
                             long long w_item_stride, unsigned* err, const TmaTile& tma, bool swizzled,
                             float2* state, const long long* item_off, cudaStream_t s) {
     const DevPass& P = dp->plan.passes[pass];
-    static bool attr = false;
-    if (!attr) {
+    static bool attr[kMaxDeviceSlots] = {};   // the attribute is per device
+    const int d = device_slot();
+    if (!attr[d]) {
         cudaError_t e = set_pass_tcs_smem<TS_NBUF, TS_NB>();
         if (e == cudaSuccess) e = set_pass_tcs_smem<TS_NBUF_RES, TS_NB_RES>();
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[d] = true;
     }
     bool rot = false;   // XOR-rotated slot reads (not needed on a swizzled tile)
     for (int si = 0; si < P.stage_count; ++si) rot = rot || dp->tcs[P.stage_begin + si].nj > 0;

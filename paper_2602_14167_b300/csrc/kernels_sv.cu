@@ -69,9 +69,10 @@ __global__ void build_matrices_kernel(const BuildBlock* __restrict__ blocks,
                                       const double* __restrict__ params, int P,
                                       C* __restrict__ table, long long table_stride,
                                       int item_base, const long long* __restrict__ prm_off,
-                                      const long long* __restrict__ tab_off) {
+                                      const long long* __restrict__ tab_off, long long pool_stride) {
     const int bi = blockIdx.x;
     const int item = blockIdx.y + item_base;
+    pool += (long long)item * pool_stride;   // per-item explicit matrices (0: shared pool)
     const BuildBlock blk = blocks[bi];
     const int D = 1 << blk.k;
     const double* th = params ? params + (prm_off ? prm_off[item] : (long long)item * P) : nullptr;
@@ -444,7 +445,8 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
         double s = 0;
         const int nw = (blockDim.x + 31) >> 5;
         for (int w = 0; w < nw; ++w) s += red[w][tid];
-        partial[((long long)item * n_out + ep.t[tid].out) * gridDim.x + blockIdx.x] = s;
+        // a timed-out wait leaves the sum short: report NaN rather than a wrong value
+        partial[((long long)item * n_out + ep.t[tid].out) * gridDim.x + blockIdx.x] = s_abort ? __longlong_as_double(0x7ff8000000000000ll) : s;
     }
 }
 
@@ -506,26 +508,33 @@ __global__ void ham_apply_kernel(const C* __restrict__ psi_all, const long long*
 }
 
 // ============================================================ launchers ==
-static int g_num_sms = 0;
+int device_slot() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    return dev < kMaxDeviceSlots ? dev : kMaxDeviceSlots - 1;
+}
+
+static int g_num_sms[kMaxDeviceSlots] = {};
 int num_sms() {
-    if (!g_num_sms) {
-        int dev = 0;
+    int& n = g_num_sms[device_slot()];
+    if (!n) {
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_num_sms <= 0) g_num_sms = 148;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        n = v > 0 ? v : 148;
     }
-    return g_num_sms;
+    return n;
 }
 
 template <typename C>
 cudaError_t launch_build_matrices(const BuildBlock* blocks, int n_blocks, const BuildOp* bops,
                                   const double2* pool, const double* params, int P, C* table,
-                                  long long table_stride, int items, cudaStream_t s) {
+                                  long long table_stride, int items, cudaStream_t s, long long pool_stride) {
     if (n_blocks == 0 || items == 0) return cudaSuccess;
     for (int i0 = 0; i0 < items; i0 += 65535) {
         dim3 grid(n_blocks, std::min(65535, items - i0));
         build_matrices_kernel<C><<<grid, 32, 0, s>>>(blocks, bops, pool, params, P, table,
-                                                      table_stride, i0, nullptr, nullptr);
+                                                      table_stride, i0, nullptr, nullptr, pool_stride);
         count_launch();
     }
     return cudaGetLastError();
@@ -540,7 +549,7 @@ cudaError_t launch_build_matrices_indexed(const BuildBlock* blocks, int n_blocks
     for (int i0 = 0; i0 < items; i0 += 65535) {
         dim3 grid(n_blocks, std::min(65535, items - i0));
         build_matrices_kernel<C><<<grid, 32, 0, s>>>(blocks, bops, pool, params, 0, table, 0, i0,
-                                                      prm_off, tab_off);
+                                                      prm_off, tab_off, 0);
         count_launch();
     }
     return cudaGetLastError();
@@ -648,9 +657,10 @@ cudaError_t launch_pass(C* state, const long long* item_off, int items, int n, c
     const size_t smem = pass_smem_bytes<C>(p, nbuf);
     (void)host_stages;
     auto kern = pass_kernel<C>;
-    static bool done = false;
-    static size_t lim = 0;
-    if (smem > dyn_smem_limit(kern, &done, &lim)) return cudaErrorInvalidConfiguration;
+    static bool done[kMaxDeviceSlots] = {};
+    static size_t lim[kMaxDeviceSlots] = {};
+    const int d = device_slot();
+    if (smem > dyn_smem_limit(kern, &done[d], &lim[d])) return cudaErrorInvalidConfiguration;
     TileCtx tc = make_ctx(p, n, items, sizeof(C), nbuf);
     const int threads = std::max(32, (1 << p.m) >> kRegBits);
     int per_sm = 1;
@@ -680,9 +690,10 @@ cudaError_t launch_expect_pass(const C* state, const long long* item_off, int it
     }
     {
         auto kern = expect_pass_kernel<C>;
-        static bool done = false;
-        static size_t lim = 0;
-        if (smem > dyn_smem_limit(kern, &done, &lim)) return cudaErrorInvalidConfiguration;
+        static bool done[kMaxDeviceSlots] = {};
+        static size_t lim[kMaxDeviceSlots] = {};
+        const int d = device_slot();
+        if (smem > dyn_smem_limit(kern, &done[d], &lim[d])) return cudaErrorInvalidConfiguration;
         const int threads = std::min(512, std::max(32, 1 << p.m));
         kern<<<grid, threads, smem, s>>>(state, item_off, p, ep, tc, partial, n_out, err, tma ? *tma : t0);
     }
@@ -713,7 +724,7 @@ cudaError_t launch_ham_apply(const C* psi, const long long* off_in, C* out, cons
 #define TCNG_INST(C)                                                                                  \
     template cudaError_t launch_build_matrices<C>(const BuildBlock*, int, const BuildOp*,             \
                                                   const double2*, const double*, int, C*, long long,  \
-                                                  int, cudaStream_t);                                 \
+                                                  int, cudaStream_t, long long);                      \
     template cudaError_t launch_set_basis<C>(C*, const long long*, int, cudaStream_t);                \
     template cudaError_t launch_build_matrices_indexed<C>(const BuildBlock*, int, const BuildOp*,     \
                                                           const double2*, const double*, C*,          \

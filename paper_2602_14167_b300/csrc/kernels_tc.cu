@@ -255,11 +255,12 @@ extern "C" tcng_status tcng_apply_shared_unitary(tcng_state* st, const int* qubi
     e = cudaStreamSynchronize(s);   // w is a host temporary
     if (e != cudaSuccess) return cuda_fail(e, "upload");
     const size_t smem = 2 * TC_A_BYTES + 2 * TC_B_BYTES + 1024;
-    static bool attr = false;
-    if (!attr) {
+    static bool attr[kMaxDeviceSlots] = {};   // the attribute is per device
+    const int d = device_slot();
+    if (!attr[d]) {
         e = cudaFuncSetAttribute(shared_unitary_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(e, "smem attribute");
-        attr = true;
+        attr[d] = true;
     }
     for (auto& kv : st->groups) {
         TcArgs a{};

@@ -10,6 +10,10 @@ namespace tcng {
 
 void count_launch();
 int num_sms();
+// Per-device caches (kernel attributes, SM counts) are indexed by this slot:
+// the current device's index, 0 .. kMaxDeviceSlots - 1.
+constexpr int kMaxDeviceSlots = 64;
+int device_slot();
 
 struct ExpTerm {
     uint32_t xm_tile;   // X mask in tile bits
@@ -66,7 +70,8 @@ struct HTerm {
 template <typename C>
 cudaError_t launch_build_matrices(const BuildBlock* blocks, int n_blocks, const BuildOp* bops,
                                   const double2* pool, const double* params, int P, C* table,
-                                  long long table_stride, int items, cudaStream_t s);
+                                  long long table_stride, int items, cudaStream_t s,
+                                  long long pool_stride = 0);
 template <typename C>
 cudaError_t launch_build_matrices_indexed(const BuildBlock* blocks, int n_blocks, const BuildOp* bops,
                                           const double2* pool, const double* params, C* table,
@@ -86,6 +91,20 @@ template <typename C>
 cudaError_t launch_expect_pass(const C* state, const long long* item_off, int items, int n,
                                const DevPass& p, const ExpPass& ep, double* partial, int n_out,
                                int nblk, unsigned* err, cudaStream_t s, const TmaTile* tma = nullptr);
+// Probabilities of k <= 10 qubits (kernels_measure.cu); partial holds
+// items * 2^k * splits doubles when splits > 1.
+template <typename C>
+cudaError_t launch_marginal(const C* state, const long long* item_off, int items, int n, const int* q, int k,
+                            double* out, double* partial, int splits, cudaStream_t s);
+int marginal_splits(int items, int n, int k);
+// Projective measurement of per-item qubit sets (kernels_measure.cu): hist holds
+// items * 1024 * splits doubles, proj measure_proj_bytes(items) bytes.
+template <typename C>
+cudaError_t launch_measure(C* state, const long long* item_off, int items, int n,
+                           const unsigned long long* mask, const double* u, signed char* outcome, double* logp,
+                           double* hist, int splits, void* proj, cudaStream_t s);
+size_t measure_proj_bytes(int items);
+int measure_splits(int items, int n);
 cudaError_t launch_expect_finalize(const double* partial, int nblk, int n_out, double* out,
                                    const double* coeffs, const double* term_coeff, double* energy,
                                    int items, cudaStream_t s);

@@ -1,10 +1,9 @@
 // Pauli expectations with no device allocation (tcng_expect_pauli_noalloc).
 //
 // Some callers cannot let a library allocate device memory: a host framework
-// whose own allocator has already reserved the GPU's free memory, a serving
+// whose own allocator has already reserved the GPU's free memory, or a serving
 // loop that forbids allocation (and the device synchronisation cudaFree brings)
-// on its hot path, or code that records work into a stream capture, where
-// cudaMalloc is not allowed.  This entry point runs the same expectation passes
+// on its hot path.  This entry point runs the same expectation passes
 // as tcng_expect_pauli but keeps the per-CTA partial sums in a fixed-size array
 // in this file's device memory, so it calls no cudaMalloc or cudaFree and never
 // touches the library's other caches.  Every GPU that loads the library holds
@@ -75,6 +74,9 @@ extern "C" tcng_status tcng_expect_pauli_noalloc(const void* psi_dev, int n, tcn
         return fail(TCNG_EINVAL, "psi_dev must be 256-byte aligned");
     if (n_terms == 0) return TCNG_OK;
     if (n_terms > 4096) return fail(TCNG_EINVAL, "at most 4096 terms per call");
+    // the options and the launchers' per-device attribute caches are shared with
+    // every other entry point: read and use them under the library lock
+    std::lock_guard<std::mutex> lk(g_mu);
     try {
         const PlanOptions o = plan_options(dt, false);
         std::vector<DevPass> passes;

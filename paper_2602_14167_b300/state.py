@@ -31,6 +31,26 @@ class StateBatch:
         off = ptr - self.buf.data_ptr()
         return self.buf[off:off + nb].view(self.cdtype)
 
+    def batch_view(self) -> torch.Tensor:
+        """A [batch, 2^n] complex view (no copy) when every item has the same n and
+        the items lie back to back (2^n amplitudes >= 256 bytes)."""
+        if len(set(self.n)) != 1:
+            raise ValueError("ragged batch")
+        n = self.n[0]
+        ptr0, nb = T.tcng_state_ptr(self.handle, 0)
+        if self.batch > 1:
+            ptr1, _ = T.tcng_state_ptr(self.handle, 1)
+            if ptr1 - ptr0 != nb:
+                raise ValueError("items are not back to back")
+        off = ptr0 - self.buf.data_ptr()
+        return self.buf[off:off + nb * self.batch].view(self.cdtype).view(self.batch, 1 << n)
+
+    def probs(self, qubits) -> torch.Tensor:
+        """Born probabilities of ``qubits`` per item (qubits[0] most significant)."""
+        out = torch.empty((self.batch, 1 << len(qubits)), dtype=torch.float64, device=self.buf.device)
+        T.tcng_marginal_probs(self.handle, list(qubits), out)
+        return out
+
     def reset(self):
         T.tcng_state_reset(self.handle)
 

@@ -59,6 +59,7 @@ def lib():
             "tcng_state_ptr": [vp, i32, C.POINTER(vp), C.POINTER(sz)],
             "tcng_state_reset": [vp, vp],
             "tcng_apply_circuit": [vp, vp, sz, vp, sz, vp, i32, vp],
+            "tcng_apply_circuit_pooled": [vp, vp, sz, vp, sz, vp, sz, vp, i32, vp],
             "tcng_expect_pauli": [vp, vp, sz, vp, vp],
             "tcng_expect_pauli_noalloc": [vp, i32, i32, vp, sz, vp, vp],
             "tcng_energy": [vp, vp, sz, vp, vp, vp],
@@ -67,6 +68,8 @@ def lib():
             "tcng_energy_grad": [vp, vp, sz, vp, sz, vp, i32, vp, sz, vp, vp, vp, vp],
             "tcng_energy_grad_ragged": [vp, i32, vp, i32, vp, vp, vp, vp, vp],
             "tcng_apply_shared_unitary": [vp, vp, i32, vp, vp],
+            "tcng_marginal_probs": [vp, vp, i32, vp, vp],
+            "tcng_measure": [vp, vp, vp, vp, vp, vp],
             "tcng_adam_step": [vp, vp, vp, vp, sz, dp, dp, dp, dp, vp, vp],
             "tcng_adam_step_f32": [vp, vp, vp, vp, sz, fp, fp, fp, fp, vp, vp],
             "tcng_mlp_forward": [vp, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp],
@@ -246,6 +249,28 @@ def tcng_apply_shared_unitary(handle, qubits, U, stream=None):
                                            _stream(stream)))
 
 
+def tcng_marginal_probs(handle, qubits, out_dev, stream=None):
+    q = np.ascontiguousarray(qubits, dtype=np.int32)
+    _check(lib().tcng_marginal_probs(handle, q.ctypes.data, int(q.size), _ptr(out_dev), _stream(stream)))
+
+
+def tcng_measure(handle, mask_dev, u_dev, outcome_dev, logp_dev=None, stream=None):
+    _check(lib().tcng_measure(handle, _ptr(mask_dev), _ptr(u_dev), _ptr(outcome_dev), _ptr(logp_dev),
+                              _stream(stream)))
+
+
+def tcng_apply_circuit_pooled(handle, gates, pool, item_pool_dev, pool_stride, params_dev=None, P=0,
+                              stream=None):
+    """Per-item explicit matrices: item b reads its gate matrices from
+    item_pool_dev[b * pool_stride ...] (device complex128); ``pool`` is a host
+    pool of the same layout used for planning."""
+    g = _gates(gates)
+    p, n_mat = _pool(pool)
+    _check(lib().tcng_apply_circuit_pooled(handle, g.ctypes.data, len(g), p.ctypes.data if n_mat else None,
+                                           n_mat, _ptr(item_pool_dev), int(pool_stride), _ptr(params_dev),
+                                           int(P), _stream(stream)))
+
+
 def tcng_adam_step(theta, m, v, grad, n, lr, b1, b2, eps, step_dev, stream=None):
     _check(lib().tcng_adam_step(_ptr(theta), _ptr(m), _ptr(v), _ptr(grad), int(n), float(lr),
                                 float(b1), float(b2), float(eps), _ptr(step_dev), _stream(stream)))
@@ -322,9 +347,10 @@ def tcng_version():
 
 EXPORTED = [
     "tcng_state_init", "tcng_state_bytes", "tcng_state_free", "tcng_state_ptr", "tcng_state_reset",
-    "tcng_apply_circuit", "tcng_expect_pauli", "tcng_expect_pauli_noalloc", "tcng_energy", "tcng_expect_energy",
+    "tcng_apply_circuit", "tcng_apply_circuit_pooled", "tcng_expect_pauli", "tcng_expect_pauli_noalloc", "tcng_energy", "tcng_expect_energy",
     "tcng_hamiltonian_apply",
-    "tcng_energy_grad", "tcng_energy_grad_ragged", "tcng_apply_shared_unitary", "tcng_adam_step",
+    "tcng_energy_grad", "tcng_energy_grad_ragged", "tcng_apply_shared_unitary", "tcng_marginal_probs", "tcng_measure",
+    "tcng_adam_step",
     "tcng_adam_step_f32", "tcng_mlp_forward", "tcng_mlp_backward", "tcng_set_option",
     "tcng_get_option", "tcng_autotune", "tcng_sync_status", "tcng_describe_plan",
     "tcng_profile_enable", "tcng_profile_read",

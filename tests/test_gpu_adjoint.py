@@ -181,3 +181,43 @@ def test_energy_above_free_fermion_ground(T):
     for i in range(B):
         e0 = dense.tfim_ground_energy_free_fermion(b["J"][i], np.full(n, b["g"][i]))
         assert e[i] >= e0 - 1e-5
+
+
+def test_ragged_mix_full_size_sampled(T):
+    """The benchmark's ragged batch: 1024 items, n in {12, 14, 16, 18, 20}, 12-layer
+    ring ansatz (36 n parameters), one launch.  One sampled item of every size
+    (and the last item): energy against the oracle, gradient through a directional
+    central difference of the oracle's energy (h = 1e-4, complex128)."""
+    from paper_2602_14167_b300 import tcng
+    B = 1024
+    probs, item_problem, theta, coeffs, ns = gen.ragged_vqe_batch(B, layers=12)
+    prm = torch.tensor(theta, dtype=torch.float64, device="cuda")
+    cf = torch.tensor(coeffs, dtype=torch.float64, device="cuda")
+    e = torch.empty(B, dtype=torch.float64, device="cuda")
+    gr = torch.empty_like(prm)
+    tcng.tcng_energy_grad_ragged(probs, item_problem, prm, cf, e, gr)
+    tcng.tcng_sync_status()
+    e = e.cpu().numpy()
+    gr = gr.cpu().numpy()
+    assert np.all(np.isfinite(e)) and np.all(np.isfinite(gr))
+    p_off = np.concatenate([[0], np.cumsum([probs[s]["P"] for s in item_problem])])
+    c_off = np.concatenate([[0], np.cumsum([len(probs[s]["terms"]) for s in item_problem])])
+    picks = sorted({int(np.flatnonzero(ns == n)[0]) for n in set(int(x) for x in ns)} | {B - 1})
+    assert {int(ns[i]) for i in picks} == {12, 14, 16, 18, 20}
+    rng = np.random.default_rng(2)
+    for i in picks:
+        pr = probs[item_problem[i]]
+        n, P = pr["n"], pr["P"]
+        th = theta[p_off[i]:p_off[i + 1]]
+        cfi = coeffs[c_off[i]:c_off[i + 1]]
+        csum = np.abs(cfi).sum()
+        e_ref = sv.energy(n, pr["gates"], pr["pool"], th, pr["terms"], cfi)
+        assert abs(e[i] - e_ref) / csum < TOL["c64"], (i, n, e[i], e_ref)
+        v = rng.standard_normal(P)
+        v /= np.linalg.norm(v)
+        h = 1e-4
+        dd = (sv.energy(n, pr["gates"], pr["pool"], th + h * v, pr["terms"], cfi) -
+              sv.energy(n, pr["gates"], pr["pool"], th - h * v, pr["terms"], cfi)) / (2 * h)
+        gi = gr[p_off[i]:p_off[i + 1]]
+        den = max(np.linalg.norm(gi), 1e-3 * csum)
+        assert abs(np.dot(gi, v) - dd) / den < TOL["c64"], (i, n, np.dot(gi, v), dd)

@@ -97,21 +97,7 @@ def test_qft_of_basis_states(n):
 
 
 # ----------------------------------------------------------------- invariants
-def inverse_circuit(c):
-    inv = Circuit(c.n)
-    for (name, qubits, param, scale, angle0, mat) in reversed(c.ops):
-        if name in ("RX", "RY", "RZ", "RZZ", "CP"):
-            inv.add(name, qubits, param=param, scale=-scale, angle0=-angle0)
-        elif name in ("U1", "U2", "UK"):
-            inv.unitary(qubits, mat.conj().T)
-        elif name == "S":
-            inv.unitary(qubits, np.diag([1, -1j]))
-        elif name == "T":
-            inv.unitary(qubits, np.diag([1, np.exp(-1j * math.pi / 4)]))
-        else:
-            inv.add(name, qubits)
-    inv.n_params = c.n_params
-    return inv
+inverse_circuit = gen.inverse_circuit
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -307,3 +293,159 @@ def test_rejects_bad_gates():
         sv.apply(3, *ir(c), None)
     with pytest.raises(ValueError):
         sv.expect(3, sv.zero_state(3), np.array([(8, 0, 1.0)], dtype=PAULI_DTYPE))
+
+
+# ------------------------------------------------- Born probabilities, measurement
+def test_marginal_probs_bit_order_and_basis_states():
+    psi = np.zeros(8, complex)
+    psi[1] = 1.0                      # qubit 0 set
+    np.testing.assert_array_equal(sv.marginal_probs(3, psi, [0, 1]), [0, 0, 1, 0])   # q[0] most significant
+    np.testing.assert_array_equal(sv.marginal_probs(3, psi, [1, 0]), [0, 1, 0, 0])
+    np.testing.assert_array_equal(sv.marginal_probs(3, psi, [2]), [1, 0])
+
+
+def test_marginal_probs_product_state_closed_form():
+    """RY(t_q) on every qubit: P(bits) = prod_q (cos^2(t_q/2) or sin^2(t_q/2))."""
+    n = 7
+    th = np.linspace(-2.5, 2.9, n)
+    c = Circuit(n)
+    for q in range(n):
+        c.ry(q, param=q)
+    psi = sv.apply(n, *ir(c), th)
+    qs = [5, 0, 3]
+    p = sv.marginal_probs(n, psi, qs)
+    for j in range(8):
+        ref = 1.0
+        for i, q in enumerate(qs):
+            bit = (j >> (len(qs) - 1 - i)) & 1
+            ref *= math.sin(th[q] / 2) ** 2 if bit else math.cos(th[q] / 2) ** 2
+        assert abs(p[j] - ref) < 1e-14
+    assert abs(p.sum() - 1) < 1e-14
+
+
+def test_marginal_probs_ghz():
+    n = 6
+    c = Circuit(n).h(0)
+    for q in range(n - 1):
+        c.cx(q, q + 1)
+    psi = sv.apply(n, *ir(c), None)
+    p = sv.marginal_probs(n, psi, [1, 3, 4])
+    np.testing.assert_allclose(p, [0.5, 0, 0, 0, 0, 0, 0, 0.5], atol=1e-15)
+
+
+def test_measure_bell_state_collapses():
+    c = Circuit(2).h(0).cx(0, 1)
+    for u, want in ((0.3, 0), (0.7, 1)):
+        psi = sv.apply(2, *ir(c), None)
+        out, prob, p0 = sv.measure_qubit(2, psi, 0, u)
+        assert out == want and abs(prob - 0.5) < 1e-15 and abs(p0 - 0.5) < 1e-15
+        ref = np.zeros(4, complex)
+        ref[3 * want] = 1.0
+        np.testing.assert_allclose(psi, ref, atol=1e-15)
+        out1, prob1, _ = sv.measure_qubit(2, psi, 1, 0.999)   # now certain
+        assert out1 == want and abs(prob1 - 1) < 1e-15
+
+
+def test_sequential_measurement_matches_joint_distribution():
+    """P(o_a) P(o_b | o_a) from two single-qubit measurements equals the joint
+    Born probability of (o_a, o_b); the post-measurement state has unit norm and
+    lives on the measured outcome."""
+    n = 6
+    psi0 = gen.random_state(n, seed=3)
+    joint = sv.marginal_probs(n, psi0, [4, 1])
+    for oa in (0, 1):
+        for ob in (0, 1):
+            psi = psi0.copy()
+            _, pa, _ = sv.measure_qubit(n, psi, 4, 0.0, forced=oa)
+            _, pb, _ = sv.measure_qubit(n, psi, 1, 0.0, forced=ob)
+            assert abs(pa * pb - joint[2 * oa + ob]) < 1e-14
+            assert abs(np.linalg.norm(psi) - 1) < 1e-14
+            m = sv.marginal_probs(n, psi, [4, 1])
+            assert abs(m[2 * oa + ob] - 1) < 1e-14
+
+
+# --------------------------------------------- MIPT trajectories, shadow snapshots
+def _pool_of(mats):
+    return np.ascontiguousarray(np.concatenate([m.reshape(-1) for m in mats]))
+
+
+def test_mipt_trajectory_without_measurement_is_the_circuit():
+    from oracle import trajectories as tr
+    b = gen.mipt_batch(6, 4, 2, 0.0, seed=2)
+    g, _ = b["circuit"].to_ir()
+    out = tr.mipt_trajectory(6, g, b["pools"][:, 1], b["masks"][:, 1], b["u"][:, 1])
+    assert np.all(out["outcomes"] == -1) and out["logp"] == 0.0
+    psi = sv.zero_state(6)
+    for t in range(4):
+        pool = np.empty(2 * b["pools"][t, 1].size)
+        pool[0::2], pool[1::2] = b["pools"][t, 1].real, b["pools"][t, 1].imag
+        psi = dense.run(6, g, pool, None, psi0=psi)
+    np.testing.assert_allclose(out["psi"], psi, atol=1e-12)
+
+
+def test_mipt_trajectory_closed_form_hadamard_steps():
+    """Even bonds H (x) I, odd bonds I: after each step qubits 0 and 2 of four are in
+    |+> (or re-measured basis states turned into |+>/|->), qubits 1 and 3 stay |0>;
+    measuring all four gives P = 1/2 for qubits 0, 2 (outcome u < 1/2 -> 0) and
+    certainty for 1, 3: log P = 2 log(1/2) per step."""
+    from oracle import trajectories as tr
+    n, D = 4, 3
+    Hm = np.array([[1, 1], [1, -1]]) / math.sqrt(2)
+    HI = np.kron(Hm, np.eye(2)).astype(np.complex128)
+    c = Circuit(n)
+    for i in (0, 2, 1):
+        c.unitary((i, i + 1), np.eye(4, dtype=np.complex128))
+    g, _ = ir(c)
+    pools = [_pool_of([HI, HI, np.eye(4, dtype=np.complex128)]) for _ in range(D)]
+    u = np.array([[0.2, 0.9, 0.7, 0.1], [0.6, 0.3, 0.4, 0.8], [0.49, 0.5, 0.51, 0.0]])
+    out = tr.mipt_trajectory(n, g, pools, [0b1111] * D, u)
+    for t in range(D):
+        assert out["outcomes"][t, 0] == (0 if u[t, 0] < 0.5 else 1)
+        assert out["outcomes"][t, 2] == (0 if u[t, 2] < 0.5 else 1)
+        assert out["outcomes"][t, 1] == 0 and out["outcomes"][t, 3] == 0
+        np.testing.assert_allclose(out["p0"][t], [0.5, 1.0, 0.5, 1.0], atol=1e-15)
+    assert abs(out["logp"] - 2 * D * math.log(0.5)) < 1e-12
+    ref = np.zeros(16, complex)
+    ref[out["outcomes"][-1, 0] | (out["outcomes"][-1, 2] << 2)] = 1.0
+    np.testing.assert_allclose(out["psi"], ref, atol=1e-15)
+
+
+def test_shadow_basis_change_measures_the_right_basis():
+    """X basis on |+>/|->, Y basis on |+i>/|-i>, Z basis on |0>/|1> give certain
+    outcomes 0/1."""
+    from oracle import trajectories as tr
+    n = 6
+    prep = Circuit(n)
+    prep.h(0).x(1).h(1)                      # |+>, |->
+    prep.rx(2, angle=-math.pi / 2)           # |+i>
+    prep.x(3).rx(3, angle=-math.pi / 2)      # |-i> (up to phase)
+    prep.x(5)                                # qubit 4 |0>, qubit 5 |1>
+    psi = sv.apply(n, *ir(prep), None)
+    out, p0, _ = tr.shadow_snapshot(n, psi, [1, 1, 2, 2, 3, 3], np.full(n, 0.5))
+    np.testing.assert_array_equal(out, [0, 1, 0, 1, 0, 1])
+    np.testing.assert_allclose(p0, [1, 0, 1, 0, 1, 0], atol=1e-14)
+
+
+def test_shadow_outcome_statistics_match_pauli_expectations():
+    """For each basis the outcome probabilities are (1 +- <P_q>)/2 with P_q the
+    basis Pauli: P(0) - P(1) on qubit q equals <X_q>, <Y_q> or <Z_q>."""
+    from oracle import trajectories as tr
+    n = 5
+    psi0 = gen.random_state(n, seed=8)
+    for b, name in ((1, "X"), (2, "Y"), (3, "Z")):
+        g, p = tr.basis_change(n, [b] * n)
+        phi = sv.apply(n, g, p, None, psi=psi0)
+        for q in range(n):
+            pz = sv.marginal_probs(n, phi, [q])
+            ev = sv.expect(n, psi0, pauli_terms([{q: name}]))[0].real
+            assert abs((pz[0] - pz[1]) - ev) < 1e-13
+
+
+def test_mipt_generator_draws_like_sequential_haar():
+    rng = np.random.default_rng(11)
+    seq = np.array([[gen.haar_su4(rng) for _ in range(3)] for _ in range(2)])
+    stack = gen.haar_su4_stack(np.random.default_rng(11), (2, 3))
+    np.testing.assert_array_equal(seq, stack)
+    for U in stack.reshape(-1, 4, 4):
+        np.testing.assert_allclose(U.conj().T @ U, np.eye(4), atol=1e-14)
+        assert abs(np.linalg.det(U) - 1) < 1e-13

@@ -93,6 +93,56 @@ def su4_brickwork(n: int, depth: int, rot: str = "RX", seed: int = 0):
     return c, theta.reshape(-1).copy()
 
 
+def cut_brickwork(n: int, depth: int, block: int, rot: str = "RZ", seed: int = 0):
+    """``su4_brickwork(n, depth, rot, seed)`` without the SU(4) gates on the bonds
+    that cross a multiple of ``block`` ((block-1, block), (2 block-1, 2 block), ...).
+
+    Every other gate, matrix and angle is the one ``su4_brickwork`` draws for the
+    same seed, so the circuit keeps the full workload's layer structure while its
+    state stays the tensor product of n/block independent block circuits (see
+    ``block_circuit``).  Returns (Circuit, theta flat).
+    """
+    c, theta = su4_brickwork(n, depth, rot, seed)
+    out = Circuit(n)
+    for (name, qubits, param, scale, angle0, mat) in c.ops:
+        if len(qubits) == 2 and min(qubits) // block != max(qubits) // block:
+            continue
+        out.add(name, qubits, param=param, scale=scale, angle0=angle0, matrix=mat)
+    out.n_params = c.n_params
+    return out, theta
+
+
+def block_circuit(c: Circuit, lo: int, nq: int) -> Circuit:
+    """The ops of ``c`` acting only inside qubits lo..lo+nq-1, moved to qubits 0..nq-1
+    (params keep their indices)."""
+    out = Circuit(nq)
+    for (name, qubits, param, scale, angle0, mat) in c.ops:
+        if all(lo <= q < lo + nq for q in qubits):
+            out.add(name, tuple(q - lo for q in qubits), param=param, scale=scale,
+                    angle0=angle0, matrix=mat)
+    out.n_params = c.n_params
+    return out
+
+
+def inverse_circuit(c: Circuit) -> Circuit:
+    """The circuit U^dagger: ops in reverse order, rotation angles negated, explicit
+    matrices conjugate-transposed, S and T replaced by their inverses."""
+    inv = Circuit(c.n)
+    for (name, qubits, param, scale, angle0, mat) in reversed(c.ops):
+        if name in ("RX", "RY", "RZ", "RZZ", "CP"):
+            inv.add(name, qubits, param=param, scale=-scale, angle0=-angle0)
+        elif name in ("U1", "U2", "UK"):
+            inv.unitary(qubits, mat.conj().T)
+        elif name == "S":
+            inv.unitary(qubits, np.diag([1, -1j]))
+        elif name == "T":
+            inv.unitary(qubits, np.diag([1, np.exp(-1j * math.pi / 4)]))
+        else:
+            inv.add(name, qubits)
+    inv.n_params = c.n_params
+    return inv
+
+
 def slice_circuit(c: Circuit, nq: int) -> Circuit:
     """Drop every op whose support is not inside {0..nq-1}; params keep indices."""
     out = Circuit(nq)
@@ -101,6 +151,21 @@ def slice_circuit(c: Circuit, nq: int) -> Circuit:
             out.add(name, qubits, param=param, scale=scale, angle0=angle0, matrix=mat)
     out.n_params = c.n_params
     return out
+
+
+def qml_brickwall(n: int, layers: int, seed: int = 0):
+    """The QML ansatz of Sec. VII.B: per layer one SU(4) on every even pair
+    (0,1), (2,3), ... then on every odd pair (1,2), (3,4), ...; each gate a Haar
+    SU(4) matrix (``haar_su4``) drawn in gate order (the trained weights are
+    replaced by random gates; the gate count is 15 parameters per gate in the
+    paper: layers * (n - 1) * 15).  No parameters: one circuit for the whole batch.
+    """
+    rng = np.random.default_rng(seed)
+    c = Circuit(n)
+    for _ in range(layers):
+        for i in list(range(0, n - 1, 2)) + list(range(1, n - 1, 2)):
+            c.unitary((i, i + 1), haar_su4(rng))
+    return c
 
 
 def hea_ring(n: int, layers: int = 12):
@@ -127,12 +192,12 @@ def random_circuit(n: int, n_ops: int, seed: int = 0, kinds=None):
     """Random mix of every op kind on random qubits (test input)."""
     rng = np.random.default_rng(seed)
     kinds = kinds or ["X", "Y", "Z", "H", "S", "T", "RX", "RY", "RZ", "CX", "CZ",
-                      "CP", "SWAP", "RZZ", "U1", "U2", "U3", "U4"]
+                      "CP", "SWAP", "RZZ", "U1", "U2", "U3", "U4", "U5"]
     c = Circuit(n)
     p = 0
     for _ in range(n_ops):
         k = kinds[int(rng.integers(len(kinds)))]
-        if k in ("U3", "U4") and n < int(k[1]):
+        if k in ("U3", "U4", "U5") and n < int(k[1]):
             k = "U2"
         if k in ("CX", "CZ", "CP", "SWAP", "RZZ", "U2") and n < 2:
             k = "RX"
@@ -246,6 +311,85 @@ def ragged_sizes(batch: int, choices=(12, 14, 16, 18, 20), seed: int = 0) -> np.
     """n_b drawn uniformly from ``choices`` (rng.integers index draw)."""
     rng = np.random.default_rng(seed)
     return np.asarray(choices)[rng.integers(0, len(choices), batch)]
+
+
+def ragged_vqe_batch(batch: int, layers: int = 12, choices=(12, 14, 16, 18, 20),
+                     seed_sizes: int = 0, seed_values: int = 1):
+    """Ragged batched-VQE input: item b is a TFIM chain of n_b qubits on the ring
+    ansatz with ``layers`` layers.
+
+    n_b = ``ragged_sizes(batch, choices, seed_sizes)``.  One structure per distinct n
+    (ascending n): dict(n, gates, pool, P, terms) with the open-chain TFIM terms.
+    Then with ``default_rng(seed_values)``: per item in order theta_b =
+    uniform(-pi, pi, P_b); then per item coefficients (-J_1..-J_{n-1}, -g x n) with
+    J_i, g drawn together as uniform(0.5, 1.5, 2n-1) (one value per term).
+    Returns (problems, item_problem, theta flat, coeffs flat, sizes).
+    """
+    ns = ragged_sizes(batch, choices, seed=seed_sizes)
+    problems, index = [], {}
+    for n in sorted(set(int(x) for x in ns)):
+        c = hea_ring(n, layers)
+        g, p = c.to_ir()
+        index[n] = len(problems)
+        problems.append(dict(n=n, gates=g, pool=p, P=c.n_params, terms=tfim_terms(n, 1.0, 1.0)))
+    item_problem = [index[int(x)] for x in ns]
+    rng = np.random.default_rng(seed_values)
+    theta = np.concatenate([rng.uniform(-math.pi, math.pi, problems[s]["P"]) for s in item_problem])
+    coeffs = np.concatenate([-rng.uniform(0.5, 1.5, 2 * problems[s]["n"] - 1) for s in item_problem])
+    return problems, item_problem, theta, coeffs, ns
+
+
+def haar_su4_stack(rng: np.random.Generator, shape) -> np.ndarray:
+    """Haar SU(4) matrices of ``shape`` in C order, by the ``haar_su4`` recipe in
+    one vectorised draw: standard_normal(shape + (2, 4, 4)) gives the same A, B
+    per matrix as consecutive ``haar_su4`` calls."""
+    g = rng.standard_normal(tuple(shape) + (2, 4, 4))
+    z = (g[..., 0, :, :] + 1j * g[..., 1, :, :]) / math.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    d = np.diagonal(r, axis1=-2, axis2=-1)
+    q = q * (d / np.abs(d))[..., None, :]
+    det = np.linalg.det(q)
+    return q / np.power(det, 0.25)[..., None, None]
+
+
+def mipt_batch(n: int, depth: int, batch: int, p: float, seed: int = 0):
+    """Measurement-induced phase transition trajectories (Sec. VII.C).
+
+    Time step t of trajectory b: an independent Haar SU(4) on every even bond
+    (0,1), (2,3), ..., then on every odd bond (1,2), (3,4), ...; then each qubit
+    is measured in the Z basis with probability p.  Draw order:
+    Haar matrices for all (b, t, gate) (``haar_su4_stack``), then
+    meas = rng.random((batch, depth, n)) < p, then u = rng.random((batch, depth, n))
+    (the Born-rule uniform of each (b, t, q)).
+    Returns dict(circuit: the gates of one time step with mat_off 16 g,
+    pools complex128 [depth][batch][16 G] (gate g of step t of item b at
+    pools[t, b, 16 g:16 g + 16], row-major 4x4), masks uint64 [depth][batch],
+    u float64 [depth][batch][n]).
+    """
+    rng = np.random.default_rng(seed)
+    bonds = list(range(0, n - 1, 2)) + list(range(1, n - 1, 2))
+    G = len(bonds)
+    mats = haar_su4_stack(rng, (batch, depth, G))
+    meas = rng.random((batch, depth, n)) < p
+    u = rng.random((batch, depth, n))
+    c = Circuit(n)
+    for i in bonds:
+        c.unitary((i, i + 1), np.eye(4, dtype=np.complex128))
+    pools = np.ascontiguousarray(mats.transpose(1, 0, 2, 3, 4).reshape(depth, batch, 16 * G))
+    masks = (meas.astype(np.uint64) << np.arange(n, dtype=np.uint64)).sum(axis=2, dtype=np.uint64)
+    return dict(n=n, depth=depth, batch=batch, p=p, circuit=c, pools=pools,
+                masks=np.ascontiguousarray(masks.T), u=np.ascontiguousarray(u.transpose(1, 0, 2)))
+
+
+def shadow_bases(snapshots: int, n: int, seed: int = 0):
+    """Random Pauli measurement bases and Born uniforms of classical-shadow
+    snapshots (Sec. VII.A): bases = rng.integers(1, 4, (snapshots, n)) with
+    1 = X, 2 = Y, 3 = Z (the paper's pauli_strings), then
+    u = rng.random((snapshots, n))."""
+    rng = np.random.default_rng(seed)
+    bases = rng.integers(1, 4, size=(snapshots, n))
+    u = rng.random((snapshots, n))
+    return bases, u
 
 
 def warmstart_chains(count: int, n_min: int = 14, n_max: int = 20, seed: int = 0):
