@@ -310,6 +310,8 @@ def run_gpu(args):
     torch.cuda.empty_cache()
     if not args.no_vqe:
         out["vqe"] = vqe_bench(args, dev, dist, world)
+    if not args.no_apps:
+        out["apps"] = apps_bench(args, dev, dist, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         moved, times, cores = oracle_sample(3, 4)
         v = moved * len(times) / sum(times) / 1e9
@@ -410,6 +412,133 @@ def vqe_bench(args, dev, dist, world):
     return res
 
 
+def tf32_peak():
+    """TF32 dense peak: the measured bf16 peak x the nominal TF32/BF16 ratio (1.1/2.25)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 x 1.1/2.25"
+    except Exception:
+        return 1800.0 * 1.1 / 2.25, "fallback bf16 x 1.1/2.25"
+
+
+def timed(fn, steps, warmup, dist, dev):
+    """Mean ms per call of fn() over `steps` calls (CUDA events, after warm-up)."""
+    import torch
+    for _ in range(max(3, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return max_over_ranks(e0.elapsed_time(e1) / steps, dist, dev)
+
+
+def plan_stages(n, gates, pool):
+    """Passes and register stages of a gate list's plan (from tcng_describe_plan)."""
+    from paper_2602_14167_b300 import tcng as T
+    head = T.tcng_describe_plan(n, gates, pool, 0, False).split("\n")[0]
+    f = dict(kv.split("=") for kv in head.split() if "=" in kv)
+    return int(f["passes"]), int(f["stages"])
+
+
+def apps_bench(args, dev, dist, world):
+    """The paper's batched applications on the same kernels (Sec. VII):
+    QML forward batches (12 q x 30 SU(4) brickwall layers x 5000 inputs; 10 q x 40
+    x 15000), MIPT trajectories (N=20, D=40, batch 1000, p=0.2) and classical-shadow
+    snapshots (256 of a 20-qubit state).  Inputs are synthetic (amplitude-encoded
+    random vectors stand in for CIFAR-100/MNIST)."""
+    import torch
+    from paper_2602_14167_b300 import StateBatch
+    from paper_2602_14167_b300 import tcng as T
+    from paper_2602_14167_b300.trajectories import MIPTBatch, shadow_snapshots
+
+    res = {}
+    tf32, tf32_kind = tf32_peak()
+    hbm, hbm_kind = peaks()
+    for (n, L, B) in ((12, 30, 5000), (10, 40, 15000)):
+        c = gen.qml_brickwall(n, L, seed=0)
+        g, p = c.to_ir()
+        x = torch.tensor(gen.amplitude_encoded_batch(B, n, seed=1), dtype=torch.complex64, device=dev)
+        st = StateBatch(n, batch=B, dtype="c64", device=dev)
+        probs = torch.empty((B, 128), dtype=torch.float64, device=dev)
+        view = st.batch_view()
+
+        def step():
+            view.copy_(x)
+            T.tcng_apply_circuit(st.handle, g, p, None, 0)
+            T.tcng_marginal_probs(st.handle, list(range(7)), probs)
+
+        ms = timed(step, args.steps, args.warmup, dist, dev)
+        T.tcng_profile_enable(True)
+        T.tcng_profile_read(reset=True)
+        step()
+        prof = T.tcng_profile_read(reset=True)
+        T.tcng_profile_enable(False)
+        passes, stages = plan_stages(13, g, p)
+        amps = B << n
+        gates_total = len(g)
+        tcs = prof.get("pass_tcs_kernel_c64", (0, 0.0))
+        executed = stages * amps * 128.0 * 3      # 16x16 complex stage = 128 real flops/amplitude, 3-term split
+        algorithmic = gates_total * amps * 32.0   # one 4x4 complex matvec per 4 amplitudes per gate
+        res[f"qml_n{n}_L{L}_b{B}"] = {
+            "samples_per_s": world * B / (ms * 1e-3), "ms_per_batch": ms,
+            "params_paper": L * (n - 1) * 15, "su4_gates": gates_total,
+            "tile_passes": passes, "register_stages": stages,
+            "pass_tcs_ms": tcs[1], "pass_tcs_launches": tcs[0],
+            "tensor_tflops_executed": executed / (tcs[1] * 1e-3) / 1e12 if tcs[1] else None,
+            "tensor_peak_tflops": tf32, "tensor_peak_kind": tf32_kind,
+            "tensor_frac": executed / (tcs[1] * 1e-3) / 1e12 / tf32 if tcs[1] else None,
+            "algorithmic_gflop_per_batch": algorithmic / 1e9,
+            "hbm_gbs_tile_passes": passes * 2 * 8 * amps / (tcs[1] * 1e-3) / 1e9 if tcs[1] else None,
+            "hbm_peak": hbm,
+            "kernel_ms": {k: [v[0], v[1]] for k, v in prof.items()},
+            "paper_context": "RTX 5090 training epochs 1.88 s (MNIST 60k) / 4.60 s (CIFAR-100 50k), "
+                             "forward+backward; this line is forward + readout only"}
+        st.free()
+        del x, view, probs
+        torch.cuda.empty_cache()
+
+    # MIPT trajectories
+    n, D, B, pm = 20, 40, 1000, 0.2
+    b = gen.mipt_batch(n, D, B, pm, seed=0)
+    g, _ = b["circuit"].to_ir()
+    rep = np.empty(2 * b["pools"][0, 0].size)
+    rep[0::2], rep[1::2] = b["pools"][0, 0].real, b["pools"][0, 0].imag
+    pools = torch.tensor(b["pools"], dtype=torch.complex128, device=dev)
+    masks = torch.tensor(b["masks"].astype(np.int64), device=dev)
+    u = torch.tensor(b["u"], dtype=torch.float64, device=dev)
+    mb = MIPTBatch(n, B, device=dev)
+    ms = timed(lambda: mb.run(g, rep, pools, masks, u), max(1, args.steps // 2), 3, dist, dev)
+    res[f"mipt_n{n}_d{D}_b{B}"] = {
+        "trajectories_per_s": world * B / (ms * 1e-3), "ms_per_batch": ms, "ms_per_trajectory": ms / B,
+        "p": pm, "measurements_per_batch": int(np.unpackbits(b["masks"].view(np.uint8)).sum()),
+        "paper_context": "84.16 s per 1000 trajectories (0.084 s each) on one H200, complex64"}
+    mb.state.free()
+    del pools, masks, u, mb
+    torch.cuda.empty_cache()
+
+    # classical-shadow snapshots
+    n, S = 20, 256
+    c, th = gen.su4_brickwork(n, 6, "RZ", seed=n)
+    g, p = c.to_ir()
+    st = StateBatch(n, dtype="c64", device=dev)
+    st.apply(g, p, torch.tensor(th.reshape(1, -1), device=dev))
+    bases, uu = gen.shadow_bases(S, n, seed=3)
+    ud = torch.tensor(uu, device=dev)
+    psi = st.amplitudes(0)
+    ms = timed(lambda: shadow_snapshots(psi, bases, ud), args.steps, args.warmup, dist, dev)
+    res[f"shadows_n{n}_s{S}"] = {"snapshots_per_s": world * S / (ms * 1e-3), "ms_per_256": ms,
+                                 "paper_context": "0.29 s for 256 snapshots of 20 qubits on an RTX 5090"}
+    st.free()
+    torch.cuda.empty_cache()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,6 +548,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-vqe", action="store_true", help="skip the batched VQE measurement")
     ap.add_argument("--vqe-only", action="store_true", help="only the n=16 batched VQE (profiling)")
+    ap.add_argument("--no-apps", action="store_true", help="skip the QML / MIPT / shadow measurements")
+    ap.add_argument("--apps-only", action="store_true", help="only the QML / MIPT / shadow measurements")
     ap.add_argument("--fuse-width", type=int, default=0, help="override the fusion width (tuning)")
     ap.add_argument("--tile-bits", type=int, default=0, help="override the tile bits (tuning)")
     ap.add_argument("--chunk-bits", type=int, default=0, help="override the chunk bits (tuning)")
@@ -434,6 +565,12 @@ def main():
         return run_reference(args)
     if args.vqe_only:
         return run_vqe_only(args)
+    if args.apps_only:
+        import torch
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"apps": apps_bench(args, dev, None, 1)}))
+        return 0
     return run_gpu(args)
 
 
