@@ -12,7 +12,7 @@
  *
  * Conventions
  *   - qubit q is bit q of the amplitude index (little-endian);
- *   - R_P(t) = exp(-i t P / 2) for RX, RY, RZ, RZZ; CP(phi) = diag(1,1,1,e^{i phi});
+ *   - R_P(t) = exp(-i t P / 2) for RX, RY, RZ, RZZ and RP; CP(phi) = diag(1,1,1,e^{i phi});
  *   - a gate's angle is angle0 + scale * params[item][param] (param < 0: angle0);
  *   - the local index of a k-qubit gate matrix is sum_j bit(q[j]) << (k-1-j);
  *   - complex64 states are interleaved float2, complex128 states double2;
@@ -54,7 +54,9 @@ typedef enum { TCNG_C64 = 0, TCNG_C128 = 1 } tcng_dtype;
 typedef enum {
     TCNG_I = 0, TCNG_X, TCNG_Y, TCNG_Z, TCNG_H, TCNG_S, TCNG_T,
     TCNG_RX, TCNG_RY, TCNG_RZ, TCNG_CX, TCNG_CZ, TCNG_CP, TCNG_SWAP, TCNG_RZZ,
-    TCNG_U1, TCNG_U2, TCNG_UK
+    TCNG_U1, TCNG_U2, TCNG_UK,
+    TCNG_RP     /* exp(-i t P / 2) for a Pauli word P on nq = 1..5 qubits: factor j on q[j]
+                   is digit j of mat_off (bits 2j, 2j+1; 0 I, 1 X, 2 Y, 3 Z) */
 } tcng_op;
 
 /* One gate of the flat gate-list IR (56 bytes).  U1/U2/UK read a row-major
@@ -224,8 +226,11 @@ tcng_status tcng_hamiltonian_apply(const tcng_state* st, const tcng_pauli* terms
  * (replaces the paper's reverse-mode AD through the tensor network, Sec. I.B
  * "Paradigms: AD"; cost independent of the number of parameters, O(1) states).
  *   st          batch of states (all items the same n); used as scratch for psi;
- *   ops/mat     gate list as in tcng_apply_circuit; parameterised gates must
- *               be RX, RY, RZ, RZZ or CP;
+ *   ops/mat     gate list as in tcng_apply_circuit; parameterised gates may be
+ *               RX, RY, RZ, RZZ, CP or RP (RP, and states of at least
+ *               TCNG_OPT_STATE_ADJOINT_N qubits, take the state-pass adjoint:
+ *               items one after another, a parameterised RP on at most 2
+ *               qubits; a scratch copy of one item's state is allocated);
  *   params_dev  device double [batch][P];
  *   H, n_terms  Pauli strings; coeffs_dev device double [batch][n_terms] or NULL;
  *   energy_dev  device double [batch];
@@ -390,20 +395,47 @@ typedef enum {
                                   (TF32 hi/lo split, ~1e-6 relative error per circuit):
                                   0 off, 1 on, 2 auto (default): on when all items share one
                                   parameter set and the state spans at least one 2^13-amplitude
-                                  tile per SM, or spans 32 tiles per SM */
+                                  tile per SM, or spans 32 tiles per SM */,
+    TCNG_OPT_STATE_ADJOINT_N = 6  /* tcng_energy_grad runs the state-pass adjoint (one pass over
+                                  psi and lambda per block of <= 2 qubits, all of a block's
+                                  parameters from one cross-density matrix) for states of at
+                                  least this many qubits (default 21; 1..35), and always for
+                                  circuits with RP parameters; smaller states use the
+                                  per-item persistent kernel */
 } tcng_option;
 
 tcng_status tcng_set_option(tcng_option opt, int value);
 tcng_status tcng_get_option(tcng_option opt, int* value);
 
 /*
- * tcng_autotune -- time candidate (fusion width, tile bits, chunk bits) on a
- * synthetic brickwork circuit of n qubits (CUDA events, device synchronised),
- * set the best as the current options and append it to cache_path (NULL: no
- * file).  If cache_path already holds an entry for (n, dt, batch) it is loaded
- * without timing.  Errors: EINVAL, ENOMEM, ECUDA.
+ * tcng_autotune -- choose the options of the fused apply path by timing every
+ * candidate (fusion width 1..5; tensor-core stages off/on for complex64; tile
+ * bits tmax-1 and tmax; chunk bits 5 and 7) with CUDA events on a synthetic
+ * SU(4)-like brickwork of n qubits applied to `batch` states of type dt (one
+ * untimed call per candidate builds its plan, two are timed).  The fastest
+ * becomes the current option set and is appended to cache_path (NULL: no file)
+ * as "n dt batch fuse_width tile_bits chunk_bits tensor_cores ms"; a cached
+ * line for (n, dt, batch) is loaded without timing.  Synchronises the device.
+ * Errors: EINVAL, ENOMEM, ECUDA.
  */
 tcng_status tcng_autotune(int n, tcng_dtype dt, int batch, const char* cache_path);
+
+/*
+ * tcng_autotune_circuit -- the same search on the caller's own circuit and
+ * state (the state's amplitudes are overwritten: it serves as scratch); the
+ * cache key is the circuit's structure hash (with dt and the batch size).
+ *   best_ms   host double, the best candidate's time per call (may be NULL;
+ *             untouched when the choice comes from the cache).
+ * Errors: EINVAL, EUNSUPPORTED (ragged state), ENOMEM, ECUDA.
+ */
+tcng_status tcng_autotune_circuit(tcng_state* st, const tcng_gate* ops, size_t n_ops,
+                                  const double* mat_pool, size_t n_mat, const void* params_dev, int P,
+                                  const char* cache_path, double* best_ms);
+
+/* The last autotune run as text: one line "fuse_width tile_bits chunk_bits
+ * tensor_cores ms" per candidate (ms < 0: the candidate failed), or "cached
+ * <cache line>" when the choice was loaded.  NUL-terminated, truncated to len. */
+tcng_status tcng_autotune_report(char* buf, size_t len);
 
 /* Synchronise the device and report a device-side error word (ETIMEOUT) if set. */
 tcng_status tcng_sync_status(void);

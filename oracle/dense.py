@@ -25,7 +25,7 @@ P0 = (I2 + PZ) / 2          # |0><0|
 P1 = (I2 - PZ) / 2          # |1><1|
 
 OPN = {0: "I", 1: "X", 2: "Y", 3: "Z", 4: "H", 5: "S", 6: "T", 7: "RX", 8: "RY", 9: "RZ",
-       10: "CX", 11: "CZ", 12: "CP", 13: "SWAP", 14: "RZZ", 15: "U1", 16: "U2", 17: "UK"}
+       10: "CX", 11: "CZ", 12: "CP", 13: "SWAP", 14: "RZZ", 15: "U1", 16: "U2", 17: "UK", 18: "RP"}
 
 
 def embed(n: int, factors: dict) -> np.ndarray:
@@ -61,7 +61,7 @@ def embed_matrix(n: int, qubits, U: np.ndarray) -> np.ndarray:
 def gate_operator(n: int, g, pool, params) -> np.ndarray:
     """Full 2^n operator of one IR record, built from generators/projectors."""
     name = OPN[int(g["op"])]
-    k = int(g["nq"]) if name == "UK" else (2 if name in ("CX", "CZ", "CP", "SWAP", "RZZ", "U2") else 1)
+    k = int(g["nq"]) if name in ("UK", "RP") else (2 if name in ("CX", "CZ", "CP", "SWAP", "RZZ", "U2") else 1)
     q = [int(v) for v in g["q"][:k]]
     ang = float(g["angle0"])
     if int(g["param"]) >= 0:
@@ -96,6 +96,11 @@ def gate_operator(n: int, g, pool, params) -> np.ndarray:
                       + embed(n, {q[0]: PY, q[1]: PY}) + embed(n, {q[0]: PZ, q[1]: PZ}))
     if name == "RZZ":
         return expm(-0.5j * ang * embed(n, {q[0]: PZ, q[1]: PZ}))
+    if name == "RP":   # exp(-i ang P / 2), P = (x)_j sigma_{word digit j} on q[j]
+        word = int(g["mat_off"])
+        paulis = [I2, PX, PY, PZ]
+        P = embed(n, {q[j]: paulis[(word >> (2 * j)) & 3] for j in range(k)})
+        return expm(-0.5j * ang * P)
     off = int(g["mat_off"])
     d = 1 << k
     flat = pool[2 * off: 2 * (off + d * d)]

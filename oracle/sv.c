@@ -21,7 +21,8 @@
  *   - Born probabilities of a subset of qubits (the QML readout of Sec. VII.B)
  *     and single-qubit projective measurements (the MIPT trajectories of
  *     Sec. VII.C, the shadow snapshots of Sec. VII.A).
- * Gate conventions: R_P(t) = exp(-i t P / 2); 2-qubit local index
+ * Gate conventions: R_P(t) = exp(-i t P / 2) (RX, RY, RZ, RZZ, and RP for any
+ * Pauli word P on 1..5 qubits, word digit j = 2 bits of mat_off, 0 I, 1 X, 2 Y, 3 Z); 2-qubit local index
  * r = 2*bit(q[0]) + bit(q[1]); CX(control, target); CP(phi) = diag(1,1,1,e^{i phi}).
  */
 #include <complex.h>
@@ -49,7 +50,7 @@ typedef struct {
 
 enum {
     O_I = 0, O_X, O_Y, O_Z, O_H, O_S, O_T, O_RX, O_RY, O_RZ,
-    O_CX, O_CZ, O_CP, O_SWAP, O_RZZ, O_U1, O_U2, O_UK
+    O_CX, O_CZ, O_CP, O_SWAP, O_RZZ, O_U1, O_U2, O_UK, O_RP
 };
 
 #define OK 0
@@ -62,7 +63,7 @@ static int op_qubits(const og_gate* g) {
         return 1;
     case O_CX: case O_CZ: case O_CP: case O_SWAP: case O_RZZ: case O_U2:
         return 2;
-    case O_UK:
+    case O_UK: case O_RP:
         return g->nq;
     default:
         return -1;
@@ -114,6 +115,22 @@ static int gate_matrix(const og_gate* g, const double* pool, const double* param
         th = gate_angle(g, params, extra);
         M[0] = cexp(-I * th / 2); M[5] = cexp(I * th / 2);
         M[10] = cexp(I * th / 2); M[15] = cexp(-I * th / 2); break;
+    case O_RP: {  /* exp(-i th P / 2), P = sigma_{w_0} (x) ... (x) sigma_{w_{k-1}}, q[0] first */
+        th = gate_angle(g, params, extra); c = cos(th / 2); s = sin(th / 2);
+        /* P[r][col] = prod_j sigma_{w_j}[bit_j(r)][bit_j(col)], bit_j = bit k-1-j */
+        static const double complex sig[4][2][2] = {
+            {{1, 0}, {0, 1}}, {{0, 1}, {1, 0}}, {{0, -I}, {I, 0}}, {{1, 0}, {0, -1}}};
+        for (int r = 0; r < d; ++r)
+            for (int col = 0; col < d; ++col) {
+                cx pv = 1.0;
+                for (int j = 0; j < k; ++j) {
+                    const int w = (int)((g->mat_off >> (2 * j)) & 3);
+                    pv *= sig[w][(r >> (k - 1 - j)) & 1][(col >> (k - 1 - j)) & 1];
+                }
+                M[r * d + col] = (r == col ? c : 0.0) - I * s * pv;
+            }
+        break;
+    }
     case O_U1: case O_U2: case O_UK:
         if (g->mat_off < 0) return EBAD;
         for (int i = 0; i < d * d; ++i)
@@ -162,6 +179,7 @@ static int check_gate(int n, const og_gate* g, int P, int64_t n_mat) {
             if (g->q[i] == g->q[j]) return EBAD;
     }
     if (g->param >= P) return EBAD;
+    if (g->op == O_RP && (g->mat_off < 0 || g->mat_off >= (1LL << (2 * k)))) return EBAD;
     if ((g->op == O_U1 || g->op == O_U2 || g->op == O_UK) &&
         (g->mat_off < 0 || g->mat_off + (1LL << (2 * k)) > n_mat))
         return EBAD;
@@ -290,7 +308,7 @@ int orc_energy(int n, const og_gate* ops, int64_t n_ops, const double* pool, int
 }
 
 static int shiftable(int op) {
-    return op == O_RX || op == O_RY || op == O_RZ || op == O_RZZ || op == O_CP;
+    return op == O_RX || op == O_RY || op == O_RZ || op == O_RZZ || op == O_CP || op == O_RP;
 }
 
 /*

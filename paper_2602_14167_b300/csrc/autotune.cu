@@ -1,15 +1,23 @@
-// Autotuner: choose fusion width, tile bits and chunk bits for the tile passes.
+// Autotuner: choose the fusion width k, tile bits, chunk bits and the
+// tensor-core switch for the tile passes (the knobs of the fused apply path).
 //
-// Candidates are timed with CUDA events on a synthetic brickwork of n qubits
-// (dense 2-qubit blocks built from RY/RZ/CX gates with fixed angles, plus an RZ
-// layer, the shape of the paper's SU(4) brickwork circuits) applied to `batch`
-// states of the requested dtype.  The best candidate becomes the process-wide
-// option set and is appended to cache_path as one line
-//   "n dtype batch fuse_width tile_bits chunk_bits ms".
+// Every candidate (k in 1..5; tensor-core register stages off/on for complex64;
+// tile bits tmax-1, tmax; chunk bits 5, 7) is timed with CUDA events on the
+// circuit to be run -- tcng_autotune_circuit -- or on a synthetic brickwork of
+// n qubits (dense 2-qubit blocks from RY/RZ/CX gates plus an RZ layer, the shape
+// of the paper's SU(4) brickwork circuits) -- tcng_autotune.  One untimed call
+// builds the candidate's plan, then two calls are timed.  The fastest candidate
+// becomes the process-wide option set and is appended to cache_path as one line
+//   "key dtype batch fuse_width tile_bits chunk_bits tensor_cores ms"
+// (key = n for the synthetic circuit, the circuit's structure hash otherwise);
+// a later call with the same key, dtype and batch loads it without timing.
+// tcng_autotune_report returns every timed candidate of the last run.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <fstream>
 #include <sstream>
 #include <string>
@@ -19,7 +27,9 @@
 
 using namespace tcng;
 
-static std::vector<tcng_gate> synthetic_brickwork(int n, int depth) {
+namespace {
+
+std::vector<tcng_gate> synthetic_brickwork(int n, int depth) {
     std::vector<tcng_gate> g;
     auto add = [&](int op, int nq, int q0, int q1, double ang) {
         tcng_gate x{};
@@ -48,80 +58,148 @@ static std::vector<tcng_gate> synthetic_brickwork(int n, int depth) {
     return g;
 }
 
+struct Cand {
+    int fw, tb, cb, tc;
+    double ms;   // < 0: failed
+};
+
+std::mutex g_report_mu;
+std::string g_report;   // last run, one candidate per line
+
+bool load_cached(const char* path, unsigned long long key, int dt, int batch) {
+    if (!path) return false;
+    std::ifstream in(path);
+    std::string line;
+    while (std::getline(in, line)) {
+        std::istringstream ss(line);
+        unsigned long long k;
+        int cd, cb, fw, tb, cbits, tc;
+        double ms;
+        if (ss >> k >> cd >> cb >> fw >> tb >> cbits >> tc >> ms && k == key && cd == dt && cb == batch) {
+            std::lock_guard<std::mutex> lk(g_mu);
+            g_opt.fuse_width = fw;
+            g_opt.tile_bits = tb;
+            g_opt.chunk_bits = cbits;
+            g_opt.tensor_cores = tc;
+            std::lock_guard<std::mutex> lr(g_report_mu);
+            g_report = "cached " + line + "\n";
+            return true;
+        }
+    }
+    return false;
+}
+
+// Time every candidate on (st, ops); set and cache the best.
+tcng_status tune(tcng_state* st, const tcng_gate* ops, size_t n_ops, const double* pool, size_t n_mat,
+                 const void* params, int P, unsigned long long key, const char* cache_path, double* best_ms) {
+    const Options saved = g_opt;
+    const int tmax = st->dt == TCNG_C64 ? 13 : 12;
+    std::vector<Cand> cands;
+    for (int fw = 1; fw <= TCNG_MAX_FUSE; ++fw)
+        for (int tc = 0; tc <= (st->dt == TCNG_C64 ? 1 : 0); ++tc)
+            for (int tb = tmax - 1; tb <= tmax; ++tb)
+                for (int cb : {5, 7}) cands.push_back({fw, tb, cb, tc, -1.0});
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = -1;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        Cand& c = cands[i];
+        {
+            std::lock_guard<std::mutex> lk(g_mu);
+            g_opt = saved;
+            g_opt.fuse_width = c.fw;
+            g_opt.tile_bits = c.tb;
+            g_opt.chunk_bits = c.cb;
+            g_opt.tensor_cores = c.tc;
+            g_opt.unfused = 0;
+            g_opt.use_graphs = 0;
+        }
+        if (tcng_apply_circuit(st, ops, n_ops, pool, n_mat, params, P, nullptr)) continue;   // plan + warm-up
+        cudaEventRecord(e0);
+        bool ok = true;
+        for (int r = 0; r < 2 && ok; ++r) ok = tcng_apply_circuit(st, ops, n_ops, pool, n_mat, params, P, nullptr) == TCNG_OK;
+        cudaEventRecord(e1);
+        if (!ok || cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        c.ms = ms / 2.0;
+        if (best < 0 || c.ms < cands[best].ms) best = (int)i;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_opt = saved;
+        if (best >= 0) {
+            g_opt.fuse_width = cands[best].fw;
+            g_opt.tile_bits = cands[best].tb;
+            g_opt.chunk_bits = cands[best].cb;
+            g_opt.tensor_cores = cands[best].tc;
+        }
+    }
+    {
+        std::ostringstream r;
+        r.precision(17);
+        for (const Cand& c : cands) r << c.fw << " " << c.tb << " " << c.cb << " " << c.tc << " " << c.ms << "\n";
+        std::lock_guard<std::mutex> lr(g_report_mu);
+        g_report = r.str();
+    }
+    if (best < 0) return fail(TCNG_ECUDA, "no autotune candidate ran");
+    if (best_ms) *best_ms = cands[best].ms;
+    if (cache_path) {
+        std::ofstream out(cache_path, std::ios::app);
+        out.precision(17);
+        const Cand& c = cands[best];
+        out << key << " " << (int)st->dt << " " << st->batch << " " << c.fw << " " << c.tb << " " << c.cb << " "
+            << c.tc << " " << c.ms << "\n";
+    }
+    return tcng_sync_status();
+}
+
+}  // namespace
+
 extern "C" tcng_status tcng_autotune(int n, tcng_dtype dt, int batch, const char* cache_path) {
     if (n < 5 || n > TCNG_MAX_QUBITS || batch < 1) return fail(TCNG_EINVAL, "need n >= 5 and batch >= 1");
     if (dt != TCNG_C64 && dt != TCNG_C128) return fail(TCNG_EINVAL, "bad dtype");
-    if (cache_path) {
-        std::ifstream in(cache_path);
-        std::string line;
-        while (std::getline(in, line)) {
-            std::istringstream ss(line);
-            int cn, cd, cb, fw, tb, cbits;
-            double ms;
-            if (ss >> cn >> cd >> cb >> fw >> tb >> cbits >> ms && cn == n && cd == (int)dt && cb == batch) {
-                std::lock_guard<std::mutex> lk(g_mu);
-                g_opt.fuse_width = fw;
-                g_opt.tile_bits = tb;
-                g_opt.chunk_bits = cbits;
-                return TCNG_OK;
-            }
-        }
-    }
-    const Options saved = g_opt;
+    if (load_cached(cache_path, (unsigned long long)n, (int)dt, batch)) return TCNG_OK;
     std::vector<int> nq(batch, n);
     tcng_state* st = nullptr;
     tcng_status s = tcng_state_init(&st, dt, batch, nq.data(), nullptr, 0, nullptr);
     if (s) return s;
     const std::vector<tcng_gate> g = synthetic_brickwork(n, 6);
-    const int tmax = dt == TCNG_C64 ? 13 : 12;
-    int best_fw = saved.fuse_width, best_tb = saved.tile_bits, best_cb = saved.chunk_bits;
-    double best = 1e300;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    for (int fw = 1; fw <= 3; ++fw)
-        for (int tb = tmax - 2; tb <= tmax; ++tb)
-            for (int cb = 5; cb <= 8; ++cb) {
-                {
-                    std::lock_guard<std::mutex> lk(g_mu);
-                    g_opt.fuse_width = fw;
-                    g_opt.tile_bits = tb;
-                    g_opt.chunk_bits = cb;
-                    g_opt.unfused = 0;
-                }
-                s = tcng_apply_circuit(st, g.data(), g.size(), nullptr, 0, nullptr, 0, nullptr);   // plan + warm-up
-                if (s) continue;
-                cudaEventRecord(e0);
-                for (int r = 0; r < 2; ++r) tcng_apply_circuit(st, g.data(), g.size(), nullptr, 0, nullptr, 0, nullptr);
-                cudaEventRecord(e1);
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    cudaGetLastError();
-                    continue;
-                }
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) {
-                    best = ms;
-                    best_fw = fw;
-                    best_tb = tb;
-                    best_cb = cb;
-                }
-            }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    s = tune(st, g.data(), g.size(), nullptr, 0, nullptr, 0, (unsigned long long)n, cache_path, nullptr);
     tcng_state_free(st);
+    return s;
+}
+
+extern "C" tcng_status tcng_autotune_circuit(tcng_state* st, const tcng_gate* ops, size_t n_ops,
+                                             const double* mat_pool, size_t n_mat, const void* params_dev,
+                                             int P, const char* cache_path, double* best_ms) {
+    if (!st || !ops || n_ops == 0) return fail(TCNG_EINVAL, "null or empty argument");
+    if (st->groups.size() != 1) return fail(TCNG_EUNSUPPORTED, "ragged state");
+    unsigned long long key;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        g_opt = saved;
-        g_opt.fuse_width = best_fw;
-        g_opt.tile_bits = best_tb;
-        g_opt.chunk_bits = best_cb;
+        PlanOptions o{};   // options excluded: the key names the circuit, not a candidate
+        try {
+            key = structure_hash(st->n[0], ops, n_ops, mat_pool, n_mat, P, o);
+        } catch (const std::exception& ex) {
+            return fail(TCNG_EINVAL, ex.what());
+        }
     }
-    if (best >= 1e300) return fail(TCNG_ECUDA, "no candidate ran");
-    if (cache_path) {
-        std::ofstream out(cache_path, std::ios::app);
-        out << n << " " << (int)dt << " " << batch << " " << best_fw << " " << best_tb << " " << best_cb
-            << " " << best / 2 << "\n";
-    }
-    return tcng_sync_status();
+    if (load_cached(cache_path, key, (int)st->dt, st->batch)) return TCNG_OK;
+    return tune(st, ops, n_ops, mat_pool, n_mat, params_dev, P, key, cache_path, best_ms);
+}
+
+extern "C" tcng_status tcng_autotune_report(char* buf, size_t len) {
+    if (!buf || !len) return fail(TCNG_EINVAL, "null buffer");
+    std::lock_guard<std::mutex> lr(g_report_mu);
+    const size_t n = std::min(len - 1, g_report.size());
+    std::memcpy(buf, g_report.data(), n);
+    buf[n] = 0;
+    return TCNG_OK;
 }

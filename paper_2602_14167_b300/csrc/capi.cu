@@ -828,6 +828,10 @@ tcng_status tcng_set_option(tcng_option opt, int value) {
         if (value < 0 || value > 2) return fail(TCNG_EINVAL, "tensor-core option is 0, 1 or 2");
         g_opt.tensor_cores = value;
         return TCNG_OK;
+    case TCNG_OPT_STATE_ADJOINT_N:
+        if (value < 1 || value > TCNG_MAX_QUBITS + 1) return fail(TCNG_EINVAL, "state-pass adjoint n is 1..35");
+        g_opt.state_adjoint_n = value;
+        return TCNG_OK;
     }
     return fail(TCNG_EINVAL, "unknown option");
 }
@@ -841,6 +845,7 @@ tcng_status tcng_get_option(tcng_option opt, int* value) {
     case TCNG_OPT_USE_GRAPHS: *value = g_opt.use_graphs; return TCNG_OK;
     case TCNG_OPT_UNFUSED: *value = g_opt.unfused; return TCNG_OK;
     case TCNG_OPT_TENSOR_CORES: *value = g_opt.tensor_cores; return TCNG_OK;
+    case TCNG_OPT_STATE_ADJOINT_N: *value = g_opt.state_adjoint_n; return TCNG_OK;
     }
     return fail(TCNG_EINVAL, "unknown option");
 }

@@ -234,6 +234,35 @@ tcng_status tcng_energy_grad(tcng_state* st, const tcng_gate* ops, size_t n_ops,
         return fail(TCNG_EUNSUPPORTED, "ragged state: use tcng_energy_grad_ragged");
     std::lock_guard<std::mutex> lk(g_mu);
     try {
+        // single large states, and circuits with Pauli-word rotation parameters,
+        // take the state-pass adjoint (one pass over psi and lambda per block)
+        bool state_path = st->n[0] >= g_opt.state_adjoint_n;
+        for (size_t i = 0; i < n_ops && !state_path; ++i)
+            state_path = ops && ops[i].op == TCNG_RP && ops[i].param >= 0;
+        if (state_path) {
+            const double* prm = static_cast<const double*>(params_dev);
+            uint64_t key = key_mix(options_key(), 5);
+            for (const void* p : {(const void*)st, (const void*)st->buf, params_dev, (const void*)coeffs_dev,
+                                  (const void*)energy_dev, (const void*)grad_dev})
+                key = key_mix(key, reinterpret_cast<uintptr_t>(p));
+            key = key_mix(key, structure_hash(st->n[0], ops, n_ops, mat_pool, n_mat, P, plan_options(st->dt, false)));
+            for (size_t t = 0; t < n_terms; ++t)
+                key = key_mix(key_mix(key, H[t].xmask ^ (H[t].zmask << 1)), (uint64_t)t);
+            return run_graphed(key, static_cast<cudaStream_t>(stream), [&](cudaStream_t s) -> tcng_status {
+                for (int b = 0; b < st->batch; ++b) {
+                    const tcng_status r =
+                        st->dt == TCNG_C64
+                            ? run_state_adjoint<float2>(st, b, ops, n_ops, mat_pool, n_mat, prm + (size_t)b * P, P,
+                                                        H, n_terms, coeffs_dev ? coeffs_dev + (size_t)b * n_terms : nullptr,
+                                                        energy_dev + b, P > 0 ? grad_dev + (size_t)b * P : nullptr, s)
+                            : run_state_adjoint<double2>(st, b, ops, n_ops, mat_pool, n_mat, prm + (size_t)b * P, P,
+                                                         H, n_terms, coeffs_dev ? coeffs_dev + (size_t)b * n_terms : nullptr,
+                                                         energy_dev + b, P > 0 ? grad_dev + (size_t)b * P : nullptr, s);
+                    if (r) return r;
+                }
+                return TCNG_OK;
+            });
+        }
         tcng_problem pr{};
         pr.n = st->n[0];
         pr.ops = ops;
@@ -277,6 +306,10 @@ tcng_status tcng_energy_grad_ragged(const tcng_problem* problems, int n_problems
     bool any_p = false;
     for (int s = 0; s < n_problems; ++s) any_p = any_p || problems[s].P > 0;
     if (any_p && (!params_dev || !grad_dev)) return fail(TCNG_EINVAL, "params_dev/grad_dev is NULL");
+    for (int s = 0; s < n_problems; ++s)
+        for (size_t i = 0; i < problems[s].n_ops; ++i)
+            if (problems[s].ops && problems[s].ops[i].op == TCNG_RP && problems[s].ops[i].param >= 0)
+                return fail(TCNG_EUNSUPPORTED, "ragged batches: RP parameters need tcng_energy_grad");
     std::lock_guard<std::mutex> lk(g_mu);
     try {
         AdjLayout* lay = get_layout(problems, n_problems, item_problem, batch, TCNG_C64, nullptr);

@@ -45,6 +45,7 @@ struct Options {
     int use_graphs = 1;
     int unfused = 0;
     int tensor_cores = 2;     // 0 off, 1 on, 2 auto
+    int state_adjoint_n = 21; // tcng_energy_grad: states of >= this many qubits use the state-pass adjoint
 };
 extern Options g_opt;
 extern std::mutex g_mu;
@@ -143,6 +144,13 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
                      const double* params, cudaStream_t s, void* tma_base = nullptr,
                      long long item_stride = -1, const double2* item_pool = nullptr,
                      long long pool_stride = 0);
+
+// State-pass adjoint of one item (adjoint_state.cu): params/coeffs/energy/grad
+// point at the item's rows (coeffs may be NULL: the terms' own coefficients).
+template <typename C>
+tcng_status run_state_adjoint(tcng_state* st, int item, const tcng_gate* ops, size_t n_ops, const double* pool,
+                              size_t n_mat, const double* params, int P, const tcng_pauli* H, size_t n_terms,
+                              const double* coeffs, double* energy, double* grad, cudaStream_t s);
 
 // Tensor-core register stages (kernels_pass_tc.cu).
 void plan_tensor_stages(DevPlan* dp);

@@ -15,50 +15,13 @@
 #include <type_traits>
 
 #include "device.cuh"
+#include "gates.cuh"
 #include "launch.hpp"
 #include "tile_io.cuh"
 
 namespace tcng {
 
 // ============================================================ prologue ==
-// Matrix of one gate in its own local order (q[0] most significant).
-__device__ void gate_matrix_d(const BuildOp& op, double ang, double2* M, int d,
-                              const double2* pool) {
-    for (int i = 0; i < d * d; ++i) M[i] = make_double2(0, 0);
-    double c, s;
-    const double r2 = 0.70710678118654752440;
-    switch (op.code) {
-    case TCNG_I: M[0].x = 1; M[3].x = 1; break;
-    case TCNG_X: M[1].x = 1; M[2].x = 1; break;
-    case TCNG_Y: M[1].y = -1; M[2].y = 1; break;
-    case TCNG_Z: M[0].x = 1; M[3].x = -1; break;
-    case TCNG_H: M[0].x = r2; M[1].x = r2; M[2].x = r2; M[3].x = -r2; break;
-    case TCNG_S: M[0].x = 1; M[3].y = 1; break;
-    case TCNG_T: M[0].x = 1; M[3] = make_double2(r2, r2); break;
-    case TCNG_RX:
-        sincos(0.5 * ang, &s, &c);
-        M[0].x = c; M[1].y = -s; M[2].y = -s; M[3].x = c; break;
-    case TCNG_RY:
-        sincos(0.5 * ang, &s, &c);
-        M[0].x = c; M[1].x = -s; M[2].x = s; M[3].x = c; break;
-    case TCNG_RZ:
-        sincos(0.5 * ang, &s, &c);
-        M[0] = make_double2(c, -s); M[3] = make_double2(c, s); break;
-    case TCNG_CX: M[0].x = 1; M[5].x = 1; M[11].x = 1; M[14].x = 1; break;
-    case TCNG_CZ: M[0].x = 1; M[5].x = 1; M[10].x = 1; M[15].x = -1; break;
-    case TCNG_CP:
-        sincos(ang, &s, &c);
-        M[0].x = 1; M[5].x = 1; M[10].x = 1; M[15] = make_double2(c, s); break;
-    case TCNG_SWAP: M[0].x = 1; M[6].x = 1; M[9].x = 1; M[15].x = 1; break;
-    case TCNG_RZZ:
-        sincos(0.5 * ang, &s, &c);
-        M[0] = make_double2(c, -s); M[5] = make_double2(c, s);
-        M[10] = make_double2(c, s); M[15] = make_double2(c, -s); break;
-    default:  // U1 / U2 / UK
-        for (int i = 0; i < d * d; ++i) M[i] = pool[op.pool_off + i];
-        break;
-    }
-}
 
 // Build every block matrix of every item from the parameters, in the block's
 // ascending local order.  One CTA per (block, item); thread c builds column c.

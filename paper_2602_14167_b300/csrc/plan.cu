@@ -24,7 +24,7 @@ static int op_arity(int code, int nq) {
         return 1;
     case TCNG_CX: case TCNG_CZ: case TCNG_CP: case TCNG_SWAP: case TCNG_RZZ: case TCNG_U2:
         return 2;
-    case TCNG_UK:
+    case TCNG_UK: case TCNG_RP:
         return (nq >= 1 && nq <= TCNG_MAX_FUSE) ? nq : -1;
     default:
         return -1;
@@ -33,7 +33,7 @@ static int op_arity(int code, int nq) {
 
 static bool is_param_code(int code) {
     return code == TCNG_RX || code == TCNG_RY || code == TCNG_RZ || code == TCNG_RZZ ||
-           code == TCNG_CP;
+           code == TCNG_CP || code == TCNG_RP;
 }
 
 std::vector<HostOp> import_ops(int n, const tcng_gate* ops, size_t n_ops, size_t n_mat, int P,
@@ -61,7 +61,7 @@ std::vector<HostOp> import_ops(int n, const tcng_gate* ops, size_t n_ops, size_t
         h.param = g.param < 0 ? -1 : g.param;
         if (g.param >= P) throw std::invalid_argument(where.str() + "param index >= P");
         if (g.param >= 0 && !is_param_code(g.op))
-            throw std::invalid_argument(where.str() + "only RX/RY/RZ/RZZ/CP take a parameter");
+            throw std::invalid_argument(where.str() + "only RX/RY/RZ/RZZ/CP/RP take a parameter");
         h.scale = g.scale;
         h.angle0 = g.angle0;
         if (!std::isfinite(g.scale) || !std::isfinite(g.angle0))
@@ -74,11 +74,25 @@ std::vector<HostOp> import_ops(int n, const tcng_gate* ops, size_t n_ops, size_t
                 throw std::invalid_argument(where.str() + "matrix outside the pool");
             h.mat_off = g.mat_off;
         }
+        if (g.op == TCNG_RP) {   // mat_off holds the Pauli word, 2 bits per qubit
+            if (g.mat_off < 0 || g.mat_off >= (int64_t(1) << (2 * h.k)))
+                throw std::invalid_argument(where.str() + "Pauli word out of range");
+            h.mat_off = g.mat_off;
+        }
         switch (g.op) {
         case TCNG_I: case TCNG_Z: case TCNG_S: case TCNG_T: case TCNG_RZ: case TCNG_CZ:
         case TCNG_CP: case TCNG_RZZ:
             h.diag = true;
             break;
+        case TCNG_RP: {   // diagonal iff every factor is I or Z
+            bool dg = true;
+            for (int j = 0; j < h.k; ++j) {
+                const int w = (int)((g.mat_off >> (2 * j)) & 3);
+                dg = dg && (w == 0 || w == 3);
+            }
+            h.diag = dg;
+            break;
+        }
         case TCNG_U1: case TCNG_U2: case TCNG_UK: {
             int d = 1 << h.k;
             bool dg = true;

@@ -24,7 +24,8 @@ PAULI_DTYPE = np.dtype([("xmask", "<u8"), ("zmask", "<u8"), ("coeff", "<f8")], a
 assert GATE_DTYPE.itemsize == 56 and PAULI_DTYPE.itemsize == 24
 
 C64, C128 = 0, 1
-OPT_FUSE_WIDTH, OPT_TILE_BITS, OPT_CHUNK_BITS, OPT_USE_GRAPHS, OPT_UNFUSED, OPT_TENSOR_CORES = range(6)
+(OPT_FUSE_WIDTH, OPT_TILE_BITS, OPT_CHUNK_BITS, OPT_USE_GRAPHS, OPT_UNFUSED, OPT_TENSOR_CORES,
+ OPT_STATE_ADJOINT_N) = range(7)
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSUPPORTED", 5: "ETIMEOUT"}
 
 
@@ -77,6 +78,8 @@ def lib():
             "tcng_set_option": [i32, i32],
             "tcng_get_option": [i32, C.POINTER(i32)],
             "tcng_autotune": [i32, i32, i32, C.c_char_p],
+            "tcng_autotune_circuit": [vp, vp, sz, vp, sz, vp, i32, C.c_char_p, C.POINTER(dp)],
+            "tcng_autotune_report": [C.c_char_p, sz],
             "tcng_sync_status": [],
             "tcng_profile_enable": [i32],
             "tcng_profile_read": [C.c_char_p, sz, i32],
@@ -307,6 +310,33 @@ def tcng_autotune(n, dtype, batch, cache_path=None):
                                cache_path.encode() if cache_path else None))
 
 
+def tcng_autotune_circuit(handle, gates, pool, params_dev, P, cache_path=None):
+    """Time every option candidate on this circuit and state; returns the best ms
+    per call (None when the choice came from the cache)."""
+    g = _gates(gates)
+    p, n_mat = _pool(pool)
+    best = C.c_double(-1.0)
+    _check(lib().tcng_autotune_circuit(handle, g.ctypes.data, len(g), p.ctypes.data if n_mat else None,
+                                       n_mat, _ptr(params_dev), int(P),
+                                       cache_path.encode() if cache_path else None, C.byref(best)))
+    return None if best.value < 0 else best.value
+
+
+def tcng_autotune_report():
+    """[(fuse_width, tile_bits, chunk_bits, tensor_cores, ms)] of the last autotune
+    run, or [("cached", line)] when its choice was loaded from the cache."""
+    buf = C.create_string_buffer(1 << 16)
+    _check(lib().tcng_autotune_report(buf, len(buf)))
+    out = []
+    for line in buf.value.decode().splitlines():
+        if line.startswith("cached"):
+            out.append(("cached", line[7:]))
+        elif line.strip():
+            f = line.split()
+            out.append((int(f[0]), int(f[1]), int(f[2]), int(f[3]), float(f[4])))
+    return out
+
+
 def tcng_sync_status():
     _check(lib().tcng_sync_status())
 
@@ -352,7 +382,7 @@ EXPORTED = [
     "tcng_energy_grad", "tcng_energy_grad_ragged", "tcng_apply_shared_unitary", "tcng_marginal_probs", "tcng_measure",
     "tcng_adam_step",
     "tcng_adam_step_f32", "tcng_mlp_forward", "tcng_mlp_backward", "tcng_set_option",
-    "tcng_get_option", "tcng_autotune", "tcng_sync_status", "tcng_describe_plan",
+    "tcng_get_option", "tcng_autotune", "tcng_autotune_circuit", "tcng_autotune_report", "tcng_sync_status", "tcng_describe_plan",
     "tcng_profile_enable", "tcng_profile_read",
     "tcng_launch_count", "tcng_last_error", "tcng_version",
 ]

@@ -96,20 +96,61 @@ def test_graph_and_eager_runs_agree(T):
 
 
 def test_autotune_sets_options_and_caches(T, tmp_path):
+    """The synthetic-brickwork search: every candidate (k = 1..5, tensor cores
+    off/on, two tile and two chunk sizes) is timed, the fastest becomes the
+    option set and the cache line; a second call loads the line."""
     cache = str(tmp_path / "tune.txt")
     saved = {o: T.tcng_get_option(o) for o in range(6)}
     try:
         T.tcng_autotune(18, T.C64, 1, cache)
-        fw, tb, cb = (T.tcng_get_option(o) for o in (T.OPT_FUSE_WIDTH, T.OPT_TILE_BITS, T.OPT_CHUNK_BITS))
-        assert 1 <= fw <= 3 and 11 <= tb <= 13 and 5 <= cb <= 8
+        rep = T.tcng_autotune_report()
+        assert len(rep) == 5 * 2 * 2 * 2
+        assert {r[0] for r in rep} == {1, 2, 3, 4, 5} and {r[3] for r in rep} == {0, 1}
+        timed = [r for r in rep if r[4] >= 0]
+        best = min(timed, key=lambda r: r[4])
+        opts = tuple(T.tcng_get_option(o) for o in (T.OPT_FUSE_WIDTH, T.OPT_TILE_BITS, T.OPT_CHUNK_BITS,
+                                                     T.OPT_TENSOR_CORES))
+        assert opts == best[:4]
         line = open(cache).read().split()
-        assert [int(v) for v in line[:6]] == [18, 0, 1, fw, tb, cb]
-        # a second call loads the entry instead of timing
+        assert [int(v) for v in line[:7]] == [18, 0, 1, *best[:4]]
         for o, v in saved.items():
             T.tcng_set_option(o, v)
         T.tcng_autotune(18, T.C64, 1, cache)
-        assert T.tcng_get_option(T.OPT_TILE_BITS) == tb
+        assert T.tcng_autotune_report()[0][0] == "cached"
+        assert tuple(T.tcng_get_option(o) for o in (T.OPT_FUSE_WIDTH, T.OPT_TILE_BITS, T.OPT_CHUNK_BITS,
+                                                     T.OPT_TENSOR_CORES)) == best[:4]
         assert len(open(cache).read().splitlines()) == 1
+    finally:
+        for o, v in saved.items():
+            T.tcng_set_option(o, v)
+
+
+def test_autotune_circuit_choice_is_fastest_and_correct(T, tmp_path):
+    """Tuning on the caller's circuit: the chosen candidate is the fastest timed,
+    and the circuit run with it still matches the oracle."""
+    from oracle import sv
+    from paper_2602_14167_b300 import StateBatch
+    cache = str(tmp_path / "tune2.txt")
+    saved = {o: T.tcng_get_option(o) for o in range(6)}
+    n = 17
+    c, th = gen.su4_brickwork(n, 6, "RZ", seed=4)
+    g, p = c.to_ir()
+    try:
+        st = StateBatch(n, dtype="c64")
+        prm = torch.tensor(th.reshape(1, -1), dtype=torch.float64, device="cuda")
+        best_ms = T.tcng_autotune_circuit(st.handle, g, p, prm, prm.shape[1], cache)
+        rep = T.tcng_autotune_report()
+        timed = [r for r in rep if r[4] >= 0]
+        best = min(timed, key=lambda r: r[4])
+        assert abs(best[4] - best_ms) <= 1e-9 * max(1.0, best_ms)
+        assert tuple(T.tcng_get_option(o) for o in (T.OPT_FUSE_WIDTH, T.OPT_TILE_BITS, T.OPT_CHUNK_BITS,
+                                                     T.OPT_TENSOR_CORES)) == best[:4]
+        st.reset()
+        st.apply(g, p, prm)
+        psi = st.amplitudes(0).cpu().numpy()
+        ref = sv.apply(n, g, p, th)
+        assert np.linalg.norm(psi - ref) / np.linalg.norm(ref) < 1e-5
+        assert T.tcng_autotune_circuit(st.handle, g, p, prm, prm.shape[1], cache) is None   # cached
     finally:
         for o, v in saved.items():
             T.tcng_set_option(o, v)

@@ -449,3 +449,48 @@ def test_mipt_generator_draws_like_sequential_haar():
     for U in stack.reshape(-1, 4, 4):
         np.testing.assert_allclose(U.conj().T @ U, np.eye(4), atol=1e-14)
         assert abs(np.linalg.det(U) - 1) < 1e-13
+
+
+# ------------------------------------------------ Pauli-word rotations, su4 ladder
+def test_pauli_rotation_special_cases():
+    """RP on one qubit equals RX/RY/RZ; RP(ZZ) equals RZZ; RP(XY) equals the
+    dense route's expm(-i t X(x)Y / 2)."""
+    n = 3
+    for word, name in (("X", "RX"), ("Y", "RY"), ("Z", "RZ")):
+        a = Circuit(n).rp((1,), word, angle=0.83)
+        b = Circuit(n).add(name, (1,), angle0=0.83)
+        psi0 = gen.random_state(n, seed=1)
+        np.testing.assert_allclose(sv.apply(n, *ir(a), None, psi=psi0), sv.apply(n, *ir(b), None, psi=psi0),
+                                   atol=1e-15)
+    a = Circuit(n).rp((0, 2), "ZZ", angle=-1.3)
+    b = Circuit(n).rzz(0, 2, angle=-1.3)
+    psi0 = gen.random_state(n, seed=2)
+    np.testing.assert_allclose(sv.apply(n, *ir(a), None, psi=psi0), sv.apply(n, *ir(b), None, psi=psi0), atol=1e-15)
+    c = Circuit(n).rp((2, 0), "XY", angle=0.4).rp((1, 2, 0), "YZX", angle=1.7)
+    g, p = ir(c)
+    np.testing.assert_allclose(sv.apply(n, g, p, None, psi=psi0), dense.run(n, g, p, None, psi0=psi0), atol=1e-14)
+
+
+def test_su4_gate_is_special_unitary_and_counts():
+    """The 15-rotation su4 gate is in SU(4); the ladder has 15 L (n - 1)
+    parameters (the paper's 7440 for n = 32, L = 16)."""
+    c = gen.su4_ladder(2, 1)
+    th = gen.random_thetas(15, seed=3)
+    g, p = ir(c)
+    U = dense.circuit_unitary(2, g, p, th)
+    np.testing.assert_allclose(U.conj().T @ U, np.eye(4), atol=1e-14)
+    assert abs(np.linalg.det(U) - 1) < 1e-13
+    assert gen.su4_ladder(32, 16).n_params == 7440
+    assert len(gen.SU4_WORDS) == 15 and len(set(gen.SU4_WORDS)) == 15
+
+
+def test_su4_ladder_parameter_shift_equals_finite_differences():
+    n = 4
+    c = gen.su4_ladder(n, 1)
+    g, p = ir(c)
+    th = gen.random_thetas(c.n_params, seed=5)
+    terms = gen.tfim_terms(n, 1.0, 0.7)
+    ps = sv.grad_param_shift(n, g, p, th, terms)
+    fd = sv.grad_fd(n, g, p, th, terms, h=1e-5)
+    assert np.max(np.abs(ps - fd)) < 1e-8
+    assert np.linalg.norm(ps) > 1e-2

@@ -129,8 +129,8 @@ def inverse_circuit(c: Circuit) -> Circuit:
     matrices conjugate-transposed, S and T replaced by their inverses."""
     inv = Circuit(c.n)
     for (name, qubits, param, scale, angle0, mat) in reversed(c.ops):
-        if name in ("RX", "RY", "RZ", "RZZ", "CP"):
-            inv.add(name, qubits, param=param, scale=-scale, angle0=-angle0)
+        if name in ("RX", "RY", "RZ", "RZZ", "CP", "RP"):
+            inv.add(name, qubits, param=param, scale=-scale, angle0=-angle0, matrix=mat)
         elif name in ("U1", "U2", "UK"):
             inv.unitary(qubits, mat.conj().T)
         elif name == "S":
@@ -168,6 +168,40 @@ def qml_brickwall(n: int, layers: int, seed: int = 0):
     return c
 
 
+SU4_WORDS = [a + b for a in "IXYZ" for b in "IXYZ" if a + b != "II"]
+
+
+def su4_ladder(n: int, layers: int):
+    """The SU(4)-ladder ansatz of the paper's distributed VQE benchmark (Sec. VI.B):
+    per layer su4(i, i+1) for i = 0..n-2 in order, 15 parameters per gate
+    (15 L (n-1) in all).  su4(i, j; t_1..t_15) is written as the ordered product of
+    the 15 two-qubit Pauli rotations exp(-i t_a P_a / 2), P_a over SU4_WORDS
+    (lexicographic in I, X, Y, Z; first letter on qubit i), applied a = 1 first.
+    Param index = (layer (n-1) + i) 15 + a.  Returns the Circuit."""
+    c = Circuit(n)
+    for l in range(layers):
+        for i in range(n - 1):
+            base = (l * (n - 1) + i) * 15
+            for a, w in enumerate(SU4_WORDS):
+                c.rp((i, i + 1), w, param=base + a)
+    c.n_params = 15 * layers * (n - 1)
+    return c
+
+
+def cut_su4_ladder(n: int, layers: int, block: int):
+    """``su4_ladder`` without the su4 gates on the bonds between blocks of ``block``
+    qubits (their 15 parameters are read by no gate): the state stays a product of
+    n / block independent ladders."""
+    c = su4_ladder(n, layers)
+    out = Circuit(n)
+    for (name, qubits, param, scale, angle0, mat) in c.ops:
+        if min(qubits) // block != max(qubits) // block:
+            continue
+        out.add(name, qubits, param=param, scale=scale, angle0=angle0, matrix=mat)
+    out.n_params = c.n_params
+    return out
+
+
 def hea_ring(n: int, layers: int = 12):
     """Hardware-efficient ring ansatz (TFIM VQE ansatz of Sec. I.B, widened).
 
@@ -199,7 +233,7 @@ def random_circuit(n: int, n_ops: int, seed: int = 0, kinds=None):
         k = kinds[int(rng.integers(len(kinds)))]
         if k in ("U3", "U4", "U5") and n < int(k[1]):
             k = "U2"
-        if k in ("CX", "CZ", "CP", "SWAP", "RZZ", "U2") and n < 2:
+        if k in ("CX", "CZ", "CP", "SWAP", "RZZ", "U2", "RP") and n < 2:
             k = "RX"
         if k in ("X", "Y", "Z", "H", "S", "T"):
             c.add(k, (int(rng.integers(n)),))
@@ -211,6 +245,13 @@ def random_circuit(n: int, n_ops: int, seed: int = 0, kinds=None):
         elif k in ("CX", "CZ", "SWAP"):
             a, b = rng.choice(n, 2, replace=False)
             c.add(k, (int(a), int(b)))
+        elif k == "RP":
+            kq = 1 + int(rng.integers(2))
+            qs = rng.choice(n, kq, replace=False)
+            word = "".join("XYZ"[int(v)] for v in rng.integers(0, 3, kq))
+            c.rp(tuple(int(q) for q in qs), word, param=p, scale=float(rng.choice([1.0, -0.5])),
+                 angle=float(rng.uniform(-1, 1)))
+            p += 1
         elif k in ("CP", "RZZ"):
             a, b = rng.choice(n, 2, replace=False)
             c.add(k, (int(a), int(b)), param=p, scale=1.0,

@@ -24,12 +24,13 @@ import numpy as np
 OPS = {
     "I": 0, "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "T": 6,
     "RX": 7, "RY": 8, "RZ": 9, "CX": 10, "CZ": 11, "CP": 12, "SWAP": 13,
-    "RZZ": 14, "U1": 15, "U2": 16, "UK": 17,
+    "RZZ": 14, "U1": 15, "U2": 16, "UK": 17, "RP": 18,
 }
 OP_NAMES = {v: k for k, v in OPS.items()}
 NQ = {"I": 1, "X": 1, "Y": 1, "Z": 1, "H": 1, "S": 1, "T": 1, "RX": 1, "RY": 1,
       "RZ": 1, "CX": 2, "CZ": 2, "CP": 2, "SWAP": 2, "RZZ": 2, "U1": 1, "U2": 2}
-PARAMETRIC = {"RX", "RY", "RZ", "RZZ", "CP"}
+PARAMETRIC = {"RX", "RY", "RZ", "RZZ", "CP", "RP"}
+PAULI_DIGIT = {"I": 0, "X": 1, "Y": 2, "Z": 3}
 
 # struct tcng_gate { uint16 op; uint8 nq; uint8 pad; int32 q[5]; int32 param;
 #                    double scale; double angle0; int64 mat_off; }  -> 56 bytes
@@ -58,7 +59,12 @@ class Circuit:
         qubits = tuple(int(q) for q in qubits)
         if name in NQ and len(qubits) != NQ[name]:
             raise ValueError(f"{name} takes {NQ[name]} qubits")
-        if matrix is not None:
+        if name == "RP":   # `matrix` carries the Pauli word: digit j (2 bits) on qubits[j]
+            word = int(matrix)
+            if not 0 <= word < 4 ** len(qubits):
+                raise ValueError("Pauli word out of range")
+            matrix = word
+        elif matrix is not None:
             matrix = np.asarray(matrix, dtype=np.complex128)
             d = 1 << len(qubits)
             if matrix.shape != (d, d):
@@ -103,6 +109,13 @@ class Circuit:
     def cp(self, a, b, param=None, angle=0.0, scale=1.0):
         return self._rot("CP", (a, b), param, angle, scale)
 
+    def rp(self, qubits, paulis, param=None, angle=0.0, scale=1.0):
+        """exp(-i t P / 2) with P = paulis[0] on qubits[0] (x) paulis[1] on qubits[1] ...,
+        paulis a string over I, X, Y, Z; t = angle + scale * params[param]."""
+        word = sum(PAULI_DIGIT[c] << (2 * j) for j, c in enumerate(paulis))
+        return self.add("RP", qubits, param=-1 if param is None else param, scale=scale,
+                        angle0=angle, matrix=word)
+
     def unitary(self, qubits, matrix):
         qubits = tuple(qubits)
         name = {1: "U1", 2: "U2"}.get(len(qubits), "UK")
@@ -124,7 +137,9 @@ class Circuit:
             g["param"] = param
             g["scale"] = scale
             g["angle0"] = angle0
-            if mat is not None:
+            if name == "RP":
+                g["mat_off"] = mat
+            elif mat is not None:
                 g["mat_off"] = off
                 pool.append(mat.reshape(-1))
                 off += mat.size
