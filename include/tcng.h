@@ -401,7 +401,13 @@ typedef enum {
                                   parameters from one cross-density matrix) for states of at
                                   least this many qubits (default 21; 1..35), and always for
                                   circuits with RP parameters; smaller states use the
-                                  per-item persistent kernel */
+                                  per-item persistent kernel */,
+    TCNG_OPT_TC_FP16 = 7          /* 1 (default): tensor-core passes of unitary plans whose
+                                  tiles share one parameter set split both GEMM operands
+                                  into FP16 hi + lo (each tile scaled by a power of two
+                                  first, FP32 accumulation; passes whose stages touch every
+                                  tile bit keep two tiles in flight per CTA); 0: the TF32
+                                  hi/lo split everywhere */
 } tcng_option;
 
 tcng_status tcng_set_option(tcng_option opt, int value);

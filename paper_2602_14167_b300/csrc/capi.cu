@@ -246,6 +246,7 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
         // complex64 register stages on the tensor cores (when enabled): W operands
         // from an FP64 table of the same blocks
         const float* wops = nullptr;
+        const void* wops_h = nullptr;   // FP16 operands (one W set for every tile)
         long long w_stride = 0;
         // auto: the W prologue is per item when items carry their own parameters, and
         // fewer tiles than SMs leave the tensor-core pipeline latency-bound (measured
@@ -265,7 +266,14 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
                 e = launch_build_matrices<double2>(dp->d_bblocks, (int)pl.bblocks.size(), dp->d_bops,
                                                    pool, pl.P > 0 ? params : nullptr, pl.P, dtab,
                                                    pl.table_size, tab_items, s, pstride);
-                if (e == cudaSuccess) e = launch_build_stage_w(dp, dtab, stride, tab_items, w, s);
+                if (e == cudaSuccess) e = launch_build_stage_w(dp, dtab, stride, tab_items, w, false, s);
+                // unitary plans whose tiles all share one W set also get the FP16 operands
+                if (e == cudaSuccess && g_opt.tc_fp16 && pl.all_unitary && tab_items == 1) {
+                    void* wh = c.scratch("tc_wh", (size_t)4096 * dp->n_tc);
+                    if (!wh) return fail(TCNG_ENOMEM, "tensor-core operand scratch");
+                    e = launch_build_stage_w(dp, dtab, stride, 1, wh, true, s);
+                    wops_h = wh;
+                }
                 if (e != cudaSuccess) return cuda_fail(e, "tensor-core operand prologue");
                 wops = w;
                 w_stride = per_item ? 2048ll * dp->n_tc : 0;
@@ -286,6 +294,13 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
                         tma = ts;
                         swz = true;
                     }
+                }
+                if (wops_h && pass_tch_eligible(dp, (int)pi)) {
+                    ProfScope ps("pass_tch_kernel_c64", s);
+                    e = launch_pass_tch(dp, (int)pi, items, wops_h, ctx().err, tma, swz,
+                                        reinterpret_cast<float2*>(state), d_item_off, s);
+                    if (e != cudaSuccess) return cuda_fail(e, "tensor-core pass kernel");
+                    continue;
                 }
                 ProfScope ps("pass_tcs_kernel_c64", s);
                 e = launch_pass_tcs(dp, (int)pi, items, wops, w_stride, ctx().err, tma, swz,
@@ -832,6 +847,9 @@ tcng_status tcng_set_option(tcng_option opt, int value) {
         if (value < 1 || value > TCNG_MAX_QUBITS + 1) return fail(TCNG_EINVAL, "state-pass adjoint n is 1..35");
         g_opt.state_adjoint_n = value;
         return TCNG_OK;
+    case TCNG_OPT_TC_FP16:
+        g_opt.tc_fp16 = value ? 1 : 0;
+        return TCNG_OK;
     }
     return fail(TCNG_EINVAL, "unknown option");
 }
@@ -846,6 +864,7 @@ tcng_status tcng_get_option(tcng_option opt, int* value) {
     case TCNG_OPT_UNFUSED: *value = g_opt.unfused; return TCNG_OK;
     case TCNG_OPT_TENSOR_CORES: *value = g_opt.tensor_cores; return TCNG_OK;
     case TCNG_OPT_STATE_ADJOINT_N: *value = g_opt.state_adjoint_n; return TCNG_OK;
+    case TCNG_OPT_TC_FP16: *value = g_opt.tc_fp16; return TCNG_OK;
     }
     return fail(TCNG_EINVAL, "unknown option");
 }

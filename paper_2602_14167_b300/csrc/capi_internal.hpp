@@ -46,6 +46,7 @@ struct Options {
     int unfused = 0;
     int tensor_cores = 2;     // 0 off, 1 on, 2 auto
     int state_adjoint_n = 21; // tcng_energy_grad: states of >= this many qubits use the state-pass adjoint
+    int tc_fp16 = 1;          // 1: FP16-split tensor-core passes where eligible, 0: TF32 split only
 };
 extern Options g_opt;
 extern std::mutex g_mu;
@@ -155,7 +156,13 @@ tcng_status run_state_adjoint(tcng_state* st, int item, const tcng_gate* ops, si
 // Tensor-core register stages (kernels_pass_tc.cu).
 void plan_tensor_stages(DevPlan* dp);
 cudaError_t launch_build_stage_w(const DevPlan* dp, const double2* table, long long table_stride,
-                                 int items, float* wops, cudaStream_t s);
+                                 int items, void* wops, bool half, cudaStream_t s);
+// FP16-split tensor-core passes (unitary plans, one W set for every tile):
+// whether pass `pass` can run them, and the launch.
+bool pass_tch_eligible(const DevPlan* dp, int pass);
+cudaError_t launch_pass_tch(const DevPlan* dp, int pass, int items, const void* wops_h, unsigned* err,
+                            const TmaTile& tma, bool swizzled, float2* state, const long long* item_off,
+                            cudaStream_t s);
 cudaError_t launch_pass_tcs(const DevPlan* dp, int pass, int items, const float* wops,
                             long long w_item_stride, unsigned* err, const TmaTile& tma, bool swizzled,
                             float2* state, const long long* item_off, cudaStream_t s);

@@ -37,6 +37,7 @@ uint64_t options_key() {
     h = key_mix(h, (uint64_t)g_opt.chunk_bits);
     h = key_mix(h, (uint64_t)g_opt.unfused);
     h = key_mix(h, (uint64_t)g_opt.tensor_cores);
+    h = key_mix(h, (uint64_t)g_opt.tc_fp16);
     return h;
 }
 

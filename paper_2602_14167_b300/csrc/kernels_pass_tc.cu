@@ -67,9 +67,12 @@ struct StageSm {            // per-stage constants, shared memory
 // ------------------------------------------------------------- prologue --
 // W_s of every tensor-core stage and item: U_s = product of the stage's ops
 // (FP64, from the FP64 matrix table), then the real form, TF32 hi/lo.
+// H: the FP16 form instead (4 KiB per stage): row nn holds [hi | lo] of the 32
+// K values as halves, 128 bytes per row, 128-byte swizzled, for kind::f16.
+template <bool H>
 __global__ void build_stage_w_kernel(const TcsStage* __restrict__ tcs, const DevOp* __restrict__ ops,
                                      const double2* __restrict__ table, long long table_stride,
-                                     float* __restrict__ wops, int n_tc) {
+                                     void* __restrict__ wops_v, int n_tc) {
     const TcsStage S = tcs[blockIdx.x];
     if (S.tc_index < 0) return;
     const int item = blockIdx.y;
@@ -112,17 +115,24 @@ __global__ void build_stage_w_kernel(const TcsStage* __restrict__ tcs, const Dev
     }
     // B operand row nn = output real 2j+b, column kk = input real 2l+a:
     // W[kk][nn] of  y_j = sum_l U[j][l] x_l  in (re, im) pairs.
-    unsigned char* out = reinterpret_cast<unsigned char*>(
-        wops + ((long long)item * n_tc + S.tc_index) * TS_W_FLOATS);
+    const uint32_t wbytes = H ? TH_W_BYTES : TS_W_BYTES;
+    unsigned char* out = static_cast<unsigned char*>(wops_v) + ((long long)item * n_tc + S.tc_index) * wbytes;
     for (int e = tid; e < 32 * 32; e += blockDim.x) {
         const int nn = e >> 5, kk = e & 31;
         const int j = nn >> 1, b = nn & 1, l = kk >> 1, a = kk & 1;
         const double2 u = U[j][l];
         const double w = (a == b) ? u.x : (a ? -u.y : u.y);
-        const float h = tf32_round((float)w);
-        const uint32_t off = sw128_offset(nn, kk, 32);
-        *reinterpret_cast<float*>(out + off) = h;
-        *reinterpret_cast<float*>(out + 4096 + off) = tf32_round((float)(w - (double)h));
+        if (H) {   // hi = w rounded to FP16, lo = the rest rounded to FP16
+            const __half h = __double2half(w);
+            const __half lo = __double2half(w - (double)__half2float(h));
+            *reinterpret_cast<__half*>(out + sw128_offset_h(nn, kk)) = h;
+            *reinterpret_cast<__half*>(out + sw128_offset_h(nn, 32 + kk)) = lo;
+        } else {
+            const float h = tf32_round((float)w);
+            const uint32_t off = sw128_offset(nn, kk, 32);
+            *reinterpret_cast<float*>(out + off) = h;
+            *reinterpret_cast<float*>(out + 4096 + off) = tf32_round((float)(w - (double)h));
+        }
     }
 }
 
@@ -664,10 +674,13 @@ void plan_tensor_stages(DevPlan* dp) {
 }
 
 cudaError_t launch_build_stage_w(const DevPlan* dp, const double2* table, long long table_stride,
-                                 int items, float* wops, cudaStream_t s) {
+                                 int items, void* wops, bool half, cudaStream_t s) {
     if (!dp->n_tc) return cudaSuccess;
     dim3 grid((unsigned)dp->tcs.size(), (unsigned)items);
-    build_stage_w_kernel<<<grid, 256, 0, s>>>(dp->d_tcs, dp->d_dops, table, table_stride, wops, dp->n_tc);
+    if (half)
+        build_stage_w_kernel<true><<<grid, 256, 0, s>>>(dp->d_tcs, dp->d_dops, table, table_stride, wops, dp->n_tc);
+    else
+        build_stage_w_kernel<false><<<grid, 256, 0, s>>>(dp->d_tcs, dp->d_dops, table, table_stride, wops, dp->n_tc);
     count_launch();
     return cudaGetLastError();
 }

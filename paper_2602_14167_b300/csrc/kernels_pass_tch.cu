@@ -1,0 +1,783 @@
+// Tile passes whose register stages run on the tensor cores with an FP16
+// split (complex64 states, unitary plans, one W set for every tile).
+//
+// A register stage is the real GEMM of kernels_pass_tc.cu: the tile's 512 rows
+// of 32 reals (re, im of one thread's 16 amplitudes) times W_s, the 32x32 real
+// form of the stage's fused 16x16 unitary.  Here both operands are split into
+// FP16 hi + lo (x = hi + lo to ~2^-23 relative), and one FP32 accumulator per
+// output takes lo*W_hi + hi*W_lo + hi*W_hi through six kind::f16 MMAs (M=128,
+// N=32, K=16); lo*W_lo (~2^-24) is dropped.
+//
+// Range.  FP16 spans 2^-24 .. 65504, so each tile is multiplied by a power of
+// two (exact) before its first stage, chosen so that the tile's largest |re| or
+// |im| lands in [2^7, 2^8).  Every stage of a unitary plan keeps the tile norm
+// (the gates act inside the tile), and no element exceeds the norm, so later
+// stages see values below sqrt(8192) * 2^8 < 2^15; elements far below the
+// maximum keep an absolute accuracy of ~2^-25 (subnormal halves), i.e. 2^-32 of
+// the maximum.  After the last stage the tile is unscaled and its norm is
+// restored to the norm it had before the pass (the tensor core's accumulation
+// rounds toward zero, a small systematic shrink per stage).
+//
+// Why: FP16 operands take half the tensor-core time of the TF32 form and half
+// its TMEM traffic, and a row's TMEM share (A hi 16 + A lo 16 + D 32 columns)
+// leaves room for a second tile per 128-row slice:
+//   * lock-step passes (the stages touch every tile bit, so each stage ends in a
+//     barrier of all 512 compute threads) keep two tiles in flight: tile A's
+//     MMAs run while the threads load and split tile B's rows, and tile B's
+//     MMAs run while the threads store tile A's results;
+//   * independent-slice passes (two tile bits that no stage touches, so each
+//     slice's 128 rows stay closed under the pass) run one tile per slice, the
+//     slice pairs half a stage apart, as in the TF32 kernel.
+// A seventeenth warp moves tiles (TMA or per-chunk bulk copies, tile_io.cuh).
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "capi_internal.hpp"
+#include "device.cuh"
+#include "tc.cuh"
+#include "tile_io.cuh"
+
+namespace tcng {
+
+namespace {
+
+constexpr int TH_THREADS = 512;                    // compute threads: 4 slices x 4 warps
+constexpr int TH_CTA_THREADS = TH_THREADS + 32;    // + one producer warp
+constexpr int TH_PRODUCER_WARP = TH_THREADS / 32;
+constexpr int TH_TILE_BITS = 13;
+constexpr int TH_TILE_ELEMS = 1 << TH_TILE_BITS;
+constexpr uint32_t TH_TILE_BYTES = sizeof(float2) << TH_TILE_BITS;   // 64 KiB
+constexpr uint32_t TH_TMEM_COLS = 512;             // 4 slices x 2 tiles x (A hi 16 + A lo 16 + D 32)
+constexpr int TH_MAX_STAGES = 22;                  // stages per pass (W of all resident)
+constexpr int TH_MAX_STAGES_3BUF = 7;              // with three tile buffers
+constexpr int FORM_PLAIN = 0, FORM_ROT = 1, FORM_SWZ = 2;
+
+struct StageH {             // per-stage constants, shared memory (64 bytes)
+    int sr[4];              // 1 << register tile bit i
+    int hm[6];              // ~((1 << b) - 1) for the bits the row index skips (ascending)
+    int nj;                 // register bits on tile bits 0..3
+    int pad[5];
+};
+
+struct PassTchArgs {
+    int gb0, gb1;               // independent-slice passes: tile bits fixed per slice
+    int renorm;                 // restore each tile's (slice's) norm after the last stage
+    const TcsStage* tcs;        // this pass's stages
+    const unsigned char* wops;  // FP16 W operands of the plan's tensor-core stages
+    long long total_tiles;
+    unsigned* err;
+    float2* state;
+    const long long* item_off;
+    TileCtx tc;
+};
+
+__device__ __forceinline__ void sync_compute() {   // the 512 compute threads
+    asm volatile("bar.sync 5, %0;" ::"n"(TH_THREADS) : "memory");
+}
+__device__ __forceinline__ void sync_slice(int slice) {   // the 128 threads of one slice
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + slice), "r"(128) : "memory");
+}
+// Barrier of the 512 compute threads that also ORs a flag over them, so every
+// thread takes the same branch on the result.
+__device__ __forceinline__ bool sync_compute_or(bool flag) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+                 "bar.red.or.pred p, 5, %2, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(r)
+                 : "r"((uint32_t)flag), "n"(TH_THREADS)
+                 : "memory");
+    return r != 0;
+}
+
+// Power-of-two scale c with m*c in [2^7, 2^8) (m >= 0; c and 1/c stay normal).
+__device__ __forceinline__ void tile_scale(float m, float& c, float& ic) {
+    const int e = (int)((__float_as_uint(m) >> 23) & 0xffu);
+    const int f = min(253, max(1, 261 - e));
+    c = __uint_as_float((uint32_t)f << 23);
+    ic = __uint_as_float((uint32_t)(254 - f) << 23);
+}
+
+// x = hi + lo, both FP16 (re in the low half of each 32-bit word).
+__device__ __forceinline__ void split_f16(float2 x, uint32_t& hi, uint32_t& lo) {
+    const __half2 h = __floats2half2_rn(x.x, x.y);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(x.x - hf.x, x.y - hf.y);
+    memcpy(&hi, &h, 4);
+    memcpy(&lo, &l, 4);
+}
+
+// a[s] holds register value s ^ tau (tau only on slots 0..nj-1): permute so
+// that a[v] holds value v (the permutation is its own inverse).
+__device__ __forceinline__ void unrotate_h(float2 (&a)[16], int tau, int nj) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (k < nj) {
+            const bool sw = (tau >> k) & 1;
+#pragma unroll
+            for (int s = 0; s < 16; ++s)
+                if (!(s & (1 << k))) {
+                    const float2 x = a[s], y = a[s | (1 << k)];
+                    a[s] = sw ? y : x;
+                    a[s | (1 << k)] = sw ? x : y;
+                }
+        }
+    }
+}
+
+// Shared-memory slots of this thread's 16 amplitudes for stage S: row g (the
+// tile index with zeros at the register bits), tau the XOR rotation (ROT).
+template <int FORM>
+__device__ __forceinline__ void stage_slots(const StageH& S, int g, int tau, int (&L)[16]) {
+    int sr[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) sr[i] = S.sr[i];
+    if (FORM == FORM_SWZ) {   // slot offset o lies at o ^ ((o >> 3) & 0xE) (linear in o)
+        g ^= (g >> 3) & 0xe;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sr[i] ^= (sr[i] >> 3) & 0xe;
+    }
+    int stau = 0;
+    if (FORM == FORM_ROT && S.nj) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) stau |= ((tau >> i) & 1) ? sr[i] : 0;
+    }
+    L[0] = g | stau;
+#pragma unroll
+    for (int v = 1; v < 16; ++v)
+        L[v] = L[v & (v - 1)] ^ ((v & 1) ? sr[0] : (v & 2) ? sr[1] : (v & 4) ? sr[2] : sr[3]);
+}
+
+// Row index of this thread in a lock-step stage: tid with zeros inserted at the
+// four register bits.
+__device__ __forceinline__ int lock_row(const StageH& S, int tid) {
+    int g = tid;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) g += g & S.hm[i];
+    return g;
+}
+// ... in an independent-slice stage: the slice's 128 rows, the slice index on
+// the pass's two fixed tile bits.
+__device__ __forceinline__ int group_row(const StageH& S, int tid, int gb0, int gb1) {
+    int g = tid & 127;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) g += g & S.hm[i];
+    return g | (((tid >> 7) & 1) << gb0) | (((tid >> 8) & 1) << gb1);
+}
+
+__device__ __forceinline__ void load_stage(const TcsStage* tcs, int nst, int gb0, int gb1, bool grouped,
+                                           StageH* sst, int tid, int nthreads) {
+    for (int i = tid; i < nst; i += nthreads) {
+        const TcsStage S = tcs[i];
+        StageH d;
+        int skip[6], ns = 0;
+        for (int r = 0; r < 4; ++r) {
+            d.sr[r] = 1 << S.rbit[r];
+            skip[ns++] = S.rbit[r];
+        }
+        if (grouped) {
+            skip[ns++] = gb0;
+            skip[ns++] = gb1;
+        }
+        for (int x = 1; x < ns; ++x)
+            for (int y = x; y > 0 && skip[y - 1] > skip[y]; --y) {
+                const int t = skip[y];
+                skip[y] = skip[y - 1];
+                skip[y - 1] = t;
+            }
+        for (int k = 0; k < 6; ++k) d.hm[k] = k < ns ? ~((1 << skip[k]) - 1) : 0;
+        d.nj = S.nj;
+        for (int k = 0; k < 5; ++k) d.pad[k] = 0;
+        sst[i] = d;
+    }
+}
+
+// The six MMAs of one stage for one 128-row slice: D = lo*W_hi + hi*W_lo + hi*W_hi.
+// A (TMEM): hi at column a, lo at a + 16, 8 columns per K step of 16 halves.
+// W (shared memory, 128-byte rows [hi 32 | lo 32]): +32 bytes per K step (+2 in
+// the descriptor's start field), the lo half at +64 bytes (+4).
+__device__ __forceinline__ void stage_mmas(uint32_t d, uint32_t a, uint64_t dw) {
+    constexpr uint32_t idesc = f16_idesc(128, 32);
+    tc_mma_f16_ts(d, a + 16u, dw, idesc, 0);
+    tc_mma_f16_ts(d, a + 24u, dw + 2u, idesc, 1);
+    tc_mma_f16_ts(d, a, dw + 4u, idesc, 1);
+    tc_mma_f16_ts(d, a + 8u, dw + 6u, idesc, 1);
+    tc_mma_f16_ts(d, a, dw, idesc, 1);
+    tc_mma_f16_ts(d, a + 8u, dw + 2u, idesc, 1);
+}
+
+__device__ __forceinline__ float warp_max(float m) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    return m;
+}
+__device__ __forceinline__ float row_max(const float2 (&x)[16]) {
+    float m = 0.f;
+#pragma unroll
+    for (int v = 0; v < 16; ++v) m = fmaxf(m, fmaxf(fabsf(x[v].x), fabsf(x[v].y)));
+    return m;
+}
+__device__ __forceinline__ float row_norm2(const float2 (&x)[16]) {
+    float p4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int v = 0; v < 16; ++v) p4[v & 3] = fmaf(x[v].x, x[v].x, fmaf(x[v].y, x[v].y, p4[v & 3]));
+    return (p4[0] + p4[1]) + (p4[2] + p4[3]);
+}
+// sqrt(ti / to) * ic; tiles of zero norm keep their values (times ic)
+__device__ __forceinline__ float norm_factor(int renorm, float ti, float to, float ic) {
+    return (renorm && ti > 0.f && to > 0.f) ? sqrtf(ti) * rsqrtf(to) * ic : ic;
+}
+
+// Tile mover (warp TH_PRODUCER_WARP): loads run `ahead` tiles in front; a tile's
+// buffer is stored once the compute side reports it done, and the load `ahead`
+// tiles later goes into the same buffer once the store has read it.
+template <int NBUF>
+__device__ void tile_mover(const DevPass& p, const PassTchArgs& a, const TmaTile& tma, float2* bufs,
+                           uint64_t* tile_bar, uint64_t* done_bar, volatile int* s_abort, long long first,
+                           long long stride, long long my_tiles, int lane) {
+    long long issued = 0;
+    for (; issued < NBUF && issued < my_tiles; ++issued)
+        issue_tile_load(a.state, a.item_off, p, a.tc, first + issued * stride, bufs + issued * TH_TILE_ELEMS,
+                        &tile_bar[issued], lane, tma);
+    for (long long i = 0; i < my_tiles; ++i) {
+        const int b = (int)(i % NBUF);
+        uint32_t done = 0;
+        if (lane == 0) {
+            const uint32_t par = (uint32_t)((i / NBUF) & 1);
+            done = mbar_try_wait(&done_bar[b], par);
+            const unsigned long long t0 = global_ns();
+            for (uint32_t k = 1; !done; ++k) {
+                if (*s_abort) break;
+                done = mbar_try_wait(&done_bar[b], par);
+                if (!done && (k & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
+                    atomicOr(a.err, ERR_TIMEOUT);
+                    *s_abort = 1;
+                    break;
+                }
+            }
+        }
+        if (!__shfl_sync(0xffffffffu, done, 0)) break;
+        issue_tile_store(a.state, a.item_off, p, a.tc, first + i * stride, bufs + (size_t)b * TH_TILE_ELEMS,
+                         lane, tma);
+        if (issued < my_tiles) {
+            bulk_wait_read<0>();
+            __syncwarp();
+            issue_tile_load(a.state, a.item_off, p, a.tc, first + issued * stride,
+                            bufs + (size_t)b * TH_TILE_ELEMS, &tile_bar[b], lane, tma);
+            ++issued;
+        }
+    }
+    bulk_wait<0>();
+    // after an abort the last loads may still be in flight: wait for them before
+    // the shared memory goes away
+    if (lane == 0)
+        for (long long i = issued > NBUF ? issued - NBUF : 0; i < issued; ++i)
+            mbar_wait_bounded(&tile_bar[i % NBUF], (uint32_t)((i / NBUF) & 1), a.err);
+    __syncwarp();
+}
+
+// Per-tile state of one of the two tiles a lock-step CTA keeps in flight.
+struct TileRun {
+    long long it;   // CTA-local tile index (this context runs it, it + 2, it + 4, ...)
+    int s;          // next stage
+    uint32_t mq;    // MMA barrier phases completed
+    float c, ic;    // the tile's scale and its inverse
+    float nin;      // this thread's share of the scaled tile norm before the pass
+};
+
+// ------------------------------------------------------- lock-step passes --
+template <int FORM, int NBUF>
+__global__ void __launch_bounds__(TH_CTA_THREADS, 1)
+    pass_tch_lock_kernel(const __grid_constant__ DevPass p, const PassTchArgs a,
+                         const __grid_constant__ TmaTile tma) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int nst = p.stage_count;
+    unsigned char* wres = base;   // nst x 4 KiB, every stage's W
+    float2* bufs = reinterpret_cast<float2*>(base + (size_t)nst * TH_W_BYTES);
+    __shared__ uint64_t tile_bar[NBUF], done_bar[NBUF], mma_bar[2][4], w_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort, s_ready[2];
+    __shared__ float redm[2][TH_THREADS / 32];
+    __shared__ float2 redn[2][TH_THREADS / 32];
+    __shared__ StageH sst[TH_MAX_STAGES];
+    const int tid = threadIdx.x, warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
+    const int quarter = warp & 3, slice = warp >> 2, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(TH_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    load_stage(a.tcs, nst, 0, 0, false, sst, tid, TH_CTA_THREADS);
+    if (tid == 0) {
+        for (int i = 0; i < NBUF; ++i) {
+            mbar_init(&tile_bar[i], 1);
+            mbar_init(&done_bar[i], 1);
+        }
+        for (int c = 0; c < 2; ++c)
+            for (int i = 0; i < 4; ++i) mbar_init(&mma_bar[c][i], 1);
+        mbar_init(&w_bar, 1);
+        fence_mbar_init();
+        s_abort = 0;
+        s_ready[0] = s_ready[1] = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = __shfl_sync(0xffffffffu, tmem_base, 0);
+    const long long first = blockIdx.x, stride = gridDim.x;
+    const long long my_tiles = first < a.total_tiles ? (a.total_tiles - first + stride - 1) / stride : 0;
+    if (warp == TH_PRODUCER_WARP) {
+        tile_mover<NBUF>(p, a, tma, bufs, tile_bar, done_bar, &s_abort, first, stride, my_tiles, lane);
+        tc_fence_before();
+        __syncthreads();
+        return;
+    }
+    if (tid == 0 && my_tiles > 0) {   // every stage's W: one bulk copy (consecutive operands)
+        const uint32_t wb = (uint32_t)nst * TH_W_BYTES;
+        mbar_arrive_expect_tx(&w_bar, wb);
+        bulk_g2s(wres, a.wops + (size_t)a.tcs[0].tc_index * TH_W_BYTES, wb, &w_bar);
+    }
+    if (my_tiles > 0 && !mbar_wait_bounded(&w_bar, 0u, a.err)) s_abort = 1;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
+    TileRun cx[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        cx[c].it = c;
+        cx[c].s = 0;
+        cx[c].mq = 0;
+        cx[c].c = cx[c].ic = 1.f;
+        cx[c].nin = 0.f;
+    }
+    // with two buffers each tile reloads its own buffer: start the second tile
+    // half a pass later so the two tiles' reload waits do not coincide
+    int delay1 = NBUF == 2 ? nst / 2 : 0;
+    bool idle = false;
+    unsigned long long idle_t0 = 0;
+    sync_compute();
+    while (cx[0].it < my_tiles || cx[1].it < my_tiles) {
+        bool run[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+            run[c] = cx[c].it < my_tiles && (cx[c].s > 0 || s_ready[c]) && !(c == 1 && delay1 > 0);
+        // ---- phase A: rows -> FP16 hi/lo -> TMEM, MMAs issued
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (!run[c]) continue;
+            const int b = (int)(cx[c].it % NBUF);
+            float2* buf = bufs + (size_t)b * TH_TILE_ELEMS;
+            if (cx[c].s == 0 && !mbar_wait_bounded(&tile_bar[b], (uint32_t)((cx[c].it / NBUF) & 1), a.err))
+                s_abort = 1;
+            const StageH& S = sst[cx[c].s];
+            const int tau = (FORM == FORM_ROT && S.nj) ? (tid & 15) >> (4 - S.nj) : 0;
+            int L[16];
+            stage_slots<FORM>(S, lock_row(S, tid), tau, L);
+            float2 x[16];
+#pragma unroll
+            for (int v = 0; v < 16; ++v) x[v] = buf[L[v]];
+            if (FORM == FORM_ROT && S.nj) unrotate_h(x, tau, S.nj);
+            if (cx[c].s == 0) {   // the tile's scale from its largest component
+                const float m = warp_max(row_max(x));
+                if (lane == 0) redm[c][warp] = m;
+                sync_compute();
+                float mt = 0.f;
+#pragma unroll
+                for (int w = 0; w < TH_THREADS / 32; ++w) mt = fmaxf(mt, redm[c][w]);
+                tile_scale(mt, cx[c].c, cx[c].ic);
+#pragma unroll
+                for (int v = 0; v < 16; ++v) x[v] = make_float2(x[v].x * cx[c].c, x[v].y * cx[c].c);
+                cx[c].nin = row_norm2(x);
+            }
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int v = 0; v < 16; ++v) split_f16(x[v], hi[v], lo[v]);
+            const uint32_t col = (uint32_t)slice * 128u + (uint32_t)c * 64u;
+            tc_st16(lane_base + col, hi);
+            tc_st16(lane_base + col + 16u, lo);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            sync_slice(slice);
+            if (quarter == 0 && elect_one()) {
+                tc_fence_after();
+                stage_mmas(tmem + col + 32u, tmem + col,
+                           sw128_desc(smem_u32(wres) + (uint32_t)cx[c].s * TH_W_BYTES));
+                tc_commit(&mma_bar[c][slice]);
+            }
+        }
+        // ---- phase B: D -> rows (the last stage unscales and restores the norm)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (!run[c]) continue;
+            const int b = (int)(cx[c].it % NBUF);
+            float2* buf = bufs + (size_t)b * TH_TILE_ELEMS;
+            if (!mbar_wait_bounded(&mma_bar[c][slice], cx[c].mq & 1u, a.err)) s_abort = 1;
+            ++cx[c].mq;
+            tc_fence_after();
+            const uint32_t col = (uint32_t)slice * 128u + (uint32_t)c * 64u;
+            float2 x[16];
+            {
+                float y[32];
+                tc_ld32(lane_base + col + 32u, y);
+#pragma unroll
+                for (int v = 0; v < 16; ++v) x[v] = make_float2(y[2 * v], y[2 * v + 1]);
+            }
+            const bool last = cx[c].s == nst - 1;
+            if (last) {
+                float nin = cx[c].nin, nout = row_norm2(x);
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    nin += __shfl_xor_sync(0xffffffffu, nin, o);
+                    nout += __shfl_xor_sync(0xffffffffu, nout, o);
+                }
+                if (lane == 0) redn[c][warp] = make_float2(nin, nout);
+                sync_compute();
+                float ti = 0.f, to = 0.f;
+#pragma unroll
+                for (int w = 0; w < TH_THREADS / 32; ++w) {
+                    ti += redn[c][w].x;
+                    to += redn[c][w].y;
+                }
+                const float f = norm_factor(a.renorm, ti, to, cx[c].ic);
+#pragma unroll
+                for (int v = 0; v < 16; ++v) x[v] = make_float2(x[v].x * f, x[v].y * f);
+            }
+            const StageH& S = sst[cx[c].s];
+            const int tau = (FORM == FORM_ROT && S.nj) ? (tid & 15) >> (4 - S.nj) : 0;
+            if (FORM == FORM_ROT && S.nj) unrotate_h(x, tau, S.nj);
+            int L[16];
+            stage_slots<FORM>(S, lock_row(S, tid), tau, L);
+#pragma unroll
+            for (int v = 0; v < 16; ++v) buf[L[v]] = x[v];
+            if (last) fence_proxy_async_smem();   // before the tile store reads them
+        }
+        // ---- end of the iteration: one barrier for both tiles
+        tc_fence_before();
+        if (tid == 0) {   // which tiles can start next iteration (published by the barrier)
+            bool any = false;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                long long it = cx[c].it;
+                int s = cx[c].s;
+                if (run[c] && ++s == nst) {
+                    s = 0;
+                    it += 2;
+                }
+                s_ready[c] = (it < my_tiles && s == 0)
+                                 ? (int)mbar_try_wait(&tile_bar[it % NBUF], (uint32_t)((it / NBUF) & 1))
+                                 : 0;
+                any = any || run[c];
+            }
+            if (any) {
+                idle = false;
+            } else if (!idle) {
+                idle = true;
+                idle_t0 = global_ns();
+            } else if (global_ns() - idle_t0 > kWaitLimitNs) {
+                atomicOr(a.err, ERR_TIMEOUT);
+                s_abort = 1;
+            }
+        }
+        // s_abort may be set by the producer warp at any moment: the OR over the
+        // barrier gives every compute thread the same decision
+        const bool stop = sync_compute_or(*reinterpret_cast<volatile int*>(&s_abort) != 0);
+        tc_fence_after();
+        if (stop) {
+            s_abort = 1;
+            break;
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (run[c] && ++cx[c].s == nst) {   // tile done: the producer stores it
+                if (tid == 0) mbar_arrive(&done_bar[cx[c].it % NBUF]);
+                cx[c].s = 0;
+                cx[c].it += 2;
+            }
+        }
+        if (delay1 > 0) --delay1;
+    }
+    if (tid == 0 && s_abort && my_tiles > 0) mbar_wait_bounded(&w_bar, 0u, a.err);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TH_TMEM_COLS)
+                     : "memory");
+}
+
+// ------------------------------------------------ independent-slice passes --
+template <int FORM>
+__global__ void __launch_bounds__(TH_CTA_THREADS, 1)
+    pass_tch_group_kernel(const __grid_constant__ DevPass p, const PassTchArgs a,
+                          const __grid_constant__ TmaTile tma) {
+    constexpr int NBUF = 3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int nst = p.stage_count;
+    unsigned char* wres = base;
+    float2* bufs = reinterpret_cast<float2*>(base + (size_t)nst * TH_W_BYTES);
+    __shared__ uint64_t tile_bar[NBUF], done_bar[NBUF], mma_bar[4], w_bar, stag_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort;
+    __shared__ float redm[TH_THREADS / 32];
+    __shared__ float2 redn[TH_THREADS / 32];
+    __shared__ StageH sst[TH_MAX_STAGES_3BUF];
+    const int tid = threadIdx.x, warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
+    const int quarter = warp & 3, slice = warp >> 2, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(TH_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    load_stage(a.tcs, nst, a.gb0, a.gb1, true, sst, tid, TH_CTA_THREADS);
+    if (tid == 0) {
+        for (int i = 0; i < NBUF; ++i) {
+            mbar_init(&tile_bar[i], 1);
+            mbar_init(&done_bar[i], 4);
+        }
+        for (int i = 0; i < 4; ++i) mbar_init(&mma_bar[i], 1);
+        mbar_init(&w_bar, 1);
+        mbar_init(&stag_bar, 2);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = __shfl_sync(0xffffffffu, tmem_base, 0);
+    const long long first = blockIdx.x, stride = gridDim.x;
+    const long long my_tiles = first < a.total_tiles ? (a.total_tiles - first + stride - 1) / stride : 0;
+    if (warp == TH_PRODUCER_WARP) {
+        tile_mover<NBUF>(p, a, tma, bufs, tile_bar, done_bar, &s_abort, first, stride, my_tiles, lane);
+        tc_fence_before();
+        __syncthreads();
+        return;
+    }
+    if (tid == 0 && my_tiles > 0) {
+        const uint32_t wb = (uint32_t)nst * TH_W_BYTES;
+        mbar_arrive_expect_tx(&w_bar, wb);
+        bulk_g2s(wres, a.wops + (size_t)a.tcs[0].tc_index * TH_W_BYTES, wb, &w_bar);
+    }
+    if (my_tiles > 0 && !mbar_wait_bounded(&w_bar, 0u, a.err)) s_abort = 1;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
+    const uint32_t col = (uint32_t)slice * 128u;
+    uint32_t q = 0;
+    long long it = 0;
+    for (long long t = first; t < a.total_tiles; t += stride, ++it) {
+        const int b = (int)(it % NBUF);
+        float2* buf = bufs + (size_t)b * TH_TILE_ELEMS;
+        const bool tile_ok = mbar_wait_bounded(&tile_bar[b], (uint32_t)((it / NBUF) & 1), a.err);
+        {   // a slice-uniform abort check
+            uint32_t stop;
+            asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+                         "bar.red.or.pred p, %2, 128, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                         : "=r"(stop)
+                         : "r"((uint32_t)(!tile_ok || s_abort)), "r"(1 + slice)
+                         : "memory");
+            if (stop) {
+                s_abort = 1;
+                break;
+            }
+        }
+        // once: slices 0 and 1 start after 2 and 3 have issued their first MMAs, so
+        // the two pairs stay half a stage apart
+        if (it == 0 && slice < 2) mbar_wait_bounded(&stag_bar, 0u, a.err);
+        float sc = 1.f, isc = 1.f, nin = 0.f;
+        for (int s = 0; s < nst; ++s, ++q) {
+            const StageH& S = sst[s];
+            const int tau = (FORM == FORM_ROT && S.nj) ? (tid & 15) >> (4 - S.nj) : 0;
+            int L[16];
+            stage_slots<FORM>(S, group_row(S, tid, a.gb0, a.gb1), tau, L);
+            float2 x[16];
+#pragma unroll
+            for (int v = 0; v < 16; ++v) x[v] = buf[L[v]];
+            if (FORM == FORM_ROT && S.nj) unrotate_h(x, tau, S.nj);
+            if (s == 0) {   // the slice's scale from its largest component
+                const float m = warp_max(row_max(x));
+                if (lane == 0) redm[warp] = m;
+                sync_slice(slice);
+                float mt = 0.f;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) mt = fmaxf(mt, redm[4 * slice + w]);
+                tile_scale(mt, sc, isc);
+#pragma unroll
+                for (int v = 0; v < 16; ++v) x[v] = make_float2(x[v].x * sc, x[v].y * sc);
+                nin = row_norm2(x);
+            }
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int v = 0; v < 16; ++v) split_f16(x[v], hi[v], lo[v]);
+            tc_st16(lane_base + col, hi);
+            tc_st16(lane_base + col + 16u, lo);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            sync_slice(slice);
+            if (quarter == 0 && elect_one()) {
+                tc_fence_after();
+                stage_mmas(tmem + col + 32u, tmem + col, sw128_desc(smem_u32(wres) + (uint32_t)s * TH_W_BYTES));
+                tc_commit(&mma_bar[slice]);
+                if (it == 0 && s == 0 && slice >= 2) mbar_arrive(&stag_bar);
+            }
+            if (!mbar_wait_bounded(&mma_bar[slice], q & 1u, a.err)) s_abort = 1;
+            tc_fence_after();
+            {
+                float y[32];
+                tc_ld32(lane_base + col + 32u, y);
+#pragma unroll
+                for (int v = 0; v < 16; ++v) x[v] = make_float2(y[2 * v], y[2 * v + 1]);
+            }
+            if (s == nst - 1) {   // unscale, restore the slice norm (its rows are closed under the pass)
+                float ni = nin, nout = row_norm2(x);
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    ni += __shfl_xor_sync(0xffffffffu, ni, o);
+                    nout += __shfl_xor_sync(0xffffffffu, nout, o);
+                }
+                if (lane == 0) redn[warp] = make_float2(ni, nout);
+                sync_slice(slice);
+                float ti = 0.f, to = 0.f;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    ti += redn[4 * slice + w].x;
+                    to += redn[4 * slice + w].y;
+                }
+                const float f = norm_factor(a.renorm, ti, to, isc);
+#pragma unroll
+                for (int v = 0; v < 16; ++v) x[v] = make_float2(x[v].x * f, x[v].y * f);
+            }
+            if (FORM == FORM_ROT && S.nj) unrotate_h(x, tau, S.nj);
+#pragma unroll
+            for (int v = 0; v < 16; ++v) buf[L[v]] = x[v];
+            tc_fence_before();
+            sync_slice(slice);
+            tc_fence_after();
+        }
+        fence_proxy_async_smem();   // this thread's tile writes before the tensor store reads them
+        sync_slice(slice);
+        if ((tid & 127) == 0) mbar_arrive(&done_bar[b]);
+    }
+    if (tid == 0 && s_abort && my_tiles > 0) mbar_wait_bounded(&w_bar, 0u, a.err);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TH_TMEM_COLS)
+                     : "memory");
+}
+
+// ------------------------------------------------------------ host side --
+size_t tch_smem_bytes(int nst, int nbuf) {
+    return 1024 + (size_t)nst * TH_W_BYTES + (size_t)nbuf * TH_TILE_BYTES;
+}
+
+template <typename K>
+cudaError_t set_smem(K k, size_t bytes) {
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t set_tch_attributes() {
+    const size_t s3 = tch_smem_bytes(TH_MAX_STAGES_3BUF, 3), s2 = tch_smem_bytes(TH_MAX_STAGES, 2);
+    cudaError_t e = set_smem(pass_tch_lock_kernel<FORM_PLAIN, 3>, s3);
+    if (e == cudaSuccess) e = set_smem(pass_tch_lock_kernel<FORM_ROT, 3>, s3);
+    if (e == cudaSuccess) e = set_smem(pass_tch_lock_kernel<FORM_SWZ, 3>, s3);
+    if (e == cudaSuccess) e = set_smem(pass_tch_lock_kernel<FORM_PLAIN, 2>, s2);
+    if (e == cudaSuccess) e = set_smem(pass_tch_lock_kernel<FORM_ROT, 2>, s2);
+    if (e == cudaSuccess) e = set_smem(pass_tch_lock_kernel<FORM_SWZ, 2>, s2);
+    if (e == cudaSuccess) e = set_smem(pass_tch_group_kernel<FORM_PLAIN>, s3);
+    if (e == cudaSuccess) e = set_smem(pass_tch_group_kernel<FORM_ROT>, s3);
+    if (e == cudaSuccess) e = set_smem(pass_tch_group_kernel<FORM_SWZ>, s3);
+    return e;
+}
+
+// Two tile bits (>= 5) that no stage of pass `pass` touches: b0 | b1 << 8, or -1.
+int free_slice_bits(const DevPlan* dp, int pass) {
+    const DevPass& P = dp->plan.passes[pass];
+    uint32_t U = 0;
+    for (int si = 0; si < P.stage_count; ++si)
+        for (int i = 0; i < 4; ++i) U |= 1u << dp->tcs[P.stage_begin + si].rbit[i];
+    int g1 = -1, g0 = -1;
+    for (int b = TH_TILE_BITS - 1; b >= 5 && g0 < 0; --b)
+        if (!((U >> b) & 1)) {
+            if (g1 < 0) g1 = b;
+            else g0 = b;
+        }
+    return g0 >= 0 ? (g0 | (g1 << 8)) : -1;
+}
+
+}  // namespace
+
+bool pass_tch_eligible(const DevPlan* dp, int pass) {
+    if (!dp->plan.all_unitary || !dp->tc_pass[pass]) return false;
+    const DevPass& P = dp->plan.passes[pass];
+    if (P.m != TH_TILE_BITS || P.stage_count < 1) return false;
+    // the W operands of a pass's stages are consecutive (one bulk copy)
+    for (int si = 1; si < P.stage_count; ++si)
+        if (dp->tcs[P.stage_begin + si].tc_index != dp->tcs[P.stage_begin].tc_index + si) return false;
+    if (free_slice_bits(dp, pass) >= 0 && P.stage_count <= TH_MAX_STAGES_3BUF) return true;
+    return P.stage_count <= TH_MAX_STAGES;
+}
+
+cudaError_t launch_pass_tch(const DevPlan* dp, int pass, int items, const void* wops_h, unsigned* err,
+                            const TmaTile& tma, bool swizzled, float2* state, const long long* item_off,
+                            cudaStream_t s) {
+    const DevPass& P = dp->plan.passes[pass];
+    static bool attr[kMaxDeviceSlots] = {};   // the attribute is per device
+    const int d = device_slot();
+    if (!attr[d]) {
+        cudaError_t e = set_tch_attributes();
+        if (e != cudaSuccess) return e;
+        attr[d] = true;
+    }
+    bool rot = false;   // XOR-rotated slot reads (not needed on a swizzled tile)
+    for (int si = 0; si < P.stage_count; ++si) rot = rot || dp->tcs[P.stage_begin + si].nj > 0;
+    rot = rot && !swizzled;
+    const int form = swizzled ? FORM_SWZ : (rot ? FORM_ROT : FORM_PLAIN);
+    PassTchArgs a{};
+    const int grp = P.stage_count <= TH_MAX_STAGES_3BUF ? free_slice_bits(dp, pass) : -1;
+    a.gb0 = grp >= 0 ? (grp & 255) : 0;
+    a.gb1 = grp >= 0 ? (grp >> 8) : 0;
+    a.renorm = dp->plan.all_unitary ? 1 : 0;
+    a.tcs = dp->d_tcs + P.stage_begin;
+    a.wops = static_cast<const unsigned char*>(wops_h);
+    const long long tpi = 1ll << (dp->plan.n - P.m);
+    a.total_tiles = tpi * items;
+    a.err = err;
+    a.state = state;
+    a.item_off = item_off;
+    a.tc.nchunks = 1 << P.ngather;
+    a.tc.chunk_bytes = (uint32_t)(sizeof(float2) << P.chunk);
+    a.tc.tile_bytes = TH_TILE_BYTES;
+    a.tc.tiles_per_item = tpi;
+    a.tc.tpi_log = dp->plan.n - P.m;
+    a.tc.total_tiles = a.total_tiles;
+    const unsigned grid = (unsigned)std::min<long long>(a.total_tiles, num_sms());
+    const int nst = P.stage_count;
+    if (grp >= 0) {
+        a.tc.nbuf = 3;
+        const size_t sm = tch_smem_bytes(nst, 3);
+        if (form == FORM_SWZ) pass_tch_group_kernel<FORM_SWZ><<<grid, TH_CTA_THREADS, sm, s>>>(P, a, tma);
+        else if (form == FORM_ROT) pass_tch_group_kernel<FORM_ROT><<<grid, TH_CTA_THREADS, sm, s>>>(P, a, tma);
+        else pass_tch_group_kernel<FORM_PLAIN><<<grid, TH_CTA_THREADS, sm, s>>>(P, a, tma);
+    } else if (nst <= TH_MAX_STAGES_3BUF) {
+        a.tc.nbuf = 3;
+        const size_t sm = tch_smem_bytes(nst, 3);
+        if (form == FORM_SWZ) pass_tch_lock_kernel<FORM_SWZ, 3><<<grid, TH_CTA_THREADS, sm, s>>>(P, a, tma);
+        else if (form == FORM_ROT) pass_tch_lock_kernel<FORM_ROT, 3><<<grid, TH_CTA_THREADS, sm, s>>>(P, a, tma);
+        else pass_tch_lock_kernel<FORM_PLAIN, 3><<<grid, TH_CTA_THREADS, sm, s>>>(P, a, tma);
+    } else {
+        a.tc.nbuf = 2;
+        const size_t sm = tch_smem_bytes(nst, 2);
+        if (form == FORM_SWZ) pass_tch_lock_kernel<FORM_SWZ, 2><<<grid, TH_CTA_THREADS, sm, s>>>(P, a, tma);
+        else if (form == FORM_ROT) pass_tch_lock_kernel<FORM_ROT, 2><<<grid, TH_CTA_THREADS, sm, s>>>(P, a, tma);
+        else pass_tch_lock_kernel<FORM_PLAIN, 2><<<grid, TH_CTA_THREADS, sm, s>>>(P, a, tma);
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace tcng

@@ -2,6 +2,7 @@
 // shared-memory and instruction descriptors, MMA issue/commit, TMEM loads.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -25,6 +26,16 @@ __device__ __forceinline__ uint32_t sw128_offset(int row, int kel, int rows) {
     return (uint32_t)kb * (uint32_t)rows * TC_ROWB + (uint32_t)(row >> 3) * 1024u +
            (uint32_t)(row & 7) * TC_ROWB + chunk * 16u + (uint32_t)(kin & 3) * 4u;
 }
+
+// The same layout for 16-bit elements: row `row` of 32 rows, element kh of the
+// row's 64 halves (128 bytes).
+__device__ __forceinline__ uint32_t sw128_offset_h(int row, int kh) {
+    const uint32_t chunk = (uint32_t)((kh >> 3) ^ (row & 7));
+    return (uint32_t)(row >> 3) * 1024u + (uint32_t)(row & 7) * TC_ROWB + chunk * 16u + (uint32_t)(kh & 7) * 2u;
+}
+
+// W operand of one FP16-split register stage: 32 rows x [hi 32 | lo 32] halves.
+constexpr uint32_t TH_W_BYTES = 32 * 128;
 
 __device__ __forceinline__ float tf32_round(float x) {
     uint32_t u = __float_as_uint(x);
@@ -50,6 +61,31 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t smem_addr) {
 // Instruction descriptor, kind::tf32: D f32, A/B tf32, both K-major, M x N.
 __host__ __device__ constexpr uint32_t tf32_idesc(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor, kind::f16: D f32, A/B f16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t f16_idesc(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D (TMEM) += A (TMEM, f16 pairs per column) * B (shared-memory descriptor, f16)
+__device__ __forceinline__ void tc_mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                              int accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+// 16 consecutive 32-bit TMEM columns of this warp's 32 lanes.
+__device__ __forceinline__ void tc_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, int accum) {

@@ -28,7 +28,7 @@ def T():
 
 @pytest.fixture(autouse=True)
 def default_options(T):
-    saved = {o: T.tcng_get_option(o) for o in range(6)}
+    saved = {o: T.tcng_get_option(o) for o in range(8)}
     yield
     for o, v in saved.items():
         T.tcng_set_option(o, v)
@@ -324,9 +324,14 @@ def test_invalid_arguments_are_rejected(T):
     T.tcng_sync_status()
 
 
-def tc_run(T, n, g, p, th, batch=1):
-    """complex64 run with register stages on the tensor cores; returns (state, tc launches)."""
+TC_KERNELS = ("pass_tcs_kernel_c64", "pass_tch_kernel_c64")   # TF32-, FP16-split stages
+
+
+def tc_run(T, n, g, p, th, batch=1, fp16=1, per_kernel=False):
+    """complex64 run with register stages on the tensor cores; returns (state, tc
+    launches) or, with per_kernel, (state, {kernel: launches})."""
     T.tcng_set_option(T.OPT_TENSOR_CORES, 1)
+    T.tcng_set_option(T.OPT_TC_FP16, fp16)
     T.tcng_profile_enable(True)
     T.tcng_profile_read(reset=True)
     try:
@@ -334,22 +339,76 @@ def tc_run(T, n, g, p, th, batch=1):
         prof = T.tcng_profile_read(reset=True)
     finally:
         T.tcng_profile_enable(False)
-    return st, prof.get("pass_tcs_kernel_c64", (0, 0.0))[0]
+    counts = {k: prof.get(k, (0, 0.0))[0] for k in TC_KERNELS}
+    return st, (counts if per_kernel else sum(counts.values()))
 
 
+@pytest.mark.parametrize("fp16", [1, 0])
 @pytest.mark.parametrize("n,depth,width", [(13, 6, 4), (16, 8, 4), (19, 6, 3), (21, 5, 2), (22, 6, 2)])
-def test_tensor_core_stages(T, n, depth, width):
-    """complex64 register stages on the tensor cores vs the oracle and vs the SIMT stages."""
+def test_tensor_core_stages(T, n, depth, width, fp16):
+    """complex64 register stages on the tensor cores (FP16 and TF32 splits) vs the
+    oracle and vs the SIMT stages."""
     c, th = gen.su4_brickwork(n, depth, "RZ", seed=n)
     g, p = c.to_ir()
     ref = sv.apply(n, g, p, th)
     T.tcng_set_option(T.OPT_FUSE_WIDTH, width)
-    st, launches = tc_run(T, n, g, p, th)
-    assert launches > 0
+    st, counts = tc_run(T, n, g, p, th, fp16=fp16, per_kernel=True)
+    assert counts["pass_tch_kernel_c64" if fp16 else "pass_tcs_kernel_c64"] > 0
+    if not fp16:
+        assert counts["pass_tch_kernel_c64"] == 0
     check_state(st.amplitudes(0).cpu().numpy(), ref, "c64")
     T.tcng_set_option(T.OPT_TENSOR_CORES, 0)
     st2 = run(n, g, p, th, "c64")
     check_state(st2.amplitudes(0).cpu().numpy(), ref, "c64")
+
+
+@pytest.mark.parametrize("n,depth,fw", [(15, 6, 2), (18, 10, 2), (20, 8, 2), (16, 12, 4)])
+def test_fp16_passes_every_kernel_form(T, n, depth, fw):
+    """Unitary single-item plans: every tensor-core pass takes the FP16 kernels
+    (independent slices, lock-step with three tile buffers and with two); the state
+    matches the oracle and the TF32 form."""
+    c, th = gen.su4_brickwork(n, depth, "RZ", seed=100 + n)
+    g, p = c.to_ir()
+    ref = sv.apply(n, g, p, th)
+    T.tcng_set_option(T.OPT_FUSE_WIDTH, fw)
+    st, counts = tc_run(T, n, g, p, th, fp16=1, per_kernel=True)
+    assert counts["pass_tch_kernel_c64"] > 0
+    psi = st.amplitudes(0).cpu().numpy()
+    check_state(psi, ref, "c64")
+    st.free()
+    st2, counts2 = tc_run(T, n, g, p, th, fp16=0, per_kernel=True)
+    assert counts2["pass_tch_kernel_c64"] == 0
+    psi2 = st2.amplitudes(0).cpu().numpy()
+    assert relerr(psi, psi2) < 2 * TOL["c64"]
+
+
+@pytest.mark.parametrize("scale_log2", [-70, -20, 0, 30, 60])
+def test_fp16_passes_scaled_states(T, scale_log2):
+    """The FP16 split scales each tile by a power of two: states of any magnitude
+    (here 2^k times a random unit state, far outside FP16's range at both ends) and
+    with a wide spread (an RY product state) come back as the oracle's."""
+    from paper_2602_14167_b300 import StateBatch
+    n = 16
+    c, th = gen.su4_brickwork(n, 6, "RZ", seed=7)
+    g, p = c.to_ir()
+    f = 2.0 ** scale_log2
+    t = np.random.default_rng(9).uniform(-np.pi, np.pi, n)
+    prod = np.ones(1, dtype=np.complex128)
+    for q in range(n):   # qubit q is index bit q
+        prod = np.kron(np.array([np.cos(t[q] / 2), np.sin(t[q] / 2)]), prod)
+    for psi0 in (gen.random_state(n, seed=8) * f, prod * f):
+        T.tcng_set_option(T.OPT_TENSOR_CORES, 1)
+        T.tcng_set_option(T.OPT_TC_FP16, 1)
+        st = StateBatch(n, dtype="c64")
+        st.amplitudes(0).copy_(torch.tensor(psi0, dtype=st.cdtype, device="cuda"))
+        prm = torch.tensor(th, dtype=torch.float64, device="cuda").reshape(1, -1)
+        st.apply(g, p, prm)
+        torch.cuda.synchronize()
+        psi = st.amplitudes(0).cpu().numpy().astype(np.complex128)
+        ref = sv.apply(n, g, p, th, psi=psi0)
+        assert np.all(np.isfinite(psi))
+        assert relerr(psi, ref) < TOL["c64"], relerr(psi, ref)
+        st.free()
 
 
 def test_tensor_core_stages_with_diagonal_and_random_ops(T):
@@ -422,7 +481,8 @@ def test_tensor_core_stages_parameter_free_batch(T):
             st.amplitudes(i).copy_(torch.tensor(psi0[i], dtype=st.cdtype, device="cuda"))
         st.apply(g, p)
         torch.cuda.synchronize()
-        launches = T.tcng_profile_read(reset=True).get("pass_tcs_kernel_c64", (0, 0.0))[0]
+        prof = T.tcng_profile_read(reset=True)
+        launches = sum(prof.get(k, (0, 0.0))[0] for k in TC_KERNELS)
     finally:
         T.tcng_profile_enable(False)
     assert launches > 0

@@ -79,7 +79,8 @@ def qml_run(T, n, layers, B, seed=0, dtype="c64"):
 def test_qml_batch_against_oracle(T, n, layers, B):
     st, g, p, x, probs, prof = qml_run(T, n, layers, B)
     if (B << n) >= (1 << 13) * 148:
-        assert prof.get("pass_tcs_kernel_c64", (0, 0.0))[0] >= 1      # packed tiles on the tensor cores
+        tc = sum(prof.get(k, (0, 0.0))[0] for k in ("pass_tcs_kernel_c64", "pass_tch_kernel_c64"))
+        assert tc >= 1      # packed tiles on the tensor cores
     rng = np.random.default_rng(3)
     picks = sorted({0, B - 1, B // 2} | set(int(i) for i in rng.integers(0, B, 4)))
     for i in picks:
