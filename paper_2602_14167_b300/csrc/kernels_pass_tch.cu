@@ -21,10 +21,10 @@
 // Why: FP16 operands take half the tensor-core time of the TF32 form and half
 // its TMEM traffic, and a row's TMEM share (A hi 16 + A lo 16 + D 32 columns)
 // leaves room for a second tile per 128-row slice:
-//   * lock-step passes (the stages touch every tile bit, so each stage ends in a
-//     barrier of all 512 compute threads) keep two tiles in flight: tile A's
-//     MMAs run while the threads load and split tile B's rows, and tile B's
-//     MMAs run while the threads store tile A's results;
+//   * lock-step passes (the stages touch every tile bit, so every row of a tile
+//     must be written before the next stage reads any) keep two tiles in flight,
+//     each run by its own group of eight warps on its own barrier: one group's
+//     shared-memory phases overlap the other's tensor-core round trips;
 //   * independent-slice passes (two tile bits that no stage touches, so each
 //     slice's 128 rows stay closed under the pass) run one tile per slice, the
 //     slice pairs half a stage apart, as in the TF32 kernel.
@@ -74,22 +74,8 @@ struct PassTchArgs {
     TileCtx tc;
 };
 
-__device__ __forceinline__ void sync_compute() {   // the 512 compute threads
-    asm volatile("bar.sync 5, %0;" ::"n"(TH_THREADS) : "memory");
-}
 __device__ __forceinline__ void sync_slice(int slice) {   // the 128 threads of one slice
     asm volatile("bar.sync %0, %1;" ::"r"(1 + slice), "r"(128) : "memory");
-}
-// Barrier of the 512 compute threads that also ORs a flag over them, so every
-// thread takes the same branch on the result.
-__device__ __forceinline__ bool sync_compute_or(bool flag) {
-    uint32_t r;
-    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
-                 "bar.red.or.pred p, 5, %2, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(r)
-                 : "r"((uint32_t)flag), "n"(TH_THREADS)
-                 : "memory");
-    return r != 0;
 }
 
 // Power-of-two scale c with m*c in [2^7, 2^8) (m >= 0; c and 1/c stay normal).
@@ -278,16 +264,128 @@ __device__ void tile_mover(const DevPass& p, const PassTchArgs& a, const TmaTile
     __syncwarp();
 }
 
-// Per-tile state of one of the two tiles a lock-step CTA keeps in flight.
-struct TileRun {
-    long long it;   // CTA-local tile index (this context runs it, it + 2, it + 4, ...)
-    int s;          // next stage
-    uint32_t mq;    // MMA barrier phases completed
-    float c, ic;    // the tile's scale and its inverse
-    float nin;      // this thread's share of the scaled tile norm before the pass
-};
+// Tile mover for the lock-step kernel, whose two groups finish tiles in either
+// order: buffer b holds tiles b, b + NBUF, b + 2 NBUF, ...; whichever buffer's
+// tile is reported done first is stored first, and the buffer's next tile is
+// loaded once the store has read it.
+template <int NBUF>
+__device__ void tile_mover_any(const DevPass& p, const PassTchArgs& a, const TmaTile& tma, float2* bufs,
+                               uint64_t* tile_bar, uint64_t* done_bar, volatile int* s_abort, long long first,
+                               long long stride, long long my_tiles, int lane) {
+    long long cur[NBUF];   // tile in buffer b, or -1
+    uint32_t ph[NBUF];     // done phases of buffer b seen so far
+    int pending = 0;
+#pragma unroll
+    for (int b = 0; b < NBUF; ++b) {
+        ph[b] = 0;
+        cur[b] = b < my_tiles ? b : -1;
+        if (cur[b] >= 0) {
+            issue_tile_load(a.state, a.item_off, p, a.tc, first + (long long)b * stride,
+                            bufs + (size_t)b * TH_TILE_ELEMS, &tile_bar[b], lane, tma);
+            ++pending;
+        }
+    }
+    unsigned long long t0 = global_ns();
+    uint32_t spins = 0;
+    while (pending > 0) {
+        int hit = -1;
+        if (lane == 0) {
+#pragma unroll
+            for (int b = 0; b < NBUF; ++b)
+                if (hit < 0 && cur[b] >= 0 && mbar_try_wait(&done_bar[b], ph[b] & 1u)) hit = b;
+        }
+        hit = __shfl_sync(0xffffffffu, hit, 0);
+        if (hit < 0) {
+            int stop = 0;
+            if (lane == 0 && (++spins & 255u) == 0) {
+                if (*s_abort) {
+                    stop = 1;
+                } else if (global_ns() - t0 > kWaitLimitNs) {
+                    atomicOr(a.err, ERR_TIMEOUT);
+                    *s_abort = 1;
+                    stop = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, stop, 0)) break;
+            continue;
+        }
+        t0 = global_ns();
+#pragma unroll
+        for (int b = 0; b < NBUF; ++b) {
+            if (b != hit) continue;
+            ++ph[b];
+            issue_tile_store(a.state, a.item_off, p, a.tc, first + cur[b] * stride,
+                             bufs + (size_t)b * TH_TILE_ELEMS, lane, tma);
+            const long long nxt = cur[b] + NBUF;
+            if (nxt < my_tiles) {
+                bulk_wait_read<0>();
+                __syncwarp();
+                issue_tile_load(a.state, a.item_off, p, a.tc, first + nxt * stride,
+                                bufs + (size_t)b * TH_TILE_ELEMS, &tile_bar[b], lane, tma);
+                cur[b] = nxt;
+            } else {
+                cur[b] = -1;
+                --pending;
+            }
+        }
+    }
+    bulk_wait<0>();
+    // after an abort the loads still in flight must land before the shared memory
+    // goes away: each buffer's last load is the tile in cur[b]
+    if (lane == 0)
+        for (int b = 0; b < NBUF; ++b)
+            if (cur[b] >= 0) mbar_wait_bounded(&tile_bar[b], (uint32_t)((cur[b] / NBUF) & 1), a.err);
+    __syncwarp();
+}
+
+// 16 amplitudes of a row from the tile (pairs as 16-byte loads when register
+// bit 0 is tile bit 0: slots v and v + 1 are then adjacent), and back.
+template <int FORM>
+__device__ __forceinline__ void load_row(const float2* buf, const int (&L)[16], bool pairs, float2 (&x)[16]) {
+    if (FORM != FORM_ROT && pairs) {
+#pragma unroll
+        for (int v = 0; v < 16; v += 2) {
+            const float4 q = *reinterpret_cast<const float4*>(buf + L[v]);
+            x[v] = make_float2(q.x, q.y);
+            x[v + 1] = make_float2(q.z, q.w);
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < 16; ++v) x[v] = buf[L[v]];
+    }
+}
+template <int FORM>
+__device__ __forceinline__ void store_row(float2* buf, const int (&L)[16], bool pairs, const float2 (&x)[16]) {
+    if (FORM != FORM_ROT && pairs) {
+#pragma unroll
+        for (int v = 0; v < 16; v += 2)
+            *reinterpret_cast<float4*>(buf + L[v]) = make_float4(x[v].x, x[v].y, x[v + 1].x, x[v + 1].y);
+    } else {
+#pragma unroll
+        for (int v = 0; v < 16; ++v) buf[L[v]] = x[v];
+    }
+}
+
+__device__ __forceinline__ void sync_group(int grp) {   // the 256 threads of one group
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(256) : "memory");
+}
+__device__ __forceinline__ bool sync_group_or(int grp, bool flag) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+                 "bar.red.or.pred p, %2, 256, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(r)
+                 : "r"((uint32_t)flag), "r"(1 + grp)
+                 : "memory");
+    return r != 0;
+}
 
 // ------------------------------------------------------- lock-step passes --
+// The 16 compute warps form two groups of eight; each group runs whole tiles
+// (its tiles are the CTA's tiles G, G + 2, ...) and syncs only on its own
+// barrier, so one group's shared-memory phases overlap the other's tensor-core
+// round trips.  A thread owns two rows of each stage (row blocks 2h and 2h + 1
+// of the tile's four 128-row blocks, h = its warp's half of the group); the
+// group's TMEM is 256 columns: per row block A hi 16 + A lo 16 + D 32.
 template <int FORM, int NBUF>
 __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
     pass_tch_lock_kernel(const __grid_constant__ DevPass p, const PassTchArgs a,
@@ -297,14 +395,14 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
     const int nst = p.stage_count;
     unsigned char* wres = base;   // nst x 4 KiB, every stage's W
     float2* bufs = reinterpret_cast<float2*>(base + (size_t)nst * TH_W_BYTES);
-    __shared__ uint64_t tile_bar[NBUF], done_bar[NBUF], mma_bar[2][4], w_bar;
+    __shared__ uint64_t tile_bar[NBUF], done_bar[NBUF], mma_bar[2], w_bar;
     __shared__ uint32_t tmem_base;
-    __shared__ int s_abort, s_ready[2];
-    __shared__ float redm[2][TH_THREADS / 32];
-    __shared__ float2 redn[2][TH_THREADS / 32];
+    __shared__ int s_abort;
+    __shared__ float redm[2][8];
+    __shared__ float2 redn[2][8];
     __shared__ StageH sst[TH_MAX_STAGES];
     const int tid = threadIdx.x, warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
-    const int quarter = warp & 3, slice = warp >> 2, lane = tid & 31;
+    const int lane = tid & 31;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base)),
@@ -318,12 +416,11 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
             mbar_init(&tile_bar[i], 1);
             mbar_init(&done_bar[i], 1);
         }
-        for (int c = 0; c < 2; ++c)
-            for (int i = 0; i < 4; ++i) mbar_init(&mma_bar[c][i], 1);
+        mbar_init(&mma_bar[0], 1);
+        mbar_init(&mma_bar[1], 1);
         mbar_init(&w_bar, 1);
         fence_mbar_init();
         s_abort = 0;
-        s_ready[0] = s_ready[1] = 0;
     }
     tc_fence_before();
     __syncthreads();
@@ -332,7 +429,7 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
     const long long first = blockIdx.x, stride = gridDim.x;
     const long long my_tiles = first < a.total_tiles ? (a.total_tiles - first + stride - 1) / stride : 0;
     if (warp == TH_PRODUCER_WARP) {
-        tile_mover<NBUF>(p, a, tma, bufs, tile_bar, done_bar, &s_abort, first, stride, my_tiles, lane);
+        tile_mover_any<NBUF>(p, a, tma, bufs, tile_bar, done_bar, &s_abort, first, stride, my_tiles, lane);
         tc_fence_before();
         __syncthreads();
         return;
@@ -343,161 +440,135 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
         bulk_g2s(wres, a.wops + (size_t)a.tcs[0].tc_index * TH_W_BYTES, wb, &w_bar);
     }
     if (my_tiles > 0 && !mbar_wait_bounded(&w_bar, 0u, a.err)) s_abort = 1;
+    const int grp = warp >> 3, gw = warp & 7, quarter = warp & 3, half = gw >> 2;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
-    TileRun cx[2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        cx[c].it = c;
-        cx[c].s = 0;
-        cx[c].mq = 0;
-        cx[c].c = cx[c].ic = 1.f;
-        cx[c].nin = 0.f;
-    }
-    // with two buffers each tile reloads its own buffer: start the second tile
-    // half a pass later so the two tiles' reload waits do not coincide
-    int delay1 = NBUF == 2 ? nst / 2 : 0;
-    bool idle = false;
-    unsigned long long idle_t0 = 0;
-    sync_compute();
-    while (cx[0].it < my_tiles || cx[1].it < my_tiles) {
-        bool run[2];
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-            run[c] = cx[c].it < my_tiles && (cx[c].s > 0 || s_ready[c]) && !(c == 1 && delay1 > 0);
-        // ---- phase A: rows -> FP16 hi/lo -> TMEM, MMAs issued
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            if (!run[c]) continue;
-            const int b = (int)(cx[c].it % NBUF);
-            float2* buf = bufs + (size_t)b * TH_TILE_ELEMS;
-            if (cx[c].s == 0 && !mbar_wait_bounded(&tile_bar[b], (uint32_t)((cx[c].it / NBUF) & 1), a.err))
-                s_abort = 1;
-            const StageH& S = sst[cx[c].s];
-            const int tau = (FORM == FORM_ROT && S.nj) ? (tid & 15) >> (4 - S.nj) : 0;
-            int L[16];
-            stage_slots<FORM>(S, lock_row(S, tid), tau, L);
-            float2 x[16];
-#pragma unroll
-            for (int v = 0; v < 16; ++v) x[v] = buf[L[v]];
-            if (FORM == FORM_ROT && S.nj) unrotate_h(x, tau, S.nj);
-            if (cx[c].s == 0) {   // the tile's scale from its largest component
-                const float m = warp_max(row_max(x));
-                if (lane == 0) redm[c][warp] = m;
-                sync_compute();
-                float mt = 0.f;
-#pragma unroll
-                for (int w = 0; w < TH_THREADS / 32; ++w) mt = fmaxf(mt, redm[c][w]);
-                tile_scale(mt, cx[c].c, cx[c].ic);
-#pragma unroll
-                for (int v = 0; v < 16; ++v) x[v] = make_float2(x[v].x * cx[c].c, x[v].y * cx[c].c);
-                cx[c].nin = row_norm2(x);
-            }
-            uint32_t hi[16], lo[16];
-#pragma unroll
-            for (int v = 0; v < 16; ++v) split_f16(x[v], hi[v], lo[v]);
-            const uint32_t col = (uint32_t)slice * 128u + (uint32_t)c * 64u;
-            tc_st16(lane_base + col, hi);
-            tc_st16(lane_base + col + 16u, lo);
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            tc_fence_before();
-            sync_slice(slice);
-            if (quarter == 0 && elect_one()) {
-                tc_fence_after();
-                stage_mmas(tmem + col + 32u, tmem + col,
-                           sw128_desc(smem_u32(wres) + (uint32_t)cx[c].s * TH_W_BYTES));
-                tc_commit(&mma_bar[c][slice]);
-            }
-        }
-        // ---- phase B: D -> rows (the last stage unscales and restores the norm)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            if (!run[c]) continue;
-            const int b = (int)(cx[c].it % NBUF);
-            float2* buf = bufs + (size_t)b * TH_TILE_ELEMS;
-            if (!mbar_wait_bounded(&mma_bar[c][slice], cx[c].mq & 1u, a.err)) s_abort = 1;
-            ++cx[c].mq;
-            tc_fence_after();
-            const uint32_t col = (uint32_t)slice * 128u + (uint32_t)c * 64u;
-            float2 x[16];
-            {
-                float y[32];
-                tc_ld32(lane_base + col + 32u, y);
-#pragma unroll
-                for (int v = 0; v < 16; ++v) x[v] = make_float2(y[2 * v], y[2 * v + 1]);
-            }
-            const bool last = cx[c].s == nst - 1;
-            if (last) {
-                float nin = cx[c].nin, nout = row_norm2(x);
-#pragma unroll
-                for (int o = 16; o; o >>= 1) {
-                    nin += __shfl_xor_sync(0xffffffffu, nin, o);
-                    nout += __shfl_xor_sync(0xffffffffu, nout, o);
-                }
-                if (lane == 0) redn[c][warp] = make_float2(nin, nout);
-                sync_compute();
-                float ti = 0.f, to = 0.f;
-#pragma unroll
-                for (int w = 0; w < TH_THREADS / 32; ++w) {
-                    ti += redn[c][w].x;
-                    to += redn[c][w].y;
-                }
-                const float f = norm_factor(a.renorm, ti, to, cx[c].ic);
-#pragma unroll
-                for (int v = 0; v < 16; ++v) x[v] = make_float2(x[v].x * f, x[v].y * f);
-            }
-            const StageH& S = sst[cx[c].s];
-            const int tau = (FORM == FORM_ROT && S.nj) ? (tid & 15) >> (4 - S.nj) : 0;
-            if (FORM == FORM_ROT && S.nj) unrotate_h(x, tau, S.nj);
-            int L[16];
-            stage_slots<FORM>(S, lock_row(S, tid), tau, L);
-#pragma unroll
-            for (int v = 0; v < 16; ++v) buf[L[v]] = x[v];
-            if (last) fence_proxy_async_smem();   // before the tile store reads them
-        }
-        // ---- end of the iteration: one barrier for both tiles
-        tc_fence_before();
-        if (tid == 0) {   // which tiles can start next iteration (published by the barrier)
-            bool any = false;
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                long long it = cx[c].it;
-                int s = cx[c].s;
-                if (run[c] && ++s == nst) {
-                    s = 0;
-                    it += 2;
-                }
-                s_ready[c] = (it < my_tiles && s == 0)
-                                 ? (int)mbar_try_wait(&tile_bar[it % NBUF], (uint32_t)((it / NBUF) & 1))
-                                 : 0;
-                any = any || run[c];
-            }
-            if (any) {
-                idle = false;
-            } else if (!idle) {
-                idle = true;
-                idle_t0 = global_ns();
-            } else if (global_ns() - idle_t0 > kWaitLimitNs) {
-                atomicOr(a.err, ERR_TIMEOUT);
-                s_abort = 1;
-            }
-        }
-        // s_abort may be set by the producer warp at any moment: the OR over the
-        // barrier gives every compute thread the same decision
-        const bool stop = sync_compute_or(*reinterpret_cast<volatile int*>(&s_abort) != 0);
-        tc_fence_after();
-        if (stop) {
+    const uint32_t gcol = (uint32_t)grp * 256u;
+    uint32_t q = 0;
+    for (long long it = grp; it < my_tiles; it += 2) {
+        const int b = (int)(it % NBUF);
+        float2* buf = bufs + (size_t)b * TH_TILE_ELEMS;
+        const bool tile_ok = mbar_wait_bounded(&tile_bar[b], (uint32_t)((it / NBUF) & 1), a.err);
+        if (sync_group_or(grp, !tile_ok || *reinterpret_cast<volatile int*>(&s_abort) != 0)) {
             s_abort = 1;
             break;
         }
+        // the tile's scale from its largest component (one extra read of the rows)
+        float sc, isc;
+        {
+            const StageH& S = sst[0];
+            const bool pairs = S.sr[0] == 1;
+            float m = 0.f;
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            if (run[c] && ++cx[c].s == nst) {   // tile done: the producer stores it
-                if (tid == 0) mbar_arrive(&done_bar[cx[c].it % NBUF]);
-                cx[c].s = 0;
-                cx[c].it += 2;
+            for (int k = 0; k < 2; ++k) {
+                const int row = (2 * half + k) * 128 + quarter * 32 + lane;
+                const int tau = (FORM == FORM_ROT && S.nj) ? (row & 15) >> (4 - S.nj) : 0;
+                int L[16];
+                stage_slots<FORM>(S, lock_row(S, row), tau, L);
+                float2 x[16];
+                load_row<FORM>(buf, L, pairs, x);
+                m = fmaxf(m, row_max(x));
             }
+            m = warp_max(m);
+            if (lane == 0) redm[grp][gw] = m;
+            sync_group(grp);
+            float mt = 0.f;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) mt = fmaxf(mt, redm[grp][w]);
+            tile_scale(mt, sc, isc);
         }
-        if (delay1 > 0) --delay1;
+        float nin = 0.f;
+        for (int s = 0; s < nst; ++s, ++q) {
+            const StageH& S = sst[s];
+            const bool pairs = S.sr[0] == 1;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int rb = 2 * half + k;
+                const int row = rb * 128 + quarter * 32 + lane;
+                const int tau = (FORM == FORM_ROT && S.nj) ? (row & 15) >> (4 - S.nj) : 0;
+                int L[16];
+                stage_slots<FORM>(S, lock_row(S, row), tau, L);
+                float2 x[16];
+                load_row<FORM>(buf, L, pairs, x);
+                if (FORM == FORM_ROT && S.nj) unrotate_h(x, tau, S.nj);
+                if (s == 0) {
+#pragma unroll
+                    for (int v = 0; v < 16; ++v) x[v] = make_float2(x[v].x * sc, x[v].y * sc);
+                    nin += row_norm2(x);
+                }
+                uint32_t hi[16], lo[16];
+#pragma unroll
+                for (int v = 0; v < 16; ++v) split_f16(x[v], hi[v], lo[v]);
+                const uint32_t col = gcol + (uint32_t)rb * 64u;
+                tc_st16(lane_base + col, hi);
+                tc_st16(lane_base + col + 16u, lo);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            sync_group(grp);
+            if (gw == 0 && elect_one()) {
+                tc_fence_after();
+                const uint64_t dw = sw128_desc(smem_u32(wres) + (uint32_t)s * TH_W_BYTES);
+#pragma unroll
+                for (int rb = 0; rb < 4; ++rb) {
+                    const uint32_t col = gcol + (uint32_t)rb * 64u;
+                    stage_mmas(tmem + col + 32u, tmem + col, dw);
+                }
+                tc_commit(&mma_bar[grp]);
+            }
+            if (!mbar_wait_bounded(&mma_bar[grp], q & 1u, a.err)) s_abort = 1;
+            tc_fence_after();
+            const bool last = s == nst - 1;
+            float f = 1.f;
+            if (last) {   // the output norm (D read once more below), then unscale and restore
+                float nout = 0.f;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    float y[32];
+                    tc_ld32(lane_base + gcol + (uint32_t)(2 * half + k) * 64u + 32u, y);
+                    float p4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int v = 0; v < 32; ++v) p4[v & 3] = fmaf(y[v], y[v], p4[v & 3]);
+                    nout += (p4[0] + p4[1]) + (p4[2] + p4[3]);
+                }
+                float ni = nin;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    ni += __shfl_xor_sync(0xffffffffu, ni, o);
+                    nout += __shfl_xor_sync(0xffffffffu, nout, o);
+                }
+                if (lane == 0) redn[grp][gw] = make_float2(ni, nout);
+                sync_group(grp);
+                float ti = 0.f, to = 0.f;
+#pragma unroll
+                for (int w = 0; w < 8; ++w) {
+                    ti += redn[grp][w].x;
+                    to += redn[grp][w].y;
+                }
+                f = norm_factor(a.renorm, ti, to, isc);
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int rb = 2 * half + k;
+                const int row = rb * 128 + quarter * 32 + lane;
+                float2 x[16];
+                {
+                    float y[32];
+                    tc_ld32(lane_base + gcol + (uint32_t)rb * 64u + 32u, y);
+#pragma unroll
+                    for (int v = 0; v < 16; ++v) x[v] = make_float2(y[2 * v] * f, y[2 * v + 1] * f);
+                }
+                const int tau = (FORM == FORM_ROT && S.nj) ? (row & 15) >> (4 - S.nj) : 0;
+                if (FORM == FORM_ROT && S.nj) unrotate_h(x, tau, S.nj);
+                int L[16];
+                stage_slots<FORM>(S, lock_row(S, row), tau, L);
+                store_row<FORM>(buf, L, pairs, x);
+            }
+            if (last) fence_proxy_async_smem();   // before the tile store reads them
+            tc_fence_before();
+            sync_group(grp);
+            tc_fence_after();
+        }
+        if ((tid & 255) == 0) mbar_arrive(&done_bar[b]);   // the producer stores it
     }
     if (tid == 0 && s_abort && my_tiles > 0) mbar_wait_bounded(&w_bar, 0u, a.err);
     tc_fence_before();
