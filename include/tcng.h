@@ -446,7 +446,9 @@ tcng_status tcng_autotune_report(char* buf, size_t len);
 /* Synchronise the device and report a device-side error word (ETIMEOUT) if set. */
 tcng_status tcng_sync_status(void);
 
-/* Human-readable summary of the plan a gate list compiles to (thread-local string). */
+/* Human-readable summary of the plan a gate list compiles to (thread-local string):
+ * the plan of a one-item complex64 tcng_apply_circuit under the current options,
+ * or with adjoint != 0 the plan of the adjoint kernel. */
 const char* tcng_describe_plan(int n, const tcng_gate* ops, size_t n_ops, const double* mat_pool,
                                size_t n_mat, int P, int adjoint);
 

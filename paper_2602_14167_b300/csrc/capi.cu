@@ -128,6 +128,18 @@ PlanOptions plan_options(tcng_dtype dt, bool adjoint) {
     o.chunk_bits = std::min(g_opt.chunk_bits, o.tile_bits);
     o.adjoint = adjoint ? 1 : 0;
     o.unfused = g_opt.unfused ? 1 : 0;
+    o.wide = 0;
+    return o;
+}
+
+// Plan options of a tcng_apply_circuit call: 32-amplitude register stages where
+// they save stages when the passes will run on the FP16 tensor-core kernels
+// (complex64, tensor cores and FP16 operands enabled, one W set for every tile:
+// no per-item parameters).
+PlanOptions apply_plan_options(tcng_dtype dt, int batch, int P) {
+    PlanOptions o = plan_options(dt, false);
+    o.wide = (dt == TCNG_C64 && !o.unfused && g_opt.tensor_cores != 0 && g_opt.tc_fp16 &&
+              o.tile_bits == 13 && (P == 0 || batch == 1)) ? 1 : 0;
     return o;
 }
 
@@ -260,7 +272,7 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
                 double2* dtab = static_cast<double2*>(
                     c.scratch("tc_table", sizeof(double2) * std::max(1, pl.table_size) * tab_items));
                 float* w = static_cast<float*>(
-                    c.scratch("tc_w", sizeof(float) * 2048 * (size_t)dp->n_tc * tab_items));
+                    c.scratch("tc_w", sizeof(float) * 2048 * (size_t)std::max(1, dp->n_tc32) * tab_items));
                 if (!dtab || !w) return fail(TCNG_ENOMEM, "tensor-core operand scratch");
                 ProfScope ps("build_stage_w", s);
                 e = launch_build_matrices<double2>(dp->d_bblocks, (int)pl.bblocks.size(), dp->d_bops,
@@ -269,14 +281,14 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
                 if (e == cudaSuccess) e = launch_build_stage_w(dp, dtab, stride, tab_items, w, false, s);
                 // unitary plans whose tiles all share one W set also get the FP16 operands
                 if (e == cudaSuccess && g_opt.tc_fp16 && pl.all_unitary && tab_items == 1) {
-                    void* wh = c.scratch("tc_wh", (size_t)4096 * dp->n_tc);
+                    void* wh = c.scratch("tc_wh", (size_t)dp->wh_bytes);
                     if (!wh) return fail(TCNG_ENOMEM, "tensor-core operand scratch");
                     e = launch_build_stage_w(dp, dtab, stride, 1, wh, true, s);
                     wops_h = wh;
                 }
                 if (e != cudaSuccess) return cuda_fail(e, "tensor-core operand prologue");
                 wops = w;
-                w_stride = per_item ? 2048ll * dp->n_tc : 0;
+                w_stride = per_item ? 2048ll * dp->n_tc32 : 0;
             }
         }
         for (size_t pi = 0; pi < pl.passes.size(); ++pi) {
@@ -302,11 +314,13 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
                     if (e != cudaSuccess) return cuda_fail(e, "tensor-core pass kernel");
                     continue;
                 }
-                ProfScope ps("pass_tcs_kernel_c64", s);
-                e = launch_pass_tcs(dp, (int)pi, items, wops, w_stride, ctx().err, tma, swz,
-                                    reinterpret_cast<float2*>(state), d_item_off, s);
-                if (e != cudaSuccess) return cuda_fail(e, "tensor-core pass kernel");
-                continue;
+                if (!dp->tc5[pi]) {   // TF32 operands: 4-bit stages only
+                    ProfScope ps("pass_tcs_kernel_c64", s);
+                    e = launch_pass_tcs(dp, (int)pi, items, wops, w_stride, ctx().err, tma, swz,
+                                        reinterpret_cast<float2*>(state), d_item_off, s);
+                    if (e != cudaSuccess) return cuda_fail(e, "tensor-core pass kernel");
+                    continue;
+                }
             }
             ProfScope ps(sizeof(C) == 8 ? "pass_kernel_c64" : "pass_kernel_c128", s);
             e = launch_pass<C>(state, d_item_off, items, pl.n, p, pl.stages.data(), dp->d_stages,
@@ -606,7 +620,7 @@ tcng_status tcng_apply_circuit(tcng_state* st, const tcng_gate* ops, size_t n_op
     std::lock_guard<std::mutex> lk(g_mu);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     TCNG_TRY({
-        const PlanOptions o = plan_options(st->dt, false);
+        const PlanOptions o = apply_plan_options(st->dt, st->batch, P);
         // graph key: structure of every size class, options and every device pointer read
         uint64_t key = key_mix(options_key(), 1);
         key = key_mix(key, reinterpret_cast<uintptr_t>(st));
@@ -927,7 +941,8 @@ const char* tcng_describe_plan(int n, const tcng_gate* ops, size_t n_ops, const 
         Plan pl;
         pl.n = n;
         pl.P = P;
-        pl.opt = plan_options(TCNG_C64, adjoint != 0);
+        // the plan a one-item complex64 tcng_apply_circuit would run (or the adjoint's)
+        pl.opt = adjoint ? plan_options(TCNG_C64, true) : apply_plan_options(TCNG_C64, 1, P);
         if (n < 5 && !adjoint) pl.opt.unfused = 1;
         pl.ops = import_ops(n, ops, n_ops, n_mat, P, mat_pool);
         build_plan(pl);

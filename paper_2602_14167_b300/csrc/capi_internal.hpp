@@ -66,8 +66,11 @@ struct DevPlan {
     bool tc_ready = false;
     std::vector<TcsStage> tcs;        // per plan stage
     std::vector<char> tc_pass;        // per pass: 1 = run on the tensor cores
+    std::vector<char> tc5;            // per pass: its stages have 5 register bits (FP16 only)
     std::vector<int> tc_group;        // per pass: slice tile bits (b0 | b1 << 8), -1 = none
-    int n_tc = 0;                     // tensor-core stages (W operands per item)
+    int n_tc = 0;                     // tensor-core stages
+    int n_tc32 = 0;                   // ... with TF32 W operands (4-bit stages; 8 KiB each per item)
+    long long wh_bytes = 0;           // FP16 W operand bytes per item
     TcsStage* d_tcs = nullptr;
     ~DevPlan();
 };
@@ -132,6 +135,7 @@ tcng_status run_graphed(uint64_t key, cudaStream_t s, const std::function<tcng_s
 tcng_status fail(tcng_status s, const std::string& msg);
 tcng_status cuda_fail(cudaError_t e, const char* where);
 PlanOptions plan_options(tcng_dtype dt, bool adjoint);
+PlanOptions apply_plan_options(tcng_dtype dt, int batch, int P);
 DevPlan* get_plan(int n, const tcng_gate* ops, size_t n_ops, const double* pool, size_t n_mat, int P,
                   const PlanOptions& o);
 void* plan_table(DevPlan* dp, size_t elem, int items);

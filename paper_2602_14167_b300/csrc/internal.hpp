@@ -88,17 +88,18 @@ struct DevPass {
 };
 
 // ---- tensor-core register stages ----------------------------------------------
-struct TcsStage {             // one register stage run as a 16x16 GEMM (24 bytes)
-    uint8_t rbit[4];          // tile bit of register bit i (ascending)
+struct TcsStage {             // one register stage run as a 16x16 (32x32) GEMM (28 bytes)
+    uint8_t rbit[5];          // tile bit of register bit i (ascending)
     uint8_t nj;               // register bits 0..nj-1 lie on tile bits 0..3 (XOR-rotated reads)
     uint8_t renorm;           // 1: every gate is unitary, restore the tile norm after the pass
-    uint16_t pad;
+    uint8_t nreg;             // register bits: 4 (16 amplitudes per row) or 5 (32)
     int32_t op_begin;         // the stage's ops (DevOp) for the matrix prologue
     int32_t op_count;
     int32_t mat_begin;        // the pass's matrix window in the item's table
-    int32_t tc_index;         // W operand index, -1: not a tensor-core stage
+    int32_t tc_index;         // TF32 W operand index, -1: not a tensor-core stage
+    int32_t wh_off;           // byte offset of the FP16 W operand (4 KiB, or 16 KiB for 5 bits)
 };
-static_assert(sizeof(TcsStage) == 24, "TcsStage layout");
+static_assert(sizeof(TcsStage) == 28, "TcsStage layout");
 
 // ---- matrix-builder prologue -----------------------------------------------
 struct BuildOp {             // one gate inside a block (40 bytes)
@@ -153,6 +154,8 @@ struct PlanOptions {
     int chunk_bits = 7;          // c (lowest contiguous bits)
     int adjoint = 0;             // parameterised gates stay single blocks
     int unfused = 0;             // one block per gate, no passes
+    int wide = 0;                // 32-amplitude register stages where they save stages
+                                 // (complex64 tensor-core passes with FP16 operands)
 };
 
 struct Plan {

@@ -66,18 +66,21 @@ struct StageSm {            // per-stage constants, shared memory
 
 // ------------------------------------------------------------- prologue --
 // W_s of every tensor-core stage and item: U_s = product of the stage's ops
-// (FP64, from the FP64 matrix table), then the real form, TF32 hi/lo.
-// H: the FP16 form instead (4 KiB per stage): row nn holds [hi | lo] of the 32
-// K values as halves, 128 bytes per row, 128-byte swizzled, for kind::f16.
-template <bool H>
+// (FP64, from the FP64 matrix table; R register bits, so U_s is 2^R x 2^R),
+// then its real form.  TF32 (H false, R = 4): hi/lo as two 32x32 K-major
+// 128-byte-swizzled blocks (8 KiB per stage).  FP16 (H true): R = 4, 32 rows of
+// [hi 32 | lo 32] halves, 128 bytes each (4 KiB); R = 5, the 64 rows as two
+// K blocks of 64 halves, hi then lo, 8 KiB each (16 KiB).
+template <bool H, int R>
 __global__ void build_stage_w_kernel(const TcsStage* __restrict__ tcs, const DevOp* __restrict__ ops,
                                      const double2* __restrict__ table, long long table_stride,
-                                     void* __restrict__ wops_v, int n_tc) {
+                                     void* __restrict__ wops_v, long long w_item_bytes) {
+    constexpr int D = 1 << R;
     const TcsStage S = tcs[blockIdx.x];
-    if (S.tc_index < 0) return;
+    if (S.nreg != R || (H ? S.wh_off < 0 : S.tc_index < 0)) return;
     const int item = blockIdx.y;
-    __shared__ double2 U[16][16];
-    const int tid = threadIdx.x, r = tid >> 4, c = tid & 15;
+    __shared__ double2 U[D][D];
+    const int tid = threadIdx.x, r = tid >> R, c = tid & (D - 1);
     U[r][c] = make_double2(r == c ? 1.0 : 0.0, 0.0);
     __syncthreads();
     const double2* tab = table + (long long)item * table_stride + S.mat_begin;
@@ -86,25 +89,31 @@ __global__ void build_stage_w_kernel(const TcsStage* __restrict__ tcs, const Dev
         const double2* M = tab + op.mat;
         double2 nv;
         if (op.kind == K_DENSE) {
-            const int D = 1 << op.k, mask = op.mask;
+            const int Dk = 1 << op.k, mask = op.mask;
             int lr = 0, j = 0;   // local index of row r
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < R; ++i)
                 if ((mask >> i) & 1) lr |= ((r >> i) & 1) << j++;
             nv = make_double2(0.0, 0.0);
-            for (int l = 0; l < D; ++l) {
+            for (int l = 0; l < Dk; ++l) {
                 int rr = r & ~mask, jj = 0;
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < R; ++i)
                     if ((mask >> i) & 1) rr |= ((l >> jj++) & 1) << i;
-                const double2 m = M[lr * D + l], u = U[rr][c];
+                const double2 m = M[lr * Dk + l], u = U[rr][c];
                 nv.x += m.x * u.x - m.y * u.y;
                 nv.y += m.x * u.y + m.y * u.x;
             }
         } else {
-            const int nib = op.mask | (op.pad << 8);
-            int idx = 0;
-            for (int i = 0; i < 4; ++i) {
-                const int jj = (nib >> (4 * i)) & 15;
-                if (jj) idx |= ((r >> i) & 1) << (jj - 1);
+            int idx = 0;   // diagonal index of row r: source j's bit of r
+            if (R == 4) {
+                const int nib = op.mask | (op.pad << 8);
+                for (int i = 0; i < 4; ++i) {
+                    const int jj = (nib >> (4 * i)) & 15;
+                    if (jj) idx |= ((r >> i) & 1) << (jj - 1);
+                }
+            } else {
+                for (int j = 0; j < op.k; ++j)
+                    for (int i = 0; i < R; ++i)
+                        if (S.rbit[i] == op.src[j]) idx |= ((r >> i) & 1) << j;
             }
             const double2 d = M[idx], u = U[r][c];
             nv = make_double2(d.x * u.x - d.y * u.y, d.x * u.y + d.y * u.x);
@@ -115,18 +124,23 @@ __global__ void build_stage_w_kernel(const TcsStage* __restrict__ tcs, const Dev
     }
     // B operand row nn = output real 2j+b, column kk = input real 2l+a:
     // W[kk][nn] of  y_j = sum_l U[j][l] x_l  in (re, im) pairs.
-    const uint32_t wbytes = H ? TH_W_BYTES : TS_W_BYTES;
-    unsigned char* out = static_cast<unsigned char*>(wops_v) + ((long long)item * n_tc + S.tc_index) * wbytes;
-    for (int e = tid; e < 32 * 32; e += blockDim.x) {
-        const int nn = e >> 5, kk = e & 31;
+    unsigned char* out = static_cast<unsigned char*>(wops_v) + (long long)item * w_item_bytes +
+                         (H ? (long long)S.wh_off : (long long)S.tc_index * TS_W_BYTES);
+    for (int e = tid; e < 4 * D * D; e += blockDim.x) {
+        const int nn = e >> (R + 1), kk = e & (2 * D - 1);
         const int j = nn >> 1, b = nn & 1, l = kk >> 1, a = kk & 1;
         const double2 u = U[j][l];
         const double w = (a == b) ? u.x : (a ? -u.y : u.y);
         if (H) {   // hi = w rounded to FP16, lo = the rest rounded to FP16
             const __half h = __double2half(w);
             const __half lo = __double2half(w - (double)__half2float(h));
-            *reinterpret_cast<__half*>(out + sw128_offset_h(nn, kk)) = h;
-            *reinterpret_cast<__half*>(out + sw128_offset_h(nn, 32 + kk)) = lo;
+            if (R == 4) {
+                *reinterpret_cast<__half*>(out + sw128_offset_h(nn, kk)) = h;
+                *reinterpret_cast<__half*>(out + sw128_offset_h(nn, 32 + kk)) = lo;
+            } else {
+                *reinterpret_cast<__half*>(out + sw128_offset_h(nn, kk)) = h;
+                *reinterpret_cast<__half*>(out + 8192 + sw128_offset_h(nn, kk)) = lo;
+            }
         } else {
             const float h = tf32_round((float)w);
             const uint32_t off = sw128_offset(nn, kk, 32);
@@ -611,36 +625,48 @@ static void launch_pass_tcs_cfg(bool rot, bool swizzled, unsigned grid, const De
 }
 
 // Which passes run their stages on the tensor cores, and the per-stage data.
+// A pass qualifies when every stage has 4 register bits (TF32 or FP16 operands)
+// or every stage has 5 (FP16 only) and each diagonal op reads only register bits.
 void plan_tensor_stages(DevPlan* dp) {
     if (dp->tc_ready) return;
     Plan& pl = dp->plan;
     dp->tcs.assign(pl.stages.size(), TcsStage{});
-    for (auto& s : dp->tcs) s.tc_index = -1;
+    for (auto& s : dp->tcs) {
+        s.tc_index = -1;
+        s.wh_off = -1;
+    }
     dp->tc_pass.assign(pl.passes.size(), 0);
+    dp->tc5.assign(pl.passes.size(), 0);
     dp->tc_group.assign(pl.passes.size(), -1);
     dp->n_tc = 0;
+    dp->n_tc32 = 0;
+    dp->wh_bytes = 0;
     if (!pl.opt.unfused && !pl.opt.adjoint) {
         for (size_t pi = 0; pi < pl.passes.size(); ++pi) {
             const DevPass& P = pl.passes[pi];
             bool ok = P.m == TS_TILE_BITS && P.stage_count > 0 && P.stage_count <= TS_MAX_STAGES;
+            const int R = ok ? pl.stages[P.stage_begin].nreg : 0;
+            ok = ok && (R == 4 || (R == 5 && pl.all_unitary));
             for (int si = 0; ok && si < P.stage_count; ++si) {
                 const DevStage& st = pl.stages[P.stage_begin + si];
-                if (st.nreg != 4) ok = false;
+                if (st.nreg != R) ok = false;
                 for (uint32_t oi = 0; ok && oi < st.op_count; ++oi) {
                     const DevOp& o = pl.dops[st.op_begin + oi];
-                    if (o.kind == K_DIAG) {   // foldable only if every source is a register bit
-                        const int nib = o.mask | (o.pad << 8);
-                        int srcs = 0;
-                        for (int i = 0; i < 4; ++i) srcs += ((nib >> (4 * i)) & 15) ? 1 : 0;
-                        if (srcs != o.k) ok = false;
+                    if (o.kind != K_DIAG) continue;
+                    // foldable only if every source is a register bit
+                    for (int j = 0; ok && j < o.k; ++j) {
+                        bool reg = false;
+                        for (int i = 0; i < R; ++i) reg = reg || st.rbit[i] == o.src[j];
+                        ok = reg;
                     }
                 }
             }
             if (!ok) continue;
             dp->tc_pass[pi] = 1;
+            dp->tc5[pi] = R == 5 ? 1 : 0;
             // two tile bits that no stage of the pass touches (>= 5, so the lanes keep the
             // low bits): rows with fixed values of them never leave their 128-row slice
-            {
+            if (R == 4) {
                 uint32_t U = 0;
                 for (int si = 0; si < P.stage_count; ++si)
                     for (int i = 0; i < 4; ++i) U |= 1u << pl.stages[P.stage_begin + si].rbit[i];
@@ -656,16 +682,20 @@ void plan_tensor_stages(DevPlan* dp) {
                 const DevStage& st = pl.stages[P.stage_begin + si];
                 TcsStage& t = dp->tcs[P.stage_begin + si];
                 int nj = 0;
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < R; ++i) {
                     t.rbit[i] = st.rbit[i];
                     if (st.rbit[i] < 4) ++nj;
                 }
                 t.nj = (uint8_t)nj;
+                t.nreg = (uint8_t)R;
                 t.renorm = pl.all_unitary ? 1 : 0;
                 t.op_begin = (int32_t)st.op_begin;
                 t.op_count = (int32_t)st.op_count;
                 t.mat_begin = P.mat_begin;
-                t.tc_index = dp->n_tc++;
+                if (R == 4) t.tc_index = dp->n_tc32++;
+                t.wh_off = (int32_t)dp->wh_bytes;
+                dp->wh_bytes += R == 5 ? 4 * TH_W_BYTES : TH_W_BYTES;
+                ++dp->n_tc;
             }
         }
     }
@@ -677,11 +707,22 @@ cudaError_t launch_build_stage_w(const DevPlan* dp, const double2* table, long l
                                  int items, void* wops, bool half, cudaStream_t s) {
     if (!dp->n_tc) return cudaSuccess;
     dim3 grid((unsigned)dp->tcs.size(), (unsigned)items);
-    if (half)
-        build_stage_w_kernel<true><<<grid, 256, 0, s>>>(dp->d_tcs, dp->d_dops, table, table_stride, wops, dp->n_tc);
-    else
-        build_stage_w_kernel<false><<<grid, 256, 0, s>>>(dp->d_tcs, dp->d_dops, table, table_stride, wops, dp->n_tc);
-    count_launch();
+    if (half) {
+        build_stage_w_kernel<true, 4><<<grid, 256, 0, s>>>(dp->d_tcs, dp->d_dops, table, table_stride, wops,
+                                                           dp->wh_bytes);
+        count_launch();
+        bool any5 = false;
+        for (char c : dp->tc5) any5 = any5 || c;
+        if (any5) {
+            build_stage_w_kernel<true, 5><<<grid, 1024, 0, s>>>(dp->d_tcs, dp->d_dops, table, table_stride, wops,
+                                                                dp->wh_bytes);
+            count_launch();
+        }
+    } else if (dp->n_tc32) {
+        build_stage_w_kernel<false, 4><<<grid, 256, 0, s>>>(dp->d_tcs, dp->d_dops, table, table_stride, wops,
+                                                            (long long)dp->n_tc32 * TS_W_BYTES);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 

@@ -53,13 +53,15 @@ constexpr uint32_t TH_TILE_BYTES = sizeof(float2) << TH_TILE_BITS;   // 64 KiB
 constexpr uint32_t TH_TMEM_COLS = 512;             // 4 slices x 2 tiles x (A hi 16 + A lo 16 + D 32)
 constexpr int TH_MAX_STAGES = 22;                  // stages per pass (W of all resident)
 constexpr int TH_MAX_STAGES_3BUF = 7;              // with three tile buffers
+constexpr int TH_MAX_STAGES_5 = 2;                 // 32-amplitude stages (16 KiB W each)
 constexpr int FORM_PLAIN = 0, FORM_ROT = 1, FORM_SWZ = 2;
 
 struct StageH {             // per-stage constants, shared memory (64 bytes)
     int sr[4];              // 1 << register tile bit i
     int hm[6];              // ~((1 << b) - 1) for the bits the row index skips (ascending)
     int nj;                 // register bits on tile bits 0..3
-    int pad[5];
+    int sr4;                // 32-amplitude stages: 1 << register tile bit 4
+    int pad[4];
 };
 
 struct PassTchArgs {
@@ -153,19 +155,26 @@ __device__ __forceinline__ int group_row(const StageH& S, int tid, int gb0, int 
     return g | (((tid >> 7) & 1) << gb0) | (((tid >> 8) & 1) << gb1);
 }
 
+// Stage constants: the row index skips the register bits and, in passes with
+// fixed tile bits per slice (or row block), those bits (gb0 only when gb1 < 0).
 __device__ __forceinline__ void load_stage(const TcsStage* tcs, int nst, int gb0, int gb1, bool grouped,
                                            StageH* sst, int tid, int nthreads) {
     for (int i = tid; i < nst; i += nthreads) {
         const TcsStage S = tcs[i];
         StageH d;
-        int skip[6], ns = 0;
+        int skip[7], ns = 0;
         for (int r = 0; r < 4; ++r) {
             d.sr[r] = 1 << S.rbit[r];
             skip[ns++] = S.rbit[r];
         }
+        d.sr4 = 0;
+        if (S.nreg == 5) {
+            d.sr4 = 1 << S.rbit[4];
+            skip[ns++] = S.rbit[4];
+        }
         if (grouped) {
             skip[ns++] = gb0;
-            skip[ns++] = gb1;
+            if (gb1 >= 0) skip[ns++] = gb1;
         }
         for (int x = 1; x < ns; ++x)
             for (int y = x; y > 0 && skip[y - 1] > skip[y]; --y) {
@@ -175,7 +184,7 @@ __device__ __forceinline__ void load_stage(const TcsStage* tcs, int nst, int gb0
             }
         for (int k = 0; k < 6; ++k) d.hm[k] = k < ns ? ~((1 << skip[k]) - 1) : 0;
         d.nj = S.nj;
-        for (int k = 0; k < 5; ++k) d.pad[k] = 0;
+        for (int k = 0; k < 4; ++k) d.pad[k] = 0;
         sst[i] = d;
     }
 }
@@ -270,8 +279,9 @@ __device__ void tile_mover(const DevPass& p, const PassTchArgs& a, const TmaTile
 // loaded once the store has read it.
 template <int NBUF>
 __device__ void tile_mover_any(const DevPass& p, const PassTchArgs& a, const TmaTile& tma, float2* bufs,
-                               uint64_t* tile_bar, uint64_t* done_bar, volatile int* s_abort, long long first,
-                               long long stride, long long my_tiles, int lane) {
+                               uint64_t* tile_bar, uint64_t* done_bar, volatile int* s_abort,
+                               volatile long long* s_issued, long long first, long long stride,
+                               long long my_tiles, int lane) {
     long long cur[NBUF];   // tile in buffer b, or -1
     uint32_t ph[NBUF];     // done phases of buffer b seen so far
     int pending = 0;
@@ -282,6 +292,7 @@ __device__ void tile_mover_any(const DevPass& p, const PassTchArgs& a, const Tma
         if (cur[b] >= 0) {
             issue_tile_load(a.state, a.item_off, p, a.tc, first + (long long)b * stride,
                             bufs + (size_t)b * TH_TILE_ELEMS, &tile_bar[b], lane, tma);
+            if (lane == 0) s_issued[b] = b;
             ++pending;
         }
     }
@@ -322,6 +333,7 @@ __device__ void tile_mover_any(const DevPass& p, const PassTchArgs& a, const Tma
                 __syncwarp();
                 issue_tile_load(a.state, a.item_off, p, a.tc, first + nxt * stride,
                                 bufs + (size_t)b * TH_TILE_ELEMS, &tile_bar[b], lane, tma);
+                if (lane == 0) s_issued[b] = nxt;
                 cur[b] = nxt;
             } else {
                 cur[b] = -1;
@@ -336,6 +348,25 @@ __device__ void tile_mover_any(const DevPass& p, const PassTchArgs& a, const Tma
         for (int b = 0; b < NBUF; ++b)
             if (cur[b] >= 0) mbar_wait_bounded(&tile_bar[b], (uint32_t)((cur[b] / NBUF) & 1), a.err);
     __syncwarp();
+}
+
+// Wait until the tile mover has issued the load of tile `it` into its buffer.
+// A buffer's tiles alternate between the two tile slots, so a slot can reach
+// its next tile while the buffer's previous load (the other slot's tile) has not
+// landed yet: its mbarrier is then two phases behind and a parity wait would
+// pass on the older phase.  Once the load of `it` is issued, the previous one
+// has been consumed, so the parity wait that follows is exact.
+__device__ __forceinline__ bool wait_issued(volatile long long* s_issued, long long it, unsigned* err) {
+    if (*s_issued == it) return true;
+    const unsigned long long t0 = global_ns();
+    for (uint32_t k = 1;; ++k) {
+        __nanosleep(32);
+        if (*s_issued == it) return true;
+        if ((k & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
+            atomicOr(err, ERR_TIMEOUT);
+            return false;
+        }
+    }
 }
 
 // 16 amplitudes of a row from the tile (pairs as 16-byte loads when register
@@ -396,6 +427,7 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
     unsigned char* wres = base;   // nst x 4 KiB, every stage's W
     float2* bufs = reinterpret_cast<float2*>(base + (size_t)nst * TH_W_BYTES);
     __shared__ uint64_t tile_bar[NBUF], done_bar[NBUF], mma_bar[2], w_bar;
+    __shared__ long long s_issued[NBUF];
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
     __shared__ float redm[2][8];
@@ -415,6 +447,7 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
         for (int i = 0; i < NBUF; ++i) {
             mbar_init(&tile_bar[i], 1);
             mbar_init(&done_bar[i], 1);
+            s_issued[i] = -1;
         }
         mbar_init(&mma_bar[0], 1);
         mbar_init(&mma_bar[1], 1);
@@ -429,7 +462,8 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
     const long long first = blockIdx.x, stride = gridDim.x;
     const long long my_tiles = first < a.total_tiles ? (a.total_tiles - first + stride - 1) / stride : 0;
     if (warp == TH_PRODUCER_WARP) {
-        tile_mover_any<NBUF>(p, a, tma, bufs, tile_bar, done_bar, &s_abort, first, stride, my_tiles, lane);
+        tile_mover_any<NBUF>(p, a, tma, bufs, tile_bar, done_bar, &s_abort, s_issued, first, stride, my_tiles,
+                             lane);
         tc_fence_before();
         __syncthreads();
         return;
@@ -437,7 +471,7 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
     if (tid == 0 && my_tiles > 0) {   // every stage's W: one bulk copy (consecutive operands)
         const uint32_t wb = (uint32_t)nst * TH_W_BYTES;
         mbar_arrive_expect_tx(&w_bar, wb);
-        bulk_g2s(wres, a.wops + (size_t)a.tcs[0].tc_index * TH_W_BYTES, wb, &w_bar);
+        bulk_g2s(wres, a.wops + a.tcs[0].wh_off, wb, &w_bar);
     }
     if (my_tiles > 0 && !mbar_wait_bounded(&w_bar, 0u, a.err)) s_abort = 1;
     const int grp = warp >> 3, gw = warp & 7, quarter = warp & 3, half = gw >> 2;
@@ -447,7 +481,8 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
     for (long long it = grp; it < my_tiles; it += 2) {
         const int b = (int)(it % NBUF);
         float2* buf = bufs + (size_t)b * TH_TILE_ELEMS;
-        const bool tile_ok = mbar_wait_bounded(&tile_bar[b], (uint32_t)((it / NBUF) & 1), a.err);
+        const bool tile_ok = wait_issued(&s_issued[b], it, a.err) &&
+                             mbar_wait_bounded(&tile_bar[b], (uint32_t)((it / NBUF) & 1), a.err);
         if (sync_group_or(grp, !tile_ok || *reinterpret_cast<volatile int*>(&s_abort) != 0)) {
             s_abort = 1;
             break;
@@ -632,7 +667,7 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
     if (tid == 0 && my_tiles > 0) {
         const uint32_t wb = (uint32_t)nst * TH_W_BYTES;
         mbar_arrive_expect_tx(&w_bar, wb);
-        bulk_g2s(wres, a.wops + (size_t)a.tcs[0].tc_index * TH_W_BYTES, wb, &w_bar);
+        bulk_g2s(wres, a.wops + a.tcs[0].wh_off, wb, &w_bar);
     }
     if (my_tiles > 0 && !mbar_wait_bounded(&w_bar, 0u, a.err)) s_abort = 1;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
@@ -741,9 +776,229 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
                      : "memory");
 }
 
+// ------------------------------------------- 32-amplitude (5-bit) stages --
+// A stage of 5 register bits is the real GEMM [256 rows x 64] . [64 x 64] per
+// tile.  The tile bit gb (>= 5, untouched by every stage of the pass) splits the
+// rows into two 128-row blocks that stay closed under the pass.  The CTA keeps
+// two tiles in flight (slots 0 and 1 run the CTA's tiles 0, 2, 4, ... and 1, 3,
+// 5, ...), so its four chains of four warps each run one row block of one tile
+// on their own barrier; a thread owns one row and takes its 32 amplitudes in
+// two halves.  TMEM per chain: A hi 32 + A lo 32 + D 64 columns.  W (64 rows, K
+// blocks of 64 halves: hi, lo) is 16 KiB per stage, every stage resident (at
+// most two, with three tile buffers).
+__device__ __forceinline__ void sync_chain(int c) {   // the 128 threads of one chain
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + c), "r"(128) : "memory");
+}
+__device__ __forceinline__ bool sync_chain_or(int c, bool flag) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+                 "bar.red.or.pred p, %2, 128, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(r)
+                 : "r"((uint32_t)flag), "r"(1 + c)
+                 : "memory");
+    return r != 0;
+}
+
+__global__ void __launch_bounds__(TH_CTA_THREADS, 1)
+    pass_tch5_kernel(const __grid_constant__ DevPass p, const PassTchArgs a,
+                     const __grid_constant__ TmaTile tma) {
+    constexpr int NBUF = 3;
+    constexpr uint32_t W5 = 4 * TH_W_BYTES;   // 16 KiB
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int nst = p.stage_count;
+    unsigned char* wres = base;
+    float2* bufs = reinterpret_cast<float2*>(base + (size_t)nst * W5);
+    __shared__ uint64_t tile_bar[NBUF], done_bar[NBUF], mma_bar[4], w_bar, stag_bar[2];
+    __shared__ long long s_issued[NBUF];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort;
+    __shared__ float redm[4][4];
+    __shared__ float2 redn[4][4];
+    __shared__ StageH sst[TH_MAX_STAGES_5];
+    const int tid = threadIdx.x, warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
+    const int lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(TH_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    load_stage(a.tcs, nst, a.gb0, -1, true, sst, tid, TH_CTA_THREADS);
+    if (tid == 0) {
+        for (int i = 0; i < NBUF; ++i) {
+            mbar_init(&tile_bar[i], 1);
+            mbar_init(&done_bar[i], 2);
+            s_issued[i] = -1;
+        }
+        for (int i = 0; i < 4; ++i) mbar_init(&mma_bar[i], 1);
+        mbar_init(&w_bar, 1);
+        mbar_init(&stag_bar[0], 1);
+        mbar_init(&stag_bar[1], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = __shfl_sync(0xffffffffu, tmem_base, 0);
+    const long long first = blockIdx.x, stride = gridDim.x;
+    const long long my_tiles = first < a.total_tiles ? (a.total_tiles - first + stride - 1) / stride : 0;
+    if (warp == TH_PRODUCER_WARP) {
+        tile_mover_any<NBUF>(p, a, tma, bufs, tile_bar, done_bar, &s_abort, s_issued, first, stride, my_tiles,
+                             lane);
+        tc_fence_before();
+        __syncthreads();
+        return;
+    }
+    if (tid == 0 && my_tiles > 0) {
+        const uint32_t wb = (uint32_t)nst * W5;
+        mbar_arrive_expect_tx(&w_bar, wb);
+        bulk_g2s(wres, a.wops + a.tcs[0].wh_off, wb, &w_bar);
+    }
+    if (my_tiles > 0 && !mbar_wait_bounded(&w_bar, 0u, a.err)) s_abort = 1;
+    const int chain = warp >> 2, slot = chain >> 1, rb = chain & 1, quarter = warp & 3;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
+    const uint32_t col = (uint32_t)chain * 128u;
+    const int r7 = quarter * 32 + lane;   // this thread's row within its block
+    uint32_t q = 0;
+    for (long long it = slot; it < my_tiles; it += 2) {
+        const int b = (int)(it % NBUF);
+        float2* buf = bufs + (size_t)b * TH_TILE_ELEMS;
+        const bool tile_ok = wait_issued(&s_issued[b], it, a.err) &&
+                             mbar_wait_bounded(&tile_bar[b], (uint32_t)((it / NBUF) & 1), a.err);
+        if (sync_chain_or(chain, !tile_ok || *reinterpret_cast<volatile int*>(&s_abort) != 0)) {
+            s_abort = 1;
+            break;
+        }
+        // once per slot: block 0 starts after block 1 has issued its first MMAs
+        if (it == slot && rb == 0) mbar_wait_bounded(&stag_bar[slot], 0u, a.err);
+        float sc = 1.f, isc = 1.f, nin = 0.f;
+        for (int s = 0; s < nst; ++s, ++q) {
+            const StageH& S = sst[s];
+            int g = r7;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) g += g & S.hm[i];
+            g |= rb << a.gb0;
+            if (s == 0) {   // the block's scale from its largest component
+                float m = 0.f;
+#pragma unroll
+                for (int ch = 0; ch < 2; ++ch) {
+                    int L[16];
+                    stage_slots<FORM_PLAIN>(S, ch ? (g | S.sr4) : g, 0, L);
+                    float2 x[16];
+                    load_row<FORM_PLAIN>(buf, L, false, x);
+                    m = fmaxf(m, row_max(x));
+                }
+                m = warp_max(m);
+                if (lane == 0) redm[chain][quarter] = m;
+                sync_chain(chain);
+                float mt = 0.f;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) mt = fmaxf(mt, redm[chain][w]);
+                tile_scale(mt, sc, isc);
+            }
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch) {
+                int L[16];
+                stage_slots<FORM_PLAIN>(S, ch ? (g | S.sr4) : g, 0, L);
+                float2 x[16];
+                load_row<FORM_PLAIN>(buf, L, false, x);
+                if (s == 0) {
+#pragma unroll
+                    for (int v = 0; v < 16; ++v) x[v] = make_float2(x[v].x * sc, x[v].y * sc);
+                    nin += row_norm2(x);
+                }
+                uint32_t hi[16], lo[16];
+#pragma unroll
+                for (int v = 0; v < 16; ++v) split_f16(x[v], hi[v], lo[v]);
+                tc_st16(lane_base + col + 16u * ch, hi);
+                tc_st16(lane_base + col + 32u + 16u * ch, lo);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            sync_chain(chain);
+            if (quarter == 0 && elect_one()) {
+                tc_fence_after();
+                constexpr uint32_t idesc = f16_idesc(128, 64);
+                const uint64_t dw = sw128_desc(smem_u32(wres) + (uint32_t)s * W5);
+                const uint32_t d = tmem + col + 64u, ah = tmem + col, al = tmem + col + 32u;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) tc_mma_f16_ts(d, al + 8u * j, dw + 2u * j, idesc, j);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) tc_mma_f16_ts(d, ah + 8u * j, dw + 512u + 2u * j, idesc, 1);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) tc_mma_f16_ts(d, ah + 8u * j, dw + 2u * j, idesc, 1);
+                tc_commit(&mma_bar[chain]);
+                if (it == slot && s == 0 && rb == 1) mbar_arrive(&stag_bar[slot]);
+            }
+            if (!mbar_wait_bounded(&mma_bar[chain], q & 1u, a.err)) s_abort = 1;
+            tc_fence_after();
+            float f = 1.f;
+            if (s == nst - 1) {   // unscale, restore the block norm (its rows are closed under the pass)
+                float nout = 0.f;
+#pragma unroll
+                for (int ch = 0; ch < 2; ++ch) {
+                    float y[32];
+                    tc_ld32(lane_base + col + 64u + 32u * ch, y);
+                    float p4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int v = 0; v < 32; ++v) p4[v & 3] = fmaf(y[v], y[v], p4[v & 3]);
+                    nout += (p4[0] + p4[1]) + (p4[2] + p4[3]);
+                }
+                float ni = nin;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    ni += __shfl_xor_sync(0xffffffffu, ni, o);
+                    nout += __shfl_xor_sync(0xffffffffu, nout, o);
+                }
+                if (lane == 0) redn[chain][quarter] = make_float2(ni, nout);
+                sync_chain(chain);
+                float ti = 0.f, to = 0.f;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    ti += redn[chain][w].x;
+                    to += redn[chain][w].y;
+                }
+                f = norm_factor(a.renorm, ti, to, isc);
+            }
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch) {
+                float2 x[16];
+                {
+                    float y[32];
+                    tc_ld32(lane_base + col + 64u + 32u * ch, y);
+#pragma unroll
+                    for (int v = 0; v < 16; ++v) x[v] = make_float2(y[2 * v] * f, y[2 * v + 1] * f);
+                }
+                int L[16];
+                stage_slots<FORM_PLAIN>(S, ch ? (g | S.sr4) : g, 0, L);
+                store_row<FORM_PLAIN>(buf, L, false, x);
+            }
+            tc_fence_before();
+            sync_chain(chain);
+            tc_fence_after();
+        }
+        fence_proxy_async_smem();   // this thread's tile writes before the tensor store reads them
+        sync_chain(chain);
+        if ((tid & 127) == 0) mbar_arrive(&done_bar[b]);
+    }
+    if (tid == 0 && s_abort && my_tiles > 0) mbar_wait_bounded(&w_bar, 0u, a.err);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TH_TMEM_COLS)
+                     : "memory");
+}
+
 // ------------------------------------------------------------ host side --
 size_t tch_smem_bytes(int nst, int nbuf) {
     return 1024 + (size_t)nst * TH_W_BYTES + (size_t)nbuf * TH_TILE_BYTES;
+}
+size_t tch5_smem_bytes(int nst) {
+    return 1024 + (size_t)nst * 4 * TH_W_BYTES + 3 * (size_t)TH_TILE_BYTES;
 }
 
 template <typename K>
@@ -762,7 +1017,19 @@ cudaError_t set_tch_attributes() {
     if (e == cudaSuccess) e = set_smem(pass_tch_group_kernel<FORM_PLAIN>, s3);
     if (e == cudaSuccess) e = set_smem(pass_tch_group_kernel<FORM_ROT>, s3);
     if (e == cudaSuccess) e = set_smem(pass_tch_group_kernel<FORM_SWZ>, s3);
+    if (e == cudaSuccess) e = set_smem(pass_tch5_kernel, tch5_smem_bytes(TH_MAX_STAGES_5));
     return e;
+}
+
+// The highest tile bit >= 5 that no 5-bit stage of pass `pass` touches, or -1.
+int free_block_bit(const DevPlan* dp, int pass) {
+    const DevPass& P = dp->plan.passes[pass];
+    uint32_t U = 0;
+    for (int si = 0; si < P.stage_count; ++si)
+        for (int i = 0; i < 5; ++i) U |= 1u << dp->tcs[P.stage_begin + si].rbit[i];
+    for (int b = TH_TILE_BITS - 1; b >= 5; --b)
+        if (!((U >> b) & 1)) return b;
+    return -1;
 }
 
 // Two tile bits (>= 5) that no stage of pass `pass` touches: b0 | b1 << 8, or -1.
@@ -787,8 +1054,15 @@ bool pass_tch_eligible(const DevPlan* dp, int pass) {
     const DevPass& P = dp->plan.passes[pass];
     if (P.m != TH_TILE_BITS || P.stage_count < 1) return false;
     // the W operands of a pass's stages are consecutive (one bulk copy)
+    const int wsz = dp->tc5[pass] ? 4 * TH_W_BYTES : TH_W_BYTES;
     for (int si = 1; si < P.stage_count; ++si)
-        if (dp->tcs[P.stage_begin + si].tc_index != dp->tcs[P.stage_begin].tc_index + si) return false;
+        if (dp->tcs[P.stage_begin + si].wh_off != dp->tcs[P.stage_begin].wh_off + si * wsz) return false;
+    if (dp->tc5[pass]) {   // two row blocks split by a free tile bit, plain slot reads
+        if (P.stage_count > TH_MAX_STAGES_5 || free_block_bit(dp, pass) < 0) return false;
+        for (int si = 0; si < P.stage_count; ++si)
+            if (dp->tcs[P.stage_begin + si].nj) return false;
+        return true;
+    }
     if (free_slice_bits(dp, pass) >= 0 && P.stage_count <= TH_MAX_STAGES_3BUF) return true;
     return P.stage_count <= TH_MAX_STAGES;
 }
@@ -828,7 +1102,12 @@ cudaError_t launch_pass_tch(const DevPlan* dp, int pass, int items, const void* 
     a.tc.total_tiles = a.total_tiles;
     const unsigned grid = (unsigned)std::min<long long>(a.total_tiles, num_sms());
     const int nst = P.stage_count;
-    if (grp >= 0) {
+    if (dp->tc5[pass]) {
+        a.gb0 = free_block_bit(dp, pass);
+        a.gb1 = -1;
+        a.tc.nbuf = 3;
+        pass_tch5_kernel<<<grid, TH_CTA_THREADS, tch5_smem_bytes(nst), s>>>(P, a, tma);
+    } else if (grp >= 0) {
         a.tc.nbuf = 3;
         const size_t sm = tch_smem_bytes(nst, 3);
         if (form == FORM_SWZ) pass_tch_group_kernel<FORM_SWZ><<<grid, TH_CTA_THREADS, sm, s>>>(P, a, tma);

@@ -361,95 +361,24 @@ void build_plan(Plan& plan) {
                 ++n_placed;
             }
             // ---- stages: list scheduling with register-set affinity ----
-            std::vector<char> done(plan.blocks.size(), 0);
-            std::vector<char> inp(plan.blocks.size(), 0);
-            for (int b : pass_list) inp[b] = 1;
-            size_t left = pass_list.size();
-            dp.stage_begin = (int)plan.stages.size();
-            uint32_t Rset = 0;  // tile-bit mask
-            int Rcap = kRegBits;
-            int cur_grads = 0;
-            std::vector<int> cur;
-            auto close_stage = [&]() {
-                if (cur.empty()) return;
-                DevStage st{};
-                // pad register set with the highest free tile bits
-                for (int tb = dp.m - 1; tb >= 0 && __builtin_popcount(Rset) < Rcap; --tb)
-                    Rset |= 1u << tb;
-                st.nreg = (uint8_t)Rcap;
-                // shared-memory banks are picked by tile bits 0..3 (8-byte amplitudes): only then
-                // do the slots need the per-group XOR rotation
-                st.rotate = (Rset & 0xFu) ? 1 : 0;
-                int ri = 0;
-                int reg_of_tb[kMaxTileBits + 2];
-                for (int tb = 0; tb < dp.m; ++tb) {
-                    reg_of_tb[tb] = -1;
-                    if ((Rset >> tb) & 1) {
-                        st.rbit[ri] = (uint8_t)tb;
-                        reg_of_tb[tb] = ri++;
-                    }
-                }
-                st.op_begin = (uint32_t)plan.dops.size();
-                for (int b : cur) {
-                    Block& blk = plan.blocks[b];
-                    blk.out_off = off;
-                    off += blk.size;
-                    plan.pass_blocks.push_back(b);
-                    DevOp d{};
-                    d.k = (uint8_t)blk.k;
-                    d.mat = (uint32_t)(blk.out_off - dp.mat_begin);
-                    int j = 0;
-                    uint64_t qm = blk.qmask;
-                    if (blk.diag) {
-                        d.kind = K_DIAG;
-                        uint16_t nib = 0;
-                        while (qm) {
-                            int q = __builtin_ctzll(qm);
-                            qm &= qm - 1;
-                            d.src[j] = (tb_of_q[q] >= 0) ? (uint8_t)tb_of_q[q]
-                                                         : (uint8_t)(kSrcBase | q);
-                            if (tb_of_q[q] >= 0 && reg_of_tb[tb_of_q[q]] >= 0 &&
-                                reg_of_tb[tb_of_q[q]] < kRegBits)
-                                nib |= (uint16_t)((j + 1) << (4 * reg_of_tb[tb_of_q[q]]));
-                            ++j;
-                        }
-                        d.mask = (uint8_t)(nib & 0xFF);
-                        d.pad = (uint8_t)(nib >> 8);
-                    } else {
-                        d.kind = K_DENSE;
-                        while (qm) {
-                            int q = __builtin_ctzll(qm);
-                            qm &= qm - 1;
-                            int r = reg_of_tb[tb_of_q[q]];
-                            if (r < 0) throw std::runtime_error("planner: block outside stage");
-                            d.mask |= (uint8_t)(1u << r);
-                        }
-                    }
-                    if (o.adjoint && blk.param_single) {
-                        d.grad = (uint8_t)blk.grad;
-                        if (plan.n_grad >= kMaxGradSlots)
-                            throw std::invalid_argument("adjoint: at most 2048 parameterised gates per circuit");
-                        d.slot = (uint16_t)plan.n_grad++;
-                        ++st.n_grad;
-                        plan.grad_param.push_back(blk.param);
-                        plan.grad_scale.push_back(blk.grad_factor * blk.scale);
-                    }
-                    plan.dops.push_back(d);
-                }
-                st.op_count = (uint32_t)(plan.dops.size() - st.op_begin);
-                plan.stages.push_back(st);
-                cur.clear();
-                Rset = 0;
-                Rcap = kRegBits;
-                cur_grads = 0;
+            // schedule(SB, out): the pass's blocks into register stages of SB tile bits
+            // (kMaxRegBits for a stage that holds a 5-qubit block); records each
+            // stage's register set (padded with the highest free tile bits) and blocks
+            struct Staged {
+                uint32_t R;
+                int cap;
+                std::vector<int> blocks;
             };
             std::vector<std::vector<int>> pdeps(plan.blocks.size());
-            for (int b : pass_list)
-                for (int d : deps[b])
-                    if (inp[d]) pdeps[b].push_back(d);
+            {
+                std::vector<char> inp(plan.blocks.size(), 0);
+                for (int b : pass_list) inp[b] = 1;
+                for (int b : pass_list)
+                    for (int d : deps[b])
+                        if (inp[d]) pdeps[b].push_back(d);
+            }
             // tile-bit mask of each block of the pass
             std::vector<uint32_t> tbm_of(plan.blocks.size(), 0);
-            bool small_blocks = !o.adjoint;   // the register-set search below: <= 4-qubit blocks
             for (int b : pass_list) {
                 uint64_t qm = plan.blocks[b].qmask;
                 while (qm) {
@@ -457,8 +386,28 @@ void build_plan(Plan& plan) {
                     qm &= qm - 1;
                     tbm_of[b] |= 1u << tb_of_q[q];
                 }
-                if (!plan.blocks[b].diag && __builtin_popcount(tbm_of[b]) > kRegBits) small_blocks = false;
             }
+            auto schedule = [&](const int SB, std::vector<Staged>& out) {
+            std::vector<char> done(plan.blocks.size(), 0);
+            size_t left = pass_list.size();
+            uint32_t Rset = 0;  // tile-bit mask
+            int Rcap = SB;
+            int cur_grads = 0;
+            std::vector<int> cur;
+            auto close_stage = [&]() {
+                if (cur.empty()) return;
+                // pad register set with the highest free tile bits
+                for (int tb = dp.m - 1; tb >= 0 && __builtin_popcount(Rset) < Rcap; --tb)
+                    Rset |= 1u << tb;
+                out.push_back(Staged{Rset, Rcap, cur});
+                cur.clear();
+                Rset = 0;
+                Rcap = SB;
+                cur_grads = 0;
+            };
+            bool small_blocks = !o.adjoint;   // the register-set search below: <= SB-qubit blocks
+            for (int b : pass_list)
+                if (!plan.blocks[b].diag && __builtin_popcount(tbm_of[b]) > SB) small_blocks = false;
             // Register sets of the stages: for passes of up to 12 dense blocks, the
             // fewest stages (a stage costs about the same whatever it holds on the
             // tensor-core passes).  A stage with register set R takes every block that
@@ -510,16 +459,17 @@ void build_plan(Plan& plan) {
                 for (int tb = 0; tb < dp.m; ++tb)
                     if ((touch >> tb) & 1) bits.push_back(tb);
                 std::vector<uint32_t> cands;
-                if ((int)bits.size() <= kRegBits) {
+                if ((int)bits.size() <= SB) {
                     cands.push_back(touch);
-                } else {
+                } else {   // every SB-subset of the touched bits
                     const int nb = (int)bits.size();
-                    for (int i0 = 0; i0 < nb; ++i0)
-                        for (int i1 = i0 + 1; i1 < nb; ++i1)
-                            for (int i2 = i1 + 1; i2 < nb; ++i2)
-                                for (int i3 = i2 + 1; i3 < nb; ++i3)
-                                    cands.push_back((1u << bits[i0]) | (1u << bits[i1]) | (1u << bits[i2]) |
-                                                    (1u << bits[i3]));
+                    for (uint32_t sel = 0; sel < (1u << nb); ++sel) {
+                        if (__builtin_popcount(sel) != SB) continue;
+                        uint32_t R = 0;
+                        for (int i = 0; i < nb; ++i)
+                            if ((sel >> i) & 1) R |= 1u << bits[i];
+                        cands.push_back(R);
+                    }
                 }
                 int best = 1 << 20, best_low = 99;
                 uint32_t bestR = 0;
@@ -575,15 +525,9 @@ void build_plan(Plan& plan) {
                         (cur_grads >= kMaxStageGrads || Rcap > kRegBits))
                         continue;   // gradient ops stay in 16-amplitude register stages
                     if (blk.diag) { pick = b; break; }
-                    uint32_t tbm = 0;
-                    uint64_t qm = blk.qmask;
-                    while (qm) {
-                        int q = __builtin_ctzll(qm);
-                        qm &= qm - 1;
-                        tbm |= 1u << tb_of_q[q];
-                    }
+                    const uint32_t tbm = tbm_of[b];
                     // a 5-qubit block opens a 32-amplitude stage of its own bits
-                    if (cur.empty() && __builtin_popcount(tbm) > kRegBits) Rcap = kMaxRegBits;
+                    if (cur.empty() && __builtin_popcount(tbm) > SB) Rcap = kMaxRegBits;
                     if (__builtin_popcount(Rset | tbm) <= Rcap) {
                         pick = b;
                         Rset |= tbm;
@@ -601,6 +545,90 @@ void build_plan(Plan& plan) {
                 --left;
             }
             close_stage();
+            };
+            std::vector<Staged> staged, wide;
+            schedule(kRegBits, staged);
+            // 32-amplitude stages where they take fewer stages: unitary passes of one
+            // or two such stages off tile bits 0..3 that leave a tile bit >= 5 untouched
+            // (the FP16 tensor-core kernel for these runs two independent row blocks)
+            if (o.wide && plan.all_unitary && !o.adjoint && dp.m == 13 && staged.size() > 1) {
+                schedule(kMaxRegBits, wide);
+                uint32_t U = 0;
+                bool ok = !wide.empty() && wide.size() <= 2 && wide.size() < staged.size();
+                for (const Staged& w : wide) {
+                    U |= w.R;
+                    ok = ok && w.cap == kMaxRegBits;
+                }
+                ok = ok && (U & 0xFu) == 0 && (U >> 5) != ((1u << (dp.m - 5)) - 1);
+                if (ok) staged.swap(wide);
+            }
+            dp.stage_begin = (int)plan.stages.size();
+            for (const Staged& sg : staged) {
+                DevStage st{};
+                const uint32_t Rset = sg.R;
+                st.nreg = (uint8_t)sg.cap;
+                // shared-memory banks are picked by tile bits 0..3 (8-byte amplitudes): only then
+                // do the slots need the per-group XOR rotation
+                st.rotate = (Rset & 0xFu) ? 1 : 0;
+                int ri = 0;
+                int reg_of_tb[kMaxTileBits + 2];
+                for (int tb = 0; tb < dp.m; ++tb) {
+                    reg_of_tb[tb] = -1;
+                    if ((Rset >> tb) & 1) {
+                        st.rbit[ri] = (uint8_t)tb;
+                        reg_of_tb[tb] = ri++;
+                    }
+                }
+                st.op_begin = (uint32_t)plan.dops.size();
+                for (int b : sg.blocks) {
+                    Block& blk = plan.blocks[b];
+                    blk.out_off = off;
+                    off += blk.size;
+                    plan.pass_blocks.push_back(b);
+                    DevOp d{};
+                    d.k = (uint8_t)blk.k;
+                    d.mat = (uint32_t)(blk.out_off - dp.mat_begin);
+                    int j = 0;
+                    uint64_t qm = blk.qmask;
+                    if (blk.diag) {
+                        d.kind = K_DIAG;
+                        uint16_t nib = 0;
+                        while (qm) {
+                            int q = __builtin_ctzll(qm);
+                            qm &= qm - 1;
+                            d.src[j] = (tb_of_q[q] >= 0) ? (uint8_t)tb_of_q[q]
+                                                         : (uint8_t)(kSrcBase | q);
+                            if (tb_of_q[q] >= 0 && reg_of_tb[tb_of_q[q]] >= 0 &&
+                                reg_of_tb[tb_of_q[q]] < kRegBits)
+                                nib |= (uint16_t)((j + 1) << (4 * reg_of_tb[tb_of_q[q]]));
+                            ++j;
+                        }
+                        d.mask = (uint8_t)(nib & 0xFF);
+                        d.pad = (uint8_t)(nib >> 8);
+                    } else {
+                        d.kind = K_DENSE;
+                        while (qm) {
+                            int q = __builtin_ctzll(qm);
+                            qm &= qm - 1;
+                            int r = reg_of_tb[tb_of_q[q]];
+                            if (r < 0) throw std::runtime_error("planner: block outside stage");
+                            d.mask |= (uint8_t)(1u << r);
+                        }
+                    }
+                    if (o.adjoint && blk.param_single) {
+                        d.grad = (uint8_t)blk.grad;
+                        if (plan.n_grad >= kMaxGradSlots)
+                            throw std::invalid_argument("adjoint: at most 2048 parameterised gates per circuit");
+                        d.slot = (uint16_t)plan.n_grad++;
+                        ++st.n_grad;
+                        plan.grad_param.push_back(blk.param);
+                        plan.grad_scale.push_back(blk.grad_factor * blk.scale);
+                    }
+                    plan.dops.push_back(d);
+                }
+                st.op_count = (uint32_t)(plan.dops.size() - st.op_begin);
+                plan.stages.push_back(st);
+            }
             dp.stage_count = (int)plan.stages.size() - dp.stage_begin;
             dp.mat_count = off - dp.mat_begin;
             plan.passes.push_back(dp);

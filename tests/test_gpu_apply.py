@@ -382,6 +382,33 @@ def test_fp16_passes_every_kernel_form(T, n, depth, fw):
     assert relerr(psi, psi2) < 2 * TOL["c64"]
 
 
+def stage_widths(T, n, g, p, P):
+    """Register bits of every stage of the plan tcng_apply_circuit runs."""
+    out = []
+    for line in T.tcng_describe_plan(n, g, p, P, False).split("\n"):
+        if "regs=" in line:
+            for tok in line.split("regs=")[1].split():
+                out.append(tok[tok.index("{") + 1:tok.index("}")].count(",") + 1)
+    return out
+
+
+@pytest.mark.parametrize("n,depth", [(18, 10), (22, 14)])
+def test_fp16_five_bit_stages(T, n, depth):
+    """Gathered passes whose gates fit two 5-qubit register stages instead of three
+    4-qubit ones run 32x32 complex (64x64 real) FP16 GEMMs: the plan has such stages,
+    they run on the FP16 kernels, and the state matches the oracle."""
+    c, th = gen.su4_brickwork(n, depth, "RZ", seed=100 + n)
+    g, p = c.to_ir()
+    T.tcng_set_option(T.OPT_TENSOR_CORES, 1)
+    T.tcng_set_option(T.OPT_TC_FP16, 1)
+    assert 5 in stage_widths(T, n, g, p, len(th))
+    st, counts = tc_run(T, n, g, p, th, fp16=1, per_kernel=True)
+    assert counts["pass_tch_kernel_c64"] > 0 and counts["pass_tcs_kernel_c64"] == 0
+    check_state(st.amplitudes(0).cpu().numpy(), sv.apply(n, g, p, th), "c64")
+    T.tcng_set_option(T.OPT_TC_FP16, 0)   # the TF32 path plans 4-qubit stages only
+    assert set(stage_widths(T, n, g, p, len(th))) == {4}
+
+
 @pytest.mark.parametrize("scale_log2", [-70, -20, 0, 30, 60])
 def test_fp16_passes_scaled_states(T, scale_log2):
     """The FP16 split scales each tile by a power of two: states of any magnitude
