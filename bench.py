@@ -43,7 +43,7 @@ PASS_KERNELS = ("pass_kernel_c64", "pass_tcs_kernel_c64", "pass_tch_kernel_c64")
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one 28-qubit
 # launch from an ncu capture of this kernel, scaled by the state size; a kernel
 # changed since its capture has no entry.
-TRAFFIC_28Q = {"pass_tcs_kernel_c64": 4.234933e9}
+TRAFFIC_28Q = {"pass_tch_kernel_c64": 4.236936e9}
 
 
 def workload(n=N_QUBITS, depth=DEPTH):

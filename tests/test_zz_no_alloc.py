@@ -1,8 +1,8 @@
 """tcng_expect_pauli_noalloc against tcng_expect_pauli (GPU).
 
 The allocation-free entry point exists for callers that must not let the
-library call cudaMalloc (their allocator owns the free memory, their hot path
-bans allocation, or they are recording a stream capture).  It keeps its
+library call cudaMalloc (their allocator owns the free memory, or their hot
+path bans allocation).  It keeps its
 partial sums in a static device array instead.  Here it must reproduce the
 ordinary entry point's values within the complex64/complex128 tolerances of the
 other expectation tests, on two calls in a row (the second call reuses the
