@@ -295,13 +295,13 @@ tcng_status run_plan(DevPlan* dp, C* state, const long long* d_item_off, int ite
             const DevPass& p = pl.passes[pi];
             TmaTile tma{};
             if (tma_base && (items == 1 || item_stride > 0))
-                tma = make_tma_tile(tma_base, pl.n, (int)sizeof(C), p, items, item_stride);
+                tma = make_tma_tile(tma_base, pl.n, (int)sizeof(C), p, items, item_stride, false, true);
             if (wops && dp->tc_pass[pi]) {   // tile map, else one bulk copy per chunk
                 // stages on tile bits 0..3 read conflict-free from a 128-byte swizzled tile
                 bool rot = false, swz = false;
                 for (int si = 0; si < p.stage_count; ++si) rot = rot || dp->tcs[p.stage_begin + si].nj > 0;
                 if (rot && p.chunk >= 4 && tma.rank) {
-                    const TmaTile ts = make_tma_tile(tma_base, pl.n, (int)sizeof(C), p, items, item_stride, true);
+                    const TmaTile ts = make_tma_tile(tma_base, pl.n, (int)sizeof(C), p, items, item_stride, true, true);
                     if (ts.rank) {
                         tma = ts;
                         swz = true;

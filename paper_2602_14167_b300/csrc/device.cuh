@@ -132,7 +132,7 @@ __device__ __forceinline__ void tma_tile_coords(const TmaTile& t, long long tile
     for (int i = 0; i < 5; ++i) {
         c[i] = 0;
         if (i < t.rank) {
-            if (t.kind[i] == 1) c[i] = (int)((tile_local >> t.shift[i]) & ((1ll << t.len[i]) - 1));
+            if (t.kind[i] == 1) c[i] = (int)((tile_local >> t.shift[i]) & ((1ll << t.len[i]) - 1)) << t.lsh[i];
             else if (t.kind[i] == 2) c[i] = item;
         }
     }

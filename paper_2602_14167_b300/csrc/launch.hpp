@@ -41,6 +41,8 @@ struct alignas(64) TmaTile {
     int8_t kind[5];            // 0 tile run (coordinate 0), 1 rest run, 2 item
     int8_t shift[5];           // rest run: first bit of the tile number it takes
     int8_t len[5];             // rest run: number of bits
+    int8_t lsh[5];             // rest run: tile bits below it in the same dimension (the
+                               // box covers them; the coordinate is the rest bits << lsh)
     int8_t g4;                 // rank 0: map is a 2D [rows x 2^g4rb] gather4 map
     long long g4base;          // gather4: element offset of the map's first row
     int32_t g4rb;              // gather4: log2 amplitudes per row (<= chunk)
@@ -51,8 +53,11 @@ struct alignas(64) TmaTile {
 // sw128: the tile lands in shared memory with the 128-byte swizzle (rows of 128
 // bytes whose 16-byte chunk index is XORed with the row index mod 8); needs a
 // 1024-byte aligned destination and a low chunk of at least 128 bytes.
+// merge: where the plain form needs more than five dimensions, give the rest run
+// above each tile run the dimension of that run's last piece (the box covers the
+// tile bits at its bottom), which needs one dimension per tile run.
 TmaTile make_tma_tile(void* base, int n, int elem_bytes, const DevPass& p, int items,
-                      long long item_stride_bytes, bool sw128 = false);
+                      long long item_stride_bytes, bool sw128 = false, bool merge = false);
 // A pass's tiles as rows of one chunk (2^chunk amplitudes, at most 256 8-byte
 // elements), four arbitrary rows per tile::gather4 copy (for passes whose bit
 // runs need more than five tensor dimensions).  base_elems: element offset of

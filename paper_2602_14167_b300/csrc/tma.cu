@@ -29,7 +29,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 TmaTile make_tma_tile(void* base, int n, int elem_bytes, const DevPass& p, int items,
-                      long long item_stride_bytes, bool sw128) {
+                      long long item_stride_bytes, bool sw128, bool merge) {
+    if (merge) {   // the plain form first; the merged one only where it needs too many dimensions
+        TmaTile t0 = make_tma_tile(base, n, elem_bytes, p, items, item_stride_bytes, sw128, false);
+        if (t0.rank) return t0;
+    }
     TmaTile t;
     std::memset(&t, 0, sizeof t);
     auto fn = encode_fn();
@@ -46,6 +50,12 @@ TmaTile make_tma_tile(void* base, int n, int elem_bytes, const DevPass& p, int i
         const int tile = in_tile[q];
         int len = 1;
         while (q + len < n && in_tile[q + len] == tile) ++len;
+        // merge: the rest run above a tile run shares the dimension of the tile
+        // run's last piece (box = the tile bits, coordinate = the rest bits << them)
+        int above = 0;
+        if (merge && tile && q + len < n) {
+            while (q + len + above < n && !in_tile[q + len + above]) ++above;
+        }
         // split tile runs so every box dimension stays <= 256 elements
         int done = 0;
         while (done < len) {
@@ -57,20 +67,31 @@ TmaTile make_tma_tile(void* base, int n, int elem_bytes, const DevPass& p, int i
             }
             if (rank == 5) return TmaTile{};   // too many dimensions
             const int start = q + done;
-            const cuuint64_t ext = 1ull << piece;
+            const bool last_piece = done + piece == len;
+            const int extra = (tile && last_piece) ? above : 0;   // merged rest bits
+            const cuuint64_t ext = 1ull << (piece + extra);
             gdim[rank] = (rank == 0) ? ext * e : ext;
             if (rank > 0) gstride[rank - 1] = (cuuint64_t)elem_bytes << start;
-            box[rank] = tile ? (cuuint32_t)gdim[rank] : 1;
+            box[rank] = tile ? (cuuint32_t)((1ull << piece) * (rank == 0 ? e : 1)) : 1;
             estr[rank] = 1;
-            t.kind[rank] = tile ? 0 : 1;
-            t.shift[rank] = (int8_t)(tile ? 0 : rest_seen);
-            t.len[rank] = (int8_t)(tile ? 0 : piece);
-            if (!tile) rest_seen += piece;
+            if (extra) {
+                t.kind[rank] = 1;
+                t.shift[rank] = (int8_t)rest_seen;
+                t.len[rank] = (int8_t)extra;
+                t.lsh[rank] = (int8_t)(piece + (rank == 0 && e == 2 ? 1 : 0));
+                rest_seen += extra;
+            } else {
+                t.kind[rank] = tile ? 0 : 1;
+                t.shift[rank] = (int8_t)(tile ? 0 : rest_seen);
+                t.len[rank] = (int8_t)(tile ? 0 : piece);
+                t.lsh[rank] = 0;
+                if (!tile) rest_seen += piece;
+            }
             if (rank == 0 && !tile) return TmaTile{};   // bit 0 is always a tile bit
             ++rank;
             done += piece;
         }
-        q += len;
+        q += len + (tile ? above : 0);
     }
     if (items > 1) {
         if (rank == 5) return TmaTile{};
