@@ -201,6 +201,26 @@ def run_gpu(args):
             T.tcng_set_option(opt, val)
     if args.tensor_cores >= 0:
         T.tcng_set_option(T.OPT_TENSOR_CORES, args.tensor_cores)
+    tuned = None
+    if not args.no_autotune and not (args.fuse_width or args.tile_bits or args.chunk_bits) and args.tensor_cores < 0:
+        # the library's autotuner on the same circuit family at min(n, 28) qubits (a
+        # 2 GiB state: every candidate timed in ~0.4 s); its choice becomes the options
+        nt = min(NQ, 28)
+        _, g_t, p_t, th_t, _, _ = workload(nt, DP)
+        st_t = StateBatch(nt, dtype="c64", device=dev)
+        prm_t = torch.tensor(th_t, dtype=torch.float64, device=dev).reshape(1, -1)
+        best = T.tcng_autotune_circuit(st_t.handle, g_t, p_t, prm_t, prm_t.shape[1], None)
+        rep = T.tcng_autotune_report()
+        st_t.free()
+        del st_t
+        torch.cuda.empty_cache()
+        default = [r[4] for r in rep if tuple(r[:4]) == (2, 13, 7, 1)]
+        tuned = {"proxy": f"n={nt}, depth {DP}, same generator", "candidates": len(rep), "best_ms": best,
+                 "library_default_ms": default[0] if default else None,
+                 "choice": {"fuse_width": T.tcng_get_option(T.OPT_FUSE_WIDTH),
+                            "tile_bits": T.tcng_get_option(T.OPT_TILE_BITS),
+                            "chunk_bits": T.tcng_get_option(T.OPT_CHUNK_BITS),
+                            "tensor_cores": T.tcng_get_option(T.OPT_TENSOR_CORES)}}
     c, gates, pool, theta, strings, tfim = workload(NQ, DP)
     # one expectation call plans the strings and the TFIM terms together (the
     # strings carry coefficient 0, so the energy is the TFIM energy)
@@ -292,6 +312,8 @@ def run_gpu(args):
                       "tile_bits": T.tcng_get_option(T.OPT_TILE_BITS),
                       "chunk_bits": T.tcng_get_option(T.OPT_CHUNK_BITS),
                       "tensor_cores": T.tcng_get_option(T.OPT_TENSOR_CORES),
+                      "fp16_split": T.tcng_get_option(T.OPT_TC_FP16),
+                      "autotune": tuned,
                       "ms_per_layer": ms_step / DP,
                       "l2": (f"inputs larger than L2 ({S / 2**30:g} GiB state), no flush" if S > 126e6
                              else f"state ({S / 2**20:g} MiB) fits in L2, no flush"),
@@ -314,6 +336,8 @@ def run_gpu(args):
         out["vqe"] = vqe_bench(args, dev, dist, world)
     if not args.no_apps:
         out["apps"] = apps_bench(args, dev, dist, world)
+    if not args.no_paths:
+        out["paths"] = paths_bench(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         moved, times, cores = oracle_sample(3, 4)
         v = moved * len(times) / sum(times) / 1e9
@@ -566,6 +590,98 @@ def apps_bench(args, dev, dist, world):
     return res
 
 
+def paths_bench(args, dev):
+    """The other measured paths, each on its own small workload: the FMA peaks
+    (denominators of the SIMT kernels), config 2 (n=24 SU(4) brickwork depth 20
+    + RX, complex64 and complex128: tile passes and the 32 strings + TFIM
+    energy), the unfused pair/quartet kernels (n=28 complex64) and the
+    shared-unitary tensor-core apply (64 states of 20 qubits)."""
+    import torch
+    from paper_2602_14167_b300 import StateBatch
+    from paper_2602_14167_b300 import tcng as T
+    hbm, _ = peaks()
+    res = {"fma_peak_tflops": {"fp32": T.tcng_fma_peak(False), "fp64": T.tcng_fma_peak(True),
+                               "note": "measured: 8 CTAs x 256 threads per SM, 8 FMA chains per thread"}}
+
+    def prof_run(fn):
+        T.tcng_profile_enable(True)
+        T.tcng_profile_read(reset=True)
+        fn()
+        torch.cuda.synchronize()
+        prof = T.tcng_profile_read(reset=True)
+        T.tcng_profile_enable(False)
+        return prof
+
+    # config 2
+    n = 24
+    c, th = gen.su4_brickwork(n, 20, "RX", seed=0)
+    g, p = c.to_ir()
+    strings = gen.random_pauli_strings(n, 32, 4, seed=1)
+    terms = np.concatenate([strings, gen.tfim_terms(n, 1.0, 1.0)])
+    coeffs = None
+    for dt, es in (("c64", 8), ("c128", 16)):
+        st = StateBatch(n, dtype=dt)
+        prm = torch.tensor(th, dtype=torch.float64, device=dev).reshape(1, -1)
+        vals = torch.empty((1, len(terms)), dtype=torch.float64, device=dev)
+        energy = torch.empty(1, dtype=torch.float64, device=dev)
+
+        def step():
+            st.reset()
+            st.apply(g, p, prm)
+            T.tcng_expect_energy(st.handle, terms, coeffs, vals, energy)
+
+        ms = timed(step, args.steps, args.warmup, None, dev)
+        prof = prof_run(step)
+        tile = [sum(prof.get(k, (0, 0.0))[i] for k in PASS_KERNELS + ("pass_kernel_c128",)) for i in (0, 1)]
+        exp = [sum(v[i] for k, v in prof.items() if k.startswith("expect_pass")) for i in (0, 1)]
+        S = es << n
+        res[f"config2_n24_{dt}"] = {
+            "ms_per_step": ms, "tile_passes": tile[0], "tile_pass_ms": tile[1],
+            "tile_pass_gbs": tile[0] * 2 * S / (tile[1] * 1e-3) / 1e9 if tile[1] else None,
+            "expect_passes": exp[0], "expect_ms": exp[1],
+            "state_MiB": S / 2**20, "note": "state fits in the 126 MB L2 only for complex64 at n=24 (128 MiB: partly)",
+            "kernel_ms": {k: [v[0], v[1]] for k, v in prof.items()}}
+        st.free()
+    # unfused pair / quartet kernels
+    n = 28
+    from workloads import Circuit
+    cu = Circuit(n)
+    for q in (0, 9, 17, 27):
+        cu.h(q)
+    for q in (0, 10, 20):
+        cu.cx(q, q + 5)
+    for q in (3, 26):
+        cu.unitary((q, q - 2), gen.haar_su4(np.random.default_rng(q)))
+    gu, pu = cu.to_ir()
+    st = StateBatch(n, dtype="c64")
+    T.tcng_set_option(T.OPT_UNFUSED, 1)
+    try:
+        ms = timed(lambda: st.apply(gu, pu, None), args.steps, args.warmup, None, dev)
+        prof = prof_run(lambda: st.apply(gu, pu, None))
+    finally:
+        T.tcng_set_option(T.OPT_UNFUSED, 0)
+    S = 8 << n
+    res["unfused_n28_c64"] = {
+        "gates": len(gu), "ms_per_circuit": ms, "gbs": len(gu) * 2 * S / (ms * 1e-3) / 1e9,
+        "hbm_peak": hbm, "frac": len(gu) * 2 * S / (ms * 1e-3) / 1e9 / hbm,
+        "kernel_ms": {k: [v[0], v[1]] for k, v in prof.items()}}
+    st.free()
+    # shared-unitary apply (tcgen05, TF32 split): 64 states of 20 qubits, 4-qubit unitaries
+    n, B = 20, 64
+    st = StateBatch(n, batch=B, dtype="c64")
+    rng = np.random.default_rng(5)
+    U = np.linalg.qr(rng.standard_normal((16, 16)) + 1j * rng.standard_normal((16, 16)))[0]
+    out = {}
+    for name, qs in (("low", [0, 1, 2, 3]), ("high", [16, 17, 18, 19])):
+        ms = timed(lambda: T.tcng_apply_shared_unitary(st.handle, qs, U), args.steps, args.warmup, None, dev)
+        S = B * (8 << n)
+        out[name] = {"qubits": qs, "ms": ms, "gbs": 2 * S / (ms * 1e-3) / 1e9, "frac": 2 * S / (ms * 1e-3) / 1e9 / hbm}
+    res["shared_unitary_n20_b64_k4"] = out
+    st.free()
+    torch.cuda.empty_cache()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -577,6 +693,10 @@ def main():
     ap.add_argument("--vqe-only", action="store_true", help="only the n=16 batched VQE (profiling)")
     ap.add_argument("--no-apps", action="store_true", help="skip the QML / MIPT / shadow measurements")
     ap.add_argument("--apps-only", action="store_true", help="only the QML / MIPT / shadow measurements")
+    ap.add_argument("--no-paths", action="store_true",
+                    help="skip the FMA peaks, config 2, unfused and shared-unitary measurements")
+    ap.add_argument("--paths-only", action="store_true", help="only those measurements")
+    ap.add_argument("--no-autotune", action="store_true", help="library default options, no autotuner run")
     ap.add_argument("--fuse-width", type=int, default=0, help="override the fusion width (tuning)")
     ap.add_argument("--tile-bits", type=int, default=0, help="override the tile bits (tuning)")
     ap.add_argument("--chunk-bits", type=int, default=0, help="override the chunk bits (tuning)")
@@ -592,6 +712,12 @@ def main():
         return run_reference(args)
     if args.vqe_only:
         return run_vqe_only(args)
+    if args.paths_only:
+        import torch
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"paths": paths_bench(args, dev)}))
+        return 0
     if args.apps_only:
         import torch
         dev = torch.device("cuda", 0)

@@ -319,11 +319,13 @@ tcng_status tcng_measure(tcng_state* st, const uint64_t* mask_dev, const double*
 /*
  * tcng_apply_shared_unitary -- apply one k-qubit unitary U (host complex128,
  * row-major, local index as in the gate list with qubits q[0..k-1]) to every
- * item of a complex64 batch: a complex GEMM [2^k x 2^k] x [2^k x batch*2^(n-k)]
- * on the tensor cores (tcgen05, fp32 accuracy by a 3-term TF32 split).  The
- * batched layer of the paper's QML demonstration (Sec. VII.B), where every
- * input state sees the same circuit.  k in 1..5; qubits distinct and < n.
- * Errors: EINVAL, EUNSUPPORTED (complex128 states), ECUDA.
+ * item of a complex64 batch: a complex GEMM [2^k x 2^k] x [2^k x batch*2^(n-k)],
+ * run as a one-gate circuit without parameters, so one W set serves every tile
+ * of every item on the tensor cores (FP16 hi/lo operands; items of fewer than
+ * 13 qubits packed several to a tile).  The batched layer of the paper's QML
+ * demonstration (Sec. VII.B), where every input state sees the same circuit.
+ * k in 1..5; qubits distinct and < n.  Errors: EINVAL, EUNSUPPORTED (complex128
+ * states), ECUDA.
  */
 tcng_status tcng_apply_shared_unitary(tcng_state* st, const int* qubits, int k,
                                       const double* U, void* stream);
@@ -442,6 +444,15 @@ tcng_status tcng_autotune_circuit(tcng_state* st, const tcng_gate* ops, size_t n
  * tensor_cores ms" per candidate (ms < 0: the candidate failed), or "cached
  * <cache line>" when the choice was loaded.  NUL-terminated, truncated to len. */
 tcng_status tcng_autotune_report(char* buf, size_t len);
+
+/*
+ * tcng_fma_peak -- measured FMA throughput of this GPU in TFLOP/s (2 flops per
+ * FMA), FP32 (fp64 = 0) or FP64: every thread of 8 CTAs x 256 threads per SM
+ * runs eight independent FMA chains; one timed launch after a warm-up.  The
+ * denominator of the roofline of the SIMT kernels (the adjoint sweep).  Not
+ * part of any computation of the paper; synchronises the device.
+ */
+tcng_status tcng_fma_peak(int fp64, double* tflops);
 
 /* Synchronise the device and report a device-side error word (ETIMEOUT) if set. */
 tcng_status tcng_sync_status(void);

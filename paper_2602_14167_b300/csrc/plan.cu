@@ -443,15 +443,49 @@ void build_plan(Plan& plan) {
                 }
                 return dm;
             };
-            std::unordered_map<uint64_t, std::pair<int, uint32_t>> memo;
-            std::function<int(uint64_t)> solve = [&](uint64_t dm) -> int {
-                if ((dm & all_mask) == all_mask) return 0;
+            // Tie-break between stagings of equal length: the shared-memory bank
+            // conflicts of the stages.  A stage on tile bits 0..3 reads its slots from a
+            // 128-byte-swizzled tile, where a float2's bank slot (16 per 128 bytes) has bit
+            // 0 = tile bit 0 and bit k = tile bit k xor tile bit k + 3 (k = 1..3); a warp's
+            // lanes take the five lowest tile bits outside R, and 16-byte pair reads (tile
+            // bit 0 in R) need only slot bits 1..3.  Each slot bit the lanes miss doubles
+            // the wavefronts.  Stages off tile bits 0..3 cost nothing.
+            auto stage_cost = [&](uint32_t R) -> int {
+                if (!(R & 0xFu)) return 0;
+                const uint32_t need_mask = (R & 1u) ? 0xEu : 0xFu;
+                uint32_t basis[4] = {0, 0, 0, 0};
+                int rank = 0, nl = 0;
+                for (int tb = 0; tb < dp.m && nl < 5; ++tb) {
+                    if ((R >> tb) & 1) continue;
+                    ++nl;
+                    uint32_t v = tb == 0 ? 1u : (tb <= 3 ? 1u << tb : (tb <= 6 ? 1u << (tb - 3) : 0u));
+                    v &= need_mask;
+                    for (int b = 3; b >= 0 && v; --b) {
+                        if (!((v >> b) & 1)) continue;
+                        if (basis[b]) {
+                            v ^= basis[b];
+                        } else {
+                            basis[b] = v;
+                            ++rank;
+                            v = 0;
+                        }
+                    }
+                }
+                return 1 + 4 * (__builtin_popcount(need_mask) - rank);
+            };
+            struct Best {
+                int stages, cost;
+                uint32_t R;
+            };
+            std::unordered_map<uint64_t, Best> memo;
+            std::function<std::pair<int, int>(uint64_t)> solve = [&](uint64_t dm) -> std::pair<int, int> {
+                if ((dm & all_mask) == all_mask) return {0, 0};
                 if (memo.size() > 20000) {   // too many reachable states: greedy instead
                     search = false;
-                    return 0;
+                    return {0, 0};
                 }
                 auto it = memo.find(dm);
-                if (it != memo.end()) return it->second.first;
+                if (it != memo.end()) return {it->second.stages, it->second.cost};
                 uint32_t touch = 0;
                 for (int i = 0; i < nbk; ++i)
                     if (!((dm >> i) & 1) && !plan.blocks[dense_ids[i]].diag) touch |= tbm_of[dense_ids[i]];
@@ -471,26 +505,22 @@ void build_plan(Plan& plan) {
                         cands.push_back(R);
                     }
                 }
-                int best = 1 << 20, best_low = 99;
-                uint32_t bestR = 0;
-                std::vector<uint64_t> seen;
+                Best best{1 << 20, 1 << 30, 0};
+                std::vector<std::pair<uint64_t, int>> seen;   // state reached, cost of the stage
                 for (uint32_t R : cands) {
                     const uint64_t nd = closure(dm, R);
                     if (nd == dm) continue;
-                    const int low = __builtin_popcount(R & 0xFu);
+                    const int c = stage_cost(R);
                     bool dup = false;
-                    for (uint64_t x : seen) dup = dup || x == nd;
-                    if (dup && low >= best_low) continue;
-                    seen.push_back(nd);
-                    const int v = 1 + solve(nd);
-                    if (v < best || (v == best && low < best_low)) {
-                        best = v;
-                        best_low = low;
-                        bestR = R;
-                    }
+                    for (const auto& x : seen) dup = dup || (x.first == nd && x.second <= c);
+                    if (dup) continue;
+                    seen.push_back({nd, c});
+                    const std::pair<int, int> r = solve(nd);
+                    const int v = 1 + r.first, vc = c + r.second;
+                    if (v < best.stages || (v == best.stages && vc < best.cost)) best = Best{v, vc, R};
                 }
-                memo[dm] = {best, bestR};
-                return best;
+                memo[dm] = best;
+                return {best.stages, best.cost};
             };
             auto choose_set = [&]() -> uint32_t {
                 if (!search) return 0;
@@ -500,7 +530,7 @@ void build_plan(Plan& plan) {
                 solve(dm);
                 if (!search) return 0;
                 auto it = memo.find(dm);
-                return it == memo.end() ? 0 : it->second.second;
+                return it == memo.end() ? 0 : it->second.R;
             };
             uint32_t Rfix = 0;   // chosen register set of the open stage (0: grow greedily)
             while (left) {

@@ -80,6 +80,7 @@ def lib():
             "tcng_autotune": [i32, i32, i32, C.c_char_p],
             "tcng_autotune_circuit": [vp, vp, sz, vp, sz, vp, i32, C.c_char_p, C.POINTER(dp)],
             "tcng_autotune_report": [C.c_char_p, sz],
+            "tcng_fma_peak": [i32, C.POINTER(dp)],
             "tcng_sync_status": [],
             "tcng_profile_enable": [i32],
             "tcng_profile_read": [C.c_char_p, sz, i32],
@@ -305,6 +306,13 @@ def tcng_get_option(opt):
     return v.value
 
 
+def tcng_fma_peak(fp64=False):
+    """Measured FMA throughput in TFLOP/s (FP32, or FP64 with fp64=True)."""
+    out = C.c_double(0.0)
+    _check(lib().tcng_fma_peak(int(bool(fp64)), C.byref(out)))
+    return out.value
+
+
 def tcng_autotune(n, dtype, batch, cache_path=None):
     _check(lib().tcng_autotune(int(n), int(dtype), int(batch),
                                cache_path.encode() if cache_path else None))
@@ -381,7 +389,7 @@ EXPORTED = [
     "tcng_hamiltonian_apply",
     "tcng_energy_grad", "tcng_energy_grad_ragged", "tcng_apply_shared_unitary", "tcng_marginal_probs", "tcng_measure",
     "tcng_adam_step",
-    "tcng_adam_step_f32", "tcng_mlp_forward", "tcng_mlp_backward", "tcng_set_option",
+    "tcng_adam_step_f32", "tcng_mlp_forward", "tcng_mlp_backward", "tcng_set_option", "tcng_fma_peak",
     "tcng_get_option", "tcng_autotune", "tcng_autotune_circuit", "tcng_autotune_report", "tcng_sync_status", "tcng_describe_plan",
     "tcng_profile_enable", "tcng_profile_read",
     "tcng_launch_count", "tcng_last_error", "tcng_version",
