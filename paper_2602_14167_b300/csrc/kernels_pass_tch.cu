@@ -487,8 +487,10 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
             s_abort = 1;
             break;
         }
-        // the tile's scale from its largest component (one extra read of the rows)
+        // the tile's scale from its largest component: one extra read of row 0; row 1
+        // stays in registers for the first stage
         float sc, isc;
+        float2 x1[16];
         {
             const StageH& S = sst[0];
             const bool pairs = S.sr[0] == 1;
@@ -499,9 +501,14 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
                 const int tau = (FORM == FORM_ROT && S.nj) ? (row & 15) >> (4 - S.nj) : 0;
                 int L[16];
                 stage_slots<FORM>(S, lock_row(S, row), tau, L);
-                float2 x[16];
-                load_row<FORM>(buf, L, pairs, x);
-                m = fmaxf(m, row_max(x));
+                if (k == 0) {
+                    float2 x[16];
+                    load_row<FORM>(buf, L, pairs, x);
+                    m = fmaxf(m, row_max(x));
+                } else {
+                    load_row<FORM>(buf, L, pairs, x1);
+                    m = fmaxf(m, row_max(x1));
+                }
             }
             m = warp_max(m);
             if (lane == 0) redm[grp][gw] = m;
@@ -512,20 +519,27 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
             tile_scale(mt, sc, isc);
         }
         float nin = 0.f;
-        for (int s = 0; s < nst; ++s, ++q) {
+        // one stage (first: stage 0, which takes row 1 from x1 and scales)
+        auto stage = [&](const int s, const bool first) {
             const StageH& S = sst[s];
             const bool pairs = S.sr[0] == 1;
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
+            for (int kk = 0; kk < 2; ++kk) {
+                const int k = first ? 1 - kk : kk;
                 const int rb = 2 * half + k;
                 const int row = rb * 128 + quarter * 32 + lane;
                 const int tau = (FORM == FORM_ROT && S.nj) ? (row & 15) >> (4 - S.nj) : 0;
                 int L[16];
                 stage_slots<FORM>(S, lock_row(S, row), tau, L);
                 float2 x[16];
-                load_row<FORM>(buf, L, pairs, x);
+                if (first && kk == 0) {
+#pragma unroll
+                    for (int v = 0; v < 16; ++v) x[v] = x1[v];
+                } else {
+                    load_row<FORM>(buf, L, pairs, x);
+                }
                 if (FORM == FORM_ROT && S.nj) unrotate_h(x, tau, S.nj);
-                if (s == 0) {
+                if (first) {
 #pragma unroll
                     for (int v = 0; v < 16; ++v) x[v] = make_float2(x[v].x * sc, x[v].y * sc);
                     nin += row_norm2(x);
@@ -602,7 +616,10 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
             tc_fence_before();
             sync_group(grp);
             tc_fence_after();
-        }
+            ++q;
+        };
+        stage(0, true);
+        for (int s = 1; s < nst; ++s) stage(s, false);
         if ((tid & 255) == 0) mbar_arrive(&done_bar[b]);   // the producer stores it
     }
     if (tid == 0 && s_abort && my_tiles > 0) mbar_wait_bounded(&w_bar, 0u, a.err);
@@ -881,31 +898,9 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
 #pragma unroll
             for (int i = 0; i < 6; ++i) g += g & S.hm[i];
             g |= rb << a.gb0;
-            if (s == 0) {   // the block's scale from its largest component
-                float m = 0.f;
-#pragma unroll
-                for (int ch = 0; ch < 2; ++ch) {
-                    int L[16];
-                    stage_slots<FORM_PLAIN>(S, ch ? (g | S.sr4) : g, 0, L);
-                    float2 x[16];
-                    load_row<FORM_PLAIN>(buf, L, false, x);
-                    m = fmaxf(m, row_max(x));
-                }
-                m = warp_max(m);
-                if (lane == 0) redm[chain][quarter] = m;
-                sync_chain(chain);
-                float mt = 0.f;
-#pragma unroll
-                for (int w = 0; w < 4; ++w) mt = fmaxf(mt, redm[chain][w]);
-                tile_scale(mt, sc, isc);
-            }
-#pragma unroll
-            for (int ch = 0; ch < 2; ++ch) {
-                int L[16];
-                stage_slots<FORM_PLAIN>(S, ch ? (g | S.sr4) : g, 0, L);
-                float2 x[16];
-                load_row<FORM_PLAIN>(buf, L, false, x);
-                if (s == 0) {
+            // one half of the row (register bit 4 = ch) -> FP16 hi/lo -> TMEM
+            auto put_half = [&](int ch, float2 (&x)[16], bool first) {
+                if (first) {
 #pragma unroll
                     for (int v = 0; v < 16; ++v) x[v] = make_float2(x[v].x * sc, x[v].y * sc);
                     nin += row_norm2(x);
@@ -915,6 +910,40 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
                 for (int v = 0; v < 16; ++v) split_f16(x[v], hi[v], lo[v]);
                 tc_st16(lane_base + col + 16u * ch, hi);
                 tc_st16(lane_base + col + 32u + 16u * ch, lo);
+            };
+            if (s == 0) {   // the block's scale from its largest component; half 1 is kept
+                float m;
+                int L[16];
+                {
+                    stage_slots<FORM_PLAIN>(S, g, 0, L);
+                    float2 x[16];
+                    load_row<FORM_PLAIN>(buf, L, false, x);
+                    m = row_max(x);
+                }
+                float2 x1[16];
+                stage_slots<FORM_PLAIN>(S, g | S.sr4, 0, L);
+                load_row<FORM_PLAIN>(buf, L, false, x1);
+                m = warp_max(fmaxf(m, row_max(x1)));
+                if (lane == 0) redm[chain][quarter] = m;
+                sync_chain(chain);
+                float mt = 0.f;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) mt = fmaxf(mt, redm[chain][w]);
+                tile_scale(mt, sc, isc);
+                put_half(1, x1, true);
+                stage_slots<FORM_PLAIN>(S, g, 0, L);
+                float2 x[16];
+                load_row<FORM_PLAIN>(buf, L, false, x);
+                put_half(0, x, true);
+            } else {
+#pragma unroll
+                for (int ch = 0; ch < 2; ++ch) {
+                    int L[16];
+                    stage_slots<FORM_PLAIN>(S, ch ? (g | S.sr4) : g, 0, L);
+                    float2 x[16];
+                    load_row<FORM_PLAIN>(buf, L, false, x);
+                    put_half(ch, x, false);
+                }
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
