@@ -586,6 +586,29 @@ def apps_bench(args, dev, dist, world):
     res[f"shadows_n{n}_s{S}"] = {"snapshots_per_s": world * S / (ms * 1e-3), "ms_per_256": ms,
                                  "paper_context": "0.29 s for 256 snapshots of 20 qubits on an RTX 5090"}
     st.free()
+    # warm-start MLP training step (forward, periodic loss, backward, Adam) on the
+    # tcgen05 BF16 GEMMs: 4096 chains, 24 -> 512 -> 512 -> 720
+    from paper_2602_14167_b300.warmstart import MLP
+    N, F, H, O = 4096, 24, 512, 720
+    mlp = MLP(F, H, O, seed=0, device=dev)
+    rng = np.random.default_rng(7)
+    x = torch.tensor(rng.uniform(-1, 1, (N, F)), dtype=torch.float32, device=dev)
+    tgt = torch.tensor(rng.uniform(-np.pi, np.pi, (N, O)), dtype=torch.float32, device=dev)
+    msk = torch.ones((N, O), dtype=torch.float32, device=dev)
+
+    def mlp_step():
+        y = mlp.forward(x)
+        mlp.backward(x, y, tgt, msk)
+        T.tcng_adam_step_f32(mlp.flat, mlp.m, mlp.v, mlp.grads, mlp.flat.numel(), 1e-3, 0.9, 0.999, 1e-8,
+                             mlp.step)
+
+    ms = timed(mlp_step, args.steps, args.warmup, dist, dev)
+    flops = 6.0 * N * (F * H + H * H + H * O)   # forward 2NK per layer, backward twice that
+    bf16_peak = tf32 * 2.25 / 1.1
+    res["warmstart_mlp_step_n4096"] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+                                       "bf16_peak_tflops": bf16_peak,
+                                       "frac": flops / (ms * 1e-3) / 1e12 / bf16_peak,
+                                       "note": "8 GEMMs of at most 4096 x 720 x 512: latency-bound"}
     torch.cuda.empty_cache()
     return res
 
