@@ -689,7 +689,19 @@ def paths_bench(args, dev):
         "hbm_peak": hbm, "frac": len(gu) * 2 * S / (ms * 1e-3) / 1e9 / hbm,
         "kernel_ms": {k: [v[0], v[1]] for k, v in prof.items()}}
     st.free()
-    # shared-unitary apply (tcgen05, TF32 split): 64 states of 20 qubits, 4-qubit unitaries
+    # a string wider than a tile (the parity X...X): one pass reading the pairs from global memory
+    n = 28
+    st = StateBatch(n, dtype="c64")
+    st.amplitudes(0).fill_(2.0 ** (-n / 2))
+    from workloads import pauli_terms
+    par = pauli_terms([{q: "X" for q in range(n)}])
+    outw = torch.empty((1, 1), dtype=torch.float64, device=dev)
+    ms = timed(lambda: T.tcng_expect_pauli(st.handle, par, outw), args.steps, args.warmup, None, dev)
+    S = 8 << n
+    res["expect_wide_parity_n28_c64"] = {"ms": ms, "gbs": S / (ms * 1e-3) / 1e9, "frac": S / (ms * 1e-3) / 1e9 / hbm,
+                                         "value": float(outw[0, 0])}
+    st.free()
+    # shared-unitary apply (one-gate circuit on the FP16 tile passes): 64 states of 20 qubits, 4-qubit unitaries
     n, B = 20, 64
     st = StateBatch(n, batch=B, dtype="c64")
     rng = np.random.default_rng(5)

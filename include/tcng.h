@@ -155,12 +155,16 @@ tcng_status tcng_apply_circuit_pooled(tcng_state* st, const tcng_gate* ops, size
 /*
  * tcng_expect_pauli -- out_dev[b][t] = <psi_b|P_t|psi_b> (real; the paper's
  * expectation_ps, Sec. I.B; coefficients are NOT applied).
- *   terms     host array [n_terms <= 4096] of Pauli strings (masks < 2^n);
+ *   terms     host array [n_terms <= 4096] of Pauli strings (masks < 2^n of
+ *             every item's n);
  *   out_dev   device double [batch][n_terms].
- * All items must have the same n.  A term may have at most tile_bits - 1 X/Y
- * factors above qubit 0 (12 for complex64, 11 for complex128 at the default
- * tile bits), else EINVAL.  Sums accumulate in FP64 in a fixed order (bitwise
- * reproducible).  Errors: EINVAL, ENOMEM, EUNSUPPORTED (ragged), ECUDA.
+ * Terms are grouped into tile passes (one read of the state per pass); a term
+ * with more X/Y factors above qubit 0 than a tile gathers (tile_bits - 1: 12
+ * for complex64, 11 for complex128 at the default tile bits), e.g. the parity
+ * X...X, gets a pass of its own that reads the amplitude pairs (x, x ^ m) from
+ * global memory.  A ragged batch is evaluated one size class at a time.  Sums
+ * accumulate in FP64 in a fixed order (bitwise reproducible).  Errors: EINVAL,
+ * ENOMEM, ECUDA.
  */
 tcng_status tcng_expect_pauli(const tcng_state* st, const tcng_pauli* terms, size_t n_terms,
                               double* out_dev, void* stream);
@@ -187,7 +191,8 @@ tcng_status tcng_expect_pauli(const tcng_state* st, const tcng_pauli* terms, siz
  * no state carries over between calls.  The call takes the library's host lock
  * like every other entry point.  No device-side error word is kept for this
  * call: a bounded device-side wait that times out ends the pass early and the
- * affected values of out_dev are NaN.
+ * affected values of out_dev are NaN.  Terms wider than a tile (see
+ * tcng_expect_pauli) are rejected with EINVAL here.
  */
 tcng_status tcng_expect_pauli_noalloc(const void* psi_dev, int n, tcng_dtype dt,
                                       const tcng_pauli* terms, size_t n_terms, double* out_dev,

@@ -351,7 +351,7 @@ static void group_span(const tcng_state* st, const std::vector<int>& items, void
 // Group Pauli terms into tile passes: a term joins a pass if its X bits above
 // the contiguous low bits fit the pass's gather set.
 void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
-                      std::vector<DevPass>& passes, std::vector<ExpPass>& eps) {
+                      std::vector<DevPass>& passes, std::vector<ExpPass>& eps, std::vector<size_t>* wide) {
     const uint64_t lim = (n >= 64) ? ~0ULL : ((1ULL << n) - 1);
     for (size_t t = 0; t < T; ++t)
         if ((terms[t].xmask & ~lim) || (terms[t].zmask & ~lim))
@@ -366,12 +366,20 @@ void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
     const int low0 = std::min(std::min(low, m), kExpLowBits);
     auto mask_below = [](int b) { return b >= 64 ? ~0ULL : ((1ULL << b) - 1); };
     // a tile keeps at least its lowest qubit contiguous (16-byte copies), so a term
-    // may have at most m - 1 X/Y factors above qubit 0
+    // may have at most m - 1 X/Y factors above qubit 0; wider terms go to `wide`
+    // (evaluated from global memory) when the caller takes them
+    std::vector<char> done(T, 0);
+    size_t left = T;
     if (n > m)
         for (size_t t = 0; t < T; ++t)
-            if (__builtin_popcountll(terms[t].xmask & ~1ULL) > m - 1)
-                throw std::invalid_argument("Pauli term " + std::to_string(t) + ": more than " +
-                                            std::to_string(m - 1) + " X/Y factors above qubit 0");
+            if (__builtin_popcountll(terms[t].xmask & ~1ULL) > m - 1) {
+                if (!wide)
+                    throw std::invalid_argument("Pauli term " + std::to_string(t) + ": more than " +
+                                                std::to_string(m - 1) + " X/Y factors above qubit 0");
+                wide->push_back(t);
+                done[t] = 1;
+                --left;
+            }
     // most constrained terms first (most X bits above the default contiguous bits):
     // the greedy packing then fills passes around them (results keep the input order)
     std::vector<size_t> order(T);
@@ -380,8 +388,6 @@ void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
         return __builtin_popcountll(terms[a].xmask & ~mask_below(low0)) >
                __builtin_popcountll(terms[b].xmask & ~mask_below(low0));
     });
-    std::vector<char> done(T, 0);
-    size_t left = T;
     while (left) {
         // contiguous low bits of this pass: the default, or fewer when the first open
         // term has more X bits above them than the tile can gather
@@ -501,7 +507,10 @@ tcng_status tcng_state_free(tcng_state* st) {
     if (!st) return TCNG_OK;
     if (st->owned) cudaFree(st->buf);
     cudaFree(st->d_off);
-    for (auto& kv : st->groups) cudaFree(kv.second.d_off);
+    for (auto& kv : st->groups) {
+        cudaFree(kv.second.d_off);
+        cudaFree(kv.second.d_items);
+    }
     for (auto& kv : st->pack) cudaFree(kv.second.first);
     delete st;
     return TCNG_OK;
@@ -556,6 +565,7 @@ tcng_status tcng_state_init(tcng_state** out, tcng_dtype dt, int batch, const in
             std::vector<long long> go;
             for (int b : kv.second.items) go.push_back(off[b]);
             kv.second.d_off = dev_copy(go);
+            kv.second.d_items = dev_copy(kv.second.items);
         }
         tcng_state* raw = st.release();
         s = tcng_state_reset(raw, stream);
@@ -736,52 +746,68 @@ static tcng_status expect_impl(const tcng_state* st, const tcng_pauli* terms, si
     if (n_terms == 0) return TCNG_OK;
     if (!terms) return fail(TCNG_EINVAL, "terms is NULL");
     if (n_terms > 4096) return fail(TCNG_EINVAL, "at most 4096 terms per call");
-    if (st->groups.size() != 1)
-        return fail(TCNG_EUNSUPPORTED, "expectations of ragged batches: call per size class");
     std::lock_guard<std::mutex> lk(g_mu);
     TCNG_TRY({
-        const int n = st->n[0];
-        const int items = st->batch;
         DeviceCtx& c = ctx();
         const PlanOptions o = plan_options(st->dt, false);
-        std::vector<DevPass> passes;
-        std::vector<ExpPass> eps;
-        plan_expectation(n, o.tile_bits, o.chunk_bits, terms, n_terms, passes, eps);
-        TermSet* ts = get_terms(terms, n_terms, n);
-        const int m = passes[0].m;
-        const long long tpi = 1ll << (n - m);
-        const long long want = (num_sms() + items - 1) / items;
-        const int nblk = (int)std::max<long long>(1, std::min<long long>(tpi, want));
-        double* partial = static_cast<double*>(
-            c.scratch("exp_partial", sizeof(double) * (size_t)items * n_terms * nblk));
-        if (!partial) return fail(TCNG_ENOMEM, "expectation scratch");
-        void* tbase = nullptr;
-        long long tstride = -1;
-        group_span(st, st->groups.begin()->second.items, &tbase, &tstride);
-        for (size_t i = 0; i < passes.size(); ++i) {
-            cudaError_t e;
-            // one tensor copy per tile where the pass's bit runs fit a tensor map
-            TmaTile tma{};
+        const bool ragged = st->groups.size() > 1;
+        // one size class at a time (a ragged batch has several); results go to the
+        // classes' batch rows
+        for (const auto& kv : st->groups) {
+            const int n = kv.first;
+            const tcng_state::Group& grp = kv.second;
+            const int items = (int)grp.items.size();
+            std::vector<DevPass> passes;
+            std::vector<ExpPass> eps;
+            std::vector<size_t> wide;   // strings wider than a tile: one global-memory pass each
+            plan_expectation(n, o.tile_bits, o.chunk_bits, terms, n_terms, passes, eps, &wide);
+            TermSet* ts = get_terms(terms, n_terms, n);
+            const int m = passes.empty() ? std::min(o.tile_bits, n) : passes[0].m;
+            const long long tpi = 1ll << (n - m);
+            const long long want = (num_sms() + items - 1) / items;
+            const int nblk = (int)std::max<long long>(1, std::min<long long>(tpi, want));
+            double* partial = static_cast<double*>(
+                c.scratch("exp_partial", sizeof(double) * (size_t)items * n_terms * nblk));
+            if (!partial) return fail(TCNG_ENOMEM, "expectation scratch");
+            void* tbase = nullptr;
+            long long tstride = -1;
+            group_span(st, grp.items, &tbase, &tstride);
             const int es = st->dt == TCNG_C64 ? 8 : 16;
-            if (items == 1 || tstride > 0) {
-                tma = make_tma_tile(tbase, n, es, passes[i], items, tstride);
-                if (!tma.rank)   // scattered gather bits: four chunks per gather4 copy
-                    tma = make_tma_gather4(tbase, st->off[st->groups.begin()->second.items[0]], n, es,
-                                           passes[i], items, tstride);
+            for (size_t i = 0; i < passes.size(); ++i) {
+                cudaError_t e;
+                // one tensor copy per tile where the pass's bit runs fit a tensor map
+                TmaTile tma{};
+                if (items == 1 || tstride > 0) {
+                    tma = make_tma_tile(tbase, n, es, passes[i], items, tstride);
+                    if (!tma.rank)   // scattered gather bits: four chunks per gather4 copy
+                        tma = make_tma_gather4(tbase, st->off[grp.items[0]], n, es, passes[i], items, tstride);
+                }
+                ProfScope ps(st->dt == TCNG_C64 ? "expect_pass_c64" : "expect_pass_c128", s);
+                if (st->dt == TCNG_C64)
+                    e = launch_expect_pass<float2>(static_cast<const float2*>(st->buf), grp.d_off, items, n,
+                                                   passes[i], eps[i], partial, (int)n_terms, nblk, c.err, s, &tma);
+                else
+                    e = launch_expect_pass<double2>(static_cast<const double2*>(st->buf), grp.d_off, items, n,
+                                                    passes[i], eps[i], partial, (int)n_terms, nblk, c.err, s,
+                                                    &tma);
+                if (e != cudaSuccess) return cuda_fail(e, "expectation pass");
             }
-            ProfScope ps(st->dt == TCNG_C64 ? "expect_pass_c64" : "expect_pass_c128", s);
-            if (st->dt == TCNG_C64)
-                e = launch_expect_pass<float2>(static_cast<const float2*>(st->buf), st->d_off, items, n,
-                                               passes[i], eps[i], partial, (int)n_terms, nblk, c.err, s, &tma);
-            else
-                e = launch_expect_pass<double2>(static_cast<const double2*>(st->buf), st->d_off, items, n,
-                                                passes[i], eps[i], partial, (int)n_terms, nblk, c.err, s, &tma);
-            if (e != cudaSuccess) return cuda_fail(e, "expectation pass");
+            for (size_t w : wide) {
+                ProfScope ps("expect_wide", s);
+                cudaError_t e;
+                if (st->dt == TCNG_C64)
+                    e = launch_expect_wide<float2>(static_cast<const float2*>(st->buf), grp.d_off, items, n,
+                                                   terms[w], (int)w, partial, (int)n_terms, nblk, s);
+                else
+                    e = launch_expect_wide<double2>(static_cast<const double2*>(st->buf), grp.d_off, items, n,
+                                                    terms[w], (int)w, partial, (int)n_terms, nblk, s);
+                if (e != cudaSuccess) return cuda_fail(e, "wide expectation pass");
+            }
+            ProfScope ps("expect_finalize", s);
+            cudaError_t e = launch_expect_finalize(partial, nblk, (int)n_terms, out_dev, coeffs_dev, ts->d_c,
+                                                   energy_dev, items, s, ragged ? grp.d_items : nullptr);
+            if (e != cudaSuccess) return cuda_fail(e, "expectation finalize");
         }
-        ProfScope ps("expect_finalize", s);
-        cudaError_t e = launch_expect_finalize(partial, nblk, (int)n_terms, out_dev, coeffs_dev, ts->d_c,
-                                               energy_dev, items, s);
-        if (e != cudaSuccess) return cuda_fail(e, "expectation finalize");
         return TCNG_OK;
     })
 }

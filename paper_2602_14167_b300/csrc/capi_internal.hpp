@@ -19,6 +19,7 @@ struct tcng_state {
     struct Group {
         std::vector<int> items;
         long long* d_off = nullptr;   // device element offsets of the group's items
+        int* d_items = nullptr;       // device batch indices of the group's items
     };
     tcng_dtype dt = TCNG_C64;
     int batch = 0;
@@ -141,7 +142,7 @@ DevPlan* get_plan(int n, const tcng_gate* ops, size_t n_ops, const double* pool,
 void* plan_table(DevPlan* dp, size_t elem, int items);
 TermSet* get_terms(const tcng_pauli* terms, size_t n_terms, int n);
 void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
-                      std::vector<DevPass>& passes, std::vector<ExpPass>& eps);
+                      std::vector<DevPass>& passes, std::vector<ExpPass>& eps, std::vector<size_t>* wide = nullptr);
 // tma_base: device address of the group's first item and item_stride its spacing
 // in bytes (< 0: items not equally spaced -> per-chunk bulk copies).
 template <typename C>
@@ -164,6 +165,11 @@ cudaError_t launch_build_stage_w(const DevPlan* dp, const double2* table, long l
 // FP16-split tensor-core passes (unitary plans, one W set for every tile):
 // whether pass `pass` can run them, and the launch.
 bool pass_tch_eligible(const DevPlan* dp, int pass);
+// One Pauli string with more X/Y factors than a tile gathers, straight from
+// global memory (kernels_expect_wide.cu): partial[(item * n_out + out) * nblk + blk].
+template <typename C>
+cudaError_t launch_expect_wide(const C* state, const long long* item_off, int items, int n, const tcng_pauli& t,
+                               int out, double* partial, int n_out, int nblk, cudaStream_t s);
 cudaError_t launch_pass_tch(const DevPlan* dp, int pass, int items, const void* wops_h, unsigned* err,
                             const TmaTile& tma, bool swizzled, float2* state, const long long* item_off,
                             cudaStream_t s);

@@ -417,22 +417,23 @@ __global__ void __launch_bounds__(512, 1) expect_pass_kernel(const C* __restrict
 __global__ void expect_finalize_kernel(const double* __restrict__ partial, int nblk, int n_out,
                                        double* __restrict__ out, const double* __restrict__ coeffs,
                                        const double* __restrict__ term_coeff, double* __restrict__ energy,
-                                       int items) {
+                                       int items, const int* __restrict__ rows) {
     const int item = blockIdx.x;
+    const long long row = rows ? rows[item] : item;
     extern __shared__ double vals[];
     for (int t = threadIdx.x; t < n_out; t += blockDim.x) {
         double s = 0;
         const double* pp = partial + ((long long)item * n_out + t) * nblk;
         for (int b = 0; b < nblk; ++b) s += pp[b];
-        if (out) out[(long long)item * n_out + t] = s;
-        const double c = energy ? (coeffs ? coeffs[(long long)item * n_out + t] : term_coeff[t]) : 0.0;
+        if (out) out[row * n_out + t] = s;
+        const double c = energy ? (coeffs ? coeffs[row * n_out + t] : term_coeff[t]) : 0.0;
         vals[t] = c * s;
     }
     __syncthreads();
     if (energy && threadIdx.x == 0) {
         double e = 0;
         for (int t = 0; t < n_out; ++t) e += vals[t];
-        energy[item] = e;
+        energy[row] = e;
     }
 }
 
@@ -666,9 +667,9 @@ cudaError_t launch_expect_pass(const C* state, const long long* item_off, int it
 
 cudaError_t launch_expect_finalize(const double* partial, int nblk, int n_out, double* out,
                                    const double* coeffs, const double* term_coeff, double* energy,
-                                   int items, cudaStream_t s) {
+                                   int items, cudaStream_t s, const int* rows) {
     expect_finalize_kernel<<<items, 256, sizeof(double) * n_out, s>>>(partial, nblk, n_out, out,
-                                                                      coeffs, term_coeff, energy, items);
+                                                                      coeffs, term_coeff, energy, items, rows);
     count_launch();
     return cudaGetLastError();
 }

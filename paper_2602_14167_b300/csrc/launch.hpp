@@ -110,9 +110,10 @@ cudaError_t launch_measure(C* state, const long long* item_off, int items, int n
                            double* hist, int splits, void* proj, cudaStream_t s);
 size_t measure_proj_bytes(int items);
 int measure_splits(int items, int n);
+// rows: batch row of each item (out, coefficients, energy), or NULL for item i -> row i
 cudaError_t launch_expect_finalize(const double* partial, int nblk, int n_out, double* out,
                                    const double* coeffs, const double* term_coeff, double* energy,
-                                   int items, cudaStream_t s);
+                                   int items, cudaStream_t s, const int* rows = nullptr);
 template <typename C>
 cudaError_t launch_ham_apply(const C* psi, const long long* off_in, C* out, const long long* off_out,
                              int items, int n, const HTerm* terms, int T, const double* coeffs,

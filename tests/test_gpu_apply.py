@@ -241,15 +241,52 @@ def test_expectations_scattered_gathers(T, dtype):
     assert np.max(np.abs(vals - vref)) < (1e-6 if dtype == "c64" else 1e-12)
 
 
-def test_expectation_term_wider_than_a_tile_is_rejected(T):
+@pytest.mark.parametrize("dtype,n", [("c128", 16), ("c64", 17), ("c64", 22)])
+def test_expectation_terms_wider_than_a_tile(T, dtype, n):
+    """Strings with more X/Y factors than a tile gathers (the parity X...X, Y-heavy
+    and random high-weight strings) run from global memory; together with
+    ordinary terms in one call, every value against the oracle."""
     from paper_2602_14167_b300 import StateBatch
     from workloads import pauli_terms
-    st = StateBatch(16, dtype="c128")   # 12 tile bits: at most 11 X/Y factors above qubit 0
-    with pytest.raises(T.TcngError):
-        st.expect(pauli_terms([{q: "X" for q in range(1, 13)}]))
-    T.tcng_sync_status()
-    vals = st.expect(pauli_terms([{q: "X" for q in range(1, 12)}]))   # 11 fit
-    assert vals.shape == (1, 1)
+    rng = np.random.default_rng(n)
+    wide = [{q: "X" for q in range(n)}, {q: "Y" for q in range(1, n)},
+            {q: "XYZ"[int(rng.integers(3))] for q in range(n)},
+            {q: "XY"[q % 2] for q in range(2, n, 1)}]
+    terms = np.concatenate([pauli_terms(wide), gen.random_pauli_strings(n, 12, 4, seed=n),
+                            gen.tfim_terms(n, 1.0, 0.7)])
+    st = StateBatch(n, dtype=dtype)
+    psi = gen.random_state(n, seed=2 * n)
+    st.amplitudes(0).copy_(torch.tensor(psi, dtype=st.cdtype, device="cuda"))
+    got = st.expect(terms)[0].cpu().numpy()
+    ref = sv.expect(n, psi, terms).real
+    assert np.max(np.abs(got - ref)) < (1e-12 if dtype == "c128" else 1e-5)
+    e = st.energy(terms)[0].item()
+    assert abs(e - float(np.dot(terms["coeff"], ref))) < (1e-11 if dtype == "c128" else 1e-4)
+    st.free()
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_expectations_of_a_ragged_batch(T, dtype):
+    """A batch of states of 9, 14 and 17 qubits: one expectation call per size class
+    inside the library, values and energies in the items' own rows."""
+    from paper_2602_14167_b300 import StateBatch
+    ns = [14, 9, 17, 14, 9]
+    st = StateBatch(ns, dtype=dtype)
+    terms = np.concatenate([gen.random_pauli_strings(9, 10, 3, seed=4), gen.tfim_terms(9, 1.0, 0.5)])
+    psis = [gen.random_state(n, seed=30 + i) for i, n in enumerate(ns)]
+    for i, psi in enumerate(psis):
+        st.amplitudes(i).copy_(torch.tensor(psi, dtype=st.cdtype, device="cuda"))
+    coeffs = torch.tensor(np.random.default_rng(1).normal(size=(len(ns), len(terms))), device="cuda")
+    vals = torch.empty((len(ns), len(terms)), dtype=torch.float64, device="cuda")
+    energy = torch.empty(len(ns), dtype=torch.float64, device="cuda")
+    T.tcng_expect_energy(st.handle, terms, coeffs, vals, energy)
+    vals, energy, cf = vals.cpu().numpy(), energy.cpu().numpy(), coeffs.cpu().numpy()
+    tol = 1e-12 if dtype == "c128" else 1e-5
+    for i, (n, psi) in enumerate(zip(ns, psis)):
+        ref = sv.expect(n, psi, terms).real
+        assert np.max(np.abs(vals[i] - ref)) < tol
+        assert abs(energy[i] - float(np.dot(cf[i], ref))) < 50 * tol
+    st.free()
 
 
 def test_energy_per_item_coefficients(T):
