@@ -381,8 +381,19 @@ def vqe_bench(args, dev, dist, world):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms, dist, dev)
+    # FP32 ALU roofline of the adjoint kernel: algorithmic flops of one unfused
+    # energy + gradient evaluation at n=16 (forward 12 (32 x 16 + 16 x 6) flop per
+    # amplitude, reverse twice that, 576 gradient dots of 8 flop per amplitude,
+    # lambda = H psi) against the measured FP32 FMA peak
+    from paper_2602_14167_b300 import tcng as T
+    flop = (12 * (32 * 16 + 16 * 6) * 3 + 576 * 8 + 31 * 8) * 2.0 ** 16
+    fp32 = T.tcng_fma_peak(False)
+    ach = flop * B / (ms * 1e-3) / 1e12
     res[f"n16_b{B}"] = {"evals_per_s": world * B / (ms * 1e-3), "ms_per_batch": ms,
-                        "params_per_item": vb.P}
+                        "params_per_item": vb.P,
+                        "roofline": {"bound": "alu", "achieved": ach, "peak": fp32, "unit": "TFLOP/s",
+                                     "frac": ach / fp32, "peak_kind": "measured FP32 FMA (tcng_fma_peak)",
+                                     "flop_per_eval": flop}}
     del vb
 
     # ragged batch, one persistent launch
