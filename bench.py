@@ -391,6 +391,7 @@ def vqe_bench(args, dev, dist, world):
     ach = flop * B / (ms * 1e-3) / 1e12
     res[f"n16_b{B}"] = {"evals_per_s": world * B / (ms * 1e-3), "ms_per_batch": ms,
                         "params_per_item": vb.P,
+                        "cuda_graph_replay": bool(T.tcng_get_option(T.OPT_USE_GRAPHS)),
                         "roofline": {"bound": "alu", "achieved": ach, "peak": fp32, "unit": "TFLOP/s",
                                      "frac": ach / fp32, "peak_kind": "measured FP32 FMA (tcng_fma_peak)",
                                      "flop_per_eval": flop}}

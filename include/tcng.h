@@ -220,7 +220,8 @@ tcng_status tcng_energy(const tcng_state* st, const tcng_pauli* terms, size_t n_
 /*
  * tcng_hamiltonian_apply -- lambda_b = H_b psi_b for every item (the co-state
  * that starts the adjoint sweep); out must be a state with the same shape and
- * dtype as st.  H_b = sum_t c[b][t] P_t with coeffs_dev as in tcng_energy.
+ * dtype as st.  H_b = sum_t c[b][t] P_t with coeffs_dev as in tcng_energy.  A
+ * ragged batch is applied one size class at a time.
  */
 tcng_status tcng_hamiltonian_apply(const tcng_state* st, const tcng_pauli* terms, size_t n_terms,
                                    const double* coeffs_dev, tcng_state* out, void* stream);

@@ -838,22 +838,28 @@ tcng_status tcng_hamiltonian_apply(const tcng_state* st, const tcng_pauli* terms
     if (!st || !out || (!terms && n_terms)) return fail(TCNG_EINVAL, "null argument");
     if (out->dt != st->dt || out->batch != st->batch || out->n != st->n)
         return fail(TCNG_EINVAL, "output state shape differs");
-    if (st->groups.size() != 1) return fail(TCNG_EUNSUPPORTED, "ragged batch");
     std::lock_guard<std::mutex> lk(g_mu);
     TCNG_TRY({
-        const int n = st->n[0];
         cudaStream_t s = static_cast<cudaStream_t>(stream);
-        TermSet* ts = get_terms(terms, n_terms, n);
-        cudaError_t e;
-        if (st->dt == TCNG_C64)
-            e = launch_ham_apply<float2>(static_cast<const float2*>(st->buf), st->d_off,
-                                         static_cast<float2*>(out->buf), out->d_off, st->batch, n,
-                                         ts->d_h, (int)n_terms, coeffs_dev, ts->d_c, s);
-        else
-            e = launch_ham_apply<double2>(static_cast<const double2*>(st->buf), st->d_off,
-                                          static_cast<double2*>(out->buf), out->d_off, st->batch, n,
-                                          ts->d_h, (int)n_terms, coeffs_dev, ts->d_c, s);
-        if (e != cudaSuccess) return cuda_fail(e, "H apply");
+        const bool ragged = st->groups.size() > 1;
+        for (const auto& kv : st->groups) {   // one size class at a time
+            const int n = kv.first;
+            const tcng_state::Group& gi = kv.second;
+            const tcng_state::Group& go = out->groups.at(n);
+            TermSet* ts = get_terms(terms, n_terms, n);
+            const int items = (int)gi.items.size();
+            const int* rows = ragged ? gi.d_items : nullptr;
+            cudaError_t e;
+            if (st->dt == TCNG_C64)
+                e = launch_ham_apply<float2>(static_cast<const float2*>(st->buf), gi.d_off,
+                                             static_cast<float2*>(out->buf), go.d_off, items, n, ts->d_h,
+                                             (int)n_terms, coeffs_dev, ts->d_c, s, rows);
+            else
+                e = launch_ham_apply<double2>(static_cast<const double2*>(st->buf), gi.d_off,
+                                              static_cast<double2*>(out->buf), go.d_off, items, n, ts->d_h,
+                                              (int)n_terms, coeffs_dev, ts->d_c, s, rows);
+            if (e != cudaSuccess) return cuda_fail(e, "H apply");
+        }
         return TCNG_OK;
     })
 }

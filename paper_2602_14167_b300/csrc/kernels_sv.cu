@@ -442,9 +442,10 @@ template <typename C>
 __global__ void ham_apply_kernel(const C* __restrict__ psi_all, const long long* __restrict__ off_in,
                                  C* __restrict__ out_all, const long long* __restrict__ off_out,
                                  const HTerm* __restrict__ terms, int T, const double* __restrict__ coeffs,
-                                 const double* __restrict__ term_coeff, long long N) {
+                                 const double* __restrict__ term_coeff, long long N, const int* __restrict__ rows) {
     using R = typename Real<C>::T;
     const int item = blockIdx.y;
+    const long long row = rows ? rows[item] : item;   // the item's coefficient row
     const C* psi = psi_all + off_in[item];
     C* out = out_all + off_out[item];
     for (long long y = blockIdx.x * (long long)blockDim.x + threadIdx.x; y < N;
@@ -454,7 +455,7 @@ __global__ void ham_apply_kernel(const C* __restrict__ psi_all, const long long*
             const HTerm h = terms[t];
             const long long x = y ^ (long long)h.xm;
             const C v = psi[x];
-            const R c = (R)(coeffs ? coeffs[(long long)item * T + t] : term_coeff[t]);
+            const R c = (R)(coeffs ? coeffs[row * T + t] : term_coeff[t]);
             const int sg = __popcll((unsigned long long)x & h.zm) & 1;
             R vr = v.x, vi = v.y, tr;
             switch (h.ny & 3) {  // multiply by i^ny
@@ -677,10 +678,11 @@ cudaError_t launch_expect_finalize(const double* partial, int nblk, int n_out, d
 template <typename C>
 cudaError_t launch_ham_apply(const C* psi, const long long* off_in, C* out, const long long* off_out,
                              int items, int n, const HTerm* terms, int T, const double* coeffs,
-                             const double* term_coeff, cudaStream_t s) {
+                             const double* term_coeff, cudaStream_t s,
+                             const int* rows) {
     const long long N = 1ll << n;
     dim3 g = grid_for(N, items, 256);
-    ham_apply_kernel<C><<<g, 256, 0, s>>>(psi, off_in, out, off_out, terms, T, coeffs, term_coeff, N);
+    ham_apply_kernel<C><<<g, 256, 0, s>>>(psi, off_in, out, off_out, terms, T, coeffs, term_coeff, N, rows);
     count_launch();
     return cudaGetLastError();
 }
@@ -704,7 +706,7 @@ cudaError_t launch_ham_apply(const C* psi, const long long* off_in, C* out, cons
                                                cudaStream_t, const TmaTile*);                         \
     template cudaError_t launch_ham_apply<C>(const C*, const long long*, C*, const long long*, int,   \
                                              int, const HTerm*, int, const double*, const double*,    \
-                                             cudaStream_t);
+                                             cudaStream_t, const int*);
 TCNG_INST(float2)
 TCNG_INST(double2)
 

@@ -117,6 +117,6 @@ cudaError_t launch_expect_finalize(const double* partial, int nblk, int n_out, d
 template <typename C>
 cudaError_t launch_ham_apply(const C* psi, const long long* off_in, C* out, const long long* off_out,
                              int items, int n, const HTerm* terms, int T, const double* coeffs,
-                             const double* term_coeff, cudaStream_t s);
+                             const double* term_coeff, cudaStream_t s, const int* rows = nullptr);
 
 }  // namespace tcng

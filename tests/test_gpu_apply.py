@@ -337,6 +337,28 @@ def test_hamiltonian_apply(T):
     assert relerr(out.amplitudes(0).cpu().numpy(), ref) < 1e-12
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_hamiltonian_apply_ragged_batch(T, dtype):
+    """lambda_b = H_b psi_b over a batch of 8-, 11- and 13-qubit states with
+    per-item coefficients: one size class at a time, each item against the oracle."""
+    from paper_2602_14167_b300 import StateBatch
+    ns = [11, 8, 13, 8]
+    st, out = StateBatch(ns, dtype=dtype), StateBatch(ns, dtype=dtype)
+    terms = gen.xxz_terms(8, np.linspace(0.5, 1.5, 7), 0.6, 0.4)
+    cf = np.random.default_rng(3).normal(size=(len(ns), len(terms)))
+    psis = [gen.random_state(n, seed=40 + i) for i, n in enumerate(ns)]
+    for i, psi in enumerate(psis):
+        st.amplitudes(i).copy_(torch.tensor(psi, dtype=st.cdtype, device="cuda"))
+    T.tcng_hamiltonian_apply(st.handle, terms, torch.tensor(cf, device="cuda"), out.handle)
+    torch.cuda.synchronize()
+    tol = 1e-12 if dtype == "c128" else 1e-5
+    for i, (n, psi) in enumerate(zip(ns, psis)):
+        ref = sv.hamiltonian_apply(n, psi, terms, cf[i])
+        assert relerr(out.amplitudes(i).cpu().numpy().astype(np.complex128), ref) < tol
+    st.free()
+    out.free()
+
+
 def test_expectation_is_deterministic(T):
     n = 18
     c, th = gen.su4_brickwork(n, 4, "RZ", seed=5)
