@@ -28,6 +28,7 @@ constexpr int kRegBits = 4;          // R of an ordinary stage: 16 amplitudes pe
 constexpr int kMaxRegBits = 5;       // R of a stage holding a 5-qubit block: 32 amplitudes
 constexpr int kMaxTileBits = 14;
 constexpr int kMaxPassMat = 2048;    // complex entries of block matrices per pass (smem)
+constexpr int kMaxWideStages = 22;   // FP16 tensor-core passes: stages whose W stay resident
 constexpr int kMaxGather = 12;
 constexpr int kMaxStageGrads = 32;   // adjoint: parameterised ops per stage
 constexpr int kMaxGradSlots = 2048;  // adjoint: parameterised ops per circuit

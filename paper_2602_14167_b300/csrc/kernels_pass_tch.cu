@@ -51,7 +51,7 @@ constexpr int TH_TILE_BITS = 13;
 constexpr int TH_TILE_ELEMS = 1 << TH_TILE_BITS;
 constexpr uint32_t TH_TILE_BYTES = sizeof(float2) << TH_TILE_BITS;   // 64 KiB
 constexpr uint32_t TH_TMEM_COLS = 512;             // 4 slices x 2 tiles x (A hi 16 + A lo 16 + D 32)
-constexpr int TH_MAX_STAGES = 22;                  // stages per pass (W of all resident)
+constexpr int TH_MAX_STAGES = kMaxWideStages;      // stages per pass (W of all resident)
 constexpr int TH_MAX_STAGES_3BUF = 7;              // with three tile buffers
 constexpr int TH_MAX_STAGES_5 = 2;                 // 32-amplitude stages (16 KiB W each)
 constexpr int FORM_PLAIN = 0, FORM_ROT = 1, FORM_SWZ = 2;

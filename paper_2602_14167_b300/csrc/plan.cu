@@ -592,6 +592,18 @@ void build_plan(Plan& plan) {
                 ok = ok && (U & 0xFu) == 0 && (U >> 5) != ((1u << (dp.m - 5)) - 1);
                 if (ok) staged.swap(wide);
             }
+            // plans for the FP16 tensor-core passes keep every stage's W resident: a
+            // longer pass ends after kMaxWideStages stages and its later blocks wait
+            // for the next pass (the stages are in dependency order, so the blocks
+            // kept never need one left out)
+            if (o.wide && plan.all_unitary && !o.adjoint && (int)staged.size() > kMaxWideStages) {
+                for (size_t k = kMaxWideStages; k < staged.size(); ++k)
+                    for (int b : staged[k].blocks) {
+                        placed[b] = 0;
+                        --n_placed;
+                    }
+                staged.resize(kMaxWideStages);
+            }
             dp.stage_begin = (int)plan.stages.size();
             for (const Staged& sg : staged) {
                 DevStage st{};

@@ -38,6 +38,36 @@ def test_brickwork_plan_structure(T):
         assert p["gather"] == sorted(p["gather"]) and all(q >= p["chunk"] for q in p["gather"])
 
 
+def stage_widths(T, n, c):
+    g, p = c.to_ir()
+    out = []
+    for line in T.tcng_describe_plan(n, g, p, c.n_params, False).splitlines()[1:]:
+        if "regs=" in line:
+            out.append([tok[tok.index("{") + 1:tok.index("}")].count(",") + 1
+                        for tok in line.split("regs=")[1].split()])
+    return out
+
+
+def test_fp16_plans_cap_stages_and_use_wide_stages(T):
+    """Plans for the FP16 tensor-core passes (the default options) keep at most 22
+    stages per pass (every W resident) and take 5-qubit stages where two of them
+    replace three 4-qubit ones; with the FP16 split off the plan has only 4-qubit
+    stages and the long passes of a deep circuit on one tile stay whole."""
+    T.tcng_set_option(T.OPT_TC_FP16, 1)
+    long = stage_widths(T, 13, gen.qml_brickwall(12, 30, seed=0))
+    assert max(len(s) for s in long) <= 22 and sum(len(s) for s in long) >= 100
+    c, _ = gen.su4_brickwork(32, 14, "RZ", seed=0)
+    wide = stage_widths(T, 32, c)
+    assert sum(1 for s in wide if s and all(w == 5 for w in s)) >= 10
+    try:
+        T.tcng_set_option(T.OPT_TC_FP16, 0)
+        narrow = stage_widths(T, 32, c)
+        assert all(w == 4 for s in narrow for w in s)
+        assert max(len(s) for s in stage_widths(T, 13, gen.qml_brickwall(12, 30, seed=0))) > 22
+    finally:
+        T.tcng_set_option(T.OPT_TC_FP16, 1)
+
+
 def test_small_state_is_one_pass(T):
     c, _ = gen.random_circuit(9, 80, seed=1)
     head, passes = plan_summary(T, 9, c)
