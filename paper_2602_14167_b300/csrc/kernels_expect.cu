@@ -56,94 +56,82 @@ __device__ __forceinline__ long long ef_tile_offset(const DevPass& p, int x) {
 
 constexpr int kEfTileBits = 13;
 constexpr int kEfNbuf = 3;
-constexpr int kEfAccCols = kExpThreads / 2;   // one FP32 sum per lane pair and term
 
-struct EfTerm {          // a term of the pass, prepared once per CTA
-    float4 sg;           // (-1)^{z bit} of the register bits: tile bits 0, 10, 11, 12
-    int32_t xt;          // X mask on tile bits 1..9 as a thread offset (partner thread t ^ xt)
-    int32_t var;         // 0: Z only; else 1 + 4 XR + 2 swap + im
-    int32_t wskip;       // >= 0: warps with this bit (xor tile parity) set skip the term (X on tile bit 6 + wskip)
-    int32_t pad1;
+struct EfTerm {          // a term of the pass, prepared once per CTA (32 bytes)
+    float2 s1, s2, s3;   // (-1)^{z bit} of pair-index bits 0, 1, 2 (tile bits 10, 11, 12), duplicated
+    float sx;            // (-1)^{z bit} of tile bit 0
+    int32_t code;        // bits 0..8: xt (partner thread t ^ xt); 9..14: form (0: Z only, else
+                         // 1 + 4 XR + 2 swap + im); 15..17: wskip + 1 (warps with bit wskip of the
+                         // warp index xor tile parity set skip the term; 0: none)
 };
 
-// sum_r (-1)^{popc(r & zr)} w_r over the 16 registers: 4-level butterfly, no branch.
-__device__ __forceinline__ float ef_butterfly(const float (&w)[kExpSlots], const float4 sg) {
-    float u[8], v[4];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) u[k] = fmaf(sg.x, w[2 * k + 1], w[2 * k]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = fmaf(sg.y, u[2 * k + 1], u[2 * k]);
-    return fmaf(sg.w, fmaf(sg.z, v[3], v[2]), fmaf(sg.z, v[1], v[0]));
+// Global index of a tile's offset 0 (tile_global_base) by one warp OR-reduction:
+// lane i holds 1 << rest[i] split into 32-bit halves (zero for i >= nrest).
+__device__ __forceinline__ long long ef_tile_base(uint32_t tile, uint32_t bit_lo, uint32_t bit_hi, int lane) {
+    const bool on = (tile >> lane) & 1u;
+    const uint32_t lo = __reduce_or_sync(0xffffffffu, on ? bit_lo : 0u);
+    const uint32_t hi = __reduce_or_sync(0xffffffffu, on ? bit_hi : 0u);
+    return (long long)(((unsigned long long)hi << 32) | lo);
 }
 
-// The same over the 8 registers whose pair index i has bit K clear: the pair
-// bit (sg.x), then the two other pair bits in ascending order (sg.y, sg.z, sg.w
-// are the signs of pair bits 0, 1, 2).
-template <int K>
-__device__ __forceinline__ float ef_butterfly_half(const float (&w)[kExpSlots / 2], const float4 sg) {
-    const float s1 = K == 0 ? sg.z : sg.y, s2 = K == 2 ? sg.z : sg.w;
-    float u[4];
+// sum_r (-1)^{popc(r & zr)} w_r over the 16 registers, w packed by register pair
+// (W_i = (w_2i, w_2i+1)): three packed levels over the pair index, then the pair bit.
+__device__ __forceinline__ float ef_butterfly(const float2 (&w)[kExpSlots / 2], const EfTerm& T) {
+    float2 u[4], v[2];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) u[k] = fmaf(sg.x, w[2 * k + 1], w[2 * k]);
-    return fmaf(s2, fmaf(s1, u[3], u[2]), fmaf(s1, u[1], u[0]));
+    for (int k = 0; k < 4; ++k) u[k] = __ffma2_rn(T.s1, w[2 * k + 1], w[2 * k]);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) v[k] = __ffma2_rn(T.s2, u[2 * k + 1], u[2 * k]);
+    const float2 z = __ffma2_rn(T.s3, v[1], v[0]);
+    return fmaf(T.sx, z.y, z.x);
+}
+
+// The same over the four register pairs whose index has bit K clear (pair jj: the
+// index with a 0 inserted at bit K).
+template <int K>
+__device__ __forceinline__ float ef_butterfly_half(const float2 (&w)[kExpSlots / 4], const EfTerm& T) {
+    const float2 sa = K == 0 ? T.s2 : T.s1, sb = K == 2 ? T.s2 : T.s3;
+    const float2 u0 = __ffma2_rn(sa, w[1], w[0]), u1 = __ffma2_rn(sa, w[3], w[2]);
+    const float2 z = __ffma2_rn(sb, u1, u0);
+    return fmaf(T.sx, z.y, z.x);
 }
 
 template <bool SWAP, bool IM>
-__device__ __forceinline__ void ef_pair(const float4 q, const float2 a0, const float2 a1, float& w0, float& w1) {
+__device__ __forceinline__ float2 ef_pair(const float4 q, const float2 a0, const float2 a1) {
     float2 b0 = make_float2(q.x, q.y), b1 = make_float2(q.z, q.w);
     if (SWAP) {
         const float2 tmp = b0;
         b0 = b1;
         b1 = tmp;
     }
-    if (!IM) {
-        w0 = fmaf(b0.x, a0.x, b0.y * a0.y);
-        w1 = fmaf(b1.x, a1.x, b1.y * a1.y);
-    } else {
-        w0 = fmaf(b0.x, a0.y, -b0.y * a0.x);
-        w1 = fmaf(b1.x, a1.y, -b1.y * a1.x);
-    }
+    if (!IM) return make_float2(fmaf(b0.x, a0.x, b0.y * a0.y), fmaf(b1.x, a1.x, b1.y * a1.y));
+    return make_float2(fmaf(b0.x, a0.y, -b0.y * a0.x), fmaf(b1.x, a1.y, -b1.y * a1.x));
 }
 
 // Term with X bits: w_r = Re (IM: Im) of conj(partner) * a_r.  The partner of
 // register pair i is pair i ^ XR of thread t ^ xt: pb[512 (i ^ XR)] with pb the
 // partner thread's first pair.  XR != 0: the half form (pairs with bit K of i
-// clear, K = XR's top bit), doubled.  (Taking the partner from the thread's own
-// registers when xt = 0 is left out: those forms raise the register count of
-// the whole term loop past the limit.)
+// clear, K = XR's top bit; the 2 is in the term's scale).  (Taking the partner
+// from the thread's own registers when xt = 0 is left out: those forms raise the
+// register count of the whole term loop past the limit.)
 template <int XR, bool SWAP, bool IM>
 __device__ __forceinline__ float ef_xterm(const float2 (&a)[kExpSlots], const float4* __restrict__ pb,
-                                          const float4 sg) {
+                                          const EfTerm& T) {
     if constexpr (XR != 0) {
         constexpr int K = XR >= 4 ? 2 : (XR >= 2 ? 1 : 0);
-        float w[kExpSlots / 2];
+        float2 w[kExpSlots / 4];
 #pragma unroll
         for (int jj = 0; jj < kExpSlots / 4; ++jj) {
             const int i = ((jj >> K) << (K + 1)) | (jj & ((1 << K) - 1));   // jj with a 0 inserted at bit K
-            ef_pair<SWAP, IM>(pb[kExpThreads * (i ^ XR)], a[2 * i], a[2 * i + 1], w[2 * jj], w[2 * jj + 1]);
+            w[jj] = ef_pair<SWAP, IM>(pb[kExpThreads * (i ^ XR)], a[2 * i], a[2 * i + 1]);
         }
-        return 2.f * ef_butterfly_half<K>(w, sg);
-    }
-    float w[kExpSlots];
+        return ef_butterfly_half<K>(w, T);
+    } else {
+        float2 w[kExpSlots / 2];
 #pragma unroll
-    for (int i = 0; i < kExpSlots / 2; ++i) {
-        const float4 q = pb[kExpThreads * (i ^ XR)];
-        float2 b0 = make_float2(q.x, q.y), b1 = make_float2(q.z, q.w);
-        if (SWAP) {
-            const float2 tmp = b0;
-            b0 = b1;
-            b1 = tmp;
-        }
-        const float2 a0 = a[2 * i], a1 = a[2 * i + 1];
-        if (!IM) {
-            w[2 * i] = fmaf(b0.x, a0.x, b0.y * a0.y);
-            w[2 * i + 1] = fmaf(b1.x, a1.x, b1.y * a1.y);
-        } else {
-            w[2 * i] = fmaf(b0.x, a0.y, -b0.y * a0.x);
-            w[2 * i + 1] = fmaf(b1.x, a1.y, -b1.y * a1.x);
-        }
+        for (int i = 0; i < kExpSlots / 2; ++i) w[i] = ef_pair<SWAP, IM>(pb[kExpThreads * i], a[2 * i], a[2 * i + 1]);
+        return ef_butterfly(w, T);
     }
-    return ef_butterfly(w, sg);
 }
 
 __global__ void __launch_bounds__(kExpThreads, 1)
@@ -156,9 +144,10 @@ __global__ void __launch_bounds__(kExpThreads, 1)
     float2* bufs = reinterpret_cast<float2*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     uint64_t* bars = reinterpret_cast<uint64_t*>(bufs + (size_t)kEfNbuf * tile_elems);
     uint64_t* ebars = bars + kEfNbuf;                             // buffer released by every warp
-    float* acc = reinterpret_cast<float*>(ebars + kEfNbuf);      // [term][lane pair]
+    float* acc = reinterpret_cast<float*>(ebars + kEfNbuf);      // [term][thread]
     __shared__ double red[kExpThreads / 32][kExpTermsPerPass];
     __shared__ EfTerm sx[kExpTermsPerPass];
+    __shared__ float sf[kExpTermsPerPass];                       // Re(i^ny w) sign x (2: half forms)
     __shared__ unsigned long long szg[kExpTermsPerPass];         // Z mask on global bits
     __shared__ int s_abort, s_hasz;
     __shared__ long long s_koff[3];   // cp.async form: offsets of tile elements 1024, 2048, 4096
@@ -166,34 +155,44 @@ __global__ void __launch_bounds__(kExpThreads, 1)
     const int item = blockIdx.y;
     const int nt = ep.nterms;
     for (int i = tid; i < (kExpThreads / 32) * kExpTermsPerPass; i += kExpThreads) (&red[0][0])[i] = 0.0;
-    for (int i = tid; i < kExpTermsPerPass * kEfAccCols; i += kExpThreads) acc[i] = 0.f;
+    for (int i = tid; i < kExpTermsPerPass * kExpThreads; i += kExpThreads) acc[i] = 0.f;
     if (tid == 0) s_hasz = 0;
     __syncthreads();
     if (tid < nt) {
         const ExpTerm T = ep.t[tid];
         EfTerm x;
-        x.sg = make_float4((T.zm_tile & 1) ? -1.f : 1.f, ((T.zm_tile >> 10) & 1) ? -1.f : 1.f,
-                           ((T.zm_tile >> 11) & 1) ? -1.f : 1.f, ((T.zm_tile >> 12) & 1) ? -1.f : 1.f);
-        x.xt = (int)((T.xm_tile >> 1) & 511u);
-        x.var = T.xm_tile == 0 ? 0
-                               : 1 + 4 * (int)((T.xm_tile >> 10) & 7u) +
-                                     2 * (int)(T.xm_tile & 1u) + (T.ny & 1);
+        const float z10 = ((T.zm_tile >> 10) & 1) ? -1.f : 1.f, z11 = ((T.zm_tile >> 11) & 1) ? -1.f : 1.f,
+                    z12 = ((T.zm_tile >> 12) & 1) ? -1.f : 1.f;
+        x.s1 = make_float2(z10, z10);
+        x.s2 = make_float2(z11, z11);
+        x.s3 = make_float2(z12, z12);
+        x.sx = (T.zm_tile & 1) ? -1.f : 1.f;
+        const uint32_t xr = (T.xm_tile >> 10) & 7u;
+        const int var = T.xm_tile == 0 ? 0 : 1 + 4 * (int)xr + 2 * (int)(T.xm_tile & 1u) + (T.ny & 1);
         // warp form: X on tile bits 6..9 (thread bits 5..8 = warp bits 0..3), none on 10..12
         const uint32_t xw = (T.xm_tile >> 6) & 15u;
-        x.wskip = (((T.xm_tile >> 10) & 7u) == 0 && xw) ? __ffs(xw) - 1 : -1;
-        x.pad1 = 0;
+        const int wskip = (xr == 0 && xw) ? __ffs(xw) - 1 : -1;
+        x.code = (int)((T.xm_tile >> 1) & 511u) | (var << 9) | ((wskip + 1) << 15);
         sx[tid] = x;
+        // Re(i^ny w) = -Re w (ny = 2), -Im w (ny = 1), Im w (ny = 3); the half forms and the
+        // warp-half form count each pair (x, x ^ m) once, doubled
+        const float sg = ((T.ny & 3) == 1 || (T.ny & 3) == 2) ? -1.f : 1.f;
+        sf[tid] = (xr != 0 || wskip >= 0) ? 2.f * sg : sg;
         szg[tid] = T.zm_glob;
         if (T.xm_tile == 0) s_hasz = 1;
     }
-    // per thread and term: Z parity over tile bits 1..9, xor Re(i^ny s) = -s for ny = 1, 2
+    // per thread and term: Z parity over tile bits 1..9
     uint32_t fm0 = 0;
-    for (int j = 0; j < nt; ++j) {
-        const ExpTerm& T = ep.t[j];
-        const uint32_t f = (uint32_t)(__popc(((unsigned)tid << 1) & T.zm_tile & 0x3feu) & 1) ^
-                           (((T.ny & 3) == 1 || (T.ny & 3) == 2) ? 1u : 0u);
-        fm0 |= f << j;
-    }
+    for (int j = 0; j < nt; ++j)
+        fm0 |= (uint32_t)(__popc(((unsigned)tid << 1) & ep.t[j].zm_tile & 0x3feu) & 1) << j;
+    // this lane's part of every tile base (ef_tile_base); the loop form past 32 global bits
+    const bool wbase = p.nrest <= 32;
+    const int rb = lane < p.nrest ? p.rest[lane] : -1;
+    const uint32_t bit_lo = (rb >= 0 && rb < 32) ? 1u << rb : 0u, bit_hi = rb >= 32 ? 1u << (rb - 32) : 0u;
+    auto tbase = [&](long long t) {
+        const long long tt = t & (tc.tiles_per_item - 1);
+        return wbase ? ef_tile_base((uint32_t)tt, bit_lo, bit_hi, lane) : tile_global_base(p, tt);
+    };
     const bool simt = tma.rank == 0;   // no tile map: cp.async pieces by every thread
     if (tid == 0) {
         for (int i = 0; i < kEfNbuf; ++i) {
@@ -214,7 +213,7 @@ __global__ void __launch_bounds__(kExpThreads, 1)
     const long long my_off = ef_tile_offset(p, 2 * tid);
     const float2* item_state = state + item_off[item];
     auto simt_load = [&](long long t, int bb) {
-        const long long gb = tile_global_base(p, t & (tc.tiles_per_item - 1));
+        const long long gb = tbase(t);
         float2* dst = bufs + (size_t)bb * tile_elems + 2 * tid;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -235,13 +234,10 @@ __global__ void __launch_bounds__(kExpThreads, 1)
         }
     }
     const unsigned long long lane_zg = lane < nt ? szg[lane] : 0ull;
-    auto flush = [&]() {   // even lanes' FP32 sums -> warp sum (fixed order) -> FP64
+    auto flush = [&]() {   // per-thread FP32 sums -> warp sum (fixed order) -> FP64
         for (int j = 0; j < nt; ++j) {
-            float v = 0.f;
-            if (!(lane & 1)) {
-                v = acc[j * kEfAccCols + (tid >> 1)];
-                acc[j * kEfAccCols + (tid >> 1)] = 0.f;
-            }
+            float v = acc[j * kExpThreads + tid];
+            acc[j * kExpThreads + tid] = 0.f;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) red[warp][j] += (double)v;
@@ -252,7 +248,7 @@ __global__ void __launch_bounds__(kExpThreads, 1)
         const int b = it % kEfNbuf;
         const float2* buf = bufs + (size_t)b * tile_elems;
         if (!mbar_wait_bounded(&bars[b], (uint32_t)((it / kEfNbuf) & 1), err)) s_abort = 1;
-        const long long gbase = tile_global_base(p, t & (tc.tiles_per_item - 1));
+        const long long gbase = tbase(t);
         // the tile's part of every term's Z parity: one term per lane, one ballot
         const uint32_t fm =
             fm0 ^ __ballot_sync(0xffffffffu, (__popcll((unsigned long long)gbase & lane_zg) & 1) != 0);
@@ -264,25 +260,38 @@ __global__ void __launch_bounds__(kExpThreads, 1)
             a[2 * i] = make_float2(q.x, q.y);
             a[2 * i + 1] = make_float2(q.z, q.w);
         }
-        float pz[kExpSlots];   // |a_r|^2 for the Z-only terms
+        float2 pz[kExpSlots / 2];   // |a_r|^2 for the Z-only terms, by register pair
         if (hasz) {
 #pragma unroll
-            for (int r = 0; r < kExpSlots; ++r) pz[r] = fmaf(a[r].x, a[r].x, a[r].y * a[r].y);
+            for (int i = 0; i < kExpSlots / 2; ++i)
+                pz[i] = make_float2(fmaf(a[2 * i].x, a[2 * i].x, a[2 * i].y * a[2 * i].y),
+                                    fmaf(a[2 * i + 1].x, a[2 * i + 1].x, a[2 * i + 1].y * a[2 * i + 1].y));
         }
-        for (int j = 0; j < nt; ++j) {
-            const EfTerm T = sx[j];
+        float* accp = acc + tid;
+        // the next term's descriptor and scale are read one term ahead, and the
+        // running sum before the term's form is dispatched, so that their latency
+        // overlaps the current term's work
+        EfTerm Tn = sx[0];
+        float sfn = sf[0];
+        for (int j = 0; j < nt; ++j, accp += kExpThreads) {
+            const EfTerm T = Tn;
+            const float sfj = sfn;
+            Tn = sx[(j + 1) & (kExpTermsPerPass - 1)];
+            sfn = sf[(j + 1) & (kExpTermsPerPass - 1)];
+            const int var = (T.code >> 9) & 63, wskip = (T.code >> 15) - 1;
+            // one half of the warps carries a warp-form term (doubled); the halves take
+            // turns tile by tile, so no warp runs ahead of the others
+            if (wskip >= 0 && (((warp >> wskip) ^ it) & 1)) continue;
+            const float accv = *accp;
+            const float f = __uint_as_float(__float_as_uint(sfj) ^ (((fm >> j) & 1u) << 31));
             float v = 0.f;
-            if (T.var == 0) {
-                v = ef_butterfly(pz, T.sg);
-            } else if (T.wskip >= 0 && (((warp >> T.wskip) ^ it) & 1)) {
-                // one half of the warps carries the term (doubled); the halves take
-                // turns tile by tile, so no warp runs ahead of the others
-                v = 0.f;
+            if (var == 0) {
+                v = ef_butterfly(pz, T);
             } else {
-                const float4* pb = buf4 + (tid ^ T.xt);
-                switch (T.var) {
+                const float4* pb = buf4 + (tid ^ (T.code & 511));
+                switch (var) {
 #define TCNG_EF1(XR, SW, IM) \
-    case 1 + 4 * (XR) + 2 * (SW) + (IM): v = ef_xterm<XR, SW, IM>(a, pb, T.sg); break;
+    case 1 + 4 * (XR) + 2 * (SW) + (IM): v = ef_xterm<XR, SW, IM>(a, pb, T); break;
 #define TCNG_EF4(XR) TCNG_EF1(XR, 0, 0) TCNG_EF1(XR, 0, 1) TCNG_EF1(XR, 1, 0) TCNG_EF1(XR, 1, 1)
                     TCNG_EF4(0) TCNG_EF4(1) TCNG_EF4(2) TCNG_EF4(3)
                     TCNG_EF4(4) TCNG_EF4(5) TCNG_EF4(6) TCNG_EF4(7)
@@ -290,11 +299,8 @@ __global__ void __launch_bounds__(kExpThreads, 1)
 #undef TCNG_EF1
                 default: break;
                 }
-                if (T.wskip >= 0) v *= 2.f;
             }
-            v = __uint_as_float(__float_as_uint(v) ^ (((fm >> j) & 1u) << 31));
-            v += __shfl_xor_sync(0xffffffffu, v, 1);
-            if (!(lane & 1)) acc[j * kEfAccCols + (tid >> 1)] += v;
+            *accp = fmaf(f, v, accv);
         }
         if ((it & 63) == 63 || t + stride >= t1) flush();
         __syncwarp();
@@ -336,7 +342,7 @@ __global__ void __launch_bounds__(kExpThreads, 1)
 
 size_t expect_fast_smem_bytes() {
     return 128 + (size_t)kEfNbuf * (sizeof(float2) << kEfTileBits) + 16 * kEfNbuf +
-           sizeof(float) * kExpTermsPerPass * kEfAccCols;
+           sizeof(float) * kExpTermsPerPass * kExpThreads;
 }
 
 cudaError_t launch_expect_fast(const float2* state, const long long* item_off, int items, const DevPass& p,
