@@ -31,6 +31,8 @@
 // the end of tile i, once every warp has left tile i - 1.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "device.cuh"
 #include "launch.hpp"
 #include "tile_io.cuh"
@@ -63,6 +65,16 @@ struct EfTerm {          // a term of the pass, prepared once per CTA (32 bytes)
     int32_t code;        // bits 0..8: xt (partner thread t ^ xt); 9..14: form (0: Z only, else
                          // 1 + 4 XR + 2 swap + im); 15..17: wskip + 1 (warps with bit wskip of the
                          // warp index xor tile parity set skip the term; 0: none)
+};
+struct EfPass {          // the pass's term constants: a kernel parameter, read from the
+                         // constant bank at the (warp-uniform) term index
+    EfTerm e[kExpTermsPerPass];
+    float sf[kExpTermsPerPass];   // Re(i^ny w) sign x (2: half forms and the warp-half form)
+    // terms sorted by (form, wskip): run r holds terms run_end[r - 1] .. run_end[r] - 1,
+    // all with form and wskip + 1 packed in run_code[r] (form | (wskip + 1) << 6)
+    int nrun;
+    int run_code[kExpTermsPerPass];
+    int run_end[kExpTermsPerPass];
 };
 
 // Global index of a tile's offset 0 (tile_global_base) by one warp OR-reduction:
@@ -134,11 +146,44 @@ __device__ __forceinline__ float ef_xterm(const float2 (&a)[kExpSlots], const fl
     }
 }
 
+// The terms j .. end - 1 of one run (one form): two terms per step in one basic
+// block, so that the second term's partner reads overlap the first one's products.
+template <int XR, bool SWAP, bool IM>
+__device__ __forceinline__ void ef_run(const float2 (&a)[kExpSlots], const float4* __restrict__ buf4, int tid,
+                                       const EfPass& ef, int j, int end, uint32_t fm, float* __restrict__ acc) {
+    auto scale = [&](int k) { return __uint_as_float(__float_as_uint(ef.sf[k]) ^ (((fm >> k) & 1u) << 31)); };
+    for (; j + 1 < end; j += 2) {
+        float* ap0 = acc + j * kExpThreads + tid;
+        float* ap1 = ap0 + kExpThreads;
+        const float acc0 = *ap0, acc1 = *ap1;
+        const float v0 = ef_xterm<XR, SWAP, IM>(a, buf4 + (tid ^ (ef.e[j].code & 511)), ef.e[j]);
+        const float v1 = ef_xterm<XR, SWAP, IM>(a, buf4 + (tid ^ (ef.e[j + 1].code & 511)), ef.e[j + 1]);
+        *ap0 = fmaf(scale(j), v0, acc0);
+        *ap1 = fmaf(scale(j + 1), v1, acc1);
+    }
+    if (j < end) {
+        float* ap = acc + j * kExpThreads + tid;
+        const float accv = *ap;
+        const float v = ef_xterm<XR, SWAP, IM>(a, buf4 + (tid ^ (ef.e[j].code & 511)), ef.e[j]);
+        *ap = fmaf(scale(j), v, accv);
+    }
+}
+// ... of the Z-only terms.
+__device__ __forceinline__ void ef_run_z(const float2 (&pz)[kExpSlots / 2], int tid, const EfPass& ef, int j,
+                                         int end, uint32_t fm, float* __restrict__ acc) {
+    for (; j < end; ++j) {
+        float* ap = acc + j * kExpThreads + tid;
+        const float accv = *ap;
+        const float v = ef_butterfly(pz, ef.e[j]);
+        *ap = fmaf(__uint_as_float(__float_as_uint(ef.sf[j]) ^ (((fm >> j) & 1u) << 31)), v, accv);
+    }
+}
+
 __global__ void __launch_bounds__(kExpThreads, 1)
     expect_fast_kernel(const float2* __restrict__ state, const long long* __restrict__ item_off,
                        const __grid_constant__ DevPass p, const __grid_constant__ ExpPass ep, TileCtx tc,
                        double* __restrict__ partial, int n_out, unsigned* __restrict__ err,
-                       const __grid_constant__ TmaTile tma) {
+                       const __grid_constant__ TmaTile tma, const __grid_constant__ EfPass ef) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int tile_elems = 1 << kEfTileBits;
     float2* bufs = reinterpret_cast<float2*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
@@ -146,8 +191,6 @@ __global__ void __launch_bounds__(kExpThreads, 1)
     uint64_t* ebars = bars + kEfNbuf;                             // buffer released by every warp
     float* acc = reinterpret_cast<float*>(ebars + kEfNbuf);      // [term][thread]
     __shared__ double red[kExpThreads / 32][kExpTermsPerPass];
-    __shared__ EfTerm sx[kExpTermsPerPass];
-    __shared__ float sf[kExpTermsPerPass];                       // Re(i^ny w) sign x (2: half forms)
     __shared__ unsigned long long szg[kExpTermsPerPass];         // Z mask on global bits
     __shared__ int s_abort, s_hasz;
     __shared__ long long s_koff[3];   // cp.async form: offsets of tile elements 1024, 2048, 4096
@@ -160,24 +203,6 @@ __global__ void __launch_bounds__(kExpThreads, 1)
     __syncthreads();
     if (tid < nt) {
         const ExpTerm T = ep.t[tid];
-        EfTerm x;
-        const float z10 = ((T.zm_tile >> 10) & 1) ? -1.f : 1.f, z11 = ((T.zm_tile >> 11) & 1) ? -1.f : 1.f,
-                    z12 = ((T.zm_tile >> 12) & 1) ? -1.f : 1.f;
-        x.s1 = make_float2(z10, z10);
-        x.s2 = make_float2(z11, z11);
-        x.s3 = make_float2(z12, z12);
-        x.sx = (T.zm_tile & 1) ? -1.f : 1.f;
-        const uint32_t xr = (T.xm_tile >> 10) & 7u;
-        const int var = T.xm_tile == 0 ? 0 : 1 + 4 * (int)xr + 2 * (int)(T.xm_tile & 1u) + (T.ny & 1);
-        // warp form: X on tile bits 6..9 (thread bits 5..8 = warp bits 0..3), none on 10..12
-        const uint32_t xw = (T.xm_tile >> 6) & 15u;
-        const int wskip = (xr == 0 && xw) ? __ffs(xw) - 1 : -1;
-        x.code = (int)((T.xm_tile >> 1) & 511u) | (var << 9) | ((wskip + 1) << 15);
-        sx[tid] = x;
-        // Re(i^ny w) = -Re w (ny = 2), -Im w (ny = 1), Im w (ny = 3); the half forms and the
-        // warp-half form count each pair (x, x ^ m) once, doubled
-        const float sg = ((T.ny & 3) == 1 || (T.ny & 3) == 2) ? -1.f : 1.f;
-        sf[tid] = (xr != 0 || wskip >= 0) ? 2.f * sg : sg;
         szg[tid] = T.zm_glob;
         if (T.xm_tile == 0) s_hasz = 1;
     }
@@ -267,40 +292,23 @@ __global__ void __launch_bounds__(kExpThreads, 1)
                 pz[i] = make_float2(fmaf(a[2 * i].x, a[2 * i].x, a[2 * i].y * a[2 * i].y),
                                     fmaf(a[2 * i + 1].x, a[2 * i + 1].x, a[2 * i + 1].y * a[2 * i + 1].y));
         }
-        float* accp = acc + tid;
-        // the next term's descriptor and scale are read one term ahead, and the
-        // running sum before the term's form is dispatched, so that their latency
-        // overlaps the current term's work
-        EfTerm Tn = sx[0];
-        float sfn = sf[0];
-        for (int j = 0; j < nt; ++j, accp += kExpThreads) {
-            const EfTerm T = Tn;
-            const float sfj = sfn;
-            Tn = sx[(j + 1) & (kExpTermsPerPass - 1)];
-            sfn = sf[(j + 1) & (kExpTermsPerPass - 1)];
-            const int var = (T.code >> 9) & 63, wskip = (T.code >> 15) - 1;
+        for (int r = 0, j = 0; r < ef.nrun; j = ef.run_end[r], ++r) {
+            const int code = ef.run_code[r], end = ef.run_end[r];
+            const int wskip = (code >> 6) - 1;
             // one half of the warps carries a warp-form term (doubled); the halves take
             // turns tile by tile, so no warp runs ahead of the others
             if (wskip >= 0 && (((warp >> wskip) ^ it) & 1)) continue;
-            const float accv = *accp;
-            const float f = __uint_as_float(__float_as_uint(sfj) ^ (((fm >> j) & 1u) << 31));
-            float v = 0.f;
-            if (var == 0) {
-                v = ef_butterfly(pz, T);
-            } else {
-                const float4* pb = buf4 + (tid ^ (T.code & 511));
-                switch (var) {
+            switch (code & 63) {
+            case 0: ef_run_z(pz, tid, ef, j, end, fm, acc); break;
 #define TCNG_EF1(XR, SW, IM) \
-    case 1 + 4 * (XR) + 2 * (SW) + (IM): v = ef_xterm<XR, SW, IM>(a, pb, T); break;
+    case 1 + 4 * (XR) + 2 * (SW) + (IM): ef_run<XR, SW, IM>(a, buf4, tid, ef, j, end, fm, acc); break;
 #define TCNG_EF4(XR) TCNG_EF1(XR, 0, 0) TCNG_EF1(XR, 0, 1) TCNG_EF1(XR, 1, 0) TCNG_EF1(XR, 1, 1)
-                    TCNG_EF4(0) TCNG_EF4(1) TCNG_EF4(2) TCNG_EF4(3)
-                    TCNG_EF4(4) TCNG_EF4(5) TCNG_EF4(6) TCNG_EF4(7)
+                TCNG_EF4(0) TCNG_EF4(1) TCNG_EF4(2) TCNG_EF4(3)
+                TCNG_EF4(4) TCNG_EF4(5) TCNG_EF4(6) TCNG_EF4(7)
 #undef TCNG_EF4
 #undef TCNG_EF1
-                default: break;
-                }
+            default: break;
             }
-            *accp = fmaf(f, v, accv);
         }
         if ((it & 63) == 63 || t + stride >= t1) flush();
         __syncwarp();
@@ -349,6 +357,41 @@ cudaError_t launch_expect_fast(const float2* state, const long long* item_off, i
                                const ExpPass& ep, const TileCtx& tc, double* partial, int n_out, int nblk,
                                unsigned* err, cudaStream_t s, const TmaTile& tma) {
     if (p.m != kEfTileBits || tc.nbuf != kEfNbuf) return cudaErrorInvalidValue;
+    // terms sorted by (form, wskip) into runs (stable: equal keys keep their order)
+    auto key = [](const ExpTerm& T) {
+        const uint32_t xr = (T.xm_tile >> 10) & 7u, xw = (T.xm_tile >> 6) & 15u;
+        const int var = T.xm_tile == 0 ? 0 : 1 + 4 * (int)xr + 2 * (int)(T.xm_tile & 1u) + (T.ny & 1);
+        const int wskip = (xr == 0 && xw) ? __builtin_ctz(xw) : -1;
+        return var | ((wskip + 1) << 6);
+    };
+    ExpPass eps = ep;
+    const int nt = ep.nterms < kExpTermsPerPass ? ep.nterms : kExpTermsPerPass;
+    std::stable_sort(eps.t, eps.t + nt, [&](const ExpTerm& x, const ExpTerm& y) { return key(x) < key(y); });
+    EfPass ef{};
+    for (int j = 0; j < nt; ++j) {
+        const int k = key(eps.t[j]);
+        if (ef.nrun == 0 || ef.run_code[ef.nrun - 1] != k) ef.run_code[ef.nrun++] = k;
+        ef.run_end[ef.nrun - 1] = j + 1;
+    }
+    for (int j = 0; j < nt; ++j) {
+        const ExpTerm& T = eps.t[j];
+        EfTerm& x = ef.e[j];
+        auto sgn = [&](int b) { return ((T.zm_tile >> b) & 1u) ? -1.f : 1.f; };
+        x.s1 = make_float2(sgn(10), sgn(10));
+        x.s2 = make_float2(sgn(11), sgn(11));
+        x.s3 = make_float2(sgn(12), sgn(12));
+        x.sx = sgn(0);
+        const uint32_t xr = (T.xm_tile >> 10) & 7u;
+        const int var = T.xm_tile == 0 ? 0 : 1 + 4 * (int)xr + 2 * (int)(T.xm_tile & 1u) + (T.ny & 1);
+        // warp form: X on tile bits 6..9 (thread bits 5..8 = warp bits 0..3), none on 10..12
+        const uint32_t xw = (T.xm_tile >> 6) & 15u;
+        const int wskip = (xr == 0 && xw) ? __builtin_ctz(xw) : -1;
+        x.code = (int)((T.xm_tile >> 1) & 511u) | (var << 9) | ((wskip + 1) << 15);
+        // Re(i^ny w) = -Re w (ny = 2), -Im w (ny = 1), Im w (ny = 3); the half forms and the
+        // warp-half form count each pair (x, x ^ m) once, doubled
+        const float sg = ((T.ny & 3) == 1 || (T.ny & 3) == 2) ? -1.f : 1.f;
+        ef.sf[j] = (xr != 0 || wskip >= 0) ? 2.f * sg : sg;
+    }
     static bool attr[kMaxDeviceSlots] = {};   // the attribute is per device
     const int d = device_slot();
     if (!attr[d]) {
@@ -358,8 +401,8 @@ cudaError_t launch_expect_fast(const float2* state, const long long* item_off, i
         attr[d] = true;
     }
     dim3 grid((unsigned)nblk, (unsigned)items);
-    expect_fast_kernel<<<grid, kExpThreads, expect_fast_smem_bytes(), s>>>(state, item_off, p, ep, tc, partial,
-                                                                           n_out, err, tma);
+    expect_fast_kernel<<<grid, kExpThreads, expect_fast_smem_bytes(), s>>>(state, item_off, p, eps, tc, partial,
+                                                                           n_out, err, tma, ef);
     count_launch();
     return cudaGetLastError();
 }
