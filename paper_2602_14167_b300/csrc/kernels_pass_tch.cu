@@ -61,7 +61,7 @@ struct StageH {             // per-stage constants, shared memory (64 bytes)
     int hm[6];              // ~((1 << b) - 1) for the bits the row index skips (ascending)
     int nj;                 // register bits on tile bits 0..3
     int sr4;                // 32-amplitude stages: 1 << register tile bit 4
-    int pad[4];
+    int srz[4];             // sr on the 128-byte-swizzled tile (o ^ ((o >> 3) & 0xE))
 };
 
 struct PassTchArgs {
@@ -121,12 +121,8 @@ template <int FORM>
 __device__ __forceinline__ void stage_slots(const StageH& S, int g, int tau, int (&L)[16]) {
     int sr[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) sr[i] = S.sr[i];
-    if (FORM == FORM_SWZ) {   // slot offset o lies at o ^ ((o >> 3) & 0xE) (linear in o)
-        g ^= (g >> 3) & 0xe;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) sr[i] ^= (sr[i] >> 3) & 0xe;
-    }
+    for (int i = 0; i < 4; ++i) sr[i] = FORM == FORM_SWZ ? S.srz[i] : S.sr[i];
+    if (FORM == FORM_SWZ) g ^= (g >> 3) & 0xe;   // slot offset o lies at o ^ ((o >> 3) & 0xE) (linear in o)
     int stau = 0;
     if (FORM == FORM_ROT && S.nj) {
 #pragma unroll
@@ -184,7 +180,7 @@ __device__ __forceinline__ void load_stage(const TcsStage* tcs, int nst, int gb0
             }
         for (int k = 0; k < 6; ++k) d.hm[k] = k < ns ? ~((1 << skip[k]) - 1) : 0;
         d.nj = S.nj;
-        for (int k = 0; k < 4; ++k) d.pad[k] = 0;
+        for (int k = 0; k < 4; ++k) d.srz[k] = d.sr[k] ^ ((d.sr[k] >> 3) & 0xe);
         sst[i] = d;
     }
 }
@@ -523,6 +519,10 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
         auto stage = [&](const int s, const bool first) {
             const StageH& S = sst[s];
             const bool pairs = S.sr[0] == 1;
+            // this thread's two rows (tile index with zeros at the register bits), for the
+            // loads and again for the stores
+            const int g0 = lock_row(S, (2 * half) * 128 + quarter * 32 + lane);
+            const int g1 = lock_row(S, (2 * half + 1) * 128 + quarter * 32 + lane);
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
                 const int k = first ? 1 - kk : kk;
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
                 const int row = rb * 128 + quarter * 32 + lane;
                 const int tau = (FORM == FORM_ROT && S.nj) ? (row & 15) >> (4 - S.nj) : 0;
                 int L[16];
-                stage_slots<FORM>(S, lock_row(S, row), tau, L);
+                stage_slots<FORM>(S, k ? g1 : g0, tau, L);
                 float2 x[16];
                 if (first && kk == 0) {
 #pragma unroll
@@ -603,13 +603,17 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
                 {
                     float y[32];
                     tc_ld32(lane_base + gcol + (uint32_t)rb * 64u + 32u, y);
+                    if (last) {   // unscale and restore the norm (earlier stages keep the scale)
 #pragma unroll
-                    for (int v = 0; v < 16; ++v) x[v] = make_float2(y[2 * v] * f, y[2 * v + 1] * f);
+                        for (int v = 0; v < 32; ++v) y[v] *= f;
+                    }
+#pragma unroll
+                    for (int v = 0; v < 16; ++v) x[v] = make_float2(y[2 * v], y[2 * v + 1]);
                 }
                 const int tau = (FORM == FORM_ROT && S.nj) ? (row & 15) >> (4 - S.nj) : 0;
                 if (FORM == FORM_ROT && S.nj) unrotate_h(x, tau, S.nj);
                 int L[16];
-                stage_slots<FORM>(S, lock_row(S, row), tau, L);
+                stage_slots<FORM>(S, k ? g1 : g0, tau, L);
                 store_row<FORM>(buf, L, pairs, x);
             }
             if (last) fence_proxy_async_smem();   // before the tile store reads them
@@ -965,7 +969,8 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
             if (!mbar_wait_bounded(&mma_bar[chain], q & 1u, a.err)) s_abort = 1;
             tc_fence_after();
             float f = 1.f;
-            if (s == nst - 1) {   // unscale, restore the block norm (its rows are closed under the pass)
+            const bool last = s == nst - 1;
+            if (last) {   // unscale, restore the block norm (its rows are closed under the pass)
                 float nout = 0.f;
 #pragma unroll
                 for (int ch = 0; ch < 2; ++ch) {
@@ -998,8 +1003,12 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
                 {
                     float y[32];
                     tc_ld32(lane_base + col + 64u + 32u * ch, y);
+                    if (last) {   // unscale and restore the norm (the first stage keeps the scale)
 #pragma unroll
-                    for (int v = 0; v < 16; ++v) x[v] = make_float2(y[2 * v] * f, y[2 * v + 1] * f);
+                        for (int v = 0; v < 32; ++v) y[v] *= f;
+                    }
+#pragma unroll
+                    for (int v = 0; v < 16; ++v) x[v] = make_float2(y[2 * v], y[2 * v + 1]);
                 }
                 int L[16];
                 stage_slots<FORM_PLAIN>(S, ch ? (g | S.sr4) : g, 0, L);
