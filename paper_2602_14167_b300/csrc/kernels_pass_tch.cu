@@ -88,13 +88,17 @@ __device__ __forceinline__ void tile_scale(float m, float& c, float& ic) {
     ic = __uint_as_float((uint32_t)(254 - f) << 23);
 }
 
-// x = hi + lo, both FP16 (re in the low half of each 32-bit word).
+// x = hi + lo, both FP16 (re in the low half of each 32-bit word).  The residual
+// x - hi is exact in FP32; it is formed by a mixed-precision FMA, hi * (-1) + x,
+// straight from the packed halves.
 __device__ __forceinline__ void split_f16(float2 x, uint32_t& hi, uint32_t& lo) {
-    const __half2 h = __floats2half2_rn(x.x, x.y);
-    const float2 hf = __half22float2(h);
-    const __half2 l = __floats2half2_rn(x.x - hf.x, x.y - hf.y);
-    memcpy(&hi, &h, 4);
-    memcpy(&lo, &l, 4);
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x.y), "f"(x.x));
+    float r0, r1;
+    asm("{\n\t.reg .f16 h0, h1, m;\n\tmov.b32 {h0, h1}, %2;\n\tmov.b16 m, 0xBC00;\n\t"
+        "fma.rn.f32.f16 %0, h0, m, %3;\n\tfma.rn.f32.f16 %1, h1, m, %4;\n\t}"
+        : "=f"(r0), "=f"(r1)
+        : "r"(hi), "f"(x.x), "f"(x.y));
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(r1), "f"(r0));
 }
 
 // a[s] holds register value s ^ tau (tau only on slots 0..nj-1): permute so
