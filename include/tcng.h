@@ -470,6 +470,20 @@ const char* tcng_describe_plan(int n, const tcng_gate* ops, size_t n_ops, const 
                                size_t n_mat, int P, int adjoint);
 
 /*
+ * Shared-memory layouts of one lock-step FP16 tile pass (host only, no device
+ * call).  rbit: nst x 4 register tile bits of the pass's stages, each stage's four
+ * ascending and in 0..12.  out (nst x 8 bytes, caller-owned): per stage the
+ * positions of its four register bits in the layout it reads, then in the layout
+ * it writes.  Every stage rewrites the whole tile, so it may move its register
+ * bits (the other bits keep their order); stage 0 reads and the last stage writes
+ * the tile map's layout.  The positions are chosen so that a warp's accesses reach
+ * every shared-memory bank slot of the 128-byte swizzle; *relocated = 0 when the
+ * tile map's layout is kept throughout (nothing to gain, or no way back to it).
+ * TCNG_EINVAL on null pointers, nst outside 1..64 or bad register bits.
+ */
+tcng_status tcng_plan_lock_layouts(const unsigned char* rbit, int nst, unsigned char* out, int* relocated);
+
+/*
  * Kernel timing with CUDA events recorded on the launch stream around every
  * kernel this library launches (off by default; a few microseconds per launch
  * when on).  tcng_profile_read synchronises the device and writes

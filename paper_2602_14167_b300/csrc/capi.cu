@@ -113,6 +113,7 @@ DevPlan::~DevPlan() {
     cudaFree(d_gparam);
     cudaFree(d_gscale);
     cudaFree(d_tcs);
+    cudaFree(d_lay);
 }
 
 TermSet::~TermSet() {

@@ -73,6 +73,10 @@ struct DevPlan {
     int n_tc32 = 0;                   // ... with TF32 W operands (4-bit stages; 8 KiB each per item)
     long long wh_bytes = 0;           // FP16 W operand bytes per item
     TcsStage* d_tcs = nullptr;
+    // FP16 lock-step passes on the swizzled tile: per stage, the shared-memory bit
+    // positions of its four register bits when read and when written (rpos[4], wpos[4])
+    std::vector<uint8_t> lay;
+    uint8_t* d_lay = nullptr;
     ~DevPlan();
 };
 
@@ -160,6 +164,7 @@ tcng_status run_state_adjoint(tcng_state* st, int item, const tcng_gate* ops, si
 
 // Tensor-core register stages (kernels_pass_tc.cu).
 void plan_tensor_stages(DevPlan* dp);
+void plan_lock_layouts(DevPlan* dp);   // fills lay / d_lay (kernels_pass_tch.cu)
 cudaError_t launch_build_stage_w(const DevPlan* dp, const double2* table, long long table_stride,
                                  int items, void* wops, bool half, cudaStream_t s);
 // FP16-split tensor-core passes (unitary plans, one W set for every tile):

@@ -700,6 +700,7 @@ void plan_tensor_stages(DevPlan* dp) {
         }
     }
     if (dp->n_tc) dp->d_tcs = dev_copy(dp->tcs);
+    if (dp->n_tc) plan_lock_layouts(dp);
     dp->tc_ready = true;
 }
 

@@ -31,6 +31,7 @@
 // A seventeenth warp moves tiles (TMA or per-chunk bulk copies, tile_io.cuh).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <cstdlib>
 
 #include <algorithm>
 #include <cstring>
@@ -62,12 +63,15 @@ struct StageH {             // per-stage constants, shared memory (64 bytes)
     int nj;                 // register bits on tile bits 0..3
     int sr4;                // 32-amplitude stages: 1 << register tile bit 4
     int srz[4];             // sr on the 128-byte-swizzled tile (o ^ ((o >> 3) & 0xE))
+    int hmw[4], srzw[4];    // lock-step stages on the swizzled tile: hm and srz of the layout
+                            // the stage writes (its register bits moved, the planner's choice)
 };
 
 struct PassTchArgs {
     int gb0, gb1;               // independent-slice passes: tile bits fixed per slice
     int renorm;                 // restore each tile's (slice's) norm after the last stage
     const TcsStage* tcs;        // this pass's stages
+    const uint8_t* lay;         // per stage: read / write positions of the register bits (or null)
     const unsigned char* wops;  // FP16 W operands of the plan's tensor-core stages
     long long total_tiles;
     unsigned* err;
@@ -146,6 +150,19 @@ __device__ __forceinline__ int lock_row(const StageH& S, int tid) {
     for (int i = 0; i < 4; ++i) g += g & S.hm[i];
     return g;
 }
+// The same row in the layout the stage writes, and its slots there (swizzled tile).
+__device__ __forceinline__ int lock_row_w(const StageH& S, int tid) {
+    int g = tid;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) g += g & S.hmw[i];
+    return g;
+}
+__device__ __forceinline__ void stage_slots_wswz(const StageH& S, int g, int (&L)[16]) {
+    L[0] = g ^ ((g >> 3) & 0xe);
+#pragma unroll
+    for (int v = 1; v < 16; ++v)
+        L[v] = L[v & (v - 1)] ^ ((v & 1) ? S.srzw[0] : (v & 2) ? S.srzw[1] : (v & 4) ? S.srzw[2] : S.srzw[3]);
+}
 // ... in an independent-slice stage: the slice's 128 rows, the slice index on
 // the pass's two fixed tile bits.
 __device__ __forceinline__ int group_row(const StageH& S, int tid, int gb0, int gb1) {
@@ -158,14 +175,30 @@ __device__ __forceinline__ int group_row(const StageH& S, int tid, int gb0, int 
 // Stage constants: the row index skips the register bits and, in passes with
 // fixed tile bits per slice (or row block), those bits (gb0 only when gb1 < 0).
 __device__ __forceinline__ void load_stage(const TcsStage* tcs, int nst, int gb0, int gb1, bool grouped,
-                                           StageH* sst, int tid, int nthreads) {
+                                           StageH* sst, int tid, int nthreads, const uint8_t* lay = nullptr) {
     for (int i = tid; i < nst; i += nthreads) {
         const TcsStage S = tcs[i];
         StageH d;
         int skip[7], ns = 0;
         for (int r = 0; r < 4; ++r) {
-            d.sr[r] = 1 << S.rbit[r];
-            skip[ns++] = S.rbit[r];
+            const int pos = lay ? lay[8 * i + r] : S.rbit[r];
+            d.sr[r] = 1 << pos;
+            skip[ns++] = pos;
+        }
+        {   // the layout this stage writes (the same one without a layout table)
+            int wp[4];
+            for (int r = 0; r < 4; ++r) {
+                wp[r] = lay ? lay[8 * i + 4 + r] : S.rbit[r];
+                const int o = 1 << wp[r];
+                d.srzw[r] = o ^ ((o >> 3) & 0xe);
+            }
+            for (int x = 1; x < 4; ++x)
+                for (int y = x; y > 0 && wp[y - 1] > wp[y]; --y) {
+                    const int t = wp[y];
+                    wp[y] = wp[y - 1];
+                    wp[y - 1] = t;
+                }
+            for (int r = 0; r < 4; ++r) d.hmw[r] = ~((1 << wp[r]) - 1);
         }
         d.sr4 = 0;
         if (S.nreg == 5) {
@@ -442,7 +475,7 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    load_stage(a.tcs, nst, 0, 0, false, sst, tid, TH_CTA_THREADS);
+    load_stage(a.tcs, nst, 0, 0, false, sst, tid, TH_CTA_THREADS, FORM == FORM_SWZ ? a.lay : nullptr);
     if (tid == 0) {
         for (int i = 0; i < NBUF; ++i) {
             mbar_init(&tile_bar[i], 1);
@@ -527,6 +560,9 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
             // loads and again for the stores
             const int g0 = lock_row(S, (2 * half) * 128 + quarter * 32 + lane);
             const int g1 = lock_row(S, (2 * half + 1) * 128 + quarter * 32 + lane);
+            // the same rows in the layout this stage writes (its register bits may move)
+            const int gw0 = FORM == FORM_SWZ ? lock_row_w(S, (2 * half) * 128 + quarter * 32 + lane) : g0;
+            const int gw1 = FORM == FORM_SWZ ? lock_row_w(S, (2 * half + 1) * 128 + quarter * 32 + lane) : g1;
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
                 const int k = first ? 1 - kk : kk;
@@ -617,7 +653,8 @@ __global__ void __launch_bounds__(TH_CTA_THREADS, 1)
                 const int tau = (FORM == FORM_ROT && S.nj) ? (row & 15) >> (4 - S.nj) : 0;
                 if (FORM == FORM_ROT && S.nj) unrotate_h(x, tau, S.nj);
                 int L[16];
-                stage_slots<FORM>(S, k ? g1 : g0, tau, L);
+                if (FORM == FORM_SWZ) stage_slots_wswz(S, k ? gw1 : gw0, L);
+                else stage_slots<FORM>(S, k ? g1 : g0, tau, L);
                 store_row<FORM>(buf, L, pairs, x);
             }
             if (last) fence_proxy_async_smem();   // before the tile store reads them
@@ -1091,6 +1128,176 @@ int free_slice_bits(const DevPlan* dp, int pass) {
 
 }  // namespace
 
+// ---------------------------------------- shared-memory layouts per stage --
+// A lock-step stage reads rows of the swizzled tile and writes them back; the
+// rows' lanes take the five lowest tile bits outside its register bits R.  A
+// float2's bank slot (16 per 128 bytes) has bit 0 = position bit 0 and bit k =
+// position bit k xor k + 3 (k = 1..3), so when R sits on both k and k + 3 (R =
+// {2,3,4,5}, {1,2,5,6}) no lane bit reaches slot bit k and a warp's accesses take
+// twice the wavefronts.  Every stage rewrites the whole tile, so each stage may
+// write its register bits to new positions (the other bits keep their order and
+// close up): stage s reads layout P_s and writes P_{s+1}, P_0 = P_last = the tile
+// map's layout.  The planner picks each P_{s+1} greedily so that stage s's writes
+// and stage s+1's reads cover every slot bit, for the whole warp and for its first
+// quarter (16-byte pair accesses, tile bit 0 in R) or half (8-byte accesses).
+namespace {
+
+uint32_t lay_slot(int p) { return p == 0 ? 1u : (p <= 3 ? 1u << p : (p <= 6 ? 1u << (p - 3) : 0u)); }
+
+int lay_rank(const uint32_t* c, int n) {
+    uint32_t basis[4];
+    int r = 0;
+    for (int i = 0; i < n; ++i) {
+        uint32_t v = c[i];
+        for (int b = 0; b < r; ++b) v = std::min(v, v ^ basis[b]);
+        if (v && r < 4) basis[r++] = v;
+    }
+    return r;
+}
+
+// 0 when accesses with register positions A (a bit set) cover every slot bit
+int lay_bad(uint32_t A) {
+    const bool pairs = A & 1u;
+    const uint32_t need = pairs ? 0xEu : 0xFu;
+    const int full = pairs ? 3 : 4, nfirst = pairs ? 3 : 4;
+    uint32_t c[5];
+    int nl = 0;
+    for (int p = 0; p < TH_TILE_BITS && nl < 5; ++p)
+        if (!((A >> p) & 1u)) c[nl++] = lay_slot(p) & need;
+    return (lay_rank(c, 5) < full ? 1 : 0) + (lay_rank(c, nfirst) < full ? 1 : 0);
+}
+
+}  // namespace
+
+// Layouts of one pass: rbit holds nst x 4 ascending tile bits; out gets nst x 8
+// bytes (per stage: positions of its register bits when read, when written).
+// Returns false (and writes the tile map's layout throughout) when the planner has
+// nothing to gain or cannot return to the tile map's layout after the last stage.
+bool lock_layouts(const uint8_t* rbit, int nst, uint8_t* out) {
+    for (int s = 0; s < nst; ++s)
+        for (int r = 0; r < 4; ++r) out[8 * s + r] = out[8 * s + 4 + r] = rbit[4 * s + r];
+    auto regs = [&](int s) { return rbit + 4 * s; };
+    int bad = 0;   // nothing to gain when the tile map's layout serves every stage
+    for (int s = 0; s < nst; ++s) {
+        uint32_t A = 0;
+        for (int r = 0; r < 4; ++r) A |= 1u << regs(s)[r];
+        bad += lay_bad(A);
+    }
+    if (!bad || nst < 2) return false;
+    int cur[TH_TILE_BITS];   // position of each tile bit in the layout stage s reads
+    for (int t = 0; t < TH_TILE_BITS; ++t) cur[t] = t;
+    std::vector<uint8_t> pl8(8 * nst);
+    for (int s = 0; s < nst; ++s) {
+        const uint8_t* R = regs(s);
+        uint32_t Rm = 0;
+        for (int r = 0; r < 4; ++r) Rm |= 1u << R[r];
+        int nxt[TH_TILE_BITS];
+        if (s == nst - 1) {
+            for (int t = 0; t < TH_TILE_BITS; ++t) nxt[t] = t;
+        } else {
+            // the other bits in their current order
+            int others[TH_TILE_BITS], no = 0;
+            for (int p = 0; p < TH_TILE_BITS; ++p)
+                for (int t = 0; t < TH_TILE_BITS; ++t)
+                    if (cur[t] == p && !((Rm >> t) & 1u)) others[no++] = t;
+            const uint8_t* Rn = regs(s + 1);
+            uint32_t Rnm = 0;
+            for (int r = 0; r < 4; ++r) Rnm |= 1u << Rn[r];
+            const bool has0 = Rm & 1u;
+            long best = -1;
+            int bestq[TH_TILE_BITS];
+            // 4-subsets of positions (with 0 exactly when tile bit 0 is a register bit)
+            for (uint32_t S = 0; S < (1u << TH_TILE_BITS); ++S) {
+                if (__builtin_popcount(S) != 4 || ((S & 1u) != 0) != has0) continue;
+                int sp[4], k = 0;
+                for (int p = 0; p < TH_TILE_BITS; ++p)
+                    if ((S >> p) & 1u) sp[k++] = p;
+                int perm[4] = {0, 1, 2, 3};
+                do {
+                    int q[TH_TILE_BITS];
+                    bool okp = true;
+                    for (int r = 0; r < 4; ++r) {
+                        q[R[r]] = sp[perm[r]];
+                        if (R[r] == 0 && sp[perm[r]] != 0) okp = false;
+                    }
+                    if (!okp) continue;
+                    for (int p = 0, o = 0; p < TH_TILE_BITS; ++p)
+                        if (!((S >> p) & 1u)) q[others[o++]] = p;
+                    // the last stage writes the tile map's layout: its other bits must be in order
+                    if (s + 1 == nst - 1) {
+                        int prev = -1;
+                        bool inorder = true;
+                        for (int t = 0; t < TH_TILE_BITS; ++t)
+                            if (!((Rnm >> t) & 1u)) {
+                                if (q[t] < prev) inorder = false;
+                                prev = q[t];
+                            }
+                        if (!inorder) continue;
+                    }
+                    uint32_t A = 0, B = 0;
+                    for (int t = 0; t < TH_TILE_BITS; ++t) {
+                        if ((Rm >> t) & 1u) A |= 1u << q[t];
+                        if ((Rnm >> t) & 1u) B |= 1u << q[t];
+                    }
+                    long disp = 0;
+                    for (int t = 0; t < TH_TILE_BITS; ++t) disp += std::abs(q[t] - t);
+                    const long score = (long)(lay_bad(A) + lay_bad(B)) * 1000 + disp;
+                    if (best < 0 || score < best) {
+                        best = score;
+                        std::memcpy(bestq, q, sizeof q);
+                    }
+                } while (std::next_permutation(perm, perm + 4));
+            }
+            if (best < 0) return false;   // the tile map's layout is out of reach: keep it throughout
+            std::memcpy(nxt, bestq, sizeof nxt);
+        }
+        for (int r = 0; r < 4; ++r) {
+            pl8[8 * s + r] = (uint8_t)cur[R[r]];
+            pl8[8 * s + 4 + r] = (uint8_t)nxt[R[r]];
+        }
+        std::memcpy(cur, nxt, sizeof cur);
+    }
+    std::memcpy(out, pl8.data(), pl8.size());
+    return true;
+}
+
+void plan_lock_layouts(DevPlan* dp) {
+    const Plan& pl = dp->plan;
+    dp->lay.assign(dp->tcs.size() * 8, 0);
+    for (size_t i = 0; i < dp->tcs.size(); ++i)
+        for (int r = 0; r < 4; ++r) dp->lay[8 * i + r] = dp->lay[8 * i + 4 + r] = dp->tcs[i].rbit[r];
+    for (int pass = 0; pass < (int)pl.passes.size(); ++pass) {
+        const DevPass& P = pl.passes[pass];
+        if (!dp->tc_pass[pass] || dp->tc5[pass] || P.m != TH_TILE_BITS || P.stage_count < 2) continue;
+        if (P.stage_count <= TH_MAX_STAGES_3BUF && free_slice_bits(dp, pass) >= 0) continue;   // slice kernel
+        const int nst = P.stage_count;
+        std::vector<uint8_t> rb(4 * nst);
+        bool four = true;
+        for (int s = 0; s < nst; ++s) {
+            const TcsStage& t = dp->tcs[P.stage_begin + s];
+            four = four && t.nreg == 4;
+            for (int r = 0; r < 4; ++r) rb[4 * s + r] = t.rbit[r];
+        }
+        if (four) lock_layouts(rb.data(), nst, &dp->lay[8 * P.stage_begin]);
+    }
+    dp->d_lay = dev_copy(dp->lay);
+}
+
+}  // namespace tcng
+
+extern "C" tcng_status tcng_plan_lock_layouts(const unsigned char* rbit, int nst, unsigned char* out,
+                                              int* relocated) {
+    if (!rbit || !out || !relocated || nst < 1 || nst > 64) return TCNG_EINVAL;
+    for (int s = 0; s < nst; ++s)
+        for (int r = 0; r < 4; ++r)
+            if (rbit[4 * s + r] >= tcng::TH_TILE_BITS || (r && rbit[4 * s + r] <= rbit[4 * s + r - 1]))
+                return TCNG_EINVAL;
+    *relocated = tcng::lock_layouts(rbit, nst, out) ? 1 : 0;
+    return TCNG_OK;
+}
+
+namespace tcng {
+
 bool pass_tch_eligible(const DevPlan* dp, int pass) {
     if (!dp->plan.all_unitary || !dp->tc_pass[pass]) return false;
     const DevPass& P = dp->plan.passes[pass];
@@ -1130,6 +1337,7 @@ cudaError_t launch_pass_tch(const DevPlan* dp, int pass, int items, const void* 
     a.gb1 = grp >= 0 ? (grp >> 8) : 0;
     a.renorm = dp->plan.all_unitary ? 1 : 0;
     a.tcs = dp->d_tcs + P.stage_begin;
+    a.lay = dp->d_lay ? dp->d_lay + 8 * P.stage_begin : nullptr;
     a.wops = static_cast<const unsigned char*>(wops_h);
     const long long tpi = 1ll << (dp->plan.n - P.m);
     a.total_tiles = tpi * items;

@@ -81,6 +81,7 @@ def lib():
             "tcng_autotune_circuit": [vp, vp, sz, vp, sz, vp, i32, C.c_char_p, C.POINTER(dp)],
             "tcng_autotune_report": [C.c_char_p, sz],
             "tcng_fma_peak": [i32, C.POINTER(dp)],
+            "tcng_plan_lock_layouts": [vp, i32, vp, C.POINTER(i32)],
             "tcng_sync_status": [],
             "tcng_profile_enable": [i32],
             "tcng_profile_read": [C.c_char_p, sz, i32],
@@ -371,6 +372,17 @@ def tcng_describe_plan(n, gates, pool, P, adjoint=False):
                                     n_mat, int(P), int(adjoint)).decode()
 
 
+def tcng_plan_lock_layouts(rbit):
+    """Shared-memory layouts of a lock-step FP16 pass: rbit is an (nst, 4) array of
+    register tile bits; returns (layouts (nst, 8) uint8, relocated)."""
+    import numpy as np
+    rb = np.ascontiguousarray(np.asarray(rbit, dtype=np.uint8).reshape(-1, 4))
+    out = np.zeros((rb.shape[0], 8), dtype=np.uint8)
+    rel = C.c_int(0)
+    _check(lib().tcng_plan_lock_layouts(rb.ctypes.data, int(rb.shape[0]), out.ctypes.data, C.byref(rel)))
+    return out, bool(rel.value)
+
+
 def tcng_launch_count():
     return int(lib().tcng_launch_count())
 
@@ -391,6 +403,7 @@ EXPORTED = [
     "tcng_adam_step",
     "tcng_adam_step_f32", "tcng_mlp_forward", "tcng_mlp_backward", "tcng_set_option", "tcng_fma_peak",
     "tcng_get_option", "tcng_autotune", "tcng_autotune_circuit", "tcng_autotune_report", "tcng_sync_status", "tcng_describe_plan",
+    "tcng_plan_lock_layouts",
     "tcng_profile_enable", "tcng_profile_read",
     "tcng_launch_count", "tcng_last_error", "tcng_version",
 ]

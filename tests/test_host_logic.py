@@ -138,3 +138,103 @@ def test_bench_timing_is_max_over_ranks_gloo():
     for p in procs:
         p.join(timeout=60)
     assert out == {0: 15.0, 1: 15.0}
+
+
+# ---- shared-memory layouts of the lock-step FP16 passes (host planner) ----
+def _insert_zeros(row, positions):
+    g = row
+    for b in sorted(positions):
+        low = (1 << b) - 1
+        g = (g & low) | ((g & ~low) << 1)
+    return g
+
+
+def _swizzle(o):   # 128-byte swizzle on 8-byte elements: 16-byte chunk ^= 128-byte row & 7
+    return o ^ ((o >> 3) & 0xE)
+
+
+def _move_tile(stages, lay):
+    """Move a tile (values = tile indices) through the stages' read/write layouts as
+    the lock-step kernel does: row r of stage s reads positions with zeros inserted
+    at the read positions plus register offsets, writes the same values at the write
+    positions.  Returns the final memory and asserts each row is one register group."""
+    mem = list(range(8192))
+    for s, regs in enumerate(stages):
+        rp, wp = [int(x) for x in lay[s][:4]], [int(x) for x in lay[s][4:]]
+        new = [-1] * 8192
+        for row in range(512):
+            gr, gw = _insert_zeros(row, rp), _insert_zeros(row, wp)
+            t0 = None
+            for v in range(16):
+                a, b, lin = gr, gw, 0
+                for i in range(4):
+                    if (v >> i) & 1:
+                        a |= 1 << rp[i]
+                        b |= 1 << wp[i]
+                        lin |= 1 << regs[i]
+                t = mem[a]
+                t0 = t if v == 0 else t0
+                assert t ^ t0 == lin and new[b] == -1
+                new[b] = t
+        mem = new
+    return mem
+
+
+def _wavefronts(positions):
+    """Shared-memory wavefronts of one stage phase (read or write) over a tile: 16
+    warps x 32 lanes (lane = row bits 0..4), 8-byte accesses served per half warp,
+    16-byte pair accesses (tile position 0 a register bit) per quarter warp."""
+    pos = [int(x) for x in positions]
+    pairs = 0 in pos
+    total = 0
+    for w in range(16):
+        for v in range(0, 16, 2 if pairs else 1):
+            words = []
+            for lane in range(32):
+                g = _insert_zeros((w // 4) * 128 + (w % 4) * 32 + lane, pos)
+                for i in range(4):
+                    if (v >> i) & 1:
+                        g |= 1 << pos[i]
+                ws = []
+                for k in range(2 if pairs else 1):
+                    o = _swizzle(g | k)
+                    ws += [2 * o, 2 * o + 1]
+                words.append(ws)
+            phase = 8 if pairs else 16
+            for p0 in range(0, 32, phase):
+                ph = [x for ws in words[p0:p0 + phase] for x in ws]
+                banks = {}
+                for x in ph:
+                    banks.setdefault(x % 32, set()).add(x)
+                total += max(max(len(b) for b in banks.values()), len(set(ph)) // 32)
+    return total
+
+
+def test_lock_layouts_move_the_tile_consistently_and_spread_banks(T):
+    """The planned layouts of a 13-qubit brickwork pass (stages on {2,3,4,5} and
+    {1,2,5,6} conflict on the tile map's layout): every row is one register group,
+    the last stage writes the tile map's layout, and each stage's reads and writes
+    take the minimum wavefronts (512 per tile) where the tile map's layout takes more."""
+    stages = [(0, 1, 2, 3), (4, 5, 6, 7), (8, 9, 10, 11), (3, 4, 7, 8), (2, 3, 4, 5), (6, 7, 8, 9),
+              (1, 2, 5, 6), (0, 1, 2, 3), (4, 5, 6, 7), (2, 3, 4, 5), (0, 1, 2, 3)]
+    lay, relocated = T.tcng_plan_lock_layouts(stages)
+    assert relocated
+    assert [tuple(lay[0][:4])] == [stages[0]] and tuple(lay[-1][4:]) == stages[-1]
+    assert _move_tile(stages, lay) == list(range(8192))
+    before = sum(2 * _wavefronts(s) for s in stages)
+    after = sum(_wavefronts(l[:4]) + _wavefronts(l[4:]) for l in lay)
+    assert after == 2 * len(stages) * 512 < before
+
+
+def test_lock_layouts_random_passes_and_rejects(T):
+    rng = np.random.default_rng(7)
+    for _ in range(6):
+        nst = int(rng.integers(2, 12))
+        stages = [tuple(sorted(rng.choice(13, 4, replace=False).tolist())) for _ in range(nst)]
+        lay, relocated = T.tcng_plan_lock_layouts(stages)
+        assert _move_tile(stages, lay) == list(range(8192))
+        if not relocated:
+            assert all(tuple(l[:4]) == s and tuple(l[4:]) == s for l, s in zip(lay, stages))
+    for bad in ([(0, 1, 2, 13)], [(3, 2, 1, 0)], []):
+        with pytest.raises(T.TcngError):
+            T.tcng_plan_lock_layouts(bad if bad else np.zeros((0, 4)))
