@@ -168,14 +168,22 @@ __device__ __forceinline__ void ef_run(const float2 (&a)[kExpSlots], const float
         *ap = fmaf(scale(j), v, accv);
     }
 }
-// ... of the Z-only terms.
+// ... of the Z-only terms, two per step.
 __device__ __forceinline__ void ef_run_z(const float2 (&pz)[kExpSlots / 2], int tid, const EfPass& ef, int j,
                                          int end, uint32_t fm, float* __restrict__ acc) {
-    for (; j < end; ++j) {
+    auto scale = [&](int k) { return __uint_as_float(__float_as_uint(ef.sf[k]) ^ (((fm >> k) & 1u) << 31)); };
+    for (; j + 1 < end; j += 2) {
+        float* ap0 = acc + j * kExpThreads + tid;
+        float* ap1 = ap0 + kExpThreads;
+        const float acc0 = *ap0, acc1 = *ap1;
+        const float v0 = ef_butterfly(pz, ef.e[j]), v1 = ef_butterfly(pz, ef.e[j + 1]);
+        *ap0 = fmaf(scale(j), v0, acc0);
+        *ap1 = fmaf(scale(j + 1), v1, acc1);
+    }
+    if (j < end) {
         float* ap = acc + j * kExpThreads + tid;
         const float accv = *ap;
-        const float v = ef_butterfly(pz, ef.e[j]);
-        *ap = fmaf(__uint_as_float(__float_as_uint(ef.sf[j]) ^ (((fm >> j) & 1u) << 31)), v, accv);
+        *ap = fmaf(scale(j), ef_butterfly(pz, ef.e[j]), accv);
     }
 }
 
