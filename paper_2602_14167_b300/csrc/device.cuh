@@ -399,6 +399,36 @@ __device__ __forceinline__ void diag_index(const DevOp& op, const int (&L)[1 << 
 }
 
 // Diagonal op: multiply slot s by M[idx(s)].
+// A lone RZ (G_Z) or RZZ (G_ZZ) is a function of the parity of its sources: entry
+// M[0] on even, M[1] on odd parity.  Bit s of the result: slot s has odd parity
+// (slot 0 from its tile offset L0; register bit i flips it when it feeds a source).
+template <int R>
+__device__ __forceinline__ uint32_t zpar_mask(const DevOp& op, int L0, long long gbase) {
+    int p0 = src_bit(op.src[0], L0, gbase);
+    if (op.k > 1) p0 ^= src_bit(op.src[1], L0, gbase);
+    uint32_t m = p0 ? 0xFFFFFFFFu : 0u;
+    const int nib = op.mask | (op.pad << 8);
+    constexpr uint32_t kSlots[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
+#pragma unroll
+    for (int i = 0; i < R && i < 4; ++i)
+        if ((nib >> (4 * i)) & 15) m ^= kSlots[i];
+    return m;
+}
+// a[s] <- d_s a[s] with d_s = M[0] (even slot) or M[1] (odd), conjugated for DAG.
+template <typename C, int R, bool DAG>
+__device__ __forceinline__ void zpar_apply(C (&a)[1 << R], uint32_t odd, C m0, C m1) {
+    if constexpr (DAG) {
+        m0 = cconj(m0);
+        m1 = cconj(m1);
+    }
+#pragma unroll
+    for (int s = 0; s < (1 << R); ++s) {
+        const bool o = (odd >> s) & 1u;
+        const C d = cmk<C>(o ? m1.x : m0.x, o ? m1.y : m0.y);
+        a[s] = cmul(d, a[s]);
+    }
+}
+
 template <typename C, int R, bool DAG>
 __device__ __forceinline__ void diag_apply(C (&a)[1 << R], const DevOp& op, const C* __restrict__ M,
                                            const int (&L)[1 << R], long long gbase) {
@@ -520,6 +550,8 @@ __device__ __forceinline__ void run_stage_group(C* __restrict__ buf, const DevSt
         if (op.kind == K_DENSE) {
             if (op.grad == G_X || op.grad == G_Y) rot_dispatch<C, R>(op, a, M, tau);   // lone RX / RY
             else dense_dispatch<C, R, false>(op.mask, a, M, tau);
+        } else if (op.grad == G_Z || op.grad == G_ZZ) {   // lone RZ / RZZ
+            zpar_apply<C, R, false>(a, zpar_mask<R>(op, L[0], gbase), M[0], M[1]);
         } else {
             diag_apply<C, R, false>(a, op, M, L, gbase);
         }

@@ -191,6 +191,26 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
                 } else if (active) {
                     dense_dispatch2<C, R, true>(op.mask, p, l, M, tau);
                 }
+            } else if (op.grad == G_Z || op.grad == G_ZZ) {
+                // lone RZ / RZZ: the generator's sign is the slot's source parity, and the
+                // uncompute takes M[0] or M[1] by the same parity (no phase-table reads)
+                const uint32_t odd = zpar_mask<R>(op, L0, gbase);
+                T v = 0;
+                if (active) {
+#pragma unroll
+                    for (int s = 0; s < (1 << R); ++s) {
+                        const T w = im_conj_mul(l[s].x, l[s].y, p[s].x, p[s].y);
+                        v += ((odd >> s) & 1u) ? -w : w;
+                    }
+                }
+                const T w = warp_sum(v);
+                if (lane == 0) red[warp * kMaxStageGrads + j] += w;
+                ++j;
+                if (active) {
+                    const C m0 = M[0], m1 = M[1];
+                    zpar_apply<C, R, true>(p, odd, m0, m1);
+                    zpar_apply<C, R, true>(l, odd, m0, m1);
+                }
             } else {
                 int idx[1 << R];
                 diag_index0<R>(op, L0, gbase, idx);
