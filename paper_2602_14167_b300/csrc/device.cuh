@@ -399,22 +399,46 @@ __device__ __forceinline__ void diag_index(const DevOp& op, const int (&L)[1 << 
 }
 
 // Diagonal op: multiply slot s by M[idx(s)].
-// A lone RZ (G_Z) or RZZ (G_ZZ) is a function of the parity of its sources: entry
-// M[0] on even, M[1] on odd parity.  Bit s of the result: slot s has odd parity
-// (slot 0 from its tile offset L0; register bit i flips it when it feeds a source).
+// Slots (bit s of a mask) where source 0 / source 1 of a diagonal op is 1: slot 0's
+// value from its tile offset L0, then one XOR of a constant slot pattern for each
+// register bit that feeds the source.
+template <int R>
+__device__ __forceinline__ void src_masks(const DevOp& op, int L0, long long gbase, uint32_t& m0, uint32_t& m1) {
+    constexpr uint32_t kSlots[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
+    m0 = src_bit(op.src[0], L0, gbase) ? 0xFFFFFFFFu : 0u;
+    m1 = (op.k > 1 && src_bit(op.src[1], L0, gbase)) ? 0xFFFFFFFFu : 0u;
+    const int nib = op.mask | (op.pad << 8);
+#pragma unroll
+    for (int i = 0; i < R && i < 4; ++i) {
+        const int jj = (nib >> (4 * i)) & 15;
+        if (jj == 1) m0 ^= kSlots[i];
+        if (jj == 2) m1 ^= kSlots[i];
+    }
+}
+// A lone RZ (G_Z) or RZZ (G_ZZ) takes M[0] on even and M[1] on odd parity of its
+// sources: the odd slots (one mask for the parity: slot 0's from its tile offset,
+// then the slot pattern of each register bit that feeds a source).
 template <int R>
 __device__ __forceinline__ uint32_t zpar_mask(const DevOp& op, int L0, long long gbase) {
+    constexpr uint32_t kSlots[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
     int p0 = src_bit(op.src[0], L0, gbase);
     if (op.k > 1) p0 ^= src_bit(op.src[1], L0, gbase);
     uint32_t m = p0 ? 0xFFFFFFFFu : 0u;
     const int nib = op.mask | (op.pad << 8);
-    constexpr uint32_t kSlots[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
 #pragma unroll
     for (int i = 0; i < R && i < 4; ++i)
         if ((nib >> (4 * i)) & 15) m ^= kSlots[i];
     return m;
 }
-// a[s] <- d_s a[s] with d_s = M[0] (even slot) or M[1] (odd), conjugated for DAG.
+// A lone controlled phase (G_P11) takes M[3] on the slots where both sources are 1,
+// else M[0].
+template <int R>
+__device__ __forceinline__ uint32_t p11_mask(const DevOp& op, int L0, long long gbase) {
+    uint32_t m0, m1;
+    src_masks<R>(op, L0, gbase, m0, m1);
+    return m0 & m1;
+}
+// a[s] <- d_s a[s] with d_s = m0, or m1 on the slots of `odd`, conjugated for DAG.
 template <typename C, int R, bool DAG>
 __device__ __forceinline__ void zpar_apply(C (&a)[1 << R], uint32_t odd, C m0, C m1) {
     if constexpr (DAG) {
@@ -552,6 +576,8 @@ __device__ __forceinline__ void run_stage_group(C* __restrict__ buf, const DevSt
             else dense_dispatch<C, R, false>(op.mask, a, M, tau);
         } else if (op.grad == G_Z || op.grad == G_ZZ) {   // lone RZ / RZZ
             zpar_apply<C, R, false>(a, zpar_mask<R>(op, L[0], gbase), M[0], M[1]);
+        } else if (op.grad == G_P11) {                     // lone controlled phase
+            zpar_apply<C, R, false>(a, p11_mask<R>(op, L[0], gbase), M[0], M[3]);
         } else {
             diag_apply<C, R, false>(a, op, M, L, gbase);
         }

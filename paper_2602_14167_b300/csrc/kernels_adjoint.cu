@@ -211,6 +211,24 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
                     zpar_apply<C, R, true>(p, odd, m0, m1);
                     zpar_apply<C, R, true>(l, odd, m0, m1);
                 }
+            } else if (op.grad == G_P11) {
+                // lone controlled phase: generator |11><11| (weight 1 on the slots with both
+                // sources set), uncompute by M[0] or M[3] on the same slots
+                const uint32_t both = p11_mask<R>(op, L0, gbase);
+                T v = 0;
+                if (active) {
+#pragma unroll
+                    for (int s = 0; s < (1 << R); ++s)
+                        if ((both >> s) & 1u) v += im_conj_mul(l[s].x, l[s].y, p[s].x, p[s].y);
+                }
+                const T w = warp_sum(v);
+                if (lane == 0) red[warp * kMaxStageGrads + j] += w;
+                ++j;
+                if (active) {
+                    const C m0 = M[0], m1 = M[3];
+                    zpar_apply<C, R, true>(p, both, m0, m1);
+                    zpar_apply<C, R, true>(l, both, m0, m1);
+                }
             } else {
                 int idx[1 << R];
                 diag_index0<R>(op, L0, gbase, idx);
