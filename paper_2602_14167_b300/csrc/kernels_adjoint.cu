@@ -42,9 +42,8 @@ __device__ __forceinline__ R im_conj_mul(R lx, R ly, R px, R py) {  // Im(conj(l
 }
 
 // Im<lambda|X|psi> or Im<lambda|Y|psi> of one group for a gate on register bit BIT.
-template <typename C, int R, int BIT>
-__device__ __forceinline__ typename Real<C>::T grad_xy(bool is_y, const C (&p)[1 << R],
-                                                      const C (&l)[1 << R], int flip) {
+template <typename C, int R, int BIT, bool is_y>
+__device__ __forceinline__ typename Real<C>::T grad_xy(const C (&p)[1 << R], const C (&l)[1 << R], int flip) {
     using T = typename Real<C>::T;
     T acc = 0;
     if constexpr (BIT < R) {
@@ -52,7 +51,7 @@ __device__ __forceinline__ typename Real<C>::T grad_xy(bool is_y, const C (&p)[1
         for (int s = 0; s < (1 << R); ++s) {
             if ((s >> BIT) & 1) continue;
             const int s1 = s | (1 << BIT);
-            if (!is_y) {
+            if constexpr (!is_y) {
                 acc += im_conj_mul(l[s].x, l[s].y, p[s1].x, p[s1].y) +
                        im_conj_mul(l[s1].x, l[s1].y, p[s].x, p[s].y);
             } else {
@@ -110,16 +109,24 @@ __device__ __forceinline__ typename Real<C>::T grad_apply_xy(const DevOp& op, C 
     switch (bit) {
 #define TCNG_GA(B)                                              \
     case B:                                                     \
-        acc = grad_xy<C, R, B>(is_y, p, l, flip);               \
-        if (is_y) rot_dag2<C, R, B, true>(p, l, c, s);          \
-        else rot_dag2<C, R, B, false>(p, l, c, s);              \
+        if (is_y) {                                             \
+            acc = grad_xy<C, R, B, true>(p, l, flip);           \
+            rot_dag2<C, R, B, true>(p, l, c, s);                \
+        } else {                                                \
+            acc = grad_xy<C, R, B, false>(p, l, flip);          \
+            rot_dag2<C, R, B, false>(p, l, c, s);               \
+        }                                                       \
         break;
         TCNG_GA(0) TCNG_GA(1) TCNG_GA(2) TCNG_GA(3)
 #undef TCNG_GA
     default:
-        acc = grad_xy<C, R, 4>(is_y, p, l, flip);
-        if (is_y) rot_dag2<C, R, 4, true>(p, l, c, s);
-        else rot_dag2<C, R, 4, false>(p, l, c, s);
+        if (is_y) {
+            acc = grad_xy<C, R, 4, true>(p, l, flip);
+            rot_dag2<C, R, 4, true>(p, l, c, s);
+        } else {
+            acc = grad_xy<C, R, 4, false>(p, l, flip);
+            rot_dag2<C, R, 4, false>(p, l, c, s);
+        }
         break;
     }
     return acc;
