@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(adjoint_threads<C>(), 1) adjoint_kernel(AdjArg
     C* mats = sl + res_elems;
     double* gacc = reinterpret_cast<double*>(mats + kMaxPassMat);
     T* red = reinterpret_cast<T*>(gacc + kMaxGradSlots);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(red + 32 * kMaxStageGrads);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(red + 2 * 32 * kMaxStageGrads);
     __shared__ int s_item;
     __shared__ double s_red[32];
     __shared__ int s_abort;
@@ -462,6 +462,8 @@ __global__ void __launch_bounds__(adjoint_threads<C>(), 1) adjoint_kernel(AdjArg
         }
         // ---------------- reverse sweep ----------------
         if (a.want_grad) {
+            for (int i = tid; i < 2 * 32 * kMaxStageGrads; i += nthreads) red[i] = T(0);
+            __syncthreads();
             for (int pi = S.n_passes - 1; pi >= 0 && !s_abort; --pi) {
                 const DevPass P = S.passes[pi];
                 for (int i = tid; i < P.mat_count; i += nthreads) mats[i] = table[P.mat_begin + i];
@@ -480,13 +482,16 @@ __global__ void __launch_bounds__(adjoint_threads<C>(), 1) adjoint_kernel(AdjArg
                     const long long gbase = resident ? 0 : tile_global_base(P, t);
                     for (int si = P.stage_count - 1; si >= 0; --si) {
                         const DevStage st = S.stages[P.stage_begin + si];
-                        for (int i = tid; i < nwarps * kMaxStageGrads; i += nthreads) red[i] = T(0);
-                        __syncthreads();
+                        // two partial-sum buffers taken in turn by consecutive stages: a stage's
+                        // fold reads and clears its buffer while the next stage fills the other,
+                        // so one barrier per stage orders both (they are all zero here: cleared
+                        // before the sweep, then by each fold)
+                        T* rs = red + (si & 1) * (32 * kMaxStageGrads);
                         if (st.nreg > kRegBits) {   // 5-qubit constant block: no gradient ops here
                             run_stage_smem<C, true>(tp, st, S.dops, mats, P.m, gbase);
                             run_stage_smem<C, true>(tl, st, S.dops, mats, P.m, gbase);
                         } else {
-                            run_stage_adjoint<C, kRegBits>(tp, tl, st, S.dops, mats, P.m, gbase, red);
+                            run_stage_adjoint<C, kRegBits>(tp, tl, st, S.dops, mats, P.m, gbase, rs);
                         }
                         __syncthreads();
                         // fold this stage's gradient partials (fixed order) into gacc
@@ -500,11 +505,14 @@ __global__ void __launch_bounds__(adjoint_threads<C>(), 1) adjoint_kernel(AdjArg
                                 }
                             }
                             double s = 0;
-                            for (int w = 0; w < nwarps; ++w) s += red[w * kMaxStageGrads + tid];
+                            for (int w = 0; w < nwarps; ++w) {
+                                s += rs[w * kMaxStageGrads + tid];
+                                rs[w * kMaxStageGrads + tid] = T(0);
+                            }
                             gacc[slot] += s;
                         }
-                        __syncthreads();
                     }
+                    __syncthreads();
                     if (!resident) {
                         C* gptr[2] = {gp, gl};
                         C* sb[2] = {tp, tl};
@@ -528,7 +536,7 @@ __global__ void __launch_bounds__(adjoint_threads<C>(), 1) adjoint_kernel(AdjArg
 template <typename C>
 size_t adjoint_smem_bytes(int res_bits) {
     return 2 * (sizeof(C) << res_bits) + sizeof(C) * kMaxPassMat + sizeof(double) * kMaxGradSlots +
-           sizeof(typename Real<C>::T) * 32 * kMaxStageGrads + 16;
+           sizeof(typename Real<C>::T) * 2 * 32 * kMaxStageGrads + 16;
 }
 
 template <typename C>
