@@ -157,7 +157,8 @@ __device__ __forceinline__ typename Real<C>::T grad_part_diag(const DevOp& op, c
 template <typename C, int R>
 __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, const DevStage& st,
                                   const DevOp* __restrict__ ops, const C* __restrict__ mats,
-                                  int tile_bits, long long gbase, typename Real<C>::T* red) {
+                                  int tile_bits, long long gbase, typename Real<C>::T* red,
+                                  int* __restrict__ gslot) {
     using T = typename Real<C>::T;
     const int ngroups = 1 << (tile_bits - R);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -194,6 +195,7 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
                     T v = active ? grad_apply_xy<C, R>(op, p, l, M, tau) : T(0);
                     const T w = warp_sum(v);
                     if (lane == 0) red[warp * kMaxStageGrads + j] += w;
+                    if (threadIdx.x == 0) gslot[j] = op.slot;
                     ++j;
                 } else if (active) {
                     dense_dispatch2<C, R, true>(op.mask, p, l, M, tau);
@@ -212,6 +214,7 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
                 }
                 const T w = warp_sum(v);
                 if (lane == 0) red[warp * kMaxStageGrads + j] += w;
+                    if (threadIdx.x == 0) gslot[j] = op.slot;
                 ++j;
                 if (active) {
                     const C m0 = M[0], m1 = M[1];
@@ -230,6 +233,7 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
                 }
                 const T w = warp_sum(v);
                 if (lane == 0) red[warp * kMaxStageGrads + j] += w;
+                    if (threadIdx.x == 0) gslot[j] = op.slot;
                 ++j;
                 if (active) {
                     const C m0 = M[0], m1 = M[3];
@@ -243,6 +247,7 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
                     T v = active ? grad_part_diag<C, R>(op, p, l, idx) : T(0);
                     const T w = warp_sum(v);
                     if (lane == 0) red[warp * kMaxStageGrads + j] += w;
+                    if (threadIdx.x == 0) gslot[j] = op.slot;
                     ++j;
                 }
                 if (active) diag_apply2<C, R, true>(p, l, M, idx);
@@ -321,14 +326,15 @@ __global__ void __launch_bounds__(adjoint_threads<C>(), 1) adjoint_kernel(AdjArg
     const int tid = threadIdx.x;
     const int nthreads = blockDim.x;
     const int nwarps = nthreads >> 5;
-    // layout: [psi tile | lam tile] (2 * 2^mres) | mats window | gacc | red | bar
+    // layout: [psi tile | lam tile] (2 * 2^mres) | mats window | gacc | red (2 buffers) | gslot (2) | bar
     const int res_elems = 1 << a.res_bits;
     C* sp = reinterpret_cast<C*>(smem_raw);
     C* sl = sp + res_elems;
     C* mats = sl + res_elems;
     double* gacc = reinterpret_cast<double*>(mats + kMaxPassMat);
     T* red = reinterpret_cast<T*>(gacc + kMaxGradSlots);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(red + 2 * 32 * kMaxStageGrads);
+    int* gslot2 = reinterpret_cast<int*>(red + 2 * 32 * kMaxStageGrads);   // 2 x kMaxStageGrads
+    uint64_t* bar = reinterpret_cast<uint64_t*>(gslot2 + 2 * kMaxStageGrads);
     __shared__ int s_item;
     __shared__ double s_red[32];
     __shared__ int s_abort;
@@ -487,23 +493,17 @@ __global__ void __launch_bounds__(adjoint_threads<C>(), 1) adjoint_kernel(AdjArg
                         // so one barrier per stage orders both (they are all zero here: cleared
                         // before the sweep, then by each fold)
                         T* rs = red + (si & 1) * (32 * kMaxStageGrads);
+                        int* gs = gslot2 + (si & 1) * kMaxStageGrads;   // slot of the stage's j-th gradient op
                         if (st.nreg > kRegBits) {   // 5-qubit constant block: no gradient ops here
                             run_stage_smem<C, true>(tp, st, S.dops, mats, P.m, gbase);
                             run_stage_smem<C, true>(tl, st, S.dops, mats, P.m, gbase);
                         } else {
-                            run_stage_adjoint<C, kRegBits>(tp, tl, st, S.dops, mats, P.m, gbase, rs);
+                            run_stage_adjoint<C, kRegBits>(tp, tl, st, S.dops, mats, P.m, gbase, rs, gs);
                         }
                         __syncthreads();
                         // fold this stage's gradient partials (fixed order) into gacc
                         if (tid < (int)st.n_grad) {
-                            int j = 0, slot = -1;
-                            for (int i = (int)st.op_count - 1; i >= 0; --i) {
-                                const DevOp op = S.dops[st.op_begin + i];
-                                if (op.grad != G_NONE) {
-                                    if (j == tid) { slot = op.slot; break; }
-                                    ++j;
-                                }
-                            }
+                            const int slot = gs[tid];
                             double s = 0;
                             for (int w = 0; w < nwarps; ++w) {
                                 s += rs[w * kMaxStageGrads + tid];
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(adjoint_threads<C>(), 1) adjoint_kernel(AdjArg
 template <typename C>
 size_t adjoint_smem_bytes(int res_bits) {
     return 2 * (sizeof(C) << res_bits) + sizeof(C) * kMaxPassMat + sizeof(double) * kMaxGradSlots +
-           sizeof(typename Real<C>::T) * 2 * 32 * kMaxStageGrads + 16;
+           sizeof(typename Real<C>::T) * 2 * 32 * kMaxStageGrads + sizeof(int) * 2 * kMaxStageGrads + 16;
 }
 
 template <typename C>
