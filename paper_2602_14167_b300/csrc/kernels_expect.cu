@@ -12,17 +12,20 @@
 //     prepared once per pass), the tile's part (global bits, one ballot per tile
 //     for all terms) and the register part (tile bits 0, 10, 11, 12: a butterfly
 //     with +-1 factors).
-// The term loop runs over the pass's terms at run time; each term jumps to a
-// form specialised for its (XR, swap, Re/Im), so the partner pairs are read at
-// fixed offsets from one base.  A Pauli string is Hermitian, so the terms of x
-// and x ^ m are complex conjugates: one member of each pair, doubled, gives
-// the same sum.  With XR != 0 only the register pairs with XR's top bit clear
-// are evaluated (four partner loads instead of eight); otherwise, with X bits on
-// tile bits 6..9 (warp bits), the warps on one side of the lowest such bit
-// (alternating per tile) skip the term.  Partner reads from shared memory
-// bound this kernel.  Per term and tile, lane pairs add their values and the
-// even lanes accumulate them in FP32 in shared memory; every 64 tiles the
-// warps fold those sums into FP64 in a fixed order.
+// The host sorts the pass's terms into runs of one form (XR, swap, Re/Im, and
+// the warp-skip bit below); the kernel dispatches once per run to code
+// specialised on the form, so the partner pairs are read at fixed offsets from
+// one base, and takes two terms of a run per step in one basic block.  The term
+// constants are a kernel parameter (constant bank).  A Pauli string is
+// Hermitian, so the terms of x and x ^ m are complex conjugates: one member of
+// each pair, doubled, gives the same sum.  With XR != 0 only the register pairs
+// with XR's top bit clear are evaluated (four partner loads instead of eight);
+// otherwise, with X bits on tile bits 6..9 (warp bits), the warps on one side of
+// the lowest such bit (alternating per tile) skip the term.  The butterflies run
+// on packed FP32 pairs.  Per term and tile each thread adds its value, times the
+// term's scale and sign, to its own FP32 sum in shared memory; every 64 tiles the
+// warps fold those sums into FP64 in a fixed order.  Each tile's base index is
+// one warp OR-reduction.
 // Tiles whose bit runs fit a tensor map arrive by one TMA copy (warp 0 refills a
 // buffer once every warp has released it).  Others (gathered qubits scattered
 // over more than five dimensions) are copied by all 512 threads with 16-byte
