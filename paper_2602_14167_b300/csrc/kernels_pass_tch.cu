@@ -29,6 +29,10 @@
 //     slice's 128 rows stay closed under the pass) run one tile per slice, the
 //     slice pairs half a stage apart, as in the TF32 kernel.
 // A seventeenth warp moves tiles (TMA or per-chunk bulk copies, tile_io.cuh).
+// In the lock-step passes on the 128-byte-swizzled tile each stage may write its
+// register bits to new shared-memory positions (planned on the host by
+// lock_layouts below) so that every stage's reads and writes reach all bank
+// slots.  The split's residual x - hi is one mixed-precision FMA per component.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdlib>
