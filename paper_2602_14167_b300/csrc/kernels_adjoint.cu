@@ -307,10 +307,18 @@ __device__ void tile_store(const DevPass& p, long long tile, C* const* gptr, C* 
                 bulk_s2g(gptr[s] + base + chunk_offset(p, j), sbuf[s] + ((long long)j << p.chunk),
                          chunk_bytes);
         bulk_commit();
+        bulk_wait_read<0>();   // the buffer may be refilled; the writes complete by the pass's end
+    }
+    __syncthreads();
+}
+
+// End of a streamed pass: this pass's tile stores complete (and ordered before
+// later reads of the state) before the next pass or phase reads it.
+__device__ __forceinline__ void pass_stores_done() {
+    if (threadIdx.x < 32) {
         bulk_wait<0>();
         fence_proxy_async_all();
     }
-    __syncthreads();
 }
 
 // ------------------------------------------------------------------ kernel --
@@ -395,6 +403,7 @@ __global__ void __launch_bounds__(adjoint_threads<C>(), 1) adjoint_kernel(AdjArg
                     tile_store<C>(P, t, gptr, sb, 1);
                 }
             }
+            if (!resident) pass_stores_done();
             __syncthreads();
         }
         if (s_abort) break;
@@ -519,6 +528,7 @@ __global__ void __launch_bounds__(adjoint_threads<C>(), 1) adjoint_kernel(AdjArg
                         tile_store<C>(P, t, gptr, sb, 2);
                     }
                 }
+                if (!resident) pass_stores_done();
                 __syncthreads();
             }
             if (s_abort) break;
