@@ -289,12 +289,28 @@ __device__ bool tile_load(const DevPass& p, long long tile, C* const* gptr, C* c
     return ok;
 }
 
+// Issue (warp 0) the copy of one tile of one state into sbuf; completion on bar.
+template <typename C>
+__device__ void tile_load_issue(const DevPass& p, long long tile, const C* gptr, C* sbuf, uint64_t* bar) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        const long long base = tile_global_base(p, tile);
+        const uint32_t chunk_bytes = (uint32_t)(sizeof(C) << p.chunk);
+        const int nchunks = 1 << p.ngather;
+        if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(C) << p.m));
+        __syncwarp();
+        for (int j = lane; j < nchunks; j += 32)
+            bulk_g2s(sbuf + ((long long)j << p.chunk), gptr + base + chunk_offset(p, j), chunk_bytes, bar);
+    }
+}
+
 __device__ __forceinline__ void fence_proxy_async_all() {
     asm volatile("fence.proxy.async;" ::: "memory");
 }
 
 template <typename C>
-__device__ void tile_store(const DevPass& p, long long tile, C* const* gptr, C* const* sbuf, int nst) {
+__device__ void tile_store(const DevPass& p, long long tile, C* const* gptr, C* const* sbuf, int nst,
+                           bool wait_read = true) {
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -307,7 +323,7 @@ __device__ void tile_store(const DevPass& p, long long tile, C* const* gptr, C* 
                 bulk_s2g(gptr[s] + base + chunk_offset(p, j), sbuf[s] + ((long long)j << p.chunk),
                          chunk_bytes);
         bulk_commit();
-        bulk_wait_read<0>();   // the buffer may be refilled; the writes complete by the pass's end
+        if (wait_read) bulk_wait_read<0>();   // the buffer may be refilled; the writes complete by the pass's end
     }
     __syncthreads();
 }
@@ -370,9 +386,13 @@ __global__ void __launch_bounds__(adjoint_threads<C>(), 1) adjoint_kernel(AdjArg
         C* gp = resident ? nullptr : scratch_p;
         C* gl = resident ? nullptr : scratch_l;
         // ---------------- forward: psi = U |0> ----------------
+        // Streamed states: the first pass makes its tiles of |0...0> in shared memory
+        // (the scratch state is first written by that pass), and the tiles of a pass
+        // alternate between the two buffers (lambda's is free here), so the copy of
+        // tile t + 1 runs while tile t is computed.
         if (resident) {
             for (long long x = tid; x < N; x += nthreads) sp[x] = cmk<C>(x == 0 ? 1 : 0, 0);
-        } else {
+        } else if (S.n_passes == 0) {
             for (long long x = tid; x < N; x += nthreads) gp[x] = cmk<C>(x == 0 ? 1 : 0, 0);
         }
         for (int g = tid; g < S.n_grad; g += nthreads) gacc[g] = 0.0;
@@ -383,24 +403,40 @@ __global__ void __launch_bounds__(adjoint_threads<C>(), 1) adjoint_kernel(AdjArg
             for (int i = tid; i < P.mat_count; i += nthreads) mats[i] = table[P.mat_begin + i];
             __syncthreads();
             const long long ntiles = resident ? 1 : (1ll << (n - P.m));
+            const bool make = pi == 0;   // streamed: the first pass's tiles are made, not loaded
+            if (!resident && !make) tile_load_issue<C>(P, 0, gp, sp, bar);
             for (long long t = 0; t < ntiles; ++t) {
+                C* cur = (!resident && (t & 1)) ? sl : sp;
                 if (!resident) {
-                    C* gptr[1] = {gp};
-                    C* sb[1] = {sp};
-                    if (!tile_load<C>(P, t, gptr, sb, 1, bar, &phase, a.err)) s_abort = 1;
+                    if (make) {
+                        if (t >= 2) {   // tile t - 2's store (the older of two in flight) has read cur
+                            if (tid < 32) bulk_wait_read<1>();
+                            __syncthreads();
+                        }
+                        const long long tn = 1ll << P.m;
+                        for (long long x = tid; x < tn; x += nthreads)
+                            cur[x] = cmk<C>(t == 0 && x == 0 ? 1 : 0, 0);
+                    } else {
+                        if (!mbar_wait_bounded(bar, phase, a.err)) s_abort = 1;
+                        phase ^= 1u;
+                    }
                     __syncthreads();
                     if (s_abort) break;
+                    if (!make && t + 1 < ntiles) {   // the other buffer, once tile t - 1's store has read it
+                        if (tid < 32) bulk_wait_read<0>();
+                        tile_load_issue<C>(P, t + 1, gp, (t & 1) ? sp : sl, bar);
+                    }
                 }
                 const long long gbase = resident ? 0 : tile_global_base(P, t);
                 for (int si = 0; si < P.stage_count; ++si) {
                     const DevStage st = S.stages[P.stage_begin + si];
-                    run_stage<C>(sp, st, S.dops, mats, P.m, gbase);
+                    run_stage<C>(cur, st, S.dops, mats, P.m, gbase);
                     __syncthreads();
                 }
                 if (!resident) {
                     C* gptr[1] = {gp};
-                    C* sb[1] = {sp};
-                    tile_store<C>(P, t, gptr, sb, 1);
+                    C* sb[1] = {cur};
+                    tile_store<C>(P, t, gptr, sb, 1, false);
                 }
             }
             if (!resident) pass_stores_done();
