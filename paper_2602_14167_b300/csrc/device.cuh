@@ -398,7 +398,6 @@ __device__ __forceinline__ void diag_index(const DevOp& op, const int (&L)[1 << 
     diag_index0<R>(op, L[0], gbase, idx);
 }
 
-// Diagonal op: multiply slot s by M[idx(s)].
 // Slots (bit s of a mask) where source 0 / source 1 of a diagonal op is 1: slot 0's
 // value from its tile offset L0, then one XOR of a constant slot pattern for each
 // register bit that feeds the source.
@@ -453,6 +452,7 @@ __device__ __forceinline__ void zpar_apply(C (&a)[1 << R], uint32_t odd, C m0, C
     }
 }
 
+// Diagonal op: multiply slot s by M[idx(s)].
 template <typename C, int R, bool DAG>
 __device__ __forceinline__ void diag_apply(C (&a)[1 << R], const DevOp& op, const C* __restrict__ M,
                                            const int (&L)[1 << R], long long gbase) {
