@@ -195,7 +195,7 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
                     T v = active ? grad_apply_xy<C, R>(op, p, l, M, tau) : T(0);
                     const T w = warp_sum(v);
                     if (lane == 0) red[warp * kMaxStageGrads + j] += w;
-                    if (threadIdx.x == 0) gslot[j] = op.slot;
+                    if (threadIdx.x == 0) gslot[j] = op.slot;   // the fold's accumulator slot
                     ++j;
                 } else if (active) {
                     dense_dispatch2<C, R, true>(op.mask, p, l, M, tau);
@@ -214,7 +214,7 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
                 }
                 const T w = warp_sum(v);
                 if (lane == 0) red[warp * kMaxStageGrads + j] += w;
-                    if (threadIdx.x == 0) gslot[j] = op.slot;
+                if (threadIdx.x == 0) gslot[j] = op.slot;   // the fold's accumulator slot
                 ++j;
                 if (active) {
                     const C m0 = M[0], m1 = M[1];
@@ -233,7 +233,7 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
                 }
                 const T w = warp_sum(v);
                 if (lane == 0) red[warp * kMaxStageGrads + j] += w;
-                    if (threadIdx.x == 0) gslot[j] = op.slot;
+                if (threadIdx.x == 0) gslot[j] = op.slot;   // the fold's accumulator slot
                 ++j;
                 if (active) {
                     const C m0 = M[0], m1 = M[3];
@@ -247,7 +247,7 @@ __device__ void run_stage_adjoint(C* __restrict__ pbuf, C* __restrict__ lbuf, co
                     T v = active ? grad_part_diag<C, R>(op, p, l, idx) : T(0);
                     const T w = warp_sum(v);
                     if (lane == 0) red[warp * kMaxStageGrads + j] += w;
-                    if (threadIdx.x == 0) gslot[j] = op.slot;
+                    if (threadIdx.x == 0) gslot[j] = op.slot;   // the fold's accumulator slot
                     ++j;
                 }
                 if (active) diag_apply2<C, R, true>(p, l, M, idx);
