@@ -351,6 +351,68 @@ static void group_span(const tcng_state* st, const std::vector<int>& items, void
 
 // Group Pauli terms into tile passes: a term joins a pass if its X bits above
 // the contiguous low bits fit the pass's gather set.
+// The complex64 expectation kernel's tile bits have roles: 1..5 pick the partner
+// lane, 6..9 the partner warp (a term whose lowest X bit there is carried by one
+// warp half per tile), 10..12 the partner register pair (the half form, half the
+// partner reads); a term with X only on lane bits reads every partner pair in every
+// warp.  The gathered qubits (tile bits chunk..12) are ordered so that the pass's
+// terms reach the cheapest form: the register bits take the gathered qubits with
+// the fewest X factors among the terms (the filler qubits, ideally), the warp bits
+// the qubits that cover the most remaining terms, the lane bits the rest.
+void order_expect_gather(const tcng_pauli* terms, const std::vector<int>& sel, int chunk, std::vector<int>& gq) {
+    const int G = (int)gq.size();
+    auto role = [&](int i) { const int b = chunk + i; return b >= 10 ? 2 : (b >= 6 ? 1 : 0); };
+    std::vector<int> xc(G, 0);
+    for (int t : sel)
+        for (int i = 0; i < G; ++i) xc[i] += (int)((terms[t].xmask >> gq[i]) & 1);
+    int want_reg = 0, want_warp = 0;
+    for (int i = 0; i < G; ++i) {
+        want_reg += role(i) == 2;
+        want_warp += role(i) == 1;
+    }
+    std::vector<char> used(G, 0);
+    std::vector<int> reg, warp, lane;
+    for (int k = 0; k < want_reg; ++k) {   // fewest X factors
+        int best = -1;
+        for (int i = 0; i < G; ++i)
+            if (!used[i] && (best < 0 || xc[i] < xc[best] || (xc[i] == xc[best] && gq[i] < gq[best]))) best = i;
+        used[best] = 1;
+        reg.push_back(gq[best]);
+    }
+    uint64_t regmask = 0;
+    for (int q : reg) regmask |= 1ULL << q;
+    std::vector<char> covered(sel.size(), 0);   // terms already in the half form or covered by a warp bit
+    for (size_t k = 0; k < sel.size(); ++k)
+        if (terms[sel[k]].xmask & regmask) covered[k] = 1;
+    for (int k = 0; k < want_warp; ++k) {   // greedy cover of the remaining X terms
+        int best = -1, bestc = -1;
+        for (int i = 0; i < G; ++i) {
+            if (used[i]) continue;
+            int c = 0;
+            for (size_t j = 0; j < sel.size(); ++j)
+                c += !covered[j] && ((terms[sel[j]].xmask >> gq[i]) & 1);
+            if (c > bestc || (c == bestc && gq[i] < gq[best])) {
+                best = i;
+                bestc = c;
+            }
+        }
+        used[best] = 1;
+        warp.push_back(gq[best]);
+        for (size_t j = 0; j < sel.size(); ++j)
+            if ((terms[sel[j]].xmask >> gq[best]) & 1) covered[j] = 1;
+    }
+    for (int i = 0; i < G; ++i)
+        if (!used[i]) lane.push_back(gq[i]);
+    std::sort(reg.begin(), reg.end());
+    std::sort(warp.begin(), warp.end());
+    std::sort(lane.begin(), lane.end());
+    std::vector<int> out;
+    size_t ir = 0, iw = 0, il = 0;
+    for (int i = 0; i < G; ++i)
+        out.push_back(role(i) == 2 ? reg[ir++] : role(i) == 1 ? warp[iw++] : lane[il++]);
+    gq.swap(out);
+}
+
 void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
                       std::vector<DevPass>& passes, std::vector<ExpPass>& eps, std::vector<size_t>* wide) {
     const uint64_t lim = (n >= 64) ? ~0ULL : ((1ULL << n) - 1);
@@ -423,19 +485,25 @@ void plan_expectation(int n, int m, int low, const tcng_pauli* terms, size_t T,
         }
         DevPass dp{};
         dp.m = __builtin_popcountll(S);
-        int tb[64];
-        int i = 0;
-        for (int q = 0; q < 64; ++q) tb[q] = ((S >> q) & 1) ? i++ : -1;
         int L = 0;
         while (L < n && ((S >> L) & 1)) ++L;
         dp.chunk = std::min(L, dp.m);
         dp.ngather = dp.m - dp.chunk;
-        int gi = 0, ri = 0;
+        std::vector<int> gq;   // gathered qubits, in the order of their tile bits
+        int ri = 0;
         for (int q = dp.chunk; q < n; ++q) {
-            if ((S >> q) & 1) dp.gather[gi++] = (uint8_t)q;
+            if ((S >> q) & 1) gq.push_back(q);
             else dp.rest[ri++] = (uint8_t)q;
         }
         dp.nrest = ri;
+        if (dp.m == 13 && dp.chunk <= 6) order_expect_gather(terms, sel, dp.chunk, gq);
+        int tb[64];
+        for (int q = 0; q < 64; ++q) tb[q] = -1;
+        for (int q = 0; q < dp.chunk; ++q) tb[q] = q;
+        for (size_t g = 0; g < gq.size(); ++g) {
+            dp.gather[g] = (uint8_t)gq[g];
+            tb[gq[g]] = dp.chunk + (int)g;
+        }
         for (int t : sel) {
             ExpTerm et{};
             const uint64_t xm = terms[t].xmask, zm = terms[t].zmask;

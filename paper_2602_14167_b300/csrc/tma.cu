@@ -39,6 +39,10 @@ TmaTile make_tma_tile(void* base, int n, int elem_bytes, const DevPass& p, int i
     auto fn = encode_fn();
     if (!fn) return t;
     // membership of each index bit in the tile
+    // the tensor map lays the tile out in ascending global bit order: a pass whose
+    // gathered qubits take their tile bits in another order has no tile map
+    for (int i = 1; i < p.ngather; ++i)
+        if (p.gather[i] <= p.gather[i - 1]) return TmaTile{};
     std::vector<int> in_tile(n, 0);
     for (int q = 0; q < p.chunk; ++q) in_tile[q] = 1;
     for (int i = 0; i < p.ngather; ++i) in_tile[p.gather[i]] = 1;
