@@ -378,17 +378,21 @@ void order_expect_gather(const tcng_pauli* terms, const std::vector<int>& sel, i
     }
     long best = -1;
     uint32_t best_reg = 0, best_warp = 0;
-    for (uint32_t rg = 0; rg < (1u << G); ++rg) {
+    const uint32_t all = (1u << G) - 1;
+    for (uint32_t rg = 0; rg <= all; ++rg) {
         if (__builtin_popcount(rg) != want_reg) continue;
-        for (uint32_t wp = 0; wp < (1u << G); ++wp) {
-            if ((wp & rg) || __builtin_popcount(wp) != want_warp) continue;
-            long c = 0;
-            for (uint32_t b : tx) c += (b & rg) ? 49 : ((b & wp) ? 39 : 69);
-            if (best < 0 || c < best) {
-                best = c;
-                best_reg = rg;
-                best_warp = wp;
+        const uint32_t rest = all & ~rg;
+        for (uint32_t wp = rest;; wp = (wp - 1) & rest) {   // the subsets of the rest
+            if (__builtin_popcount(wp) == want_warp) {
+                long c = 0;
+                for (uint32_t b : tx) c += (b & rg) ? 49 : ((b & wp) ? 39 : 69);
+                if (best < 0 || c < best) {
+                    best = c;
+                    best_reg = rg;
+                    best_warp = wp;
+                }
             }
+            if (!wp) break;
         }
     }
     std::vector<int> reg, warp, lane;
