@@ -491,6 +491,36 @@ def plan_stages(n, gates, pool):
     return int(f["passes"]), int(f["stages"])
 
 
+def su4_ladder_bench(args, dev, dist, world, res):
+    """Energy + full gradient of the 32-qubit SU(4)-ladder TFIM VQE (L = 16, 7440
+    parameters) on one GPU by the state-pass adjoint (Sec. VI.B)."""
+    import torch
+    from paper_2602_14167_b300 import StateBatch
+    from paper_2602_14167_b300 import tcng as T
+    n, L = 32, 16
+    c = gen.su4_ladder(n, L)
+    g, p = c.to_ir()
+    th = torch.tensor(gen.random_thetas(c.n_params, seed=7).reshape(1, -1), device=dev)
+    terms = gen.tfim_terms(n, 1.0, 1.0)
+    st = StateBatch(n, dtype="c64", device=dev)
+    en = torch.empty(1, dtype=torch.float64, device=dev)
+    gr = torch.empty((1, c.n_params), dtype=torch.float64, device=dev)
+
+    def su4_step():
+        T.tcng_energy_grad(st.handle, g, p, th, c.n_params, terms, None, en, gr)
+
+    ms = timed(su4_step, 1, 1, dist, dev)
+    res[f"su4_ladder_vqe_n{n}_L{L}"] = {
+        "s_per_energy_and_gradient": ms * 1e-3, "params": c.n_params, "su4_blocks": L * (n - 1),
+        "hbm_bytes_reverse_per_block": 4 * 8 * (1 << n),
+        "reverse_gbs": L * (n - 1) * 4 * 8 * (1 << n) / (ms * 1e-3) / 1e9,
+        "energy": float(en[0]), "grad_norm": float(torch.linalg.vector_norm(gr)),
+        "paper_context": "17.86 s per gradient step on one H200 (tensor-network contraction, Sec. VI.B)"}
+    st.free()
+    del st
+    torch.cuda.empty_cache()
+
+
 def apps_bench(args, dev, dist, world):
     """The paper's batched applications on the same kernels (Sec. VII):
     QML forward batches (12 q x 30 SU(4) brickwall layers x 5000 inputs; 10 q x 40
@@ -503,6 +533,9 @@ def apps_bench(args, dev, dist, world):
     from paper_2602_14167_b300.trajectories import MIPTBatch, shadow_snapshots
 
     res = {}
+    if args.apps_subset == "su4":   # profiling: the state-pass adjoint only
+        su4_ladder_bench(args, dev, dist, world, res)
+        return res
     tf32, tf32_kind = tf32_peak()
     hbm, hbm_kind = peaks()
     for (n, L, B) in ((12, 30, 5000), (10, 40, 15000)):
@@ -572,30 +605,7 @@ def apps_bench(args, dev, dist, world):
     del pools, masks, u, mb
     torch.cuda.empty_cache()
 
-    # NEXT-1: energy + full gradient of the 32-qubit SU(4)-ladder TFIM VQE (L = 16,
-    # 7440 parameters) on one GPU by the state-pass adjoint
-    n, L = 32, 16
-    c = gen.su4_ladder(n, L)
-    g, p = c.to_ir()
-    th = torch.tensor(gen.random_thetas(c.n_params, seed=7).reshape(1, -1), device=dev)
-    terms = gen.tfim_terms(n, 1.0, 1.0)
-    st = StateBatch(n, dtype="c64", device=dev)
-    en = torch.empty(1, dtype=torch.float64, device=dev)
-    gr = torch.empty((1, c.n_params), dtype=torch.float64, device=dev)
-
-    def su4_step():
-        T.tcng_energy_grad(st.handle, g, p, th, c.n_params, terms, None, en, gr)
-
-    ms = timed(su4_step, 1, 1, dist, dev)
-    res[f"su4_ladder_vqe_n{n}_L{L}"] = {
-        "s_per_energy_and_gradient": ms * 1e-3, "params": c.n_params, "su4_blocks": L * (n - 1),
-        "hbm_bytes_reverse_per_block": 4 * 8 * (1 << n),
-        "reverse_gbs": L * (n - 1) * 4 * 8 * (1 << n) / (ms * 1e-3) / 1e9,
-        "energy": float(en[0]), "grad_norm": float(torch.linalg.vector_norm(gr)),
-        "paper_context": "17.86 s per gradient step on one H200 (tensor-network contraction, Sec. VI.B)"}
-    st.free()
-    del st
-    torch.cuda.empty_cache()
+    su4_ladder_bench(args, dev, dist, world, res)
 
     # classical-shadow snapshots
     n, S = 20, 256
@@ -756,7 +766,7 @@ def main():
                     help="skip the FMA peaks, config 2, unfused and shared-unitary measurements")
     ap.add_argument("--paths-only", action="store_true", help="only those measurements")
     ap.add_argument("--no-autotune", action="store_true", help="library default options, no autotuner run")
-    ap.add_argument("--apps-subset", default="", help="qml: only the QML batches of the apps (profiling)")
+    ap.add_argument("--apps-subset", default="", help="qml | su4: only the QML batches or the SU(4)-ladder gradient (profiling)")
     ap.add_argument("--fuse-width", type=int, default=0, help="override the fusion width (tuning)")
     ap.add_argument("--tile-bits", type=int, default=0, help="override the tile bits (tuning)")
     ap.add_argument("--chunk-bits", type=int, default=0, help="override the chunk bits (tuning)")

@@ -22,8 +22,10 @@
 // instead of fifteen.
 //
 // Per block: 2 states read and written once (HBM-bound, 4 x state bytes);
-// per-thread N partials in FP32 folded into FP64 every 64 classes, then a
-// fixed-order reduction (bitwise reproducible).  The forward runs on the
+// per-thread N partials in FP32, every 64 classes summed over the warp by a
+// fixed shuffle tree into the warp's FP64 sums in shared memory (105 registers
+// for complex64 with two qubits: two CTAs per SM), then a fixed-order reduction
+// over warps and CTAs (bitwise reproducible).  The forward runs on the
 // ordinary tile passes; lambda = H psi on the Pauli-sum kernel.
 #include <cuda_runtime.h>
 
@@ -73,12 +75,27 @@ __global__ void __launch_bounds__(kSaThreads) sa_block_kernel(C* __restrict__ ps
     long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long x0 = sa_pdep((unsigned long long)j, fm);
     const unsigned long long step = sa_pdep((unsigned long long)stride, fm);
+    // N partials: per thread in FP32, every 64 classes summed over the warp (fixed
+    // shuffle tree) into the warp's FP64 sums in shared memory (few registers, so
+    // more warps per SM hide the streaming latency)
     R nacc[GRAD ? 2 * D * D : 1];
-    double nd[GRAD ? 2 * D * D : 1];
+    __shared__ double wacc[kSaThreads / 32][2 * 16];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (GRAD) {
 #pragma unroll
-        for (int i = 0; i < 2 * D * D; ++i) nacc[i] = 0, nd[i] = 0.0;
+        for (int i = 0; i < 2 * D * D; ++i) nacc[i] = 0;
+        if (lane < 2 * D * D) wacc[warp][lane] = 0.0;
     }
+    auto fold = [&]() {
+#pragma unroll
+        for (int i = 0; i < 2 * D * D; ++i) {
+            R v = nacc[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) wacc[warp][i] += (double)v;
+            nacc[i] = 0;
+        }
+    };
     int cnt = 0;
     for (; j < classes; j += stride) {
         C a[D], b[D], y[D], z[D];
@@ -118,12 +135,8 @@ __global__ void __launch_bounds__(kSaThreads) sa_block_kernel(C* __restrict__ ps
                     nacc[2 * (l * D + m)] += y[l].x * b[m].x + y[l].y * b[m].y;
                     nacc[2 * (l * D + m) + 1] += y[l].y * b[m].x - y[l].x * b[m].y;
                 }
-            if (++cnt == 64) {
-#pragma unroll
-                for (int i = 0; i < 2 * D * D; ++i) {
-                    nd[i] += (double)nacc[i];
-                    nacc[i] = 0;
-                }
+            if (++cnt == 64) {   // warp-uniform: every lane of a warp runs the same number of classes
+                fold();
                 cnt = 0;
             }
         }
@@ -135,19 +148,11 @@ __global__ void __launch_bounds__(kSaThreads) sa_block_kernel(C* __restrict__ ps
         x0 = ((x0 | ~fm) + step) & fm;
     }
     if (!GRAD) return;
-    __shared__ double red[kSaThreads / 32][2 * 16];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < 2 * D * D; ++i) {
-        double v = nd[i] + (double)nacc[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][i] = v;
-    }
+    fold();
     __syncthreads();
     if (threadIdx.x < 2 * D * D) {
         double s = 0.0;
-        for (int w = 0; w < kSaThreads / 32; ++w) s += red[w][threadIdx.x];
+        for (int w = 0; w < kSaThreads / 32; ++w) s += wacc[w][threadIdx.x];
         npart[(long long)blockIdx.x * 32 + threadIdx.x] = s;
     }
 }
