@@ -510,10 +510,29 @@ def su4_ladder_bench(args, dev, dist, world, res):
         T.tcng_energy_grad(st.handle, g, p, th, c.n_params, terms, None, en, gr)
 
     ms = timed(su4_step, 1, 1, dist, dev)
+    # one more call with per-kernel CUDA events: the phases and the reverse sweep's roofline
+    T.tcng_profile_read(reset=True)
+    T.tcng_profile_enable(True)
+    su4_step()
+    torch.cuda.synchronize()
+    T.tcng_profile_enable(False)
+    prof = T.tcng_profile_read(reset=True)
+    segs, seg_ms = prof.get("sa_seg_kernel", (0, 0.0))
+    blocks = L * (n - 1)
+    # per class of 4 amplitudes: U^dagger on psi and on lambda (16 complex MACs
+    # each) and the 16 complex products of M: 192 FMAs = 384 flop
+    flop = blocks * (1 << (n - 2)) * 384
+    fp32 = T.tcng_fma_peak(False)
+    ach = flop / (seg_ms * 1e-3) / 1e12 if seg_ms else None
     res[f"su4_ladder_vqe_n{n}_L{L}"] = {
-        "s_per_energy_and_gradient": ms * 1e-3, "params": c.n_params, "su4_blocks": L * (n - 1),
-        "hbm_bytes_reverse_per_block": 4 * 8 * (1 << n),
-        "reverse_gbs": L * (n - 1) * 4 * 8 * (1 << n) / (ms * 1e-3) / 1e9,
+        "s_per_energy_and_gradient": ms * 1e-3, "params": c.n_params, "su4_blocks": blocks,
+        "reverse_segments": segs, "blocks_per_segment": blocks / segs if segs else None,
+        "phase_s": {k: v[1] * 1e-3 for k, v in prof.items()},
+        "reverse_roofline": {"bound": "alu", "achieved": ach, "peak": fp32, "unit": "TFLOP/s",
+                             "frac": ach / fp32 if ach else None,
+                             "peak_kind": "measured FP32 FMA (tcng_fma_peak)",
+                             "algorithmic_tflop": flop / 1e12},
+        "reverse_hbm_gbs": segs * 4 * 8 * (1 << n) / (seg_ms * 1e-3) / 1e9 if seg_ms else None,
         "energy": float(en[0]), "grad_norm": float(torch.linalg.vector_norm(gr)),
         "paper_context": "17.86 s per gradient step on one H200 (tensor-network contraction, Sec. VI.B)"}
     st.free()

@@ -8,7 +8,7 @@
 // circuit backwards block by block, keeping two states.  Gates are fused into
 // blocks of at most two qubits whatever their parameters (all 15 rotations of
 // an su4 gate form one block).  For a block B (matrix U_B = M_m ... M_1 over its
-// ops, in the block's ascending-qubit local order) one pass over both states:
+// ops, in the block's ascending-qubit local order), over both states:
 //     psi_in = U_B^dagger psi_out,
 //     N_B[a][b] = sum over the other qubits of psi_in(a) conj(lambda_out(b)),
 //     lambda_in = U_B^dagger lambda_out,
@@ -21,12 +21,22 @@
 // su4 block cost one pass over the two states (one 4 x 4 cross-density matrix)
 // instead of fifteen.
 //
-// Per block: 2 states read and written once (HBM-bound, 4 x state bytes);
-// per-thread N partials in FP32, every 64 classes summed over the warp by a
-// fixed shuffle tree into the warp's FP64 sums in shared memory (105 registers
-// for complex64 with two qubits: two CTAs per SM), then a fixed-order reduction
-// over warps and CTAs (bitwise reproducible).  The forward runs on the
-// ordinary tile passes; lambda = H psi on the Pauli-sum kernel.
+// Blocks of at most two qubits run in fused segments: consecutive blocks (last
+// first) whose qubits, with the lowest qubits (32-byte pieces in memory), fit in
+// a tile of 2^12 (complex64) or 2^11 (complex128) amplitudes.  Each CTA holds a
+// tile of psi and of lambda in shared memory, applies the segment's blocks one
+// after the other (a CTA barrier between blocks) and writes the tile back, so a
+// segment costs one read and one write of the two states (the SU(4) ladder: about
+// ten blocks per segment instead of one pass per block).  The kernels sum the
+// block's outputs, M[c][b] = sum psi_out(c) conj(lambda_out(b)), and the gradient
+// kernel forms N_B = U_B^dagger M in FP64 (the same 192 FMAs per class of four
+// amplitudes, fewer live registers).  M partials: per thread in FP32 over its
+// classes of the tile, summed over the warp by a transposing shuffle tree (lane
+// i ends with element i), added to the warp's FP32 row in shared memory and
+// folded into FP64 every 16 tiles; CTA partials, then a fixed-order reduction
+// (bitwise reproducible).  Blocks of 3..5 qubits (no parameter) end a segment
+// and run on their own.  The forward runs on the ordinary tile passes; lambda =
+// H psi on tile passes of its own (below).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -54,106 +64,344 @@ __device__ __forceinline__ unsigned long long sa_pdep(unsigned long long v, unsi
     return r;
 }
 
-// One reverse block step over all 2^(n-K) index classes (grid-stride).
-template <typename C, int K, bool GRAD>
-__global__ void __launch_bounds__(kSaThreads) sa_block_kernel(C* __restrict__ psi, C* __restrict__ lam,
-                                                              const C* __restrict__ U, int diag,
-                                                              unsigned long long qmask, int n,
-                                                              double* __restrict__ npart) {
+// ---- fused segments: runs of consecutive blocks (reverse order) on one tile ----
+//
+// A segment is a run of blocks of at most two qubits whose qubits, together with
+// the lowest qubits (contiguous 32-byte pieces in memory), fit in TB tile bits.
+// Each CTA loads a tile of psi and of lambda (the segment's qubits free, all other
+// qubits fixed) into shared memory once, applies every block of the run to both
+// (with its N partials), and writes the tile back: one pass over the two states
+// per segment instead of one per block.
+constexpr int kSegMax = 16;      // blocks per segment
+constexpr int kSegThreads = 256; // complex64: two CTAs per SM (shared memory and registers)
+constexpr int kSegFold = 16;     // tiles between folds of the FP32 warp sums into FP64
+
+struct SaSegBlk {
+    int tb0, tb1;   // tile bits of the block's qubits (ascending; tb1 = -1 for one qubit)
+    int k, diag;
+    int grad;       // gradient-block index, -1 none
+    int out_off;    // matrix offset in the block table
+};
+struct SaSeg {
+    unsigned long long tmask;   // qubits of the tile
+    int tbits, nblk;
+    SaSegBlk b[kSegMax];
+};
+
+template <typename C, int TB>
+constexpr size_t sa_seg_smem() {
+    using R = typename Real<C>::T;
+    return 2 * sizeof(C) * (size_t(1) << TB) + sizeof(C) * kSegMax * 16 + 128 * sizeof(unsigned long long) +
+           sizeof(R) * (kSegThreads / 32) * kSegMax * 32 + sizeof(double) * kSegMax * 32;
+}
+
+__device__ __forceinline__ float sa_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double sa_fma(double a, double b, double c) { return fma(a, b, c); }
+
+__device__ __forceinline__ int sa_ins0(int j, int b) { return ((j >> b) << (b + 1)) | (j & ((1 << b) - 1)); }
+
+// v[0..V) per lane; afterwards, for V = 32, lane l holds the warp total of
+// element l in v[0]; for V = 8 the four lanes 4e..4e+3 hold that of element e.
+template <typename R, int V>
+__device__ __forceinline__ void sa_warp_transpose_sum(R (&v)[32], int lane) {
+#pragma unroll
+    for (int h = V / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = lane & o;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const R keep = up ? v[i + h] : v[i];
+            const R send = up ? v[i] : v[i + h];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    if (V == 8) {
+#pragma unroll
+        for (int o = 2; o >= 1; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    }
+}
+
+// One block of K qubits over the tile: psi, lambda <- U^dagger (psi, lambda)
+// and, for a gradient block, the warp's partials of M[l][m] = sum psi_out(l)
+// conj(lambda_out(m)) (the block's outputs, before U^dagger) added to wr (this
+// warp's row).  Every product is one fused multiply-add on a running sum.
+template <typename C, int K>
+__device__ __forceinline__ void sa_seg_block(C* __restrict__ sp, C* __restrict__ sl, const C* __restrict__ su,
+                                             const SaSegBlk& bk, int E, typename Real<C>::T* __restrict__ wr) {
     using R = typename Real<C>::T;
     constexpr int D = 1 << K;
-    __shared__ C su[D * D];
-    for (int i = threadIdx.x; i < (diag ? D : D * D); i += blockDim.x) su[i] = U[i];
-    __syncthreads();
-    const unsigned long long all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
-    const unsigned long long fm = all & ~qmask;
-    long long off[D];
+    const int lane = threadIdx.x & 31;
+    const bool diag = bk.diag, grad = bk.grad >= 0;
+    C u[D * D];
+    if (diag) {
 #pragma unroll
-    for (int l = 0; l < D; ++l) off[l] = (long long)sa_pdep((unsigned long long)l, qmask);
-    const long long classes = 1ll << (n - K);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long x0 = sa_pdep((unsigned long long)j, fm);
-    const unsigned long long step = sa_pdep((unsigned long long)stride, fm);
-    // N partials: per thread in FP32, every 64 classes summed over the warp (fixed
-    // shuffle tree) into the warp's FP64 sums in shared memory (few registers, so
-    // more warps per SM hide the streaming latency)
-    R nacc[GRAD ? 2 * D * D : 1];
-    __shared__ double wacc[kSaThreads / 32][2 * 16];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (GRAD) {
+        for (int l = 0; l < D; ++l) u[l] = su[l];
+    } else {
 #pragma unroll
-        for (int i = 0; i < 2 * D * D; ++i) nacc[i] = 0;
-        if (lane < 2 * D * D) wacc[warp][lane] = 0.0;
+        for (int i = 0; i < D * D; ++i) u[i] = su[i];
     }
-    auto fold = [&]() {
+    int off[D];
 #pragma unroll
-        for (int i = 0; i < 2 * D * D; ++i) {
-            R v = nacc[i];
+    for (int l = 0; l < D; ++l) off[l] = ((l & 1) ? (1 << bk.tb0) : 0) | ((K == 2 && (l & 2)) ? (1 << bk.tb1) : 0);
+    R macc[32];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) wacc[warp][i] += (double)v;
-            nacc[i] = 0;
-        }
-    };
-    int cnt = 0;
-    for (; j < classes; j += stride) {
-        C a[D], b[D], y[D], z[D];
+    for (int i = 0; i < 32; ++i) macc[i] = 0;
+    const int classes = E >> K;
+    for (int j = threadIdx.x; j < classes; j += kSegThreads) {
+        int p = sa_ins0(j, bk.tb0);
+        if (K == 2) p = sa_ins0(p, bk.tb1);
+        C a[D], b[D];
 #pragma unroll
         for (int l = 0; l < D; ++l) {
-            a[l] = psi[x0 | off[l]];
-            b[l] = lam[x0 | off[l]];
+            a[l] = sp[p | off[l]];
+            b[l] = sl[p | off[l]];
         }
-        if (diag) {
-#pragma unroll
-            for (int l = 0; l < D; ++l) {   // conj(u) * v
-                const C u = su[l];
-                y[l] = cmk<C>(u.x * a[l].x + u.y * a[l].y, u.x * a[l].y - u.y * a[l].x);
-                z[l] = cmk<C>(u.x * b[l].x + u.y * b[l].y, u.x * b[l].y - u.y * b[l].x);
-            }
-        } else {
-#pragma unroll
-            for (int l = 0; l < D; ++l) {   // y_l = sum_m conj(U[m][l]) a_m
-                R yr = 0, yi = 0, zr = 0, zi = 0;
-#pragma unroll
-                for (int m = 0; m < D; ++m) {
-                    const C u = su[m * D + l];
-                    yr += u.x * a[m].x + u.y * a[m].y;
-                    yi += u.x * a[m].y - u.y * a[m].x;
-                    zr += u.x * b[m].x + u.y * b[m].y;
-                    zi += u.x * b[m].y - u.y * b[m].x;
-                }
-                y[l] = cmk<C>(yr, yi);
-                z[l] = cmk<C>(zr, zi);
-            }
-        }
-        if (GRAD) {   // N[l][m] += psi_in(l) conj(lambda_out(m))
+        if (grad) {   // M[l][m] += a_l conj(b_m)
 #pragma unroll
             for (int l = 0; l < D; ++l)
 #pragma unroll
                 for (int m = 0; m < D; ++m) {
-                    nacc[2 * (l * D + m)] += y[l].x * b[m].x + y[l].y * b[m].y;
-                    nacc[2 * (l * D + m) + 1] += y[l].y * b[m].x - y[l].x * b[m].y;
+                    R& mr = macc[2 * (l * D + m)];
+                    R& mi = macc[2 * (l * D + m) + 1];
+                    mr = sa_fma(a[l].y, b[m].y, sa_fma(a[l].x, b[m].x, mr));
+                    mi = sa_fma(-a[l].x, b[m].y, sa_fma(a[l].y, b[m].x, mi));
                 }
-            if (++cnt == 64) {   // warp-uniform: every lane of a warp runs the same number of classes
-                fold();
-                cnt = 0;
+        }
+#pragma unroll
+        for (int l = 0; l < D; ++l) {   // y_l = sum_m conj(U[m][l]) a_m (diagonal: conj(u_l) a_l)
+            R yr = 0, yi = 0, zr = 0, zi = 0;
+#pragma unroll
+            for (int m = 0; m < D; ++m) {
+                if (diag && m != l) continue;
+                const C w = diag ? u[l] : u[m * D + l];
+                yr = sa_fma(w.y, a[m].y, sa_fma(w.x, a[m].x, yr));
+                yi = sa_fma(-w.y, a[m].x, sa_fma(w.x, a[m].y, yi));
+                zr = sa_fma(w.y, b[m].y, sa_fma(w.x, b[m].x, zr));
+                zi = sa_fma(-w.y, b[m].x, sa_fma(w.x, b[m].y, zi));
+            }
+            sp[p | off[l]] = cmk<C>(yr, yi);
+            sl[p | off[l]] = cmk<C>(zr, zi);
+        }
+    }
+    if (grad) {   // block-uniform branch: every lane of every warp takes it
+        sa_warp_transpose_sum<R, 2 * D * D>(macc, lane);
+        if (K == 2)
+            wr[lane] += macc[0];
+        else if ((lane & 3) == 0)
+            wr[lane >> 2] += macc[0];
+    }
+}
+
+template <typename C, int TB>
+__global__ void __launch_bounds__(kSegThreads, sizeof(C) == 8 ? 2 : 1)
+    sa_seg_kernel(C* __restrict__ psi, C* __restrict__ lam, const C* __restrict__ table,
+                  const __grid_constant__ SaSeg seg, int n, double* __restrict__ npart) {
+    using R = typename Real<C>::T;
+    constexpr int W = kSegThreads / 32;
+    extern __shared__ __align__(16) unsigned char sa_smem[];
+    C* sp = reinterpret_cast<C*>(sa_smem);
+    C* sl = sp + (1 << TB);
+    C* su = sl + (1 << TB);
+    unsigned long long* dep = reinterpret_cast<unsigned long long*>(su + kSegMax * 16);   // [2][64]
+    R* wr = reinterpret_cast<R*>(dep + 128);                                               // [W][kSegMax][32]
+    double* w64 = reinterpret_cast<double*>(wr + W * kSegMax * 32);                        // [kSegMax][32]
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int nb = seg.nblk;
+    for (int i = tid; i < nb * 16; i += kSegThreads) {
+        const SaSegBlk& bk = seg.b[i >> 4];
+        const int e = i & 15, d = 1 << bk.k;
+        if (e < (bk.diag ? d : d * d)) su[i] = table[bk.out_off + e];
+    }
+    if (tid < 128) {   // tile position bits 0..5 (dep[0..63]) and 6..11 (dep[64..127]) -> qubit bits
+        const int lo = (tid >> 6) * 6, v = tid & 63;
+        unsigned long long g = 0;
+        for (int b = 0, c = 0; b < 64; ++b) {
+            if (!((seg.tmask >> b) & 1)) continue;
+            if (c >= lo && c < lo + 6 && ((v >> (c - lo)) & 1)) g |= 1ull << b;
+            ++c;
+        }
+        dep[tid] = g;
+    }
+    for (int i = tid; i < W * kSegMax * 32; i += kSegThreads) wr[i] = 0;
+    for (int i = tid; i < kSegMax * 32; i += kSegThreads) w64[i] = 0.0;
+    __syncthreads();
+    auto fold = [&]() {
+        for (int i = tid; i < nb * 32; i += kSegThreads) {
+            R s = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                s += wr[w * kSegMax * 32 + i];
+                wr[w * kSegMax * 32 + i] = 0;
+            }
+            w64[i] += (double)s;
+        }
+    };
+    const unsigned long long all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+    const unsigned long long fm = all & ~seg.tmask;
+    const long long ntiles = 1ll << (n - seg.tbits);
+    const int E = 1 << seg.tbits;
+    constexpr int PW = 16 / sizeof(C);   // amplitudes per 16-byte piece (tile bit 0 is qubit 0)
+    unsigned long long base = sa_pdep((unsigned long long)blockIdx.x, fm);
+    const unsigned long long step = sa_pdep((unsigned long long)gridDim.x, fm);
+    int since = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        for (int q = tid; q < E / PW; q += kSegThreads) {
+            const int pos = q * PW;
+            const unsigned long long g = base | dep[pos & 63] | dep[64 + (pos >> 6)];
+            *reinterpret_cast<float4*>(sp + pos) = __ldcs(reinterpret_cast<const float4*>(psi + g));
+            *reinterpret_cast<float4*>(sl + pos) = __ldcs(reinterpret_cast<const float4*>(lam + g));
+        }
+        __syncthreads();
+        for (int bi = 0; bi < nb; ++bi) {
+            const SaSegBlk& bk = seg.b[bi];
+            R* w = wr + (warp * kSegMax + bi) * 32;
+            if (bk.k == 2)
+                sa_seg_block<C, 2>(sp, sl, su + bi * 16, bk, E, w);
+            else
+                sa_seg_block<C, 1>(sp, sl, su + bi * 16, bk, E, w);
+            __syncthreads();
+        }
+        for (int q = tid; q < E / PW; q += kSegThreads) {
+            const int pos = q * PW;
+            const unsigned long long g = base | dep[pos & 63] | dep[64 + (pos >> 6)];
+            __stcs(reinterpret_cast<float4*>(psi + g), *reinterpret_cast<const float4*>(sp + pos));
+            __stcs(reinterpret_cast<float4*>(lam + g), *reinterpret_cast<const float4*>(sl + pos));
+        }
+        if (++since == kSegFold) {   // CTA-uniform
+            fold();
+            since = 0;
+        }
+        base = ((base | ~fm) + step) & fm;
+        __syncthreads();
+    }
+    fold();
+    __syncthreads();
+    for (int i = tid; i < nb * 32; i += kSegThreads) {
+        const int g = seg.b[i >> 5].grad;
+        if (g >= 0) npart[((long long)g * gridDim.x + blockIdx.x) * 32 + (i & 31)] = w64[i];
+    }
+}
+
+// ---- lambda = H psi in tile passes ----
+//
+// (H psi)(y) = sum_t c_t i^{ny_t} (-1)^{popc((y ^ x_t) & z_t)} psi(y ^ x_t).  The
+// terms are grouped into passes whose X masks, with the lowest qubits, fit in
+// a tile of 2^12 (complex64) / 2^11 (complex128) amplitudes; a pass loads each
+// psi tile into shared memory once, takes every partner psi(y ^ x_t) from it and
+// writes (first pass) or adds to lambda.  The Z sign splits into the tile part,
+// popc(pos & z_t (tile bits)), and the tile's fixed part; diagonal terms (x_t =
+// 0) sum into one real factor per amplitude.
+constexpr int kHamMax = 64;      // terms per pass
+constexpr int kHamThreads = 256;
+struct SaHamPass {
+    unsigned long long tmask;
+    int tbits, nt, ndiag, first;   // terms [0, ndiag) are diagonal
+    int idx[kHamMax];              // term index
+    int xt[kHamMax], zt[kHamMax];  // X and Z masks in tile bits
+};
+
+template <typename C, int TB>
+constexpr size_t sa_ham_smem() {
+    using R = typename Real<C>::T;
+    return sizeof(C) * (size_t(1) << TB) + 128 * sizeof(unsigned long long) + kHamMax * sizeof(unsigned long long) +
+           2 * kHamMax * sizeof(R) + 3 * kHamMax * sizeof(int);
+}
+
+template <typename C, int TB>
+__global__ void __launch_bounds__(kHamThreads)
+    sa_ham_tile_kernel(const C* __restrict__ psi, C* __restrict__ lam, const HTerm* __restrict__ terms,
+                       const double* __restrict__ coeffs, const double* __restrict__ term_coeff,
+                       const __grid_constant__ SaHamPass hp, int n) {
+    using R = typename Real<C>::T;
+    constexpr int EPT = (1 << TB) / kHamThreads;   // amplitudes per thread
+    extern __shared__ __align__(16) unsigned char sh_smem[];
+    C* sp = reinterpret_cast<C*>(sh_smem);
+    unsigned long long* dep = reinterpret_cast<unsigned long long*>(sp + (1 << TB));   // [128]
+    unsigned long long* zout = dep + 128;   // Z mask outside the tile
+    R* cre = reinterpret_cast<R*>(zout + kHamMax);
+    R* cim = cre + kHamMax;
+    int* xt = reinterpret_cast<int*>(cim + kHamMax);
+    int* zt = xt + kHamMax;
+    int* pb = zt + kHamMax;   // per tile: popc(base & z_t) & 1
+    const int tid = threadIdx.x, nt = hp.nt;
+    if (tid < nt) {   // c_t i^{ny} (-1)^{popc(x_t & z_t)} as (re, im)
+        const HTerm h = terms[hp.idx[tid]];
+        const double c0 = coeffs ? coeffs[hp.idx[tid]] : term_coeff[hp.idx[tid]];
+        const double c = (__popcll(h.xm & h.zm) & 1) ? -c0 : c0;
+        const int ny = h.ny & 3;
+        cre[tid] = (R)(ny == 0 ? c : (ny == 2 ? -c : 0.0));
+        cim[tid] = (R)(ny == 1 ? c : (ny == 3 ? -c : 0.0));
+        xt[tid] = hp.xt[tid];
+        zt[tid] = hp.zt[tid];
+        zout[tid] = h.zm & ~hp.tmask;
+    }
+    if (tid < 128) {   // tile position bits 0..5 (dep[0..63]) and 6..11 (dep[64..127]) -> qubit bits
+        const int lo = (tid >> 6) * 6, v = tid & 63;
+        unsigned long long g = 0;
+        for (int b = 0, c = 0; b < 64; ++b) {
+            if (!((hp.tmask >> b) & 1)) continue;
+            if (c >= lo && c < lo + 6 && ((v >> (c - lo)) & 1)) g |= 1ull << b;
+            ++c;
+        }
+        dep[tid] = g;
+    }
+    __syncthreads();
+    const unsigned long long all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+    const unsigned long long fm = all & ~hp.tmask;
+    const long long ntiles = 1ll << (n - hp.tbits);
+    const int E = 1 << hp.tbits;
+    constexpr int PW = 16 / sizeof(C);
+    unsigned long long base = sa_pdep((unsigned long long)blockIdx.x, fm);
+    const unsigned long long step = sa_pdep((unsigned long long)gridDim.x, fm);
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        for (int q = tid; q < E / PW; q += kHamThreads) {
+            const int pos = q * PW;
+            const unsigned long long g = base | dep[pos & 63] | dep[64 + (pos >> 6)];
+            *reinterpret_cast<float4*>(sp + pos) = __ldcs(reinterpret_cast<const float4*>(psi + g));
+        }
+        if (tid < nt) pb[tid] = __popcll(base & zout[tid]) & 1;
+        __syncthreads();
+        R ar[EPT], ai[EPT], d[EPT];
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) ar[k] = ai[k] = d[k] = 0;
+        for (int i = 0; i < hp.ndiag; ++i) {   // real diagonal factor
+            const int z = zt[i];
+            const R c = pb[i] ? -cre[i] : cre[i];
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) {
+                const int pos = tid + k * kHamThreads;
+                d[k] += (__popc(pos & z) & 1) ? -c : c;
+            }
+        }
+        for (int i = hp.ndiag; i < nt; ++i) {
+            const int x = xt[i], z = zt[i];
+            const R sr = pb[i] ? -cre[i] : cre[i], si = pb[i] ? -cim[i] : cim[i];
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) {
+                const int pos = tid + k * kHamThreads;
+                if (pos >= E) break;
+                const C v = sp[pos ^ x];
+                const bool neg = __popc(pos & z) & 1;
+                const R cr = neg ? -sr : sr, ci = neg ? -si : si;
+                ar[k] = sa_fma(cr, v.x, sa_fma(-ci, v.y, ar[k]));
+                ai[k] = sa_fma(cr, v.y, sa_fma(ci, v.x, ai[k]));
             }
         }
 #pragma unroll
-        for (int l = 0; l < D; ++l) {
-            psi[x0 | off[l]] = y[l];
-            lam[x0 | off[l]] = z[l];
+        for (int k = 0; k < EPT; ++k) {
+            const int pos = tid + k * kHamThreads;
+            if (pos >= E) break;
+            const unsigned long long g = base | dep[pos & 63] | dep[64 + (pos >> 6)];
+            const C v = sp[pos];
+            R yr = sa_fma(d[k], v.x, ar[k]), yi = sa_fma(d[k], v.y, ai[k]);
+            if (!hp.first) {
+                const C o = lam[g];
+                yr += o.x;
+                yi += o.y;
+            }
+            lam[g] = cmk<C>(yr, yi);
         }
-        x0 = ((x0 | ~fm) + step) & fm;
-    }
-    if (!GRAD) return;
-    fold();
-    __syncthreads();
-    if (threadIdx.x < 2 * D * D) {
-        double s = 0.0;
-        for (int w = 0; w < kSaThreads / 32; ++w) s += wacc[w][threadIdx.x];
-        npart[(long long)blockIdx.x * 32 + threadIdx.x] = s;
+        base = ((base | ~fm) + step) & fm;
+        __syncthreads();
     }
 }
 
@@ -199,7 +447,7 @@ __global__ void __launch_bounds__(kSaThreads) sa_uncompute_kernel(C* __restrict_
     }
 }
 
-// N of every gradient block: the CTA partials summed in order.
+// M of every gradient block: the CTA partials summed in order.
 __global__ void sa_nfinal_kernel(const double* __restrict__ npart, int ncta, int nblocks, double* __restrict__ N) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nblocks * 32) return;
@@ -250,16 +498,18 @@ __device__ void sa_apply_op(double2* L, int D, const BuildOp& op, const double2*
         }
 }
 
-// contrib[e] = 2 scale Re Tr(D_j N) for parameterised op e.
+// contrib[e] = 2 scale Re Tr(D_j N) for parameterised op e, with the segment
+// kernels' M (outputs of the block: M[c][b] = sum psi_out(c) conj(lambda_out(b)))
+// and N = U_B^dagger M:  Tr(D_j N) = sum_{b,c} (D_j U_B^dagger)[b][c] M[c][b].
 __global__ void sa_grad_kernel(const SaEntry* __restrict__ ents, int n_ent, const BuildOp* __restrict__ bops,
                                const double2* __restrict__ pool, const double* __restrict__ params,
-                               const double* __restrict__ N, double* __restrict__ contrib) {
+                               const double* __restrict__ Mblk, double* __restrict__ contrib) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_ent) return;
     const SaEntry en = ents[e];
     const int D = 1 << en.k;
-    double2 L[16], M[16], Mp[16];
-    for (int i = 0; i < D * D; ++i) L[i] = make_double2((i / D) == (i % D) ? 1.0 : 0.0, 0.0);
+    double2 L[16], U[16], M[16], Mp[16];
+    for (int i = 0; i < D * D; ++i) L[i] = U[i] = make_double2((i / D) == (i % D) ? 1.0 : 0.0, 0.0);
     const double pi = 3.14159265358979323846;
     double scale = 1.0;
     for (int o = 0; o < en.op_count; ++o) {
@@ -267,6 +517,8 @@ __global__ void sa_grad_kernel(const SaEntry* __restrict__ ents, int n_ent, cons
         const int dk = 1 << op.k;
         double ang = op.angle0;
         if (op.param >= 0) ang += op.scale * params[op.param];
+        gate_matrix_d(op, ang, M, dk, pool);
+        sa_apply_op(U, D, op, M);
         if (o == en.j) {   // dM/dangle from two shifted evaluations
             scale = op.scale;
             const bool cp = op.code == TCNG_CP;
@@ -274,18 +526,20 @@ __global__ void sa_grad_kernel(const SaEntry* __restrict__ ents, int n_ent, cons
             gate_matrix_d(op, ang + h, M, dk, pool);
             gate_matrix_d(op, ang - h, Mp, dk, pool);
             for (int i = 0; i < dk * dk; ++i) M[i] = make_double2(f * (M[i].x - Mp[i].x), f * (M[i].y - Mp[i].y));
-        } else {
-            gate_matrix_d(op, ang, M, dk, pool);
         }
         sa_apply_op(L, D, op, M);
     }
-    // Tr(D N) = sum_{a,b} D[b][a] N[a][b]
-    const double* Nb = N + (long long)en.gblock * 32;
+    const double* Mb = Mblk + (long long)en.gblock * 32;
     double re = 0.0;
-    for (int a = 0; a < D; ++a)
-        for (int b = 0; b < D; ++b) {
-            const double2 d = L[b * D + a];
-            re += d.x * Nb[2 * (a * D + b)] - d.y * Nb[2 * (a * D + b) + 1];
+    for (int b = 0; b < D; ++b)
+        for (int c = 0; c < D; ++c) {
+            double pr = 0.0, pim = 0.0;   // (D U^dagger)[b][c] = sum_a D[b][a] conj(U[c][a])
+            for (int a = 0; a < D; ++a) {
+                const double2 d = L[b * D + a], u = U[c * D + a];
+                pr += d.x * u.x + d.y * u.y;
+                pim += d.y * u.x - d.x * u.y;
+            }
+            re += pr * Mb[2 * (c * D + b)] - pim * Mb[2 * (c * D + b) + 1];
         }
     contrib[e] = 2.0 * scale * re;
 }
@@ -416,20 +670,112 @@ SaPlan* get_saplan(DevPlan* dp) {
     return raw;
 }
 
-template <typename C, int K>
-cudaError_t launch_block(bool grad, C* psi, C* lam, const C* U, int diag, unsigned long long qmask, int n,
-                         double* npart, int grid, cudaStream_t s) {
-    if constexpr (K <= 2) {   // gradient blocks have at most two qubits
-        if (grad) {
-            sa_block_kernel<C, K, true><<<grid, kSaThreads, 0, s>>>(psi, lam, U, diag, qmask, n, npart);
-            count_launch();
-            return cudaGetLastError();
-        }
+template <typename C, int TB>
+cudaError_t launch_seg(C* psi, C* lam, const C* table, const SaSeg& sg, int n, double* npart, int grid,
+                       cudaStream_t s) {
+    static bool attr[kMaxDeviceSlots] = {};   // the attribute is per device
+    const int d = device_slot();
+    if (!attr[d]) {
+        const cudaError_t e = cudaFuncSetAttribute(sa_seg_kernel<C, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)sa_seg_smem<C, TB>());
+        if (e != cudaSuccess) return e;
+        attr[d] = true;
     }
-    (void)grad;
-        sa_block_kernel<C, K, false><<<grid, kSaThreads, 0, s>>>(psi, lam, U, diag, qmask, n, npart);
+    ProfScope ps("sa_seg_kernel", s);
+    sa_seg_kernel<C, TB><<<grid, kSegThreads, sa_seg_smem<C, TB>(), s>>>(psi, lam, table, sg, n, npart);
     count_launch();
     return cudaGetLastError();
+}
+
+// lambda = H psi by tile passes; returns false (nothing launched) when a term's
+// X mask does not fit in a tile with the lowest qubits.
+template <typename C>
+bool ham_apply_tiled(const C* psi, C* lam, const tcng_pauli* H, size_t n_terms, const TermSet* ts,
+                     const double* coeffs, int n, cudaStream_t s, cudaError_t* err) {
+    constexpr int TB = sizeof(C) == 8 ? 12 : 11;
+    const int tbits = std::min(TB, n);
+    const unsigned long long cmask = (unsigned long long)std::min(32 / (int)sizeof(C), 1 << tbits) - 1;
+    struct Bin {
+        unsigned long long mask;
+        std::vector<int> diag, off;
+    };
+    std::vector<Bin> bins;
+    for (size_t t = 0; t < n_terms; ++t) {
+        const unsigned long long x = H[t].xmask;
+        if (__builtin_popcountll(cmask | x) > tbits) return false;
+        if (x == 0) {
+            if (bins.empty()) bins.push_back(Bin{cmask, {}, {}});
+            bins[0].diag.push_back((int)t);
+            continue;
+        }
+        bool placed = false;
+        for (Bin& b : bins) {
+            if (b.diag.size() + b.off.size() < (size_t)kHamMax && __builtin_popcountll(b.mask | x) <= tbits) {
+                b.mask |= x;
+                b.off.push_back((int)t);
+                placed = true;
+                break;
+            }
+        }
+        if (!placed) bins.push_back(Bin{cmask | x, {}, {(int)t}});
+    }
+    if (!bins.empty())   // diagonal terms beyond the first bin's room go to bins of their own
+        while (bins[0].diag.size() + bins[0].off.size() > (size_t)kHamMax) {
+            Bin extra{cmask, {}, {}};
+            while (extra.diag.size() < (size_t)kHamMax && bins[0].diag.size() + bins[0].off.size() > (size_t)kHamMax) {
+                extra.diag.push_back(bins[0].diag.back());
+                bins[0].diag.pop_back();
+            }
+            bins.push_back(extra);
+        }
+    static bool attr[kMaxDeviceSlots] = {};
+    const int d = device_slot();
+    if (!attr[d]) {
+        *err = cudaFuncSetAttribute(sa_ham_tile_kernel<C, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sa_ham_smem<C, TB>());
+        if (*err != cudaSuccess) return true;
+        attr[d] = true;
+    }
+    const int grid = std::max(1, num_sms() * 4);
+    bool first = true;
+    for (const Bin& b : bins) {
+        SaHamPass hp{};
+        unsigned long long tm = b.mask;
+        for (int q = 0; q < n && __builtin_popcountll(tm) < tbits; ++q) tm |= 1ull << q;
+        hp.tmask = tm;
+        hp.tbits = tbits;
+        hp.first = first ? 1 : 0;
+        auto tile_bits = [&](unsigned long long m) {   // m's bits inside the tile, in tile positions
+            int r = 0;
+            for (int q = 0, c = 0; q < n; ++q)
+                if ((tm >> q) & 1) {
+                    if ((m >> q) & 1) r |= 1 << c;
+                    ++c;
+                }
+            return r;
+        };
+        for (int t : b.diag) {
+            hp.idx[hp.nt] = t;
+            hp.xt[hp.nt] = 0;
+            hp.zt[hp.nt++] = tile_bits(H[t].zmask);
+        }
+        hp.ndiag = hp.nt;
+        for (int t : b.off) {
+            hp.idx[hp.nt] = t;
+            hp.xt[hp.nt] = tile_bits(H[t].xmask);
+            hp.zt[hp.nt++] = tile_bits(H[t].zmask);
+        }
+        sa_ham_tile_kernel<C, TB><<<grid, kHamThreads, sa_ham_smem<C, TB>(), s>>>(psi, lam, ts->d_h, coeffs,
+                                                                                  ts->d_c, hp, n);
+        count_launch();
+        first = false;
+    }
+    if (bins.empty()) {   // no terms: lambda = 0
+        *err = cudaMemsetAsync(lam, 0, sizeof(C) << n, s);
+        return true;
+    }
+    *err = cudaGetLastError();
+    return true;
 }
 
 }  // namespace
@@ -464,11 +810,18 @@ tcng_status run_state_adjoint(tcng_state* st, int item, const tcng_gate* ops, si
     e = cudaMemsetAsync(zero, 0, sizeof(long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
     TermSet* ts = get_terms(H, n_terms, n);
-    e = launch_ham_apply<C>(static_cast<const C*>(st->buf), st->d_off + item, lam, zero, 1, n, ts->d_h,
+    {
+    ProfScope ps("ham_apply_kernel", s);
+    if (!ham_apply_tiled<C>(psi, lam, H, n_terms, ts, coeffs, n, s, &e))
+        e = launch_ham_apply<C>(static_cast<const C*>(st->buf), st->d_off + item, lam, zero, 1, n, ts->d_h,
                             (int)n_terms, coeffs, ts->d_c, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "H apply");
+    {
+    ProfScope ps("sa_dot_kernel", s);
     sa_dot_kernel<C><<<grid, kSaThreads, 0, s>>>(psi, lam, N, dpart);
     sa_sum_kernel<<<1, 32, 0, s>>>(dpart, grid, energy);
+    }
     count_launch();
     count_launch();
     if (!grad || P == 0) {
@@ -494,16 +847,52 @@ tcng_status run_state_adjoint(tcng_state* st, int item, const tcng_gate* ops, si
     if (!npart || !Nfin || !contrib) return fail(TCNG_ENOMEM, "state-pass adjoint scratch");
     // scratch may have moved: re-read lambda
     lam = static_cast<C*>(c.scratch("sa_lambda", sizeof(C) * (size_t)N));
+    // blocks of <= 2 qubits run in fused segments (one pass over both states per
+    // segment): consecutive blocks, last first, while their qubits and the lowest
+    // qubits fit in the tile
+    constexpr int TB = sizeof(C) == 8 ? 12 : 11;
+    const int tbits = std::min(TB, n);
+    const int chunk = std::min(32 / (int)sizeof(C), 1 << tbits);   // amplitudes per 32-byte piece
+    const unsigned long long cmask = (unsigned long long)chunk - 1;
+    SaSeg sg{};
+    unsigned long long used = 0, qm[kSegMax];
+    auto flush = [&]() -> cudaError_t {
+        if (sg.nblk == 0) return cudaSuccess;
+        unsigned long long tm = cmask | used;
+        for (int q = 0; q < n && __builtin_popcountll(tm) < tbits; ++q) tm |= 1ull << q;
+        sg.tmask = tm;
+        sg.tbits = tbits;
+        for (int i = 0; i < sg.nblk; ++i) {
+            const int q0 = __builtin_ctzll(qm[i]);
+            const unsigned long long rest = qm[i] & (qm[i] - 1);
+            sg.b[i].tb0 = __builtin_popcountll(tm & ((1ull << q0) - 1));
+            sg.b[i].tb1 = rest ? __builtin_popcountll(tm & ((1ull << __builtin_ctzll(rest)) - 1)) : -1;
+        }
+        const cudaError_t r = launch_seg<C, TB>(psi, lam, table, sg, n, npart, grid, s);
+        sg = SaSeg{};
+        used = 0;
+        return r;
+    };
     for (int bi = (int)sp->blocks.size() - 1; bi >= 0; --bi) {
         const SaPlan::Blk& b = sp->blocks[bi];
-        const bool gb = b.grad >= 0;
-        double* np = gb ? npart + (size_t)b.grad * grid * 32 : nullptr;
         const C* U = table + b.out_off;
-        if (b.k == 1) {
-            e = launch_block<C, 1>(gb, psi, lam, U, b.diag, b.qmask, n, np, grid, s);
-        } else if (b.k == 2) {
-            e = launch_block<C, 2>(gb, psi, lam, U, b.diag, b.qmask, n, np, grid, s);
-        } else {   // 3..5 qubits, no parameter: each state on its own
+        if (b.k <= 2) {
+            if (sg.nblk == kSegMax || __builtin_popcountll(cmask | used | b.qmask) > tbits) {
+                e = flush();
+                if (e != cudaSuccess) return cuda_fail(e, "adjoint segment kernel");
+            }
+            SaSegBlk& sb = sg.b[sg.nblk];
+            sb.k = b.k;
+            sb.diag = b.diag;
+            sb.grad = b.grad;
+            sb.out_off = b.out_off;
+            qm[sg.nblk++] = b.qmask;
+            used |= b.qmask;
+            continue;
+        }
+        e = flush();   // 3..5 qubits, no parameter: each state on its own
+        if (e != cudaSuccess) return cuda_fail(e, "adjoint segment kernel");
+        {
             for (C* x : {psi, lam}) {
                 if (b.k == 3)
                     sa_uncompute_kernel<C, 3><<<grid, kSaThreads, 0, s>>>(x, U, b.diag, b.qmask, n);
@@ -517,6 +906,9 @@ tcng_status run_state_adjoint(tcng_state* st, int item, const tcng_gate* ops, si
         }
         if (e != cudaSuccess) return cuda_fail(e, "adjoint block kernel");
     }
+    e = flush();
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint segment kernel");
+    ProfScope ps("sa_grad_kernels", s);
     if (sp->n_ents > 0) {
         sa_nfinal_kernel<<<(sp->n_grad_blocks * 32 + 255) / 256, 256, 0, s>>>(npart, grid, sp->n_grad_blocks, Nfin);
         sa_grad_kernel<<<(sp->n_ents + 63) / 64, 64, 0, s>>>(sp->d_ents, sp->n_ents, dq->d_bops, dq->d_pool, params,

@@ -56,7 +56,7 @@ def check(e, g, e_ref, g_ref, csum, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-@pytest.mark.parametrize("n,L", [(4, 2), (7, 1), (9, 2)])
+@pytest.mark.parametrize("n,L", [(4, 2), (7, 1), (9, 2), (14, 2), (16, 1)])
 def test_su4_ladder_against_parameter_shift(T, n, L, dtype):
     c = gen.su4_ladder(n, L)
     g, p = c.to_ir()
@@ -89,11 +89,12 @@ def test_forced_state_path_matches_per_item_kernel(T, dtype):
         check(e2[i], g2[i], e1[i], g1[i], csum, dtype)
 
 
-@pytest.mark.parametrize("seed", [0, 1])
-def test_state_path_every_gate_kind(T, seed):
+@pytest.mark.parametrize("n,seed", [(7, 0), (7, 1), (14, 2)])
+def test_state_path_every_gate_kind(T, n, seed):
     """Random circuits of every kind up to 3-qubit explicit matrices, with RP
-    parameters (1- and 2-qubit words), CP, RZZ, shared parameters: oracle PS and FD."""
-    n = 7
+    parameters (1- and 2-qubit words), CP, RZZ, shared parameters: oracle PS and FD.
+    At 14 qubits the fused runs of blocks span several tiles and alternate with the
+    3-qubit blocks' own passes."""
     c, th = gen.random_circuit(n, 60, seed=seed,
                                kinds=["X", "Y", "Z", "H", "S", "T", "RX", "RY", "RZ", "CX", "CZ", "CP",
                                       "SWAP", "RZZ", "U1", "U2", "U3", "RP"])
