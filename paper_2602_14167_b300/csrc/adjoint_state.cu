@@ -100,6 +100,17 @@ __device__ __forceinline__ double sa_fma(double a, double b, double c) { return 
 
 __device__ __forceinline__ int sa_ins0(int j, int b) { return ((j >> b) << (b + 1)) | (j & ((1 << b) - 1)); }
 
+// Shared-memory place of tile position p (complex64 tiles): tile bit 4 flips
+// bits 1 and 2, bit 5 flips bits 2 and 3.  Linear (place(p ^ o) = place(p) ^
+// place(o)), a bijection, and bit 0 is kept (a 16-byte piece stays whole); with
+// 16 eight-byte words per 128-byte row it spreads the half-warps of blocks on
+// tile bits (1,2), (2,3), (3,4) over all banks (and halves the conflict of (0,1)).
+template <typename C>
+__device__ __forceinline__ int sa_place(int p) {
+    if (sizeof(C) != 8) return p;
+    return p ^ ((0xAC60 >> (((p >> 4) & 3) * 4)) & 15);
+}
+
 // v[0..V) per lane; afterwards, for V = 32, lane l holds the warp total of
 // element l in v[0]; for V = 8 the four lanes 4e..4e+3 hold that of element e.
 template <typename R, int V>
@@ -124,24 +135,20 @@ __device__ __forceinline__ void sa_warp_transpose_sum(R (&v)[32], int lane) {
 // and, for a gradient block, the warp's partials of M[l][m] = sum psi_out(l)
 // conj(lambda_out(m)) (the block's outputs, before U^dagger) added to wr (this
 // warp's row).  Every product is one fused multiply-add on a running sum.
-template <typename C, int K>
+template <typename C, int K, bool DIAG>
 __device__ __forceinline__ void sa_seg_block(C* __restrict__ sp, C* __restrict__ sl, const C* __restrict__ su,
                                              const SaSegBlk& bk, int E, typename Real<C>::T* __restrict__ wr) {
     using R = typename Real<C>::T;
     constexpr int D = 1 << K;
     const int lane = threadIdx.x & 31;
-    const bool diag = bk.diag, grad = bk.grad >= 0;
-    C u[D * D];
-    if (diag) {
+    const bool grad = bk.grad >= 0;
+    C u[DIAG ? D : D * D];
 #pragma unroll
-        for (int l = 0; l < D; ++l) u[l] = su[l];
-    } else {
+    for (int i = 0; i < (DIAG ? D : D * D); ++i) u[i] = su[i];
+    int off[D];   // places of the class's amplitudes relative to the class's first
 #pragma unroll
-        for (int i = 0; i < D * D; ++i) u[i] = su[i];
-    }
-    int off[D];
-#pragma unroll
-    for (int l = 0; l < D; ++l) off[l] = ((l & 1) ? (1 << bk.tb0) : 0) | ((K == 2 && (l & 2)) ? (1 << bk.tb1) : 0);
+    for (int l = 0; l < D; ++l)
+        off[l] = sa_place<C>(((l & 1) ? (1 << bk.tb0) : 0) | ((K == 2 && (l & 2)) ? (1 << bk.tb1) : 0));
     R macc[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) macc[i] = 0;
@@ -149,11 +156,12 @@ __device__ __forceinline__ void sa_seg_block(C* __restrict__ sp, C* __restrict__
     for (int j = threadIdx.x; j < classes; j += kSegThreads) {
         int p = sa_ins0(j, bk.tb0);
         if (K == 2) p = sa_ins0(p, bk.tb1);
+        p = sa_place<C>(p);
         C a[D], b[D];
 #pragma unroll
         for (int l = 0; l < D; ++l) {
-            a[l] = sp[p | off[l]];
-            b[l] = sl[p | off[l]];
+            a[l] = sp[p ^ off[l]];
+            b[l] = sl[p ^ off[l]];
         }
         if (grad) {   // M[l][m] += a_l conj(b_m)
 #pragma unroll
@@ -171,15 +179,15 @@ __device__ __forceinline__ void sa_seg_block(C* __restrict__ sp, C* __restrict__
             R yr = 0, yi = 0, zr = 0, zi = 0;
 #pragma unroll
             for (int m = 0; m < D; ++m) {
-                if (diag && m != l) continue;
-                const C w = diag ? u[l] : u[m * D + l];
+                if (DIAG && m != l) continue;
+                const C w = DIAG ? u[l] : u[m * D + l];
                 yr = sa_fma(w.y, a[m].y, sa_fma(w.x, a[m].x, yr));
                 yi = sa_fma(-w.y, a[m].x, sa_fma(w.x, a[m].y, yi));
                 zr = sa_fma(w.y, b[m].y, sa_fma(w.x, b[m].x, zr));
                 zi = sa_fma(-w.y, b[m].x, sa_fma(w.x, b[m].y, zi));
             }
-            sp[p | off[l]] = cmk<C>(yr, yi);
-            sl[p | off[l]] = cmk<C>(zr, zi);
+            sp[p ^ off[l]] = cmk<C>(yr, yi);
+            sl[p ^ off[l]] = cmk<C>(zr, zi);
         }
     }
     if (grad) {   // block-uniform branch: every lane of every warp takes it
@@ -247,24 +255,33 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(C) == 8 ? 2 : 1)
         for (int q = tid; q < E / PW; q += kSegThreads) {
             const int pos = q * PW;
             const unsigned long long g = base | dep[pos & 63] | dep[64 + (pos >> 6)];
-            *reinterpret_cast<float4*>(sp + pos) = __ldcs(reinterpret_cast<const float4*>(psi + g));
-            *reinterpret_cast<float4*>(sl + pos) = __ldcs(reinterpret_cast<const float4*>(lam + g));
+            const int sq = sa_place<C>(pos);
+            *reinterpret_cast<float4*>(sp + sq) = __ldcs(reinterpret_cast<const float4*>(psi + g));
+            *reinterpret_cast<float4*>(sl + sq) = __ldcs(reinterpret_cast<const float4*>(lam + g));
         }
         __syncthreads();
         for (int bi = 0; bi < nb; ++bi) {
             const SaSegBlk& bk = seg.b[bi];
             R* w = wr + (warp * kSegMax + bi) * 32;
-            if (bk.k == 2)
-                sa_seg_block<C, 2>(sp, sl, su + bi * 16, bk, E, w);
-            else
-                sa_seg_block<C, 1>(sp, sl, su + bi * 16, bk, E, w);
+            if (bk.k == 2) {
+                if (bk.diag)
+                    sa_seg_block<C, 2, true>(sp, sl, su + bi * 16, bk, E, w);
+                else
+                    sa_seg_block<C, 2, false>(sp, sl, su + bi * 16, bk, E, w);
+            } else {
+                if (bk.diag)
+                    sa_seg_block<C, 1, true>(sp, sl, su + bi * 16, bk, E, w);
+                else
+                    sa_seg_block<C, 1, false>(sp, sl, su + bi * 16, bk, E, w);
+            }
             __syncthreads();
         }
         for (int q = tid; q < E / PW; q += kSegThreads) {
             const int pos = q * PW;
             const unsigned long long g = base | dep[pos & 63] | dep[64 + (pos >> 6)];
-            __stcs(reinterpret_cast<float4*>(psi + g), *reinterpret_cast<const float4*>(sp + pos));
-            __stcs(reinterpret_cast<float4*>(lam + g), *reinterpret_cast<const float4*>(sl + pos));
+            const int sq = sa_place<C>(pos);
+            __stcs(reinterpret_cast<float4*>(psi + g), *reinterpret_cast<const float4*>(sp + sq));
+            __stcs(reinterpret_cast<float4*>(lam + g), *reinterpret_cast<const float4*>(sl + sq));
         }
         if (++since == kSegFold) {   // CTA-uniform
             fold();
