@@ -493,11 +493,12 @@ def plan_stages(n, gates, pool):
 
 def su4_ladder_bench(args, dev, dist, world, res):
     """Energy + full gradient of the 32-qubit SU(4)-ladder TFIM VQE (L = 16, 7440
-    parameters) on one GPU by the state-pass adjoint (Sec. VI.B)."""
+    parameters) on one GPU by the state-pass adjoint (Sec. VI.B); --su4-qubits and
+    --su4-layers set a smaller case for profiling."""
     import torch
     from paper_2602_14167_b300 import StateBatch
     from paper_2602_14167_b300 import tcng as T
-    n, L = 32, 16
+    n, L = args.su4_qubits, args.su4_layers
     c = gen.su4_ladder(n, L)
     g, p = c.to_ir()
     th = torch.tensor(gen.random_thetas(c.n_params, seed=7).reshape(1, -1), device=dev)
@@ -785,6 +786,8 @@ def main():
                     help="skip the FMA peaks, config 2, unfused and shared-unitary measurements")
     ap.add_argument("--paths-only", action="store_true", help="only those measurements")
     ap.add_argument("--no-autotune", action="store_true", help="library default options, no autotuner run")
+    ap.add_argument("--su4-qubits", type=int, default=32, help="SU(4)-ladder line: qubits (profiling: smaller)")
+    ap.add_argument("--su4-layers", type=int, default=16, help="SU(4)-ladder line: layers")
     ap.add_argument("--apps-subset", default="", help="qml | su4: only the QML batches or the SU(4)-ladder gradient (profiling)")
     ap.add_argument("--fuse-width", type=int, default=0, help="override the fusion width (tuning)")
     ap.add_argument("--tile-bits", type=int, default=0, help="override the tile bits (tuning)")
