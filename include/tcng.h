@@ -405,7 +405,8 @@ typedef enum {
                                   parameter set and the state spans at least one 2^13-amplitude
                                   tile per SM, or spans 32 tiles per SM */,
     TCNG_OPT_STATE_ADJOINT_N = 6  /* tcng_energy_grad runs the state-pass adjoint (one pass over
-                                  psi and lambda per block of <= 2 qubits, all of a block's
+                                  psi and lambda per run of consecutive blocks of <= 2 qubits
+                                  that fits a shared-memory tile, all of a block's
                                   parameters from one cross-density matrix) for states of at
                                   least this many qubits (default 21; 1..35), and always for
                                   circuits with RP parameters; smaller states use the
