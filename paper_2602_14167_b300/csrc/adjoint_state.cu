@@ -70,7 +70,7 @@ __device__ __forceinline__ unsigned long long sa_pdep(unsigned long long v, unsi
 // the lowest qubits (contiguous 32-byte pieces in memory), fit in TB tile bits.
 // Each CTA loads a tile of psi and of lambda (the segment's qubits free, all other
 // qubits fixed) into shared memory once, applies every block of the run to both
-// (with its N partials), and writes the tile back: one pass over the two states
+// (with its M partials), and writes the tile back: one pass over the two states
 // per segment instead of one per block.
 constexpr int kSegMax = 16;      // blocks per segment
 constexpr int kSegThreads = 256; // complex64: two CTAs per SM (shared memory and registers)
