@@ -65,3 +65,34 @@ def test_rejects_requests_beyond_the_static_scratch(T):
         T.tcng_expect_pauli_noalloc(ptr, n, T.C64, strings, out)
     assert "static scratch" in str(ei.value)
     st.free()
+
+
+@pytest.mark.parametrize("dtype,n", [("c64", 17), ("c128", 12)])
+def test_call_recorded_in_a_cuda_graph(T, dtype, n):
+    """The entry point allocates nothing and copies nothing, so after one ordinary
+    call it can be recorded into a CUDA graph: the replay reads the state as it
+    is at replay time (changed after the capture) and matches tcng_expect_pauli."""
+    from paper_2602_14167_b300 import StateBatch
+    st = StateBatch(n, dtype=dtype)
+    dt = T.C64 if dtype == "c64" else T.C128
+    strings = np.concatenate([gen.random_pauli_strings(n, 24, min(4, n), seed=5), gen.tfim_terms(n, 1.0, 1.0)])
+    ptr, _ = T.tcng_state_ptr(st.handle, 0)
+    out = torch.full((len(strings),), float("nan"), dtype=torch.float64, device="cuda")
+    st.amplitudes(0).copy_(torch.tensor(gen.random_state(n, seed=1), dtype=st.cdtype, device="cuda"))
+    T.tcng_expect_pauli_noalloc(ptr, n, dt, strings, out)   # first call outside any capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        T.tcng_expect_pauli_noalloc(ptr, n, dt, strings, out)
+    for seed in (2, 3):
+        st.amplitudes(0).copy_(torch.tensor(gen.random_state(n, seed=seed), dtype=st.cdtype, device="cuda"))
+        out.fill_(float("nan"))
+        g.replay()
+        ref = torch.empty((1, len(strings)), dtype=torch.float64, device="cuda")
+        T.tcng_expect_pauli(st.handle, strings, ref)
+        torch.cuda.synchronize()
+        got, want = out.cpu().numpy(), ref[0].cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert np.max(np.abs(got - want)) < TOL[dtype]
+    del g
+    st.free()
