@@ -471,6 +471,21 @@ const char* tcng_describe_plan(int n, const tcng_gate* ops, size_t n_ops, const 
                                size_t n_mat, int P, int adjoint);
 
 /*
+ * Human-readable summary of the state-pass adjoint's plan for a gate list and a
+ * Pauli sum (host only, no device call; thread-local string): the reverse
+ * sweep's steps, last block first, as "seg tmask=<tile qubits> blocks=<block>:
+ * <qubit mask>,..." (runs of blocks of <= 2 qubits sharing one pass over psi
+ * and lambda) and "lone" lines (blocks of 3..5 qubits), then the passes of
+ * lambda = H psi as "ham tmask=<tile qubits> terms=<indices>" (hampasses=-1 when
+ * a term's X mask does not fit in a tile: the gather kernel runs instead).
+ * dt selects the tile size (2^12 amplitudes for complex64, 2^11 for complex128).
+ * Returns "error: ..." for an invalid gate list.
+ */
+const char* tcng_describe_state_adjoint(int n, const tcng_gate* ops, size_t n_ops, const double* mat_pool,
+                                        size_t n_mat, int P, const tcng_pauli* H, size_t n_terms,
+                                        tcng_dtype dt);
+
+/*
  * Shared-memory layouts of one lock-step FP16 tile pass (host only, no device
  * call).  rbit: nst x 4 register tile bits of the pass's stages, each stage's four
  * ascending and in 0..12.  out (nst x 8 bytes, caller-owned): per stage the

@@ -41,7 +41,9 @@
 
 #include <algorithm>
 #include <map>
+#include <cstdio>
 #include <stdexcept>
+#include <string>
 #include <vector>
 
 #include "capi_internal.hpp"
@@ -704,29 +706,77 @@ cudaError_t launch_seg(C* psi, C* lam, const C* table, const SaSeg& sg, int n, d
     return cudaGetLastError();
 }
 
-// lambda = H psi by tile passes; returns false (nothing launched) when a term's
-// X mask does not fit in a tile with the lowest qubits.
+// Tile geometry of the state-pass kernels: tile bits and the lowest qubits that
+// every tile holds (32-byte pieces in memory).
 template <typename C>
-bool ham_apply_tiled(const C* psi, C* lam, const tcng_pauli* H, size_t n_terms, const TermSet* ts,
-                     const double* coeffs, int n, cudaStream_t s, cudaError_t* err) {
+void sa_tile_geometry(int n, int* tbits, unsigned long long* cmask) {
     constexpr int TB = sizeof(C) == 8 ? 12 : 11;
-    const int tbits = std::min(TB, n);
-    const unsigned long long cmask = (unsigned long long)std::min(32 / (int)sizeof(C), 1 << tbits) - 1;
-    struct Bin {
-        unsigned long long mask;
-        std::vector<int> diag, off;
+    *tbits = std::min(TB, n);
+    *cmask = (unsigned long long)std::min(32 / (int)sizeof(C), 1 << *tbits) - 1;
+}
+
+// Pad a tile mask with the lowest qubits it lacks, up to tbits qubits.
+unsigned long long sa_pad_mask(unsigned long long tm, int n, int tbits) {
+    for (int q = 0; q < n && __builtin_popcountll(tm) < tbits; ++q) tm |= 1ull << q;
+    return tm;
+}
+
+// The reverse sweep's steps, last block first: segments (runs of blocks of <= 2
+// qubits whose qubits and cmask fit in tbits, at most kSegMax) and lone blocks
+// of 3..5 qubits (tmask 0).
+struct SaStep {
+    std::vector<int> blk;
+    unsigned long long tmask = 0;
+};
+std::vector<SaStep> plan_reverse_steps(const std::vector<unsigned long long>& qmask, const std::vector<int>& k,
+                                       int n, int tbits, unsigned long long cmask) {
+    std::vector<SaStep> out;
+    SaStep cur;
+    unsigned long long used = 0;
+    auto close = [&]() {
+        if (cur.blk.empty()) return;
+        cur.tmask = sa_pad_mask(cmask | used, n, tbits);
+        out.push_back(cur);
+        cur = SaStep{};
+        used = 0;
     };
-    std::vector<Bin> bins;
+    for (int bi = (int)qmask.size() - 1; bi >= 0; --bi) {
+        if (k[bi] <= 2) {
+            if ((int)cur.blk.size() == kSegMax || __builtin_popcountll(cmask | used | qmask[bi]) > tbits) close();
+            cur.blk.push_back(bi);
+            used |= qmask[bi];
+            continue;
+        }
+        close();
+        SaStep big;
+        big.blk.push_back(bi);
+        out.push_back(big);
+    }
+    close();
+    return out;
+}
+
+// The passes of lambda = H psi: diagonal terms (no X) in the first pass, each
+// other term in the first pass whose tile mask, widened by its X mask, stays
+// within tbits qubits (at most kHamMax terms a pass).  False when a term's X
+// mask does not fit in a tile with cmask.
+struct HamBin {
+    unsigned long long mask;   // before padding
+    std::vector<int> diag, off;
+};
+bool plan_ham_passes(const tcng_pauli* H, size_t n_terms, int tbits, unsigned long long cmask,
+                     std::vector<HamBin>& bins) {
+    bins.clear();
     for (size_t t = 0; t < n_terms; ++t) {
         const unsigned long long x = H[t].xmask;
         if (__builtin_popcountll(cmask | x) > tbits) return false;
         if (x == 0) {
-            if (bins.empty()) bins.push_back(Bin{cmask, {}, {}});
+            if (bins.empty()) bins.push_back(HamBin{cmask, {}, {}});
             bins[0].diag.push_back((int)t);
             continue;
         }
         bool placed = false;
-        for (Bin& b : bins) {
+        for (HamBin& b : bins) {
             if (b.diag.size() + b.off.size() < (size_t)kHamMax && __builtin_popcountll(b.mask | x) <= tbits) {
                 b.mask |= x;
                 b.off.push_back((int)t);
@@ -734,17 +784,31 @@ bool ham_apply_tiled(const C* psi, C* lam, const tcng_pauli* H, size_t n_terms, 
                 break;
             }
         }
-        if (!placed) bins.push_back(Bin{cmask | x, {}, {(int)t}});
+        if (!placed) bins.push_back(HamBin{cmask | x, {}, {(int)t}});
     }
     if (!bins.empty())   // diagonal terms beyond the first bin's room go to bins of their own
         while (bins[0].diag.size() + bins[0].off.size() > (size_t)kHamMax) {
-            Bin extra{cmask, {}, {}};
+            HamBin extra{cmask, {}, {}};
             while (extra.diag.size() < (size_t)kHamMax && bins[0].diag.size() + bins[0].off.size() > (size_t)kHamMax) {
                 extra.diag.push_back(bins[0].diag.back());
                 bins[0].diag.pop_back();
             }
             bins.push_back(extra);
         }
+    return true;
+}
+
+// lambda = H psi by tile passes; returns false (nothing launched) when a term's
+// X mask does not fit in a tile with the lowest qubits.
+template <typename C>
+bool ham_apply_tiled(const C* psi, C* lam, const tcng_pauli* H, size_t n_terms, const TermSet* ts,
+                     const double* coeffs, int n, cudaStream_t s, cudaError_t* err) {
+    constexpr int TB = sizeof(C) == 8 ? 12 : 11;
+    int tbits;
+    unsigned long long cmask;
+    sa_tile_geometry<C>(n, &tbits, &cmask);
+    std::vector<HamBin> bins;
+    if (!plan_ham_passes(H, n_terms, tbits, cmask, bins)) return false;
     static bool attr[kMaxDeviceSlots] = {};
     const int d = device_slot();
     if (!attr[d]) {
@@ -755,10 +819,9 @@ bool ham_apply_tiled(const C* psi, C* lam, const tcng_pauli* H, size_t n_terms, 
     }
     const int grid = std::max(1, num_sms() * 4);
     bool first = true;
-    for (const Bin& b : bins) {
+    for (const HamBin& b : bins) {
         SaHamPass hp{};
-        unsigned long long tm = b.mask;
-        for (int q = 0; q < n && __builtin_popcountll(tm) < tbits; ++q) tm |= 1ull << q;
+        const unsigned long long tm = sa_pad_mask(b.mask, n, tbits);
         hp.tmask = tm;
         hp.tbits = tbits;
         hp.first = first ? 1 : 0;
@@ -868,63 +931,51 @@ tcng_status run_state_adjoint(tcng_state* st, int item, const tcng_gate* ops, si
     // segment): consecutive blocks, last first, while their qubits and the lowest
     // qubits fit in the tile
     constexpr int TB = sizeof(C) == 8 ? 12 : 11;
-    const int tbits = std::min(TB, n);
-    const int chunk = std::min(32 / (int)sizeof(C), 1 << tbits);   // amplitudes per 32-byte piece
-    const unsigned long long cmask = (unsigned long long)chunk - 1;
-    SaSeg sg{};
-    unsigned long long used = 0, qm[kSegMax];
-    auto flush = [&]() -> cudaError_t {
-        if (sg.nblk == 0) return cudaSuccess;
-        unsigned long long tm = cmask | used;
-        for (int q = 0; q < n && __builtin_popcountll(tm) < tbits; ++q) tm |= 1ull << q;
-        sg.tmask = tm;
-        sg.tbits = tbits;
-        for (int i = 0; i < sg.nblk; ++i) {
-            const int q0 = __builtin_ctzll(qm[i]);
-            const unsigned long long rest = qm[i] & (qm[i] - 1);
-            sg.b[i].tb0 = __builtin_popcountll(tm & ((1ull << q0) - 1));
-            sg.b[i].tb1 = rest ? __builtin_popcountll(tm & ((1ull << __builtin_ctzll(rest)) - 1)) : -1;
-        }
-        const cudaError_t r = launch_seg<C, TB>(psi, lam, table, sg, n, npart, grid, s);
-        sg = SaSeg{};
-        used = 0;
-        return r;
-    };
-    for (int bi = (int)sp->blocks.size() - 1; bi >= 0; --bi) {
-        const SaPlan::Blk& b = sp->blocks[bi];
-        const C* U = table + b.out_off;
-        if (b.k <= 2) {
-            if (sg.nblk == kSegMax || __builtin_popcountll(cmask | used | b.qmask) > tbits) {
-                e = flush();
-                if (e != cudaSuccess) return cuda_fail(e, "adjoint segment kernel");
+    int tbits;
+    unsigned long long cmask;
+    sa_tile_geometry<C>(n, &tbits, &cmask);
+    std::vector<unsigned long long> qms;
+    std::vector<int> ks;
+    for (const SaPlan::Blk& b : sp->blocks) {
+        qms.push_back(b.qmask);
+        ks.push_back(b.k);
+    }
+    for (const SaStep& st_ : plan_reverse_steps(qms, ks, n, tbits, cmask)) {
+        if (st_.tmask) {
+            SaSeg sg{};
+            sg.tmask = st_.tmask;
+            sg.tbits = tbits;
+            sg.nblk = (int)st_.blk.size();
+            for (int i = 0; i < sg.nblk; ++i) {
+                const SaPlan::Blk& b = sp->blocks[st_.blk[i]];
+                SaSegBlk& sb = sg.b[i];
+                sb.k = b.k;
+                sb.diag = b.diag;
+                sb.grad = b.grad;
+                sb.out_off = b.out_off;
+                const int q0 = __builtin_ctzll(b.qmask);
+                const unsigned long long rest = b.qmask & (b.qmask - 1);
+                sb.tb0 = __builtin_popcountll(st_.tmask & ((1ull << q0) - 1));
+                sb.tb1 = rest ? __builtin_popcountll(st_.tmask & ((1ull << __builtin_ctzll(rest)) - 1)) : -1;
             }
-            SaSegBlk& sb = sg.b[sg.nblk];
-            sb.k = b.k;
-            sb.diag = b.diag;
-            sb.grad = b.grad;
-            sb.out_off = b.out_off;
-            qm[sg.nblk++] = b.qmask;
-            used |= b.qmask;
+            e = launch_seg<C, TB>(psi, lam, table, sg, n, npart, grid, s);
+            if (e != cudaSuccess) return cuda_fail(e, "adjoint segment kernel");
             continue;
         }
-        e = flush();   // 3..5 qubits, no parameter: each state on its own
-        if (e != cudaSuccess) return cuda_fail(e, "adjoint segment kernel");
-        {
-            for (C* x : {psi, lam}) {
-                if (b.k == 3)
-                    sa_uncompute_kernel<C, 3><<<grid, kSaThreads, 0, s>>>(x, U, b.diag, b.qmask, n);
-                else if (b.k == 4)
-                    sa_uncompute_kernel<C, 4><<<grid, kSaThreads, 0, s>>>(x, U, b.diag, b.qmask, n);
-                else
-                    sa_uncompute_kernel<C, 5><<<grid, kSaThreads, 0, s>>>(x, U, b.diag, b.qmask, n);
-                count_launch();
-            }
-            e = cudaGetLastError();
+        const SaPlan::Blk& b = sp->blocks[st_.blk[0]];   // 3..5 qubits, no parameter: each state on its own
+        const C* U = table + b.out_off;
+        for (C* x : {psi, lam}) {
+            if (b.k == 3)
+                sa_uncompute_kernel<C, 3><<<grid, kSaThreads, 0, s>>>(x, U, b.diag, b.qmask, n);
+            else if (b.k == 4)
+                sa_uncompute_kernel<C, 4><<<grid, kSaThreads, 0, s>>>(x, U, b.diag, b.qmask, n);
+            else
+                sa_uncompute_kernel<C, 5><<<grid, kSaThreads, 0, s>>>(x, U, b.diag, b.qmask, n);
+            count_launch();
         }
+        e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "adjoint block kernel");
     }
-    e = flush();
-    if (e != cudaSuccess) return cuda_fail(e, "adjoint segment kernel");
     ProfScope ps("sa_grad_kernels", s);
     if (sp->n_ents > 0) {
         sa_nfinal_kernel<<<(sp->n_grad_blocks * 32 + 255) / 256, 256, 0, s>>>(npart, grid, sp->n_grad_blocks, Nfin);
@@ -948,3 +999,70 @@ template tcng_status run_state_adjoint<double2>(tcng_state*, int, const tcng_gat
                                                 double*, double*, cudaStream_t);
 
 }  // namespace tcng
+
+// Host-only summary of the state-pass adjoint's plan: the reverse sweep's steps
+// and the passes of lambda = H psi (no device call).
+extern "C" const char* tcng_describe_state_adjoint(int n, const tcng_gate* ops, size_t n_ops,
+                                                   const double* mat_pool, size_t n_mat, int P,
+                                                   const tcng_pauli* H, size_t n_terms, tcng_dtype dt) {
+    using namespace tcng;
+    static thread_local std::string out;
+    try {
+        if (dt != TCNG_C64 && dt != TCNG_C128) throw std::invalid_argument("bad dtype");
+        if (n_terms && !H) throw std::invalid_argument("null terms");
+        Plan pl;
+        pl.n = n;
+        pl.P = P;
+        pl.opt = plan_options(dt, false);
+        pl.opt.fuse_width = 2;   // as the state-pass adjoint plans its blocks
+        pl.opt.unfused = 0;
+        pl.ops = import_ops(n, ops, n_ops, n_mat, P, mat_pool);
+        build_plan(pl);
+        int tbits;
+        unsigned long long cmask;
+        if (dt == TCNG_C64)
+            sa_tile_geometry<float2>(n, &tbits, &cmask);
+        else
+            sa_tile_geometry<double2>(n, &tbits, &cmask);
+        std::vector<unsigned long long> qms;
+        std::vector<int> ks;
+        for (const Block& b : pl.blocks) {
+            qms.push_back(b.qmask);
+            ks.push_back(b.k);
+        }
+        const std::vector<SaStep> steps = plan_reverse_steps(qms, ks, n, tbits, cmask);
+        std::vector<HamBin> bins;
+        const bool tiled = plan_ham_passes(H, n_terms, tbits, cmask, bins);
+        int nseg = 0;
+        for (const SaStep& st : steps) nseg += st.tmask != 0;
+        char buf[160];
+        snprintf(buf, sizeof buf, "blocks=%zu segments=%d lone=%d tbits=%d hampasses=%d\n", pl.blocks.size(),
+                 nseg, (int)steps.size() - nseg, tbits, tiled ? (int)bins.size() : -1);
+        out = buf;
+        for (const SaStep& st : steps) {
+            snprintf(buf, sizeof buf, "%s tmask=%llx blocks=", st.tmask ? "seg" : "lone", st.tmask);
+            out += buf;
+            for (size_t i = 0; i < st.blk.size(); ++i) {
+                snprintf(buf, sizeof buf, "%s%d:%llx", i ? "," : "", st.blk[i], (unsigned long long)qms[st.blk[i]]);
+                out += buf;
+            }
+            out += "\n";
+        }
+        if (tiled)
+            for (const HamBin& b : bins) {
+                snprintf(buf, sizeof buf, "ham tmask=%llx terms=", sa_pad_mask(b.mask, n, tbits));
+                out += buf;
+                bool first = true;
+                for (const std::vector<int>* v : {&b.diag, &b.off})
+                    for (int t : *v) {
+                        snprintf(buf, sizeof buf, "%s%d", first ? "" : ",", t);
+                        out += buf;
+                        first = false;
+                    }
+                out += "\n";
+            }
+    } catch (const std::exception& ex) {
+        out = std::string("error: ") + ex.what();
+    }
+    return out.c_str();
+}

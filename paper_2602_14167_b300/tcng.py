@@ -92,6 +92,8 @@ def lib():
             f.restype = C.c_int
         L.tcng_describe_plan.argtypes = [i32, vp, sz, vp, sz, i32, i32]
         L.tcng_describe_plan.restype = C.c_char_p
+        L.tcng_describe_state_adjoint.argtypes = [i32, vp, sz, vp, sz, i32, vp, sz, i32]
+        L.tcng_describe_state_adjoint.restype = C.c_char_p
         L.tcng_last_error.restype = C.c_char_p
         L.tcng_version.restype = C.c_char_p
         L.tcng_launch_count.restype = C.c_uint64
@@ -372,6 +374,16 @@ def tcng_describe_plan(n, gates, pool, P, adjoint=False):
                                     n_mat, int(P), int(adjoint)).decode()
 
 
+def tcng_describe_state_adjoint(n, gates, pool, P, terms, dtype=C64):
+    """Host-only summary of the state-pass adjoint's plan (segments, H passes)."""
+    g = _gates(gates)
+    p, n_mat = _pool(pool)
+    t = _terms(terms)
+    return lib().tcng_describe_state_adjoint(int(n), g.ctypes.data, len(g), p.ctypes.data if n_mat else None,
+                                             n_mat, int(P), t.ctypes.data if len(t) else None, len(t),
+                                             int(dtype)).decode()
+
+
 def tcng_plan_lock_layouts(rbit):
     """Shared-memory layouts of a lock-step FP16 pass: rbit is an (nst, 4) array of
     register tile bits; returns (layouts (nst, 8) uint8, relocated)."""
@@ -402,7 +414,7 @@ EXPORTED = [
     "tcng_energy_grad", "tcng_energy_grad_ragged", "tcng_apply_shared_unitary", "tcng_marginal_probs", "tcng_measure",
     "tcng_adam_step",
     "tcng_adam_step_f32", "tcng_mlp_forward", "tcng_mlp_backward", "tcng_set_option", "tcng_fma_peak",
-    "tcng_get_option", "tcng_autotune", "tcng_autotune_circuit", "tcng_autotune_report", "tcng_sync_status", "tcng_describe_plan",
+    "tcng_get_option", "tcng_autotune", "tcng_autotune_circuit", "tcng_autotune_report", "tcng_sync_status", "tcng_describe_plan", "tcng_describe_state_adjoint",
     "tcng_plan_lock_layouts",
     "tcng_profile_enable", "tcng_profile_read",
     "tcng_launch_count", "tcng_last_error", "tcng_version",

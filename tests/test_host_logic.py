@@ -238,3 +238,84 @@ def test_lock_layouts_random_passes_and_rejects(T):
     for bad in ([(0, 1, 2, 13)], [(3, 2, 1, 0)], []):
         with pytest.raises(T.TcngError):
             T.tcng_plan_lock_layouts(bad if bad else np.zeros((0, 4)))
+
+
+# ---- state-pass adjoint plan (host planner: fused segments, H passes) ----
+def _state_plan(T, n, c, terms, dtype=0):
+    g, p = c.to_ir()
+    s = T.tcng_describe_state_adjoint(n, g, p, max(c.n_params, 1), terms, dtype)
+    assert not s.startswith("error"), s
+    lines = s.splitlines()
+    head = {k: int(v) for k, v in re.findall(r"(\w+)=(-?\d+)", lines[0])}
+    steps, ham = [], []
+    for ln in lines[1:]:
+        kind, tm, rest = re.match(r"(\w+) tmask=([0-9a-f]+) (?:blocks|terms)=(.*)", ln).groups()
+        if kind == "ham":
+            ham.append((int(tm, 16), [int(t) for t in rest.split(",") if t]))
+        else:
+            blk = [tuple(int(x, 16) if i else int(x) for i, x in enumerate(b.split(":"))) for b in rest.split(",")]
+            steps.append((kind, int(tm, 16), blk))
+    return head, steps, ham
+
+
+def _popc(x):
+    return bin(x).count("1")
+
+
+@pytest.mark.parametrize("dtype,tbits,cmask", [(0, 12, 0b11), (1, 11, 0b1)])
+def test_state_adjoint_segments_of_the_su4_ladder(T, dtype, tbits, cmask):
+    """32-qubit, 16-layer SU(4) ladder: every block once, last first; each segment's
+    tile holds its blocks' qubits and the lowest qubits in exactly tbits qubits, at
+    most 16 blocks; a segment ends only where the next block does not fit."""
+    n = 32
+    c = gen.su4_ladder(n, 16)
+    head, steps, ham = _state_plan(T, n, c, gen.tfim_terms(n, 1.0, 1.0), dtype)
+    assert head["blocks"] == 496 and head["lone"] == 0 and head["tbits"] == tbits
+    order = [b for _, _, blk in steps for b, _ in blk]
+    assert order == list(range(495, -1, -1))
+    for i, (kind, tm, blk) in enumerate(steps):
+        assert kind == "seg" and _popc(tm) == tbits and tm & cmask == cmask and len(blk) <= 16
+        used = 0
+        for _, qm in blk:
+            assert _popc(qm) == 2 and qm & tm == qm
+            used |= qm
+        if i + 1 < len(steps) and len(blk) < 16:
+            assert _popc(cmask | used | steps[i + 1][2][0][1]) > tbits
+    if dtype == 0:
+        assert head["segments"] == 54
+
+
+def test_state_adjoint_plan_keeps_wide_blocks_alone(T):
+    """A circuit with explicit 3-qubit gates: the 3-qubit blocks are lone steps, the
+    segments around them keep the block order."""
+    n = 14
+    c, _ = gen.random_circuit(n, 80, seed=4, kinds=["RX", "RY", "RZ", "CX", "RZZ", "U2", "U3", "RP"])
+    head, steps, _ = _state_plan(T, n, c, gen.tfim_terms(n, 1.0, 1.0))
+    order = [b for _, _, blk in steps for b, _ in blk]
+    assert order == list(range(head["blocks"] - 1, -1, -1))
+    lone = [blk for kind, _, blk in steps if kind == "lone"]
+    assert head["lone"] == len(lone) >= 1
+    assert all(len(b) == 1 and _popc(b[0][1]) >= 3 for b in lone)
+    assert all(_popc(qm) <= 2 for kind, _, blk in steps if kind == "seg" for _, qm in blk)
+
+
+@pytest.mark.parametrize("n,seed", [(32, 0), (20, 1)])
+def test_hamiltonian_passes_cover_every_term_once(T, n, seed):
+    """lambda = H psi passes: every term in exactly one pass, its X mask inside the
+    pass's tile (12 qubits with qubits 0 and 1), the diagonal terms in the first."""
+    terms = np.concatenate([gen.tfim_terms(n, 1.0, 1.0), gen.random_pauli_strings(n, 40, 4, seed)])
+    head, _, ham = _state_plan(T, n, gen.su4_ladder(n, 1), terms)
+    assert head["hampasses"] == len(ham) >= 2
+    seen = sorted(t for _, ts in ham for t in ts)
+    assert seen == list(range(len(terms)))
+    for i, (tm, ts) in enumerate(ham):
+        assert _popc(tm) == 12 and tm & 3 == 3 and len(ts) <= 64
+        for t in ts:
+            xm = int(terms["xmask"][t])
+            assert xm & tm == xm
+            if xm == 0 and i > 0:
+                assert all(int(terms["xmask"][u]) == 0 for u in ts)   # overflow bins hold diagonals only
+    wide = terms[:1].copy()
+    wide["xmask"] = (1 << 11) - 1 << 5
+    wide["zmask"] = 0
+    assert _state_plan(T, n, gen.su4_ladder(n, 1), wide)[0]["hampasses"] == -1
