@@ -454,6 +454,23 @@ def vqe_bench(args, dev, dist, world):
                                            f"timed over {n_evals} energies and scaled to 2P+1"}
     res["speedup_vs_param_shift"] = res[f"n16_b{B}"]["evals_per_s"] / res["baseline_param_shift"]["evals_per_s"]
     st.free()
+    if world == 1 and not args.no_cpu_baseline:
+        # the oracle as it stands on the host cores: parameter-shift gradient of the
+        # first item (2P + 1 energies, complex128), timed on a bounded sample of energies
+        from oracle import sv
+        sv.energy(n, g, p, b["theta"][0], terms, b["coeffs"][0])
+        n_cpu = 24
+        t0 = time.perf_counter()
+        for k in range(n_cpu):
+            sh = b["theta"][0].copy()
+            sh[k % P] += np.pi / 2 * (1 if k % 2 == 0 else -1)
+            sv.energy(n, g, p, sh, terms, b["coeffs"][0])
+        per_e = (time.perf_counter() - t0) / n_cpu
+        res["cpu_baseline"] = {"value": 1.0 / (per_e * (2 * P + 1)), "unit": "evals/s", "cores": sv.num_threads(),
+                               "kind": "oracle",
+                               "sample": f"oracle (plain C, complex128) energies of one 16-qubit item at shifted "
+                                         f"angles: {n_cpu} timed ({per_e * 1e3:.1f} ms each), scaled to the "
+                                         f"2P+1 = {2 * P + 1} of one parameter-shift gradient"}
     return res
 
 
