@@ -4,8 +4,8 @@ The allocation-free entry point exists for callers that must not let the
 library call cudaMalloc (their allocator owns the free memory, or their hot
 path bans allocation).  It keeps its
 partial sums in a static device array instead.  Here it must reproduce the
-ordinary entry point's values within the complex64/complex128 tolerances of the
-other expectation tests, on two calls in a row (the second call reuses the
+ordinary entry point's values and the oracle's within the complex64/complex128
+tolerances of the other expectation tests, on two calls in a row (the second call reuses the
 array the first one left behind), and reject requests larger than its array.
 This file is collected last so a failure here comes after every other test.
 """
@@ -15,6 +15,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import sv  # noqa: E402
 from workloads import generators as gen  # noqa: E402
 
 TOL = {"c64": 1e-6, "c128": 1e-12}
@@ -51,6 +52,9 @@ def test_matches_allocating_entry_point_twice(T, dtype, n):
         got, want = out.cpu().numpy(), ref[0].cpu().numpy()
         assert np.all(np.isfinite(got))
         assert np.max(np.abs(got - want)) < TOL[dtype]
+        # and against the oracle directly (the state as stored on the device)
+        stored = st.amplitudes(0).cpu().numpy().astype(np.complex128)
+        assert np.max(np.abs(got - sv.expect(n, stored, strings).real)) < TOL[dtype]
     st.free()
 
 
