@@ -151,3 +151,27 @@ def test_su4_ladder_n32_cut_against_oracle_blocks(T):
     cut = np.array([(i % block) == block - 1 for l in range(L) for i in range(n - 1)])
     cut_params = np.repeat(cut, 15)
     assert np.all(gr[0][cut_params] == 0.0)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_wide_x_term_and_multi_pass_lambda(T, dtype):
+    """lambda = H psi with terms in several tile passes plus one X string on 12
+    qubits (wider than a tile with the lowest qubits: the whole Pauli sum then
+    takes the per-amplitude gather kernel), 14 qubits: energy and gradient against
+    the oracle's parameter shift, both sums."""
+    n = 14
+    c = gen.su4_ladder(n, 1)
+    g, p = c.to_ir()
+    th = gen.random_thetas(c.n_params, seed=3)
+    base = np.concatenate([gen.tfim_terms(n, 1.0, 0.7), gen.random_pauli_strings(n, 8, 3, seed=4)])
+    wide = base[:1].copy()
+    wide["xmask"] = np.uint64(((1 << 12) - 1) << 2)
+    wide["zmask"] = np.uint64(1 << 5)
+    wide["coeff"] = 0.3
+    plan = T.tcng_describe_state_adjoint(n, g, p, c.n_params, base).splitlines()[0]
+    assert "hampasses=-1" not in plan and int(plan.split("hampasses=")[1]) >= 2
+    assert "hampasses=-1" in T.tcng_describe_state_adjoint(n, g, p, c.n_params, np.concatenate([base, wide]))
+    for terms in (base, np.concatenate([base, wide])):
+        e, gr, _ = energy_grad(T, n, g, p, th, terms, dtype=dtype)
+        check(e[0], gr[0], sv.energy(n, g, p, th, terms), sv.grad_param_shift(n, g, p, th, terms),
+              np.abs(terms["coeff"]).sum(), dtype)
