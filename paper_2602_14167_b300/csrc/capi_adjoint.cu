@@ -235,7 +235,7 @@ tcng_status tcng_energy_grad(tcng_state* st, const tcng_gate* ops, size_t n_ops,
     std::lock_guard<std::mutex> lk(g_mu);
     try {
         // single large states, and circuits with Pauli-word rotation parameters,
-        // take the state-pass adjoint (one pass over psi and lambda per block)
+        // take the state-pass adjoint (one pass over psi and lambda per fused run of blocks)
         bool state_path = st->n[0] >= g_opt.state_adjoint_n;
         for (size_t i = 0; i < n_ops && !state_path; ++i)
             state_path = ops && ops[i].op == TCNG_RP && ops[i].param >= 0;
