@@ -416,7 +416,14 @@ typedef enum {
                                   into FP16 hi + lo (each tile scaled by a power of two
                                   first, FP32 accumulation; passes whose stages touch every
                                   tile bit keep two tiles in flight per CTA); 0: the TF32
-                                  hi/lo split everywhere */
+                                  hi/lo split everywhere */,
+    TCNG_OPT_STATE_ADJOINT_SMALL = 8  /* 1 (default): below TCNG_OPT_STATE_ADJOINT_N qubits, a
+                                  complex64 batch too small to occupy the GPU with the
+                                  per-item kernel (one CTA per item) takes the state-pass
+                                  adjoint when a cost model measured on a B300 says it is
+                                  faster: batch < ceil(batch / SMs) x 1.8 x 1.95^(n - 14)
+                                  (e.g. one item from 14 qubits, up to 99 items at 20);
+                                  0: only the qubit threshold decides */
 } tcng_option;
 
 tcng_status tcng_set_option(tcng_option opt, int value);

@@ -957,6 +957,9 @@ tcng_status tcng_set_option(tcng_option opt, int value) {
     case TCNG_OPT_TC_FP16:
         g_opt.tc_fp16 = value ? 1 : 0;
         return TCNG_OK;
+    case TCNG_OPT_STATE_ADJOINT_SMALL:
+        g_opt.state_adjoint_small = value ? 1 : 0;
+        return TCNG_OK;
     }
     return fail(TCNG_EINVAL, "unknown option");
 }
@@ -972,6 +975,7 @@ tcng_status tcng_get_option(tcng_option opt, int* value) {
     case TCNG_OPT_TENSOR_CORES: *value = g_opt.tensor_cores; return TCNG_OK;
     case TCNG_OPT_STATE_ADJOINT_N: *value = g_opt.state_adjoint_n; return TCNG_OK;
     case TCNG_OPT_TC_FP16: *value = g_opt.tc_fp16; return TCNG_OK;
+    case TCNG_OPT_STATE_ADJOINT_SMALL: *value = g_opt.state_adjoint_small; return TCNG_OK;
     }
     return fail(TCNG_EINVAL, "unknown option");
 }

@@ -25,7 +25,7 @@ assert GATE_DTYPE.itemsize == 56 and PAULI_DTYPE.itemsize == 24
 
 C64, C128 = 0, 1
 (OPT_FUSE_WIDTH, OPT_TILE_BITS, OPT_CHUNK_BITS, OPT_USE_GRAPHS, OPT_UNFUSED, OPT_TENSOR_CORES,
- OPT_STATE_ADJOINT_N, OPT_TC_FP16) = range(8)
+ OPT_STATE_ADJOINT_N, OPT_TC_FP16, OPT_STATE_ADJOINT_SMALL) = range(9)
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSUPPORTED", 5: "ETIMEOUT"}
 
 

@@ -28,6 +28,16 @@ def T():
     return tcng
 
 
+@pytest.fixture(autouse=True)
+def per_item_kernel(T):
+    """These tests are about the per-item persistent kernel: keep small complex64
+    batches on it (the state-pass adjoint has its own tests)."""
+    saved = T.tcng_get_option(T.OPT_STATE_ADJOINT_SMALL)
+    T.tcng_set_option(T.OPT_STATE_ADJOINT_SMALL, 0)
+    yield
+    T.tcng_set_option(T.OPT_STATE_ADJOINT_SMALL, saved)
+
+
 def energy_grad(T, n, gates, pool, theta, terms, coeffs=None, dtype="c128"):
     from paper_2602_14167_b300 import StateBatch
     theta = np.atleast_2d(theta)

@@ -27,7 +27,7 @@ def T():
 
 @pytest.fixture(autouse=True)
 def options(T):
-    saved = {o: T.tcng_get_option(o) for o in range(7)}
+    saved = {o: T.tcng_get_option(o) for o in range(9)}
     yield
     for o, v in saved.items():
         T.tcng_set_option(o, v)
@@ -175,3 +175,30 @@ def test_wide_x_term_and_multi_pass_lambda(T, dtype):
         e, gr, _ = energy_grad(T, n, g, p, th, terms, dtype=dtype)
         check(e[0], gr[0], sv.energy(n, g, p, th, terms), sv.grad_param_shift(n, g, p, th, terms),
               np.abs(terms["coeff"]).sum(), dtype)
+
+
+@pytest.mark.parametrize("n,B,state", [(16, 2, True), (16, 12, False), (18, 8, True), (12, 1, False)])
+def test_small_batches_take_the_state_pass(T, n, B, state):
+    """Below the qubit threshold, complex64 batches too small for the per-item
+    kernel take the state-pass adjoint (TCNG_OPT_STATE_ADJOINT_SMALL, on by
+    default): the path taken (seen in the kernels launched) follows the cost model,
+    and both paths give the oracle's energies and gradients."""
+    b = gen.tfim_batch(n, B, layers=2, seed=n + B)
+    g, p = b["circuit"].to_ir()
+    out = {}
+    for small in (1, 0):
+        T.tcng_set_option(T.OPT_STATE_ADJOINT_SMALL, small)
+        T.tcng_profile_read(reset=True)
+        T.tcng_profile_enable(True)
+        e, gr, st = energy_grad(T, n, g, p, b["theta"], b["terms"], b["coeffs"], "c64")
+        T.tcng_profile_enable(False)
+        used = "sa_seg_kernel" in T.tcng_profile_read(reset=True)
+        assert used == (state and small == 1)
+        out[small] = (e, gr)
+        st.free()
+    for i in range(min(B, 2)):
+        csum = np.abs(b["coeffs"][i]).sum()
+        e_ref = sv.energy(n, g, p, b["theta"][i], b["terms"], b["coeffs"][i])
+        g_ref = sv.grad_param_shift(n, g, p, b["theta"][i], b["terms"], b["coeffs"][i])
+        for small in (1, 0):
+            check(out[small][0][i], out[small][1][i], e_ref, g_ref, csum, "c64")
