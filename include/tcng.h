@@ -233,8 +233,9 @@ tcng_status tcng_hamiltonian_apply(const tcng_state* st, const tcng_pauli* terms
  * "Paradigms: AD"; cost independent of the number of parameters, O(1) states).
  *   st          batch of states (all items the same n); used as scratch for psi;
  *   ops/mat     gate list as in tcng_apply_circuit; parameterised gates may be
- *               RX, RY, RZ, RZZ, CP or RP (RP, and states of at least
- *               TCNG_OPT_STATE_ADJOINT_N qubits, take the state-pass adjoint:
+ *               RX, RY, RZ, RZZ, CP or RP (RP, states of at least
+ *               TCNG_OPT_STATE_ADJOINT_N qubits and small complex64 batches
+ *               under TCNG_OPT_STATE_ADJOINT_SMALL take the state-pass adjoint:
  *               items one after another, a parameterised RP on at most 2
  *               qubits; a scratch copy of one item's state is allocated);
  *   params_dev  device double [batch][P];
