@@ -234,8 +234,8 @@ tcng_status tcng_hamiltonian_apply(const tcng_state* st, const tcng_pauli* terms
  *   st          batch of states (all items the same n); used as scratch for psi;
  *   ops/mat     gate list as in tcng_apply_circuit; parameterised gates may be
  *               RX, RY, RZ, RZZ, CP or RP (RP, states of at least
- *               TCNG_OPT_STATE_ADJOINT_N qubits and small complex64 batches
- *               under TCNG_OPT_STATE_ADJOINT_SMALL take the state-pass adjoint:
+ *               TCNG_OPT_STATE_ADJOINT_N qubits and small batches under
+ *               TCNG_OPT_STATE_ADJOINT_SMALL take the state-pass adjoint:
  *               items one after another, a parameterised RP on at most 2
  *               qubits; a scratch copy of one item's state is allocated);
  *   params_dev  device double [batch][P];
@@ -419,11 +419,12 @@ typedef enum {
                                   tile bit keep two tiles in flight per CTA); 0: the TF32
                                   hi/lo split everywhere */,
     TCNG_OPT_STATE_ADJOINT_SMALL = 8  /* 1 (default): below TCNG_OPT_STATE_ADJOINT_N qubits, a
-                                  complex64 batch too small to occupy the GPU with the
-                                  per-item kernel (one CTA per item) takes the state-pass
-                                  adjoint when a cost model measured on a B300 says it is
-                                  faster: batch < ceil(batch / SMs) x 1.8 x 1.95^(n - 14)
-                                  (e.g. one item from 14 qubits, up to 99 items at 20);
+                                  batch too small to occupy the GPU with the per-item
+                                  kernel (one CTA per item) takes the state-pass adjoint
+                                  when a cost model measured on a B300 says it is faster:
+                                  batch < ceil(batch / SMs) x r(n), r = 1.8 x 1.95^(n - 14)
+                                  for complex64 (one item from 14 qubits, up to 99 items
+                                  at 20), min(99, 4.8 x 2^(n - 14)) for complex128;
                                   0: only the qubit threshold decides */
 } tcng_option;
 

@@ -219,15 +219,16 @@ static tcng_status run_adjoint(AdjLayout* lay, int batch, const double* params, 
     return TCNG_OK;
 }
 
-// Cost model of the two complex64 adjoint paths for a batch of one size class
-// (measured on a B300, TFIM ring ansatz, 12 layers): the per-item kernel runs one
-// item per CTA, so its time is ceil(batch / SMs) x t_item(n); the state-pass
-// adjoint takes the items one after another on the whole GPU, batch x t_state(n);
-// t_item / t_state grows about 1.95x per qubit, 1.8 at 14 qubits (0.74 / 1.0 ms
-// at 12, 9.5 / 1.4 ms at 16, 197 / 2.1 ms at 20 qubits for one item).
-bool state_path_faster(int n, int batch, int sms) {
+// Cost model of the two adjoint paths for a batch of one size class (measured on
+// a B300, TFIM ring ansatz, 12 layers): the per-item kernel runs one item per
+// CTA, so its time is ceil(batch / SMs) x t_item(n); the state-pass adjoint takes
+// the items one after another on the whole GPU, batch x t_state(n).  t_item /
+// t_state: complex64 about 1.8 x 1.95^(n - 14) (0.74 / 1.0 ms at 12 qubits, 9.5 /
+// 1.4 at 16, 197 / 2.1 at 20 for one item); complex128 about 4.8 x 2^(n - 14), at
+// most 99 (37.6 / 7.8 ms at 14, 770 / 10.1 at 18, 3422 / 34.6 at 20).
+bool state_path_faster(int n, int batch, int sms, bool c128) {
     if (n < 14) return false;
-    const double ratio = 1.8 * std::pow(1.95, n - 14);
+    const double ratio = c128 ? std::min(99.0, 4.8 * std::pow(2.0, n - 14)) : 1.8 * std::pow(1.95, n - 14);
     const double waves = (double)((batch + sms - 1) / std::max(1, sms));
     return (double)batch < waves * ratio;
 }
@@ -251,8 +252,8 @@ tcng_status tcng_energy_grad(tcng_state* st, const tcng_gate* ops, size_t n_ops,
         // single large states, and circuits with Pauli-word rotation parameters,
         // take the state-pass adjoint (one pass over psi and lambda per fused run of blocks)
         bool state_path = st->n[0] >= g_opt.state_adjoint_n ||
-                          (g_opt.state_adjoint_small && st->dt == TCNG_C64 &&
-                           state_path_faster(st->n[0], st->batch, num_sms()));
+                          (g_opt.state_adjoint_small &&
+                           state_path_faster(st->n[0], st->batch, num_sms(), st->dt == TCNG_C128));
         for (size_t i = 0; i < n_ops && !state_path; ++i)
             state_path = ops && ops[i].op == TCNG_RP && ops[i].param >= 0;
         if (state_path) {

@@ -48,8 +48,8 @@ struct Options {
     int tensor_cores = 2;     // 0 off, 1 on, 2 auto
     int state_adjoint_n = 21; // tcng_energy_grad: states of >= this many qubits use the state-pass adjoint
     int tc_fp16 = 1;          // 1: FP16-split tensor-core passes where eligible, 0: TF32 split only
-    int state_adjoint_small = 1;   // 1: small complex64 batches below state_adjoint_n take the state
-                                   // pass when the cost model says it is faster
+    int state_adjoint_small = 1;   // 1: small batches below state_adjoint_n take the state pass
+                                   // when the cost model says it is faster
 };
 extern Options g_opt;
 extern std::mutex g_mu;

@@ -177,12 +177,13 @@ def test_wide_x_term_and_multi_pass_lambda(T, dtype):
               np.abs(terms["coeff"]).sum(), dtype)
 
 
-@pytest.mark.parametrize("n,B,state", [(16, 2, True), (16, 12, False), (18, 8, True), (12, 1, False)])
-def test_small_batches_take_the_state_pass(T, n, B, state):
-    """Below the qubit threshold, complex64 batches too small for the per-item
-    kernel take the state-pass adjoint (TCNG_OPT_STATE_ADJOINT_SMALL, on by
-    default): the path taken (seen in the kernels launched) follows the cost model,
-    and both paths give the oracle's energies and gradients."""
+@pytest.mark.parametrize("n,B,state,dtype", [(16, 2, True, "c64"), (16, 12, False, "c64"), (18, 8, True, "c64"),
+                                              (12, 1, False, "c64"), (15, 6, True, "c128"), (14, 6, False, "c128")])
+def test_small_batches_take_the_state_pass(T, n, B, state, dtype):
+    """Below the qubit threshold, batches too small for the per-item kernel take
+    the state-pass adjoint (TCNG_OPT_STATE_ADJOINT_SMALL, on by default): the path
+    taken (seen in the kernels launched) follows the cost model, and both paths
+    give the oracle's energies and gradients."""
     b = gen.tfim_batch(n, B, layers=2, seed=n + B)
     g, p = b["circuit"].to_ir()
     out = {}
@@ -190,7 +191,7 @@ def test_small_batches_take_the_state_pass(T, n, B, state):
         T.tcng_set_option(T.OPT_STATE_ADJOINT_SMALL, small)
         T.tcng_profile_read(reset=True)
         T.tcng_profile_enable(True)
-        e, gr, st = energy_grad(T, n, g, p, b["theta"], b["terms"], b["coeffs"], "c64")
+        e, gr, st = energy_grad(T, n, g, p, b["theta"], b["terms"], b["coeffs"], dtype)
         T.tcng_profile_enable(False)
         used = "sa_seg_kernel" in T.tcng_profile_read(reset=True)
         assert used == (state and small == 1)
@@ -201,4 +202,4 @@ def test_small_batches_take_the_state_pass(T, n, B, state):
         e_ref = sv.energy(n, g, p, b["theta"][i], b["terms"], b["coeffs"][i])
         g_ref = sv.grad_param_shift(n, g, p, b["theta"][i], b["terms"], b["coeffs"][i])
         for small in (1, 0):
-            check(out[small][0][i], out[small][1][i], e_ref, g_ref, csum, "c64")
+            check(out[small][0][i], out[small][1][i], e_ref, g_ref, csum, dtype)
